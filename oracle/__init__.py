@@ -1,0 +1,204 @@
+"""CPU FP64 oracle for finite element assembly -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  The product library (``paper_2204_03893_gb300``)
+never imports, links or runs it; the two share no code.
+
+The arithmetic lives in ``fem_oracle.c`` (plain C, FP64): Algorithm 1 of the
+paper (element loop, quadrature loop, dense local matrices, scatter-add), the
+tangent as the Section 5.2 conductivity tensor multiplied by u in its second
+mode, and its own quadrature tables, Lagrange basis and CSR construction.
+This module compiles it with gcc and wraps it with ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fem_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+KIND = {"poly": 0, "sin": 1, "pwlin": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile fem_oracle.c into liboracle.so (plain gcc, -O2, no -ffast-math)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            dp = C.POINTER(C.c_double)
+            ip = C.POINTER(C.c_int)
+            L.oracle_rule.argtypes = [C.c_int, C.c_int, dp, dp]
+            L.oracle_rule.restype = C.c_int
+            L.oracle_basis.argtypes = [C.c_int, C.c_int, dp, dp, dp]
+            L.oracle_basis.restype = C.c_int
+            L.oracle_nlocal.argtypes = [C.c_int, C.c_int]
+            L.oracle_nlocal.restype = C.c_int
+            L.oracle_k.argtypes = [C.c_int, dp, C.c_int, C.c_double, dp]
+            L.oracle_k.restype = C.c_double
+            L.oracle_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, ip]
+            L.oracle_create.restype = C.c_void_p
+            L.oracle_destroy.argtypes = [C.c_void_p]
+            L.oracle_nnz.argtypes = [C.c_void_p]
+            L.oracle_nnz.restype = C.c_longlong
+            L.oracle_pattern.argtypes = [C.c_void_p, ip, ip]
+            L.oracle_element.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int, dp, C.c_int, dp, dp, dp, dp]
+            L.oracle_element.restype = C.c_int
+            L.oracle_geometry.argtypes = [C.c_void_p, C.c_int, dp]
+            L.oracle_geometry.restype = C.c_double
+            L.oracle_assemble.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, dp, C.c_int, dp] + [dp] * 6
+            L.oracle_assemble.restype = C.c_int
+            L.oracle_entries.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, dp, C.c_int, dp,
+                                         C.c_longlong, ip, ip] + [dp] * 6
+            L.oracle_entries.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def rule(d: int, deg: int):
+    """Quadrature rule of the given degree: (points (nq x d), weights (nq))."""
+    L = lib()
+    n = L.oracle_rule(d, deg, None, None)
+    if n < 0:
+        raise ValueError("no rule")
+    x = np.zeros((n, d))
+    w = np.zeros(n)
+    L.oracle_rule(d, deg, _dp(x), _dp(w))
+    return x, w
+
+
+def basis(d: int, p: int, xhat):
+    """Lagrange basis values (n_p) and reference gradients (n_p x d) at xhat."""
+    L = lib()
+    n = L.oracle_nlocal(d, p)
+    xh = np.ascontiguousarray(xhat, dtype=np.float64)
+    phi = np.zeros(n)
+    g = np.zeros((n, d))
+    if L.oracle_basis(d, p, _dp(xh), _dp(phi), _dp(g)) != n:
+        raise ValueError("bad element")
+    return phi, g
+
+
+def kfun(kind: str, params, u: float):
+    """(k(u), k'(u)) for a conductivity law."""
+    cp = np.ascontiguousarray(params, dtype=np.float64)
+    dk = np.zeros(1)
+    v = lib().oracle_k(KIND[kind], _dp(cp), len(cp), float(u), _dp(dk))
+    return v, float(dk[0])
+
+
+class Oracle:
+    """Oracle bound to one mesh (coords n x d float64, conn E x n_p int32)."""
+
+    def __init__(self, d: int, p: int, coords: np.ndarray, conn: np.ndarray):
+        self.d, self.p = d, p
+        self.coords = np.ascontiguousarray(coords, dtype=np.float64)
+        self.conn = np.ascontiguousarray(conn, dtype=np.int32)
+        self.n = self.coords.shape[0]
+        self.E = self.conn.shape[0]
+        self._h = lib().oracle_create(d, p, self.n, self.E, _dp(self.coords), _ip(self.conn))
+        if not self._h:
+            raise ValueError("invalid mesh")
+
+    @classmethod
+    def of(cls, mesh):
+        return cls(mesh.d, mesh.p, mesh.coords, mesh.conn)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().oracle_destroy(h)
+            self._h = None
+
+    def nnz(self) -> int:
+        return int(lib().oracle_nnz(self._h))
+
+    def pattern(self):
+        nz = self.nnz()
+        rp = np.zeros(self.n + 1, dtype=np.int32)
+        ci = np.zeros(max(nz, 1), dtype=np.int32)
+        lib().oracle_pattern(self._h, _ip(rp), _ip(ci))
+        return rp, ci[:nz]
+
+    @staticmethod
+    def _deg(deg, p):
+        return deg or 2 * p
+
+    def assemble(self, u, coeff, m: float = 1.0, deg: int = 0, want_abs: bool = True):
+        """Returns dict with 'M','K','T' (and 'absM','absK','absT') CSR values."""
+        nz = self.nnz()
+        out = {k: np.zeros(nz) for k in ("M", "K", "T")}
+        if want_abs:
+            out.update({k: np.zeros(nz) for k in ("absM", "absK", "absT")})
+        cp = coeff.numpy()
+        uu = np.ascontiguousarray(u, dtype=np.float64)
+        rc = lib().oracle_assemble(self._h, self._deg(deg, self.p), float(m), KIND[coeff.kind], _dp(cp), len(cp),
+                                   _dp(uu), _dp(out["M"]), _dp(out["K"]), _dp(out["T"]),
+                                   _dp(out.get("absM")), _dp(out.get("absK")), _dp(out.get("absT")))
+        if rc != 0:
+            raise RuntimeError(f"oracle_assemble failed ({rc})")
+        return out
+
+    def entries(self, rows, cols, u, coeff, m: float = 1.0, deg: int = 0):
+        """Selected entries computed one by one (works at any size)."""
+        r = np.ascontiguousarray(rows, dtype=np.int32)
+        c = np.ascontiguousarray(cols, dtype=np.int32)
+        n = len(r)
+        out = {k: np.zeros(n) for k in ("M", "K", "T", "absM", "absK", "absT")}
+        cp = coeff.numpy()
+        uu = np.ascontiguousarray(u, dtype=np.float64)
+        rc = lib().oracle_entries(self._h, self._deg(deg, self.p), float(m), KIND[coeff.kind], _dp(cp), len(cp),
+                                  _dp(uu), n, _ip(r), _ip(c), *[_dp(out[k]) for k in ("M", "K", "T", "absM", "absK", "absT")])
+        if rc != 0:
+            raise RuntimeError("oracle_entries failed")
+        return out
+
+    def element(self, e: int, u, coeff, m: float = 1.0, deg: int = 0):
+        """Dense local matrices (Me, Ke, Te) of element e, row = test index."""
+        np_ = self.conn.shape[1]
+        Me, Ke, Te = (np.zeros((np_, np_)) for _ in range(3))
+        cp = coeff.numpy()
+        uu = np.ascontiguousarray(u, dtype=np.float64)
+        if lib().oracle_element(self._h, int(e), self._deg(deg, self.p), float(m), KIND[coeff.kind], _dp(cp), len(cp),
+                                _dp(uu), _dp(Me), _dp(Ke), _dp(Te)) != 0:
+            raise ValueError("bad element")
+        return Me, Ke, Te
+
+    def geometry(self, e: int):
+        """(det B_e, A_e) of element e."""
+        A = np.zeros((self.d, self.d))
+        det = lib().oracle_geometry(self._h, int(e), _dp(A))
+        return det, A
+
+
+def csr_to_dense(rp, ci, vals, n):
+    """Dense matrix from CSR arrays (small n only)."""
+    D = np.zeros((n, n))
+    for r in range(n):
+        D[r, ci[rp[r]:rp[r + 1]]] = vals[rp[r]:rp[r + 1]]
+    return D

@@ -1,0 +1,571 @@
+/*
+ * fem_oracle.c -- plain, slow, obviously correct CPU reference (FP64) for
+ * the assembly of the mass matrix M, the conductivity matrix K(u) and the
+ * Newton tangent term T(u) of a scalar heat-type problem.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls, links or
+ * includes this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline leg load it.  It shares no code, header or table with the CUDA
+ * library: its quadrature tables, Lagrange basis and sparsity-pattern
+ * construction are written here independently.
+ *
+ * What it computes (Voet, "On the fast assemblage of finite element
+ * matrices with application to nonlinear heat transfer problems"):
+ *
+ *   - Algorithm 1 (classical assemblage, Section 3): a loop over elements
+ *     e, an inner loop over quadrature nodes q, dense local matrices
+ *         M_e += w_q m   phi_q phi_q^T        |det B_e|
+ *         K_e += w_q k_q J_q A_e J_q^T        |det B_e|,  A_e = (B_e^T B_e)^-1
+ *     (Section 3, steps 3-4, the "computer implementation" formulas), then
+ *     M(N_e,N_e) += M_e, K(N_e,N_e) += K_e.
+ *   - The tangent term: the conductivity tensor of Section 5.2,
+ *         C_e = sum_q w_q k'_q (J_q A_e J_q^T) o phi_q |det B_e|,
+ *     multiplied by u in its second mode (Section 5, the Jacobian
+ *     dF/du contains  (conductivity tensor) o_2 u):
+ *         T_e[i][k] = sum_j C_e[i][j][k] u_e[j]
+ *                   = sum_q w_q k'_q |det B_e| (S_q u_e)[i] phi_q[k],
+ *     with S_q = J_q A_e J_q^T; row i is the test function, column k the
+ *     trial direction.
+ *   - B_e = [x_1 - x_0, ..., x_d - x_0] (Section 3 step 3, affine map).
+ *   - Global assembly: every (row, col) pair of nodes that share an element
+ *     is a structural nonzero (Section 3 step 2); contributions are added in
+ *     ascending element order, then ascending local row, local column.
+ *
+ * Quadrature rules (Section 3 step 4 cites Gaussian simplex rules; weights
+ * here sum to the reference measure 1/2 or 1/6):
+ *   triangle: 3 points degree 2, 6 points degree 4, 12 points degree 6;
+ *   tetrahedron: 4 points degree 2, 11 points degree 4, 24 points degree 6.
+ * Lagrange basis on equispaced nodes, written with barycentric formulas.
+ *
+ * Local node order (input convention): vertices; edge nodes, edges in
+ * lexicographic order of vertex pairs (a<b), for p=3 the node nearer a first;
+ * face nodes (p=3), faces in lexicographic order of vertex triples.
+ *
+ * Conductivity laws: 0 = polynomial sum_i c_i u^i (up to 5 coefficients),
+ * 1 = alpha + beta sin(gamma u), 2 = piecewise linear through m knots
+ * (constant outside, the left knot of the first branch included in it).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXNP 20
+#define OR_MAXQ 24
+
+/* ------------------------------------------------------------------ */
+/* Quadrature: symmetric orbits on the reference simplex               */
+/* ------------------------------------------------------------------ */
+
+static int push_pt(double* xq, double* wq, int n, int d, const double* lam, double w) {
+    /* lam: barycentric coordinates (d+1); reference coordinates = lam[1..d] */
+    for (int a = 0; a < d; ++a) xq[n * d + a] = lam[a + 1];
+    wq[n] = w;
+    return n + 1;
+}
+
+/* all distinct permutations of a barycentric tuple */
+static int push_orbit(double* xq, double* wq, int n, int d, const double* base, double w) {
+    int nv = d + 1;
+    int idx[4] = {0, 1, 2, 3};
+    /* enumerate all permutations of nv items, keep distinct tuples */
+    double seen[24][4];
+    int nseen = 0;
+    int perm[24][4];
+    int np = 0;
+    if (nv == 3) {
+        int P[6][3] = {{0,1,2},{0,2,1},{1,0,2},{1,2,0},{2,0,1},{2,1,0}};
+        for (int k = 0; k < 6; ++k) { for (int a = 0; a < 3; ++a) perm[np][a] = P[k][a]; ++np; }
+    } else {
+        for (int a = 0; a < 4; ++a) for (int b = 0; b < 4; ++b) for (int c = 0; c < 4; ++c) for (int e = 0; e < 4; ++e) {
+            if (a == b || a == c || a == e || b == c || b == e || c == e) continue;
+            perm[np][0] = a; perm[np][1] = b; perm[np][2] = c; perm[np][3] = e; ++np;
+        }
+    }
+    (void)idx;
+    for (int k = 0; k < np; ++k) {
+        double t[4];
+        for (int a = 0; a < nv; ++a) t[a] = base[perm[k][a]];
+        int dup = 0;
+        for (int s = 0; s < nseen && !dup; ++s) {
+            int same = 1;
+            for (int a = 0; a < nv; ++a) if (seen[s][a] != t[a]) { same = 0; break; }
+            dup = same;
+        }
+        if (dup) continue;
+        for (int a = 0; a < nv; ++a) seen[nseen][a] = t[a];
+        ++nseen;
+        n = push_pt(xq, wq, n, d, t, w);
+    }
+    return n;
+}
+
+/* Returns the number of points of the rule of the given degree (2, 4 or 6),
+ * or -1.  xq (n x d) and wq (n) may be NULL to query the size. */
+int oracle_rule(int d, int deg, double* xq, double* wq) {
+    double xb[OR_MAXQ * 3], wb[OR_MAXQ];
+    int n = 0;
+    if (d == 2) {
+        const double area = 0.5;
+        if (deg == 2) {
+            double t[3] = {2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0};
+            n = push_orbit(xb, wb, n, 2, t, area / 3.0);
+        } else if (deg == 4) {
+            /* Strang-Fix / Dunavant 6-point rule */
+            double a1 = 0.445948490915965, w1 = 0.223381589678011;
+            double a2 = 0.091576213509771, w2 = 0.109951743655322;
+            double t1[3] = {1.0 - 2.0 * a1, a1, a1};
+            double t2[3] = {1.0 - 2.0 * a2, a2, a2};
+            n = push_orbit(xb, wb, n, 2, t1, area * w1);
+            n = push_orbit(xb, wb, n, 2, t2, area * w2);
+        } else if (deg == 6) {
+            /* Dunavant 12-point rule */
+            double a1 = 0.249286745170910, w1 = 0.116786275726379;
+            double a2 = 0.063089014491502, w2 = 0.050844906370207;
+            double b3 = 0.053145049844817, c3 = 0.310352451033784, w3 = 0.082851075618374;
+            double t1[3] = {1.0 - 2.0 * a1, a1, a1};
+            double t2[3] = {1.0 - 2.0 * a2, a2, a2};
+            double t3[3] = {b3, c3, 1.0 - b3 - c3};
+            n = push_orbit(xb, wb, n, 2, t1, area * w1);
+            n = push_orbit(xb, wb, n, 2, t2, area * w2);
+            n = push_orbit(xb, wb, n, 2, t3, area * w3);
+        } else return -1;
+    } else if (d == 3) {
+        const double vol = 1.0 / 6.0;
+        if (deg == 2) {
+            double a = (5.0 - sqrt(5.0)) / 20.0;
+            double t[4] = {1.0 - 3.0 * a, a, a, a};
+            n = push_orbit(xb, wb, n, 3, t, vol / 4.0);
+        } else if (deg == 4) {
+            /* Keast 11-point rule (one negative weight); weights for volume 1/6 */
+            double s = sqrt(5.0 / 14.0);
+            double c[4] = {0.25, 0.25, 0.25, 0.25};
+            double t1[4] = {11.0 / 14.0, 1.0 / 14.0, 1.0 / 14.0, 1.0 / 14.0};
+            double t2[4] = {(1.0 + s) / 4.0, (1.0 + s) / 4.0, (1.0 - s) / 4.0, (1.0 - s) / 4.0};
+            n = push_orbit(xb, wb, n, 3, c, -74.0 / 5625.0);
+            n = push_orbit(xb, wb, n, 3, t1, 343.0 / 45000.0);
+            n = push_orbit(xb, wb, n, 3, t2, 56.0 / 2250.0);
+        } else if (deg == 6) {
+            /* Keast 24-point rule; weights listed for volume 1, scaled below */
+            double a1 = 0.214602871259151684, w1 = 0.0399227502581679;
+            double a2 = 0.0406739585346113397, w2 = 0.0100772110553207;
+            double a3 = 0.322337890142275646, w3 = 0.0553571815436547;
+            double a4 = 0.0636610018750175299, b4 = 0.269672331458315867, w4 = 27.0 / 560.0;
+            double t1[4] = {1.0 - 3.0 * a1, a1, a1, a1};
+            double t2[4] = {1.0 - 3.0 * a2, a2, a2, a2};
+            double t3[4] = {1.0 - 3.0 * a3, a3, a3, a3};
+            double t4[4] = {1.0 - 2.0 * a4 - b4, b4, a4, a4};
+            n = push_orbit(xb, wb, n, 3, t1, vol * w1);
+            n = push_orbit(xb, wb, n, 3, t2, vol * w2);
+            n = push_orbit(xb, wb, n, 3, t3, vol * w3);
+            n = push_orbit(xb, wb, n, 3, t4, vol * w4);
+        } else return -1;
+    } else return -1;
+    if (xq) memcpy(xq, xb, sizeof(double) * n * d);
+    if (wq) memcpy(wq, wb, sizeof(double) * n);
+    return n;
+}
+
+/* ------------------------------------------------------------------ */
+/* Lagrange basis on the reference simplex (barycentric formulas)       */
+/* ------------------------------------------------------------------ */
+
+int oracle_nlocal(int d, int p) {
+    if (d == 2) return (p + 1) * (p + 2) / 2;
+    if (d == 3) return (p + 1) * (p + 2) * (p + 3) / 6;
+    return -1;
+}
+
+/* gradient (w.r.t. reference coordinates) of barycentric coordinate a */
+static void dlam(int d, int a, double* g) {
+    for (int c = 0; c < d; ++c) g[c] = (a == 0) ? -1.0 : (c == a - 1 ? 1.0 : 0.0);
+}
+
+/* Values phi[n_p] and reference gradients grad[n_p][d] at xhat[d].
+ * Returns n_p, or -1 for an unsupported (d, p). */
+int oracle_basis(int d, int p, const double* xhat, double* phi, double* grad) {
+    if ((d != 2 && d != 3) || p < 1 || p > 3) return -1;
+    int nv = d + 1;
+    double L[4], G[4][3];
+    double s = 0.0;
+    for (int a = 0; a < d; ++a) s += xhat[a];
+    L[0] = 1.0 - s;
+    for (int a = 0; a < d; ++a) L[a + 1] = xhat[a];
+    for (int a = 0; a < nv; ++a) dlam(d, a, G[a]);
+    int k = 0;
+    /* vertices */
+    for (int a = 0; a < nv; ++a, ++k) {
+        double l = L[a], f, df;
+        if (p == 1) { f = l; df = 1.0; }
+        else if (p == 2) { f = l * (2.0 * l - 1.0); df = 4.0 * l - 1.0; }
+        else { f = 0.5 * l * (3.0 * l - 1.0) * (3.0 * l - 2.0); df = 0.5 * (27.0 * l * l - 18.0 * l + 2.0); }
+        phi[k] = f;
+        for (int c = 0; c < d; ++c) grad[k * d + c] = df * G[a][c];
+    }
+    if (p >= 2) {
+        for (int a = 0; a < nv; ++a) for (int b = a + 1; b < nv; ++b) {
+            if (p == 2) {
+                phi[k] = 4.0 * L[a] * L[b];
+                for (int c = 0; c < d; ++c) grad[k * d + c] = 4.0 * (G[a][c] * L[b] + L[a] * G[b][c]);
+                ++k;
+            } else {
+                /* node nearer a: 9/2 La Lb (3La - 1); nearer b: 9/2 La Lb (3Lb - 1) */
+                for (int t = 0; t < 2; ++t) {
+                    double Ln = t == 0 ? L[a] : L[b];
+                    const double* Gn = t == 0 ? G[a] : G[b];
+                    phi[k] = 4.5 * L[a] * L[b] * (3.0 * Ln - 1.0);
+                    for (int c = 0; c < d; ++c)
+                        grad[k * d + c] = 4.5 * ((G[a][c] * L[b] + L[a] * G[b][c]) * (3.0 * Ln - 1.0)
+                                                 + L[a] * L[b] * 3.0 * Gn[c]);
+                    ++k;
+                }
+            }
+        }
+    }
+    if (p == 3) {
+        for (int a = 0; a < nv; ++a) for (int b = a + 1; b < nv; ++b) for (int e = b + 1; e < nv; ++e) {
+            phi[k] = 27.0 * L[a] * L[b] * L[e];
+            for (int c = 0; c < d; ++c)
+                grad[k * d + c] = 27.0 * (G[a][c] * L[b] * L[e] + L[a] * G[b][c] * L[e] + L[a] * L[b] * G[e][c]);
+            ++k;
+        }
+    }
+    return k;
+}
+
+/* ------------------------------------------------------------------ */
+/* Conductivity law                                                     */
+/* ------------------------------------------------------------------ */
+
+double oracle_k(int kind, const double* cp, int ncp, double u, double* dk) {
+    if (kind == 0) {
+        double v = 0.0, dv = 0.0, pw = 1.0;
+        for (int i = 0; i < ncp; ++i) {
+            v += cp[i] * pw;
+            if (i + 1 < ncp) dv += (double)(i + 1) * cp[i + 1] * pw;
+            pw *= u;
+        }
+        if (dk) *dk = dv;
+        return v;
+    }
+    if (kind == 1) {
+        if (dk) *dk = cp[1] * cp[2] * cos(cp[2] * u);
+        return cp[0] + cp[1] * sin(cp[2] * u);
+    }
+    if (kind == 2) {
+        int m = ncp / 2;
+        const double* t = cp;
+        const double* kv = cp + m;
+        if (u < t[0]) { if (dk) *dk = 0.0; return kv[0]; }
+        if (u > t[m - 1]) { if (dk) *dk = 0.0; return kv[m - 1]; }
+        int i = 0;
+        while (i + 2 < m && u > t[i + 1]) ++i;   /* branch [t_i, t_i+1] (left-closed only for i=0) */
+        double sl = (kv[i + 1] - kv[i]) / (t[i + 1] - t[i]);
+        if (dk) *dk = sl;
+        return kv[i] + sl * (u - t[i]);
+    }
+    if (dk) *dk = 0.0;
+    return 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Mesh context                                                         */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int d, p, np, n, E;
+    const double* X;     /* n x d, caller owned */
+    const int* conn;     /* E x np, caller owned */
+    /* pattern (built on demand) */
+    int* row_ptr;
+    int* col_idx;
+    long long nnz;
+    /* node -> element incidence, ascending element */
+    int* inc_ptr;
+    int* inc_el;
+} octx;
+
+void* oracle_create(int d, int p, int n_nodes, int n_elems, const double* coords, const int* conn) {
+    int np = oracle_nlocal(d, p);
+    if (np < 0 || n_nodes < 0 || n_elems < 0) return NULL;
+    for (long long k = 0; k < (long long)n_elems * np; ++k)
+        if (conn[k] < 0 || conn[k] >= n_nodes) return NULL;
+    octx* c = (octx*)calloc(1, sizeof(octx));
+    c->d = d; c->p = p; c->np = np; c->n = n_nodes; c->E = n_elems;
+    c->X = coords; c->conn = conn;
+    c->nnz = -1;
+    c->inc_ptr = (int*)calloc((size_t)n_nodes + 1, sizeof(int));
+    for (long long k = 0; k < (long long)n_elems * np; ++k) c->inc_ptr[conn[k] + 1]++;
+    for (int r = 0; r < n_nodes; ++r) c->inc_ptr[r + 1] += c->inc_ptr[r];
+    c->inc_el = (int*)malloc(sizeof(int) * ((size_t)n_elems * np + 1));
+    int* fill = (int*)calloc((size_t)n_nodes, sizeof(int));
+    for (int e = 0; e < n_elems; ++e)
+        for (int i = 0; i < np; ++i) {
+            int r = conn[(long long)e * np + i];
+            c->inc_el[c->inc_ptr[r] + fill[r]++] = e;
+        }
+    free(fill);
+    return c;
+}
+
+void oracle_destroy(void* h) {
+    octx* c = (octx*)h;
+    if (!c) return;
+    free(c->row_ptr); free(c->col_idx); free(c->inc_ptr); free(c->inc_el);
+    free(c);
+}
+
+static int cmp_ll(const void* a, const void* b) {
+    long long x = *(const long long*)a, y = *(const long long*)b;
+    return (x > y) - (x < y);
+}
+
+/* Builds the CSR pattern: all pairs (conn[e][i], conn[e][j]), sorted, unique. */
+static int build_pattern(octx* c) {
+    if (c->nnz >= 0) return 0;
+    long long m = (long long)c->E * c->np * c->np;
+    long long* keys = (long long*)malloc(sizeof(long long) * (size_t)(m > 0 ? m : 1));
+    if (!keys) return -1;
+    long long k = 0;
+    for (int e = 0; e < c->E; ++e)
+        for (int i = 0; i < c->np; ++i)
+            for (int j = 0; j < c->np; ++j)
+                keys[k++] = (long long)c->conn[(long long)e * c->np + i] * c->n + c->conn[(long long)e * c->np + j];
+    qsort(keys, (size_t)m, sizeof(long long), cmp_ll);
+    long long u = 0;
+    for (long long t = 0; t < m; ++t)
+        if (t == 0 || keys[t] != keys[t - 1]) keys[u++] = keys[t];
+    c->nnz = u;
+    c->row_ptr = (int*)calloc((size_t)c->n + 1, sizeof(int));
+    c->col_idx = (int*)malloc(sizeof(int) * (size_t)(u > 0 ? u : 1));
+    for (long long t = 0; t < u; ++t) {
+        int r = (int)(keys[t] / c->n);
+        c->row_ptr[r + 1]++;
+        c->col_idx[t] = (int)(keys[t] % c->n);
+    }
+    for (int r = 0; r < c->n; ++r) c->row_ptr[r + 1] += c->row_ptr[r];
+    free(keys);
+    return 0;
+}
+
+long long oracle_nnz(void* h) {
+    octx* c = (octx*)h;
+    if (build_pattern(c)) return -1;
+    return c->nnz;
+}
+
+void oracle_pattern(void* h, int* row_ptr, int* col_idx) {
+    octx* c = (octx*)h;
+    build_pattern(c);
+    memcpy(row_ptr, c->row_ptr, sizeof(int) * ((size_t)c->n + 1));
+    memcpy(col_idx, c->col_idx, sizeof(int) * (size_t)c->nnz);
+}
+
+/* ------------------------------------------------------------------ */
+/* Element matrices (Algorithm 1, inner loop)                           */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int nq;
+    double w[OR_MAXQ];
+    double phi[OR_MAXQ][OR_MAXNP];
+    double J[OR_MAXQ][OR_MAXNP][3];
+} otab;
+
+static int make_tab(int d, int p, int deg, otab* t) {
+    double xq[OR_MAXQ * 3];
+    int nq = oracle_rule(d, deg, xq, t->w);
+    if (nq < 0) return -1;
+    t->nq = nq;
+    for (int q = 0; q < nq; ++q) {
+        double g[OR_MAXNP * 3];
+        oracle_basis(d, p, xq + q * d, t->phi[q], g);
+        for (int i = 0; i < oracle_nlocal(d, p); ++i)
+            for (int a = 0; a < d; ++a) t->J[q][i][a] = g[i * d + a];
+    }
+    return 0;
+}
+
+/* det, |det| and A = (B^T B)^-1 = B^-1 B^-T of element e */
+static double geometry(const octx* c, int e, double A[3][3]) {
+    int d = c->d;
+    const int* v = c->conn + (long long)e * c->np;
+    double B[3][3];
+    for (int col = 0; col < d; ++col)
+        for (int row = 0; row < d; ++row)
+            B[row][col] = c->X[(long long)v[col + 1] * d + row] - c->X[(long long)v[0] * d + row];
+    double det, Bi[3][3];
+    if (d == 2) {
+        det = B[0][0] * B[1][1] - B[0][1] * B[1][0];
+        Bi[0][0] = B[1][1] / det;  Bi[0][1] = -B[0][1] / det;
+        Bi[1][0] = -B[1][0] / det; Bi[1][1] = B[0][0] / det;
+    } else {
+        double c00 = B[1][1] * B[2][2] - B[1][2] * B[2][1];
+        double c01 = B[1][2] * B[2][0] - B[1][0] * B[2][2];
+        double c02 = B[1][0] * B[2][1] - B[1][1] * B[2][0];
+        det = B[0][0] * c00 + B[0][1] * c01 + B[0][2] * c02;
+        /* inverse = adj(B)/det, adj = cofactor^T */
+        Bi[0][0] = c00 / det;
+        Bi[1][0] = c01 / det;
+        Bi[2][0] = c02 / det;
+        Bi[0][1] = (B[0][2] * B[2][1] - B[0][1] * B[2][2]) / det;
+        Bi[1][1] = (B[0][0] * B[2][2] - B[0][2] * B[2][0]) / det;
+        Bi[2][1] = (B[0][1] * B[2][0] - B[0][0] * B[2][1]) / det;
+        Bi[0][2] = (B[0][1] * B[1][2] - B[0][2] * B[1][1]) / det;
+        Bi[1][2] = (B[0][2] * B[1][0] - B[0][0] * B[1][2]) / det;
+        Bi[2][2] = (B[0][0] * B[1][1] - B[0][1] * B[1][0]) / det;
+    }
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) s += Bi[a][k] * Bi[b][k];
+            A[a][b] = s;
+        }
+    return det;
+}
+
+/* Local matrices of element e (dense n_p x n_p, row = test index). */
+static void element(const octx* c, const otab* t, int e, double m, int kkind, const double* kp, int nkp,
+                    const double* u, double* Me, double* Ke, double* Te) {
+    int np = c->np, d = c->d;
+    double A[3][3];
+    double b = fabs(geometry(c, e, A));
+    const int* v = c->conn + (long long)e * np;
+    double ue[OR_MAXNP];
+    for (int i = 0; i < np; ++i) ue[i] = u ? u[v[i]] : 0.0;
+    memset(Me, 0, sizeof(double) * np * np);
+    memset(Ke, 0, sizeof(double) * np * np);
+    memset(Te, 0, sizeof(double) * np * np);
+    for (int q = 0; q < t->nq; ++q) {
+        const double* phi = t->phi[q];
+        double uq = 0.0;
+        for (int i = 0; i < np; ++i) uq += phi[i] * ue[i];
+        double dk;
+        double kq = oracle_k(kkind, kp, nkp, uq, &dk);
+        /* S = J_q A J_q^T */
+        double JA[OR_MAXNP][3];
+        for (int i = 0; i < np; ++i)
+            for (int bb = 0; bb < d; ++bb) {
+                double s = 0.0;
+                for (int a = 0; a < d; ++a) s += t->J[q][i][a] * A[a][bb];
+                JA[i][bb] = s;
+            }
+        double S[OR_MAXNP][OR_MAXNP];
+        for (int i = 0; i < np; ++i)
+            for (int j = 0; j < np; ++j) {
+                double s = 0.0;
+                for (int a = 0; a < d; ++a) s += JA[i][a] * t->J[q][j][a];
+                S[i][j] = s;
+            }
+        double Su[OR_MAXNP];
+        for (int i = 0; i < np; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < np; ++j) s += S[i][j] * ue[j];
+            Su[i] = s;
+        }
+        double wb = t->w[q] * b;
+        for (int i = 0; i < np; ++i)
+            for (int j = 0; j < np; ++j) {
+                Me[i * np + j] += wb * m * phi[i] * phi[j];
+                Ke[i * np + j] += wb * kq * S[i][j];
+                Te[i * np + j] += wb * dk * Su[i] * phi[j];
+            }
+    }
+}
+
+/* Exported: local matrices of one element (for tests). */
+int oracle_element(void* h, int e, int deg, double m, int kkind, const double* kp, int nkp,
+                   const double* u, double* Me, double* Ke, double* Te) {
+    octx* c = (octx*)h;
+    otab t;
+    if (make_tab(c->d, c->p, deg, &t)) return -1;
+    if (e < 0 || e >= c->E) return -1;
+    element(c, &t, e, m, kkind, kp, nkp, u, Me, Ke, Te);
+    return 0;
+}
+
+/* Exported: |det B_e| and A_e (d x d row-major) of one element. */
+double oracle_geometry(void* h, int e, double* A_out) {
+    octx* c = (octx*)h;
+    double A[3][3];
+    double det = geometry(c, e, A);
+    for (int a = 0; a < c->d; ++a)
+        for (int b = 0; b < c->d; ++b) A_out[a * c->d + b] = A[a][b];
+    return det;
+}
+
+static long long find_slot(const octx* c, int r, int col) {
+    int lo = c->row_ptr[r], hi = c->row_ptr[r + 1] - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) / 2;
+        if (c->col_idx[mid] == col) return mid;
+        if (c->col_idx[mid] < col) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+/* Algorithm 1: full assembly into the CSR pattern.  Any output may be NULL. */
+int oracle_assemble(void* h, int deg, double m, int kkind, const double* kp, int nkp, const double* u,
+                    double* M, double* K, double* T, double* absM, double* absK, double* absT) {
+    octx* c = (octx*)h;
+    if (build_pattern(c)) return -1;
+    otab t;
+    if (make_tab(c->d, c->p, deg, &t)) return -1;
+    int np = c->np;
+    size_t nz = (size_t)c->nnz;
+    double* out[6] = {M, K, T, absM, absK, absT};
+    for (int k = 0; k < 6; ++k) if (out[k]) memset(out[k], 0, sizeof(double) * nz);
+    double Me[OR_MAXNP * OR_MAXNP], Ke[OR_MAXNP * OR_MAXNP], Te[OR_MAXNP * OR_MAXNP];
+    for (int e = 0; e < c->E; ++e) {
+        element(c, &t, e, m, kkind, kp, nkp, u, Me, Ke, Te);
+        const int* v = c->conn + (long long)e * np;
+        for (int i = 0; i < np; ++i)
+            for (int j = 0; j < np; ++j) {
+                long long s = find_slot(c, v[i], v[j]);
+                if (s < 0) return -2;
+                int l = i * np + j;
+                if (M) M[s] += Me[l];
+                if (K) K[s] += Ke[l];
+                if (T) T[s] += Te[l];
+                if (absM) absM[s] += fabs(Me[l]);
+                if (absK) absK[s] += fabs(Ke[l]);
+                if (absT) absT[s] += fabs(Te[l]);
+            }
+    }
+    return 0;
+}
+
+/* Selected entries (rows[k], cols[k]) computed one by one: the sum over the
+ * elements containing both nodes, in ascending element order.  Works at any
+ * mesh size without building the pattern.  Outputs may be NULL. */
+int oracle_entries(void* h, int deg, double m, int kkind, const double* kp, int nkp, const double* u,
+                   long long nq, const int* rows, const int* cols,
+                   double* M, double* K, double* T, double* absM, double* absK, double* absT) {
+    octx* c = (octx*)h;
+    otab t;
+    if (make_tab(c->d, c->p, deg, &t)) return -1;
+    int np = c->np;
+    double Me[OR_MAXNP * OR_MAXNP], Ke[OR_MAXNP * OR_MAXNP], Te[OR_MAXNP * OR_MAXNP];
+    for (long long k = 0; k < nq; ++k) {
+        int r = rows[k], col = cols[k];
+        double s[6] = {0, 0, 0, 0, 0, 0};
+        for (int p = c->inc_ptr[r]; p < c->inc_ptr[r + 1]; ++p) {
+            int e = c->inc_el[p];
+            const int* v = c->conn + (long long)e * np;
+            int i = -1, j = -1;
+            for (int a = 0; a < np; ++a) { if (v[a] == r) i = a; if (v[a] == col) j = a; }
+            if (i < 0 || j < 0) continue;
+            element(c, &t, e, m, kkind, kp, nkp, u, Me, Ke, Te);
+            int l = i * np + j;
+            s[0] += Me[l]; s[1] += Ke[l]; s[2] += Te[l];
+            s[3] += fabs(Me[l]); s[4] += fabs(Ke[l]); s[5] += fabs(Te[l]);
+        }
+        if (M) M[k] = s[0];
+        if (K) K[k] = s[1];
+        if (T) T[k] = s[2];
+        if (absM) absM[k] = s[3];
+        if (absK) absK[k] = s[4];
+        if (absT) absT[k] = s[5];
+    }
+    return 0;
+}
