@@ -1,0 +1,231 @@
+/*
+ * fem.h -- C ABI of libfem: loop-free reassembly of finite element mass,
+ * conductivity and Newton tangent matrices on one GB300 GPU (sm_103a).
+ *
+ * Method: Voet, "On the fast assemblage of finite element matrices with
+ * application to nonlinear heat transfer problems".  All element matrices of
+ * one kind come out of one tall, skinny product V = X Q (Section 4,
+ * Algorithm 2): Q depends only on the reference element and the quadrature
+ * rule, the geometric factors b_e = |det B_e| and A_e = (B_e^T B_e)^-1 only on
+ * the mesh, and the coefficient evaluations S only on the unknown u (Section
+ * 5, summary of dependencies).  The element matrices are then summed into a
+ * global CSR matrix (Algorithm 2, line 12).
+ *
+ * Conventions used by every call:
+ *  - Status: every function returns FEM_OK (0) or a negative FEM_E* code; a
+ *    message for the last failure on the calling thread is available from
+ *    fem_last_error().
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Calls that take a stream enqueue their GPU work on it
+ *    and return without synchronising unless stated otherwise.
+ *  - Memory: pointers named `d_*` must be device pointers of the current
+ *    device.  Library-owned device memory comes from the allocator set with
+ *    fem_set_allocator() (default: cudaMallocAsync/cudaFreeAsync on the
+ *    call's stream).
+ *  - Matrices: rows are test functions, columns trial functions,
+ *    M_ij = int m phi_j phi_i and K_ij = int k(u) grad phi_j . grad phi_i
+ *    (Section 2, definitions of M and of the conductivity matrix C).  The
+ *    pattern (CSR, int32, columns ascending, explicit zeros kept) is the union
+ *    over elements of all local (i, j) pairs (Section 3, step 2) and is shared
+ *    by M, K and T.
+ *  - Limits: n_elems * n_p^2 < 2^31 and nnz < 2^31.
+ */
+#ifndef FEM_H
+#define FEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+    FEM_OK = 0,
+    FEM_EINVAL = -1,      /* bad argument, shape or index */
+    FEM_ENOMEM = -2,      /* allocation failed (allocator returned NULL) */
+    FEM_EDEGENERATE = -3, /* an element has |det B_e| <= 1e-14 ||B_e||^d */
+    FEM_ECUDA = -4,       /* a CUDA runtime call or kernel launch failed */
+    FEM_EBUSY = -5,       /* admission refused (server memory budget / queue) */
+    FEM_EAGAIN = -6,      /* poll: result not ready yet */
+    FEM_ETIMEOUT = -7,    /* poll or device wait gave up after its limit */
+    FEM_ESTATE = -8       /* call out of order (e.g. assemble before symbolic) */
+};
+
+/* ------------------------------------------------------------- precision */
+enum {
+    FEM_FP64 = 0,   /* geometry, coefficients, element product and CSR sum in FP64 (SIMT) */
+    FEM_TF32X3 = 1, /* FP32 coefficients; V = X Q on tcgen05 tensor cores as three TF32
+                       products (Xhi Qhi + Xhi Qlo + Xlo Qhi), FP32 accumulate in TMEM;
+                       FP32 CSR sums */
+    FEM_FP32 = 2    /* FP32 everywhere on the SIMT pipes (no tensor cores); reference point */
+};
+
+/* -------------------------------------------------------- memory locations */
+enum { FEM_MEM_HOST = 0, FEM_MEM_DEVICE = 1 };
+
+/* ------------------------------------------------------ conductivity laws */
+enum {
+    FEM_K_POLY = 0,  /* k(u) = sum_{i<n} p[i] u^i, n <= 8 */
+    FEM_K_SIN = 1,   /* k(u) = p[0] + p[1] sin(p[2] u) */
+    FEM_K_PWLIN = 2  /* n = 2m: knots p[0..m-1] ascending, values p[m..2m-1]; linear
+                        between knots, constant outside; the first branch is closed on
+                        both ends, later branches open on the left (Section 6, Experiment 2, k(T)) */
+};
+
+/* k(u) and its derivative k'(u) are evaluated analytically from this closed
+ * description (k' enters the tangent, Section 5.2). */
+typedef struct {
+    int kind;       /* FEM_K_* */
+    int n;          /* number of parameters used */
+    double p[16];
+} fem_coeff;
+
+/* --------------------------------------------------------------- meshes */
+/* Mesh description.  Elements are affine simplices of degree `order`
+ * (Section 3 step 3: x = a + B_e xhat, B_e = [x_1 - x_0, ..., x_d - x_0]).
+ * Local node order in `conn` rows: the d+1 vertices; then edge nodes, edges
+ * in lexicographic order of their vertex pairs (a<b), for order 3 the node
+ * nearer vertex a first; then face nodes (order 3), faces in lexicographic
+ * order of their vertex triples.  Higher-order nodes must sit at the affine
+ * images of their reference positions. */
+typedef struct {
+    int dim;            /* 2 (triangles) or 3 (tetrahedra) */
+    int order;          /* Lagrange degree 1..3; n_p = C(order+dim, dim) */
+    int64_t n_nodes;    /* number of dofs (rows of the matrices) */
+    int64_t n_elems;
+    const double* coords; /* n_nodes x dim, row-major, FP64 */
+    const int32_t* conn;  /* n_elems x n_p, row-major, values in [0, n_nodes) */
+    int mem;            /* FEM_MEM_HOST or FEM_MEM_DEVICE for coords and conn */
+    int qdeg;           /* quadrature degree: 0 = 2*order (the default and only supported rule:
+                           triangles 3/6/12 points, tetrahedra 4/11/24 points) */
+    double mass_coeff;  /* constant m of the mass matrix (Section 2, eq. diff_eq) */
+} fem_mesh_desc;
+
+typedef struct fem_mesh fem_mesh;
+
+/* Creates a mesh handle: copies coords and conn to the device (the caller
+ * keeps ownership of its buffers; host buffers are read before return),
+ * checks every connectivity index (FEM_EINVAL) and computes the per-element
+ * geometric factors b_e = |det B_e| and A_e = (B_e^T B_e)^-1 once (Section 3
+ * step 3; Algorithm 2 line 4; Section 5: W and b depend only on the mesh):
+ * an FP64 cache for FEM_FP64, and an FP32 cache computed in FP32 with an FP64
+ * recomputation for elements whose condition estimate ||B||_F^d/|det B|
+ * exceeds 1e3.  Returns FEM_EDEGENERATE if an element is degenerate.
+ * Synchronises `stream` before returning. */
+int fem_mesh_create(const fem_mesh_desc* desc, void* stream, fem_mesh** out);
+int fem_mesh_destroy(fem_mesh* mesh);
+
+typedef struct {
+    int dim, order, n_p, n_q;
+    int64_t n_nodes, n_elems;
+    int64_t nnz;          /* -1 before fem_symbolic */
+    int64_t n_flagged;    /* elements recomputed in FP64 in the FP32 geometry cache */
+    size_t device_bytes;  /* library-owned device memory held by the mesh */
+} fem_mesh_info;
+int fem_mesh_get_info(const fem_mesh* mesh, fem_mesh_info* out);
+
+/* ------------------------------------------------------------- symbolic */
+typedef struct {
+    int64_t n;           /* rows = cols = n_nodes */
+    int64_t nnz;
+    const int32_t* d_row_ptr;   /* n+1, device, owned by the mesh */
+    const int32_t* d_col_idx;   /* nnz, device, owned by the mesh */
+} fem_csr_pattern;
+
+/* Builds, once per mesh, the CSR pattern and the map from element entries to
+ * CSR slots by a device sort of the keys (conn[e][i], conn[e][j]) (Section 3
+ * step 2; Algorithm 2 line 12 "the set of indices of nonzero entries"): a
+ * counting sort by row, then a per-row sort by column, stable in the element
+ * entry index c = (e n_p + i) n_p + j.  Keeps on the device: row_ptr, col_idx,
+ * slot[c] (CSR slot of element entry c) and the segmented lists seg_ptr /
+ * contrib (contributing c of every slot, ascending).  Idempotent. */
+int fem_symbolic(fem_mesh* mesh, void* stream, fem_csr_pattern* out);
+
+/* Copies the pattern into caller-owned device buffers d_row_ptr (n+1) and
+ * d_col_idx (nnz), enqueued on `stream`. */
+int fem_copy_pattern(fem_mesh* mesh, int32_t* d_row_ptr, int32_t* d_col_idx, void* stream);
+
+/* Copies the element-entry -> slot map (n_elems * n_p^2 int32, entry
+ * c = (e n_p + i) n_p + j) to d_slot (device, caller-owned). */
+int fem_get_slot_map(fem_mesh* mesh, int32_t* d_slot, void* stream);
+
+/* ------------------------------------------------------------- numeric */
+/* Reassembly of the CSR values, reusing the pattern and the geometry
+ * (Section 5: only S is recomputed at each Newton step).  For each matrix
+ * the element matrices are formed as one product V = X Q (Algorithm 2 lines
+ * 5-11; Section 4.1 mass: X = Lambda = S*(w b^T); Section 4.2 conductivity:
+ * X = Lambda (.) W; tangent: the Section 5.2 conductivity tensor multiplied
+ * by u in its second mode, T_ij = int k'(u_h) phi_j grad u_h . grad phi_i),
+ * using the symmetry of M and K to keep only the n_p(n_p+1)/2 distinct rows of
+ * Q (Section 7), then summed into the CSR values by a deterministic
+ * segmented reduction: every slot adds its contributions in ascending element
+ * entry order, with no atomics, so results are bit-reproducible run to run.
+ *
+ * u: n_nodes nodal values, FP64 for FEM_FP64 and FP32 otherwise.
+ * values: nnz outputs, FP64 for FEM_FP64 and FP32 otherwise.
+ * u and values may be device pointers or host pointers; host pointers are
+ * staged through library-owned device buffers and the call then synchronises
+ * `stream` before returning.  Requires fem_symbolic (FEM_ESTATE otherwise). */
+int fem_assemble_mass(fem_mesh* mesh, int prec, void* values, void* stream);
+int fem_assemble_stiffness(fem_mesh* mesh, const fem_coeff* k, const void* u, int prec,
+                           void* values, void* stream);
+int fem_assemble_tangent(fem_mesh* mesh, const fem_coeff* k, const void* u, int prec,
+                         void* values, void* stream);
+/* All three in one pass (any of vM, vK, vT may be NULL to skip it). */
+int fem_assemble_all(fem_mesh* mesh, const fem_coeff* k, const void* u, int prec,
+                     void* vM, void* vK, void* vT, void* stream);
+
+/* The two phases of fem_assemble_all, which the paper times separately
+ * (Section 4.2: formation of the element matrices, Algorithm 2 lines 1-11,
+ * versus assemblage of the global matrices, line 12).
+ * fem_form_elements forms V = X Q for the matrices selected by `which`
+ * (FEM_MAT_M | FEM_MAT_K | FEM_MAT_T) into scratch buffers owned by the mesh
+ * (one kernel launch); d_u is a device pointer (FP64 for FEM_FP64, FP32
+ * otherwise; unused when which == FEM_MAT_M).
+ * fem_sum_elements sums the formed V into the CSR values (one kernel
+ * launch); d_v* are device pointers, NULL to skip, and must have been formed
+ * by the last fem_form_elements with the same `prec` (FEM_ESTATE otherwise).
+ * Requires fem_symbolic. */
+enum { FEM_MAT_M = 1, FEM_MAT_K = 2, FEM_MAT_T = 4 };
+int fem_form_elements(fem_mesh* mesh, const fem_coeff* k, const void* d_u, int prec, int which,
+                      void* stream);
+int fem_sum_elements(fem_mesh* mesh, int prec, void* d_vM, void* d_vK, void* d_vT, void* stream);
+
+/* Synchronises `stream` and reports whether any library kernel recorded a
+ * device-side failure since the last call: FEM_ETIMEOUT if a tensor-core
+ * kernel gave up waiting on its MMA completion barrier (each such wait is
+ * bounded at about one second of SM clocks), FEM_OK otherwise.  Clears the
+ * record. */
+int fem_device_status(void* stream);
+
+/* ------------------------------------------------------ reference element */
+/* The library's reference tables for (dim, order, qdeg): quadrature points
+ * xq (nq x dim) and weights wq (nq, summing to 1/dim!), basis values phi
+ * (nq x n_p) and reference gradients grad (nq x n_p x dim).  Any output may
+ * be NULL; *nq receives the number of points.  Host only, no GPU needed. */
+int fem_reference_tables(int dim, int order, int qdeg, double* xq, double* wq, double* phi,
+                         double* grad, int* nq);
+
+/* ---------------------------------------------------------- allocator */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+    void* ctx;
+} fem_allocator;
+/* NULL restores the default.  Not thread-safe with concurrent calls. */
+int fem_set_allocator(const fem_allocator* a);
+
+/* ------------------------------------------------------------- errors */
+/* Copies the last error message of the calling thread into buf (always
+ * NUL-terminated); returns its full length. */
+int fem_last_error(char* buf, size_t len);
+
+/* Library version string. */
+const char* fem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEM_H */

@@ -220,29 +220,23 @@ def structured_tet(N: int, p: int = 1, alpha: float = 0.15, seed: int = 0) -> Me
     return _build_lagrange_mesh(3, p, N, vert_xyz, vidx, lat, f"tet_P{p}_N{N}")
 
 
-def sliver_tri(N: int = 8, frac: float = 0.01, seed: int = 0, pull: float = 1e-5) -> Mesh:
-    """A jitter-free structured P1 triangle mesh in which a fraction of the
-    cells have their (1,1) corner pulled to within ``pull*h`` of the
-    diagonal's opposite edge, making near-degenerate (sliver) elements.  Only
-    interior vertices are moved.  Used to exercise geometry conditioning."""
+def sliver_tri(N: int = 8, frac: float = 0.05, seed: int = 0, pull: float = 1e-5) -> Mesh:
+    """A jitter-free structured P1 triangle mesh with near-degenerate
+    (sliver) elements: for selected cells (i, j) the vertex (i+1, j) is moved
+    to within ``pull*h`` of the cell's diagonal (i,j)-(i+1,j+1), which makes
+    the cell's first triangle a sliver and keeps every other element valid.
+    Selected vertices are two cells apart so their moves do not interact."""
     m = structured_tri(N, 1, alpha=0.0, seed=seed)
     rng = np.random.default_rng(seed)
     h = 1.0 / N
     coords = m.coords.copy()
-    interior = [(i, j) for j in range(1, N) for i in range(1, N)]
-    nsel = max(1, int(round(frac * len(interior))))
-    sel = rng.choice(len(interior), size=nsel, replace=False)
+    cand = [(i, j) for j in range(1, N - 1, 2) for i in range(0, N - 2, 2)]
+    nsel = max(1, int(round(frac * len(cand))))
+    sel = rng.choice(len(cand), size=min(nsel, len(cand)), replace=False)
     for s in sel:
-        i, j = interior[s]
-        v = j * (N + 1) + i
-        # move vertex (i,j) towards the segment (i-1,j)-(i,j+1)... keep it simple:
-        # put it almost on the line x + y = (i+j)*h - h through its lower-left
-        # neighbours' diagonal, leaving a gap of pull*h.
-        x0 = coords[j * (N + 1) + (i - 1)]
-        x1 = coords[(j - 1) * (N + 1) + i]
-        mid = 0.5 * (x0 + x1)
-        nrm = np.array([1.0, 1.0]) / math.sqrt(2.0)
-        coords[v] = mid + pull * h * nrm
+        i, j = cand[s]
+        v = j * (N + 1) + (i + 1)
+        coords[v] = np.array([(i + 0.5) * h, (j + 0.5) * h]) + pull * h * np.array([1.0, -1.0]) / math.sqrt(2.0)
     return Mesh(d=2, p=1, coords=coords, conn=m.conn, name=f"sliver_N{N}")
 
 

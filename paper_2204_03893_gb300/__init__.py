@@ -1,0 +1,252 @@
+"""Python binding of libfem (include/fem.h): loop-free finite element
+reassembly of M, K(u) and the Newton tangent T(u) on one GB300 GPU.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libfem.so.  There is no CPU fallback; if the shared library is
+missing, importing the functions raises.  PyTorch is used only by the
+optional helpers in :mod:`.torch_api` for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+__all__ = [
+    "FemError", "lib", "library_path", "fem_mesh_desc", "fem_coeff", "fem_mesh_info", "fem_csr_pattern",
+    "fem_allocator", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_get_info", "fem_symbolic",
+    "fem_get_slot_map", "fem_copy_pattern", "fem_assemble_mass", "fem_assemble_stiffness", "fem_assemble_tangent",
+    "fem_assemble_all", "fem_reference_tables", "fem_set_allocator", "fem_last_error", "fem_version",
+    "fem_device_status", "fem_form_elements", "fem_sum_elements", "coeff", "FEM_MAT_M", "FEM_MAT_K", "FEM_MAT_T", "FEM_OK", "FEM_EINVAL", "FEM_ENOMEM", "FEM_EDEGENERATE", "FEM_ECUDA",
+    "FEM_EBUSY", "FEM_EAGAIN", "FEM_ETIMEOUT", "FEM_ESTATE", "FEM_FP64", "FEM_TF32X3", "FEM_FP32",
+    "FEM_MEM_HOST", "FEM_MEM_DEVICE", "FEM_K_POLY", "FEM_K_SIN", "FEM_K_PWLIN",
+]
+
+FEM_OK, FEM_EINVAL, FEM_ENOMEM, FEM_EDEGENERATE, FEM_ECUDA = 0, -1, -2, -3, -4
+FEM_EBUSY, FEM_EAGAIN, FEM_ETIMEOUT, FEM_ESTATE = -5, -6, -7, -8
+FEM_FP64, FEM_TF32X3, FEM_FP32 = 0, 1, 2
+FEM_MEM_HOST, FEM_MEM_DEVICE = 0, 1
+FEM_K_POLY, FEM_K_SIN, FEM_K_PWLIN = 0, 1, 2
+FEM_MAT_M, FEM_MAT_K, FEM_MAT_T = 1, 2, 4
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def library_path() -> str:
+    return os.environ.get("FEM_LIBRARY", os.path.join(_HERE, "libfem.so"))
+
+
+class FemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libfem error {code}: {msg}")
+        self.code = code
+
+
+class fem_mesh_desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("order", C.c_int), ("n_nodes", C.c_int64), ("n_elems", C.c_int64),
+                ("coords", C.c_void_p), ("conn", C.c_void_p), ("mem", C.c_int), ("qdeg", C.c_int),
+                ("mass_coeff", C.c_double)]
+
+
+class fem_coeff(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n", C.c_int), ("p", C.c_double * 16)]
+
+
+class fem_mesh_info(C.Structure):
+    _fields_ = [("dim", C.c_int), ("order", C.c_int), ("n_p", C.c_int), ("n_q", C.c_int),
+                ("n_nodes", C.c_int64), ("n_elems", C.c_int64), ("nnz", C.c_int64), ("n_flagged", C.c_int64),
+                ("device_bytes", C.c_size_t)]
+
+
+class fem_csr_pattern(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("d_row_ptr", C.c_void_p), ("d_col_idx", C.c_void_p)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class fem_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    "fem_mesh_create": ([C.POINTER(fem_mesh_desc), C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
+    "fem_mesh_destroy": ([C.c_void_p], C.c_int),
+    "fem_mesh_get_info": ([C.c_void_p, C.POINTER(fem_mesh_info)], C.c_int),
+    "fem_symbolic": ([C.c_void_p, C.c_void_p, C.POINTER(fem_csr_pattern)], C.c_int),
+    "fem_get_slot_map": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "fem_copy_pattern": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "fem_assemble_mass": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "fem_assemble_stiffness": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+                               C.c_int),
+    "fem_assemble_tangent": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+                             C.c_int),
+    "fem_assemble_all": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                          C.c_void_p, C.c_void_p], C.c_int),
+    "fem_device_status": ([C.c_void_p], C.c_int),
+    "fem_form_elements": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_int, C.c_void_p], C.c_int),
+    "fem_sum_elements": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "fem_reference_tables": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.POINTER(C.c_int)], C.c_int),
+    "fem_set_allocator": ([C.POINTER(fem_allocator)], C.c_int),
+    "fem_last_error": ([C.c_char_p, C.c_size_t], C.c_int),
+    "fem_version": ([], C.c_char_p),
+}
+
+
+def lib() -> C.CDLL:
+    """Loads libfem.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise FemError(FEM_EINVAL, f"{path} not found: build it with paper_2204_03893_gb300.build.build()")
+            L = C.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _err() -> str:
+    buf = C.create_string_buffer(1024)
+    lib().fem_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int) -> int:
+    if rc != FEM_OK:
+        raise FemError(rc, _err())
+    return rc
+
+
+def _vp(x):
+    """Pointer argument: int address, None, a ctypes object or an object
+    exposing data_ptr() (torch tensors) or .ctypes (numpy arrays)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    return C.cast(x, C.c_void_p).value
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return getattr(s, "cuda_stream", s)
+
+
+def coeff(kind: str, params) -> fem_coeff:
+    """fem_coeff from ('poly'|'sin'|'pwlin', parameters)."""
+    c = fem_coeff()
+    c.kind = {"poly": FEM_K_POLY, "sin": FEM_K_SIN, "pwlin": FEM_K_PWLIN}[kind]
+    params = list(params)
+    if kind == "poly":
+        while len(params) > 1 and params[-1] == 0.0:
+            params.pop()
+    c.n = len(params)
+    for i, v in enumerate(params):
+        c.p[i] = float(v)
+    return c
+
+
+# ------------------------------------------------------------------ calls
+def fem_mesh_create(desc: fem_mesh_desc, stream=None) -> int:
+    h = C.c_void_p()
+    _check(lib().fem_mesh_create(C.byref(desc), _stream(stream), C.byref(h)))
+    return h.value
+
+
+def fem_mesh_destroy(mesh: int) -> None:
+    _check(lib().fem_mesh_destroy(mesh))
+
+
+def fem_mesh_get_info(mesh: int) -> fem_mesh_info:
+    info = fem_mesh_info()
+    _check(lib().fem_mesh_get_info(mesh, C.byref(info)))
+    return info
+
+
+def fem_symbolic(mesh: int, stream=None) -> fem_csr_pattern:
+    pat = fem_csr_pattern()
+    _check(lib().fem_symbolic(mesh, _stream(stream), C.byref(pat)))
+    return pat
+
+
+def fem_copy_pattern(mesh: int, d_row_ptr, d_col_idx, stream=None) -> None:
+    _check(lib().fem_copy_pattern(mesh, _vp(d_row_ptr), _vp(d_col_idx), _stream(stream)))
+
+
+def fem_get_slot_map(mesh: int, d_slot, stream=None) -> None:
+    _check(lib().fem_get_slot_map(mesh, _vp(d_slot), _stream(stream)))
+
+
+def fem_assemble_mass(mesh: int, prec: int, values, stream=None) -> None:
+    _check(lib().fem_assemble_mass(mesh, prec, _vp(values), _stream(stream)))
+
+
+def fem_assemble_stiffness(mesh: int, k: fem_coeff, u, prec: int, values, stream=None) -> None:
+    _check(lib().fem_assemble_stiffness(mesh, C.byref(k), _vp(u), prec, _vp(values), _stream(stream)))
+
+
+def fem_assemble_tangent(mesh: int, k: fem_coeff, u, prec: int, values, stream=None) -> None:
+    _check(lib().fem_assemble_tangent(mesh, C.byref(k), _vp(u), prec, _vp(values), _stream(stream)))
+
+
+def fem_assemble_all(mesh: int, k, u, prec: int, vM, vK, vT, stream=None) -> None:
+    _check(lib().fem_assemble_all(mesh, C.byref(k) if k is not None else None, _vp(u), prec, _vp(vM), _vp(vK),
+                                  _vp(vT), _stream(stream)))
+
+
+def fem_form_elements(mesh: int, k, d_u, prec: int, which: int, stream=None) -> None:
+    _check(lib().fem_form_elements(mesh, C.byref(k) if k is not None else None, _vp(d_u), prec, which,
+                                   _stream(stream)))
+
+
+def fem_sum_elements(mesh: int, prec: int, d_vM, d_vK, d_vT, stream=None) -> None:
+    _check(lib().fem_sum_elements(mesh, prec, _vp(d_vM), _vp(d_vK), _vp(d_vT), _stream(stream)))
+
+
+def fem_device_status(stream=None) -> None:
+    _check(lib().fem_device_status(_stream(stream)))
+
+
+def fem_reference_tables(dim: int, order: int, qdeg: int = 0):
+    """(xq, wq, phi, grad) of the library's reference element as numpy arrays."""
+    import numpy as np
+    nq = C.c_int()
+    _check(lib().fem_reference_tables(dim, order, qdeg, None, None, None, None, C.byref(nq)))
+    n = nq.value
+    np_ = {2: (order + 1) * (order + 2) // 2, 3: (order + 1) * (order + 2) * (order + 3) // 6}[dim]
+    xq = np.zeros((n, dim))
+    wq = np.zeros(n)
+    phi = np.zeros((n, np_))
+    grad = np.zeros((n, np_, dim))
+    _check(lib().fem_reference_tables(dim, order, qdeg, xq.ctypes.data, wq.ctypes.data, phi.ctypes.data,
+                                      grad.ctypes.data, C.byref(nq)))
+    return xq, wq, phi, grad
+
+
+def fem_set_allocator(alloc: fem_allocator | None) -> None:
+    _check(lib().fem_set_allocator(C.byref(alloc) if alloc is not None else None))
+
+
+def fem_last_error() -> str:
+    return _err()
+
+
+def fem_version() -> str:
+    return lib().fem_version().decode()

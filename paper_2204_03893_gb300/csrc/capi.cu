@@ -1,0 +1,422 @@
+// capi.cu -- the extern "C" boundary of libfem (see include/fem.h).
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "fem_internal.h"
+#include "refelem.h"
+
+namespace fem {
+
+namespace {
+thread_local std::string g_last_error;
+fem_allocator g_alloc = {nullptr, nullptr, nullptr};
+std::mutex g_alloc_mu;
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int code, const std::string& msg) {
+    set_error(msg);
+    return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return FEM_ECUDA;
+}
+
+void* dev_alloc(size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    fem_allocator a;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+    }
+    if (a.alloc) return a.alloc(bytes, s, a.ctx);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void* p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    fem_allocator a;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+    }
+    if (a.free) a.free(p, bytes, s, a.ctx);
+    else cudaFreeAsync(p, s);
+}
+
+int buf_alloc(DevBuf& b, size_t bytes, cudaStream_t s) {
+    if (b.ptr && b.bytes >= bytes) return FEM_OK;
+    buf_free(b, s);
+    b.ptr = dev_alloc(bytes, s);
+    if (!b.ptr) return fail(FEM_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    b.bytes = bytes;
+    return FEM_OK;
+}
+
+void buf_free(DevBuf& b, cudaStream_t s) {
+    if (b.ptr) dev_free(b.ptr, b.bytes, s);
+    b.ptr = nullptr;
+    b.bytes = 0;
+}
+
+int tc_error_flag(int clear);
+
+namespace {
+
+int type_of(int d, int p) { return (d - 2) * 3 + (p - 1); }
+int nlocal(int d, int p) { return d == 2 ? (p + 1) * (p + 2) / 2 : (p + 1) * (p + 2) * (p + 3) / 6; }
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int check_coeff(const fem_coeff* k) {
+    if (!k) return fail(FEM_EINVAL, "coefficient is NULL");
+    if (k->kind == FEM_K_POLY) {
+        if (k->n < 1 || k->n > 8) return fail(FEM_EINVAL, "polynomial law needs 1..8 coefficients");
+    } else if (k->kind == FEM_K_SIN) {
+        if (k->n != 3) return fail(FEM_EINVAL, "sine law needs 3 parameters");
+    } else if (k->kind == FEM_K_PWLIN) {
+        if (k->n < 4 || k->n > 16 || (k->n & 1)) return fail(FEM_EINVAL, "piecewise-linear law needs 2m parameters, m in 2..8");
+        int m = k->n / 2;
+        for (int i = 0; i + 1 < m; ++i)
+            if (!(k->p[i] < k->p[i + 1])) return fail(FEM_EINVAL, "knots must be strictly ascending");
+    } else {
+        return fail(FEM_EINVAL, "unknown conductivity law");
+    }
+    for (int i = 0; i < k->n; ++i)
+        if (!std::isfinite(k->p[i])) return fail(FEM_EINVAL, "non-finite coefficient parameter");
+    return FEM_OK;
+}
+
+CoeffDev to_dev(const fem_coeff* k) {
+    CoeffDev c;
+    std::memset(&c, 0, sizeof(c));
+    if (!k) return c;
+    c.kind = k->kind;
+    c.n = k->n;
+    for (int i = 0; i < 16; ++i) c.p[i] = k->p[i];
+    return c;
+}
+
+// Formation (Algorithm 2 lines 1-11): V for the matrices in `mask` (bit 0 M,
+// bit 1 K, bit 2 T) into the mesh's scratch buffers.
+template <typename T>
+int form_t(fem_mesh* m, const fem_coeff* k, const T* ud, int prec, int mask, cudaStream_t s) {
+    const int64_t E = m->E;
+    const int nsym = m->np * (m->np + 1) / 2, nt = m->np * m->np;
+    int rc;
+    T *VM = nullptr, *VK = nullptr, *VT = nullptr;
+    if (mask & 1) {
+        if ((rc = buf_alloc(m->VM, sizeof(T) * (size_t)E * nsym, s))) return rc;
+        VM = m->VM.as<T>();
+    }
+    if (mask & 2) {
+        if ((rc = buf_alloc(m->VK, sizeof(T) * (size_t)E * nsym, s))) return rc;
+        VK = m->VK.as<T>();
+    }
+    if (mask & 4) {
+        if ((rc = buf_alloc(m->VT, sizeof(T) * (size_t)E * nt, s))) return rc;
+        VT = m->VT.as<T>();
+    }
+    CoeffDev kd = to_dev(k);
+    if constexpr (sizeof(T) == 8) {
+        rc = element_simt_fp64(*m, kd, ud, VM, VK, VT, s);
+    } else {
+        rc = prec == FEM_TF32X3 ? element_tc_tf32x3(*m, kd, ud, VM, VK, VT, s)
+                                : element_simt_fp32(*m, kd, ud, VM, VK, VT, s);
+    }
+    if (rc) return rc;
+    m->v_prec = prec;
+    m->v_mask = mask;
+    return FEM_OK;
+}
+
+// Global assembly (Algorithm 2 line 12) of the formed V into CSR values.
+template <typename T>
+int sum_t(fem_mesh* m, T* vM, T* vK, T* vT, cudaStream_t s) {
+    const T* VM = vM ? m->VM.as<T>() : nullptr;
+    const T* VK = vK ? m->VK.as<T>() : nullptr;
+    const T* VT = vT ? m->VT.as<T>() : nullptr;
+    if constexpr (sizeof(T) == 8) return scatter_fp64(*m, VM, VK, VT, vM, vK, vT, s);
+    else return scatter_fp32(*m, VM, VK, VT, vM, vK, vT, s);
+}
+
+template <typename T>
+int assemble_t(fem_mesh* m, const fem_coeff* k, const void* u, int prec, void* vM, void* vK, void* vT,
+               cudaStream_t s) {
+    const int64_t nnz = m->nnz;
+    bool host_io = false;
+    const T* ud = nullptr;
+    int rc;
+    if (vK || vT) {
+        if (!u) return fail(FEM_EINVAL, "u is NULL");
+        if (is_device_ptr(u)) {
+            ud = static_cast<const T*>(u);
+        } else {
+            host_io = true;
+            if ((rc = buf_alloc(m->u_stage, sizeof(T) * (size_t)m->n, s))) return rc;
+            FEM_CUDA_TRY(cudaMemcpyAsync(m->u_stage.ptr, u, sizeof(T) * (size_t)m->n, cudaMemcpyHostToDevice, s));
+            ud = m->u_stage.as<T>();
+        }
+    }
+    void* outs[3] = {vM, vK, vT};
+    T* outd[3] = {nullptr, nullptr, nullptr};
+    bool out_host[3] = {false, false, false};
+    int nhost = 0;
+    for (int i = 0; i < 3; ++i)
+        if (outs[i] && !is_device_ptr(outs[i])) {
+            out_host[i] = true;
+            ++nhost;
+        }
+    if (nhost) {
+        host_io = true;
+        if ((rc = buf_alloc(m->out_stage, sizeof(T) * (size_t)nnz * 3, s))) return rc;
+    }
+    for (int i = 0; i < 3; ++i)
+        if (outs[i]) outd[i] = out_host[i] ? m->out_stage.as<T>() + (size_t)i * nnz : static_cast<T*>(outs[i]);
+    int mask = (vM ? 1 : 0) | (vK ? 2 : 0) | (vT ? 4 : 0);
+    if ((rc = form_t<T>(m, k, ud, prec, mask, s))) return rc;
+    if ((rc = sum_t<T>(m, outd[0], outd[1], outd[2], s))) return rc;
+    for (int i = 0; i < 3; ++i)
+        if (out_host[i])
+            FEM_CUDA_TRY(cudaMemcpyAsync(outs[i], outd[i], sizeof(T) * (size_t)nnz, cudaMemcpyDeviceToHost, s));
+    if (host_io) FEM_CUDA_TRY(cudaStreamSynchronize(s));
+    return FEM_OK;
+}
+
+}  // namespace
+}  // namespace fem
+
+size_t fem_mesh::device_bytes() const {
+    const fem::DevBuf* bufs[] = {&coords, &conn, &geo64, &geo32, &row_ptr, &col_idx, &seg_ptr, &contrib, &slot,
+                                 &inc_ptr, &inc, &VM, &VK, &VT, &u_stage, &out_stage};
+    size_t t = 0;
+    for (auto* b : bufs) t += b->bytes;
+    return t;
+}
+
+using namespace fem;
+
+extern "C" {
+
+int fem_last_error(char* buf, size_t len) {
+    const std::string& e = g_last_error;
+    if (buf && len) {
+        size_t n = e.size() < len - 1 ? e.size() : len - 1;
+        std::memcpy(buf, e.data(), n);
+        buf[n] = 0;
+    }
+    return (int)e.size();
+}
+
+const char* fem_version(void) { return "libfem 0.1 (sm_103a, tcgen05 TF32x3)"; }
+
+int fem_set_allocator(const fem_allocator* a) {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (a && (!a->alloc || !a->free)) return fail(FEM_EINVAL, "allocator needs both alloc and free");
+    g_alloc = a ? *a : fem_allocator{nullptr, nullptr, nullptr};
+    return FEM_OK;
+}
+
+int fem_reference_tables(int dim, int order, int qdeg, double* xq, double* wq, double* phi, double* grad, int* nq) {
+    if ((dim != 2 && dim != 3) || order < 1 || order > 3) return fail(FEM_EINVAL, "dim must be 2|3, order 1..3");
+    if (qdeg != 0 && qdeg != 2 * order) return fail(FEM_EINVAL, "only the degree-2*order rule is provided");
+    const RefElem* R = refelem_for_type(type_of(dim, order));
+    if (!R) return fail(FEM_EINVAL, "reference tables failed");
+    if (nq) *nq = R->nq;
+    if (xq) std::memcpy(xq, R->xq.data(), sizeof(double) * R->xq.size());
+    if (wq) std::memcpy(wq, R->wq.data(), sizeof(double) * R->wq.size());
+    if (phi) std::memcpy(phi, R->phi.data(), sizeof(double) * R->phi.size());
+    if (grad) std::memcpy(grad, R->grad.data(), sizeof(double) * R->grad.size());
+    return FEM_OK;
+}
+
+int fem_mesh_create(const fem_mesh_desc* desc, void* stream, fem_mesh** out) {
+    if (!desc || !out) return fail(FEM_EINVAL, "NULL argument");
+    *out = nullptr;
+    const int d = desc->dim, p = desc->order;
+    if ((d != 2 && d != 3) || p < 1 || p > 3) return fail(FEM_EINVAL, "dim must be 2|3 and order 1..3");
+    if (desc->qdeg != 0 && desc->qdeg != 2 * p) return fail(FEM_EINVAL, "only the degree-2*order rule is provided");
+    if (desc->n_nodes <= 0 || desc->n_nodes >= (int64_t)INT32_MAX || desc->n_elems < 0)
+        return fail(FEM_EINVAL, "bad node or element count");
+    const int np = nlocal(d, p);
+    if ((desc->n_elems * np * np) >= ((int64_t)1 << 31)) return fail(FEM_EINVAL, "n_elems * n_p^2 must be < 2^31");
+    if (!desc->coords || (desc->n_elems > 0 && !desc->conn)) return fail(FEM_EINVAL, "coords/conn is NULL");
+    if (!std::isfinite(desc->mass_coeff)) return fail(FEM_EINVAL, "mass coefficient not finite");
+    if (!refelem_for_type(type_of(d, p))) return fail(FEM_EINVAL, "reference tables failed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    fem_mesh* m = new fem_mesh;
+    m->d = d;
+    m->p = p;
+    m->np = np;
+    m->type = type_of(d, p);
+    m->nq = type_nq(m->type);
+    m->n = desc->n_nodes;
+    m->E = desc->n_elems;
+    m->m = desc->mass_coeff;
+    cudaGetDevice(&m->device);
+    int rc;
+    if ((rc = buf_alloc(m->coords, sizeof(double) * (size_t)m->n * d, s)) ||
+        (rc = buf_alloc(m->conn, sizeof(int) * (size_t)m->E * np, s))) {
+        fem_mesh_destroy(m);
+        return rc;
+    }
+    cudaError_t e = cudaMemcpyAsync(m->coords.ptr, desc->coords, sizeof(double) * (size_t)m->n * d, cudaMemcpyDefault, s);
+    if (e == cudaSuccess && m->E > 0)
+        e = cudaMemcpyAsync(m->conn.ptr, desc->conn, sizeof(int) * (size_t)m->E * np, cudaMemcpyDefault, s);
+    if (e != cudaSuccess) {
+        fem_mesh_destroy(m);
+        return cuda_fail(e, "copy mesh to device");
+    }
+    if ((rc = geometry_run(*m, s))) {
+        std::string msg = g_last_error;
+        fem_mesh_destroy(m);
+        set_error(msg);
+        return rc;
+    }
+    *out = m;
+    return FEM_OK;
+}
+
+int fem_mesh_destroy(fem_mesh* m) {
+    if (!m) return FEM_OK;
+    cudaDeviceSynchronize();
+    fem::DevBuf* bufs[] = {&m->coords, &m->conn, &m->geo64, &m->geo32, &m->row_ptr, &m->col_idx, &m->seg_ptr,
+                           &m->contrib, &m->slot, &m->inc_ptr, &m->inc, &m->VM, &m->VK, &m->VT, &m->u_stage,
+                           &m->out_stage};
+    for (auto* b : bufs) buf_free(*b, nullptr);
+    cudaDeviceSynchronize();
+    delete m;
+    return FEM_OK;
+}
+
+int fem_mesh_get_info(const fem_mesh* m, fem_mesh_info* out) {
+    if (!m || !out) return fail(FEM_EINVAL, "NULL argument");
+    out->dim = m->d;
+    out->order = m->p;
+    out->n_p = m->np;
+    out->n_q = m->nq;
+    out->n_nodes = m->n;
+    out->n_elems = m->E;
+    out->nnz = m->have_pattern ? m->nnz : -1;
+    out->n_flagged = m->n_flagged;
+    out->device_bytes = m->device_bytes();
+    return FEM_OK;
+}
+
+int fem_symbolic(fem_mesh* m, void* stream, fem_csr_pattern* out) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!m->have_pattern) {
+        int rc = symbolic_run(*m, s);
+        if (rc) return rc;
+    }
+    if (out) {
+        out->n = m->n;
+        out->nnz = m->nnz;
+        out->d_row_ptr = m->row_ptr.as<int32_t>();
+        out->d_col_idx = m->col_idx.as<int32_t>();
+    }
+    return FEM_OK;
+}
+
+int fem_copy_pattern(fem_mesh* m, int32_t* d_row_ptr, int32_t* d_col_idx, void* stream) {
+    if (!m || !d_row_ptr || !d_col_idx) return fail(FEM_EINVAL, "NULL argument");
+    if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_row_ptr, m->row_ptr.ptr, sizeof(int32_t) * (size_t)(m->n + 1),
+                                 cudaMemcpyDeviceToDevice, s));
+    if (m->nnz > 0)
+        FEM_CUDA_TRY(cudaMemcpyAsync(d_col_idx, m->col_idx.ptr, sizeof(int32_t) * (size_t)m->nnz,
+                                     cudaMemcpyDeviceToDevice, s));
+    return FEM_OK;
+}
+
+int fem_get_slot_map(fem_mesh* m, int32_t* d_slot, void* stream) {
+    if (!m || !d_slot) return fail(FEM_EINVAL, "NULL argument");
+    if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_slot, m->slot.ptr, sizeof(int32_t) * (size_t)(m->E * m->np * m->np),
+                                 cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+    return FEM_OK;
+}
+
+int fem_assemble_all(fem_mesh* m, const fem_coeff* k, const void* u, int prec, void* vM, void* vK, void* vT,
+                     void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    if (prec != FEM_FP64 && prec != FEM_TF32X3 && prec != FEM_FP32) return fail(FEM_EINVAL, "unknown precision");
+    if (!vM && !vK && !vT) return FEM_OK;
+    if ((vK || vT)) {
+        int rc = check_coeff(k);
+        if (rc) return rc;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (prec == FEM_FP64) return assemble_t<double>(m, k, u, prec, vM, vK, vT, s);
+    return assemble_t<float>(m, k, u, prec, vM, vK, vT, s);
+}
+
+int fem_form_elements(fem_mesh* m, const fem_coeff* k, const void* d_u, int prec, int which, void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (prec != FEM_FP64 && prec != FEM_TF32X3 && prec != FEM_FP32) return fail(FEM_EINVAL, "unknown precision");
+    if (which <= 0 || which > 7) return fail(FEM_EINVAL, "which must be a nonzero mask of FEM_MAT_M|K|T");
+    if (which & 6) {
+        int rc = check_coeff(k);
+        if (rc) return rc;
+        if (!d_u) return fail(FEM_EINVAL, "u is NULL");
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (prec == FEM_FP64) return form_t<double>(m, k, static_cast<const double*>(d_u), prec, which, s);
+    return form_t<float>(m, k, static_cast<const float*>(d_u), prec, which, s);
+}
+
+int fem_sum_elements(fem_mesh* m, int prec, void* d_vM, void* d_vK, void* d_vT, void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    int mask = (d_vM ? 1 : 0) | (d_vK ? 2 : 0) | (d_vT ? 4 : 0);
+    if (!mask) return FEM_OK;
+    if (m->v_prec != prec || (m->v_mask & mask) != mask)
+        return fail(FEM_ESTATE, "element matrices of this precision were not formed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (prec == FEM_FP64)
+        return sum_t<double>(m, static_cast<double*>(d_vM), static_cast<double*>(d_vK), static_cast<double*>(d_vT), s);
+    return sum_t<float>(m, static_cast<float*>(d_vM), static_cast<float*>(d_vK), static_cast<float*>(d_vT), s);
+}
+
+int fem_assemble_mass(fem_mesh* m, int prec, void* values, void* stream) {
+    if (!values) return fail(FEM_EINVAL, "values is NULL");
+    return fem_assemble_all(m, nullptr, nullptr, prec, values, nullptr, nullptr, stream);
+}
+
+int fem_assemble_stiffness(fem_mesh* m, const fem_coeff* k, const void* u, int prec, void* values, void* stream) {
+    if (!values) return fail(FEM_EINVAL, "values is NULL");
+    return fem_assemble_all(m, k, u, prec, nullptr, values, nullptr, stream);
+}
+
+int fem_assemble_tangent(fem_mesh* m, const fem_coeff* k, const void* u, int prec, void* values, void* stream) {
+    if (!values) return fail(FEM_EINVAL, "values is NULL");
+    return fem_assemble_all(m, k, u, prec, nullptr, nullptr, values, stream);
+}
+
+int fem_device_status(void* stream) {
+    FEM_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int f = tc_error_flag(1);
+    if (f < 0) return fail(FEM_ECUDA, "cannot read device status word");
+    if (f) return fail(FEM_ETIMEOUT, "a tensor-core kernel gave up waiting for its MMA completion");
+    return FEM_OK;
+}
+
+}  // extern "C"

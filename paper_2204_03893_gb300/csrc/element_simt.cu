@@ -1,0 +1,222 @@
+// element_simt.cu -- element products V = X Q on the SIMT pipes (FP64 and
+// FP32), one thread per element.
+//
+// Algorithm 2 lines 5-11: the coefficient evaluations S at the quadrature
+// points (here k(u_q), k'(u_q) from u_q = phi_q . u_e), Lambda = S * (w b^T)
+// (eq. def_lambda, computed as w_q S_qe b_e in place), X_m = Lambda and
+// X_c = Lambda (.) W (Section 4.2), then V = Q X.  The tangent uses the same
+// shape with X_T[q][a] = w_q b_e k'(u_q) (A_e ghat_q)[a], which contracts the
+// Section 5.2 conductivity tensor with u in its second mode.  Only the
+// n_p(n_p+1)/2 distinct entries of the symmetric M and K are formed
+// (Section 7).  V is written element-major: V[e][n].
+#include <mutex>
+#include <vector>
+
+#include "fem_internal.h"
+#include "refelem.h"
+
+namespace fem {
+
+namespace {
+
+__host__ __device__ constexpr int q_size(int t) {
+    return type_nq(t) * (type_np(t) * (type_np(t) + 1) / 2) * (1 + type_d(t) * (type_d(t) + 1) / 2) +
+           type_nq(t) * type_d(t) * type_np(t) * type_np(t);
+}
+__host__ __device__ constexpr int q_off(int t) { return t == 0 ? 0 : q_off(t - 1) + q_size(t - 1); }
+constexpr int Q_TOTAL = q_off(6);
+
+__constant__ double c_ref64[TAB_TOTAL];
+__constant__ float c_ref32[TAB_TOTAL];
+__device__ double g_Q64[Q_TOTAL];
+__device__ float g_Q32[Q_TOTAL];
+
+template <typename T>
+struct Tabs;
+template <>
+struct Tabs<double> {
+    static __device__ __forceinline__ double ref(int i) { return c_ref64[i]; }
+    static __device__ __forceinline__ const double* Q() { return g_Q64; }
+};
+template <>
+struct Tabs<float> {
+    static __device__ __forceinline__ float ref(int i) { return c_ref32[i]; }
+    static __device__ __forceinline__ const float* Q() { return g_Q32; }
+};
+
+constexpr int BT = 64;   // elements (threads) per block
+
+template <typename ETy, typename T>
+__global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict__ conn, const T* __restrict__ geo,
+                                                          int64_t E, const T* __restrict__ u, CoeffDev k, T mass,
+                                                          T* __restrict__ VM, T* __restrict__ VK,
+                                                          T* __restrict__ VT) {
+    constexpr int D = ETy::D, NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS;
+    constexpr int KM = ETy::KM, KK = ETy::KK, KT = ETy::KT;
+    constexpr int KTOT = KM + KK + KT;
+    constexpr int LD = KTOT | 1;   // odd row stride: conflict-free per-thread rows
+    constexpr int TO = type_tab_off(ETy::TYPE);
+    constexpr int PHI = TO, GR = TO + NQ * NP, WQ = TO + NQ * NP * (1 + D);
+    constexpr int QO = q_off(ETy::TYPE);
+    constexpr int QM_O = QO, QK_O = QO + KM * ETy::NSYM, QT_O = QK_O + KK * ETy::NSYM;
+    extern __shared__ unsigned char smem_raw[];
+    T* X = reinterpret_cast<T*>(smem_raw) + threadIdx.x * LD;
+
+    const T* Q = Tabs<T>::Q();
+    for (int64_t e0 = (int64_t)blockIdx.x * BT; e0 < E; e0 += (int64_t)gridDim.x * BT) {
+        int64_t e = e0 + threadIdx.x;
+        if (e >= E) continue;
+        T ue[NP];
+        const int* ce = conn + e * NP;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) ue[i] = u[ce[i]];
+        T b = geo[e];
+        T A[NS];
+#pragma unroll
+        for (int t = 0; t < NS; ++t) A[t] = geo[(1 + t) * E + e];
+        // --- X = Lambda, Lambda (.) W, tangent factors
+#pragma unroll 1
+        for (int q = 0; q < NQ; ++q) {
+            T uq = T(0);
+            T g[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) g[a] = T(0);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                uq += Tabs<T>::ref(PHI + q * NP + i) * ue[i];
+#pragma unroll
+                for (int a = 0; a < D; ++a) g[a] += Tabs<T>::ref(GR + (q * NP + i) * D + a) * ue[i];
+            }
+            T dk;
+            T kq = k_eval<T>(k, uq, dk);
+            T lam = Tabs<T>::ref(WQ + q) * b;
+            X[q] = mass * lam;
+            T lk = lam * kq;
+#pragma unroll
+            for (int t = 0; t < NS; ++t) X[KM + q * NS + t] = lk * A[t];
+            // A ghat, A symmetric stored as upper triangle
+            T ld = lam * dk;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                T s = T(0);
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    int lo = a < c ? a : c, hi = a < c ? c : a;
+                    int t = lo * D - (lo * (lo - 1)) / 2 + (hi - lo);
+                    s += A[t] * g[c];
+                }
+                X[KM + KK + q * D + a] = ld * s;
+            }
+        }
+        // --- V = X Q, chunks of CH outputs
+        constexpr int CH = 8;
+        auto product = [&](const T* Xs, int K, const T* Qm, int N, T* V) {
+#pragma unroll 1
+            for (int n0 = 0; n0 < N; n0 += CH) {
+                T acc[CH];
+#pragma unroll
+                for (int c = 0; c < CH; ++c) acc[c] = T(0);
+#pragma unroll 2
+                for (int kk = 0; kk < K; ++kk) {
+                    T x = Xs[kk];
+                    const T* qrow = Qm + kk * N + n0;
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+                        if (n0 + c < N) acc[c] += x * qrow[c];
+                }
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    if (n0 + c < N) V[e * N + n0 + c] = acc[c];
+            }
+        };
+        if (VM) product(X, KM, Q + QM_O, ETy::NSYM, VM);
+        if (VK) product(X + KM, KK, Q + QK_O, ETy::NSYM, VK);
+        if (VT) product(X + KM + KK, KT, Q + QT_O, ETy::NT, VT);
+    }
+}
+
+template <typename ETy, typename T>
+int launch_simt(const fem_mesh& m, const CoeffDev& k, const T* u, const T* geo, T* VM, T* VK, T* VT,
+                cudaStream_t s) {
+    constexpr int KTOT = ETy::KM + ETy::KK + ETy::KT;
+    constexpr int LD = KTOT | 1;
+    size_t smem = sizeof(T) * (size_t)LD * BT;
+    auto kern = element_simt_kernel<ETy, T>;
+    FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, nsm = 0, per_sm = 0;
+    FEM_CUDA_TRY(cudaGetDevice(&dev));
+    FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t tiles = (m.E + BT - 1) / BT;
+    int64_t grid = (int64_t)nsm * per_sm;
+    if (grid > tiles) grid = tiles;
+    if (grid < 1) return FEM_OK;
+    kern<<<(unsigned)grid, BT, smem, s>>>(m.conn.as<int>(), geo, m.E, u, k, (T)m.m, VM, VK, VT);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+template <typename T>
+int dispatch(const fem_mesh& m, const CoeffDev& k, const T* u, const T* geo, T* VM, T* VK, T* VT, cudaStream_t s) {
+    switch (m.type) {
+        case 0: return launch_simt<ET<2, 1>, T>(m, k, u, geo, VM, VK, VT, s);
+        case 1: return launch_simt<ET<2, 2>, T>(m, k, u, geo, VM, VK, VT, s);
+        case 2: return launch_simt<ET<2, 3>, T>(m, k, u, geo, VM, VK, VT, s);
+        case 3: return launch_simt<ET<3, 1>, T>(m, k, u, geo, VM, VK, VT, s);
+        case 4: return launch_simt<ET<3, 2>, T>(m, k, u, geo, VM, VK, VT, s);
+        case 5: return launch_simt<ET<3, 3>, T>(m, k, u, geo, VM, VK, VT, s);
+    }
+    return fail(FEM_EINVAL, "element type");
+}
+
+std::mutex g_init_mu;
+bool g_init_done[64] = {};
+
+}  // namespace
+
+int tables_init_simt() {
+    int dev = 0;
+    FEM_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    if (dev < 64 && g_init_done[dev]) return FEM_OK;
+    std::vector<double> ref64(TAB_TOTAL, 0.0), q64(Q_TOTAL, 0.0);
+    for (int t = 0; t < 6; ++t) {
+        const RefElem* R = refelem_for_type(t);
+        if (!R) return fail(FEM_EINVAL, "reference element tables failed");
+        int o = type_tab_off(t);
+        int nq = R->nq, np = R->np, d = R->d;
+        for (int i = 0; i < nq * np; ++i) ref64[o + i] = R->phi[i];
+        for (int i = 0; i < nq * np * d; ++i) ref64[o + nq * np + i] = R->grad[i];
+        for (int i = 0; i < nq; ++i) ref64[o + nq * np * (1 + d) + i] = R->wq[i];
+        int qo = q_off(t);
+        size_t a = R->QM.size(), b = R->QK.size(), c = R->QT.size();
+        if ((int)(a + b + c) != q_size(t)) return fail(FEM_EINVAL, "Q size mismatch");
+        std::copy(R->QM.begin(), R->QM.end(), q64.begin() + qo);
+        std::copy(R->QK.begin(), R->QK.end(), q64.begin() + qo + a);
+        std::copy(R->QT.begin(), R->QT.end(), q64.begin() + qo + a + b);
+    }
+    std::vector<float> ref32(ref64.begin(), ref64.end()), q32(q64.begin(), q64.end());
+    FEM_CUDA_TRY(cudaMemcpyToSymbol(c_ref64, ref64.data(), sizeof(double) * TAB_TOTAL));
+    FEM_CUDA_TRY(cudaMemcpyToSymbol(c_ref32, ref32.data(), sizeof(float) * TAB_TOTAL));
+    FEM_CUDA_TRY(cudaMemcpyToSymbol(g_Q64, q64.data(), sizeof(double) * Q_TOTAL));
+    FEM_CUDA_TRY(cudaMemcpyToSymbol(g_Q32, q32.data(), sizeof(float) * Q_TOTAL));
+    if (dev < 64) g_init_done[dev] = true;
+    return FEM_OK;
+}
+
+int element_simt_fp64(const fem_mesh& m, const CoeffDev& k, const double* u, double* VM, double* VK, double* VT,
+                      cudaStream_t s) {
+    int rc = tables_init_simt();
+    if (rc) return rc;
+    return dispatch<double>(m, k, u, m.geo64.as<double>(), VM, VK, VT, s);
+}
+
+int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const float* u, float* VM, float* VK, float* VT,
+                      cudaStream_t s) {
+    int rc = tables_init_simt();
+    if (rc) return rc;
+    return dispatch<float>(m, k, u, m.geo32.as<float>(), VM, VK, VT, s);
+}
+
+}  // namespace fem

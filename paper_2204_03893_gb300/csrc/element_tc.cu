@@ -1,0 +1,412 @@
+// element_tc.cu -- element products V = X Q on the tcgen05 tensor cores
+// (TF32 x3 split precision, FP32 accumulation in tensor memory).
+//
+// Algorithm 2 lines 5-11 for a tile of 128 elements: every thread forms the
+// X row of one element (Lambda = S * (w b^T) in place, eq. def_lambda;
+// X_c = Lambda (.) W, Section 4.2; the tangent factors of the Section 5.2
+// tensor multiplied by u) and stores it, split as X = Xhi + Xlo with Xhi,
+// Xlo exact TF32 values, straight into the K-major shared-memory operand
+// layout.  Q (reference element only, "computed and stored once and for
+// all", Section 4.1) sits in shared memory for the whole persistent CTA,
+// split the same way.  One thread issues, per K step of 8,
+//     D += Xhi Qhi ; D += Xhi Qlo ; D += Xlo Qhi
+// for M, K and T into separate TMEM column ranges (D: 128 lanes = elements,
+// columns = entries), commits to an mbarrier, and the four warps read their
+// 32 lanes back with tcgen05.ld, transpose through shared memory and write V
+// element-major with coalesced 128-byte rows.  Only the n_p(n_p+1)/2 distinct
+// entries of M and K are formed (Section 7).
+//
+// Every mbarrier wait is bounded (~1 s of SM clocks); on timeout the kernel
+// records an error word, stops, and releases its tensor memory.
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "fem_internal.h"
+#include "refelem.h"
+#include "tc_ptx.cuh"
+
+namespace fem {
+
+namespace {
+
+__host__ __device__ constexpr int ru(int x, int m) { return (x + m - 1) / m * m; }
+__host__ __device__ constexpr int pow2_at_least(int x) {
+    int p = 32;
+    while (p < x) p *= 2;
+    return p;
+}
+
+constexpr int TILE = 128;
+constexpr int STAGE_FLOATS = 4 * 32 * 33;
+constexpr int SMEM_MAX = 227 * 1024;
+constexpr int IMG_SLOT_FLOATS = 24 * 1024;   // 96 KiB per element type
+
+template <typename ETy>
+struct TcL {
+    static constexpr int KMp = ru(ETy::KM, 8), KKp = ru(ETy::KK, 8), KTp = ru(ETy::KT, 8);
+    static constexpr int NMp = ru(ETy::NSYM, 16), NTp = ru(ETy::NT, 16);
+    static constexpr int COLM = 0, COLK = NMp, COLT = 2 * NMp, COLS = 2 * NMp + NTp;
+    static constexpr int ALLOC = pow2_at_least(COLS);
+    // shared-memory byte offsets: Q image, then X tile
+    static constexpr int QMh = 0;
+    static constexpr int QMl = QMh + NMp * KMp * 4;
+    static constexpr int QKh = QMl + NMp * KMp * 4;
+    static constexpr int QKl = QKh + NMp * KKp * 4;
+    static constexpr int QTh = QKl + NMp * KKp * 4;
+    static constexpr int QTl = QTh + NTp * KTp * 4;
+    static constexpr int QEND = QTl + NTp * KTp * 4;
+    static constexpr int XMh = 0;
+    static constexpr int XMl = XMh + TILE * KMp * 4;
+    static constexpr int XKh = XMl + TILE * KMp * 4;
+    static constexpr int XKl = XKh + TILE * KKp * 4;
+    static constexpr int XTh = XKl + TILE * KKp * 4;
+    static constexpr int XTl = XTh + TILE * KTp * 4;
+    static constexpr int XEND = XTl + TILE * KTp * 4;
+    static constexpr int SMEM = QEND + XEND;
+    // epilogue reads whole 32-column chunks: they must stay inside the allocation
+    static constexpr bool FITS = NMp <= 256 && NTp <= 256 && ALLOC <= 512 && SMEM <= SMEM_MAX &&
+                                 XEND >= STAGE_FLOATS * 4 && QEND <= IMG_SLOT_FLOATS * 4 &&
+                                 COLM + ru(ETy::NSYM, 32) <= ALLOC && COLK + ru(ETy::NSYM, 32) <= ALLOC &&
+                                 COLT + ru(ETy::NT, 32) <= ALLOC;
+};
+
+__constant__ float c_tcref[TAB_TOTAL];
+__device__ float g_tcimg[6 * IMG_SLOT_FLOATS];
+__device__ int g_tc_err;
+
+constexpr long long WAIT_LIMIT = 2000000000LL;   // SM clocks (~1 s)
+
+// store one thread's X row (Kp values) as TF32 hi / lo parts
+template <int Kp>
+__device__ __forceinline__ void store_row(unsigned char* hi, unsigned char* lo, const float (&x)[Kp], int r) {
+    constexpr uint32_t sbo = (Kp / 4) * 128;
+    unsigned char* ph = hi + (r >> 3) * sbo + (r & 7) * 16;
+    unsigned char* pl = lo + (r >> 3) * sbo + (r & 7) * 16;
+#pragma unroll
+    for (int c = 0; c < Kp / 4; ++c) {
+        float4 h, l;
+        h.x = tc::tf32_rna(x[4 * c + 0]);
+        h.y = tc::tf32_rna(x[4 * c + 1]);
+        h.z = tc::tf32_rna(x[4 * c + 2]);
+        h.w = tc::tf32_rna(x[4 * c + 3]);
+        l.x = tc::tf32_rna(x[4 * c + 0] - h.x);
+        l.y = tc::tf32_rna(x[4 * c + 1] - h.y);
+        l.z = tc::tf32_rna(x[4 * c + 2] - h.z);
+        l.w = tc::tf32_rna(x[4 * c + 3] - h.w);
+        *reinterpret_cast<float4*>(ph + c * 128) = h;
+        *reinterpret_cast<float4*>(pl + c * 128) = l;
+    }
+}
+
+// D[dcol..] = sum over K steps of (Xhi Qhi + Xhi Qlo + Xlo Qhi)
+template <int Kp>
+__device__ __forceinline__ void issue_tf32x3(uint32_t tmem_d, uint32_t xh, uint32_t xl, uint32_t qh, uint32_t ql,
+                                             uint32_t idesc) {
+    constexpr uint32_t sbo = (Kp / 4) * 128;
+#pragma unroll
+    for (int ks = 0; ks < Kp / 8; ++ks) {
+        uint64_t ah = tc::smem_desc(xh + ks * 256, 128, sbo);
+        uint64_t al = tc::smem_desc(xl + ks * 256, 128, sbo);
+        uint64_t bh = tc::smem_desc(qh + ks * 256, 128, sbo);
+        uint64_t bl = tc::smem_desc(ql + ks * 256, 128, sbo);
+        tc::mma_tf32(tmem_d, ah, bh, idesc, ks > 0 ? 1u : 0u);
+        tc::mma_tf32(tmem_d, ah, bl, idesc, 1u);
+        tc::mma_tf32(tmem_d, al, bh, idesc, 1u);
+    }
+}
+
+// TMEM (this warp's 32 lanes, columns col..col+N) -> V rows, coalesced
+template <int N>
+__device__ __forceinline__ void epilogue(uint32_t tmem, int col, float* stage, float* __restrict__ V, int64_t row0,
+                                         int64_t E, int warp, int lane) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < N; c0 += 32) {
+        uint32_t r[32];
+        tc::tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + col + c0, r);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
+        __syncwarp();
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+            int64_t er = row0 + rr;
+            int c = c0 + lane;
+            if (er < E && c < N) V[er * N + c] = stage[rr * 33 + lane];
+        }
+        __syncwarp();
+    }
+}
+
+template <typename ETy>
+__global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict__ conn, const float* __restrict__ geo,
+                                                          int64_t E, const float* __restrict__ u, CoeffDev k,
+                                                          float mass, float* __restrict__ VM, float* __restrict__ VK,
+                                                          float* __restrict__ VT, const float* __restrict__ img,
+                                                          int* __restrict__ err) {
+    using L = TcL<ETy>;
+    constexpr int D = ETy::D, NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS;
+    constexpr int TO = type_tab_off(ETy::TYPE);
+    constexpr int PHI = TO, GR = TO + NQ * NP, WQ = TO + NQ * NP * (1 + D);
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* sQ = smem;
+    unsigned char* sX = smem + L::QEND;
+
+    {   // resident Q image
+        const int4* src = reinterpret_cast<const int4*>(img);
+        int4* dst = reinterpret_cast<int4*>(sQ);
+        for (int i = tid; i < L::QEND / 16; i += TILE) dst[i] = src[i];
+    }
+    const uint32_t mb = tc::smem_u32(&mbar);
+    if (tid == 0) {
+        tc::mbar_init(mb, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(&tmem_slot), L::ALLOC);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t sQu = tc::smem_u32(sQ), sXu = tc::smem_u32(sX);
+    const bool doM = VM != nullptr, doK = VK != nullptr, doT = VT != nullptr;
+    float* stage = reinterpret_cast<float*>(sX) + warp * 32 * 33;
+    uint32_t phase = 0;
+    bool timed_out = false;
+
+    const int64_t ntiles = (E + TILE - 1) / TILE;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t e = tile * TILE + tid;
+        float xm[L::KMp], xk[L::KKp], xt[L::KTp];
+#pragma unroll
+        for (int i = 0; i < L::KMp; ++i) xm[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < L::KKp; ++i) xk[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < L::KTp; ++i) xt[i] = 0.f;
+        if (e < E) {
+            const int* ce = conn + e * NP;
+            float ue[NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) ue[i] = __ldg(u + __ldg(ce + i));
+            const float b = __ldg(geo + e);
+            float A[NS];
+#pragma unroll
+            for (int t = 0; t < NS; ++t) A[t] = __ldg(geo + (1 + t) * E + e);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                float uq = 0.f, g[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) g[a] = 0.f;
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    uq = fmaf(c_tcref[PHI + q * NP + i], ue[i], uq);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) g[a] = fmaf(c_tcref[GR + (q * NP + i) * D + a], ue[i], g[a]);
+                }
+                float dk;
+                const float kq = k_eval<float>(k, uq, dk);
+                const float lam = c_tcref[WQ + q] * b;
+                xm[q] = mass * lam;
+                const float lk = lam * kq;
+#pragma unroll
+                for (int t = 0; t < NS; ++t) xk[q * NS + t] = lk * A[t];
+                const float ld = lam * dk;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    float s = 0.f;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        const int lo = a < c ? a : c, hi = a < c ? c : a;
+                        s = fmaf(A[lo * D - (lo * (lo - 1)) / 2 + (hi - lo)], g[c], s);
+                    }
+                    xt[q * D + a] = ld * s;
+                }
+            }
+        }
+        if (doM) store_row<L::KMp>(sX + L::XMh, sX + L::XMl, xm, tid);
+        if (doK) store_row<L::KKp>(sX + L::XKh, sX + L::XKl, xk, tid);
+        if (doT) store_row<L::KTp>(sX + L::XTh, sX + L::XTl, xt, tid);
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            if (doM)
+                issue_tf32x3<L::KMp>(tmem + L::COLM, sXu + L::XMh, sXu + L::XMl, sQu + L::QMh, sQu + L::QMl,
+                                     tc::idesc_tf32(L::NMp));
+            if (doK)
+                issue_tf32x3<L::KKp>(tmem + L::COLK, sXu + L::XKh, sXu + L::XKl, sQu + L::QKh, sQu + L::QKl,
+                                     tc::idesc_tf32(L::NMp));
+            if (doT)
+                issue_tf32x3<L::KTp>(tmem + L::COLT, sXu + L::XTh, sXu + L::XTl, sQu + L::QTh, sQu + L::QTl,
+                                     tc::idesc_tf32(L::NTp));
+            tc::mma_commit(mb);
+        }
+        const uint32_t ok = tc::mbar_wait_bounded(mb, phase, WAIT_LIMIT);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        tc::fence_after_sync();
+        const int64_t row0 = tile * TILE + warp * 32;
+        if (doM) epilogue<ETy::NSYM>(tmem, L::COLM, stage, VM, row0, E, warp, lane);
+        if (doK) epilogue<ETy::NSYM>(tmem, L::COLK, stage, VK, row0, E, warp, lane);
+        if (doT) epilogue<ETy::NT>(tmem, L::COLT, stage, VT, row0, E, warp, lane);
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (timed_out) {
+        if (tid == 0) atomicExch(err, 1);
+        // give in-flight tensor-core work one more bounded chance to drain
+        tc::mbar_wait_bounded(mb, phase ^ 1u, WAIT_LIMIT);
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, L::ALLOC);
+}
+
+// host-side TF32 rounding, nearest with ties away from zero (matches cvt.rna)
+float tf32_rna_host(float x) {
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    if ((b & 0x7F800000u) != 0x7F800000u) {
+        b += 0x1000u;
+        b &= 0xFFFFE000u;
+    }
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
+}
+
+// Q (K x N, FP64, row-major) -> B operand image (N x Kp, K-major core matrices), hi and lo
+void put_operand(std::vector<float>& img, int off_hi, int off_lo, const std::vector<double>& Q, int K, int N, int Kp) {
+    const int sbo = (Kp / 4) * 128;
+    for (int n = 0; n < N; ++n)
+        for (int kk = 0; kk < K; ++kk) {
+            double v = Q[(size_t)kk * N + n];
+            float hi = tf32_rna_host((float)v);
+            float lo = tf32_rna_host((float)(v - (double)hi));
+            int byte = (n >> 3) * sbo + (kk >> 2) * 128 + (n & 7) * 16 + (kk & 3) * 4;
+            img[(off_hi + byte) / 4] = hi;
+            img[(off_lo + byte) / 4] = lo;
+        }
+}
+
+template <typename ETy>
+void build_image(std::vector<float>& all, const RefElem& R) {
+    using L = TcL<ETy>;
+    std::vector<float> img(IMG_SLOT_FLOATS, 0.f);
+    if constexpr (L::FITS) {
+        put_operand(img, L::QMh, L::QMl, R.QM, ETy::KM, ETy::NSYM, L::KMp);
+        put_operand(img, L::QKh, L::QKl, R.QK, ETy::KK, ETy::NSYM, L::KKp);
+        put_operand(img, L::QTh, L::QTl, R.QT, ETy::KT, ETy::NT, L::KTp);
+    }
+    std::copy(img.begin(), img.end(), all.begin() + (size_t)ETy::TYPE * IMG_SLOT_FLOATS);
+}
+
+std::mutex g_mu;
+bool g_done[64] = {};
+
+template <typename ETy>
+int launch_tc(const fem_mesh& m, const CoeffDev& k, const float* u, float* VM, float* VK, float* VT,
+              cudaStream_t s) {
+    using L = TcL<ETy>;
+    if constexpr (!L::FITS) {
+        return fail(FEM_EINVAL, "FEM_TF32X3 is not available for this element type (tile does not fit)");
+    } else {
+        if (m.E == 0) return FEM_OK;
+        auto kern = element_tc_kernel<ETy>;
+        int smem = L::SMEM;
+        FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX));
+        int dev = 0, nsm = 0, occ = 0;
+        FEM_CUDA_TRY(cudaGetDevice(&dev));
+        FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+        const int occ_max = 512 / L::ALLOC;   // co-resident CTAs must fit their TMEM columns
+        if (occ > occ_max) {
+            // ask for enough shared memory that at most occ_max CTAs fit on an SM
+            smem = SMEM_MAX / (occ_max + 1) + 1024;
+            if (smem > SMEM_MAX) smem = SMEM_MAX;
+            FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+            if (occ > occ_max) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
+        }
+        if (occ < 1) return fail(FEM_ECUDA, "tensor-core kernel does not fit on an SM");
+        int64_t ntiles = (m.E + TILE - 1) / TILE;
+        int64_t grid = (int64_t)nsm * occ;
+        if (grid > ntiles) grid = ntiles;
+        float* img = nullptr;
+        FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&img, g_tcimg));
+        int* err = nullptr;
+        FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&err, g_tc_err));
+        kern<<<(unsigned)grid, TILE, smem, s>>>(m.conn.as<int>(), m.geo32.as<float>(), m.E, u, k, (float)m.m, VM, VK,
+                                                VT, img + (size_t)ETy::TYPE * IMG_SLOT_FLOATS, err);
+        FEM_CUDA_TRY(cudaGetLastError());
+        return FEM_OK;
+    }
+}
+
+}  // namespace
+
+int tables_init_tc() {
+    int dev = 0;
+    FEM_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (dev < 64 && g_done[dev]) return FEM_OK;
+    std::vector<float> ref(TAB_TOTAL, 0.f), img((size_t)6 * IMG_SLOT_FLOATS, 0.f);
+    for (int t = 0; t < 6; ++t) {
+        const RefElem* R = refelem_for_type(t);
+        if (!R) return fail(FEM_EINVAL, "reference element tables failed");
+        int o = type_tab_off(t);
+        for (int i = 0; i < R->nq * R->np; ++i) ref[o + i] = (float)R->phi[i];
+        for (int i = 0; i < R->nq * R->np * R->d; ++i) ref[o + R->nq * R->np + i] = (float)R->grad[i];
+        for (int i = 0; i < R->nq; ++i) ref[o + R->nq * R->np * (1 + R->d) + i] = (float)R->wq[i];
+        switch (t) {
+            case 0: build_image<ET<2, 1>>(img, *R); break;
+            case 1: build_image<ET<2, 2>>(img, *R); break;
+            case 2: build_image<ET<2, 3>>(img, *R); break;
+            case 3: build_image<ET<3, 1>>(img, *R); break;
+            case 4: build_image<ET<3, 2>>(img, *R); break;
+            case 5: build_image<ET<3, 3>>(img, *R); break;
+        }
+    }
+    FEM_CUDA_TRY(cudaMemcpyToSymbol(c_tcref, ref.data(), sizeof(float) * TAB_TOTAL));
+    FEM_CUDA_TRY(cudaMemcpyToSymbol(g_tcimg, img.data(), sizeof(float) * img.size()));
+    int zero = 0;
+    FEM_CUDA_TRY(cudaMemcpyToSymbol(g_tc_err, &zero, sizeof(int)));
+    if (dev < 64) g_done[dev] = true;
+    return FEM_OK;
+}
+
+int tc_error_flag(int clear) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_err, sizeof(int)) != cudaSuccess) return -1;
+    if (clear && v) {
+        int zero = 0;
+        cudaMemcpyToSymbol(g_tc_err, &zero, sizeof(int));
+    }
+    return v;
+}
+
+int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const float* u, float* VM, float* VK, float* VT,
+                      cudaStream_t s) {
+    int rc = tables_init_tc();
+    if (rc) return rc;
+    switch (m.type) {
+        case 0: return launch_tc<ET<2, 1>>(m, k, u, VM, VK, VT, s);
+        case 1: return launch_tc<ET<2, 2>>(m, k, u, VM, VK, VT, s);
+        case 2: return launch_tc<ET<2, 3>>(m, k, u, VM, VK, VT, s);
+        case 3: return launch_tc<ET<3, 1>>(m, k, u, VM, VK, VT, s);
+        case 4: return launch_tc<ET<3, 2>>(m, k, u, VM, VK, VT, s);
+        case 5: return launch_tc<ET<3, 3>>(m, k, u, VM, VK, VT, s);
+    }
+    return fail(FEM_EINVAL, "element type");
+}
+
+}  // namespace fem

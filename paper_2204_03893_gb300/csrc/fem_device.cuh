@@ -1,0 +1,97 @@
+// fem_device.cuh -- element-type traits, reference-table access and the
+// conductivity law, shared by the device kernels of libfem.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fem {
+
+// Element type (dimension D, Lagrange degree P) with the default quadrature
+// rule of degree 2P.  Index conventions of the element product V = X Q:
+//   sym(i,j), i<=j : row-major upper triangle of an n_p x n_p matrix
+//                    (Section 7: only the distinct rows of Q are kept)
+//   t(a,b),  a<=b  : upper triangle of the d x d matrix A_e
+//   X_M[q]         = m w_q b_e                                  (Section 4.1)
+//   X_K[q*NS+t]    = w_q b_e k(u_q) A_e[a][b]                   (Section 4.2)
+//   X_T[q*D+a]     = w_q b_e k'(u_q) (A_e ghat_q)[a]           (Section 5.2 o_2 u)
+//   Q_M[q][sym]    = phi_q[i] phi_q[j]
+//   Q_K[q*NS+t][sym] = G_q[i][a] G_q[j][b] (+ G_q[i][b] G_q[j][a] if a != b)
+//   Q_T[q*D+a][i*NP+j] = G_q[i][a] phi_q[j]
+// with G_q the reference basis gradients (the paper's J_q) and ghat_q the
+// reference gradient of u_h at x_q.
+template <int D_, int P_>
+struct ET {
+    static constexpr int D = D_;
+    static constexpr int P = P_;
+    static constexpr int NP = (D == 2) ? (P + 1) * (P + 2) / 2 : (P + 1) * (P + 2) * (P + 3) / 6;
+    static constexpr int NQ = (D == 2) ? (P == 1 ? 3 : P == 2 ? 6 : 12) : (P == 1 ? 4 : P == 2 ? 11 : 24);
+    static constexpr int NS = D * (D + 1) / 2;
+    static constexpr int NSYM = NP * (NP + 1) / 2;
+    static constexpr int NT = NP * NP;
+    static constexpr int KM = NQ;
+    static constexpr int KK = NQ * NS;
+    static constexpr int KT = NQ * D;
+    static constexpr int TYPE = (D - 2) * 3 + (P - 1);   // 0..5
+    static constexpr int NGEO = 1 + NS;                  // b_e, A_e (upper triangle)
+};
+
+__host__ __device__ constexpr int type_nq(int t) {
+    return t == 0 ? 3 : t == 1 ? 6 : t == 2 ? 12 : t == 3 ? 4 : t == 4 ? 11 : 24;
+}
+__host__ __device__ constexpr int type_np(int t) {
+    return t == 0 ? 3 : t == 1 ? 6 : t == 2 ? 10 : t == 3 ? 4 : t == 4 ? 10 : 20;
+}
+__host__ __device__ constexpr int type_d(int t) { return t < 3 ? 2 : 3; }
+// per type: phi (NQ*NP), G (NQ*NP*D), w (NQ)
+__host__ __device__ constexpr int type_tab_size(int t) {
+    return type_nq(t) * type_np(t) * (1 + type_d(t)) + type_nq(t);
+}
+__host__ __device__ constexpr int type_tab_off(int t) {
+    return t == 0 ? 0 : type_tab_off(t - 1) + type_tab_size(t - 1);
+}
+constexpr int TAB_TOTAL = type_tab_off(6);
+
+__host__ __device__ constexpr int sym_index(int np, int i, int j) {
+    // i <= j
+    return i * np - (i * (i - 1)) / 2 + (j - i);
+}
+
+// Conductivity law (mirrors fem_coeff).
+struct CoeffDev {
+    int kind;
+    int n;
+    double p[16];
+};
+
+template <typename T>
+__device__ __forceinline__ T k_eval(const CoeffDev& c, T u, T& dk) {
+    if (c.kind == 0) {
+        T v = T(0), dv = T(0);
+        for (int i = c.n - 1; i >= 0; --i) {
+            dv = dv * u + v;      // Horner for the derivative uses the running value
+            v = v * u + T(c.p[i]);
+        }
+        dk = dv;
+        return v;
+    } else if (c.kind == 1) {
+        T g = T(c.p[2]);
+        T s, co;
+        if constexpr (sizeof(T) == 8) { sincos(g * u, &s, &co); }
+        else { sincosf(g * u, &s, &co); }
+        dk = T(c.p[1]) * g * co;
+        return T(c.p[0]) + T(c.p[1]) * s;
+    } else {
+        int m = c.n / 2;
+        const double* t = c.p;
+        const double* kv = c.p + m;
+        if (u < T(t[0])) { dk = T(0); return T(kv[0]); }
+        if (u > T(t[m - 1])) { dk = T(0); return T(kv[m - 1]); }
+        int i = 0;
+        while (i + 2 < m && u > T(t[i + 1])) ++i;
+        T sl = T((kv[i + 1] - kv[i]) / (t[i + 1] - t[i]));
+        dk = sl;
+        return T(kv[i]) + sl * (u - T(t[i]));
+    }
+}
+
+}  // namespace fem

@@ -1,0 +1,85 @@
+// fem_internal.h -- host-side internals shared by the libfem translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/fem.h"
+#include "fem_device.cuh"
+
+namespace fem {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+#define FEM_CUDA_TRY(call)                                   \
+    do {                                                     \
+        cudaError_t _e = (call);                             \
+        if (_e != cudaSuccess) return ::fem::cuda_fail(_e, #call); \
+    } while (0)
+
+// ------------------------------------------------------------- allocation
+void* dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void* p, size_t bytes, cudaStream_t s);
+
+// Tracks one library-owned device buffer.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    template <typename T>
+    T* as() const { return static_cast<T*>(ptr); }
+};
+int buf_alloc(DevBuf& b, size_t bytes, cudaStream_t s);   // FEM_OK / FEM_ENOMEM
+void buf_free(DevBuf& b, cudaStream_t s);
+
+}  // namespace fem
+
+// The mesh handle (opaque to callers).
+struct fem_mesh {
+    int d = 0, p = 0, np = 0, nq = 0, type = 0, device = 0;
+    int64_t n = 0, E = 0;
+    double m = 1.0;
+    fem::DevBuf coords, conn;           // FP64 n x d, int32 E x np
+    fem::DevBuf geo64, geo32;           // SoA [NGEO][E]: b_e, A_e upper triangle
+    int64_t n_flagged = 0;
+    // symbolic
+    bool have_pattern = false;
+    int64_t nnz = -1;
+    fem::DevBuf row_ptr, col_idx, seg_ptr, contrib, slot, inc_ptr, inc;
+    // numeric scratch: element matrices V (per matrix) in the precision of the last call
+    fem::DevBuf VM, VK, VT;
+    int v_prec = -1, v_mask = 0;        // what VM/VK/VT currently hold
+    // staging for host-pointer arguments
+    fem::DevBuf u_stage, out_stage;
+    size_t device_bytes() const;
+};
+
+namespace fem {
+
+// ---------------------------------------------------------- kernel launches
+int geometry_run(fem_mesh& m, cudaStream_t s);           // fills geo64, geo32, n_flagged
+int symbolic_run(fem_mesh& m, cudaStream_t s);           // fills pattern and segments
+
+// Element products V = X Q.  Any of VM, VK, VT may be null (matrix skipped).
+int element_simt_fp64(const fem_mesh& m, const CoeffDev& k, const double* u, double* VM, double* VK, double* VT,
+                      cudaStream_t s);
+int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const float* u, float* VM, float* VK, float* VT,
+                      cudaStream_t s);
+int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const float* u, float* VM, float* VK, float* VT,
+                      cudaStream_t s);
+
+// Segmented reduction of V into CSR values (outputs may be null).
+int scatter_fp64(const fem_mesh& m, const double* VM, const double* VK, const double* VT, double* vM, double* vK,
+                 double* vT, cudaStream_t s);
+int scatter_fp32(const fem_mesh& m, const float* VM, const float* VK, const float* VT, float* vM, float* vK,
+                 float* vT, cudaStream_t s);
+
+// One-time per-device upload of the reference tables of each kernel module.
+int tables_init_simt();
+int tables_init_tc();
+int tc_error_flag(int clear);   // device error word of the tensor-core kernels (1 = timeout)
+
+}  // namespace fem

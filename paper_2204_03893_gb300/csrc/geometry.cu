@@ -1,0 +1,175 @@
+// geometry.cu -- per-element geometric factors, computed once per mesh.
+//
+// Section 3 step 3: x = a + B_e xhat with B_e = [x_1 - x_0, ..., x_d - x_0];
+// the element integrals need b_e = |det B_e| and A_e = (B_e^T B_e)^-1 =
+// B_e^-1 B_e^-T (the chain rule J_phi_e = J_phihat B_e^-1).  Algorithm 2
+// line 4 computes "the vector b and the matrix W from mesh related data";
+// Section 5 notes that W and b depend only on the mesh.
+//
+// Output layout (structure of arrays, coalesced for one thread per element):
+//   geo[0*E + e] = b_e,  geo[(1+t)*E + e] = A_e[a][b] for the t-th (a<=b).
+// geo64: everything in FP64.  geo32: edge vectors in FP64 (the coordinates
+// are FP64 and nearby vertices cancel), det / inverse / A in FP32; elements
+// whose condition estimate kappa = ||B||_F^d / |det B| exceeds 1e3 are
+// recomputed in FP64 and rounded.
+#include "fem_internal.h"
+
+namespace fem {
+
+namespace {
+
+constexpr double KAPPA_MAX = 1e3;
+
+template <int D, typename T>
+__device__ __forceinline__ T det_inv(const T B[D][D], T Bi[D][D]) {
+    T det;
+    if constexpr (D == 2) {
+        det = B[0][0] * B[1][1] - B[0][1] * B[1][0];
+        T r = T(1) / det;
+        Bi[0][0] = B[1][1] * r;
+        Bi[0][1] = -B[0][1] * r;
+        Bi[1][0] = -B[1][0] * r;
+        Bi[1][1] = B[0][0] * r;
+    } else {
+        T c00 = B[1][1] * B[2][2] - B[1][2] * B[2][1];
+        T c01 = B[1][2] * B[2][0] - B[1][0] * B[2][2];
+        T c02 = B[1][0] * B[2][1] - B[1][1] * B[2][0];
+        det = B[0][0] * c00 + B[0][1] * c01 + B[0][2] * c02;
+        T r = T(1) / det;
+        Bi[0][0] = c00 * r;
+        Bi[1][0] = c01 * r;
+        Bi[2][0] = c02 * r;
+        Bi[0][1] = (B[0][2] * B[2][1] - B[0][1] * B[2][2]) * r;
+        Bi[1][1] = (B[0][0] * B[2][2] - B[0][2] * B[2][0]) * r;
+        Bi[2][1] = (B[0][1] * B[2][0] - B[0][0] * B[2][1]) * r;
+        Bi[0][2] = (B[0][1] * B[1][2] - B[0][2] * B[1][1]) * r;
+        Bi[1][2] = (B[0][2] * B[1][0] - B[0][0] * B[1][2]) * r;
+        Bi[2][2] = (B[0][0] * B[1][1] - B[0][1] * B[1][0]) * r;
+    }
+    return det;
+}
+
+// A = Bi Bi^T, upper triangle in (a<=b) order
+template <int D, typename T>
+__device__ __forceinline__ void make_A(const T Bi[D][D], T* A) {
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = a; b < D; ++b) {
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += Bi[a][k] * Bi[b][k];
+            A[t++] = s;
+        }
+}
+
+template <int D>
+__global__ void geometry_kernel(const double* __restrict__ X, const int* __restrict__ conn, int64_t E, int np,
+                                int64_t n, double* __restrict__ geo64, float* __restrict__ geo32,
+                                unsigned long long* __restrict__ counters /* [0] bad index, [1] degenerate, [2] flagged */) {
+    constexpr int NS = D * (D + 1) / 2;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        const int* ce = conn + e * np;
+        bool bad = false;
+        for (int i = 0; i < np; ++i) {
+            int v = ce[i];
+            bad |= (v < 0) | ((int64_t)v >= n);
+        }
+        if (bad) {
+            atomicAdd(&counters[0], 1ull);
+            for (int t = 0; t <= NS; ++t) { geo64[t * E + e] = 0.0; geo32[t * E + e] = 0.0f; }
+            continue;
+        }
+        double B[D][D];
+        int v0 = ce[0];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            int vc = ce[c + 1];
+#pragma unroll
+            for (int r = 0; r < D; ++r) B[r][c] = X[(int64_t)vc * D + r] - X[(int64_t)v0 * D + r];
+        }
+        double Bi[D][D];
+        double det = det_inv<D, double>(B, Bi);
+        double nf = 0.0;
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int c = 0; c < D; ++c) nf += B[r][c] * B[r][c];
+        double nfd = (D == 2) ? nf : nf * sqrt(nf);   // ||B||_F^d
+        if (!(fabs(det) > 1e-14 * nfd)) {
+            atomicAdd(&counters[1], 1ull);
+            for (int t = 0; t <= NS; ++t) { geo64[t * E + e] = 0.0; geo32[t * E + e] = 0.0f; }
+            continue;
+        }
+        double A[NS];
+        make_A<D, double>(Bi, A);
+        geo64[e] = fabs(det);
+#pragma unroll
+        for (int t = 0; t < NS; ++t) geo64[(1 + t) * E + e] = A[t];
+
+        // FP32 cache
+        float Bf[D][D], Bif[D][D];
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int c = 0; c < D; ++c) Bf[r][c] = (float)B[r][c];
+        float detf = det_inv<D, float>(Bf, Bif);
+        float nff = 0.0f;
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int c = 0; c < D; ++c) nff += Bf[r][c] * Bf[r][c];
+        float kappa = ((D == 2) ? nff : nff * sqrtf(nff)) / fabsf(detf);
+        if (kappa > (float)KAPPA_MAX || !(kappa == kappa)) {
+            atomicAdd(&counters[2], 1ull);
+            geo32[e] = (float)fabs(det);
+#pragma unroll
+            for (int t = 0; t < NS; ++t) geo32[(1 + t) * E + e] = (float)A[t];
+        } else {
+            float Af[NS];
+            make_A<D, float>(Bif, Af);
+            geo32[e] = fabsf(detf);
+#pragma unroll
+            for (int t = 0; t < NS; ++t) geo32[(1 + t) * E + e] = Af[t];
+        }
+    }
+}
+
+}  // namespace
+
+int geometry_run(fem_mesh& m, cudaStream_t s) {
+    int ngeo = 1 + m.d * (m.d + 1) / 2;
+    int rc = buf_alloc(m.geo64, sizeof(double) * ngeo * (size_t)m.E, s);
+    if (rc) return rc;
+    rc = buf_alloc(m.geo32, sizeof(float) * ngeo * (size_t)m.E, s);
+    if (rc) return rc;
+    DevBuf cnt;
+    rc = buf_alloc(cnt, 4 * sizeof(unsigned long long), s);
+    if (rc) return rc;
+    FEM_CUDA_TRY(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
+    if (m.E > 0) {
+        int threads = 256;
+        int64_t blocks = (m.E + threads - 1) / threads;
+        if (blocks > 152 * 64) blocks = 152 * 64;
+        if (m.d == 2)
+            geometry_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(m.coords.as<double>(), m.conn.as<int>(), m.E, m.np,
+                                                                    m.n, m.geo64.as<double>(), m.geo32.as<float>(),
+                                                                    cnt.as<unsigned long long>());
+        else
+            geometry_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(m.coords.as<double>(), m.conn.as<int>(), m.E, m.np,
+                                                                    m.n, m.geo64.as<double>(), m.geo32.as<float>(),
+                                                                    cnt.as<unsigned long long>());
+        FEM_CUDA_TRY(cudaGetLastError());
+    }
+    unsigned long long h[4] = {0, 0, 0, 0};
+    FEM_CUDA_TRY(cudaMemcpyAsync(h, cnt.ptr, sizeof(h), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA_TRY(cudaStreamSynchronize(s));
+    buf_free(cnt, s);
+    if (h[0]) return fail(FEM_EINVAL, "connectivity index out of range in " + std::to_string(h[0]) + " element(s)");
+    if (h[1]) return fail(FEM_EDEGENERATE, std::to_string(h[1]) + " degenerate element(s)");
+    m.n_flagged = (int64_t)h[2];
+    return FEM_OK;
+}
+
+}  // namespace fem

@@ -1,0 +1,297 @@
+// symbolic.cu -- CSR pattern and element-entry -> slot map, once per mesh.
+//
+// Section 3 step 2: the integral of an element contributes to (i, j) only if
+// both nodes belong to the element (the index set N_e), which makes the
+// matrix sparse; Algorithm 2 line 12 forms the global matrix from V and "the
+// set of indices of nonzero entries".  This module builds that set on the
+// device by sorting the keys (row, col) = (conn[e][i], conn[e][j]) of every
+// element entry c = (e n_p + i) n_p + j:
+//   1. counting sort of the (e, i) incidences by row (integer atomics for
+//      the counts, then each row's list sorted ascending so that the order
+//      does not depend on atomic timing);
+//   2. per row, a stable rank sort of its n_p * |incidences| entries by
+//      column (ties keep ascending c), one warp per row;
+//   3. a scan of the per-row unique-column counts gives row_ptr;
+//   4. per row, one warp walks the sorted entries and numbers the column
+//      groups: col_idx, seg_ptr (first sorted position of each slot) and the
+//      slot map slot[c].
+// contrib[] holds the element entries sorted by (slot, c); seg_ptr[s] ..
+// seg_ptr[s+1] is slot s's segment.  Everything is integer work and fully
+// deterministic.
+#include "fem_internal.h"
+
+#include <climits>
+
+namespace fem {
+
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// block-wide exclusive scan of one int per thread; returns the block total
+__device__ int block_exclusive_scan(int v, int& total) {
+    __shared__ int warp_sums[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        int s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    int wprefix = w > 0 ? warp_sums[w - 1] : 0;
+    total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return wprefix + x - v;
+}
+
+// pass 1: per-tile sums
+__global__ void scan_tile_sums(const int* __restrict__ in, int64_t n, int* __restrict__ sums) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        int64_t i = base + threadIdx.x * SCAN_ITEMS + k;
+        if (i < n) s += in[i];
+    }
+    int total;
+    block_exclusive_scan(s, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// pass 2: exclusive scan of the tile sums in one block (sequential chunks)
+__global__ void scan_sums(int* __restrict__ sums, int nt) {
+    int carry = 0;
+    for (int base = 0; base < nt; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int v = i < nt ? sums[i] : 0;
+        int total;
+        int ex = block_exclusive_scan(v, total);
+        if (i < nt) sums[i] = carry + ex;
+        carry += total;
+    }
+}
+
+// pass 3: out[i] = sum_{j<i} in[j] for i in [0, n]; out[n] is the total
+__global__ void scan_apply(const int* __restrict__ in, int64_t n, const int* __restrict__ sums, int* __restrict__ out) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    int v[SCAN_ITEMS];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        int64_t i = base + threadIdx.x * SCAN_ITEMS + k;
+        v[k] = i < n ? in[i] : 0;
+        s += v[k];
+    }
+    int total;
+    int ex = block_exclusive_scan(s, total) + sums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        int64_t i = base + threadIdx.x * SCAN_ITEMS + k;
+        if (i <= n) out[i] = ex;    // i == n receives the grand total
+        ex += v[k];
+    }
+}
+
+// ---------------------------------------------------------------- incidences
+__global__ void inc_count(const int* __restrict__ conn, int64_t m, int* __restrict__ cnt) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[conn[k]], 1);
+}
+
+__global__ void inc_fill(const int* __restrict__ conn, int64_t m, const int* __restrict__ inc_ptr,
+                         int* __restrict__ fill, int* __restrict__ inc) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        int r = conn[k];
+        int pos = inc_ptr[r] + atomicAdd(&fill[r], 1);
+        inc[pos] = (int)k;   // k = e * n_p + i
+    }
+}
+
+__global__ void inc_sort(const int* __restrict__ inc_ptr, int64_t n, int* __restrict__ inc) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        int a = inc_ptr[r], b = inc_ptr[r + 1];
+        for (int i = a + 1; i < b; ++i) {
+            int v = inc[i];
+            int j = i - 1;
+            while (j >= a && inc[j] > v) {
+                inc[j + 1] = inc[j];
+                --j;
+            }
+            inc[j + 1] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- row sort
+constexpr int RS_WARPS = 8;
+constexpr int RS_CAP = 768;   // staged columns per warp
+
+__global__ void __launch_bounds__(RS_WARPS * 32) row_sort(const int* __restrict__ conn, int np,
+                                                          const int* __restrict__ inc_ptr, const int* __restrict__ inc,
+                                                          int64_t n, int* __restrict__ contrib,
+                                                          int* __restrict__ row_nnz) {
+    __shared__ int sc_all[RS_WARPS][RS_CAP];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int* sc = sc_all[w];
+    int64_t nwarps = (int64_t)gridDim.x * RS_WARPS;
+    for (int64_t r = blockIdx.x * (int64_t)RS_WARPS + w; r < n; r += nwarps) {
+        int start = inc_ptr[r];
+        int len = inc_ptr[r + 1] - start;
+        int L = np * len;
+        int64_t base = (int64_t)np * start;
+        bool staged = L <= RS_CAP;
+        if (staged) {
+            for (int k = lane; k < L; k += 32) {
+                int ei = inc[start + k / np];
+                sc[k] = conn[(int64_t)(ei / np) * np + k % np];
+            }
+        }
+        __syncwarp();
+        int heads = 0;
+        for (int k = lane; k < L; k += 32) {
+            int ei = inc[start + k / np];
+            int ck = staged ? sc[k] : conn[(int64_t)(ei / np) * np + k % np];
+            int rank = 0;
+            int head = 1;
+            for (int k2 = 0; k2 < L; ++k2) {
+                int c2;
+                if (staged) c2 = sc[k2];
+                else {
+                    int e2 = inc[start + k2 / np];
+                    c2 = conn[(int64_t)(e2 / np) * np + k2 % np];
+                }
+                bool before = (c2 < ck) | ((c2 == ck) & (k2 < k));
+                rank += before;
+                head &= !((c2 == ck) & (k2 < k));
+            }
+            contrib[base + rank] = ei * np + (k % np);
+            heads += head;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) heads += __shfl_xor_sync(0xffffffffu, heads, o);
+        if (lane == 0) row_nnz[r] = heads;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- numbering
+__global__ void __launch_bounds__(256) row_finish(const int* __restrict__ conn, int np,
+                                                  const int* __restrict__ inc_ptr, const int* __restrict__ row_ptr,
+                                                  const int* __restrict__ contrib, int64_t n,
+                                                  int* __restrict__ col_idx, int* __restrict__ seg_ptr,
+                                                  int* __restrict__ slot) {
+    int lane = threadIdx.x & 31;
+    int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    int np2 = np * np;
+    unsigned le = (lane == 31) ? 0xffffffffu : ((1u << (lane + 1)) - 1u);
+    for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += nwarps) {
+        int64_t start = (int64_t)np * inc_ptr[r], end = (int64_t)np * inc_ptr[r + 1];
+        int slot0 = row_ptr[r];
+        int carry = -1, count = 0;
+        for (int64_t p0 = start; p0 < end; p0 += 32) {
+            int64_t p = p0 + lane;
+            bool valid = p < end;
+            int c = valid ? contrib[p] : 0;
+            int col = valid ? conn[(int64_t)(c / np2) * np + c % np] : INT_MAX;
+            int prev = __shfl_up_sync(0xffffffffu, col, 1);
+            if (lane == 0) prev = carry;
+            bool head = valid && col != prev;
+            unsigned mask = __ballot_sync(0xffffffffu, head);
+            int idx = count + __popc(mask & le) - 1;
+            if (valid) slot[c] = slot0 + idx;
+            if (head) {
+                col_idx[slot0 + idx] = col;
+                seg_ptr[slot0 + idx] = (int)p;
+            }
+            count += __popc(mask);
+            carry = __shfl_sync(0xffffffffu, col, 31);
+        }
+    }
+}
+
+__global__ void set_last(int* p, int64_t idx, int v) { p[idx] = v; }
+
+int grid_for(int64_t work, int threads, int64_t cap = 152 * 32) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+}  // namespace
+
+// exclusive scan of n ints into n+1 outputs
+int scan_exclusive(const int* in, int64_t n, int* out, cudaStream_t s) {
+    int64_t nt = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;
+    DevBuf sums;
+    int rc = buf_alloc(sums, sizeof(int) * (size_t)nt, s);
+    if (rc) return rc;
+    scan_tile_sums<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, sums.as<int>());
+    scan_sums<<<1, 1024, 0, s>>>(sums.as<int>(), (int)nt);
+    scan_apply<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, sums.as<int>(), out);
+    cudaError_t e = cudaGetLastError();
+    buf_free(sums, s);
+    if (e != cudaSuccess) return cuda_fail(e, "scan");
+    return FEM_OK;
+}
+
+int symbolic_run(fem_mesh& m, cudaStream_t s) {
+    const int np = m.np;
+    const int64_t n = m.n, E = m.E;
+    const int64_t m1 = E * np, m2 = E * np * np;
+    int rc;
+    DevBuf cnt, fill, row_nnz;
+    if ((rc = buf_alloc(cnt, sizeof(int) * (size_t)(n + 1), s))) return rc;
+    if ((rc = buf_alloc(m.inc_ptr, sizeof(int) * (size_t)(n + 1), s))) return rc;
+    if ((rc = buf_alloc(m.inc, sizeof(int) * (size_t)(m1 + 1), s))) return rc;
+    if ((rc = buf_alloc(fill, sizeof(int) * (size_t)(n + 1), s))) return rc;
+    if ((rc = buf_alloc(m.contrib, sizeof(int) * (size_t)(m2 + 1), s))) return rc;
+    if ((rc = buf_alloc(m.slot, sizeof(int) * (size_t)(m2 + 1), s))) return rc;
+    if ((rc = buf_alloc(row_nnz, sizeof(int) * (size_t)(n + 1), s))) return rc;
+    if ((rc = buf_alloc(m.row_ptr, sizeof(int) * (size_t)(n + 1), s))) return rc;
+    FEM_CUDA_TRY(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
+    FEM_CUDA_TRY(cudaMemsetAsync(fill.ptr, 0, fill.bytes, s));
+    const int* conn = m.conn.as<int>();
+    inc_count<<<grid_for(m1, 256), 256, 0, s>>>(conn, m1, cnt.as<int>());
+    if ((rc = scan_exclusive(cnt.as<int>(), n, m.inc_ptr.as<int>(), s))) return rc;
+    inc_fill<<<grid_for(m1, 256), 256, 0, s>>>(conn, m1, m.inc_ptr.as<int>(), fill.as<int>(), m.inc.as<int>());
+    inc_sort<<<grid_for(n, 128), 128, 0, s>>>(m.inc_ptr.as<int>(), n, m.inc.as<int>());
+    row_sort<<<grid_for(n, RS_WARPS, 152 * 64), RS_WARPS * 32, 0, s>>>(conn, np, m.inc_ptr.as<int>(), m.inc.as<int>(), n,
+                                                                      m.contrib.as<int>(), row_nnz.as<int>());
+    FEM_CUDA_TRY(cudaGetLastError());
+    if ((rc = scan_exclusive(row_nnz.as<int>(), n, m.row_ptr.as<int>(), s))) return rc;
+    int nnz = 0;
+    FEM_CUDA_TRY(cudaMemcpyAsync(&nnz, m.row_ptr.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA_TRY(cudaStreamSynchronize(s));
+    m.nnz = nnz;
+    if ((rc = buf_alloc(m.col_idx, sizeof(int) * (size_t)(nnz + 1), s))) return rc;
+    if ((rc = buf_alloc(m.seg_ptr, sizeof(int) * (size_t)(nnz + 1), s))) return rc;
+    row_finish<<<grid_for(n, 8, 152 * 64), 256, 0, s>>>(conn, np, m.inc_ptr.as<int>(), m.row_ptr.as<int>(),
+                                                        m.contrib.as<int>(), n, m.col_idx.as<int>(),
+                                                        m.seg_ptr.as<int>(), m.slot.as<int>());
+    set_last<<<1, 1, 0, s>>>(m.seg_ptr.as<int>(), nnz, (int)m2);
+    FEM_CUDA_TRY(cudaGetLastError());
+    buf_free(cnt, s);
+    buf_free(fill, s);
+    buf_free(row_nnz, s);
+    FEM_CUDA_TRY(cudaStreamSynchronize(s));
+    m.have_pattern = true;
+    return FEM_OK;
+}
+
+}  // namespace fem

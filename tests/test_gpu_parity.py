@@ -1,0 +1,314 @@
+"""GPU parity of libfem against the CPU FP64 oracle, through the C ABI.
+
+Bars (per matrix M, K(u), T(u)):
+  * pattern (row_ptr, col_idx) and slot map: bit-exact;
+  * FEM_FP64: |gpu - oracle| <= 1e-12 * absum per entry, absum = sum of the
+    absolute element contributions of the slot (entries that cancel are
+    judged against the size of what cancelled);
+  * FEM_TF32X3: relative Frobenius error <= 1e-6 per matrix;
+  * FEM_FP32 (SIMT reference point): relative Frobenius error <= 1e-5;
+  * every precision: bitwise identical results run to run.
+Sizes span several 128-element tiles with a ragged last tile.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import meshgen as mg
+import oracle as orc
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2204_03893_gb300 as F  # noqa: E402
+from paper_2204_03893_gb300.torch_api import FemMesh  # noqa: E402
+
+FP64_TOL = 1e-12
+TF32_TOL = 1e-6
+FP32_TOL = 1e-5
+
+
+def wl_small(name):
+    return {
+        "tri_p1": lambda: mg.workload("tri_p1_64"),
+        "tri_p2": lambda: mg.workload("tri_p2_1024", scale=41),
+        "tet_p1": lambda: mg.workload("tet_p1_128", scale=9),
+        "tet_p2": lambda: mg.workload("tet_p2_64", scale=5),
+        "tri_p3": lambda: _p3(2),
+        "tet_p3": lambda: _p3(3),
+    }[name]()
+
+
+def _p3(d):
+    m = mg.structured_tri(13, 3, 0.2, seed=77) if d == 2 else mg.structured_tet(3, 3, 0.15, seed=77)
+    return mg.Workload(f"p3_{d}", m, mg.fourier_field(m.coords, 78), mg.Coeff("poly", (1.0, 0.3, 0.6, 0.0, 0.0)))
+
+
+def gpu_assemble(fm, wl, prec):
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    u = torch.tensor(wl.u, dtype=dt, device="cuda")
+    out = fm.assemble(u, wl.coeff.kind, wl.coeff.params, prec)
+    torch.cuda.synchronize()
+    return {k: v.double().cpu().numpy() for k, v in out.items()}
+
+
+_ORACLE_CACHE = {}
+
+
+def oracle_result(name, wl):
+    if name not in _ORACLE_CACHE:
+        o = orc.Oracle.of(wl.mesh)
+        _ORACLE_CACHE[name] = (o.pattern(), o.assemble(wl.u, wl.coeff, m=wl.mass_coeff))
+    return _ORACLE_CACHE[name]
+
+
+def frob(g, o):
+    return np.linalg.norm(g - o) / np.linalg.norm(o)
+
+
+CASES = ["tri_p1", "tri_p2", "tet_p1", "tet_p2", "tri_p3", "tet_p3"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_pattern_and_slot_map_bit_exact(name):
+    wl = wl_small(name)
+    (rp_o, ci_o), _ = oracle_result(name, wl)
+    fm = FemMesh.of(wl.mesh)
+    rp, ci = fm.pattern()
+    assert np.array_equal(rp.cpu().numpy(), rp_o)
+    assert np.array_equal(ci.cpu().numpy(), ci_o)
+    # slot map: entry c = (e n_p + i) n_p + j lands on (conn[e][i], conn[e][j])
+    slot = fm.slot_map().cpu().numpy().astype(np.int64)
+    conn = wl.mesh.conn.astype(np.int64)
+    npl = conn.shape[1]
+    rows = np.repeat(conn, npl, axis=1).ravel()
+    cols = np.tile(conn, (1, npl)).ravel()
+    row_of_slot = np.repeat(np.arange(len(rp_o) - 1), np.diff(rp_o))
+    assert np.array_equal(row_of_slot[slot], rows)
+    assert np.array_equal(ci_o[slot], cols)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_fp64_parity_per_entry(name):
+    wl = wl_small(name)
+    _, o = oracle_result(name, wl)
+    fm = FemMesh.of(wl.mesh)
+    g = gpu_assemble(fm, wl, "fp64")
+    for k in ("M", "K", "T"):
+        err = np.abs(g[k] - o[k])
+        bound = FP64_TOL * o["abs" + k] + 1e-300
+        worst = (err / bound).max()
+        assert worst <= 1.0, (k, worst)
+
+
+@pytest.mark.parametrize("name", [c for c in CASES if c != "tet_p3"])
+def test_tf32x3_parity_frobenius(name):
+    wl = wl_small(name)
+    _, o = oracle_result(name, wl)
+    fm = FemMesh.of(wl.mesh)
+    g = gpu_assemble(fm, wl, "tf32x3")
+    F.fem_device_status()
+    for k in ("M", "K", "T"):
+        assert frob(g[k], o[k]) <= TF32_TOL, (k, frob(g[k], o[k]))
+
+
+def test_tf32x3_unsupported_type_is_refused():
+    wl = wl_small("tet_p3")
+    fm = FemMesh.of(wl.mesh)
+    with pytest.raises(F.FemError) as ei:
+        gpu_assemble(fm, wl, "tf32x3")
+    assert ei.value.code == F.FEM_EINVAL
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_fp32_simt_parity_frobenius(name):
+    wl = wl_small(name)
+    _, o = oracle_result(name, wl)
+    fm = FemMesh.of(wl.mesh)
+    g = gpu_assemble(fm, wl, "fp32")
+    for k in ("M", "K", "T"):
+        assert frob(g[k], o[k]) <= FP32_TOL, (k, frob(g[k], o[k]))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "fp32"])
+def test_run_to_run_bitwise(prec):
+    wl = wl_small("tri_p2")
+    fm = FemMesh.of(wl.mesh)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    u = torch.tensor(wl.u, dtype=dt, device="cuda")
+    a = fm.assemble(u, wl.coeff.kind, wl.coeff.params, prec)
+    a = {k: v.clone() for k, v in a.items()}
+    for _ in range(3):
+        b = fm.assemble(u, wl.coeff.kind, wl.coeff.params, prec)
+        for k in a:
+            assert torch.equal(a[k], b[k]), k
+
+
+def test_separate_entry_points_match_all():
+    wl = wl_small("tet_p2")
+    fm = FemMesh.of(wl.mesh)
+    u = torch.tensor(wl.u, dtype=torch.float32, device="cuda")
+    both = fm.assemble(u, wl.coeff.kind, wl.coeff.params, "tf32x3")
+    both = {k: v.clone() for k, v in both.items()}
+    for k in ("M", "K", "T"):
+        one = fm.assemble(u, wl.coeff.kind, wl.coeff.params, "tf32x3", which=(k,))
+        assert torch.equal(one[k], both[k]), k
+    vals = torch.empty(fm.nnz, dtype=torch.float32, device="cuda")
+    F.fem_assemble_mass(fm.h, F.FEM_TF32X3, vals)
+    torch.cuda.synchronize()
+    assert torch.equal(vals, both["M"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_host_pointer_path_matches_device(prec):
+    wl = wl_small("tri_p2")
+    fm = FemMesh.of(wl.mesh)
+    fm.symbolic()
+    dt = np.float64 if prec == "fp64" else np.float32
+    uh = np.ascontiguousarray(wl.u, dtype=dt)
+    outs = {k: np.zeros(fm.nnz, dtype=dt) for k in "MKT"}
+    F.fem_assemble_all(fm.h, F.coeff(wl.coeff.kind, wl.coeff.params), uh, F.torch_api.PRECISIONS[prec],
+                       outs["M"], outs["K"], outs["T"])
+    ud = torch.tensor(uh, device="cuda")
+    d = fm.assemble(ud, wl.coeff.kind, wl.coeff.params, prec)
+    for k in "MKT":
+        assert np.array_equal(outs[k], d[k].cpu().numpy()), k
+
+
+def test_coefficient_laws():
+    """sin and piecewise-linear laws against the oracle (FP64 per entry)."""
+    m = mg.structured_tri(12, 2, 0.2, seed=5)
+    u = 1200.0 * mg.fourier_field(m.coords, 6) - 100.0       # spans all pwlin branches
+    o = orc.Oracle.of(m)
+    fm = FemMesh.of(m)
+    for c in (mg.Coeff("sin", (2.0, 1.0, 3.0)), mg.Coeff("pwlin", (0.0, 200.0, 1000.0, 1.5, 0.7, 0.5)),
+              mg.Coeff("poly", (0.5, -0.25, 0.125, 0.01, -0.001))):
+        uu = u if c.kind == "pwlin" else u / 1200.0
+        r = o.assemble(uu, c)
+        g = fm.assemble(torch.tensor(uu, device="cuda"), c.kind, c.params, "fp64")
+        for k in ("K", "T"):
+            gk = g[k].cpu().numpy()
+            assert (np.abs(gk - r[k]) <= FP64_TOL * r["abs" + k] + 1e-300).all(), (c.kind, k)
+
+
+def test_mass_coefficient_scales():
+    m = mg.structured_tet(3, 2, 0.15, seed=1)
+    f1, f2 = FemMesh.of(m, mass=1.0), FemMesh.of(m, mass=2.5)
+    a = f1.assemble(None, "poly", (1.0,), "fp64", which=("M",))["M"]
+    b = f2.assemble(None, "poly", (1.0,), "fp64", which=("M",))["M"]
+    torch.testing.assert_close(b, 2.5 * a, rtol=1e-15, atol=0)
+    assert abs(a.sum().item() - 1.0) < 1e-12
+
+
+def test_errors_and_edge_cases():
+    m = mg.structured_tri(3, 1, 0.0)
+    fm = FemMesh.of(m)
+    vals = torch.empty(100, dtype=torch.float64, device="cuda")
+    with pytest.raises(F.FemError) as ei:              # before symbolic
+        F.fem_assemble_mass(fm.h, F.FEM_FP64, vals)
+    assert ei.value.code == F.FEM_ESTATE
+    fm.symbolic()
+    with pytest.raises(F.FemError) as ei:              # u missing
+        F.fem_assemble_stiffness(fm.h, F.coeff("poly", (1.0,)), None, F.FEM_FP64, vals)
+    assert ei.value.code == F.FEM_EINVAL
+    with pytest.raises(F.FemError) as ei:              # bad law
+        F.fem_assemble_stiffness(fm.h, F.coeff("pwlin", (1.0, 0.0, 2.0, 3.0)), vals, F.FEM_FP64, vals)
+    assert ei.value.code == F.FEM_EINVAL
+    bad = mg.Mesh(2, 1, m.coords, m.conn.copy())
+    bad.conn[3, 1] = m.n_nodes + 5
+    with pytest.raises(F.FemError) as ei:
+        FemMesh.of(bad)
+    assert ei.value.code == F.FEM_EINVAL
+    deg = mg.Mesh(2, 1, m.coords.copy(), m.conn)
+    deg.coords[m.conn[4, 1]] = deg.coords[m.conn[4, 0]]     # collapse an element
+    with pytest.raises(F.FemError) as ei:
+        FemMesh.of(deg)
+    assert ei.value.code == F.FEM_EDEGENERATE
+    # empty mesh: no elements, empty rows
+    empty = FemMesh(2, 1, m.coords, np.zeros((0, 3), dtype=np.int32))
+    empty.symbolic()
+    assert empty.nnz == 0
+    empty.assemble(torch.zeros(m.n_nodes, device="cuda", dtype=torch.float64), "poly", (1.0,), "fp64")
+
+
+def test_sliver_elements_use_fp64_geometry():
+    m = mg.sliver_tri(16, 0.05, seed=3)
+    fm = FemMesh.of(m)
+    assert fm.info().n_flagged > 0
+    u = mg.uniform_field(m.n_nodes, 4)
+    c = mg.Coeff("poly", (1.0, 0.5, 0.25, 0.0, 0.0))
+    o = orc.Oracle.of(m).assemble(u, c)
+    g = fm.assemble(torch.tensor(u, dtype=torch.float32, device="cuda"), c.kind, c.params, "tf32x3")
+    for k in ("M", "K", "T"):
+        assert frob(g[k].double().cpu().numpy(), o[k]) <= TF32_TOL, k
+
+
+def test_torch_caching_allocator_and_failure_injection():
+    """The allocator hook bound to torch's caching allocator; an allocator
+    that fails at the N-th request makes the call return FEM_ENOMEM and the
+    library stays usable."""
+    state = {"n": 0, "fail_at": None, "live": {}}
+
+    def alloc(size, stream, ctx):
+        state["n"] += 1
+        if state["fail_at"] is not None and state["n"] >= state["fail_at"]:
+            return None
+        p = torch.cuda.caching_allocator_alloc(size, stream=stream or 0)
+        state["live"][p] = size
+        return p
+
+    def free(ptr, size, stream, ctx):
+        state["live"].pop(ptr, None)
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = F.fem_allocator(F.ALLOC_FN(alloc), F.FREE_FN(free), None)
+    F.fem_set_allocator(a)
+    try:
+        wl = wl_small("tri_p2")
+        fm = FemMesh.of(wl.mesh)
+        g1 = gpu_assemble(fm, wl, "fp64")
+        fm.close()
+        assert not state["live"]
+        state["n"], state["fail_at"] = 0, 4
+        with pytest.raises(F.FemError) as ei:
+            fm2 = FemMesh.of(wl.mesh)
+            fm2.symbolic()
+        assert ei.value.code == F.FEM_ENOMEM
+    finally:
+        F.fem_set_allocator(None)
+    fm3 = FemMesh.of(wl.mesh)
+    g3 = gpu_assemble(fm3, wl, "fp64")
+    for k in g1:
+        assert np.array_equal(g1[k], g3[k])
+
+
+# ------------------------------------------------------------------ full size
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_full_size_tri_p2_1024_sampled(prec):
+    """2 097 152 P2 triangles in the launch configuration the benchmark
+    times: nnz by its closed form, sampled rows' patterns from the element
+    definition, sampled entries against the oracle computed one by one."""
+    wl = mg.workload("tri_p2_1024")
+    N = 1024
+    fm = FemMesh.of(wl.mesh)
+    fm.symbolic()
+    assert fm.nnz == 46 * N * N + 16 * N + 1
+    rp, ci = (t.cpu().numpy() for t in fm.pattern())
+    conn = wl.mesh.conn
+    rng = np.random.default_rng(123)
+    rows = rng.choice(wl.mesh.n_nodes, 40, replace=False)
+    for r in rows:
+        els = np.nonzero((conn == r).any(axis=1))[0]
+        assert np.array_equal(ci[rp[r]:rp[r + 1]], np.unique(conn[els]))
+    g = gpu_assemble(fm, wl, prec)
+    slots = rng.choice(fm.nnz, 3000, replace=False)
+    row_of = np.searchsorted(rp, slots, side="right") - 1
+    s = orc.Oracle.of(wl.mesh).entries(row_of, ci[slots], wl.u, wl.coeff)
+    tol = FP64_TOL if prec == "fp64" else 2e-6
+    for k in ("M", "K", "T"):
+        err = np.abs(g[k][slots] - s[k])
+        assert (err <= tol * s["abs" + k] + 1e-300).all(), (k, (err / s["abs" + k]).max())
