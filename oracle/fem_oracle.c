@@ -30,6 +30,11 @@
  *   - Global assembly: every (row, col) pair of nodes that share an element
  *     is a structural nonzero (Section 3 step 2); contributions are added in
  *     ascending element order, then ascending local row, local column.
+ *   - Error scale per CSR entry (absM/absK/absT): the sum over elements and
+ *     quadrature nodes of the magnitudes of the expanded product terms, the
+ *     natural bound for a floating-point evaluation of the same sum in any
+ *     order (entries that cancel exactly, such as P2 vertex/adjacent-edge
+ *     mass entries, keep a nonzero scale).
  *
  * Quadrature rules (Section 3 step 4 cites Gaussian simplex rules; weights
  * here sum to the reference measure 1/2 or 1/6):
@@ -424,9 +429,14 @@ static double geometry(const octx* c, int e, double A[3][3]) {
     return det;
 }
 
-/* Local matrices of element e (dense n_p x n_p, row = test index). */
+/* Local matrices of element e (dense n_p x n_p, row = test index).  If
+ * aM/aK/aT are given they receive the error scale of each entry: the sum of
+ * the magnitudes of the fully expanded product terms of the quadrature sum,
+ * with |A_ab| bounded by sqrt(A_aa A_bb) (A_e is symmetric positive
+ * definite), so that entries which cancel inside the sum are judged against
+ * what cancelled. */
 static void element(const octx* c, const otab* t, int e, double m, int kkind, const double* kp, int nkp,
-                    const double* u, double* Me, double* Ke, double* Te) {
+                    const double* u, double* Me, double* Ke, double* Te, double* aM, double* aK, double* aT) {
     int np = c->np, d = c->d;
     double A[3][3];
     double b = fabs(geometry(c, e, A));
@@ -436,6 +446,12 @@ static void element(const octx* c, const otab* t, int e, double m, int kkind, co
     memset(Me, 0, sizeof(double) * np * np);
     memset(Ke, 0, sizeof(double) * np * np);
     memset(Te, 0, sizeof(double) * np * np);
+    if (aM) memset(aM, 0, sizeof(double) * np * np);
+    if (aK) memset(aK, 0, sizeof(double) * np * np);
+    if (aT) memset(aT, 0, sizeof(double) * np * np);
+    double Ab[3][3];
+    for (int a = 0; a < d; ++a)
+        for (int bb = 0; bb < d; ++bb) Ab[a][bb] = sqrt(fabs(A[a][a] * A[bb][bb]));
     for (int q = 0; q < t->nq; ++q) {
         const double* phi = t->phi[q];
         double uq = 0.0;
@@ -470,6 +486,30 @@ static void element(const octx* c, const otab* t, int e, double m, int kkind, co
                 Ke[i * np + j] += wb * kq * S[i][j];
                 Te[i * np + j] += wb * dk * Su[i] * phi[j];
             }
+        if (aM || aK || aT) {
+            /* |S|_ij = sum_ab |J_ia| |A|_ab |J_jb| */
+            double aS[OR_MAXNP][OR_MAXNP];
+            for (int i = 0; i < np; ++i)
+                for (int j = 0; j < np; ++j) {
+                    double s2 = 0.0;
+                    for (int a = 0; a < d; ++a)
+                        for (int bb = 0; bb < d; ++bb) s2 += fabs(t->J[q][i][a]) * Ab[a][bb] * fabs(t->J[q][j][bb]);
+                    aS[i][j] = s2;
+                }
+            double aSu[OR_MAXNP];
+            for (int i = 0; i < np; ++i) {
+                double s2 = 0.0;
+                for (int j = 0; j < np; ++j) s2 += aS[i][j] * fabs(ue[j]);
+                aSu[i] = s2;
+            }
+            double awb = fabs(wb);
+            for (int i = 0; i < np; ++i)
+                for (int j = 0; j < np; ++j) {
+                    if (aM) aM[i * np + j] += awb * fabs(m * phi[i] * phi[j]);
+                    if (aK) aK[i * np + j] += awb * fabs(kq) * aS[i][j];
+                    if (aT) aT[i * np + j] += awb * fabs(dk) * aSu[i] * fabs(phi[j]);
+                }
+        }
     }
 }
 
@@ -480,7 +520,7 @@ int oracle_element(void* h, int e, int deg, double m, int kkind, const double* k
     otab t;
     if (make_tab(c->d, c->p, deg, &t)) return -1;
     if (e < 0 || e >= c->E) return -1;
-    element(c, &t, e, m, kkind, kp, nkp, u, Me, Ke, Te);
+    element(c, &t, e, m, kkind, kp, nkp, u, Me, Ke, Te, NULL, NULL, NULL);
     return 0;
 }
 
@@ -516,8 +556,11 @@ int oracle_assemble(void* h, int deg, double m, int kkind, const double* kp, int
     double* out[6] = {M, K, T, absM, absK, absT};
     for (int k = 0; k < 6; ++k) if (out[k]) memset(out[k], 0, sizeof(double) * nz);
     double Me[OR_MAXNP * OR_MAXNP], Ke[OR_MAXNP * OR_MAXNP], Te[OR_MAXNP * OR_MAXNP];
+    double aMe[OR_MAXNP * OR_MAXNP], aKe[OR_MAXNP * OR_MAXNP], aTe[OR_MAXNP * OR_MAXNP];
+    int want_abs = absM || absK || absT;
     for (int e = 0; e < c->E; ++e) {
-        element(c, &t, e, m, kkind, kp, nkp, u, Me, Ke, Te);
+        element(c, &t, e, m, kkind, kp, nkp, u, Me, Ke, Te, want_abs ? aMe : NULL, want_abs ? aKe : NULL,
+                want_abs ? aTe : NULL);
         const int* v = c->conn + (long long)e * np;
         for (int i = 0; i < np; ++i)
             for (int j = 0; j < np; ++j) {
@@ -527,9 +570,9 @@ int oracle_assemble(void* h, int deg, double m, int kkind, const double* kp, int
                 if (M) M[s] += Me[l];
                 if (K) K[s] += Ke[l];
                 if (T) T[s] += Te[l];
-                if (absM) absM[s] += fabs(Me[l]);
-                if (absK) absK[s] += fabs(Ke[l]);
-                if (absT) absT[s] += fabs(Te[l]);
+                if (absM) absM[s] += aMe[l];
+                if (absK) absK[s] += aKe[l];
+                if (absT) absT[s] += aTe[l];
             }
     }
     return 0;
@@ -546,6 +589,7 @@ int oracle_entries(void* h, int deg, double m, int kkind, const double* kp, int 
     if (make_tab(c->d, c->p, deg, &t)) return -1;
     int np = c->np;
     double Me[OR_MAXNP * OR_MAXNP], Ke[OR_MAXNP * OR_MAXNP], Te[OR_MAXNP * OR_MAXNP];
+    double aMe[OR_MAXNP * OR_MAXNP], aKe[OR_MAXNP * OR_MAXNP], aTe[OR_MAXNP * OR_MAXNP];
     for (long long k = 0; k < nq; ++k) {
         int r = rows[k], col = cols[k];
         double s[6] = {0, 0, 0, 0, 0, 0};
@@ -555,10 +599,10 @@ int oracle_entries(void* h, int deg, double m, int kkind, const double* kp, int 
             int i = -1, j = -1;
             for (int a = 0; a < np; ++a) { if (v[a] == r) i = a; if (v[a] == col) j = a; }
             if (i < 0 || j < 0) continue;
-            element(c, &t, e, m, kkind, kp, nkp, u, Me, Ke, Te);
+            element(c, &t, e, m, kkind, kp, nkp, u, Me, Ke, Te, aMe, aKe, aTe);
             int l = i * np + j;
             s[0] += Me[l]; s[1] += Ke[l]; s[2] += Te[l];
-            s[3] += fabs(Me[l]); s[4] += fabs(Ke[l]); s[5] += fabs(Te[l]);
+            s[3] += aMe[l]; s[4] += aKe[l]; s[5] += aTe[l];
         }
         if (M) M[k] = s[0];
         if (K) K[k] = s[1];

@@ -22,6 +22,7 @@ int fail(int code, const std::string& msg) {
 }
 int cuda_fail(cudaError_t e, const char* what) {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    cudaGetLastError();   // do not leave a non-sticky error for the next launch check
     return FEM_ECUDA;
 }
 

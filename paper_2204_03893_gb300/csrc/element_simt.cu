@@ -63,13 +63,15 @@ __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict_
     T* X = reinterpret_cast<T*>(smem_raw) + threadIdx.x * LD;
 
     const T* Q = Tabs<T>::Q();
+    const bool need_u = (VK != nullptr) | (VT != nullptr);
     for (int64_t e0 = (int64_t)blockIdx.x * BT; e0 < E; e0 += (int64_t)gridDim.x * BT) {
         int64_t e = e0 + threadIdx.x;
         if (e >= E) continue;
         T ue[NP];
         const int* ce = conn + e * NP;
+        // u is only needed for K and T (mass-only calls pass u = NULL)
 #pragma unroll
-        for (int i = 0; i < NP; ++i) ue[i] = u[ce[i]];
+        for (int i = 0; i < NP; ++i) ue[i] = need_u ? u[ce[i]] : T(0);
         T b = geo[e];
         T A[NS];
 #pragma unroll
@@ -152,6 +154,7 @@ int launch_simt(const fem_mesh& m, const CoeffDev& k, const T* u, const T* geo, 
     int64_t grid = (int64_t)nsm * per_sm;
     if (grid > tiles) grid = tiles;
     if (grid < 1) return FEM_OK;
+    cudaGetLastError();   // clear any stale error before the launch check
     kern<<<(unsigned)grid, BT, smem, s>>>(m.conn.as<int>(), geo, m.E, u, k, (T)m.m, VM, VK, VT);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;

@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
     const uint32_t tmem = tmem_slot;
     const uint32_t sQu = tc::smem_u32(sQ), sXu = tc::smem_u32(sX);
     const bool doM = VM != nullptr, doK = VK != nullptr, doT = VT != nullptr;
+    const bool need_u = doK | doT;
     float* stage = reinterpret_cast<float*>(sX) + warp * 32 * 33;
     uint32_t phase = 0;
     bool timed_out = false;
@@ -192,8 +193,9 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
         if (e < E) {
             const int* ce = conn + e * NP;
             float ue[NP];
+            // u is only needed for K and T (mass-only calls pass u = NULL)
 #pragma unroll
-            for (int i = 0; i < NP; ++i) ue[i] = __ldg(u + __ldg(ce + i));
+            for (int i = 0; i < NP; ++i) ue[i] = need_u ? __ldg(u + __ldg(ce + i)) : 0.f;
             const float b = __ldg(geo + e);
             float A[NS];
 #pragma unroll
@@ -323,17 +325,25 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const float* u, float* VM, f
     } else {
         if (m.E == 0) return FEM_OK;
         auto kern = element_tc_kernel<ETy>;
-        int smem = L::SMEM;
-        FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX));
-        int dev = 0, nsm = 0, occ = 0;
+        int dev = 0, nsm = 0, occ = 0, optin = 0;
         FEM_CUDA_TRY(cudaGetDevice(&dev));
         FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        FEM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        cudaFuncAttributes fa;
+        FEM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+        const int dyn_max = optin - (int)fa.sharedSizeBytes;   // static shared memory counts against the limit
+        int smem = L::SMEM;
+        if (smem > dyn_max) return fail(FEM_EINVAL, "tensor-core tile does not fit in shared memory");
+        FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
         const int occ_max = 512 / L::ALLOC;   // co-resident CTAs must fit their TMEM columns
         if (occ > occ_max) {
             // ask for enough shared memory that at most occ_max CTAs fit on an SM
-            smem = SMEM_MAX / (occ_max + 1) + 1024;
-            if (smem > SMEM_MAX) smem = SMEM_MAX;
+            int per_sm = 0;
+            FEM_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+            smem = per_sm / (occ_max + 1) + 1;
+            if (smem > dyn_max) smem = dyn_max;
+            FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
             if (occ > occ_max) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
         }
@@ -345,6 +355,7 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const float* u, float* VM, f
         FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&img, g_tcimg));
         int* err = nullptr;
         FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&err, g_tc_err));
+        cudaGetLastError();   // clear any stale error before the launch check
         kern<<<(unsigned)grid, TILE, smem, s>>>(m.conn.as<int>(), m.geo32.as<float>(), m.E, u, k, (float)m.m, VM, VK,
                                                 VT, img + (size_t)ETy::TYPE * IMG_SLOT_FLOATS, err);
         FEM_CUDA_TRY(cudaGetLastError());

@@ -149,6 +149,7 @@ int geometry_run(fem_mesh& m, cudaStream_t s) {
     if (rc) return rc;
     FEM_CUDA_TRY(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
     if (m.E > 0) {
+        cudaGetLastError();   // clear any stale error before the launch check
         int threads = 256;
         int64_t blocks = (m.E + threads - 1) / threads;
         if (blocks > 152 * 64) blocks = 152 * 64;

@@ -54,6 +54,7 @@ int run(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, 
     if (blocks > (int64_t)nsm * 16) blocks = (int64_t)nsm * 16;
     const int* sp = m.seg_ptr.as<int>();
     const int* ct = m.contrib.as<int>();
+    cudaGetLastError();   // clear any stale error before the launch check
     switch (m.np) {
         case 3: scatter_kernel<3, T><<<(unsigned)blocks, 256, 0, s>>>(sp, ct, m.nnz, VM, VK, VT, vM, vK, vT); break;
         case 4: scatter_kernel<4, T><<<(unsigned)blocks, 256, 0, s>>>(sp, ct, m.nnz, VM, VK, VT, vM, vK, vT); break;

@@ -266,6 +266,7 @@ int symbolic_run(fem_mesh& m, cudaStream_t s) {
     if ((rc = buf_alloc(m.row_ptr, sizeof(int) * (size_t)(n + 1), s))) return rc;
     FEM_CUDA_TRY(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
     FEM_CUDA_TRY(cudaMemsetAsync(fill.ptr, 0, fill.bytes, s));
+    cudaGetLastError();   // clear any stale error before the launch checks
     const int* conn = m.conn.as<int>();
     inc_count<<<grid_for(m1, 256), 256, 0, s>>>(conn, m1, cnt.as<int>());
     if ((rc = scan_exclusive(cnt.as<int>(), n, m.inc_ptr.as<int>(), s))) return rc;
