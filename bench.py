@@ -218,8 +218,8 @@ def run_ours(args, rank, world, local_rank):
         t_sym = time.perf_counter() - t0
         nnz = fm.nnz
         # a ring of nodal fields (fresh u every step, resident in HBM)
-        us = [torch.tensor(mg.fourier_field(wl.mesh.coords, 1000 + 97 * rank + s), dtype=dt, device="cuda")
-              for s in range(4)]
+        us = [torch.tensor(mg.fourier_field(wl.mesh.coords, 1000 + 97 * rank + s), dtype=torch.float64,
+                           device="cuda") for s in range(4)]
         out = {k: torch.empty(nnz, dtype=dt, device="cuda") for k in "MKT"}
         k = F.coeff(wl.coeff.kind, wl.coeff.params)
         which = F.FEM_MAT_M | F.FEM_MAT_K | F.FEM_MAT_T
@@ -290,7 +290,7 @@ def run_ours(args, rank, world, local_rank):
         # end to end through the C ABI with pinned host buffers
         e2e = None
         if not args.no_e2e:
-            uh = [torch.empty(wl.mesh.n_nodes, dtype=dt, pin_memory=True) for _ in range(2)]
+            uh = [torch.empty(wl.mesh.n_nodes, dtype=torch.float64, pin_memory=True) for _ in range(2)]
             for i, x in enumerate(uh):
                 x.copy_(us[i].cpu())
             oh = {kk: torch.empty(nnz, dtype=dt, pin_memory=True) for kk in "MKT"}
@@ -304,7 +304,7 @@ def run_ours(args, rank, world, local_rank):
             te = time.perf_counter() - t0
             esz = 8 if args.prec == "fp64" else 4
             e2e = {"value": world * E * n_e2e / te, "unit": "elements/s", "steps": n_e2e,
-                   "h2d_bytes_per_step": wl.mesh.n_nodes * esz, "d2h_bytes_per_step": 3 * nnz * esz,
+                   "h2d_bytes_per_step": wl.mesh.n_nodes * 8, "d2h_bytes_per_step": 3 * nnz * esz,
                    "api": "fem_assemble_all with pinned host u and host CSR values (library-staged copies)"}
 
     if rank != 0:
@@ -314,7 +314,7 @@ def run_ours(args, rank, world, local_rank):
     n_p, nsym, nt = 6, 21, 36
     esz = 8 if args.prec == "fp64" else 4
     n = wl.mesh.n_nodes
-    bytes_form = E * (n_p * 4 + (1 + 3) * esz + (2 * nsym + nt) * esz) + n * esz
+    bytes_form = E * (n_p * 4 + (1 + 3) * esz + (2 * nsym + nt) * esz) + n * 8
     bytes_sum = (nnz + 1) * 4 + E * n_p * n_p * 4 + E * (2 * nsym + nt) * esz + 3 * nnz * esz
     mf, ms = statistics.mean(form_ms), statistics.mean(sum_ms)
     kernels = {

@@ -163,7 +163,9 @@ int fem_get_slot_map(fem_mesh* mesh, int32_t* d_slot, void* stream);
  * segmented reduction: every slot adds its contributions in ascending element
  * entry order, with no atomics, so results are bit-reproducible run to run.
  *
- * u: n_nodes nodal values, FP64 for FEM_FP64 and FP32 otherwise.
+ * u: n_nodes nodal values in FP64 for every precision (the FP32 paths split
+ * u = hi + lo into two FP32 values on the device, so that the nodal
+ * differences that carry grad u_h in the tangent keep FP32 relative accuracy).
  * values: nnz outputs, FP64 for FEM_FP64 and FP32 otherwise.
  * u and values may be device pointers or host pointers; host pointers are
  * staged through library-owned device buffers and the call then synchronises
@@ -182,8 +184,8 @@ int fem_assemble_all(fem_mesh* mesh, const fem_coeff* k, const void* u, int prec
  * versus assemblage of the global matrices, line 12).
  * fem_form_elements forms V = X Q for the matrices selected by `which`
  * (FEM_MAT_M | FEM_MAT_K | FEM_MAT_T) into scratch buffers owned by the mesh
- * (one kernel launch); d_u is a device pointer (FP64 for FEM_FP64, FP32
- * otherwise; unused when which == FEM_MAT_M).
+ * (one kernel launch, plus the split of u for the FP32 paths); d_u is a
+ * device pointer to FP64 nodal values (unused when which == FEM_MAT_M).
  * fem_sum_elements sums the formed V into the CSR values (one kernel
  * launch); d_v* are device pointers, NULL to skip, and must have been formed
  * by the last fem_form_elements with the same `prec` (FEM_ESTATE otherwise).

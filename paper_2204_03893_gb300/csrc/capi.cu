@@ -109,14 +109,23 @@ CoeffDev to_dev(const fem_coeff* k) {
     if (!k) return c;
     c.kind = k->kind;
     c.n = k->n;
-    for (int i = 0; i < 16; ++i) c.p[i] = k->p[i];
+    if (k->kind == FEM_K_PWLIN) {
+        // device layout: knots in p[0..7], values in p[8..15]
+        const int m = k->n / 2;
+        for (int i = 0; i < m; ++i) {
+            c.p[i] = k->p[i];
+            c.p[8 + i] = k->p[m + i];
+        }
+    } else {
+        for (int i = 0; i < k->n; ++i) c.p[i] = k->p[i];   // unused parameters stay zero
+    }
     return c;
 }
 
 // Formation (Algorithm 2 lines 1-11): V for the matrices in `mask` (bit 0 M,
 // bit 1 K, bit 2 T) into the mesh's scratch buffers.
 template <typename T>
-int form_t(fem_mesh* m, const fem_coeff* k, const T* ud, int prec, int mask, cudaStream_t s) {
+int form_t(fem_mesh* m, const fem_coeff* k, const double* ud, int prec, int mask, cudaStream_t s) {
     const int64_t E = m->E;
     const int nsym = m->np * (m->np + 1) / 2, nt = m->np * m->np;
     int rc;
@@ -137,8 +146,14 @@ int form_t(fem_mesh* m, const fem_coeff* k, const T* ud, int prec, int mask, cud
     if constexpr (sizeof(T) == 8) {
         rc = element_simt_fp64(*m, kd, ud, VM, VK, VT, s);
     } else {
-        rc = prec == FEM_TF32X3 ? element_tc_tf32x3(*m, kd, ud, VM, VK, VT, s)
-                                : element_simt_fp32(*m, kd, ud, VM, VK, VT, s);
+        const float2* us = nullptr;
+        if (mask & 6) {
+            if ((rc = buf_alloc(m->u_split, sizeof(float2) * (size_t)m->n, s))) return rc;
+            us = m->u_split.as<float2>();
+            if ((rc = split_u(ud, m->n, m->u_split.as<float2>(), s))) return rc;
+        }
+        rc = prec == FEM_TF32X3 ? element_tc_tf32x3(*m, kd, us, VM, VK, VT, s)
+                                : element_simt_fp32(*m, kd, us, VM, VK, VT, s);
     }
     if (rc) return rc;
     m->v_prec = prec;
@@ -161,17 +176,17 @@ int assemble_t(fem_mesh* m, const fem_coeff* k, const void* u, int prec, void* v
                cudaStream_t s) {
     const int64_t nnz = m->nnz;
     bool host_io = false;
-    const T* ud = nullptr;
+    const double* ud = nullptr;
     int rc;
     if (vK || vT) {
         if (!u) return fail(FEM_EINVAL, "u is NULL");
         if (is_device_ptr(u)) {
-            ud = static_cast<const T*>(u);
+            ud = static_cast<const double*>(u);
         } else {
             host_io = true;
-            if ((rc = buf_alloc(m->u_stage, sizeof(T) * (size_t)m->n, s))) return rc;
-            FEM_CUDA_TRY(cudaMemcpyAsync(m->u_stage.ptr, u, sizeof(T) * (size_t)m->n, cudaMemcpyHostToDevice, s));
-            ud = m->u_stage.as<T>();
+            if ((rc = buf_alloc(m->u_stage, sizeof(double) * (size_t)m->n, s))) return rc;
+            FEM_CUDA_TRY(cudaMemcpyAsync(m->u_stage.ptr, u, sizeof(double) * (size_t)m->n, cudaMemcpyHostToDevice, s));
+            ud = m->u_stage.as<double>();
         }
     }
     void* outs[3] = {vM, vK, vT};
@@ -204,7 +219,7 @@ int assemble_t(fem_mesh* m, const fem_coeff* k, const void* u, int prec, void* v
 
 size_t fem_mesh::device_bytes() const {
     const fem::DevBuf* bufs[] = {&coords, &conn, &geo64, &geo32, &row_ptr, &col_idx, &seg_ptr, &contrib, &slot,
-                                 &inc_ptr, &inc, &VM, &VK, &VT, &u_stage, &out_stage};
+                                 &inc_ptr, &inc, &VM, &VK, &VT, &u_stage, &out_stage, &u_split};
     size_t t = 0;
     for (auto* b : bufs) t += b->bytes;
     return t;
@@ -298,7 +313,7 @@ int fem_mesh_destroy(fem_mesh* m) {
     cudaDeviceSynchronize();
     fem::DevBuf* bufs[] = {&m->coords, &m->conn, &m->geo64, &m->geo32, &m->row_ptr, &m->col_idx, &m->seg_ptr,
                            &m->contrib, &m->slot, &m->inc_ptr, &m->inc, &m->VM, &m->VK, &m->VT, &m->u_stage,
-                           &m->out_stage};
+                           &m->out_stage, &m->u_split};
     for (auto* b : bufs) buf_free(*b, nullptr);
     cudaDeviceSynchronize();
     delete m;
@@ -381,7 +396,7 @@ int fem_form_elements(fem_mesh* m, const fem_coeff* k, const void* d_u, int prec
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (prec == FEM_FP64) return form_t<double>(m, k, static_cast<const double*>(d_u), prec, which, s);
-    return form_t<float>(m, k, static_cast<const float*>(d_u), prec, which, s);
+    return form_t<float>(m, k, static_cast<const double*>(d_u), prec, which, s);
 }
 
 int fem_sum_elements(fem_mesh* m, int prec, void* d_vM, void* d_vK, void* d_vT, void* stream) {

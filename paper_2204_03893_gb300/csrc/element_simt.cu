@@ -46,10 +46,18 @@ struct Tabs<float> {
 
 constexpr int BT = 64;   // elements (threads) per block
 
+// nodal values: FP64 as given for the FP64 path; for the FP32 path the
+// host splits u = hi + lo (two FP32 values, see split_u) so that the
+// differences u_i - u_0 that carry the gradient keep FP32 relative accuracy.
+template <typename T>
+struct UType { using type = double; };
+template <>
+struct UType<float> { using type = float2; };
+
 template <typename ETy, typename T>
 __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict__ conn, const T* __restrict__ geo,
-                                                          int64_t E, const T* __restrict__ u, CoeffDev k, T mass,
-                                                          T* __restrict__ VM, T* __restrict__ VK,
+                                                          int64_t E, const typename UType<T>::type* __restrict__ u,
+                                                          CoeffDev k, T mass, T* __restrict__ VM, T* __restrict__ VK,
                                                           T* __restrict__ VT) {
     constexpr int D = ETy::D, NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS;
     constexpr int KM = ETy::KM, KK = ETy::KK, KT = ETy::KT;
@@ -67,11 +75,28 @@ __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict_
     for (int64_t e0 = (int64_t)blockIdx.x * BT; e0 < E; e0 += (int64_t)gridDim.x * BT) {
         int64_t e = e0 + threadIdx.x;
         if (e >= E) continue;
-        T ue[NP];
+        // du[i] = u_i - u_0 and u_0 (u is only needed for K and T; mass-only calls pass NULL)
+        T du[NP];
+        T u0 = T(0);
         const int* ce = conn + e * NP;
-        // u is only needed for K and T (mass-only calls pass u = NULL)
+        if (need_u) {
+            if constexpr (sizeof(T) == 8) {
+                u0 = u[ce[0]];
 #pragma unroll
-        for (int i = 0; i < NP; ++i) ue[i] = need_u ? u[ce[i]] : T(0);
+                for (int i = 0; i < NP; ++i) du[i] = u[ce[i]] - u0;
+            } else {
+                const float2 a = u[ce[0]];
+                u0 = a.x + a.y;
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    const float2 b = u[ce[i]];
+                    du[i] = (b.x - a.x) + (b.y - a.y);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) du[i] = T(0);
+        }
         T b = geo[e];
         T A[NS];
 #pragma unroll
@@ -79,16 +104,19 @@ __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict_
         // --- X = Lambda, Lambda (.) W, tangent factors
 #pragma unroll 1
         for (int q = 0; q < NQ; ++q) {
+            // u_q = u_0 + sum_i phi_i (u_i - u_0) (the basis sums to one); the
+            // reference gradient uses the differences only (its rows sum to zero)
             T uq = T(0);
             T g[D];
 #pragma unroll
             for (int a = 0; a < D; ++a) g[a] = T(0);
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                uq += Tabs<T>::ref(PHI + q * NP + i) * ue[i];
+                uq += Tabs<T>::ref(PHI + q * NP + i) * du[i];
 #pragma unroll
-                for (int a = 0; a < D; ++a) g[a] += Tabs<T>::ref(GR + (q * NP + i) * D + a) * ue[i];
+                for (int a = 0; a < D; ++a) g[a] += Tabs<T>::ref(GR + (q * NP + i) * D + a) * du[i];
             }
+            uq += u0;
             T dk;
             T kq = k_eval<T>(k, uq, dk);
             T lam = Tabs<T>::ref(WQ + q) * b;
@@ -137,14 +165,24 @@ __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict_
     }
 }
 
+__global__ void split_u_kernel(const double* __restrict__ u, int64_t n, float2* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = u[i];
+        const float hi = (float)v;
+        out[i] = make_float2(hi, (float)(v - (double)hi));
+    }
+}
+
 template <typename ETy, typename T>
-int launch_simt(const fem_mesh& m, const CoeffDev& k, const T* u, const T* geo, T* VM, T* VK, T* VT,
-                cudaStream_t s) {
+int launch_simt(const fem_mesh& m, const CoeffDev& k, const typename UType<T>::type* u, const T* geo, T* VM, T* VK,
+                T* VT, cudaStream_t s) {
     constexpr int KTOT = ETy::KM + ETy::KK + ETy::KT;
     constexpr int LD = KTOT | 1;
     size_t smem = sizeof(T) * (size_t)LD * BT;
     auto kern = element_simt_kernel<ETy, T>;
     FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
     int dev = 0, nsm = 0, per_sm = 0;
     FEM_CUDA_TRY(cudaGetDevice(&dev));
     FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -161,7 +199,8 @@ int launch_simt(const fem_mesh& m, const CoeffDev& k, const T* u, const T* geo, 
 }
 
 template <typename T>
-int dispatch(const fem_mesh& m, const CoeffDev& k, const T* u, const T* geo, T* VM, T* VK, T* VT, cudaStream_t s) {
+int dispatch(const fem_mesh& m, const CoeffDev& k, const typename UType<T>::type* u, const T* geo, T* VM, T* VK,
+             T* VT, cudaStream_t s) {
     switch (m.type) {
         case 0: return launch_simt<ET<2, 1>, T>(m, k, u, geo, VM, VK, VT, s);
         case 1: return launch_simt<ET<2, 2>, T>(m, k, u, geo, VM, VK, VT, s);
@@ -215,7 +254,17 @@ int element_simt_fp64(const fem_mesh& m, const CoeffDev& k, const double* u, dou
     return dispatch<double>(m, k, u, m.geo64.as<double>(), VM, VK, VT, s);
 }
 
-int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const float* u, float* VM, float* VK, float* VT,
+int split_u(const double* u, int64_t n, float2* out, cudaStream_t s) {
+    if (n <= 0) return FEM_OK;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    cudaGetLastError();   // clear any stale error before the launch check
+    split_u_kernel<<<(unsigned)blocks, 256, 0, s>>>(u, n, out);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
                       cudaStream_t s) {
     int rc = tables_init_simt();
     if (rc) return rc;

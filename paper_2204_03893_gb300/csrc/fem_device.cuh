@@ -63,11 +63,16 @@ struct CoeffDev {
     double p[16];
 };
 
+// k(u) and k'(u).  Loops run over the fixed maxima (8 polynomial
+// coefficients, 8 knots) with predicates so that the parameters stay in the
+// kernel-parameter space instead of being copied to local memory; unused
+// parameters are zero.
 template <typename T>
 __device__ __forceinline__ T k_eval(const CoeffDev& c, T u, T& dk) {
     if (c.kind == 0) {
         T v = T(0), dv = T(0);
-        for (int i = c.n - 1; i >= 0; --i) {
+#pragma unroll
+        for (int i = 7; i >= 0; --i) {
             dv = dv * u + v;      // Horner for the derivative uses the running value
             v = v * u + T(c.p[i]);
         }
@@ -81,16 +86,32 @@ __device__ __forceinline__ T k_eval(const CoeffDev& c, T u, T& dk) {
         dk = T(c.p[1]) * g * co;
         return T(c.p[0]) + T(c.p[1]) * s;
     } else {
-        int m = c.n / 2;
-        const double* t = c.p;
-        const double* kv = c.p + m;
-        if (u < T(t[0])) { dk = T(0); return T(kv[0]); }
-        if (u > T(t[m - 1])) { dk = T(0); return T(kv[m - 1]); }
-        int i = 0;
-        while (i + 2 < m && u > T(t[i + 1])) ++i;
-        T sl = T((kv[i + 1] - kv[i]) / (t[i + 1] - t[i]));
-        dk = sl;
-        return T(kv[i]) + sl * (u - T(t[i]));
+        // device layout (set by the host): knots in p[0..7], values in p[8..15], m = n/2 knots
+        const int m = c.n / 2;
+        T val = T(0), slope = T(0), last = T(0);
+        bool found = false;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (i < m) last = T(c.p[8 + i]);
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            if (i + 1 < m && !found) {
+                const T t0 = T(c.p[i]), t1 = T(c.p[i + 1]);
+                // branch i covers (t_i, t_i+1]; the first one is closed on the left too
+                const bool in = (i == 0) ? (u >= t0 && u <= t1) : (u > t0 && u <= t1);
+                if (in) {
+                    slope = T((c.p[8 + i + 1] - c.p[8 + i]) / (c.p[i + 1] - c.p[i]));
+                    val = T(c.p[8 + i]) + slope * (u - t0);
+                    found = true;
+                }
+            }
+        }
+        if (!found) {
+            slope = T(0);
+            val = (u < T(c.p[0])) ? T(c.p[8]) : last;
+        }
+        dk = slope;
+        return val;
     }
 }
 

@@ -54,6 +54,7 @@ struct fem_mesh {
     int v_prec = -1, v_mask = 0;        // what VM/VK/VT currently hold
     // staging for host-pointer arguments
     fem::DevBuf u_stage, out_stage;
+    fem::DevBuf u_split;                // FP32 paths: u as (hi, lo) float pairs
     size_t device_bytes() const;
 };
 
@@ -66,10 +67,12 @@ int symbolic_run(fem_mesh& m, cudaStream_t s);           // fills pattern and se
 // Element products V = X Q.  Any of VM, VK, VT may be null (matrix skipped).
 int element_simt_fp64(const fem_mesh& m, const CoeffDev& k, const double* u, double* VM, double* VK, double* VT,
                       cudaStream_t s);
-int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const float* u, float* VM, float* VK, float* VT,
+// FP32 paths take the nodal values split as u = hi + lo (float2), see split_u.
+int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
                       cudaStream_t s);
-int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const float* u, float* VM, float* VK, float* VT,
+int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
                       cudaStream_t s);
+int split_u(const double* u, int64_t n, float2* out, cudaStream_t s);
 
 // Segmented reduction of V into CSR values (outputs may be null).
 int scatter_fp64(const fem_mesh& m, const double* VM, const double* VK, const double* VT, double* vM, double* vK,

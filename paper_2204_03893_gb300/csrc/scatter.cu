@@ -15,6 +15,15 @@ namespace fem {
 
 namespace {
 
+template <typename T>
+__device__ __forceinline__ void store_stream(T* p, T v) {
+    __stcs(p, v);   // outputs are not re-read by this kernel: evict-first
+}
+
+// Each thread sums SPT slots spaced blockDim.x apart (coalesced across the
+// warp) with independent load chains, so that several gathers are in flight.
+constexpr int SPT = 4;
+
 template <int NP, typename T>
 __global__ void __launch_bounds__(256) scatter_kernel(const int* __restrict__ seg_ptr, const int* __restrict__ contrib,
                                                       int64_t nnz, const T* __restrict__ VM, const T* __restrict__ VK,
@@ -22,25 +31,49 @@ __global__ void __launch_bounds__(256) scatter_kernel(const int* __restrict__ se
                                                       T* __restrict__ vK, T* __restrict__ vT) {
     constexpr int NT = NP * NP, NSYM = NP * (NP + 1) / 2;
     const bool dM = vM != nullptr, dK = vK != nullptr, dT = vT != nullptr;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x) {
-        const int a = seg_ptr[s], b = seg_ptr[s + 1];
-        T am = T(0), ak = T(0), at = T(0);
-        for (int p = a; p < b; ++p) {
-            const int c = contrib[p];
-            const int e = c / NT;
-            const int l = c - e * NT;
-            if (dT) at += VT[(int64_t)e * NT + l];
-            if (dM | dK) {
-                const int i = l / NP, j = l - (l / NP) * NP;
-                const int lo = i < j ? i : j, hi = i < j ? j : i;
-                const int si = lo * NP - (lo * (lo - 1)) / 2 + (hi - lo);
-                if (dM) am += VM[(int64_t)e * NSYM + si];
-                if (dK) ak += VK[(int64_t)e * NSYM + si];
+    const int64_t chunk = (int64_t)blockDim.x * SPT;
+    for (int64_t base = blockIdx.x * chunk; base < nnz; base += (int64_t)gridDim.x * chunk) {
+        int a[SPT], b[SPT];
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+            const int64_t s = base + k * blockDim.x + threadIdx.x;
+            a[k] = s < nnz ? __ldg(seg_ptr + s) : 0;
+            b[k] = s < nnz ? __ldg(seg_ptr + s + 1) : 0;
+        }
+        T am[SPT], ak[SPT], at[SPT];
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) am[k] = ak[k] = at[k] = T(0);
+        int len = 0;
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) len = max(len, b[k] - a[k]);
+        for (int p = 0; p < len; ++p) {
+            int c[SPT];
+#pragma unroll
+            for (int k = 0; k < SPT; ++k) c[k] = (a[k] + p < b[k]) ? __ldg(contrib + a[k] + p) : -1;
+#pragma unroll
+            for (int k = 0; k < SPT; ++k) {
+                if (c[k] < 0) continue;
+                const int e = c[k] / NT;
+                const int l = c[k] - e * NT;
+                if (dT) at[k] += __ldg(VT + (int64_t)e * NT + l);
+                if (dM | dK) {
+                    const int i = l / NP, j = l - (l / NP) * NP;
+                    const int lo = i < j ? i : j, hi = i < j ? j : i;
+                    const int si = lo * NP - (lo * (lo - 1)) / 2 + (hi - lo);
+                    if (dM) am[k] += __ldg(VM + (int64_t)e * NSYM + si);
+                    if (dK) ak[k] += __ldg(VK + (int64_t)e * NSYM + si);
+                }
             }
         }
-        if (dM) vM[s] = am;
-        if (dK) vK[s] = ak;
-        if (dT) vT[s] = at;
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+            const int64_t s = base + k * blockDim.x + threadIdx.x;
+            if (s < nnz) {
+                if (dM) store_stream(vM + s, am[k]);
+                if (dK) store_stream(vK + s, ak[k]);
+                if (dT) store_stream(vT + s, at[k]);
+            }
+        }
     }
 }
 
@@ -50,8 +83,8 @@ int run(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, 
     int dev = 0, nsm = 0;
     FEM_CUDA_TRY(cudaGetDevice(&dev));
     FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    int64_t blocks = (m.nnz + 255) / 256;
-    if (blocks > (int64_t)nsm * 16) blocks = (int64_t)nsm * 16;
+    int64_t blocks = (m.nnz + 256 * SPT - 1) / (256 * SPT);
+    if (blocks > (int64_t)nsm * 8) blocks = (int64_t)nsm * 8;
     const int* sp = m.seg_ptr.as<int>();
     const int* ct = m.contrib.as<int>();
     cudaGetLastError();   // clear any stale error before the launch check

@@ -2,9 +2,9 @@
 
 Bars (per matrix M, K(u), T(u)):
   * pattern (row_ptr, col_idx) and slot map: bit-exact;
-  * FEM_FP64: |gpu - oracle| <= 1e-12 * absum per entry, absum = sum of the
-    absolute element contributions of the slot (entries that cancel are
-    judged against the size of what cancelled);
+  * FEM_FP64: |gpu - oracle| <= 1e-12 * absum per entry, absum = the
+    oracle's sum of the magnitudes of the expanded quadrature terms of the
+    slot (entries that cancel are judged against the size of what cancelled);
   * FEM_TF32X3: relative Frobenius error <= 1e-6 per matrix;
   * FEM_FP32 (SIMT reference point): relative Frobenius error <= 1e-5;
   * every precision: bitwise identical results run to run.
@@ -49,8 +49,7 @@ def _p3(d):
 
 
 def gpu_assemble(fm, wl, prec):
-    dt = torch.float64 if prec == "fp64" else torch.float32
-    u = torch.tensor(wl.u, dtype=dt, device="cuda")
+    u = torch.tensor(wl.u, dtype=torch.float64, device="cuda")   # u is FP64 in every precision
     out = fm.assemble(u, wl.coeff.kind, wl.coeff.params, prec)
     torch.cuda.synchronize()
     return {k: v.double().cpu().numpy() for k, v in out.items()}
@@ -138,8 +137,7 @@ def test_fp32_simt_parity_frobenius(name):
 def test_run_to_run_bitwise(prec):
     wl = wl_small("tri_p2")
     fm = FemMesh.of(wl.mesh)
-    dt = torch.float64 if prec == "fp64" else torch.float32
-    u = torch.tensor(wl.u, dtype=dt, device="cuda")
+    u = torch.tensor(wl.u, dtype=torch.float64, device="cuda")
     a = fm.assemble(u, wl.coeff.kind, wl.coeff.params, prec)
     a = {k: v.clone() for k, v in a.items()}
     for _ in range(3):
@@ -151,7 +149,7 @@ def test_run_to_run_bitwise(prec):
 def test_separate_entry_points_match_all():
     wl = wl_small("tet_p2")
     fm = FemMesh.of(wl.mesh)
-    u = torch.tensor(wl.u, dtype=torch.float32, device="cuda")
+    u = torch.tensor(wl.u, dtype=torch.float64, device="cuda")
     both = fm.assemble(u, wl.coeff.kind, wl.coeff.params, "tf32x3")
     both = {k: v.clone() for k, v in both.items()}
     for k in ("M", "K", "T"):
@@ -169,7 +167,7 @@ def test_host_pointer_path_matches_device(prec):
     fm = FemMesh.of(wl.mesh)
     fm.symbolic()
     dt = np.float64 if prec == "fp64" else np.float32
-    uh = np.ascontiguousarray(wl.u, dtype=dt)
+    uh = np.ascontiguousarray(wl.u, dtype=np.float64)
     outs = {k: np.zeros(fm.nnz, dtype=dt) for k in "MKT"}
     F.fem_assemble_all(fm.h, F.coeff(wl.coeff.kind, wl.coeff.params), uh, F.torch_api.PRECISIONS[prec],
                        outs["M"], outs["K"], outs["T"])
@@ -193,6 +191,41 @@ def test_coefficient_laws():
         for k in ("K", "T"):
             gk = g[k].cpu().numpy()
             assert (np.abs(gk - r[k]) <= FP64_TOL * r["abs" + k] + 1e-300).all(), (c.kind, k)
+
+
+@pytest.mark.parametrize("law", [("sin", (2.0, 1.0, 3.0), 1.0, 0.0),
+                                 ("pwlin", (0.0, 200.0, 1000.0, 1.5, 0.7, 0.5), 1200.0, -100.0)])
+def test_tf32x3_coefficient_laws(law):
+    kind, params, scale, shift = law
+    m = mg.structured_tet(5, 2, 0.15, seed=8)
+    u = scale * mg.fourier_field(m.coords, 9) + shift
+    c = mg.Coeff(kind, params)
+    r = orc.Oracle.of(m).assemble(u, c)
+    g = FemMesh.of(m).assemble(torch.tensor(u, device="cuda"), kind, params, "tf32x3")
+    for k in ("M", "K", "T"):
+        assert frob(g[k].double().cpu().numpy(), r[k]) <= TF32_TOL, k
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_form_and_sum_phases(prec):
+    """fem_form_elements + fem_sum_elements == fem_assemble_all, bit for bit;
+    summing with another precision than was formed is refused."""
+    wl = wl_small("tri_p3")
+    fm = FemMesh.of(wl.mesh)
+    u = torch.tensor(wl.u, dtype=torch.float64, device="cuda")
+    ref = {k: v.clone() for k, v in fm.assemble(u, wl.coeff.kind, wl.coeff.params, prec).items()}
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    out = {k: torch.empty(fm.nnz, dtype=dt, device="cuda") for k in "MKT"}
+    pc = F.torch_api.PRECISIONS[prec]
+    F.fem_form_elements(fm.h, F.coeff(wl.coeff.kind, wl.coeff.params), u, pc, F.FEM_MAT_M | F.FEM_MAT_K | F.FEM_MAT_T)
+    F.fem_sum_elements(fm.h, pc, out["M"], out["K"], out["T"])
+    torch.cuda.synchronize()
+    for k in "MKT":
+        assert torch.equal(out[k], ref[k]), k
+    other = F.FEM_FP32 if prec == "fp64" else F.FEM_FP64
+    with pytest.raises(F.FemError) as ei:
+        F.fem_sum_elements(fm.h, other, out["M"], None, None)
+    assert ei.value.code == F.FEM_ESTATE
 
 
 def test_mass_coefficient_scales():
@@ -242,7 +275,7 @@ def test_sliver_elements_use_fp64_geometry():
     u = mg.uniform_field(m.n_nodes, 4)
     c = mg.Coeff("poly", (1.0, 0.5, 0.25, 0.0, 0.0))
     o = orc.Oracle.of(m).assemble(u, c)
-    g = fm.assemble(torch.tensor(u, dtype=torch.float32, device="cuda"), c.kind, c.params, "tf32x3")
+    g = fm.assemble(torch.tensor(u, dtype=torch.float64, device="cuda"), c.kind, c.params, "tf32x3")
     for k in ("M", "K", "T"):
         assert frob(g[k].double().cpu().numpy(), o[k]) <= TF32_TOL, k
 
