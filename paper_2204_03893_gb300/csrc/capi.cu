@@ -431,6 +431,7 @@ int fem_device_status(void* stream) {
     FEM_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
     int f = tc_error_flag(1);
     if (f < 0) return fail(FEM_ECUDA, "cannot read device status word");
+    if (f == 2) return fail(FEM_ECUDA, "a tensor-core kernel was launched with a wrong configuration and did not run");
     if (f) return fail(FEM_ETIMEOUT, "a tensor-core kernel gave up waiting for its MMA completion");
     return FEM_OK;
 }

@@ -175,6 +175,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) element_tc_kernel(
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    {   // self-check of the launch configuration (uniform over the CTA)
+        uint32_t dsmem;
+        asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsmem));
+        if (dsmem < (uint32_t)L::SMEM || blockDim.x != NTHREADS) {
+            if (tid == 0) atomicExch(err, 2);
+            return;
+        }
+    }
     unsigned char* sQ = smem;
     unsigned char* sX = smem + L::QEND;
     float* sStage = reinterpret_cast<float*>(smem + L::QEND + L::XEND);
@@ -307,7 +315,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) element_tc_kernel(
             tc::fence_before_sync();
             mbar_arrive(buf ? mb_emp1 : mb_emp0);
         }
-    } else if (lane == 0) {
+    } else {
+      if (lane == 0) {
         // ------------------------------------------------------------ MMA issuer
         int j = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
@@ -327,11 +336,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) element_tc_kernel(
                                      tc::idesc_tf32(L::NTp));
             tc::mma_commit(buf ? mb_mma1 : mb_mma0);
         }
-        if (*abortp && j > 0) {
-            // let the last committed MMAs drain (bounded) before the memory is released
+        if (j > 0) {
+            // the last committed MMAs must have completed before the tensor memory
+            // is released (normally the epilogue already waited for them)
             const int jl = j - 1;
             tc::mbar_wait_bounded((jl & 1) ? mb_mma1 : mb_mma0, (jl >> 1) & 1, WAIT_LIMIT);
         }
+      }
+      __syncwarp();   // reconverge the issuer warp before the CTA-wide (aligned) barrier
     }
     __syncthreads();
     if (tid == 0 && abort_flag) atomicExch(err, 1);
