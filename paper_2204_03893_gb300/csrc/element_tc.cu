@@ -8,7 +8,8 @@
 //     Section 4.2; the tangent factors of the Section 5.2 tensor multiplied
 //     by u), splits it as X = Xhi + Xlo with exact TF32 parts and stores it
 //     into the K-major shared-memory operand layout;
-//   * warp 8 (issuer): one thread issues, per K step of 8,
+//   * after a named barrier among the producers, producer thread 0 issues,
+//     per K step of 8,
 //         D += Xhi Qhi ; D += Xhi Qlo ; D += Xlo Qhi
 //     for M, K and T into a TMEM buffer (D: 128 lanes = elements, columns =
 //     entries) and commits to that buffer's mbarrier; TMEM is double
@@ -42,7 +43,7 @@ __host__ __device__ constexpr int pow2_at_least(int x) {
 }
 
 constexpr int TILE = 128;
-constexpr int NTHREADS = 9 * 32;   // 4 producer warps, 4 epilogue warps, 1 MMA warp
+constexpr int NTHREADS = 8 * 32;   // two complete warpgroups: producers (+ MMA issue), epilogue
 constexpr int STAGE_FLOATS = 4 * 32 * 33;
 constexpr int SMEM_MAX = 227 * 1024;
 constexpr int IMG_SLOT_FLOATS = 24 * 1024;   // 96 KiB per element type
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) element_tc_kernel(
     constexpr int TO = type_tab_off(ETy::TYPE);
     constexpr int PHI = TO, GR = TO + NQ * NP, WQ = TO + NQ * NP * (1 + D);
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_full, bar_mma[2], bar_empty[2];
+    __shared__ __align__(8) uint64_t bar_mma[2], bar_empty[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -192,11 +193,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) element_tc_kernel(
         int4* dst = reinterpret_cast<int4*>(sQ);
         for (int i = tid; i < L::QEND / 16; i += NTHREADS) dst[i] = src[i];
     }
-    const uint32_t mb_full = tc::smem_u32(&bar_full);
     const uint32_t mb_mma0 = tc::smem_u32(&bar_mma[0]), mb_mma1 = tc::smem_u32(&bar_mma[1]);
     const uint32_t mb_emp0 = tc::smem_u32(&bar_empty[0]), mb_emp1 = tc::smem_u32(&bar_empty[1]);
     if (tid == 0) {
-        tc::mbar_init(mb_full, TILE);
         tc::mbar_init(mb_mma0, 1);
         tc::mbar_init(mb_mma1, 1);
         tc::mbar_init(mb_emp0, TILE);
@@ -204,7 +203,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) element_tc_kernel(
         abort_flag = 0;
         tc::fence_mbar_init();
     }
-    if (warp == 8) {
+    if (warp == 0) {
         tc::tmem_alloc(tc::smem_u32(&tmem_slot), L::TALLOC);
         tc::tmem_relinquish();
     }
@@ -219,7 +218,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) element_tc_kernel(
     const int64_t ntiles = (E + TILE - 1) / TILE;
 
     if (warp < 4) {
-        // ------------------------------------------------------------ producers
+        // ------------------------------------------------ warpgroup 0: producers
         int j = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
             const int64_t e = tile * TILE + tid;
@@ -287,19 +286,60 @@ __global__ void __launch_bounds__(NTHREADS, 1) element_tc_kernel(
                 }
             }
             // the X buffer is free once the previous tile's MMAs have completed
-            if (j >= 1) {
-                const bool ok = wait_or_abort(((j - 1) & 1) ? mb_mma1 : mb_mma0, ((j - 1) >> 1) & 1, abortp);
-                if (!__all_sync(0xffffffffu, ok)) break;   // warp-uniform exit
+            bool ok = true;
+            if (j >= 1) ok = wait_or_abort(((j - 1) & 1) ? mb_mma1 : mb_mma0, ((j - 1) >> 1) & 1, abortp);
+            ok = __all_sync(0xffffffffu, ok);
+            if (ok) {
+                if (doM) store_row<L::KMp>(sX + L::XMh, sX + L::XMl, xm, tid);
+                if (doK) store_row<L::KKp>(sX + L::XKh, sX + L::XKl, xk, tid);
+                if (doT) store_row<L::KTp>(sX + L::XTh, sX + L::XTl, xt, tid);
+                tc::fence_proxy_async_smem();
             }
-            if (doM) store_row<L::KMp>(sX + L::XMh, sX + L::XMl, xm, tid);
-            if (doK) store_row<L::KKp>(sX + L::XKh, sX + L::XKl, xk, tid);
-            if (doT) store_row<L::KTp>(sX + L::XTh, sX + L::XTl, xt, tid);
-            tc::fence_proxy_async_smem();
-            mbar_arrive(mb_full);
+            // all producers of this tile have stored X (named barrier 1, warpgroup 0
+            // only); the barrier also ORs the abort flag so that the exit is uniform
+            {
+                const int ab = *abortp ? 1 : 0;
+                int any;
+                asm volatile(
+                    "{\n\t.reg .pred p, q;\n\t"
+                    "setp.ne.s32 q, %1, 0;\n\t"
+                    "bar.red.or.pred p, 1, 128, q;\n\t"
+                    "selp.s32 %0, 1, 0, p;\n\t}\n"
+                    : "=r"(any)
+                    : "r"(ab)
+                    : "memory");
+                if (any) break;
+            }
+            if (tid == 0) {
+                const uint32_t buf = j & 1;
+                bool free_ok = true;
+                if (j >= 2) free_ok = wait_or_abort(buf ? mb_emp1 : mb_emp0, ((j >> 1) - 1) & 1, abortp);
+                if (free_ok) {
+                    tc::fence_after_sync();
+                    const uint32_t tb = tmem + buf * L::ALLOC;
+                    if (doM)
+                        issue_tf32x3<L::KMp>(tb + L::COLM, sXu + L::XMh, sXu + L::XMl, sQu + L::QMh, sQu + L::QMl,
+                                             tc::idesc_tf32(L::NMp));
+                    if (doK)
+                        issue_tf32x3<L::KKp>(tb + L::COLK, sXu + L::XKh, sXu + L::XKl, sQu + L::QKh, sQu + L::QKl,
+                                             tc::idesc_tf32(L::NMp));
+                    if (doT)
+                        issue_tf32x3<L::KTp>(tb + L::COLT, sXu + L::XTh, sXu + L::XTl, sQu + L::QTh, sQu + L::QTl,
+                                             tc::idesc_tf32(L::NTp));
+                    tc::mma_commit(buf ? mb_mma1 : mb_mma0);
+                }
+            }
+            __syncwarp();
         }
-    } else if (warp < 8) {
-        // ------------------------------------------------------------ epilogue
-        const int c4 = warp - 4;                       // TMEM lanes 32*c4 .. 32*c4+31
+        if (tid == 0 && j > 0 && *abortp) {
+            // let the last committed MMAs drain (bounded) before the memory is released
+            const int jl = j - 1;
+            tc::mbar_wait_bounded((jl & 1) ? mb_mma1 : mb_mma0, (jl >> 1) & 1, WAIT_LIMIT);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ warpgroup 1: epilogue
+        const int c4 = warp - 4;                       // warpgroup rank: TMEM lanes 32*c4 .. 32*c4+31
         float* stage = sStage + c4 * 32 * 33;
         int j = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
@@ -315,40 +355,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) element_tc_kernel(
             tc::fence_before_sync();
             mbar_arrive(buf ? mb_emp1 : mb_emp0);
         }
-    } else {
-      if (lane == 0) {
-        // ------------------------------------------------------------ MMA issuer
-        int j = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
-            const uint32_t buf = j & 1;
-            if (!wait_or_abort(mb_full, j & 1, abortp)) break;
-            if (j >= 2 && !wait_or_abort(buf ? mb_emp1 : mb_emp0, ((j >> 1) - 1) & 1, abortp)) break;
-            tc::fence_after_sync();
-            const uint32_t tb = tmem + buf * L::ALLOC;
-            if (doM)
-                issue_tf32x3<L::KMp>(tb + L::COLM, sXu + L::XMh, sXu + L::XMl, sQu + L::QMh, sQu + L::QMl,
-                                     tc::idesc_tf32(L::NMp));
-            if (doK)
-                issue_tf32x3<L::KKp>(tb + L::COLK, sXu + L::XKh, sXu + L::XKl, sQu + L::QKh, sQu + L::QKl,
-                                     tc::idesc_tf32(L::NMp));
-            if (doT)
-                issue_tf32x3<L::KTp>(tb + L::COLT, sXu + L::XTh, sXu + L::XTl, sQu + L::QTh, sQu + L::QTl,
-                                     tc::idesc_tf32(L::NTp));
-            tc::mma_commit(buf ? mb_mma1 : mb_mma0);
-        }
-        if (j > 0) {
-            // the last committed MMAs must have completed before the tensor memory
-            // is released (normally the epilogue already waited for them)
-            const int jl = j - 1;
-            tc::mbar_wait_bounded((jl & 1) ? mb_mma1 : mb_mma0, (jl >> 1) & 1, WAIT_LIMIT);
-        }
-      }
-      __syncwarp();   // reconverge the issuer warp before the CTA-wide (aligned) barrier
     }
     __syncthreads();
     if (tid == 0 && abort_flag) atomicExch(err, 1);
     tc::fence_after_sync();
-    if (warp == 8) tc::tmem_dealloc(tmem, L::TALLOC);
+    if (warp == 0) tc::tmem_dealloc(tmem, L::TALLOC);
 }
 
 // host-side TF32 rounding, nearest with ties away from zero (matches cvt.rna)
