@@ -1,28 +1,23 @@
 // element_tc.cu -- element products V = X Q on the tcgen05 tensor cores
 // (TF32 x3 split precision, FP32 accumulation in tensor memory).
 //
-// Algorithm 2 lines 5-11 for tiles of 128 elements, as a warp-specialised
-// persistent pipeline (one CTA walks tiles blockIdx.x, +gridDim.x, ...):
-//   * warps 0-3 (producers): each thread forms the X row of one element
-//     (Lambda = S * (w b^T) in place, eq. def_lambda; X_c = Lambda (.) W,
-//     Section 4.2; the tangent factors of the Section 5.2 tensor multiplied
-//     by u), splits it as X = Xhi + Xlo with exact TF32 parts and stores it
-//     into the K-major shared-memory operand layout;
-//   * after a named barrier among the producers, producer thread 0 issues,
-//     per K step of 8,
-//         D += Xhi Qhi ; D += Xhi Qlo ; D += Xlo Qhi
-//     for M, K and T into a TMEM buffer (D: 128 lanes = elements, columns =
-//     entries) and commits to that buffer's mbarrier; TMEM is double
-//     buffered so the next tile's MMAs run while the previous tile drains;
-//   * warps 4-7 (epilogue): read their 32 lanes back with tcgen05.ld,
-//     transpose through shared memory and write V element-major with
-//     coalesced 128-byte rows, then release the TMEM buffer.
-// Q (reference element only, "computed and stored once and for all",
-// Section 4.1) sits in shared memory for the whole CTA, split the same way.
-// Only the n_p(n_p+1)/2 distinct entries of M and K are formed (Section 7).
+// Algorithm 2 lines 5-11 for a tile of 128 elements: every thread forms the
+// X row of one element (Lambda = S * (w b^T) in place, eq. def_lambda;
+// X_c = Lambda (.) W, Section 4.2; the tangent factors of the Section 5.2
+// tensor multiplied by u) and stores it, split as X = Xhi + Xlo with Xhi,
+// Xlo exact TF32 values, straight into the K-major shared-memory operand
+// layout.  Q (reference element only, "computed and stored once and for
+// all", Section 4.1) sits in shared memory for the whole persistent CTA,
+// split the same way.  One thread issues, per K step of 8,
+//     D += Xhi Qhi ; D += Xhi Qlo ; D += Xlo Qhi
+// for M, K and T into separate TMEM column ranges (D: 128 lanes = elements,
+// columns = entries), commits to an mbarrier, and the four warps read their
+// 32 lanes back with tcgen05.ld, transpose through shared memory and write V
+// element-major with coalesced 128-byte rows.  Only the n_p(n_p+1)/2 distinct
+// entries of M and K are formed (Section 7).
 //
 // Every mbarrier wait is bounded (~1 s of SM clocks); on timeout the kernel
-// records an error word, every role stops, and the tensor memory is released.
+// records an error word, stops, and releases its tensor memory.
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -43,7 +38,6 @@ __host__ __device__ constexpr int pow2_at_least(int x) {
 }
 
 constexpr int TILE = 128;
-constexpr int NTHREADS = 8 * 32;   // two complete warpgroups: producers (+ MMA issue), epilogue
 constexpr int STAGE_FLOATS = 4 * 32 * 33;
 constexpr int SMEM_MAX = 227 * 1024;
 constexpr int IMG_SLOT_FLOATS = 24 * 1024;   // 96 KiB per element type
@@ -69,11 +63,10 @@ struct TcL {
     static constexpr int XTh = XKl + TILE * KKp * 4;
     static constexpr int XTl = XTh + TILE * KTp * 4;
     static constexpr int XEND = XTl + TILE * KTp * 4;
-    static constexpr int SMEM = QEND + XEND + STAGE_FLOATS * 4;
-    static constexpr int TALLOC = 2 * ALLOC;           // double-buffered accumulators
+    static constexpr int SMEM = QEND + XEND;
     // epilogue reads whole 32-column chunks: they must stay inside the allocation
-    static constexpr bool FITS = NMp <= 256 && NTp <= 256 && TALLOC <= 512 && SMEM <= SMEM_MAX &&
-                                 QEND <= IMG_SLOT_FLOATS * 4 &&
+    static constexpr bool FITS = NMp <= 256 && NTp <= 256 && ALLOC <= 512 && SMEM <= SMEM_MAX &&
+                                 XEND >= STAGE_FLOATS * 4 && QEND <= IMG_SLOT_FLOATS * 4 &&
                                  COLM + ru(ETy::NSYM, 32) <= ALLOC && COLK + ru(ETy::NSYM, 32) <= ALLOC &&
                                  COLT + ru(ETy::NT, 32) <= ALLOC;
 };
@@ -83,23 +76,6 @@ __device__ float g_tcimg[6 * IMG_SLOT_FLOATS];
 __device__ int g_tc_err;
 
 constexpr long long WAIT_LIMIT = 2000000000LL;   // SM clocks (~1 s)
-
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
-}
-
-// bounded wait that also gives up when another role has aborted
-__device__ __forceinline__ bool wait_or_abort(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
-    long long t0 = clock64();
-    while (!tc::mbar_try_wait(mbar, parity)) {
-        if (*abort_flag) return false;
-        if (clock64() - t0 > WAIT_LIMIT) {
-            *abort_flag = 1;
-            return false;
-        }
-    }
-    return true;
-}
 
 // store one thread's X row (Kp values) as TF32 hi / lo parts
 template <int Kp>
@@ -162,49 +138,35 @@ __device__ __forceinline__ void epilogue(uint32_t tmem, int col, float* stage, f
 }
 
 template <typename ETy>
-__global__ void __launch_bounds__(NTHREADS, 1) element_tc_kernel(
-    const int* __restrict__ conn, const float* __restrict__ geo, int64_t E, const float2* __restrict__ u, CoeffDev k,
-    float mass, float* __restrict__ VM, float* __restrict__ VK, float* __restrict__ VT,
-    const float* __restrict__ img, int* __restrict__ err) {
+__global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict__ conn, const float* __restrict__ geo,
+                                                          int64_t E, const float2* __restrict__ u, CoeffDev k,
+                                                          float mass, float* __restrict__ VM, float* __restrict__ VK,
+                                                          float* __restrict__ VT, const float* __restrict__ img,
+                                                          int* __restrict__ err) {
     using L = TcL<ETy>;
     constexpr int D = ETy::D, NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS;
     constexpr int TO = type_tab_off(ETy::TYPE);
     constexpr int PHI = TO, GR = TO + NQ * NP, WQ = TO + NQ * NP * (1 + D);
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_mma[2], bar_empty[2];
+    __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
-    __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    {   // self-check of the launch configuration (uniform over the CTA)
-        uint32_t dsmem;
-        asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsmem));
-        if (dsmem < (uint32_t)L::SMEM || blockDim.x != NTHREADS) {
-            if (tid == 0) atomicExch(err, 2);
-            return;
-        }
-    }
     unsigned char* sQ = smem;
     unsigned char* sX = smem + L::QEND;
-    float* sStage = reinterpret_cast<float*>(smem + L::QEND + L::XEND);
 
     {   // resident Q image
         const int4* src = reinterpret_cast<const int4*>(img);
         int4* dst = reinterpret_cast<int4*>(sQ);
-        for (int i = tid; i < L::QEND / 16; i += NTHREADS) dst[i] = src[i];
+        for (int i = tid; i < L::QEND / 16; i += TILE) dst[i] = src[i];
     }
-    const uint32_t mb_mma0 = tc::smem_u32(&bar_mma[0]), mb_mma1 = tc::smem_u32(&bar_mma[1]);
-    const uint32_t mb_emp0 = tc::smem_u32(&bar_empty[0]), mb_emp1 = tc::smem_u32(&bar_empty[1]);
+    const uint32_t mb = tc::smem_u32(&mbar);
     if (tid == 0) {
-        tc::mbar_init(mb_mma0, 1);
-        tc::mbar_init(mb_mma1, 1);
-        tc::mbar_init(mb_emp0, TILE);
-        tc::mbar_init(mb_emp1, TILE);
-        abort_flag = 0;
+        tc::mbar_init(mb, 1);
         tc::fence_mbar_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(tc::smem_u32(&tmem_slot), L::TALLOC);
+        tc::tmem_alloc(tc::smem_u32(&tmem_slot), L::ALLOC);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -214,152 +176,118 @@ __global__ void __launch_bounds__(NTHREADS, 1) element_tc_kernel(
     const uint32_t sQu = tc::smem_u32(sQ), sXu = tc::smem_u32(sX);
     const bool doM = VM != nullptr, doK = VK != nullptr, doT = VT != nullptr;
     const bool need_u = doK | doT;
-    volatile int* abortp = &abort_flag;
-    const int64_t ntiles = (E + TILE - 1) / TILE;
+    float* stage = reinterpret_cast<float*>(sX) + warp * 32 * 33;
+    uint32_t phase = 0;
+    bool timed_out = false;
 
-    if (warp < 4) {
-        // ------------------------------------------------ warpgroup 0: producers
-        int j = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
-            const int64_t e = tile * TILE + tid;
-            float xm[L::KMp], xk[L::KKp], xt[L::KTp];
+    const int64_t ntiles = (E + TILE - 1) / TILE;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t e = tile * TILE + tid;
+        float xm[L::KMp], xk[L::KKp], xt[L::KTp];
 #pragma unroll
-            for (int i = 0; i < L::KMp; ++i) xm[i] = 0.f;
+        for (int i = 0; i < L::KMp; ++i) xm[i] = 0.f;
 #pragma unroll
-            for (int i = 0; i < L::KKp; ++i) xk[i] = 0.f;
+        for (int i = 0; i < L::KKp; ++i) xk[i] = 0.f;
 #pragma unroll
-            for (int i = 0; i < L::KTp; ++i) xt[i] = 0.f;
-            if (e < E) {
-                const int* ce = conn + e * NP;
-                // du[i] = u_i - u_0 from the (hi, lo) split of u: exact differences of the hi parts
-                float du[NP];
-                float u0 = 0.f;
-                if (need_u) {
-                    int idx[NP];
+        for (int i = 0; i < L::KTp; ++i) xt[i] = 0.f;
+        if (e < E) {
+            const int* ce = conn + e * NP;
+            // du[i] = u_i - u_0 from the (hi, lo) split of u (exact differences of
+            // the hi parts); u is only needed for K and T (mass-only calls pass NULL)
+            float du[NP];
+            float u0 = 0.f;
+            if (need_u) {
+                int idx[NP];
 #pragma unroll
-                    for (int i = 0; i < NP; ++i) idx[i] = __ldg(ce + i);
-                    const float2 a = __ldg(u + idx[0]);
-                    u0 = a.x + a.y;
+                for (int i = 0; i < NP; ++i) idx[i] = __ldg(ce + i);
+                const float2 a = __ldg(u + idx[0]);
+                u0 = a.x + a.y;
 #pragma unroll
-                    for (int i = 0; i < NP; ++i) {
-                        const float2 bb = __ldg(u + idx[i]);
-                        du[i] = (bb.x - a.x) + (bb.y - a.y);
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < NP; ++i) du[i] = 0.f;
+                for (int i = 0; i < NP; ++i) {
+                    const float2 bb = __ldg(u + idx[i]);
+                    du[i] = (bb.x - a.x) + (bb.y - a.y);
                 }
-                const float b = __ldg(geo + e);
-                float A[NS];
+            } else {
 #pragma unroll
-                for (int t = 0; t < NS; ++t) A[t] = __ldg(geo + (1 + t) * E + e);
+                for (int i = 0; i < NP; ++i) du[i] = 0.f;
+            }
+            const float b = __ldg(geo + e);
+            float A[NS];
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    float uq = 0.f, g[D];
+            for (int t = 0; t < NS; ++t) A[t] = __ldg(geo + (1 + t) * E + e);
 #pragma unroll
-                    for (int a2 = 0; a2 < D; ++a2) g[a2] = 0.f;
+            for (int q = 0; q < NQ; ++q) {
+                float uq = 0.f, g[D];
 #pragma unroll
-                    for (int i = 0; i < NP; ++i) {
-                        uq = fmaf(c_tcref[PHI + q * NP + i], du[i], uq);
+                for (int a = 0; a < D; ++a) g[a] = 0.f;
 #pragma unroll
-                        for (int a2 = 0; a2 < D; ++a2) g[a2] = fmaf(c_tcref[GR + (q * NP + i) * D + a2], du[i], g[a2]);
+                for (int i = 0; i < NP; ++i) {
+                    uq = fmaf(c_tcref[PHI + q * NP + i], du[i], uq);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) g[a] = fmaf(c_tcref[GR + (q * NP + i) * D + a], du[i], g[a]);
+                }
+                uq += u0;
+                float dk;
+                const float kq = k_eval<float>(k, uq, dk);
+                const float lam = c_tcref[WQ + q] * b;
+                xm[q] = mass * lam;
+                const float lk = lam * kq;
+#pragma unroll
+                for (int t = 0; t < NS; ++t) xk[q * NS + t] = lk * A[t];
+                const float ld = lam * dk;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    float s = 0.f;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        const int lo = a < c ? a : c, hi = a < c ? c : a;
+                        s = fmaf(A[lo * D - (lo * (lo - 1)) / 2 + (hi - lo)], g[c], s);
                     }
-                    uq += u0;
-                    float dk;
-                    const float kq = k_eval<float>(k, uq, dk);
-                    const float lam = c_tcref[WQ + q] * b;
-                    xm[q] = mass * lam;
-                    const float lk = lam * kq;
-#pragma unroll
-                    for (int t = 0; t < NS; ++t) xk[q * NS + t] = lk * A[t];
-                    const float ld = lam * dk;
-#pragma unroll
-                    for (int a2 = 0; a2 < D; ++a2) {
-                        float sacc = 0.f;
-#pragma unroll
-                        for (int c = 0; c < D; ++c) {
-                            const int lo = a2 < c ? a2 : c, hi = a2 < c ? c : a2;
-                            sacc = fmaf(A[lo * D - (lo * (lo - 1)) / 2 + (hi - lo)], g[c], sacc);
-                        }
-                        xt[q * D + a2] = ld * sacc;
-                    }
+                    xt[q * D + a] = ld * s;
                 }
             }
-            // the X buffer is free once the previous tile's MMAs have completed
-            bool ok = true;
-            if (j >= 1) ok = wait_or_abort(((j - 1) & 1) ? mb_mma1 : mb_mma0, ((j - 1) >> 1) & 1, abortp);
-            ok = __all_sync(0xffffffffu, ok);
-            if (ok) {
-                if (doM) store_row<L::KMp>(sX + L::XMh, sX + L::XMl, xm, tid);
-                if (doK) store_row<L::KKp>(sX + L::XKh, sX + L::XKl, xk, tid);
-                if (doT) store_row<L::KTp>(sX + L::XTh, sX + L::XTl, xt, tid);
-                tc::fence_proxy_async_smem();
-            }
-            // all producers of this tile have stored X (named barrier 1, warpgroup 0
-            // only); the barrier also ORs the abort flag so that the exit is uniform
-            {
-                const int ab = *abortp ? 1 : 0;
-                int any;
-                asm volatile(
-                    "{\n\t.reg .pred p, q;\n\t"
-                    "setp.ne.s32 q, %1, 0;\n\t"
-                    "bar.red.or.pred p, 1, 128, q;\n\t"
-                    "selp.s32 %0, 1, 0, p;\n\t}\n"
-                    : "=r"(any)
-                    : "r"(ab)
-                    : "memory");
-                if (any) break;
-            }
-            if (tid == 0) {
-                const uint32_t buf = j & 1;
-                bool free_ok = true;
-                if (j >= 2) free_ok = wait_or_abort(buf ? mb_emp1 : mb_emp0, ((j >> 1) - 1) & 1, abortp);
-                if (free_ok) {
-                    tc::fence_after_sync();
-                    const uint32_t tb = tmem + buf * L::ALLOC;
-                    if (doM)
-                        issue_tf32x3<L::KMp>(tb + L::COLM, sXu + L::XMh, sXu + L::XMl, sQu + L::QMh, sQu + L::QMl,
-                                             tc::idesc_tf32(L::NMp));
-                    if (doK)
-                        issue_tf32x3<L::KKp>(tb + L::COLK, sXu + L::XKh, sXu + L::XKl, sQu + L::QKh, sQu + L::QKl,
-                                             tc::idesc_tf32(L::NMp));
-                    if (doT)
-                        issue_tf32x3<L::KTp>(tb + L::COLT, sXu + L::XTh, sXu + L::XTl, sQu + L::QTh, sQu + L::QTl,
-                                             tc::idesc_tf32(L::NTp));
-                    tc::mma_commit(buf ? mb_mma1 : mb_mma0);
-                }
-            }
-            __syncwarp();
         }
-        if (tid == 0 && j > 0 && *abortp) {
-            // let the last committed MMAs drain (bounded) before the memory is released
-            const int jl = j - 1;
-            tc::mbar_wait_bounded((jl & 1) ? mb_mma1 : mb_mma0, (jl >> 1) & 1, WAIT_LIMIT);
-        }
-        __syncwarp();
-    } else {
-        // ------------------------------------------------ warpgroup 1: epilogue
-        const int c4 = warp - 4;                       // warpgroup rank: TMEM lanes 32*c4 .. 32*c4+31
-        float* stage = sStage + c4 * 32 * 33;
-        int j = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
-            const uint32_t buf = j & 1;
-            const bool ok = wait_or_abort(buf ? mb_mma1 : mb_mma0, (j >> 1) & 1, abortp);
-            if (!__all_sync(0xffffffffu, ok)) break;   // warp-uniform: tcgen05.ld is .sync.aligned
+        if (doM) store_row<L::KMp>(sX + L::XMh, sX + L::XMl, xm, tid);
+        if (doK) store_row<L::KKp>(sX + L::XKh, sX + L::XKl, xk, tid);
+        if (doT) store_row<L::KTp>(sX + L::XTh, sX + L::XTl, xt, tid);
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
             tc::fence_after_sync();
-            const uint32_t tb = tmem + buf * L::ALLOC;
-            const int64_t row0 = tile * TILE + c4 * 32;
-            if (doM) epilogue<ETy::NSYM>(tb, L::COLM, stage, VM, row0, E, c4, lane);
-            if (doK) epilogue<ETy::NSYM>(tb, L::COLK, stage, VK, row0, E, c4, lane);
-            if (doT) epilogue<ETy::NT>(tb, L::COLT, stage, VT, row0, E, c4, lane);
-            tc::fence_before_sync();
-            mbar_arrive(buf ? mb_emp1 : mb_emp0);
+            if (doM)
+                issue_tf32x3<L::KMp>(tmem + L::COLM, sXu + L::XMh, sXu + L::XMl, sQu + L::QMh, sQu + L::QMl,
+                                     tc::idesc_tf32(L::NMp));
+            if (doK)
+                issue_tf32x3<L::KKp>(tmem + L::COLK, sXu + L::XKh, sXu + L::XKl, sQu + L::QKh, sQu + L::QKl,
+                                     tc::idesc_tf32(L::NMp));
+            if (doT)
+                issue_tf32x3<L::KTp>(tmem + L::COLT, sXu + L::XTh, sXu + L::XTl, sQu + L::QTh, sQu + L::QTl,
+                                     tc::idesc_tf32(L::NTp));
+            tc::mma_commit(mb);
         }
+        const uint32_t ok = tc::mbar_wait_bounded(mb, phase, WAIT_LIMIT);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        tc::fence_after_sync();
+        const int64_t row0 = tile * TILE + warp * 32;
+        if (doM) epilogue<ETy::NSYM>(tmem, L::COLM, stage, VM, row0, E, warp, lane);
+        if (doK) epilogue<ETy::NSYM>(tmem, L::COLK, stage, VK, row0, E, warp, lane);
+        if (doT) epilogue<ETy::NT>(tmem, L::COLT, stage, VT, row0, E, warp, lane);
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (timed_out) {
+        if (tid == 0) atomicExch(err, 1);
+        // give in-flight tensor-core work one more bounded chance to drain
+        tc::mbar_wait_bounded(mb, phase ^ 1u, WAIT_LIMIT);
     }
     __syncthreads();
-    if (tid == 0 && abort_flag) atomicExch(err, 1);
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, L::TALLOC);
+    if (warp == 0) tc::tmem_dealloc(tmem, L::ALLOC);
 }
 
 // host-side TF32 rounding, nearest with ties away from zero (matches cvt.rna)
@@ -423,10 +351,8 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, 
         int smem = L::SMEM;
         if (smem > dyn_max) return fail(FEM_EINVAL, "tensor-core tile does not fit in shared memory");
         FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                          (int)cudaSharedmemCarveoutMaxShared));
-        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NTHREADS, smem));
-        const int occ_max = 512 / L::TALLOC;   // co-resident CTAs must fit their TMEM columns
+        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+        const int occ_max = 512 / L::ALLOC;   // co-resident CTAs must fit their TMEM columns
         if (occ > occ_max) {
             // ask for enough shared memory that at most occ_max CTAs fit on an SM
             int per_sm = 0;
@@ -434,7 +360,7 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, 
             smem = per_sm / (occ_max + 1) + 1;
             if (smem > dyn_max) smem = dyn_max;
             FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-            FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NTHREADS, smem));
+            FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
             if (occ > occ_max) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
         }
         if (occ < 1) return fail(FEM_ECUDA, "tensor-core kernel does not fit on an SM");
@@ -446,7 +372,7 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, 
         int* err = nullptr;
         FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&err, g_tc_err));
         cudaGetLastError();   // clear any stale error before the launch check
-        kern<<<(unsigned)grid, NTHREADS, smem, s>>>(m.conn.as<int>(), m.geo32.as<float>(), m.E, u, k, (float)m.m, VM, VK,
+        kern<<<(unsigned)grid, TILE, smem, s>>>(m.conn.as<int>(), m.geo32.as<float>(), m.E, u, k, (float)m.m, VM, VK,
                                                 VT, img + (size_t)ETy::TYPE * IMG_SLOT_FLOATS, err);
         FEM_CUDA_TRY(cudaGetLastError());
         return FEM_OK;
