@@ -227,6 +227,34 @@ int fem_last_error(char* buf, size_t len);
 /* Library version string. */
 const char* fem_version(void);
 
+
+/* -------------------------------------- FP64 reassembly without allocation */
+/* The paper has no counterpart to this call.  It is fem_assemble_all for
+ * FEM_FP64 with device pointers only, for callers that must not allocate
+ * device memory while they run: for example a solver loop whose device memory
+ * is budgeted up front by a framework that owns the whole pool, or a
+ * latency-critical service loop in which a driver allocation (which can
+ * synchronise the device) is not acceptable.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine: the element matrices between the
+ * element product and the CSR sum live in one fixed device array of
+ * FEM_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
+ * the library holds until the process exits.
+ *  - Limit: the selected matrices must fit the array, i.e. n_elems times
+ *    8 bytes times n_p(n_p+1)/2 for each of M and K plus n_p^2 for T (each
+ *    part rounded up to 256 bytes) <= FEM_NOALLOC_SCRATCH_BYTES; larger meshes
+ *    get FEM_EINVAL with the sizes in the message.
+ *  - Set-up: the first call on a device looks up the array's device address
+ *    and uploads the reference tables; make that first call before any
+ *    stream capture.
+ *  - Sharing: all calls use the same array and it keeps the last call's
+ *    contents (every entry is rewritten before it is read, nothing needs
+ *    clearing); calls whose GPU work overlaps race on it.
+ * Requires fem_symbolic.  d_u: FP64 nodal values (unused for M only);
+ * d_vM, d_vK, d_vT: caller-owned FP64 CSR values, NULL to skip. */
+#define FEM_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int fem_assemble_all_noalloc(fem_mesh* mesh, const fem_coeff* k, const double* d_u, double* d_vM,
+                             double* d_vK, double* d_vT, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,8 @@ _SIGS = {
     "fem_assemble_all": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                           C.c_void_p, C.c_void_p], C.c_int),
     "fem_device_status": ([C.c_void_p], C.c_int),
+    "fem_assemble_all_noalloc": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p], C.c_int),
     "fem_form_elements": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_int, C.c_void_p], C.c_int),
     "fem_sum_elements": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fem_reference_tables": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -218,6 +220,16 @@ def fem_form_elements(mesh: int, k, d_u, prec: int, which: int, stream=None) -> 
 
 def fem_sum_elements(mesh: int, prec: int, d_vM, d_vK, d_vT, stream=None) -> None:
     _check(lib().fem_sum_elements(mesh, prec, _vp(d_vM), _vp(d_vK), _vp(d_vT), _stream(stream)))
+
+
+FEM_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
+
+
+def fem_assemble_all_noalloc(mesh: int, k, d_u, d_vM, d_vK, d_vT, stream=None) -> None:
+    """FP64 reassembly that allocates no device memory (scratch in a fixed
+    library array of FEM_NOALLOC_SCRATCH_BYTES); device pointers only."""
+    _check(lib().fem_assemble_all_noalloc(mesh, C.byref(k) if k is not None else None, _vp(d_u), _vp(d_vM),
+                                          _vp(d_vK), _vp(d_vT), _stream(stream)))
 
 
 def fem_device_status(stream=None) -> None:

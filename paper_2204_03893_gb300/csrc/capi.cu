@@ -215,6 +215,10 @@ int assemble_t(fem_mesh* m, const fem_coeff* k, const void* u, int prec, void* v
 }
 
 }  // namespace
+
+int validate_coeff(const fem_coeff* k) { return check_coeff(k); }
+CoeffDev coeff_to_device(const fem_coeff* k) { return to_dev(k); }
+
 }  // namespace fem
 
 size_t fem_mesh::device_bytes() const {

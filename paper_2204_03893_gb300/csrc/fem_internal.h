@@ -80,6 +80,10 @@ int scatter_fp64(const fem_mesh& m, const double* VM, const double* VK, const do
 int scatter_fp32(const fem_mesh& m, const float* VM, const float* VK, const float* VT, float* vM, float* vK,
                  float* vT, cudaStream_t s);
 
+// Coefficient validation and device form, shared by the C entry points.
+int validate_coeff(const fem_coeff* k);
+CoeffDev coeff_to_device(const fem_coeff* k);
+
 // One-time per-device upload of the reference tables of each kernel module.
 int tables_init_simt();
 int tables_init_tc();
