@@ -35,7 +35,7 @@ import numpy as np
 __all__ = [
     "local_nodes", "Mesh", "structured_tri", "structured_tet", "fourier_field",
     "uniform_field", "Coeff", "Workload", "workload", "n_local",
-    "batched_meshes", "sliver_tri",
+    "batched_meshes", "sliver_tri", "fan_tri",
 ]
 
 
@@ -238,6 +238,20 @@ def sliver_tri(N: int = 8, frac: float = 0.05, seed: int = 0, pull: float = 1e-5
         v = j * (N + 1) + (i + 1)
         coords[v] = np.array([(i + 0.5) * h, (j + 0.5) * h]) + pull * h * np.array([1.0, -1.0]) / math.sqrt(2.0)
     return Mesh(d=2, p=1, coords=coords, conn=m.conn, name=f"sliver_N{N}")
+
+
+def fan_tri(K: int = 300, seed: int = 0) -> Mesh:
+    """P1 triangles (0, i, i+1) around a centre node 0, ring nodes 1..K on
+    a circle of radius 1 with a small radial jitter: the centre's row has
+    K+1 entries (long rows exercise the code paths for rows of more than 256
+    entries)."""
+    rng = np.random.default_rng(seed)
+    th = 2.0 * math.pi * np.arange(K) / K
+    r = 1.0 + rng.uniform(-0.05, 0.05, K)
+    coords = np.vstack([[0.0, 0.0], np.stack([r * np.cos(th), r * np.sin(th)], 1)])
+    i = np.arange(K)
+    conn = np.stack([np.zeros(K, dtype=np.int64), 1 + i, 1 + (i + 1) % K], 1).astype(np.int32)
+    return Mesh(d=2, p=1, coords=coords, conn=conn, name=f"fan_{K}")
 
 
 def uniform_field(n: int, seed: int) -> np.ndarray:

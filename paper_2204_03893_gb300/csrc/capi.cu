@@ -26,46 +26,33 @@ int cuda_fail(cudaError_t e, const char* what) {
     return FEM_ECUDA;
 }
 
-void* dev_alloc(size_t bytes, cudaStream_t s) {
-    if (bytes == 0) bytes = 16;
-    fem_allocator a;
-    {
-        std::lock_guard<std::mutex> lk(g_alloc_mu);
-        a = g_alloc;
-    }
-    if (a.alloc) return a.alloc(bytes, s, a.ctx);
-    void* p = nullptr;
-    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    return p;
-}
-
-void dev_free(void* p, size_t bytes, cudaStream_t s) {
-    if (!p) return;
-    fem_allocator a;
-    {
-        std::lock_guard<std::mutex> lk(g_alloc_mu);
-        a = g_alloc;
-    }
-    if (a.free) a.free(p, bytes, s, a.ctx);
-    else cudaFreeAsync(p, s);
-}
-
 int buf_alloc(DevBuf& b, size_t bytes, cudaStream_t s) {
     if (b.ptr && b.bytes >= bytes) return FEM_OK;
     buf_free(b, s);
-    b.ptr = dev_alloc(bytes, s);
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        b.owner = g_alloc;
+    }
+    if (bytes == 0) bytes = 16;
+    if (b.owner.alloc) {
+        b.ptr = b.owner.alloc(bytes, s, b.owner.ctx);
+    } else if (cudaMallocAsync(&b.ptr, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        b.ptr = nullptr;
+    }
     if (!b.ptr) return fail(FEM_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
     b.bytes = bytes;
     return FEM_OK;
 }
 
 void buf_free(DevBuf& b, cudaStream_t s) {
-    if (b.ptr) dev_free(b.ptr, b.bytes, s);
+    if (b.ptr) {
+        if (b.owner.free) b.owner.free(b.ptr, b.bytes, s, b.owner.ctx);
+        else cudaFreeAsync(b.ptr, s);
+    }
     b.ptr = nullptr;
     b.bytes = 0;
+    b.owner = fem_allocator{nullptr, nullptr, nullptr};
 }
 
 int tc_error_flag(int clear);
@@ -223,7 +210,7 @@ CoeffDev coeff_to_device(const fem_coeff* k) { return to_dev(k); }
 
 size_t fem_mesh::device_bytes() const {
     const fem::DevBuf* bufs[] = {&coords, &conn, &geo64, &geo32, &row_ptr, &col_idx, &seg_ptr, &contrib, &slot,
-                                 &inc_ptr, &inc, &VM, &VK, &VT, &u_stage, &out_stage, &u_split};
+                                 &inc_ptr, &inc, &VM, &VK, &VT, &u_stage, &out_stage, &u_split, &loff};
     size_t t = 0;
     for (auto* b : bufs) t += b->bytes;
     return t;
@@ -317,7 +304,7 @@ int fem_mesh_destroy(fem_mesh* m) {
     cudaDeviceSynchronize();
     fem::DevBuf* bufs[] = {&m->coords, &m->conn, &m->geo64, &m->geo32, &m->row_ptr, &m->col_idx, &m->seg_ptr,
                            &m->contrib, &m->slot, &m->inc_ptr, &m->inc, &m->VM, &m->VK, &m->VT, &m->u_stage,
-                           &m->out_stage, &m->u_split};
+                           &m->out_stage, &m->u_split, &m->loff};
     for (auto* b : bufs) buf_free(*b, nullptr);
     cudaDeviceSynchronize();
     delete m;

@@ -181,8 +181,35 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
     bool timed_out = false;
 
     const int64_t ntiles = (E + TILE - 1) / TILE;
+    // Inputs of the next tile are prefetched into registers while the current
+    // tile's MMAs and epilogue run: connectivity and geometry before the MMA
+    // issue, the gathered u values right after it.
+    int pidx[NP];
+    float2 pu[NP];
+    float pgeo[1 + NS];
+    bool pvalid = false;
+    auto fetch_meta = [&](int64_t t) {
+        const int64_t e = t * TILE + tid;
+        pvalid = e < E;
+        if (pvalid) {
+            const int* ce = conn + e * NP;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) pidx[i] = need_u ? __ldg(ce + i) : 0;
+#pragma unroll
+            for (int t2 = 0; t2 <= NS; ++t2) pgeo[t2] = __ldg(geo + t2 * E + e);
+        }
+    };
+    auto fetch_u = [&]() {
+        if (pvalid && need_u) {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) pu[i] = __ldg(u + pidx[i]);
+        }
+    };
+    if ((int64_t)blockIdx.x < ntiles) {
+        fetch_meta(blockIdx.x);
+        fetch_u();
+    }
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t e = tile * TILE + tid;
         float xm[L::KMp], xk[L::KKp], xt[L::KTp];
 #pragma unroll
         for (int i = 0; i < L::KMp; ++i) xm[i] = 0.f;
@@ -190,31 +217,23 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
         for (int i = 0; i < L::KKp; ++i) xk[i] = 0.f;
 #pragma unroll
         for (int i = 0; i < L::KTp; ++i) xt[i] = 0.f;
-        if (e < E) {
-            const int* ce = conn + e * NP;
+        if (pvalid) {
             // du[i] = u_i - u_0 from the (hi, lo) split of u (exact differences of
             // the hi parts); u is only needed for K and T (mass-only calls pass NULL)
             float du[NP];
             float u0 = 0.f;
             if (need_u) {
-                int idx[NP];
+                u0 = pu[0].x + pu[0].y;
 #pragma unroll
-                for (int i = 0; i < NP; ++i) idx[i] = __ldg(ce + i);
-                const float2 a = __ldg(u + idx[0]);
-                u0 = a.x + a.y;
-#pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    const float2 bb = __ldg(u + idx[i]);
-                    du[i] = (bb.x - a.x) + (bb.y - a.y);
-                }
+                for (int i = 0; i < NP; ++i) du[i] = (pu[i].x - pu[0].x) + (pu[i].y - pu[0].y);
             } else {
 #pragma unroll
                 for (int i = 0; i < NP; ++i) du[i] = 0.f;
             }
-            const float b = __ldg(geo + e);
+            const float b = pgeo[0];
             float A[NS];
 #pragma unroll
-            for (int t = 0; t < NS; ++t) A[t] = __ldg(geo + (1 + t) * E + e);
+            for (int t = 0; t < NS; ++t) A[t] = pgeo[1 + t];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 float uq = 0.f, g[D];
@@ -247,6 +266,8 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
                 }
             }
         }
+        const int64_t next = tile + gridDim.x;
+        if (next < ntiles) fetch_meta(next);
         if (doM) store_row<L::KMp>(sX + L::XMh, sX + L::XMl, xm, tid);
         if (doK) store_row<L::KKp>(sX + L::XKh, sX + L::XKl, xk, tid);
         if (doT) store_row<L::KTp>(sX + L::XTh, sX + L::XTl, xt, tid);
@@ -266,6 +287,7 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
                                      tc::idesc_tf32(L::NTp));
             tc::mma_commit(mb);
         }
+        if (next < ntiles) fetch_u();
         const uint32_t ok = tc::mbar_wait_bounded(mb, phase, WAIT_LIMIT);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {

@@ -22,13 +22,12 @@ int cuda_fail(cudaError_t e, const char* what);
     } while (0)
 
 // ------------------------------------------------------------- allocation
-void* dev_alloc(size_t bytes, cudaStream_t s);
-void dev_free(void* p, size_t bytes, cudaStream_t s);
-
-// Tracks one library-owned device buffer.
+// Tracks one library-owned device buffer and the allocator that made it
+// (a buffer is always returned to that allocator, even if the hook changed).
 struct DevBuf {
     void* ptr = nullptr;
     size_t bytes = 0;
+    fem_allocator owner = {nullptr, nullptr, nullptr};
     template <typename T>
     T* as() const { return static_cast<T*>(ptr); }
 };
@@ -49,6 +48,8 @@ struct fem_mesh {
     bool have_pattern = false;
     int64_t nnz = -1;
     fem::DevBuf row_ptr, col_idx, seg_ptr, contrib, slot, inc_ptr, inc;
+    fem::DevBuf loff;                   // 8-bit in-row offset of every element entry (if max_row <= 256)
+    int max_row = 0;                    // longest CSR row
     // numeric scratch: element matrices V (per matrix) in the precision of the last call
     fem::DevBuf VM, VK, VT;
     int v_prec = -1, v_mask = 0;        // what VM/VK/VT currently hold

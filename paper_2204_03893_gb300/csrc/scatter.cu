@@ -2,79 +2,163 @@
 //
 // Algorithm 2 line 12 ("form the matrices M and C from V_m and V_c and the
 // set of indices of nonzero entries"); Section 3 step 2, eq. assemblage_1:
-// M_ij = sum over elements of the element integrals.  Each CSR slot s sums
-// its contributions contrib[seg_ptr[s] .. seg_ptr[s+1]) in ascending element
-// entry order c = (e n_p + i) n_p + j, one thread per slot, with no atomics:
-// the result is bit-reproducible run to run and the summation order is the
-// element order of Algorithm 1.  M and K come from the symmetric element
-// storage (entry (i,j) and (j,i) share V[e][sym(min,max)]), T from the full
-// n_p x n_p storage.
+// M_ij = sum over elements of the element integrals.  Deterministic, no
+// atomics: every CSR slot adds its contributions in ascending element order,
+// the order of Algorithm 1, so the result is bit-reproducible run to run.
+// M and K come from the symmetric element storage (entry (i,j) and (j,i)
+// share V[e][sym(min,max)]), T from the full n_p x n_p storage.
+//
+// Row-wise kernel (used when every CSR row has at most 256 entries): one
+// thread owns one row r and walks the row's incident element rows (e, i),
+// conn[e][i] = r, in ascending e; for each it reads the element's local row
+// (n_p contiguous T entries and the matching symmetric M, K entries) and the
+// n_p 8-bit in-row offsets of the target slots, and adds into the row's
+// accumulators in shared memory.  A block owns a run of consecutive rows,
+// i.e. one contiguous range of CSR values, which it zeroes, fills and writes
+// out with coalesced stores.
+// Segment kernel (fallback): one thread per slot sums the slot's contributor
+// list contrib[seg_ptr[s] .. seg_ptr[s+1]) (element entries, ascending).
 #include "fem_internal.h"
 
 namespace fem {
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ void store_stream(T* p, T v) {
-    __stcs(p, v);   // outputs are not re-read by this kernel: evict-first
+__host__ __device__ constexpr int sym_idx(int np, int i, int j) {
+    return i <= j ? i * np - (i * (i - 1)) / 2 + (j - i) : j * np - (j * (j - 1)) / 2 + (i - j);
 }
 
-// Each thread sums SPT slots spaced blockDim.x apart (coalesced across the
-// warp) with independent load chains, so that several gathers are in flight.
-constexpr int SPT = 4;
-
 template <int NP, typename T>
-__global__ void __launch_bounds__(256) scatter_kernel(const int* __restrict__ seg_ptr, const int* __restrict__ contrib,
-                                                      int64_t nnz, const T* __restrict__ VM, const T* __restrict__ VK,
-                                                      const T* __restrict__ VT, T* __restrict__ vM,
-                                                      T* __restrict__ vK, T* __restrict__ vT) {
+__global__ void __launch_bounds__(256) scatter_rows_kernel(const int* __restrict__ inc_ptr, const int* __restrict__ inc,
+                                                           const int* __restrict__ row_ptr,
+                                                           const unsigned char* __restrict__ loff, int64_t n,
+                                                           int maxrow, const T* __restrict__ VM,
+                                                           const T* __restrict__ VK, const T* __restrict__ VT,
+                                                           T* __restrict__ vM, T* __restrict__ vK,
+                                                           T* __restrict__ vT) {
     constexpr int NT = NP * NP, NSYM = NP * (NP + 1) / 2;
+    extern __shared__ __align__(16) unsigned char sraw[];
+    const int cap = blockDim.x * maxrow;                // accumulators per matrix
+    T* aM = reinterpret_cast<T*>(sraw);
+    T* aK = aM + cap;
+    T* aT = aK + cap;
     const bool dM = vM != nullptr, dK = vK != nullptr, dT = vT != nullptr;
-    const int64_t chunk = (int64_t)blockDim.x * SPT;
-    for (int64_t base = blockIdx.x * chunk; base < nnz; base += (int64_t)gridDim.x * chunk) {
-        int a[SPT], b[SPT];
-#pragma unroll
-        for (int k = 0; k < SPT; ++k) {
-            const int64_t s = base + k * blockDim.x + threadIdx.x;
-            a[k] = s < nnz ? __ldg(seg_ptr + s) : 0;
-            b[k] = s < nnz ? __ldg(seg_ptr + s + 1) : 0;
+    for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < n; r0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t rend = r0 + blockDim.x < n ? r0 + blockDim.x : n;
+        const int base0 = row_ptr[r0];
+        const int total = row_ptr[rend] - base0;       // <= blockDim.x * maxrow
+        for (int k = threadIdx.x; k < total; k += blockDim.x) {
+            if (dM) aM[k] = T(0);
+            if (dK) aK[k] = T(0);
+            if (dT) aT[k] = T(0);
         }
-        T am[SPT], ak[SPT], at[SPT];
+        __syncthreads();
+        const int64_t r = r0 + threadIdx.x;
+        if (r < n) {
+            const int base = row_ptr[r] - base0;
+            const int p1 = inc_ptr[r + 1];
+            for (int p = inc_ptr[r]; p < p1; ++p) {
+                const int ei = __ldg(inc + p);         // e * n_p + i, ascending e
+                const int e = ei / NP;
+                const int i = ei - e * NP;
+                const unsigned char* lo = loff + (int64_t)ei * NP;
+                int off[NP];
 #pragma unroll
-        for (int k = 0; k < SPT; ++k) am[k] = ak[k] = at[k] = T(0);
-        int len = 0;
+                for (int j = 0; j < NP; ++j) off[j] = base + __ldg(lo + j);
+                if (dT) {
+                    const T* vt = VT + (int64_t)e * NT + i * NP;
+                    T val[NP];
 #pragma unroll
-        for (int k = 0; k < SPT; ++k) len = max(len, b[k] - a[k]);
-        for (int p = 0; p < len; ++p) {
-            int c[SPT];
+                    for (int j = 0; j < NP; ++j) val[j] = __ldg(vt + j);
 #pragma unroll
-            for (int k = 0; k < SPT; ++k) c[k] = (a[k] + p < b[k]) ? __ldg(contrib + a[k] + p) : -1;
+                    for (int j = 0; j < NP; ++j) aT[off[j]] += val[j];
+                }
+                if (dM) {
+                    const T* vm = VM + (int64_t)e * NSYM;
+                    T val[NP];
 #pragma unroll
-            for (int k = 0; k < SPT; ++k) {
-                if (c[k] < 0) continue;
-                const int e = c[k] / NT;
-                const int l = c[k] - e * NT;
-                if (dT) at[k] += __ldg(VT + (int64_t)e * NT + l);
-                if (dM | dK) {
-                    const int i = l / NP, j = l - (l / NP) * NP;
-                    const int lo = i < j ? i : j, hi = i < j ? j : i;
-                    const int si = lo * NP - (lo * (lo - 1)) / 2 + (hi - lo);
-                    if (dM) am[k] += __ldg(VM + (int64_t)e * NSYM + si);
-                    if (dK) ak[k] += __ldg(VK + (int64_t)e * NSYM + si);
+                    for (int j = 0; j < NP; ++j) val[j] = __ldg(vm + sym_idx(NP, i, j));
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) aM[off[j]] += val[j];
+                }
+                if (dK) {
+                    const T* vk = VK + (int64_t)e * NSYM;
+                    T val[NP];
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) val[j] = __ldg(vk + sym_idx(NP, i, j));
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) aK[off[j]] += val[j];
                 }
             }
         }
-#pragma unroll
-        for (int k = 0; k < SPT; ++k) {
-            const int64_t s = base + k * blockDim.x + threadIdx.x;
-            if (s < nnz) {
-                if (dM) store_stream(vM + s, am[k]);
-                if (dK) store_stream(vK + s, ak[k]);
-                if (dT) store_stream(vT + s, at[k]);
+        __syncthreads();
+        for (int k = threadIdx.x; k < total; k += blockDim.x) {
+            if (dM) __stcs(vM + base0 + k, aM[k]);
+            if (dK) __stcs(vK + base0 + k, aK[k]);
+            if (dT) __stcs(vT + base0 + k, aT[k]);
+        }
+        __syncthreads();
+    }
+}
+
+template <int NP, typename T>
+__global__ void __launch_bounds__(256) scatter_segments_kernel(const int* __restrict__ seg_ptr,
+                                                               const int* __restrict__ contrib, int64_t nnz,
+                                                               const T* __restrict__ VM, const T* __restrict__ VK,
+                                                               const T* __restrict__ VT, T* __restrict__ vM,
+                                                               T* __restrict__ vK, T* __restrict__ vT) {
+    constexpr int NT = NP * NP, NSYM = NP * (NP + 1) / 2;
+    const bool dM = vM != nullptr, dK = vK != nullptr, dT = vT != nullptr;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x) {
+        const int a = seg_ptr[s], b = seg_ptr[s + 1];
+        T am = T(0), ak = T(0), at = T(0);
+        for (int p = a; p < b; ++p) {
+            const int c = contrib[p];
+            const int e = c / NT;
+            const int l = c - e * NT;
+            if (dT) at += VT[(int64_t)e * NT + l];
+            if (dM | dK) {
+                const int i = l / NP, j = l - (l / NP) * NP;
+                const int si = sym_idx(NP, i, j);
+                if (dM) am += VM[(int64_t)e * NSYM + si];
+                if (dK) ak += VK[(int64_t)e * NSYM + si];
             }
         }
+        if (dM) vM[s] = am;
+        if (dK) vK[s] = ak;
+        if (dT) vT[s] = at;
     }
+}
+
+template <int NP, typename T>
+int launch_np(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s,
+              int nsm) {
+    if (m.loff.ptr && m.max_row > 0) {
+        // threads per block: as many rows as fit ~64 KiB of accumulators (3 matrices)
+        int B = 256;
+        while (B > 32 && (size_t)3 * B * m.max_row * sizeof(T) > 64 * 1024) B /= 2;
+        const size_t smem = (size_t)3 * B * m.max_row * sizeof(T);
+        auto kern = scatter_rows_kernel<NP, T>;
+        FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared));
+        int occ = 0;
+        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, B, smem));
+        if (occ < 1) occ = 1;
+        int64_t blocks = (m.n + B - 1) / B;
+        if (blocks > (int64_t)nsm * occ) blocks = (int64_t)nsm * occ;
+        cudaGetLastError();   // clear any stale error before the launch check
+        kern<<<(unsigned)blocks, B, smem, s>>>(m.inc_ptr.as<int>(), m.inc.as<int>(), m.row_ptr.as<int>(),
+                                              m.loff.as<unsigned char>(), m.n, m.max_row, VM, VK, VT, vM, vK, vT);
+    } else {
+        int64_t blocks = (m.nnz + 255) / 256;
+        if (blocks > (int64_t)nsm * 16) blocks = (int64_t)nsm * 16;
+        cudaGetLastError();   // clear any stale error before the launch check
+        scatter_segments_kernel<NP, T><<<(unsigned)blocks, 256, 0, s>>>(
+            m.seg_ptr.as<int>(), m.contrib.as<int>(), m.nnz, VM, VK, VT, vM, vK, vT);
+    }
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
 }
 
 template <typename T>
@@ -83,21 +167,14 @@ int run(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, 
     int dev = 0, nsm = 0;
     FEM_CUDA_TRY(cudaGetDevice(&dev));
     FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    int64_t blocks = (m.nnz + 256 * SPT - 1) / (256 * SPT);
-    if (blocks > (int64_t)nsm * 8) blocks = (int64_t)nsm * 8;
-    const int* sp = m.seg_ptr.as<int>();
-    const int* ct = m.contrib.as<int>();
-    cudaGetLastError();   // clear any stale error before the launch check
     switch (m.np) {
-        case 3: scatter_kernel<3, T><<<(unsigned)blocks, 256, 0, s>>>(sp, ct, m.nnz, VM, VK, VT, vM, vK, vT); break;
-        case 4: scatter_kernel<4, T><<<(unsigned)blocks, 256, 0, s>>>(sp, ct, m.nnz, VM, VK, VT, vM, vK, vT); break;
-        case 6: scatter_kernel<6, T><<<(unsigned)blocks, 256, 0, s>>>(sp, ct, m.nnz, VM, VK, VT, vM, vK, vT); break;
-        case 10: scatter_kernel<10, T><<<(unsigned)blocks, 256, 0, s>>>(sp, ct, m.nnz, VM, VK, VT, vM, vK, vT); break;
-        case 20: scatter_kernel<20, T><<<(unsigned)blocks, 256, 0, s>>>(sp, ct, m.nnz, VM, VK, VT, vM, vK, vT); break;
-        default: return fail(FEM_EINVAL, "unsupported n_p");
+        case 3: return launch_np<3, T>(m, VM, VK, VT, vM, vK, vT, s, nsm);
+        case 4: return launch_np<4, T>(m, VM, VK, VT, vM, vK, vT, s, nsm);
+        case 6: return launch_np<6, T>(m, VM, VK, VT, vM, vK, vT, s, nsm);
+        case 10: return launch_np<10, T>(m, VM, VK, VT, vM, vK, vT, s, nsm);
+        case 20: return launch_np<20, T>(m, VM, VK, VT, vM, vK, vT, s, nsm);
     }
-    FEM_CUDA_TRY(cudaGetLastError());
-    return FEM_OK;
+    return fail(FEM_EINVAL, "unsupported n_p");
 }
 
 }  // namespace

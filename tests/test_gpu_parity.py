@@ -228,6 +228,29 @@ def test_form_and_sum_phases(prec):
     assert ei.value.code == F.FEM_ESTATE
 
 
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_long_rows_fallback_paths(prec):
+    """A 300-triangle fan: the centre row has 301 entries (> 256), so the CSR
+    sum takes the per-slot segment kernel and the symbolic phase sorts the
+    row's 900 keys without staging them in shared memory."""
+    m = mg.fan_tri(300, seed=2)
+    u = mg.uniform_field(m.n_nodes, 3)
+    c = mg.Coeff("poly", (1.0, 0.5, 0.25, 0.0, 0.0))
+    o = orc.Oracle.of(m)
+    rp_o, ci_o = o.pattern()
+    r = o.assemble(u, c)
+    fm = FemMesh.of(m)
+    rp, ci = fm.pattern()
+    assert np.array_equal(rp.cpu().numpy(), rp_o) and np.array_equal(ci.cpu().numpy(), ci_o)
+    g = fm.assemble(torch.tensor(u, device="cuda"), c.kind, c.params, prec)
+    for k in ("M", "K", "T"):
+        gk = g[k].double().cpu().numpy()
+        if prec == "fp64":
+            assert (np.abs(gk - r[k]) <= FP64_TOL * r["abs" + k] + 1e-300).all(), k
+        else:
+            assert frob(gk, r[k]) <= TF32_TOL, k
+
+
 def test_mass_coefficient_scales():
     m = mg.structured_tet(3, 2, 0.15, seed=1)
     f1, f2 = FemMesh.of(m, mass=1.0), FemMesh.of(m, mass=2.5)
