@@ -202,6 +202,134 @@ int fem_sum_elements(fem_mesh* mesh, int prec, void* d_vM, void* d_vK, void* d_v
  * record. */
 int fem_device_status(void* stream);
 
+/* ---------------------------------------------------------------- batches */
+/* Many meshes of uneven size and element type reassembled by one captured
+ * CUDA graph of a few persistent kernels (Section 7: a mesh with several
+ * element types is split into one mesh per type whose contributions are
+ * merged, and the formation of all element matrices can run in parallel).
+ * The element tiles of all meshes form one work list, grouped by element
+ * type, walked by one persistent tensor-core kernel (FEM_TF32X3; P3
+ * tetrahedra, whose tile does not fit the tensor-core layout, and FEM_FP64 /
+ * FEM_FP32 batches go through one batched SIMT kernel); one batched kernel
+ * forms the CSR sums of all meshes.  Results are bit-identical to the same
+ * meshes reassembled one by one with the same precision (FEM_FP32 for P3
+ * tetrahedra in a FEM_TF32X3 batch). */
+typedef struct {
+    int prec;       /* FEM_TF32X3 (default if opts is NULL), FEM_FP32 or FEM_FP64 */
+    int tune;       /* 1: on the first launch, time the CSR-sum block size and the SIMT grid
+                       on the real inputs and keep the fastest (the graph is captured after) */
+    int use_graph;  /* 1: replay one CUDA graph per launch (default when opts is NULL) */
+    int reserved;
+} fem_batch_opts;
+typedef struct {
+    int n_meshes;
+    int kernels_per_launch;  /* launches in one reassembly of the whole batch */
+    int tc_tiles;            /* 128-element tensor-core tiles in the work list */
+    int simt_blocks;         /* 64-element SIMT blocks */
+    int sum_chunks;          /* CSR-sum work items */
+    int sum_block;           /* threads per block of the CSR sum (tuned) */
+    int simt_grid;           /* blocks of the SIMT kernel (tuned) */
+    int tuned;               /* 1 once the tuner has run */
+    int graph;               /* 1 if launches replay a CUDA graph */
+    double tuned_ms;         /* fastest measured reassembly during tuning */
+} fem_batch_info;
+typedef struct fem_batch fem_batch;
+
+/* Every mesh must have run fem_symbolic.  Allocates the meshes' element
+ * scratch for the batch precision, builds the work lists and (unless tuning
+ * is requested) captures the graph.  Synchronises `stream`.  While a batch
+ * launch is in flight, its meshes must not be used by other calls. */
+int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts, void* stream, fem_batch** out);
+/* One reassembly of every mesh i: k[i] (law), d_u[i] (FP64 device nodal
+ * values, may be NULL if mesh i needs M only), outputs d_vM[i], d_vK[i],
+ * d_vT[i] (device CSR values, FP64 for FEM_FP64 and FP32 otherwise, NULL to
+ * skip; any of the three arrays may be NULL).  Enqueued on `stream`. */
+int fem_batch_launch(fem_batch* b, const fem_coeff* k, const double* const* d_u, void* const* d_vM,
+                     void* const* d_vK, void* const* d_vT, void* stream);
+int fem_batch_get_info(const fem_batch* b, fem_batch_info* out);
+int fem_batch_destroy(fem_batch* b);
+
+/* ----------------------------------------------------------- serving */
+/* A request server for assembly and reassembly (Introduction: repeated
+ * reassembly inside nonlinear solvers is a bottleneck; Section 5: between
+ * Newton steps only S changes, the pattern, W and b stay).  A mesh sent with
+ * an ASSEMBLE request stays resident on the device (geometry caches, CSR
+ * pattern, slot segments, element scratch) under a mesh id; REASSEMBLE
+ * requests then carry only a coefficient law and new nodal values.
+ *
+ * One scheduler thread per server owns the device work.  Continuous
+ * batching: a queued request starts as soon as an in-flight slot is free
+ * (max_inflight) and the device-memory budget allows, without waiting for
+ * other requests to finish; started requests are spread over n_streams CUDA
+ * streams so that the work of different meshes overlaps on the device.
+ * Requests start in arrival order, except that a request waits (and later
+ * ones may pass it) while another request of its mesh is in flight, so the
+ * requests of one mesh run one at a time in submission order.  If the oldest
+ * startable request does not fit the budget, nothing behind it starts.
+ *
+ * Budget accounting (bytes): every resident mesh (estimated from its size at
+ * submit, its real size once built) plus the outputs of every request not yet
+ * released.  A request that alone exceeds the budget, or that finds the
+ * queue full, is refused at submit with FEM_EBUSY.  An ASSEMBLE request builds
+ * the mesh and its pattern on the scheduler thread (it synchronises its
+ * stream there), then reassembles it.  Results are the same values as
+ * fem_assemble_all with the same precision (FEM_FP32 for P3 tetrahedra in a
+ * FEM_TF32X3 server). */
+enum { FEM_REQ_ASSEMBLE = 1, FEM_REQ_REASSEMBLE = 2 };
+typedef struct {
+    int prec;             /* FEM_FP64, FEM_TF32X3 or FEM_FP32 for every request */
+    int max_inflight;     /* requests started and not finished, >= 1 */
+    int n_streams;        /* CUDA streams the requests are spread over, 1..64 */
+    int max_queue;        /* pending requests before submit refuses (FEM_EBUSY) */
+    size_t budget_bytes;  /* device bytes for resident meshes + unreleased outputs */
+} fem_serve_opts;
+typedef struct {
+    int kind;                    /* FEM_REQ_ASSEMBLE or FEM_REQ_REASSEMBLE */
+    int which;                   /* FEM_MAT_M | FEM_MAT_K | FEM_MAT_T, nonzero */
+    uint64_t mesh_id;            /* REASSEMBLE: id from an earlier ASSEMBLE result */
+    const fem_mesh_desc* desc;   /* ASSEMBLE: the mesh (host or device buffers, copied at submit) */
+    const fem_coeff* k;          /* law of k(u) (needed for K or T) */
+    const double* u;             /* host FP64 nodal values (needed for K or T; copied at submit) */
+} fem_request;
+typedef struct {
+    int status;                  /* FEM_OK, or the request's error (message in fem_last_error) */
+    int prec;                    /* precision the values were computed in */
+    uint64_t mesh_id;            /* the mesh's id (new for ASSEMBLE) */
+    int64_t n, nnz;
+    const int32_t* d_row_ptr;    /* device CSR pattern, owned by the resident mesh */
+    const int32_t* d_col_idx;
+    void* d_vM;                  /* device CSR values (NULL if not requested); library-owned */
+    void* d_vK;                  /* until fem_serve_release(ticket) */
+    void* d_vT;
+    double t_submit_us, t_start_us, t_done_us;  /* host clock, microseconds since server creation;
+                                                   t_done is when the scheduler saw completion */
+} fem_result;
+typedef struct {
+    int pending, inflight, resident_meshes;
+    size_t bytes_in_use, peak_bytes;
+} fem_serve_counters;
+typedef struct fem_server fem_server;
+
+/* Creates a server on the current device (starts its scheduler thread). */
+int fem_serve_create(const fem_serve_opts* opts, fem_server** out);
+/* Copies the request's inputs and queues it; *ticket identifies it. */
+int fem_serve_submit(fem_server* s, const fem_request* req, uint64_t* ticket);
+/* Waits up to timeout_us for the request: FEM_OK with *out filled once it
+ * finished (out->status is the request's own status), FEM_EAGAIN if
+ * timeout_us <= 0 and it has not, FEM_ETIMEOUT if the wait ran out. */
+int fem_serve_poll(fem_server* s, uint64_t ticket, int timeout_us, fem_result* out);
+/* Frees a finished request's outputs (the caller's reads of them must have
+ * completed) and forgets the ticket. */
+int fem_serve_release(fem_server* s, uint64_t ticket);
+/* Destroys a resident mesh (FEM_ESTATE while a request of it is in flight).
+ * Queued requests of the mesh then fail; pattern pointers of earlier results
+ * become invalid. */
+int fem_serve_evict(fem_server* s, uint64_t mesh_id);
+int fem_serve_stats(fem_server* s, fem_serve_counters* out);
+/* Stops the scheduler (queued requests are dropped), waits for the device
+ * work in flight and frees everything the server holds. */
+int fem_serve_destroy(fem_server* s);
+
 /* ------------------------------------------------------ reference element */
 /* The library's reference tables for (dim, order, qdeg): quadrature points
  * xq (nq x dim) and weights wq (nq, summing to 1/dim!), basis values phi

@@ -17,7 +17,10 @@ __all__ = [
     "fem_allocator", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_get_info", "fem_symbolic",
     "fem_get_slot_map", "fem_copy_pattern", "fem_assemble_mass", "fem_assemble_stiffness", "fem_assemble_tangent",
     "fem_assemble_all", "fem_reference_tables", "fem_set_allocator", "fem_last_error", "fem_version",
-    "fem_device_status", "fem_form_elements", "fem_sum_elements", "coeff", "FEM_MAT_M", "FEM_MAT_K", "FEM_MAT_T", "FEM_OK", "FEM_EINVAL", "FEM_ENOMEM", "FEM_EDEGENERATE", "FEM_ECUDA",
+    "fem_device_status", "fem_batch_create", "fem_batch_launch", "fem_batch_get_info", "fem_batch_destroy",
+    "fem_batch_opts", "fem_batch_info", "fem_serve_opts", "fem_request", "fem_result", "fem_serve_counters",
+    "fem_serve_create", "fem_serve_submit", "fem_serve_poll", "fem_serve_release", "fem_serve_evict",
+    "fem_serve_stats", "fem_serve_destroy", "FEM_REQ_ASSEMBLE", "FEM_REQ_REASSEMBLE", "fem_form_elements", "fem_sum_elements", "coeff", "FEM_MAT_M", "FEM_MAT_K", "FEM_MAT_T", "FEM_OK", "FEM_EINVAL", "FEM_ENOMEM", "FEM_EDEGENERATE", "FEM_ECUDA",
     "FEM_EBUSY", "FEM_EAGAIN", "FEM_ETIMEOUT", "FEM_ESTATE", "FEM_FP64", "FEM_TF32X3", "FEM_FP32",
     "FEM_MEM_HOST", "FEM_MEM_DEVICE", "FEM_K_POLY", "FEM_K_SIN", "FEM_K_PWLIN",
 ]
@@ -28,6 +31,7 @@ FEM_FP64, FEM_TF32X3, FEM_FP32 = 0, 1, 2
 FEM_MEM_HOST, FEM_MEM_DEVICE = 0, 1
 FEM_K_POLY, FEM_K_SIN, FEM_K_PWLIN = 0, 1, 2
 FEM_MAT_M, FEM_MAT_K, FEM_MAT_T = 1, 2, 4
+FEM_REQ_ASSEMBLE, FEM_REQ_REASSEMBLE = 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -70,6 +74,38 @@ class fem_allocator(C.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
 
 
+class fem_batch_opts(C.Structure):
+    _fields_ = [("prec", C.c_int), ("tune", C.c_int), ("use_graph", C.c_int), ("reserved", C.c_int)]
+
+
+class fem_batch_info(C.Structure):
+    _fields_ = [("n_meshes", C.c_int), ("kernels_per_launch", C.c_int), ("tc_tiles", C.c_int),
+                ("simt_blocks", C.c_int), ("sum_chunks", C.c_int), ("sum_block", C.c_int), ("simt_grid", C.c_int),
+                ("tuned", C.c_int), ("graph", C.c_int), ("tuned_ms", C.c_double)]
+
+
+class fem_serve_opts(C.Structure):
+    _fields_ = [("prec", C.c_int), ("max_inflight", C.c_int), ("n_streams", C.c_int), ("max_queue", C.c_int),
+                ("budget_bytes", C.c_size_t)]
+
+
+class fem_request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("which", C.c_int), ("mesh_id", C.c_uint64),
+                ("desc", C.POINTER(fem_mesh_desc)), ("k", C.POINTER(fem_coeff)), ("u", C.c_void_p)]
+
+
+class fem_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("prec", C.c_int), ("mesh_id", C.c_uint64), ("n", C.c_int64),
+                ("nnz", C.c_int64), ("d_row_ptr", C.c_void_p), ("d_col_idx", C.c_void_p), ("d_vM", C.c_void_p),
+                ("d_vK", C.c_void_p), ("d_vT", C.c_void_p), ("t_submit_us", C.c_double),
+                ("t_start_us", C.c_double), ("t_done_us", C.c_double)]
+
+
+class fem_serve_counters(C.Structure):
+    _fields_ = [("pending", C.c_int), ("inflight", C.c_int), ("resident_meshes", C.c_int),
+                ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -88,6 +124,19 @@ _SIGS = {
     "fem_assemble_all": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                           C.c_void_p, C.c_void_p], C.c_int),
     "fem_device_status": ([C.c_void_p], C.c_int),
+    "fem_batch_create": ([C.POINTER(C.c_void_p), C.c_int, C.POINTER(fem_batch_opts), C.c_void_p,
+                          C.POINTER(C.c_void_p)], C.c_int),
+    "fem_batch_launch": ([C.c_void_p, C.POINTER(fem_coeff), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                          C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p], C.c_int),
+    "fem_batch_get_info": ([C.c_void_p, C.POINTER(fem_batch_info)], C.c_int),
+    "fem_batch_destroy": ([C.c_void_p], C.c_int),
+    "fem_serve_create": ([C.POINTER(fem_serve_opts), C.POINTER(C.c_void_p)], C.c_int),
+    "fem_serve_submit": ([C.c_void_p, C.POINTER(fem_request), C.POINTER(C.c_uint64)], C.c_int),
+    "fem_serve_poll": ([C.c_void_p, C.c_uint64, C.c_int, C.POINTER(fem_result)], C.c_int),
+    "fem_serve_release": ([C.c_void_p, C.c_uint64], C.c_int),
+    "fem_serve_evict": ([C.c_void_p, C.c_uint64], C.c_int),
+    "fem_serve_stats": ([C.c_void_p, C.POINTER(fem_serve_counters)], C.c_int),
+    "fem_serve_destroy": ([C.c_void_p], C.c_int),
     "fem_assemble_all_noalloc": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p], C.c_int),
     "fem_form_elements": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_int, C.c_void_p], C.c_int),
@@ -230,6 +279,89 @@ def fem_assemble_all_noalloc(mesh: int, k, d_u, d_vM, d_vK, d_vT, stream=None) -
     library array of FEM_NOALLOC_SCRATCH_BYTES); device pointers only."""
     _check(lib().fem_assemble_all_noalloc(mesh, C.byref(k) if k is not None else None, _vp(d_u), _vp(d_vM),
                                           _vp(d_vK), _vp(d_vT), _stream(stream)))
+
+
+def _ptr_array(seq):
+    if seq is None:
+        return None
+    arr = (C.c_void_p * len(seq))()
+    for i, x in enumerate(seq):
+        arr[i] = _vp(x)
+    return arr
+
+
+def fem_batch_create(meshes, opts: fem_batch_opts | None = None, stream=None) -> int:
+    arr = (C.c_void_p * len(meshes))(*meshes)
+    h = C.c_void_p()
+    _check(lib().fem_batch_create(arr, len(meshes), C.byref(opts) if opts is not None else None, _stream(stream),
+                                  C.byref(h)))
+    return h.value
+
+
+def fem_batch_launch(batch: int, coeffs, d_u, d_vM, d_vK, d_vT, stream=None) -> None:
+    """coeffs: sequence of fem_coeff (one per mesh); the other arguments are
+    sequences of device pointers / tensors (or None)."""
+    karr = (fem_coeff * len(coeffs))(*coeffs) if coeffs is not None else None
+    _check(lib().fem_batch_launch(batch, karr, _ptr_array(d_u), _ptr_array(d_vM), _ptr_array(d_vK),
+                                  _ptr_array(d_vT), _stream(stream)))
+
+
+def fem_batch_get_info(batch: int) -> fem_batch_info:
+    info = fem_batch_info()
+    _check(lib().fem_batch_get_info(batch, C.byref(info)))
+    return info
+
+
+def fem_batch_destroy(batch: int) -> None:
+    _check(lib().fem_batch_destroy(batch))
+
+
+def fem_serve_create(opts: fem_serve_opts) -> int:
+    h = C.c_void_p()
+    _check(lib().fem_serve_create(C.byref(opts), C.byref(h)))
+    return h.value
+
+
+def fem_serve_submit(server: int, kind: int, which: int = 7, mesh_id: int = 0, desc: fem_mesh_desc | None = None,
+                     k: fem_coeff | None = None, u=None) -> int:
+    """Queues one request; u is a host FP64 array (copied), desc a
+    fem_mesh_desc whose buffers stay alive for the call.  Returns the ticket."""
+    import numpy as np
+    ua = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+    req = fem_request(kind, which, mesh_id, C.pointer(desc) if desc is not None else None,
+                      C.pointer(k) if k is not None else None, ua.ctypes.data if ua is not None else None)
+    t = C.c_uint64()
+    _check(lib().fem_serve_submit(server, C.byref(req), C.byref(t)))
+    return t.value
+
+
+def fem_serve_poll(server: int, ticket: int, timeout_us: int = 0) -> fem_result | None:
+    """The finished request's result, or None if it is not finished and
+    timeout_us <= 0.  Raises FemError(FEM_ETIMEOUT) if a wait ran out."""
+    out = fem_result()
+    rc = lib().fem_serve_poll(server, ticket, timeout_us, C.byref(out))
+    if rc == FEM_EAGAIN:
+        return None
+    _check(rc)
+    return out
+
+
+def fem_serve_release(server: int, ticket: int) -> None:
+    _check(lib().fem_serve_release(server, ticket))
+
+
+def fem_serve_evict(server: int, mesh_id: int) -> None:
+    _check(lib().fem_serve_evict(server, mesh_id))
+
+
+def fem_serve_stats(server: int) -> fem_serve_counters:
+    out = fem_serve_counters()
+    _check(lib().fem_serve_stats(server, C.byref(out)))
+    return out
+
+
+def fem_serve_destroy(server: int) -> None:
+    _check(lib().fem_serve_destroy(server))
 
 
 def fem_device_status(stream=None) -> None:

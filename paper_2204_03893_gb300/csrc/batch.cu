@@ -1,0 +1,351 @@
+// batch.cu -- batched reassembly of many meshes of uneven size and element
+// type in one CUDA graph of a few persistent kernels.
+//
+// The paper splits a mesh with several element types into one mesh per type
+// and merges the contributions before forming the sparse matrix (Section 7),
+// and notes that the formation of all element matrices can be done in
+// parallel (Section 7).  A batch generalises both: the element tiles of all
+// meshes form one work list (grouped by element type) that one persistent
+// tensor-core kernel walks, P3 tetrahedra (whose tile does not fit the
+// tensor-core layout) and FP64/FP32 batches go through one batched SIMT
+// kernel, and one batched CSR-sum kernel walks slot chunks of all meshes.
+// Per-launch inputs (u, coefficient laws, output pointers) live in a
+// device-side table that is rewritten from pinned host memory before each
+// graph launch; the graph itself never changes.  An optional tuner times the
+// launch shapes on the first launch (all candidates give identical bits:
+// per-slot summation order is independent of the launch shape).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "fem_internal.h"
+
+struct fem_batch {
+    int n = 0, prec = 0, device = 0;
+    bool use_graph = true, tune = false, tuned = false;
+    std::vector<fem_mesh*> meshes;
+    std::vector<fem::BatchMesh> host;      // static fields filled at creation
+    fem::DevBuf d_meshes;
+    fem::BatchMesh* pinned[2] = {nullptr, nullptr};
+    cudaEvent_t staged[2] = {nullptr, nullptr};
+    int cur = 0;
+    fem::DevBuf d_tc, d_simt, d_split, d_scatter;
+    int n_tc = 0, n_simt = 0, n_split = 0, n_scatter = 0;
+    int tc_talloc = 0, tc_smem = 0, tc_grid = 0;
+    int simt_smem = 0, simt_grid = 0;
+    int scatter_block = 256;
+    double tuned_ms = 0.0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+};
+
+namespace fem {
+int validate_coeff(const fem_coeff* k);
+CoeffDev coeff_to_device(const fem_coeff* k);
+
+namespace {
+
+int upload_items(DevBuf& buf, const std::vector<BatchItem>& items, cudaStream_t s) {
+    int rc = buf_alloc(buf, sizeof(BatchItem) * (items.empty() ? 1 : items.size()), s);
+    if (rc) return rc;
+    if (!items.empty())
+        FEM_CUDA_TRY(cudaMemcpyAsync(buf.ptr, items.data(), sizeof(BatchItem) * items.size(),
+                                     cudaMemcpyHostToDevice, s));
+    return FEM_OK;
+}
+
+// the kernels of one reassembly, in order, on stream s
+int enqueue(fem_batch* b, cudaStream_t s) {
+    int rc;
+    const BatchMesh* tab = b->d_meshes.as<BatchMesh>();
+    if (b->prec != FEM_FP64 &&
+        (rc = batch_split_launch(b->d_split.as<BatchItem>(), b->n_split, tab, s)))
+        return rc;
+    if (b->prec == FEM_FP64) {
+        if ((rc = batch_simt_launch<double>(b->d_simt.as<BatchItem>(), b->n_simt, tab, b->simt_smem, b->simt_grid, s)))
+            return rc;
+        return batch_scatter_launch<double>(b->d_scatter.as<BatchItem>(), b->n_scatter, tab, b->scatter_block, s);
+    }
+    if (b->n_tc &&
+        (rc = batch_tc_launch(b->d_tc.as<BatchItem>(), b->n_tc, tab, b->tc_talloc, b->tc_smem, b->tc_grid, s)))
+        return rc;
+    if ((rc = batch_simt_launch<float>(b->d_simt.as<BatchItem>(), b->n_simt, tab, b->simt_smem, b->simt_grid, s)))
+        return rc;
+    return batch_scatter_launch<float>(b->d_scatter.as<BatchItem>(), b->n_scatter, tab, b->scatter_block, s);
+}
+
+int build_scatter_items(fem_batch* b, int block, cudaStream_t s) {
+    std::vector<BatchItem> items;
+    const int chunk = block * 4;
+    for (int i = 0; i < b->n; ++i)
+        for (int64_t f = 0; f < b->meshes[i]->nnz; f += chunk)
+            items.push_back(BatchItem{i, b->meshes[i]->type, f, chunk, 0});
+    b->n_scatter = (int)items.size();
+    return upload_items(b->d_scatter, items, s);
+}
+
+int capture(fem_batch* b) {
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    FEM_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue(b, b->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    b->graph = g;
+    FEM_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
+    return FEM_OK;
+}
+
+// time a few launch shapes on the real inputs and keep the fastest
+int autotune(fem_batch* b, cudaStream_t s) {
+    int dev = b->device, nsm = 0;
+    FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks[] = {128, 256, 512};
+    const int simt_per_sm[] = {8, 16, 32};
+    cudaEvent_t e0, e1;
+    FEM_CUDA_TRY(cudaEventCreate(&e0));
+    FEM_CUDA_TRY(cudaEventCreate(&e1));
+    double best = 1e300;
+    int best_block = b->scatter_block, best_simt = b->simt_grid;
+    int rc = FEM_OK;
+    for (int bl : blocks) {
+        if ((rc = build_scatter_items(b, bl, s))) break;
+        b->scatter_block = bl;
+        for (int sp : simt_per_sm) {
+            b->simt_grid = nsm * sp;
+            if ((rc = enqueue(b, s))) break;       // warm-up
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 3; ++r)
+                if ((rc = enqueue(b, s))) break;
+            cudaEventRecord(e1, s);
+            if (rc) break;
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms / 3.0 < best) {
+                best = ms / 3.0;
+                best_block = bl;
+                best_simt = b->simt_grid;
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    b->simt_grid = best_simt;
+    b->tuned_ms = best;
+    if ((rc = build_scatter_items(b, best_block, s))) return rc;
+    b->scatter_block = best_block;
+    FEM_CUDA_TRY(cudaStreamSynchronize(s));
+    return FEM_OK;
+}
+
+}  // namespace
+}  // namespace fem
+
+using namespace fem;
+
+extern "C" {
+
+int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts, void* stream, fem_batch** out) {
+    if (!meshes || n <= 0 || !out) return fail(FEM_EINVAL, "need at least one mesh");
+    *out = nullptr;
+    const int prec = opts ? opts->prec : FEM_TF32X3;
+    if (prec != FEM_FP64 && prec != FEM_TF32X3 && prec != FEM_FP32) return fail(FEM_EINVAL, "unknown precision");
+    for (int i = 0; i < n; ++i) {
+        if (!meshes[i]) return fail(FEM_EINVAL, "NULL mesh in batch");
+        if (!meshes[i]->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run on every mesh");
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    if ((rc = tables_init_tc()) || (rc = tables_init_simt())) return rc;
+    fem_batch* b = new fem_batch;
+    b->n = n;
+    b->prec = prec;
+    b->use_graph = opts ? opts->use_graph != 0 : true;
+    b->tune = opts ? opts->tune != 0 : false;
+    b->meshes.assign(meshes, meshes + n);
+    cudaGetDevice(&b->device);
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+    const size_t esz = prec == FEM_FP64 ? 8 : 4;
+    std::vector<BatchItem> tc, simt, split;
+    b->host.resize(n);
+    for (int i = 0; i < n; ++i) {
+        fem_mesh* m = meshes[i];
+        const size_t nsym = (size_t)m->np * (m->np + 1) / 2, nt = (size_t)m->np * m->np;
+        if ((rc = buf_alloc(m->VM, esz * (size_t)m->E * nsym, s)) || (rc = buf_alloc(m->VK, esz * (size_t)m->E * nsym, s)) ||
+            (rc = buf_alloc(m->VT, esz * (size_t)m->E * nt, s))) {
+            fem_batch_destroy(b);
+            return rc;
+        }
+        m->v_prec = -1;   // scratch now belongs to the batch's precision
+        if (prec != FEM_FP64 && (rc = buf_alloc(m->u_split, sizeof(float2) * (size_t)m->n, s))) {
+            fem_batch_destroy(b);
+            return rc;
+        }
+        BatchMesh& h = b->host[i];
+        std::memset(&h, 0, sizeof(h));
+        h.conn = m->conn.as<int>();
+        h.geo32 = m->geo32.as<float>();
+        h.geo64 = m->geo64.as<double>();
+        h.E = m->E;
+        h.n = m->n;
+        h.nnz = m->nnz;
+        h.np = m->np;
+        h.type = m->type;
+        h.mass = m->m;
+        h.u2 = prec != FEM_FP64 ? m->u_split.as<float2>() : nullptr;
+        h.VM = m->VM.ptr;
+        h.VK = m->VK.ptr;
+        h.VT = m->VT.ptr;
+        h.seg_ptr = m->seg_ptr.as<int>();
+        h.contrib = m->contrib.as<int>();
+        const bool on_tc = prec == FEM_TF32X3 && tc_type_supported(m->type);
+        if (on_tc) {
+            for (int64_t f = 0; f < m->E; f += 128) tc.push_back(BatchItem{i, m->type, f, 128, 0});
+            b->tc_smem = std::max(b->tc_smem, tc_type_smem(m->type));
+            b->tc_talloc = std::max(b->tc_talloc, tc_type_alloc(m->type));
+        } else {
+            for (int64_t f = 0; f < m->E; f += 64) simt.push_back(BatchItem{i, m->type, f, 64, 0});
+            b->simt_smem = std::max(b->simt_smem, batch_simt_smem(m->type, prec == FEM_FP64));
+        }
+        if (prec != FEM_FP64)
+            for (int64_t f = 0; f < m->n; f += 2048) split.push_back(BatchItem{i, m->type, f, 2048, 0});
+    }
+    // tensor-core tiles grouped by element type, so each CTA reloads Q rarely
+    std::stable_sort(tc.begin(), tc.end(), [](const BatchItem& a, const BatchItem& c) { return a.type < c.type; });
+    b->n_tc = (int)tc.size();
+    b->n_simt = (int)simt.size();
+    b->n_split = (int)split.size();
+    b->tc_grid = nsm;
+    b->simt_grid = nsm * 16;
+    if (b->simt_smem == 0) b->simt_smem = 16;
+    if ((rc = upload_items(b->d_tc, tc, s)) || (rc = upload_items(b->d_simt, simt, s)) ||
+        (rc = upload_items(b->d_split, split, s)) || (rc = build_scatter_items(b, b->scatter_block, s)) ||
+        (rc = buf_alloc(b->d_meshes, sizeof(BatchMesh) * n, s))) {
+        fem_batch_destroy(b);
+        return rc;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMallocHost((void**)&b->pinned[k], sizeof(BatchMesh) * n);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        fem_batch_destroy(b);
+        return cuda_fail(e, "batch set-up");
+    }
+    if (b->use_graph && !b->tune && (rc = capture(b))) {
+        fem_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return FEM_OK;
+}
+
+int fem_batch_launch(fem_batch* b, const fem_coeff* k, const double* const* d_u, void* const* d_vM,
+                     void* const* d_vK, void* const* d_vT, void* stream) {
+    if (!b) return fail(FEM_EINVAL, "NULL batch");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // per-launch table: static fields + this launch's u, laws and outputs
+    BatchMesh* st = b->pinned[b->cur];
+    FEM_CUDA_TRY(cudaEventSynchronize(b->staged[b->cur]));   // the previous copy out of this buffer is done
+    const size_t esz = b->prec == FEM_FP64 ? 8 : 4;
+    for (int i = 0; i < b->n; ++i) {
+        // scratch pointers are taken from the mesh at every launch: a
+        // single-mesh call in between may have reallocated them
+        fem_mesh* m = b->meshes[i];
+        const size_t nsym = (size_t)m->np * (m->np + 1) / 2, nt = (size_t)m->np * m->np;
+        int rc0;
+        if ((rc0 = buf_alloc(m->VM, esz * (size_t)m->E * nsym, s)) || (rc0 = buf_alloc(m->VK, esz * (size_t)m->E * nsym, s)) ||
+            (rc0 = buf_alloc(m->VT, esz * (size_t)m->E * nt, s)) ||
+            (b->prec != FEM_FP64 && (rc0 = buf_alloc(m->u_split, sizeof(float2) * (size_t)m->n, s))))
+            return rc0;
+        m->v_prec = -1;
+        BatchMesh h = b->host[i];
+        h.VM = m->VM.ptr;
+        h.VK = m->VK.ptr;
+        h.VT = m->VT.ptr;
+        h.u2 = b->prec != FEM_FP64 ? m->u_split.as<float2>() : nullptr;
+        h.vM = d_vM ? d_vM[i] : nullptr;
+        h.vK = d_vK ? d_vK[i] : nullptr;
+        h.vT = d_vT ? d_vT[i] : nullptr;
+        if (h.vK || h.vT) {
+            if (!k) return fail(FEM_EINVAL, "coefficient laws are NULL");
+            int rc = validate_coeff(&k[i]);
+            if (rc) return rc;
+            if (!d_u || !d_u[i]) return fail(FEM_EINVAL, "u is NULL for a mesh that needs it");
+            h.u = d_u[i];
+            h.k = coeff_to_device(&k[i]);
+        } else {
+            h.u = nullptr;
+            h.u2 = nullptr;
+        }
+        st[i] = h;
+    }
+    FEM_CUDA_TRY(cudaMemcpyAsync(b->d_meshes.ptr, st, sizeof(BatchMesh) * b->n, cudaMemcpyHostToDevice, s));
+    FEM_CUDA_TRY(cudaEventRecord(b->staged[b->cur], s));
+    b->cur ^= 1;
+    int rc;
+    if (b->tune && !b->tuned) {
+        if ((rc = autotune(b, s))) return rc;
+        b->tuned = true;
+        if (b->use_graph && (rc = capture(b))) return rc;
+    }
+    if (b->use_graph && b->exec) {
+        FEM_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+        return FEM_OK;
+    }
+    return enqueue(b, s);
+}
+
+int fem_batch_get_info(const fem_batch* b, fem_batch_info* out) {
+    if (!b || !out) return fail(FEM_EINVAL, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    out->n_meshes = b->n;
+    out->kernels_per_launch = (b->prec != FEM_FP64 ? 1 : 0) + (b->n_tc ? 1 : 0) + (b->n_simt ? 1 : 0) + 1;
+    out->tc_tiles = b->n_tc;
+    out->simt_blocks = b->n_simt;
+    out->sum_chunks = b->n_scatter;
+    out->sum_block = b->scatter_block;
+    out->simt_grid = b->simt_grid;
+    out->tuned = b->tuned ? 1 : 0;
+    out->tuned_ms = b->tuned_ms;
+    out->graph = b->exec != nullptr ? 1 : 0;
+    return FEM_OK;
+}
+
+int fem_batch_destroy(fem_batch* b) {
+    if (!b) return FEM_OK;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (int k = 0; k < 2; ++k) {
+        if (b->pinned[k]) cudaFreeHost(b->pinned[k]);
+        if (b->staged[k]) cudaEventDestroy(b->staged[k]);
+    }
+    DevBuf* bufs[] = {&b->d_meshes, &b->d_tc, &b->d_simt, &b->d_split, &b->d_scatter};
+    for (auto* x : bufs) buf_free(*x, nullptr);
+    cudaDeviceSynchronize();
+    delete b;
+    return FEM_OK;
+}
+
+}  // extern "C"

@@ -54,114 +54,175 @@ struct UType { using type = double; };
 template <>
 struct UType<float> { using type = float2; };
 
+// X row and V = X Q of element e (thread-private X row in shared memory).
+template <typename ETy, typename T>
+__device__ __forceinline__ void simt_element(int64_t e, const int* __restrict__ conn, const T* __restrict__ geo,
+                                             int64_t E, const typename UType<T>::type* __restrict__ u,
+                                             const CoeffDev& k, T mass, T* __restrict__ VM, T* __restrict__ VK,
+                                             T* __restrict__ VT, T* X) {
+    constexpr int D = ETy::D, NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS;
+    constexpr int KM = ETy::KM, KK = ETy::KK, KT = ETy::KT;
+    constexpr int TO = type_tab_off(ETy::TYPE);
+    constexpr int PHI = TO, GR = TO + NQ * NP, WQ = TO + NQ * NP * (1 + D);
+    constexpr int QO = q_off(ETy::TYPE);
+    constexpr int QM_O = QO, QK_O = QO + KM * ETy::NSYM, QT_O = QK_O + KK * ETy::NSYM;
+    const T* Q = Tabs<T>::Q();
+    const bool need_u = (VK != nullptr) | (VT != nullptr);
+    // du[i] = u_i - u_0 and u_0 (u is only needed for K and T; mass-only calls pass NULL)
+    T du[NP];
+    T u0 = T(0);
+    const int* ce = conn + e * NP;
+    if (need_u) {
+        if constexpr (sizeof(T) == 8) {
+            u0 = u[ce[0]];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) du[i] = u[ce[i]] - u0;
+        } else {
+            const float2 a = u[ce[0]];
+            u0 = a.x + a.y;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const float2 b = u[ce[i]];
+                du[i] = (b.x - a.x) + (b.y - a.y);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) du[i] = T(0);
+    }
+    T b = geo[e];
+    T A[NS];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) A[t] = geo[(1 + t) * E + e];
+    // --- X = Lambda, Lambda (.) W, tangent factors
+#pragma unroll 1
+    for (int q = 0; q < NQ; ++q) {
+        // u_q = u_0 + sum_i phi_i (u_i - u_0) (the basis sums to one); the
+        // reference gradient uses the differences only (its rows sum to zero)
+        T uq = T(0);
+        T g[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) g[a] = T(0);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            uq += Tabs<T>::ref(PHI + q * NP + i) * du[i];
+#pragma unroll
+            for (int a = 0; a < D; ++a) g[a] += Tabs<T>::ref(GR + (q * NP + i) * D + a) * du[i];
+        }
+        uq += u0;
+        T dk;
+        T kq = k_eval<T>(k, uq, dk);
+        T lam = Tabs<T>::ref(WQ + q) * b;
+        X[q] = mass * lam;
+        T lk = lam * kq;
+#pragma unroll
+        for (int t = 0; t < NS; ++t) X[KM + q * NS + t] = lk * A[t];
+        // A ghat, A symmetric stored as upper triangle
+        T ld = lam * dk;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            T s = T(0);
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                int lo = a < c ? a : c, hi = a < c ? c : a;
+                int t = lo * D - (lo * (lo - 1)) / 2 + (hi - lo);
+                s += A[t] * g[c];
+            }
+            X[KM + KK + q * D + a] = ld * s;
+        }
+    }
+    // --- V = X Q, chunks of CH outputs
+    constexpr int CH = 8;
+    auto product = [&](const T* Xs, int K, const T* Qm, int N, T* V) {
+#pragma unroll 1
+        for (int n0 = 0; n0 < N; n0 += CH) {
+            T acc[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) acc[c] = T(0);
+#pragma unroll 2
+            for (int kk = 0; kk < K; ++kk) {
+                T x = Xs[kk];
+                const T* qrow = Qm + kk * N + n0;
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    if (n0 + c < N) acc[c] += x * qrow[c];
+            }
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                if (n0 + c < N) V[e * N + n0 + c] = acc[c];
+        }
+    };
+    if (VM) product(X, KM, Q + QM_O, ETy::NSYM, VM);
+    if (VK) product(X + KM, KK, Q + QK_O, ETy::NSYM, VK);
+    if (VT) product(X + KM + KK, KT, Q + QT_O, ETy::NT, VT);
+}
+
 template <typename ETy, typename T>
 __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict__ conn, const T* __restrict__ geo,
                                                           int64_t E, const typename UType<T>::type* __restrict__ u,
                                                           CoeffDev k, T mass, T* __restrict__ VM, T* __restrict__ VK,
                                                           T* __restrict__ VT) {
-    constexpr int D = ETy::D, NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS;
-    constexpr int KM = ETy::KM, KK = ETy::KK, KT = ETy::KT;
-    constexpr int KTOT = KM + KK + KT;
+    constexpr int KTOT = ETy::KM + ETy::KK + ETy::KT;
     constexpr int LD = KTOT | 1;   // odd row stride: conflict-free per-thread rows
-    constexpr int TO = type_tab_off(ETy::TYPE);
-    constexpr int PHI = TO, GR = TO + NQ * NP, WQ = TO + NQ * NP * (1 + D);
-    constexpr int QO = q_off(ETy::TYPE);
-    constexpr int QM_O = QO, QK_O = QO + KM * ETy::NSYM, QT_O = QK_O + KK * ETy::NSYM;
     extern __shared__ unsigned char smem_raw[];
     T* X = reinterpret_cast<T*>(smem_raw) + threadIdx.x * LD;
-
-    const T* Q = Tabs<T>::Q();
-    const bool need_u = (VK != nullptr) | (VT != nullptr);
     for (int64_t e0 = (int64_t)blockIdx.x * BT; e0 < E; e0 += (int64_t)gridDim.x * BT) {
         int64_t e = e0 + threadIdx.x;
         if (e >= E) continue;
-        // du[i] = u_i - u_0 and u_0 (u is only needed for K and T; mass-only calls pass NULL)
-        T du[NP];
-        T u0 = T(0);
-        const int* ce = conn + e * NP;
-        if (need_u) {
-            if constexpr (sizeof(T) == 8) {
-                u0 = u[ce[0]];
-#pragma unroll
-                for (int i = 0; i < NP; ++i) du[i] = u[ce[i]] - u0;
-            } else {
-                const float2 a = u[ce[0]];
-                u0 = a.x + a.y;
-#pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    const float2 b = u[ce[i]];
-                    du[i] = (b.x - a.x) + (b.y - a.y);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < NP; ++i) du[i] = T(0);
+        simt_element<ETy, T>(e, conn, geo, E, u, k, mass, VM, VK, VT, X);
+    }
+}
+
+// Batched: the work list holds blocks of BT elements of many meshes.
+template <typename T>
+__global__ void __launch_bounds__(BT) batch_simt_kernel(const BatchItem* __restrict__ items, int nitems,
+                                                        const BatchMesh* __restrict__ meshes) {
+    extern __shared__ unsigned char smem_raw[];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        const BatchMesh& bm = meshes[w.mesh];
+        const int64_t e = w.first + threadIdx.x;
+        if (threadIdx.x >= w.count || e >= bm.E) continue;
+        const T* geo = static_cast<const T*>(sizeof(T) == 8 ? (const void*)bm.geo64 : (const void*)bm.geo32);
+        const typename UType<T>::type* u;
+        if constexpr (sizeof(T) == 8) u = bm.u;
+        else u = bm.u2;
+        T* VM = bm.vM ? static_cast<T*>(bm.VM) : nullptr;
+        T* VK = bm.vK ? static_cast<T*>(bm.VK) : nullptr;
+        T* VT = bm.vT ? static_cast<T*>(bm.VT) : nullptr;
+        const T mass = (T)bm.mass;
+        switch (w.type) {
+#define FEM_BATCH_SIMT_CASE(TY, DD, PP)                                                                     \
+    case TY: {                                                                                          \
+        constexpr int LD = (ET<DD, PP>::KM + ET<DD, PP>::KK + ET<DD, PP>::KT) | 1;                      \
+        simt_element<ET<DD, PP>, T>(e, bm.conn, geo, bm.E, u, bm.k, mass, VM, VK, VT,                   \
+                                    reinterpret_cast<T*>(smem_raw) + threadIdx.x * LD);                 \
+    } break;
+            FEM_BATCH_SIMT_CASE(0, 2, 1)
+            FEM_BATCH_SIMT_CASE(1, 2, 2)
+            FEM_BATCH_SIMT_CASE(2, 2, 3)
+            FEM_BATCH_SIMT_CASE(3, 3, 1)
+            FEM_BATCH_SIMT_CASE(4, 3, 2)
+            FEM_BATCH_SIMT_CASE(5, 3, 3)
+#undef FEM_BATCH_SIMT_CASE
+            default: break;
         }
-        T b = geo[e];
-        T A[NS];
-#pragma unroll
-        for (int t = 0; t < NS; ++t) A[t] = geo[(1 + t) * E + e];
-        // --- X = Lambda, Lambda (.) W, tangent factors
-#pragma unroll 1
-        for (int q = 0; q < NQ; ++q) {
-            // u_q = u_0 + sum_i phi_i (u_i - u_0) (the basis sums to one); the
-            // reference gradient uses the differences only (its rows sum to zero)
-            T uq = T(0);
-            T g[D];
-#pragma unroll
-            for (int a = 0; a < D; ++a) g[a] = T(0);
-#pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                uq += Tabs<T>::ref(PHI + q * NP + i) * du[i];
-#pragma unroll
-                for (int a = 0; a < D; ++a) g[a] += Tabs<T>::ref(GR + (q * NP + i) * D + a) * du[i];
-            }
-            uq += u0;
-            T dk;
-            T kq = k_eval<T>(k, uq, dk);
-            T lam = Tabs<T>::ref(WQ + q) * b;
-            X[q] = mass * lam;
-            T lk = lam * kq;
-#pragma unroll
-            for (int t = 0; t < NS; ++t) X[KM + q * NS + t] = lk * A[t];
-            // A ghat, A symmetric stored as upper triangle
-            T ld = lam * dk;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                T s = T(0);
-#pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    int lo = a < c ? a : c, hi = a < c ? c : a;
-                    int t = lo * D - (lo * (lo - 1)) / 2 + (hi - lo);
-                    s += A[t] * g[c];
-                }
-                X[KM + KK + q * D + a] = ld * s;
-            }
+    }
+}
+
+__global__ void batch_split_kernel(const BatchItem* __restrict__ items, int nitems,
+                                   const BatchMesh* __restrict__ meshes) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        const BatchMesh& bm = meshes[w.mesh];
+        if (!bm.u2 || !bm.u) continue;
+        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
+            const int64_t i = w.first + k;
+            if (i >= bm.n) break;
+            const double v = bm.u[i];
+            const float hi = (float)v;
+            bm.u2[i] = make_float2(hi, (float)(v - (double)hi));
         }
-        // --- V = X Q, chunks of CH outputs
-        constexpr int CH = 8;
-        auto product = [&](const T* Xs, int K, const T* Qm, int N, T* V) {
-#pragma unroll 1
-            for (int n0 = 0; n0 < N; n0 += CH) {
-                T acc[CH];
-#pragma unroll
-                for (int c = 0; c < CH; ++c) acc[c] = T(0);
-#pragma unroll 2
-                for (int kk = 0; kk < K; ++kk) {
-                    T x = Xs[kk];
-                    const T* qrow = Qm + kk * N + n0;
-#pragma unroll
-                    for (int c = 0; c < CH; ++c)
-                        if (n0 + c < N) acc[c] += x * qrow[c];
-                }
-#pragma unroll
-                for (int c = 0; c < CH; ++c)
-                    if (n0 + c < N) V[e * N + n0 + c] = acc[c];
-            }
-        };
-        if (VM) product(X, KM, Q + QM_O, ETy::NSYM, VM);
-        if (VK) product(X + KM, KK, Q + QK_O, ETy::NSYM, VK);
-        if (VT) product(X + KM + KK, KT, Q + QT_O, ETy::NT, VT);
     }
 }
 
@@ -252,6 +313,37 @@ int element_simt_fp64(const fem_mesh& m, const CoeffDev& k, const double* u, dou
     int rc = tables_init_simt();
     if (rc) return rc;
     return dispatch<double>(m, k, u, m.geo64.as<double>(), VM, VK, VT, s);
+}
+
+int batch_simt_smem(int type, int fp64) {
+    const int ktot = type_nq(type) * (1 + type_d(type) * (type_d(type) + 1) / 2 + type_d(type));
+    return (ktot | 1) * BT * (fp64 ? 8 : 4);
+}
+
+template <typename T>
+int batch_simt_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int max_type_smem, int grid,
+                      cudaStream_t s) {
+    if (nitems <= 0) return FEM_OK;
+    int rc = tables_init_simt();
+    if (rc) return rc;
+    auto kern = batch_simt_kernel<T>;
+    FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_type_smem));
+    if (grid > nitems) grid = nitems;
+    cudaGetLastError();   // clear any stale error before the launch check
+    kern<<<grid, BT, max_type_smem, s>>>(items, nitems, meshes);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+template int batch_simt_launch<float>(const BatchItem*, int, const BatchMesh*, int, int, cudaStream_t);
+template int batch_simt_launch<double>(const BatchItem*, int, const BatchMesh*, int, int, cudaStream_t);
+
+int batch_split_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, cudaStream_t s) {
+    if (nitems <= 0) return FEM_OK;
+    int grid = nitems < 152 * 16 ? nitems : 152 * 16;
+    cudaGetLastError();   // clear any stale error before the launch check
+    batch_split_kernel<<<grid, 256, 0, s>>>(items, nitems, meshes);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
 }
 
 int split_u(const double* u, int64_t n, float2* out, cudaStream_t s) {

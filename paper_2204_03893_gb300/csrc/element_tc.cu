@@ -137,6 +137,66 @@ __device__ __forceinline__ void epilogue(uint32_t tmem, int col, float* stage, f
     }
 }
 
+// X row of one element (Section 4: Lambda = S * (w b^T) in place; X_c =
+// Lambda (.) W; the tangent factors), from its gathered nodal values (split
+// as hi + lo) and its geometry (b_e, A_e upper triangle).  Entries beyond
+// the true K of each matrix stay zero.
+template <typename ETy, int KMp, int KKp, int KTp>
+__device__ __forceinline__ void form_x(const float2 (&pu)[ETy::NP], const float (&pgeo)[1 + ETy::NS], bool need_u,
+                                       const CoeffDev& k, float mass, float (&xm)[KMp], float (&xk)[KKp],
+                                       float (&xt)[KTp]) {
+    constexpr int D = ETy::D, NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS;
+    constexpr int TO = type_tab_off(ETy::TYPE);
+    constexpr int PHI = TO, GR = TO + NQ * NP, WQ = TO + NQ * NP * (1 + D);
+    // du[i] = u_i - u_0 from the (hi, lo) split of u (exact differences of
+    // the hi parts); u is only needed for K and T (mass-only calls pass NULL)
+    float du[NP];
+    float u0 = 0.f;
+    if (need_u) {
+        u0 = pu[0].x + pu[0].y;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) du[i] = (pu[i].x - pu[0].x) + (pu[i].y - pu[0].y);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) du[i] = 0.f;
+    }
+    const float b = pgeo[0];
+    float A[NS];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) A[t] = pgeo[1 + t];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        float uq = 0.f, g[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) g[a] = 0.f;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            uq = fmaf(c_tcref[PHI + q * NP + i], du[i], uq);
+#pragma unroll
+            for (int a = 0; a < D; ++a) g[a] = fmaf(c_tcref[GR + (q * NP + i) * D + a], du[i], g[a]);
+        }
+        uq += u0;
+        float dk;
+        const float kq = k_eval<float>(k, uq, dk);
+        const float lam = c_tcref[WQ + q] * b;
+        xm[q] = mass * lam;
+        const float lk = lam * kq;
+#pragma unroll
+        for (int t = 0; t < NS; ++t) xk[q * NS + t] = lk * A[t];
+        const float ld = lam * dk;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            float sacc = 0.f;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const int lo = a < c ? a : c, hi = a < c ? c : a;
+                sacc = fmaf(A[lo * D - (lo * (lo - 1)) / 2 + (hi - lo)], g[c], sacc);
+            }
+            xt[q * D + a] = ld * sacc;
+        }
+    }
+}
+
 template <typename ETy>
 __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict__ conn, const float* __restrict__ geo,
                                                           int64_t E, const float2* __restrict__ u, CoeffDev k,
@@ -144,9 +204,7 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
                                                           float* __restrict__ VT, const float* __restrict__ img,
                                                           int* __restrict__ err) {
     using L = TcL<ETy>;
-    constexpr int D = ETy::D, NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS;
-    constexpr int TO = type_tab_off(ETy::TYPE);
-    constexpr int PHI = TO, GR = TO + NQ * NP, WQ = TO + NQ * NP * (1 + D);
+    constexpr int NP = ETy::NP, NS = ETy::NS;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
@@ -217,55 +275,7 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
         for (int i = 0; i < L::KKp; ++i) xk[i] = 0.f;
 #pragma unroll
         for (int i = 0; i < L::KTp; ++i) xt[i] = 0.f;
-        if (pvalid) {
-            // du[i] = u_i - u_0 from the (hi, lo) split of u (exact differences of
-            // the hi parts); u is only needed for K and T (mass-only calls pass NULL)
-            float du[NP];
-            float u0 = 0.f;
-            if (need_u) {
-                u0 = pu[0].x + pu[0].y;
-#pragma unroll
-                for (int i = 0; i < NP; ++i) du[i] = (pu[i].x - pu[0].x) + (pu[i].y - pu[0].y);
-            } else {
-#pragma unroll
-                for (int i = 0; i < NP; ++i) du[i] = 0.f;
-            }
-            const float b = pgeo[0];
-            float A[NS];
-#pragma unroll
-            for (int t = 0; t < NS; ++t) A[t] = pgeo[1 + t];
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                float uq = 0.f, g[D];
-#pragma unroll
-                for (int a = 0; a < D; ++a) g[a] = 0.f;
-#pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    uq = fmaf(c_tcref[PHI + q * NP + i], du[i], uq);
-#pragma unroll
-                    for (int a = 0; a < D; ++a) g[a] = fmaf(c_tcref[GR + (q * NP + i) * D + a], du[i], g[a]);
-                }
-                uq += u0;
-                float dk;
-                const float kq = k_eval<float>(k, uq, dk);
-                const float lam = c_tcref[WQ + q] * b;
-                xm[q] = mass * lam;
-                const float lk = lam * kq;
-#pragma unroll
-                for (int t = 0; t < NS; ++t) xk[q * NS + t] = lk * A[t];
-                const float ld = lam * dk;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    float s = 0.f;
-#pragma unroll
-                    for (int c = 0; c < D; ++c) {
-                        const int lo = a < c ? a : c, hi = a < c ? c : a;
-                        s = fmaf(A[lo * D - (lo * (lo - 1)) / 2 + (hi - lo)], g[c], s);
-                    }
-                    xt[q * D + a] = ld * s;
-                }
-            }
-        }
+        if (pvalid) form_x<ETy, L::KMp, L::KKp, L::KTp>(pu, pgeo, need_u, k, mass, xm, xk, xt);
         const int64_t next = tile + gridDim.x;
         if (next < ntiles) fetch_meta(next);
         if (doM) store_row<L::KMp>(sX + L::XMh, sX + L::XMl, xm, tid);
@@ -310,6 +320,142 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
     __syncthreads();
     tc::fence_after_sync();
     if (warp == 0) tc::tmem_dealloc(tmem, L::ALLOC);
+}
+
+// One 128-element tile of one mesh in the batched kernel: the same steps as
+// one iteration of element_tc_kernel (X rows -> shared memory, MMAs, bounded
+// wait, epilogue), with the mesh's parameters from the batch table.  The
+// type's Q image is already resident at smem[0, QEND).
+template <typename ETy>
+__device__ __forceinline__ bool batch_tc_tile(const BatchMesh& bm, int64_t first, unsigned char* smem,
+                                              uint32_t tmem, uint32_t mb, uint32_t& phase) {
+    using L = TcL<ETy>;
+    constexpr int NP = ETy::NP, NS = ETy::NS;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* sX = smem + L::QEND;
+    const uint32_t sQu = tc::smem_u32(smem), sXu = tc::smem_u32(sX);
+    const bool doM = bm.vM != nullptr, doK = bm.vK != nullptr, doT = bm.vT != nullptr;
+    if (!(doM | doK | doT)) return true;   // mesh skipped in this launch (uniform over the CTA)
+    const bool need_u = doK | doT;
+    const int64_t E = bm.E;
+    float xm[L::KMp], xk[L::KKp], xt[L::KTp];
+#pragma unroll
+    for (int i = 0; i < L::KMp; ++i) xm[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < L::KKp; ++i) xk[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < L::KTp; ++i) xt[i] = 0.f;
+    const int64_t e = first + tid;
+    if (e < E) {
+        float2 pu[NP];
+        float pgeo[1 + NS];
+        const int* ce = bm.conn + e * NP;
+        if (need_u) {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) pu[i] = __ldg(bm.u2 + __ldg(ce + i));
+        }
+#pragma unroll
+        for (int t = 0; t <= NS; ++t) pgeo[t] = __ldg(bm.geo32 + t * E + e);
+        form_x<ETy, L::KMp, L::KKp, L::KTp>(pu, pgeo, need_u, bm.k, (float)bm.mass, xm, xk, xt);
+    }
+    if (doM) store_row<L::KMp>(sX + L::XMh, sX + L::XMl, xm, tid);
+    if (doK) store_row<L::KKp>(sX + L::XKh, sX + L::XKl, xk, tid);
+    if (doT) store_row<L::KTp>(sX + L::XTh, sX + L::XTl, xt, tid);
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+        tc::fence_after_sync();
+        if (doM)
+            issue_tf32x3<L::KMp>(tmem + L::COLM, sXu + L::XMh, sXu + L::XMl, sQu + L::QMh, sQu + L::QMl,
+                                 tc::idesc_tf32(L::NMp));
+        if (doK)
+            issue_tf32x3<L::KKp>(tmem + L::COLK, sXu + L::XKh, sXu + L::XKl, sQu + L::QKh, sQu + L::QKl,
+                                 tc::idesc_tf32(L::NMp));
+        if (doT)
+            issue_tf32x3<L::KTp>(tmem + L::COLT, sXu + L::XTh, sXu + L::XTl, sQu + L::QTh, sQu + L::QTl,
+                                 tc::idesc_tf32(L::NTp));
+        tc::mma_commit(mb);
+    }
+    const uint32_t ok = tc::mbar_wait_bounded(mb, phase, WAIT_LIMIT);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) return false;
+    tc::fence_after_sync();
+    // the epilogue stages through the X region (the MMAs are complete)
+    float* stage = reinterpret_cast<float*>(sX) + warp * 32 * 33;
+    const int64_t row0 = first + warp * 32;
+    if (doM) epilogue<ETy::NSYM>(tmem, L::COLM, stage, static_cast<float*>(bm.VM), row0, E, warp, lane);
+    if (doK) epilogue<ETy::NSYM>(tmem, L::COLK, stage, static_cast<float*>(bm.VK), row0, E, warp, lane);
+    if (doT) epilogue<ETy::NT>(tmem, L::COLT, stage, static_cast<float*>(bm.VT), row0, E, warp, lane);
+    tc::fence_before_sync();
+    __syncthreads();
+    return true;
+}
+
+__host__ __device__ constexpr int tc_qend(int t) {
+    return t == 0 ? TcL<ET<2, 1>>::QEND : t == 1 ? TcL<ET<2, 2>>::QEND : t == 2 ? TcL<ET<2, 3>>::QEND
+         : t == 3 ? TcL<ET<3, 1>>::QEND : t == 4 ? TcL<ET<3, 2>>::QEND : 0;
+}
+
+// Persistent batched kernel: one 128-thread CTA per SM walks the work list
+// (tiles of all meshes, grouped by element type) and reloads the resident Q
+// image whenever the type changes.
+__global__ void __launch_bounds__(TILE) batch_tc_kernel(const BatchItem* __restrict__ items, int nitems,
+                                                        const BatchMesh* __restrict__ meshes,
+                                                        const float* __restrict__ img_all, uint32_t talloc,
+                                                        int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mb = tc::smem_u32(&mbar);
+    if (tid == 0) {
+        tc::mbar_init(mb, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(&tmem_slot), talloc);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    uint32_t phase = 0;
+    int cur = -1;
+    bool timed_out = false;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        if (w.type != cur) {
+            const int4* src = reinterpret_cast<const int4*>(img_all + (size_t)w.type * IMG_SLOT_FLOATS);
+            int4* dst = reinterpret_cast<int4*>(smem);
+            const int n16 = tc_qend(w.type) / 16;
+            for (int i = tid; i < n16; i += TILE) dst[i] = src[i];
+            __syncthreads();
+            cur = w.type;
+        }
+        const BatchMesh& bm = meshes[w.mesh];
+        bool ok = true;
+        switch (w.type) {
+            case 0: ok = batch_tc_tile<ET<2, 1>>(bm, w.first, smem, tmem, mb, phase); break;
+            case 1: ok = batch_tc_tile<ET<2, 2>>(bm, w.first, smem, tmem, mb, phase); break;
+            case 2: ok = batch_tc_tile<ET<2, 3>>(bm, w.first, smem, tmem, mb, phase); break;
+            case 3: ok = batch_tc_tile<ET<3, 1>>(bm, w.first, smem, tmem, mb, phase); break;
+            case 4: ok = batch_tc_tile<ET<3, 2>>(bm, w.first, smem, tmem, mb, phase); break;
+            default: break;
+        }
+        if (!ok) {   // uniform: decided by __syncthreads_or inside the tile
+            timed_out = true;
+            break;
+        }
+    }
+    if (timed_out) {
+        if (tid == 0) atomicExch(err, 1);
+        tc::mbar_wait_bounded(mb, phase ^ 1u, WAIT_LIMIT);
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, talloc);
 }
 
 // host-side TF32 rounding, nearest with ties away from zero (matches cvt.rna)
@@ -430,6 +576,65 @@ int tables_init_tc() {
     int zero = 0;
     FEM_CUDA_TRY(cudaMemcpyToSymbol(g_tc_err, &zero, sizeof(int)));
     if (dev < 64) g_done[dev] = true;
+    return FEM_OK;
+}
+
+int tc_type_supported(int type) {
+    switch (type) {
+        case 0: return TcL<ET<2, 1>>::FITS;
+        case 1: return TcL<ET<2, 2>>::FITS;
+        case 2: return TcL<ET<2, 3>>::FITS;
+        case 3: return TcL<ET<3, 1>>::FITS;
+        case 4: return TcL<ET<3, 2>>::FITS;
+        case 5: return TcL<ET<3, 3>>::FITS;
+    }
+    return 0;
+}
+int tc_type_smem(int type) {
+    switch (type) {
+        case 0: return TcL<ET<2, 1>>::SMEM;
+        case 1: return TcL<ET<2, 2>>::SMEM;
+        case 2: return TcL<ET<2, 3>>::SMEM;
+        case 3: return TcL<ET<3, 1>>::SMEM;
+        case 4: return TcL<ET<3, 2>>::SMEM;
+    }
+    return 0;
+}
+int tc_type_alloc(int type) {
+    switch (type) {
+        case 0: return TcL<ET<2, 1>>::ALLOC;
+        case 1: return TcL<ET<2, 2>>::ALLOC;
+        case 2: return TcL<ET<2, 3>>::ALLOC;
+        case 3: return TcL<ET<3, 1>>::ALLOC;
+        case 4: return TcL<ET<3, 2>>::ALLOC;
+    }
+    return 0;
+}
+
+int batch_tc_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int talloc, int smem, int grid,
+                    cudaStream_t s) {
+    if (nitems <= 0) return FEM_OK;
+    int rc = tables_init_tc();
+    if (rc) return rc;
+    if (talloc < 32 || talloc > 512 || (talloc & (talloc - 1))) return fail(FEM_EINVAL, "bad TMEM allocation");
+    auto kern = batch_tc_kernel;
+    int dev = 0, optin = 0, occ = 0;
+    FEM_CUDA_TRY(cudaGetDevice(&dev));
+    FEM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    FEM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+    if (smem > optin - (int)fa.sharedSizeBytes) return fail(FEM_EINVAL, "batched tile does not fit in shared memory");
+    FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+    if (occ < 1) return fail(FEM_ECUDA, "batched tensor-core kernel does not fit on an SM");
+    float* img = nullptr;
+    int* err = nullptr;
+    FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&img, g_tcimg));
+    FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&err, g_tc_err));
+    if (grid > nitems) grid = nitems;
+    cudaGetLastError();   // clear any stale error before the launch check
+    kern<<<grid, TILE, smem, s>>>(items, nitems, meshes, img, (uint32_t)talloc, err);
+    FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
 

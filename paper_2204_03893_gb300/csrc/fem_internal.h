@@ -50,6 +50,8 @@ struct fem_mesh {
     fem::DevBuf row_ptr, col_idx, seg_ptr, contrib, slot, inc_ptr, inc;
     fem::DevBuf loff;                   // 8-bit in-row offset of every element entry (if max_row <= 256)
     int max_row = 0;                    // longest CSR row
+    int sum_kernel = 0;                 // CSR sum variant: 0 = per-slot segments, 1 = row-wise (needs loff)
+    int sum_block = 256;                // threads per block of the CSR sum
     // numeric scratch: element matrices V (per matrix) in the precision of the last call
     fem::DevBuf VM, VK, VT;
     int v_prec = -1, v_mask = 0;        // what VM/VK/VT currently hold
@@ -84,6 +86,45 @@ int scatter_fp32(const fem_mesh& m, const float* VM, const float* VK, const floa
 // Coefficient validation and device form, shared by the C entry points.
 int validate_coeff(const fem_coeff* k);
 CoeffDev coeff_to_device(const fem_coeff* k);
+
+// ------------------------------------------------------------ batched launch
+// Per-mesh parameters of a batched launch (a device-side table the batched
+// kernels read; the host rewrites it before every launch).
+struct BatchMesh {
+    const int* conn;
+    const float* geo32;
+    const double* geo64;
+    int64_t E, n, nnz;
+    int np, type;
+    const double* u;                     // FP64 nodal values
+    float2* u2;                          // (hi, lo) split of u for the FP32 paths
+    CoeffDev k;
+    double mass;
+    void* VM; void* VK; void* VT;        // element-matrix scratch (FP32 or FP64)
+    const int* seg_ptr;
+    const int* contrib;
+    void* vM; void* vK; void* vT;        // CSR outputs, NULL = skip
+};
+// One unit of work: `count` consecutive elements (or slots, or nodes) of one mesh.
+struct BatchItem {
+    int mesh;
+    int type;
+    int64_t first;
+    int count;
+    int pad;
+};
+int tc_type_supported(int type);        // does the tensor-core tile of this element type fit?
+int tc_type_smem(int type);             // dynamic shared memory of its tile
+int tc_type_alloc(int type);            // TMEM columns of its tile (power of two)
+int batch_tc_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int talloc, int smem, int grid,
+                    cudaStream_t s);
+template <typename T>
+int batch_simt_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int max_type_smem, int grid,
+                      cudaStream_t s);
+int batch_simt_smem(int type, int fp64);
+int batch_split_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, cudaStream_t s);
+template <typename T>
+int batch_scatter_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int block, cudaStream_t s);
 
 // One-time per-device upload of the reference tables of each kernel module.
 int tables_init_simt();

@@ -8,7 +8,9 @@
 // M and K come from the symmetric element storage (entry (i,j) and (j,i)
 // share V[e][sym(min,max)]), T from the full n_p x n_p storage.
 //
-// Row-wise kernel (used when every CSR row has at most 256 entries): one
+// Two interchangeable kernels give identical bits (same order per slot); the
+// mesh records which one, and its block size, the tuner measured fastest.
+// Row-wise kernel (requires every CSR row to have at most 256 entries): one
 // thread owns one row r and walks the row's incident element rows (e, i),
 // conn[e][i] = r, in ascending e; for each it reads the element's local row
 // (n_p contiguous T entries and the matching symmetric M, K entries) and the
@@ -16,7 +18,7 @@
 // accumulators in shared memory.  A block owns a run of consecutive rows,
 // i.e. one contiguous range of CSR values, which it zeroes, fills and writes
 // out with coalesced stores.
-// Segment kernel (fallback): one thread per slot sums the slot's contributor
+// Segment kernel (default): one thread per slot sums the slot's contributor
 // list contrib[seg_ptr[s] .. seg_ptr[s+1]) (element entries, ascending).
 #include "fem_internal.h"
 
@@ -130,12 +132,66 @@ __global__ void __launch_bounds__(256) scatter_segments_kernel(const int* __rest
     }
 }
 
+// One slot of the segment sum (shared by the single-mesh and batched kernels).
+template <int NP, typename T>
+__device__ __forceinline__ void segment_slot(int64_t s, const int* __restrict__ seg_ptr,
+                                             const int* __restrict__ contrib, const T* __restrict__ VM,
+                                             const T* __restrict__ VK, const T* __restrict__ VT, T* __restrict__ vM,
+                                             T* __restrict__ vK, T* __restrict__ vT) {
+    constexpr int NT = NP * NP, NSYM = NP * (NP + 1) / 2;
+    const int a = seg_ptr[s], b = seg_ptr[s + 1];
+    T am = T(0), ak = T(0), at = T(0);
+    for (int p = a; p < b; ++p) {
+        const int c = contrib[p];
+        const int e = c / NT;
+        const int l = c - e * NT;
+        if (vT) at += VT[(int64_t)e * NT + l];
+        if (vM || vK) {
+            const int i = l / NP, j = l - (l / NP) * NP;
+            const int si = sym_idx(NP, i, j);
+            if (vM) am += VM[(int64_t)e * NSYM + si];
+            if (vK) ak += VK[(int64_t)e * NSYM + si];
+        }
+    }
+    if (vM) vM[s] = am;
+    if (vK) vK[s] = ak;
+    if (vT) vT[s] = at;
+}
+
+// Batched: the work list holds chunks of `count` slots of many meshes.
+template <typename T>
+__global__ void __launch_bounds__(512) batch_scatter_kernel(const BatchItem* __restrict__ items, int nitems,
+                                                            const BatchMesh* __restrict__ meshes) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        const BatchMesh& bm = meshes[w.mesh];
+        const T* VM = bm.vM ? static_cast<const T*>(bm.VM) : nullptr;
+        const T* VK = bm.vK ? static_cast<const T*>(bm.VK) : nullptr;
+        const T* VT = bm.vT ? static_cast<const T*>(bm.VT) : nullptr;
+        T* vM = static_cast<T*>(bm.vM);
+        T* vK = static_cast<T*>(bm.vK);
+        T* vT = static_cast<T*>(bm.vT);
+        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
+            const int64_t s = w.first + k;
+            if (s >= bm.nnz) break;
+            switch (bm.np) {
+                case 3: segment_slot<3, T>(s, bm.seg_ptr, bm.contrib, VM, VK, VT, vM, vK, vT); break;
+                case 4: segment_slot<4, T>(s, bm.seg_ptr, bm.contrib, VM, VK, VT, vM, vK, vT); break;
+                case 6: segment_slot<6, T>(s, bm.seg_ptr, bm.contrib, VM, VK, VT, vM, vK, vT); break;
+                case 10: segment_slot<10, T>(s, bm.seg_ptr, bm.contrib, VM, VK, VT, vM, vK, vT); break;
+                case 20: segment_slot<20, T>(s, bm.seg_ptr, bm.contrib, VM, VK, VT, vM, vK, vT); break;
+                default: break;
+            }
+        }
+    }
+}
+
 template <int NP, typename T>
 int launch_np(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s,
               int nsm) {
-    if (m.loff.ptr && m.max_row > 0) {
+    if (m.sum_kernel == 1 && m.loff.ptr && m.max_row > 0) {
         // threads per block: as many rows as fit ~64 KiB of accumulators (3 matrices)
-        int B = 256;
+        int B = m.sum_block > 0 ? m.sum_block : 256;
         while (B > 32 && (size_t)3 * B * m.max_row * sizeof(T) > 64 * 1024) B /= 2;
         const size_t smem = (size_t)3 * B * m.max_row * sizeof(T);
         auto kern = scatter_rows_kernel<NP, T>;
@@ -151,10 +207,11 @@ int launch_np(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T
         kern<<<(unsigned)blocks, B, smem, s>>>(m.inc_ptr.as<int>(), m.inc.as<int>(), m.row_ptr.as<int>(),
                                               m.loff.as<unsigned char>(), m.n, m.max_row, VM, VK, VT, vM, vK, vT);
     } else {
-        int64_t blocks = (m.nnz + 255) / 256;
-        if (blocks > (int64_t)nsm * 16) blocks = (int64_t)nsm * 16;
+        const int B = (m.sum_kernel == 0 && m.sum_block >= 32) ? m.sum_block : 256;
+        int64_t blocks = (m.nnz + B - 1) / B;
+        if (blocks > (int64_t)nsm * (4096 / B)) blocks = (int64_t)nsm * (4096 / B);
         cudaGetLastError();   // clear any stale error before the launch check
-        scatter_segments_kernel<NP, T><<<(unsigned)blocks, 256, 0, s>>>(
+        scatter_segments_kernel<NP, T><<<(unsigned)blocks, B, 0, s>>>(
             m.seg_ptr.as<int>(), m.contrib.as<int>(), m.nnz, VM, VK, VT, vM, vK, vT);
     }
     FEM_CUDA_TRY(cudaGetLastError());
@@ -178,6 +235,23 @@ int run(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, 
 }
 
 }  // namespace
+
+template <typename T>
+int batch_scatter_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int block, cudaStream_t s) {
+    if (nitems <= 0) return FEM_OK;
+    if (block < 32 || block > 512) block = 256;
+    int dev = 0, nsm = 0;
+    FEM_CUDA_TRY(cudaGetDevice(&dev));
+    FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int grid = nsm * (2048 / block);
+    if (grid > nitems) grid = nitems;
+    cudaGetLastError();   // clear any stale error before the launch check
+    batch_scatter_kernel<T><<<grid, block, 0, s>>>(items, nitems, meshes);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+template int batch_scatter_launch<float>(const BatchItem*, int, const BatchMesh*, int, cudaStream_t);
+template int batch_scatter_launch<double>(const BatchItem*, int, const BatchMesh*, int, cudaStream_t);
 
 int scatter_fp64(const fem_mesh& m, const double* VM, const double* VK, const double* VT, double* vM, double* vK,
                  double* vT, cudaStream_t s) {

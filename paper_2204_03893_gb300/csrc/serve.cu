@@ -1,0 +1,489 @@
+// serve.cu -- a request server for assembly / reassembly with continuous
+// batching.
+//
+// The paper's motivation is that repeated reassembly inside nonlinear
+// solvers is a bottleneck (Introduction), and that only S (the coefficient
+// evaluations) changes between Newton steps while Q, w, W and b stay fixed
+// (Section 5).  A server keeps, per mesh, everything that does not change
+// resident on the device (geometry, CSR pattern, slot segments, element
+// scratch) and turns each request into one element-product launch and one
+// CSR-sum launch.
+//
+// Threading: submit/poll/release run on caller threads; one scheduler thread
+// owns all device work.  It admits queued requests in arrival order while a
+// slot is free (max_inflight) and the device-memory budget allows (resident
+// meshes + outputs of requests not yet released), skipping a request only to
+// keep the requests of one mesh in order (a mesh's scratch is reused, so its
+// requests never overlap).  Admitted requests are spread over several CUDA
+// streams, so work of different meshes overlaps on the device; completion is
+// detected with CUDA events.  A request that can never fit the budget is
+// refused at submit (FEM_EBUSY).
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "fem_internal.h"
+
+namespace fem {
+int validate_coeff(const fem_coeff* k);
+CoeffDev coeff_to_device(const fem_coeff* k);
+}  // namespace fem
+
+namespace {
+
+using fem::buf_alloc;
+using fem::buf_free;
+using fem::cuda_fail;
+using fem::fail;
+using fem::set_error;
+using Clock = std::chrono::steady_clock;
+
+enum State { PENDING = 0, RUNNING = 1, DONE = 2 };
+
+struct Resident {
+    fem_mesh* mesh = nullptr;
+    fem::DevBuf u;            // FP64 nodal values of the current request
+    int busy = 0;             // a request of this mesh is in flight
+    bool evicted = false;     // fem_serve_evict was called; destroyed once idle
+    size_t bytes = 0;         // device bytes accounted for the mesh
+};
+
+struct Request {
+    uint64_t ticket = 0;
+    int kind = 0, which = 7, status = FEM_OK;
+    uint64_t mesh_id = 0;
+    fem_coeff k;
+    std::vector<double> u;                 // host copy of the nodal values
+    // ASSEMBLE: host copies of the mesh description
+    fem_mesh_desc desc;
+    std::vector<double> coords;
+    std::vector<int32_t> conn;
+    size_t est_bytes = 0;                  // admission estimate (outputs + mesh if new)
+    size_t out_bytes = 0;
+    fem::DevBuf out[3];
+    cudaEvent_t done = nullptr;
+    int stream = 0;
+    State state = PENDING;
+    std::string msg;                       // error message of a failed request
+    double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+}  // namespace
+
+struct fem_server {
+    fem_serve_opts opts;
+    int device = 0;
+    Clock::time_point t0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    std::thread th;
+    uint64_t next_ticket = 1, next_mesh = 1;
+    std::deque<uint64_t> queue;                                  // pending tickets, arrival order
+    std::map<uint64_t, std::unique_ptr<Request>> reqs;
+    std::map<uint64_t, Resident> meshes;
+    std::vector<cudaStream_t> streams;
+    std::vector<uint64_t> running;                               // tickets in flight
+    int rr = 0, inflight = 0;
+    size_t in_use = 0;                                           // accounted device bytes
+    size_t peak = 0;
+};
+
+namespace {
+
+double now_us(const fem_server* s) {
+    return std::chrono::duration<double, std::micro>(Clock::now() - s->t0).count();
+}
+
+size_t esz_of(int prec) { return prec == FEM_FP64 ? 8 : 4; }
+
+size_t nlocal(int d, int p) { return d == 2 ? (size_t)(p + 1) * (p + 2) / 2 : (size_t)(p + 1) * (p + 2) * (p + 3) / 6; }
+
+// upper bound of the device bytes a new mesh will hold (coords, conn, two
+// geometry caches, pattern, segments, slot map, offsets, scratch, u)
+size_t mesh_estimate(const fem_mesh_desc& d, int prec) {
+    const size_t np = nlocal(d.dim, d.order), E = (size_t)d.n_elems, n = (size_t)d.n_nodes;
+    const size_t m2 = E * np * np, ngeo = 1 + (size_t)d.dim * (d.dim + 1) / 2;
+    size_t b = n * d.dim * 8 + E * np * 4 + ngeo * E * 12;
+    b += (n + 1) * 4 * 5;                 // row_ptr, inc_ptr and three transient counters of the sort
+    b += m2 * 4 * 4 + m2 + E * np * 4;    // col_idx and seg_ptr (nnz <= m2), contrib, slot, loff, inc
+    b += esz_of(prec) * E * (np * (np + 1) + np * np) + n * 8 + n * 8;   // V scratch, u split, u
+    return b + 4096;                      // rounding of small buffers
+}
+
+// Precision a mesh is reassembled in: the server's, except that P3
+// tetrahedra (whose tile does not fit the tensor-core layout) use FP32 SIMT
+// in a FEM_TF32X3 server.
+int mesh_prec(int prec, const fem_mesh* m) {
+    return (prec == FEM_TF32X3 && m->d == 3 && m->p == 3) ? FEM_FP32 : prec;
+}
+
+// Runs on the scheduler thread with the lock released.  For ASSEMBLE the new
+// mesh is returned in *created (the caller publishes it under the lock).
+int start_request(fem_server* S, Request& r, Resident* res, fem_mesh** created, cudaStream_t st) {
+    int rc;
+    fem_mesh* m = res->mesh;
+    if (r.kind == FEM_REQ_ASSEMBLE) {
+        fem_mesh_desc d = r.desc;
+        d.coords = r.coords.data();
+        d.conn = r.conn.data();
+        d.mem = FEM_MEM_HOST;
+        if ((rc = fem_mesh_create(&d, st, &m))) return rc;
+        *created = m;
+        if ((rc = fem_symbolic(m, st, nullptr))) return rc;
+    }
+    const int prec = mesh_prec(S->opts.prec, m);
+    const size_t esz = esz_of(prec);
+    for (int i = 0; i < 3; ++i)
+        if (r.which & (1 << i))
+            if ((rc = buf_alloc(r.out[i], esz * (size_t)(m->nnz > 0 ? m->nnz : 1), st))) return rc;
+    const double* du = nullptr;
+    if (r.which & 6) {
+        if (r.u.size() != (size_t)m->n) return fail(FEM_EINVAL, "u has the wrong length for this mesh");
+        if ((rc = buf_alloc(res->u, sizeof(double) * (size_t)m->n, st))) return rc;
+        cudaError_t e = cudaMemcpyAsync(res->u.ptr, r.u.data(), sizeof(double) * r.u.size(), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "upload u");
+        du = res->u.as<double>();
+    }
+    if ((rc = fem_form_elements(m, &r.k, du, prec, r.which, st))) return rc;
+    if ((rc = fem_sum_elements(m, prec, r.out[0].ptr, r.out[1].ptr, r.out[2].ptr, st))) return rc;
+    cudaError_t e = cudaEventRecord(r.done, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    return FEM_OK;
+}
+
+void finish(fem_server* S, Request& r, int status, const std::string& msg) {
+    r.status = status;
+    r.msg = msg;
+    r.state = DONE;
+    r.t_done = now_us(S);
+}
+
+// Moves finished requests to DONE.  Lock held.
+bool reap(fem_server* S) {
+    bool progress = false;
+    for (size_t i = 0; i < S->running.size();) {
+        Request& r = *S->reqs[S->running[i]];
+        cudaError_t q = cudaEventQuery(r.done);
+        if (q == cudaErrorNotReady) {
+            ++i;
+            continue;
+        }
+        if (q == cudaSuccess) finish(S, r, FEM_OK, "");
+        else finish(S, r, FEM_ECUDA, std::string("request failed on the device: ") + cudaGetErrorString(q));
+        --S->inflight;
+        Resident& res = S->meshes[r.mesh_id];
+        res.busy = 0;
+        // account the mesh at its real size once it exists
+        const size_t real = res.mesh ? res.mesh->device_bytes() : 0;
+        if (real && real != res.bytes) {
+            S->in_use = S->in_use - res.bytes + real;
+            res.bytes = real;
+        }
+        S->running[i] = S->running.back();
+        S->running.pop_back();
+        progress = true;
+    }
+    return progress;
+}
+
+// Admits one queued request if one can start now (arrival order; a request
+// waits while another request of its mesh is in flight; when the head of the
+// line does not fit the budget, nothing behind it is admitted).  Starts it
+// with the lock released.  Returns false if nothing could be admitted.
+bool admit_one(fem_server* S, std::unique_lock<std::mutex>& lk) {
+    if (S->inflight >= S->opts.max_inflight) return false;
+    for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+        Request& r = *S->reqs[*it];
+        Resident* res = nullptr;
+        if (r.kind == FEM_REQ_REASSEMBLE) {
+            auto m = S->meshes.find(r.mesh_id);
+            if (m == S->meshes.end() || m->second.evicted) {
+                finish(S, r, FEM_EINVAL, "mesh was evicted before the request started");
+                S->queue.erase(it);
+                return true;
+            }
+            res = &m->second;
+            if (res->busy) continue;
+        }
+        if (S->in_use + r.est_bytes > S->opts.budget_bytes) return false;
+        if (r.kind == FEM_REQ_ASSEMBLE) {
+            r.mesh_id = S->next_mesh++;
+            res = &S->meshes[r.mesh_id];
+            res->bytes = r.est_bytes - r.out_bytes;
+        }
+        res->busy = 1;
+        S->in_use += r.est_bytes;
+        S->peak = std::max(S->peak, S->in_use);
+        r.state = RUNNING;
+        r.t_start = now_us(S);
+        r.stream = S->rr;
+        S->rr = (S->rr + 1) % (int)S->streams.size();
+        ++S->inflight;
+        S->queue.erase(it);
+        cudaStream_t st = S->streams[r.stream];
+        fem_mesh* created = nullptr;
+        lk.unlock();
+        int rc = start_request(S, r, res, &created, st);
+        std::string msg;
+        if (rc) {
+            char buf[512];
+            fem_last_error(buf, sizeof buf);
+            msg = buf;
+            if (created && r.kind == FEM_REQ_ASSEMBLE) {
+                cudaStreamSynchronize(st);
+                fem_mesh_destroy(created);
+                created = nullptr;
+            }
+        }
+        lk.lock();
+        if (created) res->mesh = created;
+        if (rc) {
+            finish(S, r, rc, msg);
+            --S->inflight;
+            res->busy = 0;
+            // the outputs stay accounted until release; a mesh that was not created is dropped
+            S->in_use -= r.est_bytes - r.out_bytes;
+            if (r.kind == FEM_REQ_ASSEMBLE) S->meshes.erase(r.mesh_id);
+        } else {
+            S->running.push_back(r.ticket);
+        }
+        return true;
+    }
+    return false;
+}
+
+void scheduler(fem_server* S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        bool progress = reap(S);
+        while (!S->stop && admit_one(S, lk)) progress = true;
+        if (progress) S->cv_done.notify_all();
+        else S->cv_work.wait_for(lk, std::chrono::microseconds(S->inflight ? 10 : 1000));
+    }
+}
+
+}  // namespace
+
+using namespace fem;
+
+extern "C" {
+
+int fem_serve_create(const fem_serve_opts* opts, fem_server** out) {
+    if (!opts || !out) return fail(FEM_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (opts->prec != FEM_FP64 && opts->prec != FEM_TF32X3 && opts->prec != FEM_FP32)
+        return fail(FEM_EINVAL, "unknown precision");
+    if (opts->max_inflight < 1 || opts->n_streams < 1 || opts->n_streams > 64 || opts->budget_bytes == 0)
+        return fail(FEM_EINVAL, "need max_inflight >= 1, 1 <= n_streams <= 64 and a nonzero budget");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    fem_server* S = new fem_server;
+    S->opts = *opts;
+    S->device = dev;
+    S->t0 = Clock::now();
+    for (int i = 0; i < opts->n_streams; ++i) {
+        cudaStream_t st;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            for (auto x : S->streams) cudaStreamDestroy(x);
+            delete S;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        S->streams.push_back(st);
+    }
+    S->th = std::thread(scheduler, S);
+    *out = S;
+    return FEM_OK;
+}
+
+int fem_serve_submit(fem_server* S, const fem_request* q, uint64_t* ticket) {
+    if (!S || !q || !ticket) return fail(FEM_EINVAL, "NULL argument");
+    if (q->kind != FEM_REQ_ASSEMBLE && q->kind != FEM_REQ_REASSEMBLE) return fail(FEM_EINVAL, "unknown request kind");
+    if (q->which <= 0 || q->which > 7) return fail(FEM_EINVAL, "which must be a nonzero mask of FEM_MAT_M|K|T");
+    if (q->which & 6) {
+        if (!q->k) return fail(FEM_EINVAL, "K or T requested without a coefficient law");
+        int rc = validate_coeff(q->k);
+        if (rc) return rc;
+        if (!q->u) return fail(FEM_EINVAL, "K or T requested without u");
+    }
+    auto r = std::make_unique<Request>();
+    r->kind = q->kind;
+    r->which = q->which;
+    if (q->k) r->k = *q->k;
+    else std::memset(&r->k, 0, sizeof r->k);
+    size_t n = 0, nnz_bound = 0;
+    int prec = S->opts.prec;
+    if (q->kind == FEM_REQ_ASSEMBLE) {
+        if (!q->desc) return fail(FEM_EINVAL, "ASSEMBLE needs a mesh description");
+        const fem_mesh_desc& d = *q->desc;
+        if ((d.dim != 2 && d.dim != 3) || d.order < 1 || d.order > 3 || d.n_nodes <= 0 || d.n_elems < 0 ||
+            !d.coords || (d.n_elems > 0 && !d.conn) || (d.mem != FEM_MEM_HOST && d.mem != FEM_MEM_DEVICE))
+            return fail(FEM_EINVAL, "bad mesh description");
+        const size_t np = nlocal(d.dim, d.order);
+        r->desc = d;
+        r->coords.resize((size_t)d.n_nodes * d.dim);
+        r->conn.resize((size_t)d.n_elems * np);
+        if (d.mem == FEM_MEM_DEVICE) {
+            cudaError_t e = cudaMemcpy(r->coords.data(), d.coords, sizeof(double) * r->coords.size(), cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && !r->conn.empty())
+                e = cudaMemcpy(r->conn.data(), d.conn, sizeof(int32_t) * r->conn.size(), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e, "copy mesh description");
+        } else {
+            std::memcpy(r->coords.data(), d.coords, sizeof(double) * r->coords.size());
+            if (!r->conn.empty()) std::memcpy(r->conn.data(), d.conn, sizeof(int32_t) * r->conn.size());
+        }
+        n = (size_t)d.n_nodes;
+        nnz_bound = std::min((size_t)d.n_elems * np * np, n * n);
+        if (prec == FEM_TF32X3 && d.dim == 3 && d.order == 3) prec = FEM_FP32;
+        r->est_bytes = mesh_estimate(d, prec);
+    } else {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->meshes.find(q->mesh_id);
+        if (it == S->meshes.end() || !it->second.mesh || it->second.evicted)
+            return fail(FEM_EINVAL, "unknown, evicted or not yet assembled mesh id");
+        n = (size_t)it->second.mesh->n;
+        nnz_bound = (size_t)it->second.mesh->nnz;
+        r->mesh_id = q->mesh_id;
+    }
+    int nout = 0;
+    for (int i = 0; i < 3; ++i) nout += (q->which >> i) & 1;
+    r->out_bytes = esz_of(prec) * std::max<size_t>(nnz_bound, 1) * nout;
+    r->est_bytes += r->out_bytes;
+    if (r->est_bytes > S->opts.budget_bytes)
+        return fail(FEM_EBUSY, "request needs " + std::to_string(r->est_bytes) + " device bytes, the budget is " +
+                                   std::to_string(S->opts.budget_bytes));
+    if (q->which & 6) r->u.assign(q->u, q->u + n);
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    r->done = ev;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->queue.size() >= (size_t)std::max(S->opts.max_queue, 1)) {
+        cudaEventDestroy(ev);
+        return fail(FEM_EBUSY, "queue full (" + std::to_string(S->queue.size()) + " pending requests)");
+    }
+    r->ticket = S->next_ticket++;
+    r->t_submit = now_us(S);
+    *ticket = r->ticket;
+    S->queue.push_back(r->ticket);
+    S->reqs[r->ticket] = std::move(r);
+    S->cv_work.notify_one();
+    return FEM_OK;
+}
+
+int fem_serve_poll(fem_server* S, uint64_t ticket, int timeout_us, fem_result* out) {
+    if (!S || !out) return fail(FEM_EINVAL, "NULL argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(FEM_EINVAL, "unknown ticket");
+    Request& r = *it->second;
+    if (r.state != DONE && timeout_us > 0) {
+        const auto deadline = Clock::now() + std::chrono::microseconds(timeout_us);
+        while (r.state != DONE)
+            if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) break;
+    }
+    if (r.state != DONE) {
+        if (timeout_us <= 0) return FEM_EAGAIN;
+        return fail(FEM_ETIMEOUT, "request not finished within the timeout");
+    }
+    std::memset(out, 0, sizeof(*out));
+    out->status = r.status;
+    out->mesh_id = r.mesh_id;
+    auto m = S->meshes.find(r.mesh_id);
+    if (r.status == FEM_OK && m != S->meshes.end() && m->second.mesh) {
+        const fem_mesh* mesh = m->second.mesh;
+        out->n = mesh->n;
+        out->nnz = mesh->nnz;
+        out->prec = mesh_prec(S->opts.prec, mesh);
+        out->d_row_ptr = mesh->row_ptr.as<int32_t>();
+        out->d_col_idx = mesh->col_idx.as<int32_t>();
+        out->d_vM = r.out[0].ptr;
+        out->d_vK = r.out[1].ptr;
+        out->d_vT = r.out[2].ptr;
+    }
+    out->t_submit_us = r.t_submit;
+    out->t_start_us = r.t_start;
+    out->t_done_us = r.t_done;
+    if (r.status != FEM_OK) set_error(r.msg);
+    return FEM_OK;
+}
+
+int fem_serve_release(fem_server* S, uint64_t ticket) {
+    if (!S) return fail(FEM_EINVAL, "NULL server");
+    std::unique_ptr<Request> r;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(ticket);
+        if (it == S->reqs.end()) return fail(FEM_EINVAL, "unknown ticket");
+        if (it->second->state != DONE) return fail(FEM_ESTATE, "request still pending or running");
+        r = std::move(it->second);
+        S->reqs.erase(it);
+        S->in_use -= std::min(S->in_use, r->out_bytes);
+    }
+    for (auto& b : r->out) buf_free(b, nullptr);
+    if (r->done) cudaEventDestroy(r->done);
+    S->cv_work.notify_one();
+    return FEM_OK;
+}
+
+int fem_serve_evict(fem_server* S, uint64_t mesh_id) {
+    if (!S) return fail(FEM_EINVAL, "NULL server");
+    Resident res;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->meshes.find(mesh_id);
+        if (it == S->meshes.end() || !it->second.mesh) return fail(FEM_EINVAL, "unknown or not yet assembled mesh id");
+        if (it->second.busy) return fail(FEM_ESTATE, "a request of this mesh is in flight");
+        res = it->second;
+        S->in_use -= std::min(S->in_use, res.bytes);
+        S->meshes.erase(it);
+    }
+    buf_free(res.u, nullptr);
+    fem_mesh_destroy(res.mesh);
+    S->cv_work.notify_one();
+    return FEM_OK;
+}
+
+int fem_serve_stats(fem_server* S, fem_serve_counters* out) {
+    if (!S || !out) return fail(FEM_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    out->pending = (int)S->queue.size();
+    out->inflight = S->inflight;
+    out->resident_meshes = (int)S->meshes.size();
+    out->bytes_in_use = S->in_use;
+    out->peak_bytes = S->peak;
+    return FEM_OK;
+}
+
+int fem_serve_destroy(fem_server* S) {
+    if (!S) return FEM_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->th.joinable()) S->th.join();
+    for (auto st : S->streams) cudaStreamSynchronize(st);
+    for (auto& kv : S->reqs) {
+        for (auto& b : kv.second->out) buf_free(b, nullptr);
+        if (kv.second->done) cudaEventDestroy(kv.second->done);
+    }
+    for (auto& kv : S->meshes) {
+        buf_free(kv.second.u, nullptr);
+        if (kv.second.mesh) fem_mesh_destroy(kv.second.mesh);
+    }
+    for (auto st : S->streams) cudaStreamDestroy(st);
+    delete S;
+    return FEM_OK;
+}
+
+}  // extern "C"
