@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-mesh batched measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-stream measurement")
+    ap.add_argument("--serve-requests", type=int, default=20000)
     return ap.parse_args()
 
 
@@ -185,6 +188,197 @@ def run_reference(args, rank, world):
             "e2e": {"value": val, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    i = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[i]
+
+
+def _per_mesh_prec(F, mesh):
+    # P3 tetrahedra have no tensor-core tile; they use the FP32 SIMT product
+    return F.FEM_FP32 if (mesh.d == 3 and mesh.p == 3) else F.FEM_TF32X3
+
+
+def measure_batched(F, torch, stream, wls, steps=50, warmup=5):
+    """64 meshes of uneven size and type (2D/3D, P1-P3, 1e3-2e5 elements,
+    log-uniform) reassembled (M, K, T) per launch: one CUDA graph of
+    persistent kernels, launch shapes tuned on the first launch; compared with
+    the same meshes reassembled one mesh at a time (2 launches per mesh)."""
+    from paper_2204_03893_gb300.torch_api import FemMesh
+    sh = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        fms = [FemMesh.of(w.mesh, stream=stream) for w in wls]
+        for fm in fms:
+            fm.symbolic()
+        torch.cuda.synchronize()
+        E_tot = sum(w.mesh.n_elems for w in wls)
+        us = [torch.tensor(w.u, dtype=torch.float64, device="cuda") for w in wls]
+        outs = [{kk: torch.empty(max(fm.nnz, 1), dtype=torch.float32, device="cuda") for kk in "MKT"} for fm in fms]
+        ks = [F.coeff(w.coeff.kind, w.coeff.params) for w in wls]
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b = F.fem_batch_create([fm.h for fm in fms], F.fem_batch_opts(F.FEM_TF32X3, 1, 1, 0), sh)
+        try:
+            def launch():
+                F.fem_batch_launch(b, ks, us, [o["M"] for o in outs], [o["K"] for o in outs],
+                                   [o["T"] for o in outs], sh)
+            for _ in range(warmup):
+                launch()
+            torch.cuda.synchronize()
+            F.fem_device_status(sh)
+            a.record(stream)
+            for _ in range(steps):
+                launch()
+            z.record(stream)
+            torch.cuda.synchronize()
+            F.fem_device_status(sh)
+            ms = a.elapsed_time(z) / steps
+            info = F.fem_batch_get_info(b)
+            # bit-identity with single-mesh calls on three meshes
+            same = True
+            for i in (0, len(wls) // 2, len(wls) - 1):
+                ref = {kk: torch.empty(max(fms[i].nnz, 1), dtype=torch.float32, device="cuda") for kk in "MKT"}
+                F.fem_assemble_all(fms[i].h, ks[i], us[i], _per_mesh_prec(F, wls[i].mesh), ref["M"], ref["K"],
+                                   ref["T"], sh)
+                torch.cuda.synchronize()
+                same = same and all(torch.equal(ref[kk], outs[i][kk]) for kk in "MKT")
+        finally:
+            F.fem_batch_destroy(b)
+
+        def per_mesh():
+            for i, fm in enumerate(fms):
+                p = _per_mesh_prec(F, wls[i].mesh)
+                F.fem_form_elements(fm.h, ks[i], us[i], p, 7, sh)
+                F.fem_sum_elements(fm.h, p, outs[i]["M"], outs[i]["K"], outs[i]["T"], sh)
+        for _ in range(2):
+            per_mesh()
+        torch.cuda.synchronize()
+        n_pm = max(3, steps // 5)
+        a.record(stream)
+        for _ in range(n_pm):
+            per_mesh()
+        z.record(stream)
+        torch.cuda.synchronize()
+        ms_pm = a.elapsed_time(z) / n_pm
+        for fm in fms:
+            fm.close()
+    types = {}
+    for w in wls:
+        key = f"{'tri' if w.mesh.d == 2 else 'tet'}_p{w.mesh.p}"
+        types[key] = types.get(key, 0) + 1
+    return {"workload": "64 meshes, 2D/3D P1-P3, 1e3-2e5 elements each (log-uniform, seed 4), k = 1 + a u + b u^2",
+            "meshes": len(wls), "elements": E_tot, "types": types, "value": E_tot / (ms / 1e3),
+            "unit": "elements/s", "ms_per_launch": ms, "steps": steps,
+            "per_mesh_launches": {"value": E_tot / (ms_pm / 1e3), "ms": ms_pm, "launches": 2 * len(wls)},
+            "kernels_per_launch": info.kernels_per_launch, "graph": bool(info.graph),
+            "tuned": {"sum_block": info.sum_block, "simt_grid": info.simt_grid, "ms": info.tuned_ms},
+            "tc_tiles": info.tc_tiles, "simt_blocks": info.simt_blocks,
+            "bitwise_equal_single_mesh_calls": bool(same),
+            "precision": "tf32x3 (P3 tetrahedra: fp32 SIMT)"}
+
+
+def measure_serve(F, torch, wls, n_requests=20000, rates=(1000.0, 3000.0, 10000.0, None), seed=11):
+    """Served stream: REASSEMBLE requests (M, K, T) with Poisson arrivals over
+    resident meshes (the 64 batched meshes plus two 3D P2 meshes of 998,250
+    elements that get 5 % of the requests), after every mesh was sent once as
+    an ASSEMBLE request; admission under a 120 GB device budget.  Latency is
+    submit -> completion seen by the server's scheduler."""
+    import queue
+    import threading
+    from paper_2204_03893_gb300.torch_api import FemMesh, FemServer
+    large = [mg.structured_tet(55, 2, 0.15, seed=900 + i) for i in range(2)]
+    meshes = [w.mesh for w in wls] + large
+    rng = np.random.default_rng(seed)
+    fields = [[mg.fourier_field(m.coords, 5000 + 3 * j + t) for t in range(2)] for j, m in enumerate(meshes)]
+    laws = [(w.coeff.kind, w.coeff.params) for w in wls] + [("sin", (2.0, 1.0, 3.0))] * len(large)
+    S = FemServer("tf32x3", budget_bytes=120 * 10**9, max_inflight=16, n_streams=8, max_queue=1 << 20)
+    out = {"workload": "REASSEMBLE of M, K, T over 66 resident meshes (64 batched + 2 tet P2 of 998,250 elements "
+                       "taking 5% of requests); Poisson arrivals", "budget_bytes": 120 * 10**9, "max_inflight": 16,
+           "n_streams": 8, "precision": "tf32x3 (P3 tetrahedra: fp32)"}
+    try:
+        t0 = time.perf_counter()
+        tick = [S.assemble(m, laws[j][0], laws[j][1], fields[j][0]) for j, m in enumerate(meshes)]
+        ids, lat = [], []
+        for t in tick:
+            r, _ = S.result(t, copy=False)
+            if r.status != 0:
+                raise RuntimeError(f"ASSEMBLE failed with status {r.status}")
+            ids.append(r.mesh_id)
+            lat.append((r.t_done_us - r.t_submit_us) / 1e3)
+        out["assemble"] = {"requests": len(meshes), "wall_s": time.perf_counter() - t0, "p50_ms": _pct(lat, 50),
+                           "p99_ms": _pct(lat, 99)}
+        E_of = [m.n_elems for m in meshes]
+        sweeps = []
+        for rate in rates:
+            n = n_requests if rate is None else min(n_requests, int(rate * 4))
+            big = rng.random(n) < 0.05
+            pick = np.where(big, rng.integers(len(wls), len(meshes), n), rng.integers(0, len(wls), n))
+            gaps = np.zeros(n) if rate is None else rng.exponential(1.0 / rate, n)
+            tq = queue.Queue()
+
+            def submitter():
+                t_next = time.perf_counter()
+                for i in range(n):
+                    t_next += gaps[i]
+                    while True:
+                        dt = t_next - time.perf_counter()
+                        if dt <= 0:
+                            break
+                        time.sleep(min(dt, 0.0005))
+                    j = int(pick[i])
+                    tq.put((j, S.reassemble(ids[j], laws[j][0], laws[j][1], fields[j][i % 2])))
+                tq.put(None)
+
+            th = threading.Thread(target=submitter)
+            w0 = time.perf_counter()
+            th.start()
+            lat, first, last, elems = [], None, None, 0
+            while True:
+                item = tq.get()
+                if item is None:
+                    break
+                j, t = item
+                r = F.fem_serve_poll(S.h, t, 120_000_000)
+                if r.status != 0:
+                    raise RuntimeError(f"REASSEMBLE failed with status {r.status}")
+                lat.append((r.t_done_us - r.t_submit_us) / 1e3)
+                first = r.t_submit_us if first is None else min(first, r.t_submit_us)
+                last = r.t_done_us if last is None else max(last, r.t_done_us)
+                elems += E_of[j]
+                F.fem_serve_release(S.h, t)
+            th.join()
+            span = (last - first) / 1e6
+            sweeps.append({"offered_req_per_s": rate if rate is not None else "all at once",
+                           "requests": n, "req_per_s": n / span, "elements_per_s": elems / span,
+                           "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "wall_s": time.perf_counter() - w0})
+        out["sweeps"] = sweeps
+        out["peak_bytes"] = int(S.stats().peak_bytes)
+        # accuracy of served results: bitwise against single-mesh calls, and
+        # relative Frobenius error against FP64 reassembly of the same request
+        worst, same = 0.0, True
+        for j in (0, len(wls) // 3, len(meshes) - 1):
+            m = meshes[j]
+            r, vals = S.result(S.reassemble(ids[j], laws[j][0], laws[j][1], fields[j][1]))
+            fm = FemMesh.of(m)
+            fm.symbolic()
+            u = torch.tensor(fields[j][1], dtype=torch.float64, device="cuda")
+            p = "fp32" if (m.d == 3 and m.p == 3) else "tf32x3"
+            ref = fm.assemble(u, laws[j][0], laws[j][1], p)
+            r64 = fm.assemble(u, laws[j][0], laws[j][1], "fp64")
+            torch.cuda.synchronize()
+            for kk in "MKT":
+                same = same and torch.equal(vals[kk], ref[kk])
+                err = torch.linalg.norm(vals[kk].double() - r64[kk]) / torch.linalg.norm(r64[kk])
+                worst = max(worst, float(err))
+            fm.close()
+        out["bitwise_equal_single_mesh_calls"] = bool(same)
+        out["max_rel_frobenius_err_vs_fp64"] = worst
+    finally:
+        S.close()
+    return out
 
 
 # ------------------------------------------------------------------ our arm
@@ -334,6 +528,13 @@ def run_ours(args, rank, world, local_rank):
     phases = {name: {"ms": d["ms"], "GB/s": d["bytes"] / (d["ms"] / 1e3) / 1e9,
                      "frac_hbm": d["bytes"] / (d["ms"] / 1e3) / 1e9 / peak} for name, d in kernels.items()}
 
+    # batched and served configurations (rank 0, after the timed region)
+    del fm, us, out
+    torch.cuda.empty_cache()
+    bwls = None if (args.no_batched and args.no_serve) else mg.batched_meshes(64, seed=4)
+    batched = None if args.no_batched else measure_batched(F, torch, stream, bwls)
+    served = None if args.no_serve else measure_serve(F, torch, bwls, n_requests=args.serve_requests)
+
     cpu = None if args.no_cpu_baseline else cpu_baseline_oracle()
     line = {
         "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
@@ -348,7 +549,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roofline, "phases": phases,
         "setup_once_per_mesh_ms": {"mesh_create_geometry": 1e3 * t_mesh, "symbolic_pattern": 1e3 * t_sym},
         "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64, "clocks": clk.summary(),
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 2 * args.steps, "batched": batched, "serve": served,
     }
     print(json.dumps(line), flush=True)
     if dist:

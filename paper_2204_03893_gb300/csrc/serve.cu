@@ -59,7 +59,10 @@ struct Request {
     int kind = 0, which = 7, status = FEM_OK;
     uint64_t mesh_id = 0;
     fem_coeff k;
-    std::vector<double> u;                 // host copy of the nodal values
+    std::vector<double> u;                 // host copy of the nodal values (pageable fallback)
+    double* u_pin = nullptr;               // ... or in a pinned block of the server's pool
+    size_t u_cls = 0, u_n = 0;
+    const double* u_data() const { return u_pin ? u_pin : u.data(); }
     // ASSEMBLE: host copies of the mesh description
     fem_mesh_desc desc;
     std::vector<double> coords;
@@ -72,6 +75,47 @@ struct Request {
     State state = PENDING;
     std::string msg;                       // error message of a failed request
     double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+// Pinned host blocks for the nodal values of queued requests, so that the
+// scheduler's upload is an asynchronous DMA and the host copy happens on the
+// submitting thread.  Blocks come in power-of-two size classes and are
+// reused; past `cap` bytes held, requests keep a pageable copy instead.
+struct PinnedPool {
+    std::mutex mu;
+    std::map<size_t, std::vector<void*>> free;
+    size_t held = 0, cap = size_t(1) << 30;
+    void* get(size_t bytes, size_t& cls) {
+        cls = 4096;
+        while (cls < bytes) cls <<= 1;
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = free.find(cls);
+        if (it != free.end() && !it->second.empty()) {
+            void* p = it->second.back();
+            it->second.pop_back();
+            return p;
+        }
+        if (held + cls > cap) return nullptr;
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, cls, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        held += cls;
+        return p;
+    }
+    void put(void* p, size_t cls) {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(mu);
+        free[cls].push_back(p);
+    }
+    void clear() {
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto& kv : free)
+            for (void* p : kv.second) cudaFreeHost(p);
+        free.clear();
+        held = 0;
+    }
 };
 
 }  // namespace
@@ -93,6 +137,7 @@ struct fem_server {
     int rr = 0, inflight = 0;
     size_t in_use = 0;                                           // accounted device bytes
     size_t peak = 0;
+    PinnedPool pinned;
 };
 
 namespace {
@@ -145,9 +190,9 @@ int start_request(fem_server* S, Request& r, Resident* res, fem_mesh** created, 
             if ((rc = buf_alloc(r.out[i], esz * (size_t)(m->nnz > 0 ? m->nnz : 1), st))) return rc;
     const double* du = nullptr;
     if (r.which & 6) {
-        if (r.u.size() != (size_t)m->n) return fail(FEM_EINVAL, "u has the wrong length for this mesh");
+        if (r.u_n != (size_t)m->n) return fail(FEM_EINVAL, "u has the wrong length for this mesh");
         if ((rc = buf_alloc(res->u, sizeof(double) * (size_t)m->n, st))) return rc;
-        cudaError_t e = cudaMemcpyAsync(res->u.ptr, r.u.data(), sizeof(double) * r.u.size(), cudaMemcpyHostToDevice, st);
+        cudaError_t e = cudaMemcpyAsync(res->u.ptr, r.u_data(), sizeof(double) * r.u_n, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "upload u");
         du = res->u.as<double>();
     }
@@ -158,7 +203,16 @@ int start_request(fem_server* S, Request& r, Resident* res, fem_mesh** created, 
     return FEM_OK;
 }
 
+// The request's inputs are no longer needed (its upload has completed or
+// never started): the pinned block goes back to the pool.
+void drop_inputs(fem_server* S, Request& r) {
+    if (r.u_pin) S->pinned.put(r.u_pin, r.u_cls);
+    r.u_pin = nullptr;
+    std::vector<double>().swap(r.u);
+}
+
 void finish(fem_server* S, Request& r, int status, const std::string& msg) {
+    drop_inputs(S, r);
     r.status = status;
     r.msg = msg;
     r.state = DONE;
@@ -236,8 +290,8 @@ bool admit_one(fem_server* S, std::unique_lock<std::mutex>& lk) {
             char buf[512];
             fem_last_error(buf, sizeof buf);
             msg = buf;
+            cudaStreamSynchronize(st);    // nothing of the failed request stays in flight
             if (created && r.kind == FEM_REQ_ASSEMBLE) {
-                cudaStreamSynchronize(st);
                 fem_mesh_destroy(created);
                 created = nullptr;
             }
@@ -307,6 +361,7 @@ int fem_serve_create(const fem_serve_opts* opts, fem_server** out) {
 
 int fem_serve_submit(fem_server* S, const fem_request* q, uint64_t* ticket) {
     if (!S || !q || !ticket) return fail(FEM_EINVAL, "NULL argument");
+    const double t_in = now_us(S);   // latency includes the copy of the inputs
     if (q->kind != FEM_REQ_ASSEMBLE && q->kind != FEM_REQ_REASSEMBLE) return fail(FEM_EINVAL, "unknown request kind");
     if (q->which <= 0 || q->which > 7) return fail(FEM_EINVAL, "which must be a nonzero mask of FEM_MAT_M|K|T");
     if (q->which & 6) {
@@ -361,18 +416,24 @@ int fem_serve_submit(fem_server* S, const fem_request* q, uint64_t* ticket) {
     if (r->est_bytes > S->opts.budget_bytes)
         return fail(FEM_EBUSY, "request needs " + std::to_string(r->est_bytes) + " device bytes, the budget is " +
                                    std::to_string(S->opts.budget_bytes));
-    if (q->which & 6) r->u.assign(q->u, q->u + n);
     cudaEvent_t ev;
     cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
     r->done = ev;
+    if (q->which & 6) {
+        r->u_n = n;
+        r->u_pin = static_cast<double*>(S->pinned.get(sizeof(double) * n, r->u_cls));
+        if (r->u_pin) std::memcpy(r->u_pin, q->u, sizeof(double) * n);
+        else r->u.assign(q->u, q->u + n);
+    }
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->queue.size() >= (size_t)std::max(S->opts.max_queue, 1)) {
         cudaEventDestroy(ev);
+        drop_inputs(S, *r);
         return fail(FEM_EBUSY, "queue full (" + std::to_string(S->queue.size()) + " pending requests)");
     }
     r->ticket = S->next_ticket++;
-    r->t_submit = now_us(S);
+    r->t_submit = t_in;
     *ticket = r->ticket;
     S->queue.push_back(r->ticket);
     S->reqs[r->ticket] = std::move(r);
@@ -476,7 +537,9 @@ int fem_serve_destroy(fem_server* S) {
     for (auto& kv : S->reqs) {
         for (auto& b : kv.second->out) buf_free(b, nullptr);
         if (kv.second->done) cudaEventDestroy(kv.second->done);
+        drop_inputs(S, *kv.second);
     }
+    S->pinned.clear();
     for (auto& kv : S->meshes) {
         buf_free(kv.second.u, nullptr);
         if (kv.second.mesh) fem_mesh_destroy(kv.second.mesh);

@@ -139,7 +139,7 @@ def test_serve_budget_admission_and_eviction():
         S.evict(r1.mesh_id)
         r2, vals = S.result(t2)
         assert r2.status == 0 and r2.mesh_id != r1.mesh_id
-        ref = single(m2, np.zeros(m2.n), "poly", (1.0,), "tf32x3")
+        ref = single(m2, np.zeros(m2.coords.shape[0]), "poly", (1.0,), "tf32x3")
         assert torch.equal(vals["M"], ref["M"])
         assert S.stats().peak_bytes <= int(one * 1.2)
     finally:
@@ -154,7 +154,7 @@ def test_serve_errors():
             F.fem_serve_submit(S.h, 7)
         assert ei.value.code == F.FEM_EINVAL
         with pytest.raises(F.FemError) as ei:
-            S.reassemble(12345, "poly", (1.0,), np.zeros(m.n))
+            S.reassemble(12345, "poly", (1.0,), np.zeros(m.coords.shape[0]))
         assert ei.value.code == F.FEM_EINVAL
         with pytest.raises(F.FemError) as ei:
             S.assemble(m, "poly", (1.0,), None, which="K")       # K without u
