@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "fp32", "fp64"])
     ap.add_argument("--scale", type=int, default=None, help="override grid size N (not a bench line)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=["tri_p1_64", "tri_p2_1024", "tet_p1_128", "tet_p2_64", "tet_p3_32"],
+                    help="single-mesh workload (anything but the default is not a bench line)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -199,8 +202,8 @@ def _pct(xs, q):
 
 
 def _per_mesh_prec(F, mesh):
-    # P3 tetrahedra have no tensor-core tile; they use the FP32 SIMT product
-    return F.FEM_FP32 if (mesh.d == 3 and mesh.p == 3) else F.FEM_TF32X3
+    # every element type has a tensor-core product (P3 tetrahedra: the chunked one)
+    return F.FEM_TF32X3
 
 
 def measure_batched(F, torch, stream, wls, steps=50, warmup=5):
@@ -263,6 +266,24 @@ def measure_batched(F, torch, stream, wls, steps=50, warmup=5):
         z.record(stream)
         torch.cuda.synchronize()
         ms_pm = a.elapsed_time(z) / n_pm
+        # one more pass with events around every mesh: time per element type
+        evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in fms]
+        for i, fm in enumerate(fms):
+            p = _per_mesh_prec(F, wls[i].mesh)
+            evm[i][0].record(stream)
+            F.fem_form_elements(fm.h, ks[i], us[i], p, 7, sh)
+            F.fem_sum_elements(fm.h, p, outs[i]["M"], outs[i]["K"], outs[i]["T"], sh)
+            evm[i][1].record(stream)
+        torch.cuda.synchronize()
+        by_type = {}
+        for i, w in enumerate(wls):
+            key = f"{'tri' if w.mesh.d == 2 else 'tet'}_p{w.mesh.p}"
+            d = by_type.setdefault(key, {"meshes": 0, "elements": 0, "ms": 0.0})
+            d["meshes"] += 1
+            d["elements"] += w.mesh.n_elems
+            d["ms"] += evm[i][0].elapsed_time(evm[i][1])
+        for d in by_type.values():
+            d["elements_per_s"] = d["elements"] / (d["ms"] / 1e3)
         for fm in fms:
             fm.close()
     types = {}
@@ -272,12 +293,13 @@ def measure_batched(F, torch, stream, wls, steps=50, warmup=5):
     return {"workload": "64 meshes, 2D/3D P1-P3, 1e3-2e5 elements each (log-uniform, seed 4), k = 1 + a u + b u^2",
             "meshes": len(wls), "elements": E_tot, "types": types, "value": E_tot / (ms / 1e3),
             "unit": "elements/s", "ms_per_launch": ms, "steps": steps,
-            "per_mesh_launches": {"value": E_tot / (ms_pm / 1e3), "ms": ms_pm, "launches": 2 * len(wls)},
+            "per_mesh_launches": {"value": E_tot / (ms_pm / 1e3), "ms": ms_pm, "launches": 2 * len(wls),
+                                  "by_type": by_type},
             "kernels_per_launch": info.kernels_per_launch, "graph": bool(info.graph),
             "tuned": {"sum_block": info.sum_block, "simt_grid": info.simt_grid, "ms": info.tuned_ms},
             "tc_tiles": info.tc_tiles, "simt_blocks": info.simt_blocks,
             "bitwise_equal_single_mesh_calls": bool(same),
-            "precision": "tf32x3 (P3 tetrahedra: fp32 SIMT)"}
+            "precision": "tf32x3 (P3 tetrahedra: chunked tensor-core product)"}
 
 
 def measure_serve(F, torch, wls, n_requests=20000, rates=(1000.0, 3000.0, 10000.0, None), seed=11):
@@ -297,7 +319,7 @@ def measure_serve(F, torch, wls, n_requests=20000, rates=(1000.0, 3000.0, 10000.
     S = FemServer("tf32x3", budget_bytes=120 * 10**9, max_inflight=16, n_streams=8, max_queue=1 << 20)
     out = {"workload": "REASSEMBLE of M, K, T over 66 resident meshes (64 batched + 2 tet P2 of 998,250 elements "
                        "taking 5% of requests); Poisson arrivals", "budget_bytes": 120 * 10**9, "max_inflight": 16,
-           "n_streams": 8, "precision": "tf32x3 (P3 tetrahedra: fp32)"}
+           "n_streams": 8, "precision": "tf32x3"}
     try:
         t0 = time.perf_counter()
         tick = [S.assemble(m, laws[j][0], laws[j][1], fields[j][0]) for j, m in enumerate(meshes)]
@@ -365,7 +387,7 @@ def measure_serve(F, torch, wls, n_requests=20000, rates=(1000.0, 3000.0, 10000.
             fm = FemMesh.of(m)
             fm.symbolic()
             u = torch.tensor(fields[j][1], dtype=torch.float64, device="cuda")
-            p = "fp32" if (m.d == 3 and m.p == 3) else "tf32x3"
+            p = "tf32x3"
             ref = fm.assemble(u, laws[j][0], laws[j][1], p)
             r64 = fm.assemble(u, laws[j][0], laws[j][1], "fp64")
             torch.cuda.synchronize()
@@ -397,7 +419,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
 
-    wl = mg.workload(WORKLOAD, scale=args.scale)
+    wl = mg.workload(args.workload, scale=args.scale)
     E = wl.mesh.n_elems
     prec = PRECISIONS[args.prec]
     dt = torch.float64 if args.prec == "fp64" else torch.float32
@@ -505,17 +527,19 @@ def run_ours(args, rank, world, local_rank):
         return 0
 
     # roofline of the dominant kernel (algorithmic bytes per launch / mean launch time)
-    n_p, nsym, nt = 6, 21, 36
+    n_p = wl.mesh.conn.shape[1]
+    nsym, nt, ngeo = n_p * (n_p + 1) // 2, n_p * n_p, 1 + wl.mesh.d * (wl.mesh.d + 1) // 2
     esz = 8 if args.prec == "fp64" else 4
     n = wl.mesh.n_nodes
-    bytes_form = E * (n_p * 4 + (1 + 3) * esz + (2 * nsym + nt) * esz) + n * 8
+    bytes_form = E * (n_p * 4 + ngeo * esz + (2 * nsym + nt) * esz) + n * 8
     bytes_sum = (nnz + 1) * 4 + E * n_p * n_p * 4 + E * (2 * nsym + nt) * esz + 3 * nnz * esz
     mf, ms = statistics.mean(form_ms), statistics.mean(sum_ms)
     kernels = {
-        "element_form": {"kernel": "element_tc_kernel" if args.prec == "tf32x3" else "element_simt_kernel",
+        "element_form": {"kernel": ("element_tc_chunked_kernel" if (wl.mesh.d, wl.mesh.p) == (3, 3) else
+                                    "element_tc_kernel") if args.prec == "tf32x3" else "element_simt_kernel",
                          "src": "element_tc.cu" if args.prec == "tf32x3" else "element_simt.cu",
                          "ms": mf, "bytes": bytes_form},
-        "csr_sum": {"kernel": "scatter_kernel", "src": "scatter.cu", "ms": ms, "bytes": bytes_sum},
+        "csr_sum": {"kernel": "scatter_segments_kernel", "src": "scatter.cu", "ms": ms, "bytes": bytes_sum},
     }
     dom = max(kernels.values(), key=lambda d: d["ms"])
     peak, peak_kind = measured_peaks()
@@ -540,8 +564,8 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.prec != "fp64" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.scale is None else f"{WORKLOAD}@N={args.scale}",
-                   "desc": WORKLOAD_DESC, "precision": args.prec,
+        "config": {"workload": args.workload if args.scale is None else f"{args.workload}@N={args.scale}",
+                   "desc": WORKLOAD_DESC if args.workload == WORKLOAD else wl.name, "precision": args.prec,
                    "element_product": "tcgen05 kind::tf32 x3 (Xhi Qhi + Xhi Qlo + Xlo Qhi), FP32 accumulate in TMEM"
                    if args.prec == "tf32x3" else args.prec,
                    "elements": E, "nnz": nnz, "l2": "inputs larger than L2 (per-step traffic > 2 GB; no explicit flush)",

@@ -208,12 +208,12 @@ int fem_device_status(void* stream);
  * element types is split into one mesh per type whose contributions are
  * merged, and the formation of all element matrices can run in parallel).
  * The element tiles of all meshes form one work list, grouped by element
- * type, walked by one persistent tensor-core kernel (FEM_TF32X3; P3
- * tetrahedra, whose tile does not fit the tensor-core layout, and FEM_FP64 /
+ * type, walked by one persistent tensor-core kernel (FEM_TF32X3; the tiles
+ * of P3 tetrahedra, whose Q does not fit in shared memory, by a second
+ * persistent kernel that streams Q in quadrature-point chunks; FEM_FP64 /
  * FEM_FP32 batches go through one batched SIMT kernel); one batched kernel
  * forms the CSR sums of all meshes.  Results are bit-identical to the same
- * meshes reassembled one by one with the same precision (FEM_FP32 for P3
- * tetrahedra in a FEM_TF32X3 batch). */
+ * meshes reassembled one by one with the same precision. */
 typedef struct {
     int prec;       /* FEM_TF32X3 (default if opts is NULL), FEM_FP32 or FEM_FP64 */
     int tune;       /* 1: on the first launch, time the CSR-sum block size and the SIMT grid
@@ -273,8 +273,7 @@ int fem_batch_destroy(fem_batch* b);
  * queue full, is refused at submit with FEM_EBUSY.  An ASSEMBLE request builds
  * the mesh and its pattern on the scheduler thread (it synchronises its
  * stream there), then reassembles it.  Results are the same values as
- * fem_assemble_all with the same precision (FEM_FP32 for P3 tetrahedra in a
- * FEM_TF32X3 server). */
+ * fem_assemble_all with the same precision. */
 enum { FEM_REQ_ASSEMBLE = 1, FEM_REQ_REASSEMBLE = 2 };
 typedef struct {
     int prec;             /* FEM_FP64, FEM_TF32X3 or FEM_FP32 for every request */

@@ -310,6 +310,8 @@ def workload(name: str, scale: int | None = None) -> Workload:
       u = Fourier field, k = 2 + sin(3u).  Seed 3.
     * ``tet_p2_64``: 64^3 cubes, 1 572 864 P2 tetrahedra, otherwise as
       tet_p1_128.  Seed 3.
+    * ``tet_p3_32``: 32^3 cubes, 196 608 P3 tetrahedra (20 dofs, 24-point
+      rule), otherwise as tet_p1_128.  Seed 3.
     """
     if name == "tri_p1_64":
         N = scale or 64
@@ -323,9 +325,9 @@ def workload(name: str, scale: int | None = None) -> Workload:
         m = structured_tri(N, 2, 0.2, seed=int(s_mesh.generate_state(1)[0]))
         u = fourier_field(m.coords, int(s_u.generate_state(1)[0]))
         return Workload(name, m, u, Coeff("poly", (1.0, 0.0, 1.0, 0.0, 0.0)))
-    if name in ("tet_p1_128", "tet_p2_64"):
-        p = 1 if name == "tet_p1_128" else 2
-        N = scale or (128 if p == 1 else 64)
+    if name in ("tet_p1_128", "tet_p2_64", "tet_p3_32"):
+        p = {"tet_p1_128": 1, "tet_p2_64": 2, "tet_p3_32": 3}[name]
+        N = scale or {1: 128, 2: 64, 3: 32}[p]
         s_mesh, s_u = np.random.SeedSequence(3).spawn(2)
         m = structured_tet(N, p, 0.15, seed=int(s_mesh.generate_state(1)[0]))
         u = fourier_field(m.coords, int(s_u.generate_state(1)[0]))

@@ -29,9 +29,18 @@ struct fem_batch {
     fem::BatchMesh* pinned[2] = {nullptr, nullptr};
     cudaEvent_t staged[2] = {nullptr, nullptr};
     int cur = 0;
-    fem::DevBuf d_tc, d_simt, d_split, d_scatter;
-    int n_tc = 0, n_simt = 0, n_split = 0, n_scatter = 0;
-    int tc_talloc = 0, tc_smem = 0, tc_grid = 0;
+    fem::DevBuf d_tc, d_tc5, d_simt, d_split, d_scatter;
+    int n_tc = 0, n_tc5 = 0, n_simt = 0, n_split = 0, n_scatter = 0;
+    int tc_grid = 0;
+    // tensor-core tiles are grouped by element type; each type gets its own
+    // launch (sized for that type's shared memory and TMEM) on its own branch
+    struct TypeRange {
+        int type, begin, count, talloc, smem;
+    };
+    std::vector<TypeRange> tc_ranges;
+    static constexpr int NBRANCH = 6;
+    cudaStream_t branch[NBRANCH] = {};
+    cudaEvent_t fork = nullptr, join[NBRANCH] = {};
     int simt_smem = 0, simt_grid = 0;
     int scatter_block = 256;
     double tuned_ms = 0.0;
@@ -55,23 +64,48 @@ int upload_items(DevBuf& buf, const std::vector<BatchItem>& items, cudaStream_t 
     return FEM_OK;
 }
 
-// the kernels of one reassembly, in order, on stream s
+// The kernels of one reassembly on stream s: the u split, then the element
+// products as parallel branches (one per tensor-core element type, plus the
+// SIMT walker), joined before the chunked P3-tetrahedron kernel (which holds
+// all TMEM columns of its SMs) and the CSR sum.
 int enqueue(fem_batch* b, cudaStream_t s) {
     int rc;
     const BatchMesh* tab = b->d_meshes.as<BatchMesh>();
-    if (b->prec != FEM_FP64 &&
-        (rc = batch_split_launch(b->d_split.as<BatchItem>(), b->n_split, tab, s)))
-        return rc;
     if (b->prec == FEM_FP64) {
         if ((rc = batch_simt_launch<double>(b->d_simt.as<BatchItem>(), b->n_simt, tab, b->simt_smem, b->simt_grid, s)))
             return rc;
         return batch_scatter_launch<double>(b->d_scatter.as<BatchItem>(), b->n_scatter, tab, b->scatter_block, s);
     }
-    if (b->n_tc &&
-        (rc = batch_tc_launch(b->d_tc.as<BatchItem>(), b->n_tc, tab, b->tc_talloc, b->tc_smem, b->tc_grid, s)))
-        return rc;
-    if ((rc = batch_simt_launch<float>(b->d_simt.as<BatchItem>(), b->n_simt, tab, b->simt_smem, b->simt_grid, s)))
-        return rc;
+    if ((rc = batch_split_launch(b->d_split.as<BatchItem>(), b->n_split, tab, s))) return rc;
+    int nb = 0;
+    FEM_CUDA_TRY(cudaEventRecord(b->fork, s));
+    auto next_branch = [&](cudaStream_t& out) -> int {
+        if (nb >= fem_batch::NBRANCH) {
+            out = s;
+            return FEM_OK;
+        }
+        out = b->branch[nb];
+        FEM_CUDA_TRY(cudaStreamWaitEvent(out, b->fork, 0));
+        ++nb;
+        return FEM_OK;
+    };
+    for (const auto& r : b->tc_ranges) {
+        cudaStream_t bs;
+        if ((rc = next_branch(bs))) return rc;
+        if ((rc = batch_tc_launch(b->d_tc.as<BatchItem>() + r.begin, r.count, tab, r.talloc, r.smem, b->tc_grid, bs)))
+            return rc;
+    }
+    if (b->n_simt) {
+        cudaStream_t bs;
+        if ((rc = next_branch(bs))) return rc;
+        if ((rc = batch_simt_launch<float>(b->d_simt.as<BatchItem>(), b->n_simt, tab, b->simt_smem, b->simt_grid, bs)))
+            return rc;
+    }
+    for (int k = 0; k < nb; ++k) {
+        FEM_CUDA_TRY(cudaEventRecord(b->join[k], b->branch[k]));
+        FEM_CUDA_TRY(cudaStreamWaitEvent(s, b->join[k], 0));
+    }
+    if (b->n_tc5 && (rc = batch_tc_chunked_launch(b->d_tc5.as<BatchItem>(), b->n_tc5, tab, s))) return rc;
     return batch_scatter_launch<float>(b->d_scatter.as<BatchItem>(), b->n_scatter, tab, b->scatter_block, s);
 }
 
@@ -182,7 +216,7 @@ int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts,
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
     const size_t esz = prec == FEM_FP64 ? 8 : 4;
-    std::vector<BatchItem> tc, simt, split;
+    std::vector<BatchItem> tc, tc5, simt, split;
     b->host.resize(n);
     for (int i = 0; i < n; ++i) {
         fem_mesh* m = meshes[i];
@@ -215,10 +249,11 @@ int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts,
         h.seg_ptr = m->seg_ptr.as<int>();
         h.contrib = m->contrib.as<int>();
         const bool on_tc = prec == FEM_TF32X3 && tc_type_supported(m->type);
-        if (on_tc) {
+        const bool on_tc5 = prec == FEM_TF32X3 && !on_tc && tc_chunked_supported(m->type);
+        if (on_tc5) {
+            for (int64_t f = 0; f < m->E; f += 128) tc5.push_back(BatchItem{i, m->type, f, 128, 0});
+        } else if (on_tc) {
             for (int64_t f = 0; f < m->E; f += 128) tc.push_back(BatchItem{i, m->type, f, 128, 0});
-            b->tc_smem = std::max(b->tc_smem, tc_type_smem(m->type));
-            b->tc_talloc = std::max(b->tc_talloc, tc_type_alloc(m->type));
         } else {
             for (int64_t f = 0; f < m->E; f += 64) simt.push_back(BatchItem{i, m->type, f, 64, 0});
             b->simt_smem = std::max(b->simt_smem, batch_simt_smem(m->type, prec == FEM_FP64));
@@ -226,15 +261,24 @@ int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts,
         if (prec != FEM_FP64)
             for (int64_t f = 0; f < m->n; f += 2048) split.push_back(BatchItem{i, m->type, f, 2048, 0});
     }
-    // tensor-core tiles grouped by element type, so each CTA reloads Q rarely
+    // tensor-core tiles grouped by element type: one launch per type
     std::stable_sort(tc.begin(), tc.end(), [](const BatchItem& a, const BatchItem& c) { return a.type < c.type; });
+    for (int i0 = 0; i0 < (int)tc.size();) {
+        int i1 = i0;
+        while (i1 < (int)tc.size() && tc[i1].type == tc[i0].type) ++i1;
+        const int t = tc[i0].type;
+        b->tc_ranges.push_back({t, i0, i1 - i0, tc_type_alloc(t), tc_type_smem(t)});
+        i0 = i1;
+    }
     b->n_tc = (int)tc.size();
+    b->n_tc5 = (int)tc5.size();
     b->n_simt = (int)simt.size();
     b->n_split = (int)split.size();
     b->tc_grid = nsm;
     b->simt_grid = nsm * 16;
     if (b->simt_smem == 0) b->simt_smem = 16;
-    if ((rc = upload_items(b->d_tc, tc, s)) || (rc = upload_items(b->d_simt, simt, s)) ||
+    if ((rc = upload_items(b->d_tc, tc, s)) || (rc = upload_items(b->d_tc5, tc5, s)) ||
+        (rc = upload_items(b->d_simt, simt, s)) ||
         (rc = upload_items(b->d_split, split, s)) || (rc = build_scatter_items(b, b->scatter_block, s)) ||
         (rc = buf_alloc(b->d_meshes, sizeof(BatchMesh) * n, s))) {
         fem_batch_destroy(b);
@@ -246,6 +290,11 @@ int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts,
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged[k], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    for (int k = 0; k < fem_batch::NBRANCH && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         fem_batch_destroy(b);
@@ -319,8 +368,9 @@ int fem_batch_get_info(const fem_batch* b, fem_batch_info* out) {
     if (!b || !out) return fail(FEM_EINVAL, "NULL argument");
     std::memset(out, 0, sizeof(*out));
     out->n_meshes = b->n;
-    out->kernels_per_launch = (b->prec != FEM_FP64 ? 1 : 0) + (b->n_tc ? 1 : 0) + (b->n_simt ? 1 : 0) + 1;
-    out->tc_tiles = b->n_tc;
+    out->kernels_per_launch = (b->prec != FEM_FP64 ? 1 : 0) + (int)b->tc_ranges.size() + (b->n_tc5 ? 1 : 0) +
+                              (b->n_simt ? 1 : 0) + 1;
+    out->tc_tiles = b->n_tc + b->n_tc5;
     out->simt_blocks = b->n_simt;
     out->sum_chunks = b->n_scatter;
     out->sum_block = b->scatter_block;
@@ -337,11 +387,16 @@ int fem_batch_destroy(fem_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (int k = 0; k < fem_batch::NBRANCH; ++k) {
+        if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     for (int k = 0; k < 2; ++k) {
         if (b->pinned[k]) cudaFreeHost(b->pinned[k]);
         if (b->staged[k]) cudaEventDestroy(b->staged[k]);
     }
-    DevBuf* bufs[] = {&b->d_meshes, &b->d_tc, &b->d_simt, &b->d_split, &b->d_scatter};
+    DevBuf* bufs[] = {&b->d_meshes, &b->d_tc, &b->d_tc5, &b->d_simt, &b->d_split, &b->d_scatter};
     for (auto* x : bufs) buf_free(*x, nullptr);
     cudaDeviceSynchronize();
     delete b;

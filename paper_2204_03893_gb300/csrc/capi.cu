@@ -4,6 +4,10 @@
 #include <mutex>
 #include <string>
 
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+
 #include "fem_internal.h"
 #include "refelem.h"
 
@@ -43,6 +47,30 @@ int buf_alloc(DevBuf& b, size_t bytes, cudaStream_t s) {
     if (!b.ptr) return fail(FEM_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
     b.bytes = bytes;
     return FEM_OK;
+}
+
+void trace_launch(const char* kernel, long long grid, int block, size_t smem, int ctas) {
+    static const bool on = std::getenv("FEM_TRACE_LAUNCH") != nullptr;
+    if (on)
+        std::fprintf(stderr, "[libfem] %s grid=%lld block=%d smem=%zu ctas_per_sm=%d\n", kernel, grid, block, smem,
+                     ctas);
+}
+
+int ctas_per_sm(const cudaFuncAttributes& fa, int threads, size_t smem, int dev) {
+    int per_sm_smem = 0, reserved = 0, regs = 0, max_threads = 0, max_blocks = 0;
+    cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&max_threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    cudaDeviceGetAttribute(&max_blocks, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+    const size_t per_block = smem + fa.sharedSizeBytes + (size_t)reserved;
+    int n = max_blocks > 0 ? max_blocks : 16;
+    if (per_block > 0) n = std::min<long long>(n, (long long)per_sm_smem / (long long)per_block);
+    const int warps = (threads + 31) / 32;
+    const int regs_per_warp = ((fa.numRegs > 0 ? fa.numRegs : 1) * 32 + 255) / 256 * 256;
+    if (regs > 0) n = std::min(n, regs / (regs_per_warp * warps));
+    if (max_threads > 0) n = std::min(n, max_threads / (warps * 32));
+    return n;
 }
 
 void buf_free(DevBuf& b, cudaStream_t s) {

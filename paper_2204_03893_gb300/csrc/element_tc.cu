@@ -18,6 +18,7 @@
 //
 // Every mbarrier wait is bounded (~1 s of SM clocks); on timeout the kernel
 // records an error word, stops, and releases its tensor memory.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -99,10 +100,11 @@ __device__ __forceinline__ void store_row(unsigned char* hi, unsigned char* lo, 
     }
 }
 
-// D[dcol..] = sum over K steps of (Xhi Qhi + Xhi Qlo + Xlo Qhi)
+// D[dcol..] (+)= sum over K steps of (Xhi Qhi + Xhi Qlo + Xlo Qhi); with
+// `acc` the first product also accumulates onto what D holds
 template <int Kp>
 __device__ __forceinline__ void issue_tf32x3(uint32_t tmem_d, uint32_t xh, uint32_t xl, uint32_t qh, uint32_t ql,
-                                             uint32_t idesc) {
+                                             uint32_t idesc, bool acc = false) {
     constexpr uint32_t sbo = (Kp / 4) * 128;
 #pragma unroll
     for (int ks = 0; ks < Kp / 8; ++ks) {
@@ -110,7 +112,7 @@ __device__ __forceinline__ void issue_tf32x3(uint32_t tmem_d, uint32_t xh, uint3
         uint64_t al = tc::smem_desc(xl + ks * 256, 128, sbo);
         uint64_t bh = tc::smem_desc(qh + ks * 256, 128, sbo);
         uint64_t bl = tc::smem_desc(ql + ks * 256, 128, sbo);
-        tc::mma_tf32(tmem_d, ah, bh, idesc, ks > 0 ? 1u : 0u);
+        tc::mma_tf32(tmem_d, ah, bh, idesc, (ks > 0 || acc) ? 1u : 0u);
         tc::mma_tf32(tmem_d, ah, bl, idesc, 1u);
         tc::mma_tf32(tmem_d, al, bh, idesc, 1u);
     }
@@ -458,6 +460,331 @@ __global__ void __launch_bounds__(TILE) batch_tc_kernel(const BatchItem* __restr
     if (warp == 0) tc::tmem_dealloc(tmem, talloc);
 }
 
+// ---------------------------------------------------------------------------
+// Chunked tensor-core product for element types whose Q does not fit in
+// shared memory (P3 tetrahedra: Q_M, Q_K and Q_T are 541 KB as TF32 hi/lo
+// parts, the X rows of a 128-element tile 245 KB).  The contraction index
+// K = (q, a<=b) (or (q), (q, a)) runs over quadrature points, so it is cut
+// into chunks of whole quadrature points: per chunk, the CTA forms the X
+// columns of those points in shared memory while one bulk copy brings the
+// matching rows of Q (a precomputed operand image in global memory, resident
+// in L2), then thread 0 issues the TF32x3 MMAs that accumulate into TMEM.
+// M and K accumulate side by side (224 + 224 columns), are drained, then T
+// (400 columns, issued as two MMAs of N = 208 and 192) reuses the columns.
+template <typename ETy>
+struct ChL {
+    static constexpr int NQ = ETy::NQ, NS = ETy::NS, D = ETy::D;
+    static constexpr int QCM = 8, QCK = 4, QCT = 8;                      // quadrature points per chunk
+    static constexpr int KcM = QCM, KcK = QCK * NS, KcT = QCT * D;       // chunk widths (multiples of 8)
+    static constexpr int NCM = NQ / QCM, NCK = NQ / QCK, NCT = NQ / QCT;
+    static constexpr int NSTEP = NCM + NCK + NCT;
+    static constexpr int NMp = ru(ETy::NSYM, 16), NTp = ru(ETy::NT, 16);
+    static constexpr int NTa = NTp > 256 ? ru(NTp / 2, 16) : NTp, NTb = NTp - NTa;
+    static constexpr int COLM = 0, COLK = NMp, COLT = 0;
+    static constexpr int ALLOC = 512;
+    static constexpr int KcMax = KcK > KcT ? (KcK > KcM ? KcK : KcM) : (KcT > KcM ? KcT : KcM);
+    static constexpr int XBYTES = TILE * KcMax * 8;                      // X chunk, hi + lo
+    static constexpr int QB_M = NMp * KcM * 8, QB_K = NMp * KcK * 8, QB_T = NTp * KcT * 8;
+    static constexpr int QBMAX = QB_T > QB_K ? (QB_T > QB_M ? QB_T : QB_M) : (QB_K > QB_M ? QB_K : QB_M);
+    static constexpr int IMG_BYTES = NCM * QB_M + NCK * QB_K + NCT * QB_T;
+    static constexpr int SMEM = XBYTES + QBMAX;
+    static constexpr bool OK = NQ % QCM == 0 && NQ % QCK == 0 && NQ % QCT == 0 && KcK % 8 == 0 && KcT % 8 == 0 &&
+                               NMp <= 256 && NTa <= 256 && NTb <= 256 && NTb % 16 == 0 && 2 * NMp <= ALLOC &&
+                               COLK + ru(ETy::NSYM, 32) <= ALLOC && COLT + ru(ETy::NT, 32) <= ALLOC &&
+                               XBYTES >= STAGE_FLOATS * 4 && SMEM <= SMEM_MAX;
+    // step s -> (matrix 0/1/2 = M/K/T, chunk index)
+    __host__ __device__ static constexpr int kind(int s) { return s < NCM ? 0 : s < NCM + NCK ? 1 : 2; }
+    __host__ __device__ static constexpr int chunk(int s) { return s < NCM ? s : s < NCM + NCK ? s - NCM : s - NCM - NCK; }
+    __host__ __device__ static constexpr int qbytes(int s) { return kind(s) == 0 ? QB_M : kind(s) == 1 ? QB_K : QB_T; }
+    __host__ __device__ static constexpr int img_off(int s) {
+        return s <= NCM ? s * QB_M : s <= NCM + NCK ? NCM * QB_M + (s - NCM) * QB_K
+                                                    : NCM * QB_M + NCK * QB_K + (s - NCM - NCK) * QB_T;
+    }
+};
+
+constexpr int CHUNK_IMG_BYTES = ChL<ET<3, 3>>::IMG_BYTES;
+__device__ __align__(128) unsigned char g_tcbig[CHUNK_IMG_BYTES];
+
+// X columns of quadrature points q0 .. q0+QC-1 for one matrix (the same
+// quantities as form_x, restricted to a chunk).
+template <typename ETy, int QC>
+__device__ __forceinline__ void form_chunk_m(int q0, float b, float mass, float (&x)[QC]) {
+    constexpr int TO = type_tab_off(ETy::TYPE);
+    constexpr int WQ = TO + ETy::NQ * ETy::NP * (1 + ETy::D);
+#pragma unroll
+    for (int j = 0; j < QC; ++j) x[j] = mass * (c_tcref[WQ + q0 + j] * b);
+}
+
+template <typename ETy, int QC>
+__device__ __forceinline__ void form_chunk_k(int q0, const float (&du)[ETy::NP], float u0, float b,
+                                             const float (&A)[ETy::NS], const CoeffDev& k,
+                                             float (&x)[QC * ETy::NS]) {
+    constexpr int NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS, D = ETy::D;
+    constexpr int TO = type_tab_off(ETy::TYPE);
+    constexpr int PHI = TO, WQ = TO + NQ * NP * (1 + D);
+#pragma unroll
+    for (int j = 0; j < QC; ++j) {
+        const int q = q0 + j;
+        float uq = 0.f;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) uq = fmaf(c_tcref[PHI + q * NP + i], du[i], uq);
+        uq += u0;
+        float dk;
+        const float kq = k_eval<float>(k, uq, dk);
+        const float lk = (c_tcref[WQ + q] * b) * kq;
+#pragma unroll
+        for (int t = 0; t < NS; ++t) x[j * NS + t] = lk * A[t];
+    }
+}
+
+template <typename ETy, int QC>
+__device__ __forceinline__ void form_chunk_t(int q0, const float (&du)[ETy::NP], float u0, float b,
+                                             const float (&A)[ETy::NS], const CoeffDev& k,
+                                             float (&x)[QC * ETy::D]) {
+    constexpr int NP = ETy::NP, NQ = ETy::NQ, D = ETy::D;
+    constexpr int TO = type_tab_off(ETy::TYPE);
+    constexpr int PHI = TO, GR = TO + NQ * NP, WQ = TO + NQ * NP * (1 + D);
+#pragma unroll
+    for (int j = 0; j < QC; ++j) {
+        const int q = q0 + j;
+        float uq = 0.f, g[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) g[a] = 0.f;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            uq = fmaf(c_tcref[PHI + q * NP + i], du[i], uq);
+#pragma unroll
+            for (int a = 0; a < D; ++a) g[a] = fmaf(c_tcref[GR + (q * NP + i) * D + a], du[i], g[a]);
+        }
+        uq += u0;
+        float dk;
+        k_eval<float>(k, uq, dk);
+        const float ld = (c_tcref[WQ + q] * b) * dk;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            float sacc = 0.f;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const int lo = a < c ? a : c, hi = a < c ? c : a;
+                sacc = fmaf(A[lo * D - (lo * (lo - 1)) / 2 + (hi - lo)], g[c], sacc);
+            }
+            x[j * D + a] = ld * sacc;
+        }
+    }
+}
+
+// One 128-element tile of the chunked product (all 128 threads; uniform
+// control).  Returns false if a bounded wait gave up; *pend_q / *pend_mma
+// then tell which barrier still has an operation in flight.
+template <typename ETy>
+__device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const float* __restrict__ geo, int64_t E,
+                                             const float2* __restrict__ u, const CoeffDev& k, float mass,
+                                             float* __restrict__ VM, float* __restrict__ VK, float* __restrict__ VT,
+                                             const unsigned char* __restrict__ img, int64_t first,
+                                             unsigned char* smem, uint32_t tmem, uint32_t mb_mma, uint32_t mb_q,
+                                             uint32_t& ph_mma, uint32_t& ph_q, bool& pend_q, bool& pend_mma) {
+    using L = ChL<ETy>;
+    constexpr int NP = ETy::NP, NS = ETy::NS;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool doM = VM != nullptr, doK = VK != nullptr, doT = VT != nullptr;
+    const bool need_u = doK | doT;
+    const int64_t e = first + tid;
+    // element data for the whole tile: u differences (hi/lo split, as in
+    // form_x) and the geometry
+    float du[NP], A[NS];
+    float u0 = 0.f, b = 0.f;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) du[i] = 0.f;
+#pragma unroll
+    for (int t = 0; t < NS; ++t) A[t] = 0.f;
+    if (e < E) {
+        b = __ldg(geo + e);
+#pragma unroll
+        for (int t = 0; t < NS; ++t) A[t] = __ldg(geo + (int64_t)(1 + t) * E + e);
+        if (need_u) {
+            const int* ce = conn + e * NP;
+            const float2 p0 = __ldg(u + __ldg(ce));
+            u0 = p0.x + p0.y;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const float2 pi = __ldg(u + __ldg(ce + i));
+                du[i] = (pi.x - p0.x) + (pi.y - p0.y);
+            }
+        }
+    }
+    unsigned char* sX = smem;
+    unsigned char* sQ = smem + L::XBYTES;
+    const uint32_t sXu = tc::smem_u32(sX), sQu = tc::smem_u32(sQ);
+    const int64_t row0 = first + warp * 32;
+    float* stage = reinterpret_cast<float*>(smem) + warp * 32 * 33;
+#pragma unroll 1
+    for (int s = 0; s < L::NSTEP; ++s) {
+        const int kd = L::kind(s), c = L::chunk(s);
+        const bool active = kd == 0 ? doM : kd == 1 ? doK : doT;
+        if (active) {
+            const int qb = L::qbytes(s);
+            if (tid == 0) {
+                tc::mbar_arrive_expect_tx(mb_q, (uint32_t)qb);
+                for (int o = 0; o < qb; o += 32768) {
+                    const int n = qb - o < 32768 ? qb - o : 32768;
+                    tc::bulk_g2s(sQu + o, img + L::img_off(s) + o, (uint32_t)n, mb_q);
+                }
+            }
+            pend_q = true;
+            if (kd == 0) {
+                float x[L::KcM];
+                form_chunk_m<ETy, L::QCM>(c * L::QCM, b, mass, x);
+                store_row<L::KcM>(sX, sX + TILE * L::KcM * 4, x, tid);
+            } else if (kd == 1) {
+                float x[L::KcK];
+                form_chunk_k<ETy, L::QCK>(c * L::QCK, du, u0, b, A, k, x);
+                store_row<L::KcK>(sX, sX + TILE * L::KcK * 4, x, tid);
+            } else {
+                float x[L::KcT];
+                form_chunk_t<ETy, L::QCT>(c * L::QCT, du, u0, b, A, k, x);
+                store_row<L::KcT>(sX, sX + TILE * L::KcT * 4, x, tid);
+            }
+            tc::fence_proxy_async_smem();
+            const uint32_t okq = tc::mbar_wait_bounded(mb_q, ph_q, WAIT_LIMIT);
+            tc::fence_before_sync();
+            if (__syncthreads_or(!okq)) return false;
+            ph_q ^= 1u;
+            pend_q = false;
+            if (tid == 0) {
+                tc::fence_after_sync();
+                if (kd == 0) {
+                    constexpr int Kc = L::KcM;
+                    issue_tf32x3<Kc>(tmem + L::COLM, sXu, sXu + TILE * Kc * 4, sQu, sQu + L::NMp * Kc * 4,
+                                     tc::idesc_tf32(L::NMp), c > 0);
+                } else if (kd == 1) {
+                    constexpr int Kc = L::KcK;
+                    issue_tf32x3<Kc>(tmem + L::COLK, sXu, sXu + TILE * Kc * 4, sQu, sQu + L::NMp * Kc * 4,
+                                     tc::idesc_tf32(L::NMp), c > 0);
+                } else {
+                    constexpr int Kc = L::KcT;
+                    constexpr uint32_t half = (L::NTa / 8) * ((Kc / 4) * 128);   // N-offset of the second MMA
+                    issue_tf32x3<Kc>(tmem + L::COLT, sXu, sXu + TILE * Kc * 4, sQu, sQu + L::NTp * Kc * 4,
+                                     tc::idesc_tf32(L::NTa), c > 0);
+                    if constexpr (L::NTb > 0)
+                        issue_tf32x3<Kc>(tmem + L::COLT + L::NTa, sXu, sXu + TILE * Kc * 4, sQu + half,
+                                         sQu + L::NTp * Kc * 4 + half, tc::idesc_tf32(L::NTb), c > 0);
+                }
+                tc::mma_commit(mb_mma);
+            }
+            pend_mma = true;
+            const uint32_t okm = tc::mbar_wait_bounded(mb_mma, ph_mma, WAIT_LIMIT);
+            if (__syncthreads_or(!okm)) return false;
+            ph_mma ^= 1u;
+            pend_mma = false;
+            tc::fence_after_sync();
+        }
+        // drain the accumulators once their last chunk is in (the stage
+        // area aliases the X chunk, which the completed MMAs no longer read)
+        if (s == L::NCM + L::NCK - 1) {
+            if (doM) epilogue<ETy::NSYM>(tmem, L::COLM, stage, VM, row0, E, warp, lane);
+            if (doK) epilogue<ETy::NSYM>(tmem, L::COLK, stage, VK, row0, E, warp, lane);
+            tc::fence_before_sync();
+            __syncthreads();
+        } else if (s == L::NSTEP - 1) {
+            if (doT) epilogue<ETy::NT>(tmem, L::COLT, stage, VT, row0, E, warp, lane);
+            tc::fence_before_sync();
+            __syncthreads();
+        }
+    }
+    return true;
+}
+
+template <typename ETy>
+__global__ void __launch_bounds__(TILE, 1) element_tc_chunked_kernel(
+    const int* __restrict__ conn, const float* __restrict__ geo, int64_t E, const float2* __restrict__ u,
+    CoeffDev k, float mass, float* __restrict__ VM, float* __restrict__ VK, float* __restrict__ VT,
+    const unsigned char* __restrict__ img, int* __restrict__ err) {
+    using L = ChL<ETy>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_mma, bar_q;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mb_mma = tc::smem_u32(&bar_mma), mb_q = tc::smem_u32(&bar_q);
+    if (tid == 0) {
+        tc::mbar_init(mb_mma, 1);
+        tc::mbar_init(mb_q, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(&tmem_slot), L::ALLOC);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    uint32_t ph_mma = 0, ph_q = 0;
+    bool pend_q = false, pend_mma = false, ok = true;
+    const int64_t ntiles = (E + TILE - 1) / TILE;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+        ok = chunked_tile<ETy>(conn, geo, E, u, k, mass, VM, VK, VT, img, tile * TILE, smem, tmem, mb_mma, mb_q,
+                               ph_mma, ph_q, pend_q, pend_mma);
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+        // give the copy or the MMAs still in flight one more bounded chance to finish
+        if (pend_q) tc::mbar_wait_bounded(mb_q, ph_q, WAIT_LIMIT);
+        if (pend_mma) tc::mbar_wait_bounded(mb_mma, ph_mma, WAIT_LIMIT);
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, L::ALLOC);
+}
+
+// Batched chunked product: a persistent walk over the 128-element tiles of
+// every P3-tetrahedron mesh of a batch (the same tile code as the
+// single-mesh kernel, so the bits are the same).
+__global__ void __launch_bounds__(TILE, 1) batch_tc_chunked_kernel(const BatchItem* __restrict__ items, int nitems,
+                                                                   const BatchMesh* __restrict__ meshes,
+                                                                   const unsigned char* __restrict__ img,
+                                                                   int* __restrict__ err) {
+    using ETy = ET<3, 3>;
+    using L = ChL<ETy>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_mma, bar_q;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mb_mma = tc::smem_u32(&bar_mma), mb_q = tc::smem_u32(&bar_q);
+    if (tid == 0) {
+        tc::mbar_init(mb_mma, 1);
+        tc::mbar_init(mb_q, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(&tmem_slot), L::ALLOC);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    uint32_t ph_mma = 0, ph_q = 0;
+    bool pend_q = false, pend_mma = false, ok = true;
+    for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+        const BatchItem w = items[it];
+        const BatchMesh& bm = meshes[w.mesh];
+        if (w.type != ETy::TYPE) continue;
+        float* VM = bm.vM ? static_cast<float*>(bm.VM) : nullptr;
+        float* VK = bm.vK ? static_cast<float*>(bm.VK) : nullptr;
+        float* VT = bm.vT ? static_cast<float*>(bm.VT) : nullptr;
+        if (!(VM || VK || VT)) continue;   // mesh skipped in this launch
+        ok = chunked_tile<ETy>(bm.conn, bm.geo32, bm.E, bm.u2, bm.k, (float)bm.mass, VM, VK, VT, img, w.first, smem,
+                               tmem, mb_mma, mb_q, ph_mma, ph_q, pend_q, pend_mma);
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+        if (pend_q) tc::mbar_wait_bounded(mb_q, ph_q, WAIT_LIMIT);
+        if (pend_mma) tc::mbar_wait_bounded(mb_mma, ph_mma, WAIT_LIMIT);
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, L::ALLOC);
+}
+
 // host-side TF32 rounding, nearest with ties away from zero (matches cvt.rna)
 float tf32_rna_host(float x) {
     uint32_t b;
@@ -472,7 +799,7 @@ float tf32_rna_host(float x) {
 }
 
 // Q (K x N, FP64, row-major) -> B operand image (N x Kp, K-major core matrices), hi and lo
-void put_operand(std::vector<float>& img, int off_hi, int off_lo, const std::vector<double>& Q, int K, int N, int Kp) {
+void put_operand(std::vector<float>& img, int off_hi, int off_lo, const double* Q, int K, int N, int Kp) {
     const int sbo = (Kp / 4) * 128;
     for (int n = 0; n < N; ++n)
         for (int kk = 0; kk < K; ++kk) {
@@ -490,22 +817,80 @@ void build_image(std::vector<float>& all, const RefElem& R) {
     using L = TcL<ETy>;
     std::vector<float> img(IMG_SLOT_FLOATS, 0.f);
     if constexpr (L::FITS) {
-        put_operand(img, L::QMh, L::QMl, R.QM, ETy::KM, ETy::NSYM, L::KMp);
-        put_operand(img, L::QKh, L::QKl, R.QK, ETy::KK, ETy::NSYM, L::KKp);
-        put_operand(img, L::QTh, L::QTl, R.QT, ETy::KT, ETy::NT, L::KTp);
+        put_operand(img, L::QMh, L::QMl, R.QM.data(), ETy::KM, ETy::NSYM, L::KMp);
+        put_operand(img, L::QKh, L::QKl, R.QK.data(), ETy::KK, ETy::NSYM, L::KKp);
+        put_operand(img, L::QTh, L::QTl, R.QT.data(), ETy::KT, ETy::NT, L::KTp);
     }
     std::copy(img.begin(), img.end(), all.begin() + (size_t)ETy::TYPE * IMG_SLOT_FLOATS);
+}
+
+// Operand images of the Q chunks of the chunked product, step after step:
+// rows k0 .. k0+Kc of Q (K x N, row-major) as an N x Kc K-major operand,
+// hi part then lo part, N padded with zero rows.
+template <typename ETy>
+void build_chunk_image(std::vector<float>& img, const RefElem& R) {
+    using L = ChL<ETy>;
+    img.assign(L::IMG_BYTES / 4, 0.f);
+    for (int st = 0; st < L::NSTEP; ++st) {
+        const int kd = L::kind(st), c = L::chunk(st);
+        const int Kc = kd == 0 ? L::KcM : kd == 1 ? L::KcK : L::KcT;
+        const int N = kd == 2 ? ETy::NT : ETy::NSYM, Np = kd == 2 ? L::NTp : L::NMp;
+        const std::vector<double>& Q = kd == 0 ? R.QM : kd == 1 ? R.QK : R.QT;
+        const int off = L::img_off(st);
+        put_operand(img, off, off + Np * Kc * 4, Q.data() + (size_t)c * Kc * N, Kc, N, Kc);
+    }
 }
 
 std::mutex g_mu;
 bool g_done[64] = {};
 
 template <typename ETy>
+int launch_tc_chunked(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
+                      cudaStream_t s) {
+    using L = ChL<ETy>;
+    if (m.E == 0) return FEM_OK;
+    auto kern = element_tc_chunked_kernel<ETy>;
+    int dev = 0, nsm = 0, optin = 0, per_sm = 0, occ = 0;
+    FEM_CUDA_TRY(cudaGetDevice(&dev));
+    FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    FEM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    FEM_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    cudaFuncAttributes fa;
+    FEM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;
+    // one CTA per SM (it holds all 512 TMEM columns): ask for more than half
+    // of the SM's shared memory
+    const int smem = std::min(dyn_max, std::max(L::SMEM, per_sm / 2 + 1));
+    if (smem < L::SMEM) return fail(FEM_EINVAL, "chunked tensor-core tile does not fit in shared memory");
+    FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+    if (occ > 1) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
+    const int64_t ntiles = (m.E + TILE - 1) / TILE;
+    int64_t grid = nsm;
+    if (grid > ntiles) grid = ntiles;
+    unsigned char* img = nullptr;
+    int* err = nullptr;
+    FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&img, g_tcbig));
+    FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&err, g_tc_err));
+    trace_launch("element_tc_chunked_kernel", grid, TILE, smem, 1);
+    cudaGetLastError();   // clear any stale error before the launch check
+    kern<<<(unsigned)grid, TILE, smem, s>>>(m.conn.as<int>(), m.geo32.as<float>(), m.E, u, k, (float)m.m, VM, VK, VT,
+                                            img, err);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+template <typename ETy>
 int launch_tc(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
               cudaStream_t s) {
     using L = TcL<ETy>;
     if constexpr (!L::FITS) {
-        return fail(FEM_EINVAL, "FEM_TF32X3 is not available for this element type (tile does not fit)");
+        if constexpr (ChL<ETy>::OK && ChL<ETy>::IMG_BYTES == CHUNK_IMG_BYTES)
+            return launch_tc_chunked<ETy>(m, k, u, VM, VK, VT, s);
+        else
+            return fail(FEM_EINVAL, "FEM_TF32X3 is not available for this element type (tile does not fit)");
     } else {
         if (m.E == 0) return FEM_OK;
         auto kern = element_tc_kernel<ETy>;
@@ -519,6 +904,11 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, 
         int smem = L::SMEM;
         if (smem > dyn_max) return fail(FEM_EINVAL, "tensor-core tile does not fit in shared memory");
         FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        // the whole unified L1/shared array as shared memory, so that several
+        // CTAs (each with its own TMEM columns) overlap their load, MMA and
+        // epilogue phases on one SM
+        FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared));
         FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
         const int occ_max = 512 / L::ALLOC;   // co-resident CTAs must fit their TMEM columns
         if (occ > occ_max) {
@@ -532,9 +922,14 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, 
             if (occ > occ_max) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
         }
         if (occ < 1) return fail(FEM_ECUDA, "tensor-core kernel does not fit on an SM");
+        // the occupancy query can under-report with the carveout preference;
+        // the register / shared-memory budget (bounded by TMEM) decides, and
+        // a persistent grid larger than what is co-resident stays correct
+        occ = std::max(occ, std::min(occ_max, ctas_per_sm(fa, TILE, smem, dev)));
         int64_t ntiles = (m.E + TILE - 1) / TILE;
         int64_t grid = (int64_t)nsm * occ;
         if (grid > ntiles) grid = ntiles;
+        trace_launch("element_tc_kernel", grid, TILE, smem, occ);
         float* img = nullptr;
         FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&img, g_tcimg));
         int* err = nullptr;
@@ -573,6 +968,13 @@ int tables_init_tc() {
     }
     FEM_CUDA_TRY(cudaMemcpyToSymbol(c_tcref, ref.data(), sizeof(float) * TAB_TOTAL));
     FEM_CUDA_TRY(cudaMemcpyToSymbol(g_tcimg, img.data(), sizeof(float) * img.size()));
+    {
+        std::vector<float> big;
+        const RefElem* R5 = refelem_for_type(5);
+        if (!R5) return fail(FEM_EINVAL, "reference element tables failed");
+        build_chunk_image<ET<3, 3>>(big, *R5);
+        FEM_CUDA_TRY(cudaMemcpyToSymbol(g_tcbig, big.data(), sizeof(float) * big.size()));
+    }
     int zero = 0;
     FEM_CUDA_TRY(cudaMemcpyToSymbol(g_tc_err, &zero, sizeof(int)));
     if (dev < 64) g_done[dev] = true;
@@ -625,18 +1027,68 @@ int batch_tc_launch(const BatchItem* items, int nitems, const BatchMesh* meshes,
     FEM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
     if (smem > optin - (int)fa.sharedSizeBytes) return fail(FEM_EINVAL, "batched tile does not fit in shared memory");
     FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
     FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
     if (occ < 1) return fail(FEM_ECUDA, "batched tensor-core kernel does not fit on an SM");
+    // co-resident CTAs must fit their TMEM columns: ask for enough shared
+    // memory that at most 512 / talloc CTAs fit on an SM
+    const int occ_max = 512 / talloc;
+    if (occ > occ_max) {
+        int per_sm = 0;
+        FEM_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        smem = std::min(per_sm / (occ_max + 1) + 1, optin - (int)fa.sharedSizeBytes);
+        FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+        if (occ > occ_max) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
+    }
+    occ = std::max(occ, std::min(occ_max, ctas_per_sm(fa, TILE, smem, dev)));
+    grid *= occ;
     float* img = nullptr;
     int* err = nullptr;
     FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&img, g_tcimg));
     FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&err, g_tc_err));
     if (grid > nitems) grid = nitems;
+    trace_launch("batch_tc_kernel", grid, TILE, smem, occ);
     cudaGetLastError();   // clear any stale error before the launch check
     kern<<<grid, TILE, smem, s>>>(items, nitems, meshes, img, (uint32_t)talloc, err);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
+
+int batch_tc_chunked_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, cudaStream_t s) {
+    if (nitems <= 0) return FEM_OK;
+    int rc = tables_init_tc();
+    if (rc) return rc;
+    using L = ChL<ET<3, 3>>;
+    auto kern = batch_tc_chunked_kernel;
+    int dev = 0, nsm = 0, optin = 0, per_sm = 0, occ = 0;
+    FEM_CUDA_TRY(cudaGetDevice(&dev));
+    FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    FEM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    FEM_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    cudaFuncAttributes fa;
+    FEM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+    const int smem = std::min(optin - (int)fa.sharedSizeBytes, std::max(L::SMEM, per_sm / 2 + 1));
+    if (smem < L::SMEM) return fail(FEM_EINVAL, "chunked tensor-core tile does not fit in shared memory");
+    FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+    if (occ > 1) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
+    const int grid = nitems < nsm ? nitems : nsm;
+    unsigned char* img = nullptr;
+    int* err = nullptr;
+    FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&img, g_tcbig));
+    FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&err, g_tc_err));
+    trace_launch("batch_tc_chunked_kernel", grid, TILE, smem, 1);
+    cudaGetLastError();   // clear any stale error before the launch check
+    kern<<<grid, TILE, smem, s>>>(items, nitems, meshes, img, err);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+int tc_chunked_supported(int type) { return type == 5 && ChL<ET<3, 3>>::OK; }
 
 int tc_error_flag(int clear) {
     int v = 0;

@@ -32,6 +32,15 @@ struct DevBuf {
     T* as() const { return static_cast<T*>(ptr); }
 };
 int buf_alloc(DevBuf& b, size_t bytes, cudaStream_t s);   // FEM_OK / FEM_ENOMEM
+
+// Launch tracing: with FEM_TRACE_LAUNCH set in the environment, every
+// persistent kernel launch prints its shape to stderr.
+void trace_launch(const char* kernel, long long grid, int block, size_t smem, int ctas_per_sm);
+
+// CTAs of `fa` that fit on one SM with `smem` dynamic shared memory (the full
+// unified array as shared memory), from the register and shared-memory
+// budgets; persistent kernels size their grids with it.
+int ctas_per_sm(const cudaFuncAttributes& fa, int threads, size_t smem, int dev);
 void buf_free(DevBuf& b, cudaStream_t s);
 
 }  // namespace fem
@@ -118,6 +127,9 @@ int tc_type_smem(int type);             // dynamic shared memory of its tile
 int tc_type_alloc(int type);            // TMEM columns of its tile (power of two)
 int batch_tc_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int talloc, int smem, int grid,
                     cudaStream_t s);
+// P3 tetrahedra: tensor-core product with Q streamed in quadrature-point chunks
+int tc_chunked_supported(int type);
+int batch_tc_chunked_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, cudaStream_t s);
 template <typename T>
 int batch_simt_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int max_type_smem, int grid,
                       cudaStream_t s);

@@ -103,65 +103,145 @@ __global__ void __launch_bounds__(256) scatter_rows_kernel(const int* __restrict
     }
 }
 
+// V entries of one element entry c = (e n_p + i) n_p + j: T from the full
+// storage (its index is c itself), M and K from the symmetric storage at
+// e n_p(n_p+1)/2 + sym[i n_p + j], with the local symmetric index from a
+// small shared-memory table.
+template <int NP, typename T>
+struct Contribution {
+    T m, k, t;
+    __device__ __forceinline__ void load(int c, const short* __restrict__ sym, const T* __restrict__ VM,
+                                         const T* __restrict__ VK, const T* __restrict__ VT) {
+        constexpr int NT = NP * NP, NSYM = NP * (NP + 1) / 2;
+        t = VT ? __ldg(VT + c) : T(0);
+        if (VM || VK) {
+            const int e = c / NT;
+            const int64_t off = (int64_t)e * NSYM + sym[c - e * NT];
+            m = VM ? __ldg(VM + off) : T(0);
+            k = VK ? __ldg(VK + off) : T(0);
+        } else {
+            m = k = T(0);
+        }
+    }
+};
+
+// the table sym[i n_p + j] of one element type, filled by the whole block
+template <int NP>
+__device__ __forceinline__ void fill_sym_table(short* sym) {
+    for (int l = threadIdx.x; l < NP * NP; l += blockDim.x) sym[l] = (short)sym_idx(NP, l / NP, l % NP);
+}
+
 template <int NP, typename T>
 __global__ void __launch_bounds__(256) scatter_segments_kernel(const int* __restrict__ seg_ptr,
                                                                const int* __restrict__ contrib, int64_t nnz,
                                                                const T* __restrict__ VM, const T* __restrict__ VK,
                                                                const T* __restrict__ VT, T* __restrict__ vM,
                                                                T* __restrict__ vK, T* __restrict__ vT) {
-    constexpr int NT = NP * NP, NSYM = NP * (NP + 1) / 2;
-    const bool dM = vM != nullptr, dK = vK != nullptr, dT = vT != nullptr;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x) {
-        const int a = seg_ptr[s], b = seg_ptr[s + 1];
-        T am = T(0), ak = T(0), at = T(0);
-        for (int p = a; p < b; ++p) {
-            const int c = contrib[p];
-            const int e = c / NT;
-            const int l = c - e * NT;
-            if (dT) at += VT[(int64_t)e * NT + l];
-            if (dM | dK) {
-                const int i = l / NP, j = l - (l / NP) * NP;
-                const int si = sym_idx(NP, i, j);
-                if (dM) am += VM[(int64_t)e * NSYM + si];
-                if (dK) ak += VK[(int64_t)e * NSYM + si];
-            }
+    __shared__ short sym[NP * NP];
+    fill_sym_table<NP>(sym);
+    __syncthreads();
+    const T* vm_src = vM ? VM : nullptr;
+    const T* vk_src = vK ? VK : nullptr;
+    const T* vt_src = vT ? VT : nullptr;
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= nnz) return;
+    // pipeline registers: bounds of s and s+G, first two contributors of s
+    int a0 = __ldg(seg_ptr + s), b0 = __ldg(seg_ptr + s + 1);
+    int a1 = 0, b1 = 0;
+    if (s + G < nnz) {
+        a1 = __ldg(seg_ptr + s + G);
+        b1 = __ldg(seg_ptr + s + G + 1);
+    }
+    int c0 = a0 < b0 ? __ldg(contrib + a0) : -1;
+    int c1 = a0 + 1 < b0 ? __ldg(contrib + a0 + 1) : -1;
+    while (true) {
+        const int64_t s1 = s + G, s2 = s + 2 * G;
+        // in flight together: V of slot s, contributors of s+G, bounds of s+2G
+        Contribution<NP, T> x0, x1;
+        if (c0 >= 0) x0.load(c0, sym, vm_src, vk_src, vt_src);
+        if (c1 >= 0) x1.load(c1, sym, vm_src, vk_src, vt_src);
+        int n0 = -1, n1 = -1;
+        if (s1 < nnz) {
+            n0 = a1 < b1 ? __ldg(contrib + a1) : -1;
+            n1 = a1 + 1 < b1 ? __ldg(contrib + a1 + 1) : -1;
         }
-        if (dM) vM[s] = am;
-        if (dK) vK[s] = ak;
-        if (dT) vT[s] = at;
+        int a2 = 0, b2 = 0;
+        if (s2 < nnz) {
+            a2 = __ldg(seg_ptr + s2);
+            b2 = __ldg(seg_ptr + s2 + 1);
+        }
+        T am = T(0), ak = T(0), at = T(0);
+        if (c0 >= 0) {
+            am += x0.m;
+            ak += x0.k;
+            at += x0.t;
+        }
+        if (c1 >= 0) {
+            am += x1.m;
+            ak += x1.k;
+            at += x1.t;
+        }
+        for (int p = a0 + 2; p < b0; ++p) {
+            Contribution<NP, T> x;
+            x.load(__ldg(contrib + p), sym, vm_src, vk_src, vt_src);
+            am += x.m;
+            ak += x.k;
+            at += x.t;
+        }
+        if (vM) vM[s] = am;
+        if (vK) vK[s] = ak;
+        if (vT) vT[s] = at;
+        if (s1 >= nnz) break;
+        s = s1;
+        a0 = a1;
+        b0 = b1;
+        a1 = a2;
+        b1 = b2;
+        c0 = n0;
+        c1 = n1;
     }
 }
 
-// One slot of the segment sum (shared by the single-mesh and batched kernels).
+// One slot of the segment sum, contributions in ascending order (the same
+// order as the single-mesh kernel, so batched sums carry the same bits).
 template <int NP, typename T>
 __device__ __forceinline__ void segment_slot(int64_t s, const int* __restrict__ seg_ptr,
-                                             const int* __restrict__ contrib, const T* __restrict__ VM,
-                                             const T* __restrict__ VK, const T* __restrict__ VT, T* __restrict__ vM,
-                                             T* __restrict__ vK, T* __restrict__ vT) {
-    constexpr int NT = NP * NP, NSYM = NP * (NP + 1) / 2;
-    const int a = seg_ptr[s], b = seg_ptr[s + 1];
+                                             const int* __restrict__ contrib, const short* __restrict__ sym,
+                                             const T* __restrict__ VM, const T* __restrict__ VK,
+                                             const T* __restrict__ VT, T* __restrict__ vM, T* __restrict__ vK,
+                                             T* __restrict__ vT) {
+    const int a = __ldg(seg_ptr + s), b = __ldg(seg_ptr + s + 1);
     T am = T(0), ak = T(0), at = T(0);
     for (int p = a; p < b; ++p) {
-        const int c = contrib[p];
-        const int e = c / NT;
-        const int l = c - e * NT;
-        if (vT) at += VT[(int64_t)e * NT + l];
-        if (vM || vK) {
-            const int i = l / NP, j = l - (l / NP) * NP;
-            const int si = sym_idx(NP, i, j);
-            if (vM) am += VM[(int64_t)e * NSYM + si];
-            if (vK) ak += VK[(int64_t)e * NSYM + si];
-        }
+        Contribution<NP, T> x;
+        x.load(__ldg(contrib + p), sym, VM, VK, VT);
+        am += x.m;
+        ak += x.k;
+        at += x.t;
     }
     if (vM) vM[s] = am;
     if (vK) vK[s] = ak;
     if (vT) vT[s] = at;
 }
 
+// offsets of the per-type symmetric-index tables in the batched kernel
+__host__ __device__ constexpr int sym_tab_off(int np) {
+    return np == 3 ? 0 : np == 4 ? 9 : np == 6 ? 25 : np == 10 ? 61 : 161;
+}
+constexpr int SYM_TAB_TOTAL = 561;
+
 // Batched: the work list holds chunks of `count` slots of many meshes.
 template <typename T>
 __global__ void __launch_bounds__(512) batch_scatter_kernel(const BatchItem* __restrict__ items, int nitems,
                                                             const BatchMesh* __restrict__ meshes) {
+    __shared__ short sym[SYM_TAB_TOTAL];
+    fill_sym_table<3>(sym + sym_tab_off(3));
+    fill_sym_table<4>(sym + sym_tab_off(4));
+    fill_sym_table<6>(sym + sym_tab_off(6));
+    fill_sym_table<10>(sym + sym_tab_off(10));
+    fill_sym_table<20>(sym + sym_tab_off(20));
+    __syncthreads();
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BatchItem w = items[it];
         const BatchMesh& bm = meshes[w.mesh];
@@ -171,15 +251,16 @@ __global__ void __launch_bounds__(512) batch_scatter_kernel(const BatchItem* __r
         T* vM = static_cast<T*>(bm.vM);
         T* vK = static_cast<T*>(bm.vK);
         T* vT = static_cast<T*>(bm.vT);
+        const short* st = sym + sym_tab_off(bm.np);
         for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
             const int64_t s = w.first + k;
             if (s >= bm.nnz) break;
             switch (bm.np) {
-                case 3: segment_slot<3, T>(s, bm.seg_ptr, bm.contrib, VM, VK, VT, vM, vK, vT); break;
-                case 4: segment_slot<4, T>(s, bm.seg_ptr, bm.contrib, VM, VK, VT, vM, vK, vT); break;
-                case 6: segment_slot<6, T>(s, bm.seg_ptr, bm.contrib, VM, VK, VT, vM, vK, vT); break;
-                case 10: segment_slot<10, T>(s, bm.seg_ptr, bm.contrib, VM, VK, VT, vM, vK, vT); break;
-                case 20: segment_slot<20, T>(s, bm.seg_ptr, bm.contrib, VM, VK, VT, vM, vK, vT); break;
+                case 3: segment_slot<3, T>(s, bm.seg_ptr, bm.contrib, st, VM, VK, VT, vM, vK, vT); break;
+                case 4: segment_slot<4, T>(s, bm.seg_ptr, bm.contrib, st, VM, VK, VT, vM, vK, vT); break;
+                case 6: segment_slot<6, T>(s, bm.seg_ptr, bm.contrib, st, VM, VK, VT, vM, vK, vT); break;
+                case 10: segment_slot<10, T>(s, bm.seg_ptr, bm.contrib, st, VM, VK, VT, vM, vK, vT); break;
+                case 20: segment_slot<20, T>(s, bm.seg_ptr, bm.contrib, st, VM, VK, VT, vM, vK, vT); break;
                 default: break;
             }
         }

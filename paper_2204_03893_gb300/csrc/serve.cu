@@ -162,12 +162,8 @@ size_t mesh_estimate(const fem_mesh_desc& d, int prec) {
     return b + 4096;                      // rounding of small buffers
 }
 
-// Precision a mesh is reassembled in: the server's, except that P3
-// tetrahedra (whose tile does not fit the tensor-core layout) use FP32 SIMT
-// in a FEM_TF32X3 server.
-int mesh_prec(int prec, const fem_mesh* m) {
-    return (prec == FEM_TF32X3 && m->d == 3 && m->p == 3) ? FEM_FP32 : prec;
-}
+// Precision a mesh is reassembled in (the server's, for every element type).
+int mesh_prec(int prec, const fem_mesh*) { return prec; }
 
 // Runs on the scheduler thread with the lock released.  For ASSEMBLE the new
 // mesh is returned in *created (the caller publishes it under the lock).
@@ -398,7 +394,6 @@ int fem_serve_submit(fem_server* S, const fem_request* q, uint64_t* ticket) {
         }
         n = (size_t)d.n_nodes;
         nnz_bound = std::min((size_t)d.n_elems * np * np, n * n);
-        if (prec == FEM_TF32X3 && d.dim == 3 && d.order == 3) prec = FEM_FP32;
         r->est_bytes = mesh_estimate(d, prec);
     } else {
         std::lock_guard<std::mutex> lk(S->mu);

@@ -116,6 +116,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
                  : "memory");
 }
 
+// Arrive on the barrier (count 1) and raise its expected transaction bytes.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}\n" ::"r"(mbar),
+        "r"(bytes)
+        : "memory");
+}
+
+// Bulk copy (no tensor map) of `bytes` from global memory into this CTA's
+// shared memory; both addresses 16-byte aligned, bytes a multiple of 16.
+// Completion is counted in transaction bytes on `mbar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst_smem, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst_smem),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
 // round-to-nearest (ties away) to TF32, returned as an FP32 bit pattern
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;

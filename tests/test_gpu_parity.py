@@ -104,7 +104,7 @@ def test_fp64_parity_per_entry(name):
         assert worst <= 1.0, (k, worst)
 
 
-@pytest.mark.parametrize("name", [c for c in CASES if c != "tet_p3"])
+@pytest.mark.parametrize("name", CASES)
 def test_tf32x3_parity_frobenius(name):
     wl = wl_small(name)
     _, o = oracle_result(name, wl)
@@ -115,12 +115,27 @@ def test_tf32x3_parity_frobenius(name):
         assert frob(g[k], o[k]) <= TF32_TOL, (k, frob(g[k], o[k]))
 
 
-def test_tf32x3_unsupported_type_is_refused():
-    wl = wl_small("tet_p3")
-    fm = FemMesh.of(wl.mesh)
-    with pytest.raises(F.FemError) as ei:
-        gpu_assemble(fm, wl, "tf32x3")
-    assert ei.value.code == F.FEM_EINVAL
+@pytest.mark.parametrize("which", ["MKT", "M", "K", "T", "KT"])
+def test_tf32x3_chunked_p3_tet(which):
+    """P3 tetrahedra take the chunked tensor-core product (Q streamed
+    through shared memory by quadrature-point chunks): 1296 elements (11
+    tiles, ragged last tile), every subset of matrices, repeatable bits."""
+    m = mg.structured_tet(6, 3, 0.15, seed=91)
+    u = mg.fourier_field(m.coords, 92)
+    wl = mg.Workload("tet_p3_chunked", m, u, mg.Coeff("sin", (2.0, 1.0, 3.0)))
+    o = orc.Oracle.of(m).assemble(u, wl.coeff)
+    fm = FemMesh.of(m)
+    fm.symbolic()
+    uu = torch.tensor(u, dtype=torch.float64, device="cuda")
+    r1 = {k: v.clone() for k, v in fm.assemble(uu, "sin", (2.0, 1.0, 3.0), "tf32x3", which=tuple(which)).items()}
+    r2 = fm.assemble(uu, "sin", (2.0, 1.0, 3.0), "tf32x3", which=tuple(which))
+    torch.cuda.synchronize()
+    F.fem_device_status()
+    assert set(r1) == set(which)
+    for k in which:
+        assert torch.equal(r1[k], r2[k])
+        g = r1[k].double().cpu().numpy()
+        assert frob(g, o[k]) <= TF32_TOL, (k, frob(g, o[k]))
 
 
 @pytest.mark.parametrize("name", CASES)

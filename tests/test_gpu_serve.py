@@ -49,9 +49,8 @@ def test_serve_matches_single_calls(prec):
             r, vals = S.result(t)
             assert r.status == 0, F._err()
             ids.append(r.mesh_id)
-            p = "fp32" if (prec == "tf32x3" and m.d == 3 and m.p == 3) else prec
-            assert r.prec == PRECISIONS[p]
-            ref = single(m, mg.fourier_field(m.coords, 1 + i), "poly", (1.0, 0.3, 0.2), p)
+            assert r.prec == PRECISIONS[prec]
+            ref = single(m, mg.fourier_field(m.coords, 1 + i), "poly", (1.0, 0.3, 0.2), prec)
             for k in "MKT":
                 assert torch.equal(vals[k], ref[k]), (i, k)
         pend = []
@@ -64,8 +63,7 @@ def test_serve_matches_single_calls(prec):
             r, vals = S.result(t)
             assert r.status == 0
             m = ms[i]
-            p = "fp32" if (prec == "tf32x3" and m.d == 3 and m.p == 3) else prec
-            ref = single(m, u, law[0], law[1], p)
+            ref = single(m, u, law[0], law[1], prec)
             for k in "MKT":
                 assert torch.equal(vals[k], ref[k]), (i, k)
         st = S.stats()
