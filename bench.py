@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-mesh batched measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream measurement")
     ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the sweeps on the other configurations (tri_p1_64, tet_p1_128, tet_p2_64)")
     return ap.parse_args()
 
 
@@ -204,6 +206,54 @@ def _pct(xs, q):
 def _per_mesh_prec(F, mesh):
     # every element type has a tensor-core product (P3 tetrahedra: the chunked one)
     return F.FEM_TF32X3
+
+
+def measure_sweep(F, torch, stream, name, precs=("tf32x3", "fp64"), nsweep=10, warmup=2):
+    """A Newton-style sweep on one of the other configurations: the pattern
+    and geometry built once, then `nsweep` reassemblies of M, K(u), T(u) with
+    a fresh Fourier field u^(s) each (seed 3+s), timed with CUDA events."""
+    from paper_2204_03893_gb300.torch_api import PRECISIONS, FemMesh
+    sh = stream.cuda_stream
+    wl = mg.workload(name)
+    out = {"elements": wl.mesh.n_elems, "nodes": wl.mesh.n_nodes, "sweep": nsweep,
+           "law": f"{wl.coeff.kind} {tuple(wl.coeff.params)}"}
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        fm = FemMesh.of(wl.mesh, stream=stream)
+        torch.cuda.synchronize()
+        t_mesh = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        fm.symbolic()
+        torch.cuda.synchronize()
+        out["nnz"] = fm.nnz
+        out["setup_ms"] = {"mesh_create_geometry": 1e3 * t_mesh, "symbolic_pattern": 1e3 * (time.perf_counter() - t0)}
+        us = [torch.tensor(mg.sweep_field(wl, s_), dtype=torch.float64, device="cuda") for s_ in range(nsweep)]
+        k = F.coeff(wl.coeff.kind, wl.coeff.params)
+        for pname in precs:
+            prec = PRECISIONS[pname]
+            dt = torch.float64 if pname == "fp64" else torch.float32
+            o = {kk: torch.empty(max(fm.nnz, 1), dtype=dt, device="cuda") for kk in "MKT"}
+            for i in range(warmup):
+                F.fem_form_elements(fm.h, k, us[i % nsweep], prec, 7, sh)
+                F.fem_sum_elements(fm.h, prec, o["M"], o["K"], o["T"], sh)
+            torch.cuda.synchronize()
+            ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nsweep)]
+            for i in range(nsweep):
+                ev[i][0].record(stream)
+                F.fem_form_elements(fm.h, k, us[i], prec, 7, sh)
+                ev[i][1].record(stream)
+                F.fem_sum_elements(fm.h, prec, o["M"], o["K"], o["T"], sh)
+                ev[i][2].record(stream)
+            torch.cuda.synchronize()
+            F.fem_device_status(sh)
+            tot = ev[0][0].elapsed_time(ev[-1][2])
+            out[pname] = {"value": wl.mesh.n_elems * nsweep / (tot / 1e3), "unit": "elements/s",
+                          "ms_per_reassembly": tot / nsweep,
+                          "element_form_ms": statistics.mean(e[0].elapsed_time(e[1]) for e in ev),
+                          "csr_sum_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in ev)}
+            del o
+        fm.close()
+    return out
 
 
 def measure_batched(F, torch, stream, wls, steps=50, warmup=5):
@@ -544,7 +594,8 @@ def run_ours(args, rank, world, local_rank):
     dom = max(kernels.values(), key=lambda d: d["ms"])
     peak, peak_kind = measured_peaks()
     achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
-    traffic = kernel_traffic(dom["kernel"] + ":" + args.prec, dom["src"])
+    traffic = None if args.scale is not None else kernel_traffic(f"{dom['kernel']}:{args.prec}:{args.workload}",
+                                                                  dom["src"])
     roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": achieved, "peak": peak,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs copy)" if peak_kind == "measured" else peak_kind,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
@@ -558,6 +609,12 @@ def run_ours(args, rank, world, local_rank):
     bwls = None if (args.no_batched and args.no_serve) else mg.batched_meshes(64, seed=4)
     batched = None if args.no_batched else measure_batched(F, torch, stream, bwls)
     served = None if args.no_serve else measure_serve(F, torch, bwls, n_requests=args.serve_requests)
+    del bwls
+    configs = None
+    if not args.no_configs:
+        configs = {"tri_p1_64": measure_sweep(F, torch, stream, "tri_p1_64", precs=("fp64", "tf32x3")),
+                   "tet_p1_128": measure_sweep(F, torch, stream, "tet_p1_128"),
+                   "tet_p2_64": measure_sweep(F, torch, stream, "tet_p2_64")}
 
     cpu = None if args.no_cpu_baseline else cpu_baseline_oracle()
     line = {
@@ -573,7 +630,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roofline, "phases": phases,
         "setup_once_per_mesh_ms": {"mesh_create_geometry": 1e3 * t_mesh, "symbolic_pattern": 1e3 * t_sym},
         "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64, "clocks": clk.summary(),
-        "gpu_launches": 2 * args.steps, "batched": batched, "serve": served,
+        "gpu_launches": 2 * args.steps, "batched": batched, "serve": served, "configs": configs,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -19,6 +19,7 @@
 // Every mbarrier wait is bounded (~1 s of SM clocks); on timeout the kernel
 // records an error word, stops, and releases its tensor memory.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -39,8 +40,8 @@ __host__ __device__ constexpr int pow2_at_least(int x) {
 }
 
 constexpr int TILE = 128;
-constexpr int STAGE_FLOATS = 4 * 32 * 33;
 constexpr int SMEM_MAX = 227 * 1024;
+constexpr int STAGE_FLOATS = 4 * 32 * 33;   // epilogue_staged: 32 x 33 floats per warp
 constexpr int IMG_SLOT_FLOATS = 24 * 1024;   // 96 KiB per element type
 
 template <typename ETy>
@@ -67,7 +68,7 @@ struct TcL {
     static constexpr int SMEM = QEND + XEND;
     // epilogue reads whole 32-column chunks: they must stay inside the allocation
     static constexpr bool FITS = NMp <= 256 && NTp <= 256 && ALLOC <= 512 && SMEM <= SMEM_MAX &&
-                                 XEND >= STAGE_FLOATS * 4 && QEND <= IMG_SLOT_FLOATS * 4 &&
+                                 XEND >= 4 * 32 * ETy::NT * 4 && QEND <= IMG_SLOT_FLOATS * 4 &&
                                  COLM + ru(ETy::NSYM, 32) <= ALLOC && COLK + ru(ETy::NSYM, 32) <= ALLOC &&
                                  COLT + ru(ETy::NT, 32) <= ALLOC;
 };
@@ -118,10 +119,54 @@ __device__ __forceinline__ void issue_tf32x3(uint32_t tmem_d, uint32_t xh, uint3
     }
 }
 
-// TMEM (this warp's 32 lanes, columns col..col+N) -> V rows, coalesced
-template <int N>
+// TMEM (this warp's 32 lanes = 32 consecutive elements, columns col..col+N)
+// -> V.  The warp's 32 rows of V are one contiguous block of 32 N floats:
+// every thread writes its row into the warp's own block in shared memory
+// (stage + warp 32 NMAX floats, NMAX >= N for every matrix of the tile, so
+// warps never share a block), then the warp copies the block out with
+// 16-byte, fully coalesced stores.  Rows past E are not written.
+template <int N, int NMAX>
 __device__ __forceinline__ void epilogue(uint32_t tmem, int col, float* stage, float* __restrict__ V, int64_t row0,
                                          int64_t E, int warp, int lane) {
+    static_assert(N <= NMAX, "epilogue block too small");
+    if (row0 >= E) return;   // warp-uniform
+    float* blk = stage + warp * 32 * NMAX;
+#pragma unroll 1
+    for (int c0 = 0; c0 < N; c0 += 32) {
+        uint32_t r[32];
+        tc::tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + col + c0, r);
+        float* dst = blk + lane * N + c0;
+        if constexpr (N % 4 == 0) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+                if (c0 + j < N)
+                    *reinterpret_cast<float4*>(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                                      __uint_as_float(r[j + 2]),
+                                                                      __uint_as_float(r[j + 3]));
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (c0 + j < N) dst[j] = __uint_as_float(r[j]);
+        }
+    }
+    __syncwarp();
+    const int rows = E - row0 < 32 ? (int)(E - row0) : 32;
+    const int nf = rows * N;
+    float* g = V + row0 * N;   // row0 is a multiple of 32: 16-byte aligned
+    const int nv = nf >> 2;
+    for (int i = lane; i < nv; i += 32) reinterpret_cast<float4*>(g)[i] = reinterpret_cast<const float4*>(blk)[i];
+    for (int i = (nv << 2) + lane; i < nf; i += 32) g[i] = blk[i];
+    __syncwarp();
+}
+
+// TMEM (this warp's 32 lanes, columns col..col+N) -> V rows through a
+// 32 x 33 staging tile per warp (stage + warp 32 x 33 floats): each store
+// instruction writes one row.  Used where the whole-block staging of
+// `epilogue` would not fit (the chunked product's 400-column T).
+template <int N>
+__device__ __forceinline__ void epilogue_staged(uint32_t tmem, int col, float* stage_base, float* __restrict__ V,
+                                                int64_t row0, int64_t E, int warp, int lane) {
+    float* stage = stage_base + warp * 32 * 33;
 #pragma unroll 1
     for (int c0 = 0; c0 < N; c0 += 32) {
         uint32_t r[32];
@@ -236,7 +281,7 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
     const uint32_t sQu = tc::smem_u32(sQ), sXu = tc::smem_u32(sX);
     const bool doM = VM != nullptr, doK = VK != nullptr, doT = VT != nullptr;
     const bool need_u = doK | doT;
-    float* stage = reinterpret_cast<float*>(sX) + warp * 32 * 33;
+    float* stage = reinterpret_cast<float*>(sX);   // epilogue blocks (the X tile is consumed by then)
     uint32_t phase = 0;
     bool timed_out = false;
 
@@ -308,9 +353,9 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
         }
         tc::fence_after_sync();
         const int64_t row0 = tile * TILE + warp * 32;
-        if (doM) epilogue<ETy::NSYM>(tmem, L::COLM, stage, VM, row0, E, warp, lane);
-        if (doK) epilogue<ETy::NSYM>(tmem, L::COLK, stage, VK, row0, E, warp, lane);
-        if (doT) epilogue<ETy::NT>(tmem, L::COLT, stage, VT, row0, E, warp, lane);
+        if (doM) epilogue<ETy::NSYM, ETy::NT>(tmem, L::COLM, stage, VM, row0, E, warp, lane);
+        if (doK) epilogue<ETy::NSYM, ETy::NT>(tmem, L::COLK, stage, VK, row0, E, warp, lane);
+        if (doT) epilogue<ETy::NT, ETy::NT>(tmem, L::COLT, stage, VT, row0, E, warp, lane);
         tc::fence_before_sync();
         __syncthreads();
     }
@@ -384,11 +429,11 @@ __device__ __forceinline__ bool batch_tc_tile(const BatchMesh& bm, int64_t first
     if (__syncthreads_or(!ok)) return false;
     tc::fence_after_sync();
     // the epilogue stages through the X region (the MMAs are complete)
-    float* stage = reinterpret_cast<float*>(sX) + warp * 32 * 33;
+    float* stage = reinterpret_cast<float*>(sX);
     const int64_t row0 = first + warp * 32;
-    if (doM) epilogue<ETy::NSYM>(tmem, L::COLM, stage, static_cast<float*>(bm.VM), row0, E, warp, lane);
-    if (doK) epilogue<ETy::NSYM>(tmem, L::COLK, stage, static_cast<float*>(bm.VK), row0, E, warp, lane);
-    if (doT) epilogue<ETy::NT>(tmem, L::COLT, stage, static_cast<float*>(bm.VT), row0, E, warp, lane);
+    if (doM) epilogue<ETy::NSYM, ETy::NT>(tmem, L::COLM, stage, static_cast<float*>(bm.VM), row0, E, warp, lane);
+    if (doK) epilogue<ETy::NSYM, ETy::NT>(tmem, L::COLK, stage, static_cast<float*>(bm.VK), row0, E, warp, lane);
+    if (doT) epilogue<ETy::NT, ETy::NT>(tmem, L::COLT, stage, static_cast<float*>(bm.VT), row0, E, warp, lane);
     tc::fence_before_sync();
     __syncthreads();
     return true;
@@ -487,7 +532,7 @@ struct ChL {
     static constexpr int QB_M = NMp * KcM * 8, QB_K = NMp * KcK * 8, QB_T = NTp * KcT * 8;
     static constexpr int QBMAX = QB_T > QB_K ? (QB_T > QB_M ? QB_T : QB_M) : (QB_K > QB_M ? QB_K : QB_M);
     static constexpr int IMG_BYTES = NCM * QB_M + NCK * QB_K + NCT * QB_T;
-    static constexpr int SMEM = XBYTES + QBMAX;
+    static constexpr int SMEM = XBYTES + QBMAX;                          // X chunk + Q chunk
     static constexpr bool OK = NQ % QCM == 0 && NQ % QCK == 0 && NQ % QCT == 0 && KcK % 8 == 0 && KcT % 8 == 0 &&
                                NMp <= 256 && NTa <= 256 && NTb <= 256 && NTb % 16 == 0 && 2 * NMp <= ALLOC &&
                                COLK + ru(ETy::NSYM, 32) <= ALLOC && COLT + ru(ETy::NT, 32) <= ALLOC &&
@@ -616,7 +661,7 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
     unsigned char* sQ = smem + L::XBYTES;
     const uint32_t sXu = tc::smem_u32(sX), sQu = tc::smem_u32(sQ);
     const int64_t row0 = first + warp * 32;
-    float* stage = reinterpret_cast<float*>(smem) + warp * 32 * 33;
+    float* stage = reinterpret_cast<float*>(smem);
 #pragma unroll 1
     for (int s = 0; s < L::NSTEP; ++s) {
         const int kd = L::kind(s), c = L::chunk(s);
@@ -681,12 +726,12 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
         // drain the accumulators once their last chunk is in (the stage
         // area aliases the X chunk, which the completed MMAs no longer read)
         if (s == L::NCM + L::NCK - 1) {
-            if (doM) epilogue<ETy::NSYM>(tmem, L::COLM, stage, VM, row0, E, warp, lane);
-            if (doK) epilogue<ETy::NSYM>(tmem, L::COLK, stage, VK, row0, E, warp, lane);
+            if (doM) epilogue_staged<ETy::NSYM>(tmem, L::COLM, stage, VM, row0, E, warp, lane);
+            if (doK) epilogue_staged<ETy::NSYM>(tmem, L::COLK, stage, VK, row0, E, warp, lane);
             tc::fence_before_sync();
             __syncthreads();
         } else if (s == L::NSTEP - 1) {
-            if (doT) epilogue<ETy::NT>(tmem, L::COLT, stage, VT, row0, E, warp, lane);
+            if (doT) epilogue_staged<ETy::NT>(tmem, L::COLT, stage, VT, row0, E, warp, lane);
             tc::fence_before_sync();
             __syncthreads();
         }
@@ -843,6 +888,40 @@ void build_chunk_image(std::vector<float>& img, const RefElem& R) {
 
 std::mutex g_mu;
 bool g_done[64] = {};
+std::atomic<bool> g_ready[64];   // lock-free fast path of tables_init_tc
+
+// Launch shape of a tensor-core kernel on one device: computed (and the
+// kernel's shared-memory attributes set) on first use, then cached.
+struct LaunchShape {
+    int nsm = 0, smem = 0, occ = 0;
+    const void* img = nullptr;
+    int* err = nullptr;
+};
+
+template <typename F>
+int cached_shape(std::atomic<int>* have, LaunchShape* cache, std::mutex& mu, F compute, LaunchShape& out) {
+    int dev = 0;
+    FEM_CUDA_TRY(cudaGetDevice(&dev));
+    const bool slot = dev >= 0 && dev < 64;
+    if (slot && have[dev].load(std::memory_order_acquire)) {
+        out = cache[dev];
+        return FEM_OK;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (slot && have[dev].load(std::memory_order_relaxed)) {
+        out = cache[dev];
+        return FEM_OK;
+    }
+    LaunchShape sh;
+    const int rc = compute(dev, sh);
+    if (rc) return rc;
+    if (slot) {
+        cache[dev] = sh;
+        have[dev].store(1, std::memory_order_release);
+    }
+    out = sh;
+    return FEM_OK;
+}
 
 template <typename ETy>
 int launch_tc_chunked(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
@@ -850,34 +929,42 @@ int launch_tc_chunked(const fem_mesh& m, const CoeffDev& k, const float2* u, flo
     using L = ChL<ETy>;
     if (m.E == 0) return FEM_OK;
     auto kern = element_tc_chunked_kernel<ETy>;
-    int dev = 0, nsm = 0, optin = 0, per_sm = 0, occ = 0;
-    FEM_CUDA_TRY(cudaGetDevice(&dev));
-    FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    FEM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    FEM_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-    cudaFuncAttributes fa;
-    FEM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
-    const int dyn_max = optin - (int)fa.sharedSizeBytes;
-    // one CTA per SM (it holds all 512 TMEM columns): ask for more than half
-    // of the SM's shared memory
-    const int smem = std::min(dyn_max, std::max(L::SMEM, per_sm / 2 + 1));
-    if (smem < L::SMEM) return fail(FEM_EINVAL, "chunked tensor-core tile does not fit in shared memory");
-    FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                      (int)cudaSharedmemCarveoutMaxShared));
-    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
-    if (occ > 1) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
+    static std::atomic<int> have[64];
+    static LaunchShape cache[64];
+    static std::mutex mu;
+    LaunchShape sh;
+    int rc = cached_shape(have, cache, mu, [&](int dev, LaunchShape& o) -> int {
+        int optin = 0, per_sm = 0, occ = 0;
+        FEM_CUDA_TRY(cudaDeviceGetAttribute(&o.nsm, cudaDevAttrMultiProcessorCount, dev));
+        FEM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        FEM_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        cudaFuncAttributes fa;
+        FEM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+        const int dyn_max = optin - (int)fa.sharedSizeBytes;
+        // one CTA per SM (it holds all 512 TMEM columns): ask for more than
+        // half of the SM's shared memory
+        o.smem = std::min(dyn_max, std::max(L::SMEM, per_sm / 2 + 1));
+        if (o.smem < L::SMEM) return fail(FEM_EINVAL, "chunked tensor-core tile does not fit in shared memory");
+        FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, o.smem));
+        FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared));
+        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, o.smem));
+        if (occ > 1) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
+        o.occ = 1;
+        void* img = nullptr;
+        FEM_CUDA_TRY(cudaGetSymbolAddress(&img, g_tcbig));
+        o.img = img;
+        FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&o.err, g_tc_err));
+        return FEM_OK;
+    }, sh);
+    if (rc) return rc;
     const int64_t ntiles = (m.E + TILE - 1) / TILE;
-    int64_t grid = nsm;
+    int64_t grid = sh.nsm;
     if (grid > ntiles) grid = ntiles;
-    unsigned char* img = nullptr;
-    int* err = nullptr;
-    FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&img, g_tcbig));
-    FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&err, g_tc_err));
-    trace_launch("element_tc_chunked_kernel", grid, TILE, smem, 1);
+    trace_launch("element_tc_chunked_kernel", grid, TILE, sh.smem, 1);
     cudaGetLastError();   // clear any stale error before the launch check
-    kern<<<(unsigned)grid, TILE, smem, s>>>(m.conn.as<int>(), m.geo32.as<float>(), m.E, u, k, (float)m.m, VM, VK, VT,
-                                            img, err);
+    kern<<<(unsigned)grid, TILE, sh.smem, s>>>(m.conn.as<int>(), m.geo32.as<float>(), m.E, u, k, (float)m.m, VM, VK,
+                                               VT, static_cast<const unsigned char*>(sh.img), sh.err);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
@@ -894,49 +981,60 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, 
     } else {
         if (m.E == 0) return FEM_OK;
         auto kern = element_tc_kernel<ETy>;
-        int dev = 0, nsm = 0, occ = 0, optin = 0;
-        FEM_CUDA_TRY(cudaGetDevice(&dev));
-        FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        FEM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        cudaFuncAttributes fa;
-        FEM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
-        const int dyn_max = optin - (int)fa.sharedSizeBytes;   // static shared memory counts against the limit
-        int smem = L::SMEM;
-        if (smem > dyn_max) return fail(FEM_EINVAL, "tensor-core tile does not fit in shared memory");
-        FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        // the whole unified L1/shared array as shared memory, so that several
-        // CTAs (each with its own TMEM columns) overlap their load, MMA and
-        // epilogue phases on one SM
-        FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                          (int)cudaSharedmemCarveoutMaxShared));
-        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
-        const int occ_max = 512 / L::ALLOC;   // co-resident CTAs must fit their TMEM columns
-        if (occ > occ_max) {
-            // ask for enough shared memory that at most occ_max CTAs fit on an SM
-            int per_sm = 0;
-            FEM_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-            smem = per_sm / (occ_max + 1) + 1;
-            if (smem > dyn_max) smem = dyn_max;
+        constexpr int SMEM0 = L::SMEM;
+        constexpr int ALLOC0 = L::ALLOC;
+        static std::atomic<int> have[64];
+        static LaunchShape cache[64];
+        static std::mutex mu;
+        LaunchShape sh;
+        int rc = cached_shape(have, cache, mu, [&](int dev, LaunchShape& o) -> int {
+            int optin = 0, occ = 0;
+            FEM_CUDA_TRY(cudaDeviceGetAttribute(&o.nsm, cudaDevAttrMultiProcessorCount, dev));
+            FEM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            cudaFuncAttributes fa;
+            FEM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+            const int dyn_max = optin - (int)fa.sharedSizeBytes;   // static shared memory counts against the limit
+            int smem = SMEM0;
+            if (smem > dyn_max) return fail(FEM_EINVAL, "tensor-core tile does not fit in shared memory");
             FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            // the whole unified L1/shared array as shared memory, so that
+            // several CTAs (each with its own TMEM columns) overlap their load,
+            // MMA and epilogue phases on one SM
+            FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                              (int)cudaSharedmemCarveoutMaxShared));
             FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
-            if (occ > occ_max) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
-        }
-        if (occ < 1) return fail(FEM_ECUDA, "tensor-core kernel does not fit on an SM");
-        // the occupancy query can under-report with the carveout preference;
-        // the register / shared-memory budget (bounded by TMEM) decides, and
-        // a persistent grid larger than what is co-resident stays correct
-        occ = std::max(occ, std::min(occ_max, ctas_per_sm(fa, TILE, smem, dev)));
-        int64_t ntiles = (m.E + TILE - 1) / TILE;
-        int64_t grid = (int64_t)nsm * occ;
+            const int occ_max = 512 / ALLOC0;   // co-resident CTAs must fit their TMEM columns
+            if (occ > occ_max) {
+                // ask for enough shared memory that at most occ_max CTAs fit on an SM
+                int per_sm = 0;
+                FEM_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+                smem = per_sm / (occ_max + 1) + 1;
+                if (smem > dyn_max) smem = dyn_max;
+                FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+                if (occ > occ_max) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
+            }
+            if (occ < 1) return fail(FEM_ECUDA, "tensor-core kernel does not fit on an SM");
+            // the occupancy query can under-report with the carveout
+            // preference; the register / shared-memory budget (bounded by
+            // TMEM) decides, and a persistent grid larger than what is
+            // co-resident stays correct
+            o.occ = std::max(occ, std::min(occ_max, ctas_per_sm(fa, TILE, smem, dev)));
+            o.smem = smem;
+            void* img = nullptr;
+            FEM_CUDA_TRY(cudaGetSymbolAddress(&img, g_tcimg));
+            o.img = static_cast<const float*>(img) + (size_t)ETy::TYPE * IMG_SLOT_FLOATS;
+            FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&o.err, g_tc_err));
+            return FEM_OK;
+        }, sh);
+        if (rc) return rc;
+        const int64_t ntiles = (m.E + TILE - 1) / TILE;
+        int64_t grid = (int64_t)sh.nsm * sh.occ;
         if (grid > ntiles) grid = ntiles;
-        trace_launch("element_tc_kernel", grid, TILE, smem, occ);
-        float* img = nullptr;
-        FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&img, g_tcimg));
-        int* err = nullptr;
-        FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&err, g_tc_err));
+        trace_launch("element_tc_kernel", grid, TILE, sh.smem, sh.occ);
         cudaGetLastError();   // clear any stale error before the launch check
-        kern<<<(unsigned)grid, TILE, smem, s>>>(m.conn.as<int>(), m.geo32.as<float>(), m.E, u, k, (float)m.m, VM, VK,
-                                                VT, img + (size_t)ETy::TYPE * IMG_SLOT_FLOATS, err);
+        kern<<<(unsigned)grid, TILE, sh.smem, s>>>(m.conn.as<int>(), m.geo32.as<float>(), m.E, u, k, (float)m.m, VM,
+                                                   VK, VT, static_cast<const float*>(sh.img), sh.err);
         FEM_CUDA_TRY(cudaGetLastError());
         return FEM_OK;
     }
@@ -947,6 +1045,7 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, 
 int tables_init_tc() {
     int dev = 0;
     FEM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && g_ready[dev].load(std::memory_order_acquire)) return FEM_OK;
     std::lock_guard<std::mutex> lk(g_mu);
     if (dev < 64 && g_done[dev]) return FEM_OK;
     std::vector<float> ref(TAB_TOTAL, 0.f), img((size_t)6 * IMG_SLOT_FLOATS, 0.f);
@@ -977,7 +1076,10 @@ int tables_init_tc() {
     }
     int zero = 0;
     FEM_CUDA_TRY(cudaMemcpyToSymbol(g_tc_err, &zero, sizeof(int)));
-    if (dev < 64) g_done[dev] = true;
+    if (dev >= 0 && dev < 64) {
+        g_done[dev] = true;
+        g_ready[dev].store(true, std::memory_order_release);
+    }
     return FEM_OK;
 }
 
