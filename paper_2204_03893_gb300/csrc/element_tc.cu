@@ -44,33 +44,46 @@ constexpr int SMEM_MAX = 227 * 1024;
 constexpr int STAGE_FLOATS = 4 * 32 * 33;   // epilogue_staged: 32 x 33 floats per warp
 constexpr int IMG_SLOT_FLOATS = 24 * 1024;   // 96 KiB per element type
 
+// Tile layout.  The X columns of M, K and T are packed into one K-major
+// operand of KTOTp = ru(KM + KK + KT, 8) columns per element row (M at 0, K
+// at KM, T at KM + KK).  Each matrix's MMAs run over the 8-wide K slices that
+// overlap its own columns, and its Q image has zero rows at the columns of
+// the neighbouring matrices, so the packing costs no extra products of any
+// weight and saves the per-matrix padding (40 instead of 48 columns for P2
+// triangles, which lets 4 CTAs share an SM).
 template <typename ETy>
 struct TcL {
-    static constexpr int KMp = ru(ETy::KM, 8), KKp = ru(ETy::KK, 8), KTp = ru(ETy::KT, 8);
+    static constexpr int KM = ETy::KM, KK = ETy::KK, KT = ETy::KT;
+    static constexpr int KTOT = KM + KK + KT, KTOTp = ru(KTOT, 8);
+    static constexpr int OFF_M = 0, OFF_K = KM, OFF_T = KM + KK;
+    // first slice and slice count of each matrix
+    static constexpr int SM0 = 0, NSM = ru(KM, 8) / 8;
+    static constexpr int SK0 = KM / 8, NSK = ru(KM + KK, 8) / 8 - KM / 8;
+    static constexpr int ST0 = (KM + KK) / 8, NST = KTOTp / 8 - (KM + KK) / 8;
     static constexpr int NMp = ru(ETy::NSYM, 16), NTp = ru(ETy::NT, 16);
     static constexpr int COLM = 0, COLK = NMp, COLT = 2 * NMp, COLS = 2 * NMp + NTp;
     static constexpr int ALLOC = pow2_at_least(COLS);
-    // shared-memory byte offsets: Q image, then X tile
+    // shared-memory byte offsets: Q images (each matrix's slices), then X
     static constexpr int QMh = 0;
-    static constexpr int QMl = QMh + NMp * KMp * 4;
-    static constexpr int QKh = QMl + NMp * KMp * 4;
-    static constexpr int QKl = QKh + NMp * KKp * 4;
-    static constexpr int QTh = QKl + NMp * KKp * 4;
-    static constexpr int QTl = QTh + NTp * KTp * 4;
-    static constexpr int QEND = QTl + NTp * KTp * 4;
-    static constexpr int XMh = 0;
-    static constexpr int XMl = XMh + TILE * KMp * 4;
-    static constexpr int XKh = XMl + TILE * KMp * 4;
-    static constexpr int XKl = XKh + TILE * KKp * 4;
-    static constexpr int XTh = XKl + TILE * KKp * 4;
-    static constexpr int XTl = XTh + TILE * KTp * 4;
-    static constexpr int XEND = XTl + TILE * KTp * 4;
+    static constexpr int QMl = QMh + NMp * NSM * 8 * 4;
+    static constexpr int QKh = QMl + NMp * NSM * 8 * 4;
+    static constexpr int QKl = QKh + NMp * NSK * 8 * 4;
+    static constexpr int QTh = QKl + NMp * NSK * 8 * 4;
+    static constexpr int QTl = QTh + NTp * NST * 8 * 4;
+    static constexpr int QEND = QTl + NTp * NST * 8 * 4;
+    static constexpr int XH = 0, XL = TILE * KTOTp * 4;
+    static constexpr int XEND = 2 * TILE * KTOTp * 4;
+    static constexpr uint32_t SBO_X = (KTOTp / 4) * 128;
     static constexpr int SMEM = QEND + XEND;
     // epilogue reads whole 32-column chunks: they must stay inside the allocation
     static constexpr bool FITS = NMp <= 256 && NTp <= 256 && ALLOC <= 512 && SMEM <= SMEM_MAX &&
                                  XEND >= 4 * 32 * ETy::NT * 4 && QEND <= IMG_SLOT_FLOATS * 4 &&
                                  COLM + ru(ETy::NSYM, 32) <= ALLOC && COLK + ru(ETy::NSYM, 32) <= ALLOC &&
-                                 COLT + ru(ETy::NT, 32) <= ALLOC;
+                                 COLT + ru(ETy::NT, 32) <= ALLOC &&
+                                 // packed order M, K, T; slices cover each matrix's columns
+                                 OFF_M == 0 && SM0 == 0 && OFF_K <= OFF_T && SK0 * 8 <= OFF_K &&
+                                 ST0 * 8 <= OFF_T && (SK0 + NSK) * 8 >= OFF_T && (ST0 + NST) * 8 == KTOTp &&
+                                 XH == 0 && XL == XEND / 2 && SBO_X == (uint32_t)KTOTp * 32;
 };
 
 __constant__ float c_tcref[TAB_TOTAL];
@@ -117,6 +130,40 @@ __device__ __forceinline__ void issue_tf32x3(uint32_t tmem_d, uint32_t xh, uint3
         tc::mma_tf32(tmem_d, ah, bl, idesc, 1u);
         tc::mma_tf32(tmem_d, al, bh, idesc, 1u);
     }
+}
+
+// One matrix of the packed tile: D (+)= sum over its `ns` K slices of
+// (Xhi Qhi + Xhi Qlo + Xlo Qhi), X slices s0 .. s0+ns-1 of the packed row
+// (stride sbo_x), Q slices 0 .. ns-1 of the matrix's own image.
+template <int NS_>
+__device__ __forceinline__ void issue_packed(uint32_t tmem_d, uint32_t xh, uint32_t xl, uint32_t sbo_x, int s0,
+                                             uint32_t qh, uint32_t ql, uint32_t idesc) {
+    constexpr uint32_t sbo_q = (NS_ * 8 / 4) * 128;
+#pragma unroll
+    for (int ks = 0; ks < NS_; ++ks) {
+        const uint32_t xo = (uint32_t)(s0 + ks) * 256, qo = (uint32_t)ks * 256;
+        uint64_t ah = tc::smem_desc(xh + xo, 128, sbo_x);
+        uint64_t al = tc::smem_desc(xl + xo, 128, sbo_x);
+        uint64_t bh = tc::smem_desc(qh + qo, 128, sbo_q);
+        uint64_t bl = tc::smem_desc(ql + qo, 128, sbo_q);
+        tc::mma_tf32(tmem_d, ah, bh, idesc, ks > 0 ? 1u : 0u);
+        tc::mma_tf32(tmem_d, ah, bl, idesc, 1u);
+        tc::mma_tf32(tmem_d, al, bh, idesc, 1u);
+    }
+}
+
+// The MMAs of one packed tile for the requested matrices (thread 0).
+template <typename L>
+__device__ __forceinline__ void issue_tile(uint32_t tmem, uint32_t sXu, uint32_t sQu, bool doM, bool doK, bool doT) {
+    if (doM)
+        issue_packed<L::NSM>(tmem + L::COLM, sXu + L::XH, sXu + L::XL, L::SBO_X, L::SM0, sQu + L::QMh, sQu + L::QMl,
+                             tc::idesc_tf32(L::NMp));
+    if (doK)
+        issue_packed<L::NSK>(tmem + L::COLK, sXu + L::XH, sXu + L::XL, L::SBO_X, L::SK0, sQu + L::QKh, sQu + L::QKl,
+                             tc::idesc_tf32(L::NMp));
+    if (doT)
+        issue_packed<L::NST>(tmem + L::COLT, sXu + L::XH, sXu + L::XL, L::SBO_X, L::ST0, sQu + L::QTh, sQu + L::QTl,
+                             tc::idesc_tf32(L::NTp));
 }
 
 // TMEM (this warp's 32 lanes = 32 consecutive elements, columns col..col+N)
@@ -186,12 +233,12 @@ __device__ __forceinline__ void epilogue_staged(uint32_t tmem, int col, float* s
 
 // X row of one element (Section 4: Lambda = S * (w b^T) in place; X_c =
 // Lambda (.) W; the tangent factors), from its gathered nodal values (split
-// as hi + lo) and its geometry (b_e, A_e upper triangle).  Entries beyond
-// the true K of each matrix stay zero.
-template <typename ETy, int KMp, int KKp, int KTp>
+// as hi + lo) and its geometry (b_e, A_e upper triangle), packed as
+// [X_M | X_K | X_T]; the padding columns stay as the caller set them (zero).
+template <typename ETy, int KTOTp>
 __device__ __forceinline__ void form_x(const float2 (&pu)[ETy::NP], const float (&pgeo)[1 + ETy::NS], bool need_u,
-                                       const CoeffDev& k, float mass, float (&xm)[KMp], float (&xk)[KKp],
-                                       float (&xt)[KTp]) {
+                                       const CoeffDev& k, float mass, float (&x)[KTOTp]) {
+    constexpr int OFF_K = ETy::KM, OFF_T = ETy::KM + ETy::KK;
     constexpr int D = ETy::D, NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS;
     constexpr int TO = type_tab_off(ETy::TYPE);
     constexpr int PHI = TO, GR = TO + NQ * NP, WQ = TO + NQ * NP * (1 + D);
@@ -226,10 +273,10 @@ __device__ __forceinline__ void form_x(const float2 (&pu)[ETy::NP], const float 
         float dk;
         const float kq = k_eval<float>(k, uq, dk);
         const float lam = c_tcref[WQ + q] * b;
-        xm[q] = mass * lam;
+        x[q] = mass * lam;
         const float lk = lam * kq;
 #pragma unroll
-        for (int t = 0; t < NS; ++t) xk[q * NS + t] = lk * A[t];
+        for (int t = 0; t < NS; ++t) x[OFF_K + q * NS + t] = lk * A[t];
         const float ld = lam * dk;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
@@ -239,7 +286,7 @@ __device__ __forceinline__ void form_x(const float2 (&pu)[ETy::NP], const float 
                 const int lo = a < c ? a : c, hi = a < c ? c : a;
                 sacc = fmaf(A[lo * D - (lo * (lo - 1)) / 2 + (hi - lo)], g[c], sacc);
             }
-            xt[q * D + a] = ld * sacc;
+            x[OFF_T + q * D + a] = ld * sacc;
         }
     }
 }
@@ -315,33 +362,21 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
         fetch_u();
     }
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        float xm[L::KMp], xk[L::KKp], xt[L::KTp];
+        // the whole packed row is written (unrequested parts too: every
+        // matrix's slices overlap its neighbours' columns)
+        float x[L::KTOTp];
 #pragma unroll
-        for (int i = 0; i < L::KMp; ++i) xm[i] = 0.f;
-#pragma unroll
-        for (int i = 0; i < L::KKp; ++i) xk[i] = 0.f;
-#pragma unroll
-        for (int i = 0; i < L::KTp; ++i) xt[i] = 0.f;
-        if (pvalid) form_x<ETy, L::KMp, L::KKp, L::KTp>(pu, pgeo, need_u, k, mass, xm, xk, xt);
+        for (int i = 0; i < L::KTOTp; ++i) x[i] = 0.f;
+        if (pvalid) form_x<ETy, L::KTOTp>(pu, pgeo, need_u, k, mass, x);
         const int64_t next = tile + gridDim.x;
         if (next < ntiles) fetch_meta(next);
-        if (doM) store_row<L::KMp>(sX + L::XMh, sX + L::XMl, xm, tid);
-        if (doK) store_row<L::KKp>(sX + L::XKh, sX + L::XKl, xk, tid);
-        if (doT) store_row<L::KTp>(sX + L::XTh, sX + L::XTl, xt, tid);
+        store_row<L::KTOTp>(sX + L::XH, sX + L::XL, x, tid);
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
-            if (doM)
-                issue_tf32x3<L::KMp>(tmem + L::COLM, sXu + L::XMh, sXu + L::XMl, sQu + L::QMh, sQu + L::QMl,
-                                     tc::idesc_tf32(L::NMp));
-            if (doK)
-                issue_tf32x3<L::KKp>(tmem + L::COLK, sXu + L::XKh, sXu + L::XKl, sQu + L::QKh, sQu + L::QKl,
-                                     tc::idesc_tf32(L::NMp));
-            if (doT)
-                issue_tf32x3<L::KTp>(tmem + L::COLT, sXu + L::XTh, sXu + L::XTl, sQu + L::QTh, sQu + L::QTl,
-                                     tc::idesc_tf32(L::NTp));
+            issue_tile<L>(tmem, sXu, sQu, doM, doK, doT);
             tc::mma_commit(mb);
         }
         if (next < ntiles) fetch_u();
@@ -385,13 +420,9 @@ __device__ __forceinline__ bool batch_tc_tile(const BatchMesh& bm, int64_t first
     if (!(doM | doK | doT)) return true;   // mesh skipped in this launch (uniform over the CTA)
     const bool need_u = doK | doT;
     const int64_t E = bm.E;
-    float xm[L::KMp], xk[L::KKp], xt[L::KTp];
+    float x[L::KTOTp];
 #pragma unroll
-    for (int i = 0; i < L::KMp; ++i) xm[i] = 0.f;
-#pragma unroll
-    for (int i = 0; i < L::KKp; ++i) xk[i] = 0.f;
-#pragma unroll
-    for (int i = 0; i < L::KTp; ++i) xt[i] = 0.f;
+    for (int i = 0; i < L::KTOTp; ++i) x[i] = 0.f;
     const int64_t e = first + tid;
     if (e < E) {
         float2 pu[NP];
@@ -403,25 +434,15 @@ __device__ __forceinline__ bool batch_tc_tile(const BatchMesh& bm, int64_t first
         }
 #pragma unroll
         for (int t = 0; t <= NS; ++t) pgeo[t] = __ldg(bm.geo32 + t * E + e);
-        form_x<ETy, L::KMp, L::KKp, L::KTp>(pu, pgeo, need_u, bm.k, (float)bm.mass, xm, xk, xt);
+        form_x<ETy, L::KTOTp>(pu, pgeo, need_u, bm.k, (float)bm.mass, x);
     }
-    if (doM) store_row<L::KMp>(sX + L::XMh, sX + L::XMl, xm, tid);
-    if (doK) store_row<L::KKp>(sX + L::XKh, sX + L::XKl, xk, tid);
-    if (doT) store_row<L::KTp>(sX + L::XTh, sX + L::XTl, xt, tid);
+    store_row<L::KTOTp>(sX + L::XH, sX + L::XL, x, tid);
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 0) {
         tc::fence_after_sync();
-        if (doM)
-            issue_tf32x3<L::KMp>(tmem + L::COLM, sXu + L::XMh, sXu + L::XMl, sQu + L::QMh, sQu + L::QMl,
-                                 tc::idesc_tf32(L::NMp));
-        if (doK)
-            issue_tf32x3<L::KKp>(tmem + L::COLK, sXu + L::XKh, sXu + L::XKl, sQu + L::QKh, sQu + L::QKl,
-                                 tc::idesc_tf32(L::NMp));
-        if (doT)
-            issue_tf32x3<L::KTp>(tmem + L::COLT, sXu + L::XTh, sXu + L::XTl, sQu + L::QTh, sQu + L::QTl,
-                                 tc::idesc_tf32(L::NTp));
+        issue_tile<L>(tmem, sXu, sQu, doM, doK, doT);
         tc::mma_commit(mb);
     }
     const uint32_t ok = tc::mbar_wait_bounded(mb, phase, WAIT_LIMIT);
@@ -862,9 +883,23 @@ void build_image(std::vector<float>& all, const RefElem& R) {
     using L = TcL<ETy>;
     std::vector<float> img(IMG_SLOT_FLOATS, 0.f);
     if constexpr (L::FITS) {
-        put_operand(img, L::QMh, L::QMl, R.QM.data(), ETy::KM, ETy::NSYM, L::KMp);
-        put_operand(img, L::QKh, L::QKl, R.QK.data(), ETy::KK, ETy::NSYM, L::KKp);
-        put_operand(img, L::QTh, L::QTl, R.QT.data(), ETy::KT, ETy::NT, L::KTp);
+        // rows of each matrix's slices: its own Q rows at their packed
+        // columns, zero rows at the neighbours' columns
+        auto slices = [](const std::vector<double>& Q, int K, int N, int off, int s0, int ns) {
+            std::vector<double> P((size_t)ns * 8 * N, 0.0);
+            for (int kk = 0; kk < ns * 8; ++kk) {
+                const int own = s0 * 8 + kk - off;
+                if (own >= 0 && own < K)
+                    for (int n = 0; n < N; ++n) P[(size_t)kk * N + n] = Q[(size_t)own * N + n];
+            }
+            return P;
+        };
+        const auto PM = slices(R.QM, ETy::KM, ETy::NSYM, L::OFF_M, L::SM0, L::NSM);
+        const auto PK = slices(R.QK, ETy::KK, ETy::NSYM, L::OFF_K, L::SK0, L::NSK);
+        const auto PT = slices(R.QT, ETy::KT, ETy::NT, L::OFF_T, L::ST0, L::NST);
+        put_operand(img, L::QMh, L::QMl, PM.data(), L::NSM * 8, ETy::NSYM, L::NSM * 8);
+        put_operand(img, L::QKh, L::QKl, PK.data(), L::NSK * 8, ETy::NSYM, L::NSK * 8);
+        put_operand(img, L::QTh, L::QTl, PT.data(), L::NST * 8, ETy::NT, L::NST * 8);
     }
     std::copy(img.begin(), img.end(), all.begin() + (size_t)ETy::TYPE * IMG_SLOT_FLOATS);
 }
