@@ -195,6 +195,38 @@ int fem_form_elements(fem_mesh* mesh, const fem_coeff* k, const void* d_u, int p
                       void* stream);
 int fem_sum_elements(fem_mesh* mesh, int prec, void* d_vM, void* d_vK, void* d_vT, void* stream);
 
+/* ------------------------------------------------------ chunked reassembly */
+/* Formation and summation over ranges: a caller can form part of the mesh
+ * and sum the slots that part completes, e.g. to start summing before all
+ * elements are formed, to interleave other work, or to keep one range's
+ * element matrices in the GPU's L2 cache while they are summed.  (On GB300
+ * the one-shot schedule of fem_assemble_all measured faster for the whole
+ * 2-million-element P2 mesh, so fem_assemble_all does not chunk.)
+ *
+ * fem_chunk_plan splits the mesh into n <= max_chunks consecutive element
+ * ranges [e_bounds[c], e_bounds[c+1]) of about target_bytes of V each
+ * (0 = the library default, 48 MB), and gives for each the slot range
+ * [s_bounds[c], s_bounds[c+1]) of CSR slots whose contributing elements all
+ * lie in ranges 0..c, i.e. the slots that can be summed once range c is
+ * formed.  e_bounds and s_bounds must hold max_chunks + 1 entries.  The plan
+ * depends only on the pattern; it is computed once per mesh (a device pass
+ * over the slots that synchronises `stream`).  Requires fem_symbolic.
+ *
+ * fem_form_elements_range forms V for elements [e_begin, e_end) (e_begin a
+ * multiple of 128) into the mesh's scratch, as fem_form_elements does for
+ * all elements; the FP32 paths split u when e_begin == 0, and later ranges of
+ * the same reassembly (same u, precision and matrices) reuse that split.
+ * fem_sum_elements_range writes the CSR values of slots [s_begin, s_end)
+ * (d_v* are the whole nnz arrays); every element contributing to those slots
+ * must have been formed.  A plan's ranges, formed and summed in order, give
+ * the same values bit for bit as fem_form_elements + fem_sum_elements. */
+int fem_chunk_plan(fem_mesh* mesh, int prec, size_t target_bytes, int max_chunks, int* n_chunks,
+                   int64_t* e_bounds, int64_t* s_bounds, void* stream);
+int fem_form_elements_range(fem_mesh* mesh, const fem_coeff* k, const void* d_u, int prec, int which,
+                            int64_t e_begin, int64_t e_end, void* stream);
+int fem_sum_elements_range(fem_mesh* mesh, int prec, int64_t s_begin, int64_t s_end, void* d_vM, void* d_vK,
+                           void* d_vT, void* stream);
+
 /* Synchronises `stream` and reports whether any library kernel recorded a
  * device-side failure since the last call: FEM_ETIMEOUT if a tensor-core
  * kernel gave up waiting on its MMA completion barrier (each such wait is

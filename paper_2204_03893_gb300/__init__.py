@@ -20,7 +20,8 @@ __all__ = [
     "fem_device_status", "fem_batch_create", "fem_batch_launch", "fem_batch_get_info", "fem_batch_destroy",
     "fem_batch_opts", "fem_batch_info", "fem_serve_opts", "fem_request", "fem_result", "fem_serve_counters",
     "fem_serve_create", "fem_serve_submit", "fem_serve_poll", "fem_serve_release", "fem_serve_evict",
-    "fem_serve_stats", "fem_serve_destroy", "FEM_REQ_ASSEMBLE", "FEM_REQ_REASSEMBLE", "fem_form_elements", "fem_sum_elements", "coeff", "FEM_MAT_M", "FEM_MAT_K", "FEM_MAT_T", "FEM_OK", "FEM_EINVAL", "FEM_ENOMEM", "FEM_EDEGENERATE", "FEM_ECUDA",
+    "fem_serve_stats", "fem_serve_destroy", "FEM_REQ_ASSEMBLE", "FEM_REQ_REASSEMBLE", "fem_form_elements", "fem_sum_elements", "fem_chunk_plan", "fem_form_elements_range",
+    "fem_sum_elements_range", "coeff", "FEM_MAT_M", "FEM_MAT_K", "FEM_MAT_T", "FEM_OK", "FEM_EINVAL", "FEM_ENOMEM", "FEM_EDEGENERATE", "FEM_ECUDA",
     "FEM_EBUSY", "FEM_EAGAIN", "FEM_ETIMEOUT", "FEM_ESTATE", "FEM_FP64", "FEM_TF32X3", "FEM_FP32",
     "FEM_MEM_HOST", "FEM_MEM_DEVICE", "FEM_K_POLY", "FEM_K_SIN", "FEM_K_PWLIN",
 ]
@@ -140,6 +141,12 @@ _SIGS = {
     "fem_assemble_all_noalloc": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p], C.c_int),
     "fem_form_elements": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_int, C.c_void_p], C.c_int),
+    "fem_chunk_plan": ([C.c_void_p, C.c_int, C.c_size_t, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64),
+                        C.POINTER(C.c_int64), C.c_void_p], C.c_int),
+    "fem_form_elements_range": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_int, C.c_int64,
+                                 C.c_int64, C.c_void_p], C.c_int),
+    "fem_sum_elements_range": ([C.c_void_p, C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_void_p], C.c_int),
     "fem_sum_elements": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fem_reference_tables": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                               C.POINTER(C.c_int)], C.c_int),
@@ -362,6 +369,25 @@ def fem_serve_stats(server: int) -> fem_serve_counters:
 
 def fem_serve_destroy(server: int) -> None:
     _check(lib().fem_serve_destroy(server))
+
+
+def fem_chunk_plan(mesh: int, prec: int, target_bytes: int = 0, max_chunks: int = 64, stream=None):
+    """(element bounds, slot bounds) of the chunked schedule, as lists of n+1."""
+    n = C.c_int()
+    eb = (C.c_int64 * (max_chunks + 1))()
+    sb = (C.c_int64 * (max_chunks + 1))()
+    _check(lib().fem_chunk_plan(mesh, prec, target_bytes, max_chunks, C.byref(n), eb, sb, _stream(stream)))
+    return list(eb[: n.value + 1]), list(sb[: n.value + 1])
+
+
+def fem_form_elements_range(mesh: int, k, d_u, prec: int, which: int, e_begin: int, e_end: int, stream=None) -> None:
+    _check(lib().fem_form_elements_range(mesh, C.byref(k) if k is not None else None, _vp(d_u), prec, which,
+                                         e_begin, e_end, _stream(stream)))
+
+
+def fem_sum_elements_range(mesh: int, prec: int, s_begin: int, s_end: int, d_vM, d_vK, d_vT, stream=None) -> None:
+    _check(lib().fem_sum_elements_range(mesh, prec, s_begin, s_end, _vp(d_vM), _vp(d_vK), _vp(d_vT),
+                                        _stream(stream)))
 
 
 def fem_device_status(stream=None) -> None:

@@ -140,7 +140,8 @@ CoeffDev to_dev(const fem_coeff* k) {
 // Formation (Algorithm 2 lines 1-11): V for the matrices in `mask` (bit 0 M,
 // bit 1 K, bit 2 T) into the mesh's scratch buffers.
 template <typename T>
-int form_t(fem_mesh* m, const fem_coeff* k, const double* ud, int prec, int mask, cudaStream_t s) {
+int form_t(fem_mesh* m, const fem_coeff* k, const double* ud, int prec, int mask, cudaStream_t s, int64_t e0 = 0,
+           int64_t e1 = -1, bool split = true) {
     const int64_t E = m->E;
     const int nsym = m->np * (m->np + 1) / 2, nt = m->np * m->np;
     int rc;
@@ -159,16 +160,16 @@ int form_t(fem_mesh* m, const fem_coeff* k, const double* ud, int prec, int mask
     }
     CoeffDev kd = to_dev(k);
     if constexpr (sizeof(T) == 8) {
-        rc = element_simt_fp64(*m, kd, ud, VM, VK, VT, s);
+        rc = element_simt_fp64(*m, kd, ud, VM, VK, VT, s, e0, e1);
     } else {
         const float2* us = nullptr;
         if (mask & 6) {
             if ((rc = buf_alloc(m->u_split, sizeof(float2) * (size_t)m->n, s))) return rc;
             us = m->u_split.as<float2>();
-            if ((rc = split_u(ud, m->n, m->u_split.as<float2>(), s))) return rc;
+            if (split && (rc = split_u(ud, m->n, m->u_split.as<float2>(), s))) return rc;
         }
-        rc = prec == FEM_TF32X3 ? element_tc_tf32x3(*m, kd, us, VM, VK, VT, s)
-                                : element_simt_fp32(*m, kd, us, VM, VK, VT, s);
+        rc = prec == FEM_TF32X3 ? element_tc_tf32x3(*m, kd, us, VM, VK, VT, s, e0, e1)
+                                : element_simt_fp32(*m, kd, us, VM, VK, VT, s, e0, e1);
     }
     if (rc) return rc;
     m->v_prec = prec;
@@ -178,13 +179,50 @@ int form_t(fem_mesh* m, const fem_coeff* k, const double* ud, int prec, int mask
 
 // Global assembly (Algorithm 2 line 12) of the formed V into CSR values.
 template <typename T>
-int sum_t(fem_mesh* m, T* vM, T* vK, T* vT, cudaStream_t s) {
+int sum_t(fem_mesh* m, T* vM, T* vK, T* vT, cudaStream_t s, int64_t s0 = 0, int64_t s1 = -1) {
     const T* VM = vM ? m->VM.as<T>() : nullptr;
     const T* VK = vK ? m->VK.as<T>() : nullptr;
     const T* VT = vT ? m->VT.as<T>() : nullptr;
-    if constexpr (sizeof(T) == 8) return scatter_fp64(*m, VM, VK, VT, vM, vK, vT, s);
-    else return scatter_fp32(*m, VM, VK, VT, vM, vK, vT, s);
+    if constexpr (sizeof(T) == 8) return scatter_fp64(*m, VM, VK, VT, vM, vK, vT, s, s0, s1);
+    else return scatter_fp32(*m, VM, VK, VT, vM, vK, vT, s, s0, s1);
 }
+
+// Element bytes of V per element (all three matrices) in a precision.
+size_t v_bytes_per_element(const fem_mesh& m, int prec) {
+    const size_t nsym = (size_t)m.np * (m.np + 1) / 2, nt = (size_t)m.np * m.np;
+    return (prec == FEM_FP64 ? 8 : 4) * (2 * nsym + nt);
+}
+
+// Chunks of the fine plan of about `target` bytes of V each (at most
+// max_chunks): element bounds eb[0..n], slot bounds sb[0..n].
+int plan_chunks(fem_mesh* m, int prec, size_t target, int max_chunks, cudaStream_t s, std::vector<int64_t>& eb,
+                std::vector<int64_t>& sb) {
+    int rc = chunk_plan_fine(*m, s);
+    if (rc) return rc;
+    const int nfine = (int)m->plan_e.size() - 1;
+    eb.clear();
+    sb.clear();
+    if (nfine <= 0) {
+        eb = {0, 0};
+        sb = {0, m->nnz > 0 ? m->nnz : 0};
+        return FEM_OK;
+    }
+    const int64_t ec = m->plan_e[1] - m->plan_e[0];
+    const size_t per_fine = (size_t)ec * v_bytes_per_element(*m, prec);
+    int g = (int)std::max<size_t>(1, target / std::max<size_t>(per_fine, 1));
+    if (max_chunks < 1) max_chunks = 1;
+    while ((nfine + g - 1) / g > max_chunks) ++g;
+    for (int j = 0;; j += g) {
+        const int jj = std::min(j, nfine);
+        eb.push_back(m->plan_e[jj]);
+        sb.push_back(m->plan_s[jj]);
+        if (jj == nfine) break;
+    }
+    return FEM_OK;
+}
+
+// default chunk size: V of one chunk stays well inside the 129 MB L2
+constexpr size_t CHUNK_TARGET_BYTES = size_t(48) << 20;
 
 template <typename T>
 int assemble_t(fem_mesh* m, const fem_coeff* k, const void* u, int prec, void* vM, void* vK, void* vT,
@@ -220,6 +258,10 @@ int assemble_t(fem_mesh* m, const fem_coeff* k, const void* u, int prec, void* v
     for (int i = 0; i < 3; ++i)
         if (outs[i]) outd[i] = out_host[i] ? m->out_stage.as<T>() + (size_t)i * nnz : static_cast<T*>(outs[i]);
     int mask = (vM ? 1 : 0) | (vK ? 2 : 0) | (vT ? 4 : 0);
+    // One formation, then one sum.  (Chunking the two phases so that each
+    // range's V is summed while in L2 -- fem_chunk_plan and the range calls
+    // -- measured slower on GB300: the sum is bound by its gather latency,
+    // not by where V lives, and every extra launch adds a tail.)
     if ((rc = form_t<T>(m, k, ud, prec, mask, s))) return rc;
     if ((rc = sum_t<T>(m, outd[0], outd[1], outd[2], s))) return rc;
     for (int i = 0; i < 3; ++i)
@@ -429,6 +471,61 @@ int fem_sum_elements(fem_mesh* m, int prec, void* d_vM, void* d_vK, void* d_vT, 
     if (prec == FEM_FP64)
         return sum_t<double>(m, static_cast<double*>(d_vM), static_cast<double*>(d_vK), static_cast<double*>(d_vT), s);
     return sum_t<float>(m, static_cast<float*>(d_vM), static_cast<float*>(d_vK), static_cast<float*>(d_vT), s);
+}
+
+int fem_chunk_plan(fem_mesh* m, int prec, size_t target_bytes, int max_chunks, int* n_chunks, int64_t* e_bounds,
+                   int64_t* s_bounds, void* stream) {
+    if (!m || !n_chunks || !e_bounds || !s_bounds) return fail(FEM_EINVAL, "NULL argument");
+    if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    if (prec != FEM_FP64 && prec != FEM_TF32X3 && prec != FEM_FP32) return fail(FEM_EINVAL, "unknown precision");
+    if (max_chunks < 1) return fail(FEM_EINVAL, "max_chunks must be >= 1");
+    std::vector<int64_t> eb, sb;
+    int rc = plan_chunks(m, prec, target_bytes ? target_bytes : CHUNK_TARGET_BYTES, max_chunks,
+                         static_cast<cudaStream_t>(stream), eb, sb);
+    if (rc) return rc;
+    *n_chunks = (int)eb.size() - 1;
+    for (size_t i = 0; i < eb.size(); ++i) {
+        e_bounds[i] = eb[i];
+        s_bounds[i] = sb[i];
+    }
+    return FEM_OK;
+}
+
+int fem_form_elements_range(fem_mesh* m, const fem_coeff* k, const void* d_u, int prec, int which, int64_t e_begin,
+                            int64_t e_end, void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (prec != FEM_FP64 && prec != FEM_TF32X3 && prec != FEM_FP32) return fail(FEM_EINVAL, "unknown precision");
+    if (which <= 0 || which > 7) return fail(FEM_EINVAL, "which must be a nonzero mask of FEM_MAT_M|K|T");
+    if (e_begin < 0 || e_begin > e_end || e_end > m->E || (e_begin % 128 != 0 && e_begin != e_end))
+        return fail(FEM_EINVAL, "element range must satisfy 0 <= begin <= end <= n_elems, begin % 128 == 0");
+    if (which & 6) {
+        int rc = check_coeff(k);
+        if (rc) return rc;
+        if (!d_u) return fail(FEM_EINVAL, "u is NULL");
+    }
+    if (e_begin > 0 && (m->v_prec != prec || m->v_mask != which))
+        return fail(FEM_ESTATE, "later ranges must follow a range starting at 0 with the same precision and matrices");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (prec == FEM_FP64)
+        return form_t<double>(m, k, static_cast<const double*>(d_u), prec, which, s, e_begin, e_end, e_begin == 0);
+    return form_t<float>(m, k, static_cast<const double*>(d_u), prec, which, s, e_begin, e_end, e_begin == 0);
+}
+
+int fem_sum_elements_range(fem_mesh* m, int prec, int64_t s_begin, int64_t s_end, void* d_vM, void* d_vK,
+                           void* d_vT, void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    if (s_begin < 0 || s_begin > s_end || s_end > m->nnz) return fail(FEM_EINVAL, "slot range out of bounds");
+    int mask = (d_vM ? 1 : 0) | (d_vK ? 2 : 0) | (d_vT ? 4 : 0);
+    if (!mask) return FEM_OK;
+    if (m->v_prec != prec || (m->v_mask & mask) != mask)
+        return fail(FEM_ESTATE, "element matrices of this precision were not formed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (prec == FEM_FP64)
+        return sum_t<double>(m, static_cast<double*>(d_vM), static_cast<double*>(d_vK), static_cast<double*>(d_vT), s,
+                             s_begin, s_end);
+    return sum_t<float>(m, static_cast<float*>(d_vM), static_cast<float*>(d_vK), static_cast<float*>(d_vT), s,
+                        s_begin, s_end);
 }
 
 int fem_assemble_mass(fem_mesh* m, int prec, void* values, void* stream) {

@@ -57,7 +57,7 @@ struct UType<float> { using type = float2; };
 // X row and V = X Q of element e (thread-private X row in shared memory).
 template <typename ETy, typename T>
 __device__ __forceinline__ void simt_element(int64_t e, const int* __restrict__ conn, const T* __restrict__ geo,
-                                             int64_t E, const typename UType<T>::type* __restrict__ u,
+                                             int64_t gs, const typename UType<T>::type* __restrict__ u,
                                              const CoeffDev& k, T mass, T* __restrict__ VM, T* __restrict__ VK,
                                              T* __restrict__ VT, T* X) {
     constexpr int D = ETy::D, NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS;
@@ -93,7 +93,7 @@ __device__ __forceinline__ void simt_element(int64_t e, const int* __restrict__ 
     T b = geo[e];
     T A[NS];
 #pragma unroll
-    for (int t = 0; t < NS; ++t) A[t] = geo[(1 + t) * E + e];
+    for (int t = 0; t < NS; ++t) A[t] = geo[(1 + t) * gs + e];
     // --- X = Lambda, Lambda (.) W, tangent factors
 #pragma unroll 1
     for (int q = 0; q < NQ; ++q) {
@@ -159,7 +159,8 @@ __device__ __forceinline__ void simt_element(int64_t e, const int* __restrict__ 
 
 template <typename ETy, typename T>
 __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict__ conn, const T* __restrict__ geo,
-                                                          int64_t E, const typename UType<T>::type* __restrict__ u,
+                                                          int64_t E, int64_t gs,
+                                                          const typename UType<T>::type* __restrict__ u,
                                                           CoeffDev k, T mass, T* __restrict__ VM, T* __restrict__ VK,
                                                           T* __restrict__ VT) {
     constexpr int KTOT = ETy::KM + ETy::KK + ETy::KT;
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict_
     for (int64_t e0 = (int64_t)blockIdx.x * BT; e0 < E; e0 += (int64_t)gridDim.x * BT) {
         int64_t e = e0 + threadIdx.x;
         if (e >= E) continue;
-        simt_element<ETy, T>(e, conn, geo, E, u, k, mass, VM, VK, VT, X);
+        simt_element<ETy, T>(e, conn, geo, gs, u, k, mass, VM, VK, VT, X);
     }
 }
 
@@ -236,7 +237,9 @@ __global__ void split_u_kernel(const double* __restrict__ u, int64_t n, float2* 
 
 template <typename ETy, typename T>
 int launch_simt(const fem_mesh& m, const CoeffDev& k, const typename UType<T>::type* u, const T* geo, T* VM, T* VK,
-                T* VT, cudaStream_t s) {
+                T* VT, cudaStream_t s, int64_t e0, int64_t e1) {
+    const int64_t E = e1 - e0;
+    if (E <= 0) return FEM_OK;
     constexpr int KTOT = ETy::KM + ETy::KK + ETy::KT;
     constexpr int LD = KTOT | 1;
     size_t smem = sizeof(T) * (size_t)LD * BT;
@@ -249,26 +252,30 @@ int launch_simt(const fem_mesh& m, const CoeffDev& k, const typename UType<T>::t
     FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, smem));
     if (per_sm < 1) per_sm = 1;
-    int64_t tiles = (m.E + BT - 1) / BT;
+    int64_t tiles = (E + BT - 1) / BT;
     int64_t grid = (int64_t)nsm * per_sm;
     if (grid > tiles) grid = tiles;
     if (grid < 1) return FEM_OK;
     cudaGetLastError();   // clear any stale error before the launch check
-    kern<<<(unsigned)grid, BT, smem, s>>>(m.conn.as<int>(), geo, m.E, u, k, (T)m.m, VM, VK, VT);
+    kern<<<(unsigned)grid, BT, smem, s>>>(m.conn.as<int>() + e0 * ETy::NP, geo + e0, E, m.E, u, k, (T)m.m,
+                                          VM ? VM + e0 * ETy::NSYM : nullptr, VK ? VK + e0 * ETy::NSYM : nullptr,
+                                          VT ? VT + e0 * ETy::NT : nullptr);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
 
 template <typename T>
 int dispatch(const fem_mesh& m, const CoeffDev& k, const typename UType<T>::type* u, const T* geo, T* VM, T* VK,
-             T* VT, cudaStream_t s) {
+             T* VT, cudaStream_t s, int64_t e0, int64_t e1) {
+    if (e1 < 0) e1 = m.E;
+    if (e0 < 0 || e0 > e1 || e1 > m.E) return fail(FEM_EINVAL, "element range out of bounds");
     switch (m.type) {
-        case 0: return launch_simt<ET<2, 1>, T>(m, k, u, geo, VM, VK, VT, s);
-        case 1: return launch_simt<ET<2, 2>, T>(m, k, u, geo, VM, VK, VT, s);
-        case 2: return launch_simt<ET<2, 3>, T>(m, k, u, geo, VM, VK, VT, s);
-        case 3: return launch_simt<ET<3, 1>, T>(m, k, u, geo, VM, VK, VT, s);
-        case 4: return launch_simt<ET<3, 2>, T>(m, k, u, geo, VM, VK, VT, s);
-        case 5: return launch_simt<ET<3, 3>, T>(m, k, u, geo, VM, VK, VT, s);
+        case 0: return launch_simt<ET<2, 1>, T>(m, k, u, geo, VM, VK, VT, s, e0, e1);
+        case 1: return launch_simt<ET<2, 2>, T>(m, k, u, geo, VM, VK, VT, s, e0, e1);
+        case 2: return launch_simt<ET<2, 3>, T>(m, k, u, geo, VM, VK, VT, s, e0, e1);
+        case 3: return launch_simt<ET<3, 1>, T>(m, k, u, geo, VM, VK, VT, s, e0, e1);
+        case 4: return launch_simt<ET<3, 2>, T>(m, k, u, geo, VM, VK, VT, s, e0, e1);
+        case 5: return launch_simt<ET<3, 3>, T>(m, k, u, geo, VM, VK, VT, s, e0, e1);
     }
     return fail(FEM_EINVAL, "element type");
 }
@@ -309,10 +316,10 @@ int tables_init_simt() {
 }
 
 int element_simt_fp64(const fem_mesh& m, const CoeffDev& k, const double* u, double* VM, double* VK, double* VT,
-                      cudaStream_t s) {
+                      cudaStream_t s, int64_t e0, int64_t e1) {
     int rc = tables_init_simt();
     if (rc) return rc;
-    return dispatch<double>(m, k, u, m.geo64.as<double>(), VM, VK, VT, s);
+    return dispatch<double>(m, k, u, m.geo64.as<double>(), VM, VK, VT, s, e0, e1);
 }
 
 int batch_simt_smem(int type, int fp64) {
@@ -357,10 +364,10 @@ int split_u(const double* u, int64_t n, float2* out, cudaStream_t s) {
 }
 
 int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
-                      cudaStream_t s) {
+                      cudaStream_t s, int64_t e0, int64_t e1) {
     int rc = tables_init_simt();
     if (rc) return rc;
-    return dispatch<float>(m, k, u, m.geo32.as<float>(), VM, VK, VT, s);
+    return dispatch<float>(m, k, u, m.geo32.as<float>(), VM, VK, VT, s, e0, e1);
 }
 
 }  // namespace fem

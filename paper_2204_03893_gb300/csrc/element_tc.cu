@@ -293,7 +293,7 @@ __device__ __forceinline__ void form_x(const float2 (&pu)[ETy::NP], const float 
 
 template <typename ETy>
 __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict__ conn, const float* __restrict__ geo,
-                                                          int64_t E, const float2* __restrict__ u, CoeffDev k,
+                                                          int64_t E, int64_t gs, const float2* __restrict__ u, CoeffDev k,
                                                           float mass, float* __restrict__ VM, float* __restrict__ VK,
                                                           float* __restrict__ VT, const float* __restrict__ img,
                                                           int* __restrict__ err) {
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
 #pragma unroll
             for (int i = 0; i < NP; ++i) pidx[i] = need_u ? __ldg(ce + i) : 0;
 #pragma unroll
-            for (int t2 = 0; t2 <= NS; ++t2) pgeo[t2] = __ldg(geo + t2 * E + e);
+            for (int t2 = 0; t2 <= NS; ++t2) pgeo[t2] = __ldg(geo + t2 * gs + e);
         }
     };
     auto fetch_u = [&]() {
@@ -644,6 +644,7 @@ __device__ __forceinline__ void form_chunk_t(int q0, const float (&du)[ETy::NP],
 // then tell which barrier still has an operation in flight.
 template <typename ETy>
 __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const float* __restrict__ geo, int64_t E,
+                                             int64_t gs,
                                              const float2* __restrict__ u, const CoeffDev& k, float mass,
                                              float* __restrict__ VM, float* __restrict__ VK, float* __restrict__ VT,
                                              const unsigned char* __restrict__ img, int64_t first,
@@ -666,7 +667,7 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
     if (e < E) {
         b = __ldg(geo + e);
 #pragma unroll
-        for (int t = 0; t < NS; ++t) A[t] = __ldg(geo + (int64_t)(1 + t) * E + e);
+        for (int t = 0; t < NS; ++t) A[t] = __ldg(geo + (int64_t)(1 + t) * gs + e);
         if (need_u) {
             const int* ce = conn + e * NP;
             const float2 p0 = __ldg(u + __ldg(ce));
@@ -762,7 +763,7 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
 
 template <typename ETy>
 __global__ void __launch_bounds__(TILE, 1) element_tc_chunked_kernel(
-    const int* __restrict__ conn, const float* __restrict__ geo, int64_t E, const float2* __restrict__ u,
+    const int* __restrict__ conn, const float* __restrict__ geo, int64_t E, int64_t gs, const float2* __restrict__ u,
     CoeffDev k, float mass, float* __restrict__ VM, float* __restrict__ VK, float* __restrict__ VT,
     const unsigned char* __restrict__ img, int* __restrict__ err) {
     using L = ChL<ETy>;
@@ -788,7 +789,7 @@ __global__ void __launch_bounds__(TILE, 1) element_tc_chunked_kernel(
     bool pend_q = false, pend_mma = false, ok = true;
     const int64_t ntiles = (E + TILE - 1) / TILE;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
-        ok = chunked_tile<ETy>(conn, geo, E, u, k, mass, VM, VK, VT, img, tile * TILE, smem, tmem, mb_mma, mb_q,
+        ok = chunked_tile<ETy>(conn, geo, E, gs, u, k, mass, VM, VK, VT, img, tile * TILE, smem, tmem, mb_mma, mb_q,
                                ph_mma, ph_q, pend_q, pend_mma);
     if (!ok) {
         if (tid == 0) atomicExch(err, 1);
@@ -838,7 +839,7 @@ __global__ void __launch_bounds__(TILE, 1) batch_tc_chunked_kernel(const BatchIt
         float* VK = bm.vK ? static_cast<float*>(bm.VK) : nullptr;
         float* VT = bm.vT ? static_cast<float*>(bm.VT) : nullptr;
         if (!(VM || VK || VT)) continue;   // mesh skipped in this launch
-        ok = chunked_tile<ETy>(bm.conn, bm.geo32, bm.E, bm.u2, bm.k, (float)bm.mass, VM, VK, VT, img, w.first, smem,
+        ok = chunked_tile<ETy>(bm.conn, bm.geo32, bm.E, bm.E, bm.u2, bm.k, (float)bm.mass, VM, VK, VT, img, w.first, smem,
                                tmem, mb_mma, mb_q, ph_mma, ph_q, pend_q, pend_mma);
     }
     if (!ok) {
@@ -960,9 +961,10 @@ int cached_shape(std::atomic<int>* have, LaunchShape* cache, std::mutex& mu, F c
 
 template <typename ETy>
 int launch_tc_chunked(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
-                      cudaStream_t s) {
+                      cudaStream_t s, int64_t e0, int64_t e1) {
     using L = ChL<ETy>;
-    if (m.E == 0) return FEM_OK;
+    const int64_t E = e1 - e0;
+    if (E <= 0) return FEM_OK;
     auto kern = element_tc_chunked_kernel<ETy>;
     static std::atomic<int> have[64];
     static LaunchShape cache[64];
@@ -993,28 +995,31 @@ int launch_tc_chunked(const fem_mesh& m, const CoeffDev& k, const float2* u, flo
         return FEM_OK;
     }, sh);
     if (rc) return rc;
-    const int64_t ntiles = (m.E + TILE - 1) / TILE;
+    const int64_t ntiles = (E + TILE - 1) / TILE;
     int64_t grid = sh.nsm;
     if (grid > ntiles) grid = ntiles;
     trace_launch("element_tc_chunked_kernel", grid, TILE, sh.smem, 1);
     cudaGetLastError();   // clear any stale error before the launch check
-    kern<<<(unsigned)grid, TILE, sh.smem, s>>>(m.conn.as<int>(), m.geo32.as<float>(), m.E, u, k, (float)m.m, VM, VK,
-                                               VT, static_cast<const unsigned char*>(sh.img), sh.err);
+    kern<<<(unsigned)grid, TILE, sh.smem, s>>>(m.conn.as<int>() + e0 * ETy::NP, m.geo32.as<float>() + e0, E, m.E, u, k,
+                                               (float)m.m, VM ? VM + e0 * ETy::NSYM : nullptr,
+                                               VK ? VK + e0 * ETy::NSYM : nullptr, VT ? VT + e0 * ETy::NT : nullptr,
+                                               static_cast<const unsigned char*>(sh.img), sh.err);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
 
 template <typename ETy>
 int launch_tc(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
-              cudaStream_t s) {
+              cudaStream_t s, int64_t e0, int64_t e1) {
     using L = TcL<ETy>;
     if constexpr (!L::FITS) {
         if constexpr (ChL<ETy>::OK && ChL<ETy>::IMG_BYTES == CHUNK_IMG_BYTES)
-            return launch_tc_chunked<ETy>(m, k, u, VM, VK, VT, s);
+            return launch_tc_chunked<ETy>(m, k, u, VM, VK, VT, s, e0, e1);
         else
             return fail(FEM_EINVAL, "FEM_TF32X3 is not available for this element type (tile does not fit)");
     } else {
-        if (m.E == 0) return FEM_OK;
+        const int64_t E = e1 - e0;
+        if (E <= 0) return FEM_OK;
         auto kern = element_tc_kernel<ETy>;
         constexpr int SMEM0 = L::SMEM;
         constexpr int ALLOC0 = L::ALLOC;
@@ -1063,13 +1068,16 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, 
             return FEM_OK;
         }, sh);
         if (rc) return rc;
-        const int64_t ntiles = (m.E + TILE - 1) / TILE;
+        const int64_t ntiles = (E + TILE - 1) / TILE;
         int64_t grid = (int64_t)sh.nsm * sh.occ;
         if (grid > ntiles) grid = ntiles;
         trace_launch("element_tc_kernel", grid, TILE, sh.smem, sh.occ);
         cudaGetLastError();   // clear any stale error before the launch check
-        kern<<<(unsigned)grid, TILE, sh.smem, s>>>(m.conn.as<int>(), m.geo32.as<float>(), m.E, u, k, (float)m.m, VM,
-                                                   VK, VT, static_cast<const float*>(sh.img), sh.err);
+        kern<<<(unsigned)grid, TILE, sh.smem, s>>>(m.conn.as<int>() + e0 * ETy::NP, m.geo32.as<float>() + e0, E, m.E, u,
+                                                   k, (float)m.m, VM ? VM + e0 * ETy::NSYM : nullptr,
+                                                   VK ? VK + e0 * ETy::NSYM : nullptr,
+                                                   VT ? VT + e0 * ETy::NT : nullptr, static_cast<const float*>(sh.img),
+                                                   sh.err);
         FEM_CUDA_TRY(cudaGetLastError());
         return FEM_OK;
     }
@@ -1238,16 +1246,18 @@ int tc_error_flag(int clear) {
 }
 
 int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
-                      cudaStream_t s) {
+                      cudaStream_t s, int64_t e0, int64_t e1) {
+    if (e1 < 0) e1 = m.E;
+    if (e0 < 0 || e0 > e1 || e1 > m.E) return fail(FEM_EINVAL, "element range out of bounds");
     int rc = tables_init_tc();
     if (rc) return rc;
     switch (m.type) {
-        case 0: return launch_tc<ET<2, 1>>(m, k, u, VM, VK, VT, s);
-        case 1: return launch_tc<ET<2, 2>>(m, k, u, VM, VK, VT, s);
-        case 2: return launch_tc<ET<2, 3>>(m, k, u, VM, VK, VT, s);
-        case 3: return launch_tc<ET<3, 1>>(m, k, u, VM, VK, VT, s);
-        case 4: return launch_tc<ET<3, 2>>(m, k, u, VM, VK, VT, s);
-        case 5: return launch_tc<ET<3, 3>>(m, k, u, VM, VK, VT, s);
+        case 0: return launch_tc<ET<2, 1>>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 1: return launch_tc<ET<2, 2>>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 2: return launch_tc<ET<2, 3>>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 3: return launch_tc<ET<3, 1>>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 4: return launch_tc<ET<3, 2>>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 5: return launch_tc<ET<3, 3>>(m, k, u, VM, VK, VT, s, e0, e1);
     }
     return fail(FEM_EINVAL, "element type");
 }

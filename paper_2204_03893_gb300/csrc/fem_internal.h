@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/fem.h"
 #include "fem_device.cuh"
@@ -61,6 +62,9 @@ struct fem_mesh {
     int max_row = 0;                    // longest CSR row
     int sum_kernel = 0;                 // CSR sum variant: 0 = per-slot segments, 1 = row-wise (needs loff)
     int sum_block = 256;                // threads per block of the CSR sum
+    // chunk plan: fine element chunks and the slot prefix each one completes
+    bool have_plan = false;
+    std::vector<int64_t> plan_e, plan_s;
     // numeric scratch: element matrices V (per matrix) in the precision of the last call
     fem::DevBuf VM, VK, VT;
     int v_prec = -1, v_mask = 0;        // what VM/VK/VT currently hold
@@ -78,19 +82,28 @@ int symbolic_run(fem_mesh& m, cudaStream_t s);           // fills pattern and se
 
 // Element products V = X Q.  Any of VM, VK, VT may be null (matrix skipped).
 int element_simt_fp64(const fem_mesh& m, const CoeffDev& k, const double* u, double* VM, double* VK, double* VT,
-                      cudaStream_t s);
+                      cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);
 // FP32 paths take the nodal values split as u = hi + lo (float2), see split_u.
 int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
-                      cudaStream_t s);
+                      cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);
+// e0, e1: element range [e0, e1) (e1 = -1: to the end); V pointers are the
+// whole-mesh arrays, rows e0.. are written.
 int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
-                      cudaStream_t s);
+                      cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);
 int split_u(const double* u, int64_t n, float2* out, cudaStream_t s);
 
 // Segmented reduction of V into CSR values (outputs may be null).
+// s0, s1: slot range [s0, s1) (s1 = -1: to the end); outputs are the
+// whole CSR arrays.
 int scatter_fp64(const fem_mesh& m, const double* VM, const double* VK, const double* VT, double* vM, double* vK,
-                 double* vT, cudaStream_t s);
+                 double* vT, cudaStream_t s, int64_t s0 = 0, int64_t s1 = -1);
 int scatter_fp32(const fem_mesh& m, const float* VM, const float* VK, const float* VT, float* vM, float* vK,
-                 float* vT, cudaStream_t s);
+                 float* vT, cudaStream_t s, int64_t s0 = 0, int64_t s1 = -1);
+
+// Fine chunk plan of a mesh (once): plan_e[j] = first element of fine chunk
+// j, plan_s[j] = number of slots whose contributors all lie in chunks < j.
+constexpr int PLAN_MAX_FINE = 64;
+int chunk_plan_fine(fem_mesh& m, cudaStream_t s);
 
 // Coefficient validation and device form, shared by the C entry points.
 int validate_coeff(const fem_coeff* k);

@@ -20,6 +20,9 @@
 // out with coalesced stores.
 // Segment kernel (default): one thread per slot sums the slot's contributor
 // list contrib[seg_ptr[s] .. seg_ptr[s+1]) (element entries, ascending).
+#include <algorithm>
+#include <vector>
+
 #include "fem_internal.h"
 
 namespace fem {
@@ -275,8 +278,9 @@ __global__ void __launch_bounds__(512) batch_scatter_kernel(const BatchItem* __r
 
 template <int NP, typename T>
 int launch_np(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s,
-              int nsm) {
-    if (m.sum_kernel == 1 && m.loff.ptr && m.max_row > 0) {
+              int nsm, int64_t s0, int64_t s1) {
+    const bool whole = s0 == 0 && s1 == m.nnz;
+    if (whole && m.sum_kernel == 1 && m.loff.ptr && m.max_row > 0) {
         // threads per block: as many rows as fit ~64 KiB of accumulators (3 matrices)
         int B = m.sum_block > 0 ? m.sum_block : 256;
         while (B > 32 && (size_t)3 * B * m.max_row * sizeof(T) > 64 * 1024) B /= 2;
@@ -294,29 +298,37 @@ int launch_np(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T
         kern<<<(unsigned)blocks, B, smem, s>>>(m.inc_ptr.as<int>(), m.inc.as<int>(), m.row_ptr.as<int>(),
                                               m.loff.as<unsigned char>(), m.n, m.max_row, VM, VK, VT, vM, vK, vT);
     } else {
+        // a slot range [s0, s1): the segment bounds and the outputs offset
+        // by s0 (contributor indices address the whole V)
         const int B = (m.sum_kernel == 0 && m.sum_block >= 32) ? m.sum_block : 256;
-        int64_t blocks = (m.nnz + B - 1) / B;
+        const int64_t ns = s1 - s0;
+        if (ns <= 0) return FEM_OK;
+        int64_t blocks = (ns + B - 1) / B;
         if (blocks > (int64_t)nsm * (4096 / B)) blocks = (int64_t)nsm * (4096 / B);
         cudaGetLastError();   // clear any stale error before the launch check
         scatter_segments_kernel<NP, T><<<(unsigned)blocks, B, 0, s>>>(
-            m.seg_ptr.as<int>(), m.contrib.as<int>(), m.nnz, VM, VK, VT, vM, vK, vT);
+            m.seg_ptr.as<int>() + s0, m.contrib.as<int>(), ns, VM, VK, VT, vM ? vM + s0 : nullptr,
+            vK ? vK + s0 : nullptr, vT ? vT + s0 : nullptr);
     }
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
 
 template <typename T>
-int run(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s) {
-    if (m.nnz <= 0) return FEM_OK;
+int run(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s, int64_t s0,
+        int64_t s1) {
+    if (s1 < 0) s1 = m.nnz;
+    if (s0 < 0 || s0 > s1 || s1 > m.nnz) return fail(FEM_EINVAL, "slot range out of bounds");
+    if (m.nnz <= 0 || s1 == s0) return FEM_OK;
     int dev = 0, nsm = 0;
     FEM_CUDA_TRY(cudaGetDevice(&dev));
     FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     switch (m.np) {
-        case 3: return launch_np<3, T>(m, VM, VK, VT, vM, vK, vT, s, nsm);
-        case 4: return launch_np<4, T>(m, VM, VK, VT, vM, vK, vT, s, nsm);
-        case 6: return launch_np<6, T>(m, VM, VK, VT, vM, vK, vT, s, nsm);
-        case 10: return launch_np<10, T>(m, VM, VK, VT, vM, vK, vT, s, nsm);
-        case 20: return launch_np<20, T>(m, VM, VK, VT, vM, vK, vT, s, nsm);
+        case 3: return launch_np<3, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+        case 4: return launch_np<4, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+        case 6: return launch_np<6, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+        case 10: return launch_np<10, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+        case 20: return launch_np<20, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
     }
     return fail(FEM_EINVAL, "unsupported n_p");
 }
@@ -341,13 +353,77 @@ template int batch_scatter_launch<float>(const BatchItem*, int, const BatchMesh*
 template int batch_scatter_launch<double>(const BatchItem*, int, const BatchMesh*, int, cudaStream_t);
 
 int scatter_fp64(const fem_mesh& m, const double* VM, const double* VK, const double* VT, double* vM, double* vK,
-                 double* vT, cudaStream_t s) {
-    return run<double>(m, VM, VK, VT, vM, vK, vT, s);
+                 double* vT, cudaStream_t s, int64_t s0, int64_t s1) {
+    return run<double>(m, VM, VK, VT, vM, vK, vT, s, s0, s1);
 }
 
 int scatter_fp32(const fem_mesh& m, const float* VM, const float* VK, const float* VT, float* vM, float* vK,
-                 float* vT, cudaStream_t s) {
-    return run<float>(m, VM, VK, VT, vM, vK, vT, s);
+                 float* vT, cudaStream_t s, int64_t s0, int64_t s1) {
+    return run<float>(m, VM, VK, VT, vM, vK, vT, s, s0, s1);
+}
+
+
+namespace {
+
+// For every slot, the fine element chunk of its last (largest) contributor;
+// per chunk, the smallest slot that needs it (block minimum in shared
+// memory, then one atomic per block and chunk).
+__global__ void slot_ready_kernel(const int* __restrict__ seg_ptr, const int* __restrict__ contrib, int64_t nnz,
+                                  int nt, int64_t ec, int nfine, int* __restrict__ first_slot) {
+    __shared__ int smin[PLAN_MAX_FINE];
+    for (int i = threadIdx.x; i < nfine; i += blockDim.x) smin[i] = 0x7fffffff;
+    __syncthreads();
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x) {
+        const int b = seg_ptr[s + 1];
+        if (b <= seg_ptr[s]) continue;
+        const int64_t e = contrib[b - 1] / nt;
+        const int j = (int)(e / ec);
+        atomicMin(&smin[j < nfine ? j : nfine - 1], (int)s);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nfine; i += blockDim.x)
+        if (smin[i] != 0x7fffffff) atomicMin(&first_slot[i], smin[i]);
+}
+
+}  // namespace
+
+int chunk_plan_fine(fem_mesh& m, cudaStream_t s) {
+    if (m.have_plan) return FEM_OK;
+    const int64_t E = m.E;
+    const int nt = m.np * m.np;
+    int64_t ec = ((E + PLAN_MAX_FINE - 1) / PLAN_MAX_FINE + 127) / 128 * 128;
+    if (ec < 128) ec = 128;
+    const int nfine = E > 0 ? (int)((E + ec - 1) / ec) : 0;
+    m.plan_e.assign(nfine + 1, 0);
+    m.plan_s.assign(nfine + 1, 0);
+    for (int j = 0; j <= nfine; ++j) m.plan_e[j] = std::min<int64_t>((int64_t)j * ec, E);
+    if (nfine > 0) m.plan_s[nfine] = m.nnz;
+    if (nfine > 1 && m.nnz > 0) {
+        DevBuf fs;
+        int rc = buf_alloc(fs, sizeof(int) * nfine, s);
+        if (rc) return rc;
+        std::vector<int> host(nfine, 0x7fffffff);
+        FEM_CUDA_TRY(cudaMemcpyAsync(fs.ptr, host.data(), sizeof(int) * nfine, cudaMemcpyHostToDevice, s));
+        int64_t blocks = (m.nnz + 255) / 256;
+        if (blocks > 152 * 8) blocks = 152 * 8;
+        cudaGetLastError();   // clear any stale error before the launch check
+        slot_ready_kernel<<<(unsigned)blocks, 256, 0, s>>>(m.seg_ptr.as<int>(), m.contrib.as<int>(), m.nnz, nt, ec,
+                                                          nfine, fs.as<int>());
+        FEM_CUDA_TRY(cudaGetLastError());
+        FEM_CUDA_TRY(cudaMemcpyAsync(host.data(), fs.ptr, sizeof(int) * nfine, cudaMemcpyDeviceToHost, s));
+        FEM_CUDA_TRY(cudaStreamSynchronize(s));
+        buf_free(fs, s);
+        // slots ready once chunks 0..j-1 are formed: those below the first
+        // slot needing any chunk >= j (suffix minimum)
+        int64_t run = m.nnz;
+        for (int j = nfine - 1; j >= 0; --j) {
+            run = std::min<int64_t>(run, host[j]);
+            m.plan_s[j] = run;
+        }
+        m.plan_s[0] = 0;
+    }
+    m.have_plan = true;
+    return FEM_OK;
 }
 
 }  // namespace fem

@@ -192,8 +192,8 @@ int start_request(fem_server* S, Request& r, Resident* res, fem_mesh** created, 
         if (e != cudaSuccess) return cuda_fail(e, "upload u");
         du = res->u.as<double>();
     }
-    if ((rc = fem_form_elements(m, &r.k, du, prec, r.which, st))) return rc;
-    if ((rc = fem_sum_elements(m, prec, r.out[0].ptr, r.out[1].ptr, r.out[2].ptr, st))) return rc;
+    // device pointers: fem_assemble_all enqueues without synchronising
+    if ((rc = fem_assemble_all(m, &r.k, du, prec, r.out[0].ptr, r.out[1].ptr, r.out[2].ptr, st))) return rc;
     cudaError_t e = cudaEventRecord(r.done, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     return FEM_OK;
