@@ -380,7 +380,10 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
             tc::mma_commit(mb);
         }
         if (next < ntiles) fetch_u();
-        const uint32_t ok = tc::mbar_wait_bounded(mb, phase, WAIT_LIMIT);
+        // one thread waits (the other warps sleep at the barrier instead of
+        // spinning on the mbarrier and taking issue slots from other CTAs)
+        uint32_t ok = 1;
+        if (tid == 0) ok = tc::mbar_wait_bounded(mb, phase, WAIT_LIMIT);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {
             timed_out = true;
@@ -445,7 +448,8 @@ __device__ __forceinline__ bool batch_tc_tile(const BatchMesh& bm, int64_t first
         issue_tile<L>(tmem, sXu, sQu, doM, doK, doT);
         tc::mma_commit(mb);
     }
-    const uint32_t ok = tc::mbar_wait_bounded(mb, phase, WAIT_LIMIT);
+    uint32_t ok = 1;
+    if (tid == 0) ok = tc::mbar_wait_bounded(mb, phase, WAIT_LIMIT);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) return false;
     tc::fence_after_sync();
@@ -712,7 +716,8 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
                 store_row<L::KcT>(sX, sX + TILE * L::KcT * 4, x, tid);
             }
             tc::fence_proxy_async_smem();
-            const uint32_t okq = tc::mbar_wait_bounded(mb_q, ph_q, WAIT_LIMIT);
+            uint32_t okq = 1;
+            if (tid == 0) okq = tc::mbar_wait_bounded(mb_q, ph_q, WAIT_LIMIT);
             tc::fence_before_sync();
             if (__syncthreads_or(!okq)) return false;
             ph_q ^= 1u;
@@ -739,7 +744,8 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
                 tc::mma_commit(mb_mma);
             }
             pend_mma = true;
-            const uint32_t okm = tc::mbar_wait_bounded(mb_mma, ph_mma, WAIT_LIMIT);
+            uint32_t okm = 1;
+            if (tid == 0) okm = tc::mbar_wait_bounded(mb_mma, ph_mma, WAIT_LIMIT);
             if (__syncthreads_or(!okm)) return false;
             ph_mma ^= 1u;
             pend_mma = false;

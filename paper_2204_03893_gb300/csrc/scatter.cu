@@ -113,13 +113,15 @@ __global__ void __launch_bounds__(256) scatter_rows_kernel(const int* __restrict
 template <int NP, typename T>
 struct Contribution {
     T m, k, t;
-    __device__ __forceinline__ void load(int c, const short* __restrict__ sym, const T* __restrict__ VM,
+    // 32-bit unsigned index arithmetic (element entries, slots and V
+    // offsets of a mesh are below 2^31)
+    __device__ __forceinline__ void load(uint32_t c, const short* __restrict__ sym, const T* __restrict__ VM,
                                          const T* __restrict__ VK, const T* __restrict__ VT) {
-        constexpr int NT = NP * NP, NSYM = NP * (NP + 1) / 2;
+        constexpr uint32_t NT = NP * NP, NSYM = NP * (NP + 1) / 2;
         t = VT ? __ldg(VT + c) : T(0);
         if (VM || VK) {
-            const int e = c / NT;
-            const int64_t off = (int64_t)e * NSYM + sym[c - e * NT];
+            const uint32_t e = c / NT;
+            const uint32_t off = e * NSYM + (uint32_t)sym[c - e * NT];
             m = VM ? __ldg(VM + off) : T(0);
             k = VK ? __ldg(VK + off) : T(0);
         } else {
@@ -142,7 +144,7 @@ __device__ __forceinline__ void fill_sym_table(short* sym) {
 // order per slot (ascending contributor) is unchanged.
 template <int NP, typename T>
 __global__ void __launch_bounds__(256) scatter_segments_kernel(const int* __restrict__ seg_ptr,
-                                                               const int* __restrict__ contrib, int64_t nnz,
+                                                               const int* __restrict__ contrib, int64_t nnz64,
                                                                const T* __restrict__ VM, const T* __restrict__ VK,
                                                                const T* __restrict__ VT, T* __restrict__ vM,
                                                                T* __restrict__ vK, T* __restrict__ vT) {
@@ -152,48 +154,52 @@ __global__ void __launch_bounds__(256) scatter_segments_kernel(const int* __rest
     const T* vm_src = vM ? VM : nullptr;
     const T* vk_src = vK ? VK : nullptr;
     const T* vt_src = vT ? VT : nullptr;
-    const int64_t G = (int64_t)gridDim.x * blockDim.x;
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    constexpr uint32_t NONE = 0xffffffffu;
+    const uint32_t nnz = (uint32_t)nnz64;   // < 2^31 (int32 CSR)
+    const uint32_t G = gridDim.x * blockDim.x;
+    uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nnz) return;
+    const uint32_t* sp = reinterpret_cast<const uint32_t*>(seg_ptr);
+    const uint32_t* cp = reinterpret_cast<const uint32_t*>(contrib);
     // pipeline registers: bounds of s and s+G, first two contributors of s
-    int a0 = __ldg(seg_ptr + s), b0 = __ldg(seg_ptr + s + 1);
-    int a1 = 0, b1 = 0;
+    uint32_t a0 = __ldg(sp + s), b0 = __ldg(sp + s + 1);
+    uint32_t a1 = 0, b1 = 0;
     if (s + G < nnz) {
-        a1 = __ldg(seg_ptr + s + G);
-        b1 = __ldg(seg_ptr + s + G + 1);
+        a1 = __ldg(sp + s + G);
+        b1 = __ldg(sp + s + G + 1);
     }
-    int c0 = a0 < b0 ? __ldg(contrib + a0) : -1;
-    int c1 = a0 + 1 < b0 ? __ldg(contrib + a0 + 1) : -1;
+    uint32_t c0 = a0 < b0 ? __ldg(cp + a0) : NONE;
+    uint32_t c1 = a0 + 1 < b0 ? __ldg(cp + a0 + 1) : NONE;
     while (true) {
-        const int64_t s1 = s + G, s2 = s + 2 * G;
+        const uint32_t s1 = s + G, s2 = s + 2 * G;
         // in flight together: V of slot s, contributors of s+G, bounds of s+2G
         Contribution<NP, T> x0, x1;
-        if (c0 >= 0) x0.load(c0, sym, vm_src, vk_src, vt_src);
-        if (c1 >= 0) x1.load(c1, sym, vm_src, vk_src, vt_src);
-        int n0 = -1, n1 = -1;
+        if (c0 != NONE) x0.load(c0, sym, vm_src, vk_src, vt_src);
+        if (c1 != NONE) x1.load(c1, sym, vm_src, vk_src, vt_src);
+        uint32_t n0 = NONE, n1 = NONE;
         if (s1 < nnz) {
-            n0 = a1 < b1 ? __ldg(contrib + a1) : -1;
-            n1 = a1 + 1 < b1 ? __ldg(contrib + a1 + 1) : -1;
+            n0 = a1 < b1 ? __ldg(cp + a1) : NONE;
+            n1 = a1 + 1 < b1 ? __ldg(cp + a1 + 1) : NONE;
         }
-        int a2 = 0, b2 = 0;
+        uint32_t a2 = 0, b2 = 0;
         if (s2 < nnz) {
-            a2 = __ldg(seg_ptr + s2);
-            b2 = __ldg(seg_ptr + s2 + 1);
+            a2 = __ldg(sp + s2);
+            b2 = __ldg(sp + s2 + 1);
         }
         T am = T(0), ak = T(0), at = T(0);
-        if (c0 >= 0) {
+        if (c0 != NONE) {
             am += x0.m;
             ak += x0.k;
             at += x0.t;
         }
-        if (c1 >= 0) {
+        if (c1 != NONE) {
             am += x1.m;
             ak += x1.k;
             at += x1.t;
         }
-        for (int p = a0 + 2; p < b0; ++p) {
+        for (uint32_t p = a0 + 2; p < b0; ++p) {
             Contribution<NP, T> x;
-            x.load(__ldg(contrib + p), sym, vm_src, vk_src, vt_src);
+            x.load(__ldg(cp + p), sym, vm_src, vk_src, vt_src);
             am += x.m;
             ak += x.k;
             at += x.t;
@@ -201,7 +207,7 @@ __global__ void __launch_bounds__(256) scatter_segments_kernel(const int* __rest
         if (vM) vM[s] = am;
         if (vK) vK[s] = ak;
         if (vT) vT[s] = at;
-        if (s1 >= nnz) break;
+        if (s1 >= nnz || s1 < s) break;
         s = s1;
         a0 = a1;
         b0 = b1;
@@ -224,7 +230,7 @@ __device__ __forceinline__ void segment_slot(int64_t s, const int* __restrict__ 
     T am = T(0), ak = T(0), at = T(0);
     for (int p = a; p < b; ++p) {
         Contribution<NP, T> x;
-        x.load(__ldg(contrib + p), sym, VM, VK, VT);
+        x.load((uint32_t)__ldg(contrib + p), sym, VM, VK, VT);
         am += x.m;
         ak += x.k;
         at += x.t;
