@@ -22,6 +22,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <set>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -52,6 +53,11 @@ struct Resident {
     int busy = 0;             // a request of this mesh is in flight
     bool evicted = false;     // fem_serve_evict was called; destroyed once idle
     size_t bytes = 0;         // device bytes accounted for the mesh
+    // pending requests of the mesh: the oldest is in the server's ready set
+    // while the mesh is idle, the others wait here in submission order
+    bool in_ready = false;
+    uint64_t ready_ticket = 0;
+    std::deque<uint64_t> waiting;
 };
 
 struct Request {
@@ -129,7 +135,8 @@ struct fem_server {
     bool stop = false;
     std::thread th;
     uint64_t next_ticket = 1, next_mesh = 1;
-    std::deque<uint64_t> queue;                                  // pending tickets, arrival order
+    std::set<uint64_t> ready;                                    // startable tickets, arrival order
+    size_t pending = 0;                                          // submitted, not started
     std::map<uint64_t, std::unique_ptr<Request>> reqs;
     std::map<uint64_t, Resident> meshes;
     std::vector<cudaStream_t> streams;
@@ -192,8 +199,8 @@ int start_request(fem_server* S, Request& r, Resident* res, fem_mesh** created, 
         if (e != cudaSuccess) return cuda_fail(e, "upload u");
         du = res->u.as<double>();
     }
-    // device pointers: fem_assemble_all enqueues without synchronising
-    if ((rc = fem_assemble_all(m, &r.k, du, prec, r.out[0].ptr, r.out[1].ptr, r.out[2].ptr, st))) return rc;
+    if ((rc = fem_form_elements(m, &r.k, du, prec, r.which, st))) return rc;
+    if ((rc = fem_sum_elements(m, prec, r.out[0].ptr, r.out[1].ptr, r.out[2].ptr, st))) return rc;
     cudaError_t e = cudaEventRecord(r.done, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     return FEM_OK;
@@ -215,6 +222,34 @@ void finish(fem_server* S, Request& r, int status, const std::string& msg) {
     r.t_done = now_us(S);
 }
 
+// Puts a request of an idle mesh (or an ASSEMBLE) into the ready set, or
+// queues it behind the mesh's pending requests.  Lock held.
+void enqueue_request(fem_server* S, Request& r) {
+    if (r.kind == FEM_REQ_REASSEMBLE) {
+        Resident& res = S->meshes[r.mesh_id];
+        if (res.busy || res.in_ready) {
+            res.waiting.push_back(r.ticket);
+            return;
+        }
+        res.in_ready = true;
+        res.ready_ticket = r.ticket;
+    }
+    S->ready.insert(r.ticket);
+}
+
+// The mesh has no request in flight any more: its next pending request (if
+// any) becomes startable.  Lock held.
+void mesh_idle(fem_server* S, Resident& res) {
+    res.busy = 0;
+    if (!res.in_ready && !res.waiting.empty()) {
+        const uint64_t t = res.waiting.front();
+        res.waiting.pop_front();
+        res.in_ready = true;
+        res.ready_ticket = t;
+        S->ready.insert(t);
+    }
+}
+
 // Moves finished requests to DONE.  Lock held.
 bool reap(fem_server* S) {
     bool progress = false;
@@ -229,7 +264,7 @@ bool reap(fem_server* S) {
         else finish(S, r, FEM_ECUDA, std::string("request failed on the device: ") + cudaGetErrorString(q));
         --S->inflight;
         Resident& res = S->meshes[r.mesh_id];
-        res.busy = 0;
+        mesh_idle(S, res);
         // account the mesh at its real size once it exists
         const size_t real = res.mesh ? res.mesh->device_bytes() : 0;
         if (real && real != res.bytes) {
@@ -243,70 +278,71 @@ bool reap(fem_server* S) {
     return progress;
 }
 
-// Admits one queued request if one can start now (arrival order; a request
-// waits while another request of its mesh is in flight; when the head of the
-// line does not fit the budget, nothing behind it is admitted).  Starts it
-// with the lock released.  Returns false if nothing could be admitted.
+// Admits the oldest startable request if it can start now (requests of a
+// mesh that is busy are not startable; when the oldest startable request does
+// not fit the budget, nothing behind it is admitted).  Starts it with the lock
+// released.  Returns false if nothing could be admitted.
 bool admit_one(fem_server* S, std::unique_lock<std::mutex>& lk) {
-    if (S->inflight >= S->opts.max_inflight) return false;
-    for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
-        Request& r = *S->reqs[*it];
-        Resident* res = nullptr;
-        if (r.kind == FEM_REQ_REASSEMBLE) {
-            auto m = S->meshes.find(r.mesh_id);
-            if (m == S->meshes.end() || m->second.evicted) {
-                finish(S, r, FEM_EINVAL, "mesh was evicted before the request started");
-                S->queue.erase(it);
-                return true;
-            }
-            res = &m->second;
-            if (res->busy) continue;
+    if (S->inflight >= S->opts.max_inflight || S->ready.empty()) return false;
+    const uint64_t ticket = *S->ready.begin();
+    Request& r = *S->reqs[ticket];
+    Resident* res = nullptr;
+    if (r.kind == FEM_REQ_REASSEMBLE) {
+        auto m = S->meshes.find(r.mesh_id);
+        if (m == S->meshes.end() || m->second.evicted) {
+            S->ready.erase(S->ready.begin());
+            --S->pending;
+            finish(S, r, FEM_EINVAL, "mesh was evicted before the request started");
+            return true;
         }
-        if (S->in_use + r.est_bytes > S->opts.budget_bytes) return false;
-        if (r.kind == FEM_REQ_ASSEMBLE) {
-            r.mesh_id = S->next_mesh++;
-            res = &S->meshes[r.mesh_id];
-            res->bytes = r.est_bytes - r.out_bytes;
-        }
-        res->busy = 1;
-        S->in_use += r.est_bytes;
-        S->peak = std::max(S->peak, S->in_use);
-        r.state = RUNNING;
-        r.t_start = now_us(S);
-        r.stream = S->rr;
-        S->rr = (S->rr + 1) % (int)S->streams.size();
-        ++S->inflight;
-        S->queue.erase(it);
-        cudaStream_t st = S->streams[r.stream];
-        fem_mesh* created = nullptr;
-        lk.unlock();
-        int rc = start_request(S, r, res, &created, st);
-        std::string msg;
-        if (rc) {
-            char buf[512];
-            fem_last_error(buf, sizeof buf);
-            msg = buf;
-            cudaStreamSynchronize(st);    // nothing of the failed request stays in flight
-            if (created && r.kind == FEM_REQ_ASSEMBLE) {
-                fem_mesh_destroy(created);
-                created = nullptr;
-            }
-        }
-        lk.lock();
-        if (created) res->mesh = created;
-        if (rc) {
-            finish(S, r, rc, msg);
-            --S->inflight;
-            res->busy = 0;
-            // the outputs stay accounted until release; a mesh that was not created is dropped
-            S->in_use -= r.est_bytes - r.out_bytes;
-            if (r.kind == FEM_REQ_ASSEMBLE) S->meshes.erase(r.mesh_id);
-        } else {
-            S->running.push_back(r.ticket);
-        }
-        return true;
+        res = &m->second;
     }
-    return false;
+    if (S->in_use + r.est_bytes > S->opts.budget_bytes) return false;
+    S->ready.erase(S->ready.begin());
+    --S->pending;
+    if (r.kind == FEM_REQ_ASSEMBLE) {
+        r.mesh_id = S->next_mesh++;
+        res = &S->meshes[r.mesh_id];
+        res->bytes = r.est_bytes - r.out_bytes;
+    } else {
+        res->in_ready = false;
+    }
+    res->busy = 1;
+    S->in_use += r.est_bytes;
+    S->peak = std::max(S->peak, S->in_use);
+    r.state = RUNNING;
+    r.t_start = now_us(S);
+    r.stream = S->rr;
+    S->rr = (S->rr + 1) % (int)S->streams.size();
+    ++S->inflight;
+    cudaStream_t st = S->streams[r.stream];
+    fem_mesh* created = nullptr;
+    lk.unlock();
+    int rc = start_request(S, r, res, &created, st);
+    std::string msg;
+    if (rc) {
+        char buf[512];
+        fem_last_error(buf, sizeof buf);
+        msg = buf;
+        cudaStreamSynchronize(st);    // nothing of the failed request stays in flight
+        if (created && r.kind == FEM_REQ_ASSEMBLE) {
+            fem_mesh_destroy(created);
+            created = nullptr;
+        }
+    }
+    lk.lock();
+    if (created) res->mesh = created;
+    if (rc) {
+        finish(S, r, rc, msg);
+        --S->inflight;
+        // the outputs stay accounted until release; a mesh that was not created is dropped
+        S->in_use -= r.est_bytes - r.out_bytes;
+        if (r.kind == FEM_REQ_ASSEMBLE) S->meshes.erase(r.mesh_id);
+        else mesh_idle(S, *res);
+    } else {
+        S->running.push_back(r.ticket);
+    }
+    return true;
 }
 
 void scheduler(fem_server* S) {
@@ -422,16 +458,26 @@ int fem_serve_submit(fem_server* S, const fem_request* q, uint64_t* ticket) {
         else r->u.assign(q->u, q->u + n);
     }
     std::lock_guard<std::mutex> lk(S->mu);
-    if (S->queue.size() >= (size_t)std::max(S->opts.max_queue, 1)) {
+    if (S->pending >= (size_t)std::max(S->opts.max_queue, 1)) {
         cudaEventDestroy(ev);
         drop_inputs(S, *r);
-        return fail(FEM_EBUSY, "queue full (" + std::to_string(S->queue.size()) + " pending requests)");
+        return fail(FEM_EBUSY, "queue full (" + std::to_string(S->pending) + " pending requests)");
+    }
+    if (r->kind == FEM_REQ_REASSEMBLE) {
+        auto it = S->meshes.find(r->mesh_id);
+        if (it == S->meshes.end() || !it->second.mesh || it->second.evicted) {
+            cudaEventDestroy(ev);
+            drop_inputs(S, *r);
+            return fail(FEM_EINVAL, "unknown, evicted or not yet assembled mesh id");
+        }
     }
     r->ticket = S->next_ticket++;
     r->t_submit = t_in;
     *ticket = r->ticket;
-    S->queue.push_back(r->ticket);
+    Request& rr = *r;
     S->reqs[r->ticket] = std::move(r);
+    ++S->pending;
+    enqueue_request(S, rr);
     S->cv_work.notify_one();
     return FEM_OK;
 }
@@ -499,6 +545,19 @@ int fem_serve_evict(fem_server* S, uint64_t mesh_id) {
         auto it = S->meshes.find(mesh_id);
         if (it == S->meshes.end() || !it->second.mesh) return fail(FEM_EINVAL, "unknown or not yet assembled mesh id");
         if (it->second.busy) return fail(FEM_ESTATE, "a request of this mesh is in flight");
+        // its pending requests fail now
+        Resident& rs = it->second;
+        std::vector<uint64_t> drop(rs.waiting.begin(), rs.waiting.end());
+        if (rs.in_ready) {
+            S->ready.erase(rs.ready_ticket);
+            drop.push_back(rs.ready_ticket);
+        }
+        for (uint64_t t : drop) {
+            --S->pending;
+            finish(S, *S->reqs[t], FEM_EINVAL, "mesh was evicted before the request started");
+        }
+        rs.waiting.clear();
+        rs.in_ready = false;
         res = it->second;
         S->in_use -= std::min(S->in_use, res.bytes);
         S->meshes.erase(it);
@@ -512,7 +571,7 @@ int fem_serve_evict(fem_server* S, uint64_t mesh_id) {
 int fem_serve_stats(fem_server* S, fem_serve_counters* out) {
     if (!S || !out) return fail(FEM_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(S->mu);
-    out->pending = (int)S->queue.size();
+    out->pending = (int)S->pending;
     out->inflight = S->inflight;
     out->resident_meshes = (int)S->meshes.size();
     out->bytes_in_use = S->in_use;
