@@ -210,9 +210,9 @@ __device__ __forceinline__ void epilogue(uint32_t tmem, int col, float* stage, f
 // 32 x 33 staging tile per warp (stage + warp 32 x 33 floats): each store
 // instruction writes one row.  Used where the whole-block staging of
 // `epilogue` would not fit (the chunked product's 400-column T).
-template <int N>
+template <int N, int LD = N>
 __device__ __forceinline__ void epilogue_staged(uint32_t tmem, int col, float* stage_base, float* __restrict__ V,
-                                                int64_t row0, int64_t E, int warp, int lane) {
+                                                int64_t row0, int64_t E, int warp, int lane, int c_off = 0) {
     float* stage = stage_base + warp * 32 * 33;
 #pragma unroll 1
     for (int c0 = 0; c0 < N; c0 += 32) {
@@ -225,7 +225,7 @@ __device__ __forceinline__ void epilogue_staged(uint32_t tmem, int col, float* s
         for (int rr = 0; rr < 32; ++rr) {
             int64_t er = row0 + rr;
             int c = c0 + lane;
-            if (er < E && c < N) V[er * N + c] = stage[rr * 33 + lane];
+            if (er < E && c < N) V[er * LD + c_off + c] = stage[rr * 33 + lane];
         }
         __syncwarp();
     }
@@ -547,28 +547,42 @@ struct ChL {
     static constexpr int QCM = 8, QCK = 4, QCT = 8;                      // quadrature points per chunk
     static constexpr int KcM = QCM, KcK = QCK * NS, KcT = QCT * D;       // chunk widths (multiples of 8)
     static constexpr int NCM = NQ / QCM, NCK = NQ / QCK, NCT = NQ / QCT;
-    static constexpr int NSTEP = NCM + NCK + NCT;
+    // four passes, each accumulating at TMEM column 0 and drained before the
+    // next: M, K, T rows [0, NTa), T rows [NTa, NTp)
+    static constexpr int NSTEP = NCM + NCK + 2 * NCT;
     static constexpr int NMp = ru(ETy::NSYM, 16), NTp = ru(ETy::NT, 16);
     static constexpr int NTa = NTp > 256 ? ru(NTp / 2, 16) : NTp, NTb = NTp - NTa;
-    static constexpr int COLM = 0, COLK = NMp, COLT = 0;
-    static constexpr int ALLOC = 512;
+    static constexpr int NMAXp = NMp > NTa ? NMp : NTa;
+    static constexpr int ALLOC = pow2_at_least(ru(NMAXp, 32));
     static constexpr int KcMax = KcK > KcT ? (KcK > KcM ? KcK : KcM) : (KcT > KcM ? KcT : KcM);
     static constexpr int XBYTES = TILE * KcMax * 8;                      // X chunk, hi + lo
-    static constexpr int QB_M = NMp * KcM * 8, QB_K = NMp * KcK * 8, QB_T = NTp * KcT * 8;
-    static constexpr int QBMAX = QB_T > QB_K ? (QB_T > QB_M ? QB_T : QB_M) : (QB_K > QB_M ? QB_K : QB_M);
-    static constexpr int IMG_BYTES = NCM * QB_M + NCK * QB_K + NCT * QB_T;
+    static constexpr int QB_M = NMp * KcM * 8, QB_K = NMp * KcK * 8, QB_Ta = NTa * KcT * 8, QB_Tb = NTb * KcT * 8;
+    static constexpr int QBMAX = QB_K > QB_M ? (QB_K > QB_Ta ? QB_K : QB_Ta) : (QB_M > QB_Ta ? QB_M : QB_Ta);
+    static constexpr int IMG_BYTES = NCM * QB_M + NCK * QB_K + NCT * (QB_Ta + QB_Tb);
     static constexpr int SMEM = XBYTES + QBMAX;                          // X chunk + Q chunk
     static constexpr bool OK = NQ % QCM == 0 && NQ % QCK == 0 && NQ % QCT == 0 && KcK % 8 == 0 && KcT % 8 == 0 &&
-                               NMp <= 256 && NTa <= 256 && NTb <= 256 && NTb % 16 == 0 && 2 * NMp <= ALLOC &&
-                               COLK + ru(ETy::NSYM, 32) <= ALLOC && COLT + ru(ETy::NT, 32) <= ALLOC &&
-                               XBYTES >= STAGE_FLOATS * 4 && SMEM <= SMEM_MAX;
-    // step s -> (matrix 0/1/2 = M/K/T, chunk index)
-    __host__ __device__ static constexpr int kind(int s) { return s < NCM ? 0 : s < NCM + NCK ? 1 : 2; }
-    __host__ __device__ static constexpr int chunk(int s) { return s < NCM ? s : s < NCM + NCK ? s - NCM : s - NCM - NCK; }
-    __host__ __device__ static constexpr int qbytes(int s) { return kind(s) == 0 ? QB_M : kind(s) == 1 ? QB_K : QB_T; }
+                               NMp <= 256 && NTa <= 256 && NTb <= 256 && NTb % 16 == 0 && NTb > 0 &&
+                               QB_Tb <= QBMAX && ALLOC <= 256 && ru(ETy::NSYM, 32) <= ALLOC &&
+                               ru(NTa, 32) <= ALLOC && ru(NTb, 32) <= ALLOC && XBYTES >= STAGE_FLOATS * 4 &&
+                               SMEM <= SMEM_MAX;
+    // step s -> (pass 0/1/2/3 = M/K/Ta/Tb, chunk index)
+    __host__ __device__ static constexpr int kind(int s) {
+        return s < NCM ? 0 : s < NCM + NCK ? 1 : s < NCM + NCK + NCT ? 2 : 3;
+    }
+    __host__ __device__ static constexpr int chunk(int s) {
+        return s < NCM ? s : s < NCM + NCK ? s - NCM : s < NCM + NCK + NCT ? s - NCM - NCK : s - NCM - NCK - NCT;
+    }
+    __host__ __device__ static constexpr int qbytes(int s) {
+        return kind(s) == 0 ? QB_M : kind(s) == 1 ? QB_K : kind(s) == 2 ? QB_Ta : QB_Tb;
+    }
     __host__ __device__ static constexpr int img_off(int s) {
-        return s <= NCM ? s * QB_M : s <= NCM + NCK ? NCM * QB_M + (s - NCM) * QB_K
-                                                    : NCM * QB_M + NCK * QB_K + (s - NCM - NCK) * QB_T;
+        return s <= NCM ? s * QB_M
+             : s <= NCM + NCK ? NCM * QB_M + (s - NCM) * QB_K
+             : s <= NCM + NCK + NCT ? NCM * QB_M + NCK * QB_K + (s - NCM - NCK) * QB_Ta
+                                    : NCM * QB_M + NCK * QB_K + NCT * QB_Ta + (s - NCM - NCK - NCT) * QB_Tb;
+    }
+    __host__ __device__ static constexpr bool last_of_pass(int s) {
+        return s == NCM - 1 || s == NCM + NCK - 1 || s == NCM + NCK + NCT - 1 || s == NSTEP - 1;
     }
 };
 
@@ -710,7 +724,7 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
                 float x[L::KcK];
                 form_chunk_k<ETy, L::QCK>(c * L::QCK, du, u0, b, A, k, x);
                 store_row<L::KcK>(sX, sX + TILE * L::KcK * 4, x, tid);
-            } else {
+            } else {   // both halves of T use the same X columns
                 float x[L::KcT];
                 form_chunk_t<ETy, L::QCT>(c * L::QCT, du, u0, b, A, k, x);
                 store_row<L::KcT>(sX, sX + TILE * L::KcT * 4, x, tid);
@@ -724,22 +738,23 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
             pend_q = false;
             if (tid == 0) {
                 tc::fence_after_sync();
+                // every pass accumulates at TMEM column 0
                 if (kd == 0) {
                     constexpr int Kc = L::KcM;
-                    issue_tf32x3<Kc>(tmem + L::COLM, sXu, sXu + TILE * Kc * 4, sQu, sQu + L::NMp * Kc * 4,
+                    issue_tf32x3<Kc>(tmem, sXu, sXu + TILE * Kc * 4, sQu, sQu + L::NMp * Kc * 4,
                                      tc::idesc_tf32(L::NMp), c > 0);
                 } else if (kd == 1) {
                     constexpr int Kc = L::KcK;
-                    issue_tf32x3<Kc>(tmem + L::COLK, sXu, sXu + TILE * Kc * 4, sQu, sQu + L::NMp * Kc * 4,
+                    issue_tf32x3<Kc>(tmem, sXu, sXu + TILE * Kc * 4, sQu, sQu + L::NMp * Kc * 4,
                                      tc::idesc_tf32(L::NMp), c > 0);
+                } else if (kd == 2) {
+                    constexpr int Kc = L::KcT;
+                    issue_tf32x3<Kc>(tmem, sXu, sXu + TILE * Kc * 4, sQu, sQu + L::NTa * Kc * 4,
+                                     tc::idesc_tf32(L::NTa), c > 0);
                 } else {
                     constexpr int Kc = L::KcT;
-                    constexpr uint32_t half = (L::NTa / 8) * ((Kc / 4) * 128);   // N-offset of the second MMA
-                    issue_tf32x3<Kc>(tmem + L::COLT, sXu, sXu + TILE * Kc * 4, sQu, sQu + L::NTp * Kc * 4,
-                                     tc::idesc_tf32(L::NTa), c > 0);
-                    if constexpr (L::NTb > 0)
-                        issue_tf32x3<Kc>(tmem + L::COLT + L::NTa, sXu, sXu + TILE * Kc * 4, sQu + half,
-                                         sQu + L::NTp * Kc * 4 + half, tc::idesc_tf32(L::NTb), c > 0);
+                    issue_tf32x3<Kc>(tmem, sXu, sXu + TILE * Kc * 4, sQu, sQu + L::NTb * Kc * 4,
+                                     tc::idesc_tf32(L::NTb), c > 0);
                 }
                 tc::mma_commit(mb_mma);
             }
@@ -751,15 +766,13 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
             pend_mma = false;
             tc::fence_after_sync();
         }
-        // drain the accumulators once their last chunk is in (the stage
+        // drain the pass's accumulator once its last chunk is in (the stage
         // area aliases the X chunk, which the completed MMAs no longer read)
-        if (s == L::NCM + L::NCK - 1) {
-            if (doM) epilogue_staged<ETy::NSYM>(tmem, L::COLM, stage, VM, row0, E, warp, lane);
-            if (doK) epilogue_staged<ETy::NSYM>(tmem, L::COLK, stage, VK, row0, E, warp, lane);
-            tc::fence_before_sync();
-            __syncthreads();
-        } else if (s == L::NSTEP - 1) {
-            if (doT) epilogue_staged<ETy::NT>(tmem, L::COLT, stage, VT, row0, E, warp, lane);
+        if (active && L::last_of_pass(s)) {
+            if (kd == 0) epilogue_staged<ETy::NSYM>(tmem, 0, stage, VM, row0, E, warp, lane);
+            else if (kd == 1) epilogue_staged<ETy::NSYM>(tmem, 0, stage, VK, row0, E, warp, lane);
+            else if (kd == 2) epilogue_staged<L::NTa, ETy::NT>(tmem, 0, stage, VT, row0, E, warp, lane, 0);
+            else epilogue_staged<ETy::NT - L::NTa, ETy::NT>(tmem, 0, stage, VT, row0, E, warp, lane, L::NTa);
             tc::fence_before_sync();
             __syncthreads();
         }
@@ -768,7 +781,7 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
 }
 
 template <typename ETy>
-__global__ void __launch_bounds__(TILE, 1) element_tc_chunked_kernel(
+__global__ void __launch_bounds__(TILE, 2) element_tc_chunked_kernel(
     const int* __restrict__ conn, const float* __restrict__ geo, int64_t E, int64_t gs, const float2* __restrict__ u,
     CoeffDev k, float mass, float* __restrict__ VM, float* __restrict__ VK, float* __restrict__ VT,
     const unsigned char* __restrict__ img, int* __restrict__ err) {
@@ -811,7 +824,7 @@ __global__ void __launch_bounds__(TILE, 1) element_tc_chunked_kernel(
 // Batched chunked product: a persistent walk over the 128-element tiles of
 // every P3-tetrahedron mesh of a batch (the same tile code as the
 // single-mesh kernel, so the bits are the same).
-__global__ void __launch_bounds__(TILE, 1) batch_tc_chunked_kernel(const BatchItem* __restrict__ items, int nitems,
+__global__ void __launch_bounds__(TILE, 2) batch_tc_chunked_kernel(const BatchItem* __restrict__ items, int nitems,
                                                                    const BatchMesh* __restrict__ meshes,
                                                                    const unsigned char* __restrict__ img,
                                                                    int* __restrict__ err) {
@@ -921,10 +934,17 @@ void build_chunk_image(std::vector<float>& img, const RefElem& R) {
     for (int st = 0; st < L::NSTEP; ++st) {
         const int kd = L::kind(st), c = L::chunk(st);
         const int Kc = kd == 0 ? L::KcM : kd == 1 ? L::KcK : L::KcT;
-        const int N = kd == 2 ? ETy::NT : ETy::NSYM, Np = kd == 2 ? L::NTp : L::NMp;
+        const int N = kd >= 2 ? ETy::NT : ETy::NSYM;
+        // the pass's output columns [n0, n0 + nw) and their padded row count
+        const int n0 = kd == 3 ? L::NTa : 0;
+        const int nw = kd == 2 ? std::min(L::NTa, N) : kd == 3 ? N - L::NTa : N;
+        const int Np = kd == 2 ? L::NTa : kd == 3 ? L::NTb : L::NMp;
         const std::vector<double>& Q = kd == 0 ? R.QM : kd == 1 ? R.QK : R.QT;
+        std::vector<double> sub((size_t)Kc * nw);
+        for (int kk = 0; kk < Kc; ++kk)
+            for (int n = 0; n < nw; ++n) sub[(size_t)kk * nw + n] = Q[((size_t)c * Kc + kk) * N + n0 + n];
         const int off = L::img_off(st);
-        put_operand(img, off, off + Np * Kc * 4, Q.data() + (size_t)c * Kc * N, Kc, N, Kc);
+        put_operand(img, off, off + Np * Kc * 4, sub.data(), Kc, nw, Kc);
     }
 }
 
@@ -984,16 +1004,17 @@ int launch_tc_chunked(const fem_mesh& m, const CoeffDev& k, const float2* u, flo
         cudaFuncAttributes fa;
         FEM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
         const int dyn_max = optin - (int)fa.sharedSizeBytes;
-        // one CTA per SM (it holds all 512 TMEM columns): ask for more than
-        // half of the SM's shared memory
-        o.smem = std::min(dyn_max, std::max(L::SMEM, per_sm / 2 + 1));
+        // at most 512 / ALLOC CTAs per SM (each holds ALLOC TMEM columns):
+        // ask for enough shared memory that no more fit
+        const int cmax = 512 / L::ALLOC;
+        o.smem = std::min(dyn_max, std::max(L::SMEM, per_sm / (cmax + 1) + 1));
         if (o.smem < L::SMEM) return fail(FEM_EINVAL, "chunked tensor-core tile does not fit in shared memory");
         FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, o.smem));
         FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                           (int)cudaSharedmemCarveoutMaxShared));
         FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, o.smem));
-        if (occ > 1) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
-        o.occ = 1;
+        if (occ > cmax) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
+        o.occ = std::max(1, std::min(cmax, ctas_per_sm(fa, TILE, o.smem, dev)));
         void* img = nullptr;
         FEM_CUDA_TRY(cudaGetSymbolAddress(&img, g_tcbig));
         o.img = img;
@@ -1002,9 +1023,9 @@ int launch_tc_chunked(const fem_mesh& m, const CoeffDev& k, const float2* u, flo
     }, sh);
     if (rc) return rc;
     const int64_t ntiles = (E + TILE - 1) / TILE;
-    int64_t grid = sh.nsm;
+    int64_t grid = (int64_t)sh.nsm * sh.occ;
     if (grid > ntiles) grid = ntiles;
-    trace_launch("element_tc_chunked_kernel", grid, TILE, sh.smem, 1);
+    trace_launch("element_tc_chunked_kernel", grid, TILE, sh.smem, sh.occ);
     cudaGetLastError();   // clear any stale error before the launch check
     kern<<<(unsigned)grid, TILE, sh.smem, s>>>(m.conn.as<int>() + e0 * ETy::NP, m.geo32.as<float>() + e0, E, m.E, u, k,
                                                (float)m.m, VM ? VM + e0 * ETy::NSYM : nullptr,
@@ -1220,19 +1241,21 @@ int batch_tc_chunked_launch(const BatchItem* items, int nitems, const BatchMesh*
     FEM_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     cudaFuncAttributes fa;
     FEM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
-    const int smem = std::min(optin - (int)fa.sharedSizeBytes, std::max(L::SMEM, per_sm / 2 + 1));
+    const int cmax = 512 / L::ALLOC;
+    const int smem = std::min(optin - (int)fa.sharedSizeBytes, std::max(L::SMEM, per_sm / (cmax + 1) + 1));
     if (smem < L::SMEM) return fail(FEM_EINVAL, "chunked tensor-core tile does not fit in shared memory");
     FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
     FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
-    if (occ > 1) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
-    const int grid = nitems < nsm ? nitems : nsm;
+    if (occ > cmax) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
+    const int per = std::max(1, std::min(cmax, ctas_per_sm(fa, TILE, smem, dev)));
+    const int grid = nitems < nsm * per ? nitems : nsm * per;
     unsigned char* img = nullptr;
     int* err = nullptr;
     FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&img, g_tcbig));
     FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&err, g_tc_err));
-    trace_launch("batch_tc_chunked_kernel", grid, TILE, smem, 1);
+    trace_launch("batch_tc_chunked_kernel", grid, TILE, smem, per);
     cudaGetLastError();   // clear any stale error before the launch check
     kern<<<grid, TILE, smem, s>>>(items, nitems, meshes, img, err);
     FEM_CUDA_TRY(cudaGetLastError());
