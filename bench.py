@@ -195,6 +195,26 @@ def run_reference(args, rank, world):
     return 0
 
 
+def rank_field_seed(rank: int, s: int) -> int:
+    """Seed of the s-th nodal field of a rank: every rank reassembles its own
+    independent problem (same mesh recipe, its own fields)."""
+    return 1000 + 97 * rank + s
+
+
+def whole_job_rate(local_ms: float, units_per_rank: int, steps: int, dist=None, device="cpu"):
+    """(max over ranks of the timed region in ms, whole-job units/s): the
+    ranks work on independent problems (weak scaling, no data-path
+    collective); the job's rate is all ranks' units over the slowest rank's
+    time.  `dist` is torch.distributed (or None for one process)."""
+    import torch
+    world = dist.get_world_size() if dist else 1
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * units_per_rank * steps / (ms / 1e3)
+
+
 def _pct(xs, q):
     xs = sorted(xs)
     if not xs:
@@ -481,7 +501,7 @@ def run_ours(args, rank, world, local_rank):
         t_sym = time.perf_counter() - t0
         nnz = fm.nnz
         # a ring of nodal fields (fresh u every step, resident in HBM)
-        us = [torch.tensor(mg.fourier_field(wl.mesh.coords, 1000 + 97 * rank + s), dtype=torch.float64,
+        us = [torch.tensor(mg.fourier_field(wl.mesh.coords, rank_field_seed(rank, s)), dtype=torch.float64,
                            device="cuda") for s in range(4)]
         out = {k: torch.empty(nnz, dtype=dt, device="cuda") for k in "MKT"}
         k = F.coeff(wl.coeff.kind, wl.coeff.params)
@@ -519,12 +539,8 @@ def run_ours(args, rank, world, local_rank):
         total_ms = t_start.elapsed_time(t_end)
         form_ms = [e[0].elapsed_time(e[1]) for e in evs]
         sum_ms = [e[1].elapsed_time(e[2]) for e in evs]
-        if dist:
-            tt = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            total_ms = float(tt.item())
+        total_ms, value = whole_job_rate(total_ms, E, args.steps, dist, "cuda")
         ms_per_step = total_ms / args.steps
-        value = world * E * args.steps / (total_ms / 1e3)
 
         # FP64 plain path on the same workload (one-matrix-at-a-time reference point)
         fp64 = None

@@ -280,7 +280,7 @@ CoeffDev coeff_to_device(const fem_coeff* k) { return to_dev(k); }
 
 size_t fem_mesh::device_bytes() const {
     const fem::DevBuf* bufs[] = {&coords, &conn, &geo64, &geo32, &row_ptr, &col_idx, &seg_ptr, &contrib, &slot,
-                                 &inc_ptr, &inc, &VM, &VK, &VT, &u_stage, &out_stage, &u_split, &loff};
+                                 &inc_ptr, &inc, &VM, &VK, &VT, &u_stage, &out_stage, &u_split};
     size_t t = 0;
     for (auto* b : bufs) t += b->bytes;
     return t;
@@ -374,7 +374,7 @@ int fem_mesh_destroy(fem_mesh* m) {
     cudaDeviceSynchronize();
     fem::DevBuf* bufs[] = {&m->coords, &m->conn, &m->geo64, &m->geo32, &m->row_ptr, &m->col_idx, &m->seg_ptr,
                            &m->contrib, &m->slot, &m->inc_ptr, &m->inc, &m->VM, &m->VK, &m->VT, &m->u_stage,
-                           &m->out_stage, &m->u_split, &m->loff};
+                           &m->out_stage, &m->u_split};
     for (auto* b : bufs) buf_free(*b, nullptr);
     cudaDeviceSynchronize();
     delete m;

@@ -58,9 +58,6 @@ struct fem_mesh {
     bool have_pattern = false;
     int64_t nnz = -1;
     fem::DevBuf row_ptr, col_idx, seg_ptr, contrib, slot, inc_ptr, inc;
-    fem::DevBuf loff;                   // 8-bit in-row offset of every element entry (if max_row <= 256)
-    int max_row = 0;                    // longest CSR row
-    int sum_kernel = 0;                 // CSR sum variant: 0 = per-slot segments, 1 = row-wise (needs loff)
     int sum_block = 256;                // threads per block of the CSR sum
     // chunk plan: fine element chunks and the slot prefix each one completes
     bool have_plan = false;

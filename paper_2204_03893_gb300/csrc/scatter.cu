@@ -8,18 +8,8 @@
 // M and K come from the symmetric element storage (entry (i,j) and (j,i)
 // share V[e][sym(min,max)]), T from the full n_p x n_p storage.
 //
-// Two interchangeable kernels give identical bits (same order per slot); the
-// mesh records which one, and its block size, the tuner measured fastest.
-// Row-wise kernel (requires every CSR row to have at most 256 entries): one
-// thread owns one row r and walks the row's incident element rows (e, i),
-// conn[e][i] = r, in ascending e; for each it reads the element's local row
-// (n_p contiguous T entries and the matching symmetric M, K entries) and the
-// n_p 8-bit in-row offsets of the target slots, and adds into the row's
-// accumulators in shared memory.  A block owns a run of consecutive rows,
-// i.e. one contiguous range of CSR values, which it zeroes, fills and writes
-// out with coalesced stores.
-// Segment kernel (default): one thread per slot sums the slot's contributor
-// list contrib[seg_ptr[s] .. seg_ptr[s+1]) (element entries, ascending).
+// One thread per CSR slot sums the slot's contributor list
+// contrib[seg_ptr[s] .. seg_ptr[s+1]) (element entries, ascending).
 #include <algorithm>
 #include <vector>
 
@@ -31,79 +21,6 @@ namespace {
 
 __host__ __device__ constexpr int sym_idx(int np, int i, int j) {
     return i <= j ? i * np - (i * (i - 1)) / 2 + (j - i) : j * np - (j * (j - 1)) / 2 + (i - j);
-}
-
-template <int NP, typename T>
-__global__ void __launch_bounds__(256) scatter_rows_kernel(const int* __restrict__ inc_ptr, const int* __restrict__ inc,
-                                                           const int* __restrict__ row_ptr,
-                                                           const unsigned char* __restrict__ loff, int64_t n,
-                                                           int maxrow, const T* __restrict__ VM,
-                                                           const T* __restrict__ VK, const T* __restrict__ VT,
-                                                           T* __restrict__ vM, T* __restrict__ vK,
-                                                           T* __restrict__ vT) {
-    constexpr int NT = NP * NP, NSYM = NP * (NP + 1) / 2;
-    extern __shared__ __align__(16) unsigned char sraw[];
-    const int cap = blockDim.x * maxrow;                // accumulators per matrix
-    T* aM = reinterpret_cast<T*>(sraw);
-    T* aK = aM + cap;
-    T* aT = aK + cap;
-    const bool dM = vM != nullptr, dK = vK != nullptr, dT = vT != nullptr;
-    for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < n; r0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t rend = r0 + blockDim.x < n ? r0 + blockDim.x : n;
-        const int base0 = row_ptr[r0];
-        const int total = row_ptr[rend] - base0;       // <= blockDim.x * maxrow
-        for (int k = threadIdx.x; k < total; k += blockDim.x) {
-            if (dM) aM[k] = T(0);
-            if (dK) aK[k] = T(0);
-            if (dT) aT[k] = T(0);
-        }
-        __syncthreads();
-        const int64_t r = r0 + threadIdx.x;
-        if (r < n) {
-            const int base = row_ptr[r] - base0;
-            const int p1 = inc_ptr[r + 1];
-            for (int p = inc_ptr[r]; p < p1; ++p) {
-                const int ei = __ldg(inc + p);         // e * n_p + i, ascending e
-                const int e = ei / NP;
-                const int i = ei - e * NP;
-                const unsigned char* lo = loff + (int64_t)ei * NP;
-                int off[NP];
-#pragma unroll
-                for (int j = 0; j < NP; ++j) off[j] = base + __ldg(lo + j);
-                if (dT) {
-                    const T* vt = VT + (int64_t)e * NT + i * NP;
-                    T val[NP];
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) val[j] = __ldg(vt + j);
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) aT[off[j]] += val[j];
-                }
-                if (dM) {
-                    const T* vm = VM + (int64_t)e * NSYM;
-                    T val[NP];
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) val[j] = __ldg(vm + sym_idx(NP, i, j));
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) aM[off[j]] += val[j];
-                }
-                if (dK) {
-                    const T* vk = VK + (int64_t)e * NSYM;
-                    T val[NP];
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) val[j] = __ldg(vk + sym_idx(NP, i, j));
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) aK[off[j]] += val[j];
-                }
-            }
-        }
-        __syncthreads();
-        for (int k = threadIdx.x; k < total; k += blockDim.x) {
-            if (dM) __stcs(vM + base0 + k, aM[k]);
-            if (dK) __stcs(vK + base0 + k, aK[k]);
-            if (dT) __stcs(vT + base0 + k, aT[k]);
-        }
-        __syncthreads();
-    }
 }
 
 // V entries of one element entry c = (e n_p + i) n_p + j: T from the full
@@ -285,28 +202,10 @@ __global__ void __launch_bounds__(512) batch_scatter_kernel(const BatchItem* __r
 template <int NP, typename T>
 int launch_np(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s,
               int nsm, int64_t s0, int64_t s1) {
-    const bool whole = s0 == 0 && s1 == m.nnz;
-    if (whole && m.sum_kernel == 1 && m.loff.ptr && m.max_row > 0) {
-        // threads per block: as many rows as fit ~64 KiB of accumulators (3 matrices)
-        int B = m.sum_block > 0 ? m.sum_block : 256;
-        while (B > 32 && (size_t)3 * B * m.max_row * sizeof(T) > 64 * 1024) B /= 2;
-        const size_t smem = (size_t)3 * B * m.max_row * sizeof(T);
-        auto kern = scatter_rows_kernel<NP, T>;
-        FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                          (int)cudaSharedmemCarveoutMaxShared));
-        int occ = 0;
-        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, B, smem));
-        if (occ < 1) occ = 1;
-        int64_t blocks = (m.n + B - 1) / B;
-        if (blocks > (int64_t)nsm * occ) blocks = (int64_t)nsm * occ;
-        cudaGetLastError();   // clear any stale error before the launch check
-        kern<<<(unsigned)blocks, B, smem, s>>>(m.inc_ptr.as<int>(), m.inc.as<int>(), m.row_ptr.as<int>(),
-                                              m.loff.as<unsigned char>(), m.n, m.max_row, VM, VK, VT, vM, vK, vT);
-    } else {
+    {
         // a slot range [s0, s1): the segment bounds and the outputs offset
         // by s0 (contributor indices address the whole V)
-        const int B = (m.sum_kernel == 0 && m.sum_block >= 32) ? m.sum_block : 256;
+        const int B = m.sum_block >= 32 ? m.sum_block : 256;
         const int64_t ns = s1 - s0;
         if (ns <= 0) return FEM_OK;
         int64_t blocks = (ns + B - 1) / B;

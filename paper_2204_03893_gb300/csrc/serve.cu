@@ -164,7 +164,7 @@ size_t mesh_estimate(const fem_mesh_desc& d, int prec) {
     const size_t m2 = E * np * np, ngeo = 1 + (size_t)d.dim * (d.dim + 1) / 2;
     size_t b = n * d.dim * 8 + E * np * 4 + ngeo * E * 12;
     b += (n + 1) * 4 * 5;                 // row_ptr, inc_ptr and three transient counters of the sort
-    b += m2 * 4 * 4 + m2 + E * np * 4;    // col_idx and seg_ptr (nnz <= m2), contrib, slot, loff, inc
+    b += m2 * 4 * 4 + E * np * 4;         // col_idx and seg_ptr (nnz <= m2), contrib, slot, inc
     b += esz_of(prec) * E * (np * (np + 1) + np * np) + n * 8 + n * 8;   // V scratch, u split, u
     return b + 4096;                      // rounding of small buffers
 }

@@ -226,27 +226,6 @@ __global__ void __launch_bounds__(256) row_finish(const int* __restrict__ conn, 
 
 __global__ void set_last(int* p, int64_t idx, int v) { p[idx] = v; }
 
-// In-row offset of every element entry: loff[c] = slot[c] - row_ptr[conn[e][i]]
-// (c = (e n_p + i) n_p + j), stored in 8 bits (rows of at most 256 entries).
-__global__ void local_offsets(const int* __restrict__ conn, int np, int64_t m2, const int* __restrict__ slot,
-                              const int* __restrict__ row_ptr, unsigned char* __restrict__ loff) {
-    const int np2 = np * np;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < m2; c += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t ei = c / np;                       // e n_p + i
-        const int r = conn[ei];
-        loff[c] = (unsigned char)(slot[c] - row_ptr[r]);
-        (void)np2;
-    }
-}
-
-__global__ void max_row_len(const int* __restrict__ row_ptr, int64_t n, int* __restrict__ out) {
-    int mx = 0;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
-        mx = max(mx, row_ptr[r + 1] - row_ptr[r]);
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
-}
-
 int grid_for(int64_t work, int threads, int64_t cap = 152 * 32) {
     int64_t b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -308,20 +287,6 @@ int symbolic_run(fem_mesh& m, cudaStream_t s) {
                                                         m.seg_ptr.as<int>(), m.slot.as<int>());
     set_last<<<1, 1, 0, s>>>(m.seg_ptr.as<int>(), nnz, (int)m2);
     FEM_CUDA_TRY(cudaGetLastError());
-    // longest row; rows of at most 256 entries get 8-bit in-row offsets for the row-wise CSR sum
-    FEM_CUDA_TRY(cudaMemsetAsync(cnt.ptr, 0, sizeof(int), s));
-    max_row_len<<<grid_for(n, 256), 256, 0, s>>>(m.row_ptr.as<int>(), n, cnt.as<int>());
-    FEM_CUDA_TRY(cudaGetLastError());
-    int mx = 0;
-    FEM_CUDA_TRY(cudaMemcpyAsync(&mx, cnt.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FEM_CUDA_TRY(cudaStreamSynchronize(s));
-    m.max_row = mx;
-    if (mx <= 256) {
-        if ((rc = buf_alloc(m.loff, (size_t)(m2 > 0 ? m2 : 1), s))) return rc;
-        local_offsets<<<grid_for(m2, 256), 256, 0, s>>>(conn, np, m2, m.slot.as<int>(), m.row_ptr.as<int>(),
-                                                       m.loff.as<unsigned char>());
-        FEM_CUDA_TRY(cudaGetLastError());
-    }
     buf_free(cnt, s);
     buf_free(fill, s);
     buf_free(row_nnz, s);

@@ -245,9 +245,9 @@ def test_form_and_sum_phases(prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
 def test_long_rows_fallback_paths(prec):
-    """A 300-triangle fan: the centre row has 301 entries (> 256), so the CSR
-    sum takes the per-slot segment kernel and the symbolic phase sorts the
-    row's 900 keys without staging them in shared memory."""
+    """A 300-triangle fan: the centre row has 301 entries and its diagonal
+    slot 300 contributors; the symbolic phase sorts the row's 900 keys
+    without staging them in shared memory."""
     m = mg.fan_tri(300, seed=2)
     u = mg.uniform_field(m.n_nodes, 3)
     c = mg.Coeff("poly", (1.0, 0.5, 0.25, 0.0, 0.0))
