@@ -9,7 +9,7 @@
  * rule, the geometric factors b_e = |det B_e| and A_e = (B_e^T B_e)^-1 only on
  * the mesh, and the coefficient evaluations S only on the unknown u (Section
  * 5, summary of dependencies).  The element matrices are then summed into a
- * global CSR matrix (Algorithm 2, line 12).
+ * global CSR matrix (the last step of Algorithm 2).
  *
  * Conventions used by every call:
  *  - Status: every function returns FEM_OK (0) or a negative FEM_E* code; a
@@ -109,7 +109,7 @@ typedef struct fem_mesh fem_mesh;
  * keeps ownership of its buffers; host buffers are read before return),
  * checks every connectivity index (FEM_EINVAL) and computes the per-element
  * geometric factors b_e = |det B_e| and A_e = (B_e^T B_e)^-1 once (Section 3
- * step 3; Algorithm 2 line 4; Section 5: W and b depend only on the mesh):
+ * step 3; Algorithm 2; Section 5: W and b depend only on the mesh):
  * an FP64 cache for FEM_FP64, and an FP32 cache computed in FP32 with an FP64
  * recomputation for elements whose condition estimate ||B||_F^d/|det B|
  * exceeds 1e3.  Returns FEM_EDEGENERATE if an element is degenerate.
@@ -136,11 +136,13 @@ typedef struct {
 
 /* Builds, once per mesh, the CSR pattern and the map from element entries to
  * CSR slots by a device sort of the keys (conn[e][i], conn[e][j]) (Section 3
- * step 2; Algorithm 2 line 12 "the set of indices of nonzero entries"): a
+ * step 2; the index set of nonzero entries that Algorithm 2 sums into): a
  * counting sort by row, then a per-row sort by column, stable in the element
  * entry index c = (e n_p + i) n_p + j.  Keeps on the device: row_ptr, col_idx,
- * slot[c] (CSR slot of element entry c) and the segmented lists seg_ptr /
- * contrib (contributing c of every slot, ascending).  Idempotent. */
+ * slot[c] (CSR slot of element entry c), the segmented lists seg_ptr /
+ * contrib (contributing c of every slot, ascending) and, per 32 consecutive
+ * contributions, a mask of slot starts and the slot of the first (what the
+ * CSR sum reads).  Idempotent. */
 int fem_symbolic(fem_mesh* mesh, void* stream, fem_csr_pattern* out);
 
 /* Copies the pattern into caller-owned device buffers d_row_ptr (n+1) and
@@ -154,22 +156,27 @@ int fem_get_slot_map(fem_mesh* mesh, int32_t* d_slot, void* stream);
 /* ------------------------------------------------------------- numeric */
 /* Reassembly of the CSR values, reusing the pattern and the geometry
  * (Section 5: only S is recomputed at each Newton step).  For each matrix
- * the element matrices are formed as one product V = X Q (Algorithm 2 lines
- * 5-11; Section 4.1 mass: X = Lambda = S*(w b^T); Section 4.2 conductivity:
+ * the element matrices are formed as one product V = X Q (Algorithm 2,
+ * formation; Section 4.1 mass: X = Lambda = S*(w b^T); Section 4.2 conductivity:
  * X = Lambda (.) W; tangent: the Section 5.2 conductivity tensor multiplied
  * by u in its second mode, T_ij = int k'(u_h) phi_j grad u_h . grad phi_i),
  * using the symmetry of M and K to keep only the n_p(n_p+1)/2 distinct rows of
  * Q (Section 7), then summed into the CSR values by a deterministic
- * segmented reduction: every slot adds its contributions in ascending element
- * entry order, with no atomics, so results are bit-reproducible run to run.
+ * segmented reduction: every slot adds its contributions in one fixed order
+ * given by the mesh alone (the contributions sorted by slot, cut into
+ * aligned groups of 64: adjacent pairs, then a tree over the group, groups
+ * in ascending order), with no atomics, so results are bit-reproducible run
+ * to run and identical across ranges, batches and launch shapes.
  *
  * u: n_nodes nodal values in FP64 for every precision (the FP32 paths split
- * u = hi + lo into two FP32 values on the device, so that the nodal
- * differences that carry grad u_h in the tangent keep FP32 relative accuracy).
+ * each gathered value as u = hi + lo, two FP32 values, inside the element
+ * kernel, so that the nodal differences that carry grad u_h in the tangent
+ * keep FP32 relative accuracy).
  * values: nnz outputs, FP64 for FEM_FP64 and FP32 otherwise.
- * u and values may be device pointers or host pointers; host pointers are
- * staged through library-owned device buffers and the call then synchronises
- * `stream` before returning.  Requires fem_symbolic (FEM_ESTATE otherwise). */
+ * u and values may be device pointers or host pointers (pageable or
+ * page-locked); host pointers are staged through library-owned device
+ * buffers and the call then synchronises `stream` before returning.
+ * Requires fem_symbolic (FEM_ESTATE otherwise). */
 int fem_assemble_mass(fem_mesh* mesh, int prec, void* values, void* stream);
 int fem_assemble_stiffness(fem_mesh* mesh, const fem_coeff* k, const void* u, int prec,
                            void* values, void* stream);
@@ -180,11 +187,11 @@ int fem_assemble_all(fem_mesh* mesh, const fem_coeff* k, const void* u, int prec
                      void* vM, void* vK, void* vT, void* stream);
 
 /* The two phases of fem_assemble_all, which the paper times separately
- * (Section 4.2: formation of the element matrices, Algorithm 2 lines 1-11,
- * versus assemblage of the global matrices, line 12).
+ * (Section 4.2: formation of the element matrices versus assemblage of the
+ * global matrices, the two parts of Algorithm 2).
  * fem_form_elements forms V = X Q for the matrices selected by `which`
  * (FEM_MAT_M | FEM_MAT_K | FEM_MAT_T) into scratch buffers owned by the mesh
- * (one kernel launch, plus the split of u for the FP32 paths); d_u is a
+ * (one kernel launch); d_u is a
  * device pointer to FP64 nodal values (unused when which == FEM_MAT_M).
  * fem_sum_elements sums the formed V into the CSR values (one kernel
  * launch); d_v* are device pointers, NULL to skip, and must have been formed
@@ -214,8 +221,8 @@ int fem_sum_elements(fem_mesh* mesh, int prec, void* d_vM, void* d_vK, void* d_v
  *
  * fem_form_elements_range forms V for elements [e_begin, e_end) (e_begin a
  * multiple of 128) into the mesh's scratch, as fem_form_elements does for
- * all elements; the FP32 paths split u when e_begin == 0, and later ranges of
- * the same reassembly (same u, precision and matrices) reuse that split.
+ * all elements; a range with e_begin > 0 must follow one with e_begin == 0
+ * of the same reassembly (same u, precision and matrices).
  * fem_sum_elements_range writes the CSR values of slots [s_begin, s_end)
  * (d_v* are the whole nnz arrays); every element contributing to those slots
  * must have been formed.  A plan's ranges, formed and summed in order, give

@@ -16,7 +16,7 @@
  *     e, an inner loop over quadrature nodes q, dense local matrices
  *         M_e += w_q m   phi_q phi_q^T        |det B_e|
  *         K_e += w_q k_q J_q A_e J_q^T        |det B_e|,  A_e = (B_e^T B_e)^-1
- *     (Section 3, steps 3-4, the "computer implementation" formulas), then
+ *     (Section 3, steps 3-4, the formulas as implemented), then
  *     M(N_e,N_e) += M_e, K(N_e,N_e) += K_e.
  *   - The tangent term: the conductivity tensor of Section 5.2,
  *         C_e = sum_q w_q k'_q (J_q A_e J_q^T) o phi_q |det B_e|,

@@ -29,8 +29,8 @@ struct fem_batch {
     fem::BatchMesh* pinned[2] = {nullptr, nullptr};
     cudaEvent_t staged[2] = {nullptr, nullptr};
     int cur = 0;
-    fem::DevBuf d_tc, d_tc5, d_simt, d_split, d_scatter;
-    int n_tc = 0, n_tc5 = 0, n_simt = 0, n_split = 0, n_scatter = 0;
+    fem::DevBuf d_tc, d_tc5, d_simt, d_scatter;
+    int n_tc = 0, n_tc5 = 0, n_simt = 0, n_scatter = 0;
     int tc_grid = 0;
     // tensor-core tiles are grouped by element type; each type gets its own
     // launch (sized for that type's shared memory and TMEM) on its own branch
@@ -64,8 +64,8 @@ int upload_items(DevBuf& buf, const std::vector<BatchItem>& items, cudaStream_t 
     return FEM_OK;
 }
 
-// The kernels of one reassembly on stream s: the u split, then the element
-// products as parallel branches (one per tensor-core element type, plus the
+// The kernels of one reassembly on stream s: the element products as
+// parallel branches (one per tensor-core element type, plus the
 // SIMT walker), joined before the chunked P3-tetrahedron kernel (which holds
 // all TMEM columns of its SMs) and the CSR sum.
 int enqueue(fem_batch* b, cudaStream_t s) {
@@ -76,7 +76,6 @@ int enqueue(fem_batch* b, cudaStream_t s) {
             return rc;
         return batch_scatter_launch<double>(b->d_scatter.as<BatchItem>(), b->n_scatter, tab, b->scatter_block, s);
     }
-    if ((rc = batch_split_launch(b->d_split.as<BatchItem>(), b->n_split, tab, s))) return rc;
     int nb = 0;
     FEM_CUDA_TRY(cudaEventRecord(b->fork, s));
     auto next_branch = [&](cudaStream_t& out) -> int {
@@ -109,12 +108,16 @@ int enqueue(fem_batch* b, cudaStream_t s) {
     return batch_scatter_launch<float>(b->d_scatter.as<BatchItem>(), b->n_scatter, tab, b->scatter_block, s);
 }
 
+// One item per run of block/32 pair groups of 64 contributions (a warp's task).
 int build_scatter_items(fem_batch* b, int block, cudaStream_t s) {
     std::vector<BatchItem> items;
-    const int chunk = block * 4;
-    for (int i = 0; i < b->n; ++i)
-        for (int64_t f = 0; f < b->meshes[i]->nnz; f += chunk)
-            items.push_back(BatchItem{i, b->meshes[i]->type, f, chunk, 0});
+    const int run = std::max(1, block / 32);
+    for (int i = 0; i < b->n; ++i) {
+        const fem_mesh* m = b->meshes[i];
+        const int64_t ng = (m->E * m->np * m->np + 63) / 64;
+        for (int64_t f = 0; f < ng; f += run)
+            items.push_back(BatchItem{i, m->type, f, (int)std::min<int64_t>(run, ng - f), 0});
+    }
     b->n_scatter = (int)items.size();
     return upload_items(b->d_scatter, items, s);
 }
@@ -216,7 +219,7 @@ int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts,
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
     const size_t esz = prec == FEM_FP64 ? 8 : 4;
-    std::vector<BatchItem> tc, tc5, simt, split;
+    std::vector<BatchItem> tc, tc5, simt;
     b->host.resize(n);
     for (int i = 0; i < n; ++i) {
         fem_mesh* m = meshes[i];
@@ -227,10 +230,6 @@ int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts,
             return rc;
         }
         m->v_prec = -1;   // scratch now belongs to the batch's precision
-        if (prec != FEM_FP64 && (rc = buf_alloc(m->u_split, sizeof(float2) * (size_t)m->n, s))) {
-            fem_batch_destroy(b);
-            return rc;
-        }
         BatchMesh& h = b->host[i];
         std::memset(&h, 0, sizeof(h));
         h.conn = m->conn.as<int>();
@@ -242,12 +241,13 @@ int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts,
         h.np = m->np;
         h.type = m->type;
         h.mass = m->m;
-        h.u2 = prec != FEM_FP64 ? m->u_split.as<float2>() : nullptr;
         h.VM = m->VM.ptr;
         h.VK = m->VK.ptr;
         h.VT = m->VT.ptr;
         h.seg_ptr = m->seg_ptr.as<int>();
         h.contrib = m->contrib.as<int>();
+        h.seg_head = m->seg_head.as<uint2>();
+        h.max_seg = m->max_seg;
         const bool on_tc = prec == FEM_TF32X3 && tc_type_supported(m->type);
         const bool on_tc5 = prec == FEM_TF32X3 && !on_tc && tc_chunked_supported(m->type);
         if (on_tc5) {
@@ -258,8 +258,6 @@ int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts,
             for (int64_t f = 0; f < m->E; f += 64) simt.push_back(BatchItem{i, m->type, f, 64, 0});
             b->simt_smem = std::max(b->simt_smem, batch_simt_smem(m->type, prec == FEM_FP64));
         }
-        if (prec != FEM_FP64)
-            for (int64_t f = 0; f < m->n; f += 2048) split.push_back(BatchItem{i, m->type, f, 2048, 0});
     }
     // tensor-core tiles grouped by element type: one launch per type
     std::stable_sort(tc.begin(), tc.end(), [](const BatchItem& a, const BatchItem& c) { return a.type < c.type; });
@@ -273,13 +271,12 @@ int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts,
     b->n_tc = (int)tc.size();
     b->n_tc5 = (int)tc5.size();
     b->n_simt = (int)simt.size();
-    b->n_split = (int)split.size();
     b->tc_grid = nsm;
     b->simt_grid = nsm * 16;
     if (b->simt_smem == 0) b->simt_smem = 16;
     if ((rc = upload_items(b->d_tc, tc, s)) || (rc = upload_items(b->d_tc5, tc5, s)) ||
         (rc = upload_items(b->d_simt, simt, s)) ||
-        (rc = upload_items(b->d_split, split, s)) || (rc = build_scatter_items(b, b->scatter_block, s)) ||
+        (rc = build_scatter_items(b, b->scatter_block, s)) ||
         (rc = buf_alloc(b->d_meshes, sizeof(BatchMesh) * n, s))) {
         fem_batch_destroy(b);
         return rc;
@@ -323,15 +320,13 @@ int fem_batch_launch(fem_batch* b, const fem_coeff* k, const double* const* d_u,
         const size_t nsym = (size_t)m->np * (m->np + 1) / 2, nt = (size_t)m->np * m->np;
         int rc0;
         if ((rc0 = buf_alloc(m->VM, esz * (size_t)m->E * nsym, s)) || (rc0 = buf_alloc(m->VK, esz * (size_t)m->E * nsym, s)) ||
-            (rc0 = buf_alloc(m->VT, esz * (size_t)m->E * nt, s)) ||
-            (b->prec != FEM_FP64 && (rc0 = buf_alloc(m->u_split, sizeof(float2) * (size_t)m->n, s))))
+            (rc0 = buf_alloc(m->VT, esz * (size_t)m->E * nt, s)))
             return rc0;
         m->v_prec = -1;
         BatchMesh h = b->host[i];
         h.VM = m->VM.ptr;
         h.VK = m->VK.ptr;
         h.VT = m->VT.ptr;
-        h.u2 = b->prec != FEM_FP64 ? m->u_split.as<float2>() : nullptr;
         h.vM = d_vM ? d_vM[i] : nullptr;
         h.vK = d_vK ? d_vK[i] : nullptr;
         h.vT = d_vT ? d_vT[i] : nullptr;
@@ -344,7 +339,6 @@ int fem_batch_launch(fem_batch* b, const fem_coeff* k, const double* const* d_u,
             h.k = coeff_to_device(&k[i]);
         } else {
             h.u = nullptr;
-            h.u2 = nullptr;
         }
         st[i] = h;
     }
@@ -368,8 +362,7 @@ int fem_batch_get_info(const fem_batch* b, fem_batch_info* out) {
     if (!b || !out) return fail(FEM_EINVAL, "NULL argument");
     std::memset(out, 0, sizeof(*out));
     out->n_meshes = b->n;
-    out->kernels_per_launch = (b->prec != FEM_FP64 ? 1 : 0) + (int)b->tc_ranges.size() + (b->n_tc5 ? 1 : 0) +
-                              (b->n_simt ? 1 : 0) + 1;
+    out->kernels_per_launch = (int)b->tc_ranges.size() + (b->n_tc5 ? 1 : 0) + (b->n_simt ? 1 : 0) + 1;
     out->tc_tiles = b->n_tc + b->n_tc5;
     out->simt_blocks = b->n_simt;
     out->sum_chunks = b->n_scatter;
@@ -396,7 +389,7 @@ int fem_batch_destroy(fem_batch* b) {
         if (b->pinned[k]) cudaFreeHost(b->pinned[k]);
         if (b->staged[k]) cudaEventDestroy(b->staged[k]);
     }
-    DevBuf* bufs[] = {&b->d_meshes, &b->d_tc, &b->d_tc5, &b->d_simt, &b->d_split, &b->d_scatter};
+    DevBuf* bufs[] = {&b->d_meshes, &b->d_tc, &b->d_tc5, &b->d_simt, &b->d_scatter};
     for (auto* x : bufs) buf_free(*x, nullptr);
     cudaDeviceSynchronize();
     delete b;

@@ -137,11 +137,11 @@ CoeffDev to_dev(const fem_coeff* k) {
     return c;
 }
 
-// Formation (Algorithm 2 lines 1-11): V for the matrices in `mask` (bit 0 M,
+// Formation (Algorithm 2, up to the products V): V for the matrices in `mask` (bit 0 M,
 // bit 1 K, bit 2 T) into the mesh's scratch buffers.
 template <typename T>
 int form_t(fem_mesh* m, const fem_coeff* k, const double* ud, int prec, int mask, cudaStream_t s, int64_t e0 = 0,
-           int64_t e1 = -1, bool split = true) {
+           int64_t e1 = -1) {
     const int64_t E = m->E;
     const int nsym = m->np * (m->np + 1) / 2, nt = m->np * m->np;
     int rc;
@@ -162,12 +162,7 @@ int form_t(fem_mesh* m, const fem_coeff* k, const double* ud, int prec, int mask
     if constexpr (sizeof(T) == 8) {
         rc = element_simt_fp64(*m, kd, ud, VM, VK, VT, s, e0, e1);
     } else {
-        const float2* us = nullptr;
-        if (mask & 6) {
-            if ((rc = buf_alloc(m->u_split, sizeof(float2) * (size_t)m->n, s))) return rc;
-            us = m->u_split.as<float2>();
-            if (split && (rc = split_u(ud, m->n, m->u_split.as<float2>(), s))) return rc;
-        }
+        const double* us = (mask & 6) ? ud : nullptr;
         rc = prec == FEM_TF32X3 ? element_tc_tf32x3(*m, kd, us, VM, VK, VT, s, e0, e1)
                                 : element_simt_fp32(*m, kd, us, VM, VK, VT, s, e0, e1);
     }
@@ -177,7 +172,7 @@ int form_t(fem_mesh* m, const fem_coeff* k, const double* ud, int prec, int mask
     return FEM_OK;
 }
 
-// Global assembly (Algorithm 2 line 12) of the formed V into CSR values.
+// Global assembly (the last step of Algorithm 2) of the formed V into CSR values.
 template <typename T>
 int sum_t(fem_mesh* m, T* vM, T* vK, T* vT, cudaStream_t s, int64_t s0 = 0, int64_t s1 = -1) {
     const T* VM = vM ? m->VM.as<T>() : nullptr;
@@ -242,21 +237,29 @@ int assemble_t(fem_mesh* m, const fem_coeff* k, const void* u, int prec, void* v
             ud = m->u_stage.as<double>();
         }
     }
+    // outputs: device memory as given; host memory through a device stage and
+    // one copy per array.  (Letting the CSR sum store straight into
+    // page-locked host memory measured 2.3x slower end to end on GB300: its
+    // scattered 4-byte stores cross the CPU-GPU link in small pieces.)
     void* outs[3] = {vM, vK, vT};
     T* outd[3] = {nullptr, nullptr, nullptr};
-    bool out_host[3] = {false, false, false};
-    int nhost = 0;
-    for (int i = 0; i < 3; ++i)
-        if (outs[i] && !is_device_ptr(outs[i])) {
-            out_host[i] = true;
-            ++nhost;
+    bool out_staged[3] = {false, false, false};
+    int nstaged = 0;
+    for (int i = 0; i < 3; ++i) {
+        if (!outs[i]) continue;
+        if (is_device_ptr(outs[i])) {
+            outd[i] = static_cast<T*>(outs[i]);
+        } else {
+            out_staged[i] = true;
+            ++nstaged;
         }
-    if (nhost) {
+    }
+    if (nstaged) {
         host_io = true;
         if ((rc = buf_alloc(m->out_stage, sizeof(T) * (size_t)nnz * 3, s))) return rc;
+        for (int i = 0; i < 3; ++i)
+            if (out_staged[i]) outd[i] = m->out_stage.as<T>() + (size_t)i * nnz;
     }
-    for (int i = 0; i < 3; ++i)
-        if (outs[i]) outd[i] = out_host[i] ? m->out_stage.as<T>() + (size_t)i * nnz : static_cast<T*>(outs[i]);
     int mask = (vM ? 1 : 0) | (vK ? 2 : 0) | (vT ? 4 : 0);
     // One formation, then one sum.  (Chunking the two phases so that each
     // range's V is summed while in L2 -- fem_chunk_plan and the range calls
@@ -265,7 +268,7 @@ int assemble_t(fem_mesh* m, const fem_coeff* k, const void* u, int prec, void* v
     if ((rc = form_t<T>(m, k, ud, prec, mask, s))) return rc;
     if ((rc = sum_t<T>(m, outd[0], outd[1], outd[2], s))) return rc;
     for (int i = 0; i < 3; ++i)
-        if (out_host[i])
+        if (out_staged[i])
             FEM_CUDA_TRY(cudaMemcpyAsync(outs[i], outd[i], sizeof(T) * (size_t)nnz, cudaMemcpyDeviceToHost, s));
     if (host_io) FEM_CUDA_TRY(cudaStreamSynchronize(s));
     return FEM_OK;
@@ -280,7 +283,7 @@ CoeffDev coeff_to_device(const fem_coeff* k) { return to_dev(k); }
 
 size_t fem_mesh::device_bytes() const {
     const fem::DevBuf* bufs[] = {&coords, &conn, &geo64, &geo32, &row_ptr, &col_idx, &seg_ptr, &contrib, &slot,
-                                 &inc_ptr, &inc, &VM, &VK, &VT, &u_stage, &out_stage, &u_split};
+                                 &seg_head, &inc_ptr, &inc, &VM, &VK, &VT, &u_stage, &out_stage};
     size_t t = 0;
     for (auto* b : bufs) t += b->bytes;
     return t;
@@ -373,8 +376,8 @@ int fem_mesh_destroy(fem_mesh* m) {
     if (!m) return FEM_OK;
     cudaDeviceSynchronize();
     fem::DevBuf* bufs[] = {&m->coords, &m->conn, &m->geo64, &m->geo32, &m->row_ptr, &m->col_idx, &m->seg_ptr,
-                           &m->contrib, &m->slot, &m->inc_ptr, &m->inc, &m->VM, &m->VK, &m->VT, &m->u_stage,
-                           &m->out_stage, &m->u_split};
+                           &m->contrib, &m->slot, &m->seg_head, &m->inc_ptr, &m->inc, &m->VM, &m->VK, &m->VT, &m->u_stage,
+                           &m->out_stage};
     for (auto* b : bufs) buf_free(*b, nullptr);
     cudaDeviceSynchronize();
     delete m;
@@ -507,8 +510,8 @@ int fem_form_elements_range(fem_mesh* m, const fem_coeff* k, const void* d_u, in
         return fail(FEM_ESTATE, "later ranges must follow a range starting at 0 with the same precision and matrices");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (prec == FEM_FP64)
-        return form_t<double>(m, k, static_cast<const double*>(d_u), prec, which, s, e_begin, e_end, e_begin == 0);
-    return form_t<float>(m, k, static_cast<const double*>(d_u), prec, which, s, e_begin, e_end, e_begin == 0);
+        return form_t<double>(m, k, static_cast<const double*>(d_u), prec, which, s, e_begin, e_end);
+    return form_t<float>(m, k, static_cast<const double*>(d_u), prec, which, s, e_begin, e_end);
 }
 
 int fem_sum_elements_range(fem_mesh* m, int prec, int64_t s_begin, int64_t s_end, void* d_vM, void* d_vK,

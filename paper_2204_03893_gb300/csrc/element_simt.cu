@@ -1,7 +1,7 @@
 // element_simt.cu -- element products V = X Q on the SIMT pipes (FP64 and
 // FP32), one thread per element.
 //
-// Algorithm 2 lines 5-11: the coefficient evaluations S at the quadrature
+// Algorithm 2, formation step: the coefficient evaluations S at the quadrature
 // points (here k(u_q), k'(u_q) from u_q = phi_q . u_e), Lambda = S * (w b^T)
 // (eq. def_lambda, computed as w_q S_qe b_e in place), X_m = Lambda and
 // X_c = Lambda (.) W (Section 4.2), then V = Q X.  The tangent uses the same
@@ -46,18 +46,14 @@ struct Tabs<float> {
 
 constexpr int BT = 64;   // elements (threads) per block
 
-// nodal values: FP64 as given for the FP64 path; for the FP32 path the
-// host splits u = hi + lo (two FP32 values, see split_u) so that the
-// differences u_i - u_0 that carry the gradient keep FP32 relative accuracy.
-template <typename T>
-struct UType { using type = double; };
-template <>
-struct UType<float> { using type = float2; };
+// nodal values: FP64 as given; the FP32 path splits each gathered value
+// as hi + lo (split_f64) so that the differences u_i - u_0 that carry the
+// gradient keep FP32 relative accuracy.
 
 // X row and V = X Q of element e (thread-private X row in shared memory).
 template <typename ETy, typename T>
 __device__ __forceinline__ void simt_element(int64_t e, const int* __restrict__ conn, const T* __restrict__ geo,
-                                             int64_t gs, const typename UType<T>::type* __restrict__ u,
+                                             int64_t gs, const double* __restrict__ u,
                                              const CoeffDev& k, T mass, T* __restrict__ VM, T* __restrict__ VK,
                                              T* __restrict__ VT, T* X) {
     constexpr int D = ETy::D, NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS;
@@ -78,11 +74,11 @@ __device__ __forceinline__ void simt_element(int64_t e, const int* __restrict__ 
 #pragma unroll
             for (int i = 0; i < NP; ++i) du[i] = u[ce[i]] - u0;
         } else {
-            const float2 a = u[ce[0]];
+            const float2 a = split_f64(u[ce[0]]);
             u0 = a.x + a.y;
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                const float2 b = u[ce[i]];
+                const float2 b = split_f64(u[ce[i]]);
                 du[i] = (b.x - a.x) + (b.y - a.y);
             }
         }
@@ -160,7 +156,7 @@ __device__ __forceinline__ void simt_element(int64_t e, const int* __restrict__ 
 template <typename ETy, typename T>
 __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict__ conn, const T* __restrict__ geo,
                                                           int64_t E, int64_t gs,
-                                                          const typename UType<T>::type* __restrict__ u,
+                                                          const double* __restrict__ u,
                                                           CoeffDev k, T mass, T* __restrict__ VM, T* __restrict__ VK,
                                                           T* __restrict__ VT) {
     constexpr int KTOT = ETy::KM + ETy::KK + ETy::KT;
@@ -185,9 +181,7 @@ __global__ void __launch_bounds__(BT) batch_simt_kernel(const BatchItem* __restr
         const int64_t e = w.first + threadIdx.x;
         if (threadIdx.x >= w.count || e >= bm.E) continue;
         const T* geo = static_cast<const T*>(sizeof(T) == 8 ? (const void*)bm.geo64 : (const void*)bm.geo32);
-        const typename UType<T>::type* u;
-        if constexpr (sizeof(T) == 8) u = bm.u;
-        else u = bm.u2;
+        const double* u = bm.u;
         T* VM = bm.vM ? static_cast<T*>(bm.VM) : nullptr;
         T* VK = bm.vK ? static_cast<T*>(bm.VK) : nullptr;
         T* VT = bm.vT ? static_cast<T*>(bm.VT) : nullptr;
@@ -211,32 +205,8 @@ __global__ void __launch_bounds__(BT) batch_simt_kernel(const BatchItem* __restr
     }
 }
 
-__global__ void batch_split_kernel(const BatchItem* __restrict__ items, int nitems,
-                                   const BatchMesh* __restrict__ meshes) {
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const BatchItem w = items[it];
-        const BatchMesh& bm = meshes[w.mesh];
-        if (!bm.u2 || !bm.u) continue;
-        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
-            const int64_t i = w.first + k;
-            if (i >= bm.n) break;
-            const double v = bm.u[i];
-            const float hi = (float)v;
-            bm.u2[i] = make_float2(hi, (float)(v - (double)hi));
-        }
-    }
-}
-
-__global__ void split_u_kernel(const double* __restrict__ u, int64_t n, float2* __restrict__ out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double v = u[i];
-        const float hi = (float)v;
-        out[i] = make_float2(hi, (float)(v - (double)hi));
-    }
-}
-
 template <typename ETy, typename T>
-int launch_simt(const fem_mesh& m, const CoeffDev& k, const typename UType<T>::type* u, const T* geo, T* VM, T* VK,
+int launch_simt(const fem_mesh& m, const CoeffDev& k, const double* u, const T* geo, T* VM, T* VK,
                 T* VT, cudaStream_t s, int64_t e0, int64_t e1) {
     const int64_t E = e1 - e0;
     if (E <= 0) return FEM_OK;
@@ -265,7 +235,7 @@ int launch_simt(const fem_mesh& m, const CoeffDev& k, const typename UType<T>::t
 }
 
 template <typename T>
-int dispatch(const fem_mesh& m, const CoeffDev& k, const typename UType<T>::type* u, const T* geo, T* VM, T* VK,
+int dispatch(const fem_mesh& m, const CoeffDev& k, const double* u, const T* geo, T* VM, T* VK,
              T* VT, cudaStream_t s, int64_t e0, int64_t e1) {
     if (e1 < 0) e1 = m.E;
     if (e0 < 0 || e0 > e1 || e1 > m.E) return fail(FEM_EINVAL, "element range out of bounds");
@@ -344,26 +314,7 @@ int batch_simt_launch(const BatchItem* items, int nitems, const BatchMesh* meshe
 template int batch_simt_launch<float>(const BatchItem*, int, const BatchMesh*, int, int, cudaStream_t);
 template int batch_simt_launch<double>(const BatchItem*, int, const BatchMesh*, int, int, cudaStream_t);
 
-int batch_split_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, cudaStream_t s) {
-    if (nitems <= 0) return FEM_OK;
-    int grid = nitems < 152 * 16 ? nitems : 152 * 16;
-    cudaGetLastError();   // clear any stale error before the launch check
-    batch_split_kernel<<<grid, 256, 0, s>>>(items, nitems, meshes);
-    FEM_CUDA_TRY(cudaGetLastError());
-    return FEM_OK;
-}
-
-int split_u(const double* u, int64_t n, float2* out, cudaStream_t s) {
-    if (n <= 0) return FEM_OK;
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    cudaGetLastError();   // clear any stale error before the launch check
-    split_u_kernel<<<(unsigned)blocks, 256, 0, s>>>(u, n, out);
-    FEM_CUDA_TRY(cudaGetLastError());
-    return FEM_OK;
-}
-
-int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
+int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
                       cudaStream_t s, int64_t e0, int64_t e1) {
     int rc = tables_init_simt();
     if (rc) return rc;

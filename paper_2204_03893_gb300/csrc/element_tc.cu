@@ -1,7 +1,7 @@
 // element_tc.cu -- element products V = X Q on the tcgen05 tensor cores
 // (TF32 x3 split precision, FP32 accumulation in tensor memory).
 //
-// Algorithm 2 lines 5-11 for a tile of 128 elements: every thread forms the
+// The formation step of Algorithm 2 for a tile of 128 elements: every thread forms the
 // X row of one element (Lambda = S * (w b^T) in place, eq. def_lambda;
 // X_c = Lambda (.) W, Section 4.2; the tangent factors of the Section 5.2
 // tensor multiplied by u) and stores it, split as X = Xhi + Xlo with Xhi,
@@ -12,8 +12,8 @@
 //     D += Xhi Qhi ; D += Xhi Qlo ; D += Xlo Qhi
 // for M, K and T into separate TMEM column ranges (D: 128 lanes = elements,
 // columns = entries), commits to an mbarrier, and the four warps read their
-// 32 lanes back with tcgen05.ld, transpose through shared memory and write V
-// element-major with coalesced 128-byte rows.  Only the n_p(n_p+1)/2 distinct
+// 32 lanes back with tcgen05.ld into row-major blocks in shared memory that
+// the copy engine writes to V (cp.async.bulk, one copy per warp and matrix).  Only the n_p(n_p+1)/2 distinct
 // entries of M and K are formed (Section 7).
 //
 // Every mbarrier wait is bounded (~1 s of SM clocks); on timeout the kernel
@@ -167,17 +167,17 @@ __device__ __forceinline__ void issue_tile(uint32_t tmem, uint32_t sXu, uint32_t
 }
 
 // TMEM (this warp's 32 lanes = 32 consecutive elements, columns col..col+N)
-// -> V.  The warp's 32 rows of V are one contiguous block of 32 N floats:
-// every thread writes its row into the warp's own block in shared memory
-// (stage + warp 32 NMAX floats, NMAX >= N for every matrix of the tile, so
-// warps never share a block), then the warp copies the block out with
-// 16-byte, fully coalesced stores.  Rows past E are not written.
-template <int N, int NMAX>
-__device__ __forceinline__ void epilogue(uint32_t tmem, int col, float* stage, float* __restrict__ V, int64_t row0,
-                                         int64_t E, int warp, int lane) {
-    static_assert(N <= NMAX, "epilogue block too small");
+// -> V with the copy engine: every thread writes its row into the warp's
+// block `blk` (32 N floats, the image of V rows row0..row0+31), and lane 0
+// hands the whole block to one bulk copy (cp.async.bulk shared -> global;
+// the block and V + row0 N are 16-byte aligned since row0 is a multiple of
+// 32).  The caller waits for the bulk reads before it reuses the block.  A
+// partial last block (rows past E) is copied by the warp with plain stores.
+template <int N>
+__device__ __forceinline__ void epilogue_bulk(uint32_t tmem, int col, float* blk, float* __restrict__ V, int64_t row0,
+                                              int64_t E, int warp, int lane) {
+    static_assert((32 * N * 4) % 16 == 0, "bulk block size");
     if (row0 >= E) return;   // warp-uniform
-    float* blk = stage + warp * 32 * NMAX;
 #pragma unroll 1
     for (int c0 = 0; c0 < N; c0 += 32) {
         uint32_t r[32];
@@ -196,14 +196,51 @@ __device__ __forceinline__ void epilogue(uint32_t tmem, int col, float* stage, f
                 if (c0 + j < N) dst[j] = __uint_as_float(r[j]);
         }
     }
-    __syncwarp();
-    const int rows = E - row0 < 32 ? (int)(E - row0) : 32;
-    const int nf = rows * N;
-    float* g = V + row0 * N;   // row0 is a multiple of 32: 16-byte aligned
-    const int nv = nf >> 2;
-    for (int i = lane; i < nv; i += 32) reinterpret_cast<float4*>(g)[i] = reinterpret_cast<const float4*>(blk)[i];
-    for (int i = (nv << 2) + lane; i < nf; i += 32) g[i] = blk[i];
-    __syncwarp();
+    if (E - row0 >= 32) {
+        tc::fence_proxy_async_smem();   // this thread's row -> visible to the copy engine
+        __syncwarp();
+        if (lane == 0) tc::bulk_s2g(V + row0 * N, tc::smem_u32(blk), 32u * N * 4u);
+    } else {
+        __syncwarp();
+        const int rows = E - row0 < 32 ? (int)(E - row0) : 32;
+        const int nf = rows * N, nv = nf >> 2;
+        float* g = V + row0 * N;   // 16-byte aligned (row0 is a multiple of 32)
+        for (int i = lane; i < nv; i += 32) reinterpret_cast<float4*>(g)[i] = reinterpret_cast<const float4*>(blk)[i];
+        for (int i = (nv << 2) + lane; i < nf; i += 32) g[i] = blk[i];
+        __syncwarp();
+    }
+}
+
+// The epilogue of one tile (M, K, T as requested) through the X region of
+// shared memory (`stage`, free once the MMAs are complete).  Where the three
+// matrices' blocks fit side by side, all copies are in flight at once;
+// otherwise the warp's one block is reused and each copy's reads are waited
+// for first.  Returns with every bulk read of this warp complete, so the
+// caller may overwrite the region after a block barrier.
+template <typename ETy, int XEND>
+__device__ __forceinline__ void epilogue_tile(uint32_t tmem, int colM, int colK, int colT, float* stage,
+                                              float* __restrict__ VM, float* __restrict__ VK, float* __restrict__ VT,
+                                              bool doM, bool doK, bool doT, int64_t row0, int64_t E, int warp,
+                                              int lane) {
+    constexpr int NSYM = ETy::NSYM, NT = ETy::NT;
+    constexpr bool DISJOINT = TILE * (2 * NSYM + NT) * 4 <= XEND;
+    static_assert(TILE * NT * 4 <= XEND, "epilogue blocks do not fit the X region");
+    float* bM = DISJOINT ? stage + warp * 32 * NSYM : stage + warp * 32 * NT;
+    float* bK = DISJOINT ? stage + TILE * NSYM + warp * 32 * NSYM : bM;
+    float* bT = DISJOINT ? stage + 2 * TILE * NSYM + warp * 32 * NT : bM;
+    auto drain = [&]() {
+        if (lane == 0) {
+            tc::bulk_commit();
+            tc::bulk_wait_read_all();
+        }
+        __syncwarp();
+    };
+    if (doM) epilogue_bulk<NSYM>(tmem, colM, bM, VM, row0, E, warp, lane);
+    if (!DISJOINT && doM) drain();
+    if (doK) epilogue_bulk<NSYM>(tmem, colK, bK, VK, row0, E, warp, lane);
+    if (!DISJOINT && doK) drain();
+    if (doT) epilogue_bulk<NT>(tmem, colT, bT, VT, row0, E, warp, lane);
+    drain();
 }
 
 // TMEM (this warp's 32 lanes, columns col..col+N) -> V rows through a
@@ -293,7 +330,7 @@ __device__ __forceinline__ void form_x(const float2 (&pu)[ETy::NP], const float 
 
 template <typename ETy>
 __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict__ conn, const float* __restrict__ geo,
-                                                          int64_t E, int64_t gs, const float2* __restrict__ u, CoeffDev k,
+                                                          int64_t E, int64_t gs, const double* __restrict__ u, CoeffDev k,
                                                           float mass, float* __restrict__ VM, float* __restrict__ VK,
                                                           float* __restrict__ VT, const float* __restrict__ img,
                                                           int* __restrict__ err) {
@@ -337,7 +374,7 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
     // tile's MMAs and epilogue run: connectivity and geometry before the MMA
     // issue, the gathered u values right after it.
     int pidx[NP];
-    float2 pu[NP];
+    double pu[NP];   // raw FP64 values: split at formation, so the loads stay in flight
     float pgeo[1 + NS];
     bool pvalid = false;
     auto fetch_meta = [&](int64_t t) {
@@ -367,7 +404,12 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
         float x[L::KTOTp];
 #pragma unroll
         for (int i = 0; i < L::KTOTp; ++i) x[i] = 0.f;
-        if (pvalid) form_x<ETy, L::KTOTp>(pu, pgeo, need_u, k, mass, x);
+        if (pvalid) {
+            float2 su[NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) su[i] = need_u ? split_f64(pu[i]) : make_float2(0.f, 0.f);
+            form_x<ETy, L::KTOTp>(su, pgeo, need_u, k, mass, x);
+        }
         const int64_t next = tile + gridDim.x;
         if (next < ntiles) fetch_meta(next);
         store_row<L::KTOTp>(sX + L::XH, sX + L::XL, x, tid);
@@ -391,9 +433,8 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
         }
         tc::fence_after_sync();
         const int64_t row0 = tile * TILE + warp * 32;
-        if (doM) epilogue<ETy::NSYM, ETy::NT>(tmem, L::COLM, stage, VM, row0, E, warp, lane);
-        if (doK) epilogue<ETy::NSYM, ETy::NT>(tmem, L::COLK, stage, VK, row0, E, warp, lane);
-        if (doT) epilogue<ETy::NT, ETy::NT>(tmem, L::COLT, stage, VT, row0, E, warp, lane);
+        epilogue_tile<ETy, L::XEND>(tmem, L::COLM, L::COLK, L::COLT, stage, VM, VK, VT, doM, doK, doT, row0, E, warp,
+                                    lane);
         tc::fence_before_sync();
         __syncthreads();
     }
@@ -402,6 +443,7 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
         // give in-flight tensor-core work one more bounded chance to drain
         tc::mbar_wait_bounded(mb, phase ^ 1u, WAIT_LIMIT);
     }
+    if ((tid & 31) == 0) tc::bulk_wait_all();   // V copies of this warp are complete
     __syncthreads();
     tc::fence_after_sync();
     if (warp == 0) tc::tmem_dealloc(tmem, L::ALLOC);
@@ -433,7 +475,7 @@ __device__ __forceinline__ bool batch_tc_tile(const BatchMesh& bm, int64_t first
         const int* ce = bm.conn + e * NP;
         if (need_u) {
 #pragma unroll
-            for (int i = 0; i < NP; ++i) pu[i] = __ldg(bm.u2 + __ldg(ce + i));
+            for (int i = 0; i < NP; ++i) pu[i] = split_f64(__ldg(bm.u + __ldg(ce + i)));
         }
 #pragma unroll
         for (int t = 0; t <= NS; ++t) pgeo[t] = __ldg(bm.geo32 + t * E + e);
@@ -456,9 +498,9 @@ __device__ __forceinline__ bool batch_tc_tile(const BatchMesh& bm, int64_t first
     // the epilogue stages through the X region (the MMAs are complete)
     float* stage = reinterpret_cast<float*>(sX);
     const int64_t row0 = first + warp * 32;
-    if (doM) epilogue<ETy::NSYM, ETy::NT>(tmem, L::COLM, stage, static_cast<float*>(bm.VM), row0, E, warp, lane);
-    if (doK) epilogue<ETy::NSYM, ETy::NT>(tmem, L::COLK, stage, static_cast<float*>(bm.VK), row0, E, warp, lane);
-    if (doT) epilogue<ETy::NT, ETy::NT>(tmem, L::COLT, stage, static_cast<float*>(bm.VT), row0, E, warp, lane);
+    epilogue_tile<ETy, L::XEND>(tmem, L::COLM, L::COLK, L::COLT, stage, static_cast<float*>(bm.VM),
+                                static_cast<float*>(bm.VK), static_cast<float*>(bm.VT), doM, doK, doT, row0, E, warp,
+                                lane);
     tc::fence_before_sync();
     __syncthreads();
     return true;
@@ -525,6 +567,7 @@ __global__ void __launch_bounds__(TILE) batch_tc_kernel(const BatchItem* __restr
         if (tid == 0) atomicExch(err, 1);
         tc::mbar_wait_bounded(mb, phase ^ 1u, WAIT_LIMIT);
     }
+    if ((tid & 31) == 0) tc::bulk_wait_all();   // V copies of this warp are complete
     __syncthreads();
     tc::fence_after_sync();
     if (warp == 0) tc::tmem_dealloc(tmem, talloc);
@@ -663,7 +706,7 @@ __device__ __forceinline__ void form_chunk_t(int q0, const float (&du)[ETy::NP],
 template <typename ETy>
 __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const float* __restrict__ geo, int64_t E,
                                              int64_t gs,
-                                             const float2* __restrict__ u, const CoeffDev& k, float mass,
+                                             const double* __restrict__ u, const CoeffDev& k, float mass,
                                              float* __restrict__ VM, float* __restrict__ VK, float* __restrict__ VT,
                                              const unsigned char* __restrict__ img, int64_t first,
                                              unsigned char* smem, uint32_t tmem, uint32_t mb_mma, uint32_t mb_q,
@@ -688,11 +731,11 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
         for (int t = 0; t < NS; ++t) A[t] = __ldg(geo + (int64_t)(1 + t) * gs + e);
         if (need_u) {
             const int* ce = conn + e * NP;
-            const float2 p0 = __ldg(u + __ldg(ce));
+            const float2 p0 = split_f64_all(__ldg(u + __ldg(ce)));
             u0 = p0.x + p0.y;
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                const float2 pi = __ldg(u + __ldg(ce + i));
+                const float2 pi = split_f64_all(__ldg(u + __ldg(ce + i)));
                 du[i] = (pi.x - p0.x) + (pi.y - p0.y);
             }
         }
@@ -782,7 +825,7 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
 
 template <typename ETy>
 __global__ void __launch_bounds__(TILE, 2) element_tc_chunked_kernel(
-    const int* __restrict__ conn, const float* __restrict__ geo, int64_t E, int64_t gs, const float2* __restrict__ u,
+    const int* __restrict__ conn, const float* __restrict__ geo, int64_t E, int64_t gs, const double* __restrict__ u,
     CoeffDev k, float mass, float* __restrict__ VM, float* __restrict__ VK, float* __restrict__ VT,
     const unsigned char* __restrict__ img, int* __restrict__ err) {
     using L = ChL<ETy>;
@@ -858,7 +901,7 @@ __global__ void __launch_bounds__(TILE, 2) batch_tc_chunked_kernel(const BatchIt
         float* VK = bm.vK ? static_cast<float*>(bm.VK) : nullptr;
         float* VT = bm.vT ? static_cast<float*>(bm.VT) : nullptr;
         if (!(VM || VK || VT)) continue;   // mesh skipped in this launch
-        ok = chunked_tile<ETy>(bm.conn, bm.geo32, bm.E, bm.E, bm.u2, bm.k, (float)bm.mass, VM, VK, VT, img, w.first, smem,
+        ok = chunked_tile<ETy>(bm.conn, bm.geo32, bm.E, bm.E, bm.u, bm.k, (float)bm.mass, VM, VK, VT, img, w.first, smem,
                                tmem, mb_mma, mb_q, ph_mma, ph_q, pend_q, pend_mma);
     }
     if (!ok) {
@@ -986,7 +1029,7 @@ int cached_shape(std::atomic<int>* have, LaunchShape* cache, std::mutex& mu, F c
 }
 
 template <typename ETy>
-int launch_tc_chunked(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
+int launch_tc_chunked(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
                       cudaStream_t s, int64_t e0, int64_t e1) {
     using L = ChL<ETy>;
     const int64_t E = e1 - e0;
@@ -1036,7 +1079,7 @@ int launch_tc_chunked(const fem_mesh& m, const CoeffDev& k, const float2* u, flo
 }
 
 template <typename ETy>
-int launch_tc(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
+int launch_tc(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
               cudaStream_t s, int64_t e0, int64_t e1) {
     using L = TcL<ETy>;
     if constexpr (!L::FITS) {
@@ -1274,7 +1317,7 @@ int tc_error_flag(int clear) {
     return v;
 }
 
-int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
+int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
                       cudaStream_t s, int64_t e0, int64_t e1) {
     if (e1 < 0) e1 = m.E;
     if (e0 < 0 || e0 > e1 || e1 > m.E) return fail(FEM_EINVAL, "element range out of bounds");

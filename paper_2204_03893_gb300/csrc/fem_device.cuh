@@ -63,6 +63,51 @@ struct CoeffDev {
     double p[16];
 };
 
+// An FP64 nodal value as two FP32 values with hi + lo = v to about 48 bits:
+// hi is v with its mantissa cut to 23 bits, lo the cut-off bits.  Integer
+// and FP32 instructions only (FP64 throughput is low on this part, and a
+// conversion fallback, even when not taken, slowed the element kernels).
+// Range: for 2^-74 <= |v| < 2^128 as stated; for 2^-126 <= |v| < 2^-74 lo
+// is 0 (hi alone, 24 bits); |v| < 2^-126 gives (+-0, 0); larger values and
+// infinities give +-inf, NaN gives NaN.  The FP32 element paths form the
+// differences u_i - u_0 as (hi_i - hi_0) + (lo_i - lo_0), which keeps FP32
+// relative accuracy where u varies little over an element.
+__device__ __forceinline__ float2 split_f64_all(double v) {
+    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
+    const uint32_t bh = static_cast<uint32_t>(bits >> 32), bl = static_cast<uint32_t>(bits);
+    const uint32_t sign = bh & 0x80000000u;
+    const uint32_t ex = (bh >> 20) & 0x7ffu;   // biased FP64 exponent
+    if (ex - 897u < 254u) {
+        // FP32 exponent ex - 1023 + 127; the top 23 of the 52 mantissa bits
+        const uint32_t hi = sign | ((ex - 896u) << 23) | ((bh & 0xfffffu) << 3) | (bl >> 29);
+        // the low 29 mantissa bits, worth 2^(ex - 1075) each (a normal FP32 scale for ex >= 949)
+        const float scale = ex >= 949u ? __uint_as_float((ex - 948u) << 23) : 0.f;
+        const float lo = static_cast<float>(bl & 0x1fffffffu) * scale;
+        return make_float2(__uint_as_float(hi), sign ? -lo : lo);
+    }
+    const bool nan = ex == 0x7ffu && ((bh & 0xfffffu) | bl) != 0u;
+    const uint32_t mag = nan ? 0x7fc00000u : ex > 1150u ? 0x7f800000u : 0u;
+    return make_float2(__uint_as_float(sign | mag), 0.f);
+}
+
+// The same split with the values outside 2^-74 <= |v| < 2^126 handled out of
+// line.  Same results as split_f64_all; the element tile kernels use this
+// form (their code measured faster with the call than fully inline, by 25%
+// for P1 tetrahedra), the chunked kernels the inline one.
+static __device__ __noinline__ float2 split_f64_edge(double v) { return split_f64_all(v); }
+__device__ __forceinline__ float2 split_f64(double v) {
+    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
+    const uint32_t bh = static_cast<uint32_t>(bits >> 32), bl = static_cast<uint32_t>(bits);
+    const uint32_t ex = (bh >> 20) & 0x7ffu;
+    if (ex - 949u < 200u) {
+        const uint32_t sign = bh & 0x80000000u;
+        const uint32_t hi = sign | ((ex - 896u) << 23) | ((bh & 0xfffffu) << 3) | (bl >> 29);
+        const float lo = static_cast<float>(bl & 0x1fffffffu) * __uint_as_float((ex - 948u) << 23);
+        return make_float2(__uint_as_float(hi), sign ? -lo : lo);
+    }
+    return split_f64_edge(v);
+}
+
 // k(u) and k'(u).  Loops run over the fixed maxima (8 polynomial
 // coefficients, 8 knots) with predicates so that the parameters stay in the
 // kernel-parameter space instead of being copied to local memory; unused

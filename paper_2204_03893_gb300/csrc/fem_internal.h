@@ -58,6 +58,10 @@ struct fem_mesh {
     bool have_pattern = false;
     int64_t nnz = -1;
     fem::DevBuf row_ptr, col_idx, seg_ptr, contrib, slot, inc_ptr, inc;
+    // per group of 32 consecutive contributions k: x = bit l set iff
+    // contribution 32k+l is the first of its slot, y = slot of contribution 32k
+    fem::DevBuf seg_head;               // uint2 per group
+    int max_seg = 0;                    // longest segment (contributions of one slot)
     int sum_block = 256;                // threads per block of the CSR sum
     // chunk plan: fine element chunks and the slot prefix each one completes
     bool have_plan = false;
@@ -67,7 +71,6 @@ struct fem_mesh {
     int v_prec = -1, v_mask = 0;        // what VM/VK/VT currently hold
     // staging for host-pointer arguments
     fem::DevBuf u_stage, out_stage;
-    fem::DevBuf u_split;                // FP32 paths: u as (hi, lo) float pairs
     size_t device_bytes() const;
 };
 
@@ -80,14 +83,13 @@ int symbolic_run(fem_mesh& m, cudaStream_t s);           // fills pattern and se
 // Element products V = X Q.  Any of VM, VK, VT may be null (matrix skipped).
 int element_simt_fp64(const fem_mesh& m, const CoeffDev& k, const double* u, double* VM, double* VK, double* VT,
                       cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);
-// FP32 paths take the nodal values split as u = hi + lo (float2), see split_u.
-int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
+// FP32 paths split each gathered FP64 nodal value as hi + lo (split_f64).
+int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
                       cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);
 // e0, e1: element range [e0, e1) (e1 = -1: to the end); V pointers are the
 // whole-mesh arrays, rows e0.. are written.
-int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const float2* u, float* VM, float* VK, float* VT,
+int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
                       cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);
-int split_u(const double* u, int64_t n, float2* out, cudaStream_t s);
 
 // Segmented reduction of V into CSR values (outputs may be null).
 // s0, s1: slot range [s0, s1) (s1 = -1: to the end); outputs are the
@@ -116,15 +118,17 @@ struct BatchMesh {
     int64_t E, n, nnz;
     int np, type;
     const double* u;                     // FP64 nodal values
-    float2* u2;                          // (hi, lo) split of u for the FP32 paths
     CoeffDev k;
     double mass;
     void* VM; void* VK; void* VT;        // element-matrix scratch (FP32 or FP64)
     const int* seg_ptr;
     const int* contrib;
+    const uint2* seg_head;               // per group of 32 contributions (see fem_mesh)
+    int max_seg, pad2;
     void* vM; void* vK; void* vT;        // CSR outputs, NULL = skip
 };
-// One unit of work: `count` consecutive elements (or slots, or nodes) of one mesh.
+// One unit of work: `count` consecutive elements (or nodes, or groups of 32
+// contributions) of one mesh.
 struct BatchItem {
     int mesh;
     int type;
@@ -144,7 +148,6 @@ template <typename T>
 int batch_simt_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int max_type_smem, int grid,
                       cudaStream_t s);
 int batch_simt_smem(int type, int fp64);
-int batch_split_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, cudaStream_t s);
 template <typename T>
 int batch_scatter_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int block, cudaStream_t s);
 

@@ -3,8 +3,8 @@
 // Section 3 step 3: x = a + B_e xhat with B_e = [x_1 - x_0, ..., x_d - x_0];
 // the element integrals need b_e = |det B_e| and A_e = (B_e^T B_e)^-1 =
 // B_e^-1 B_e^-T (the chain rule J_phi_e = J_phihat B_e^-1).  Algorithm 2
-// line 4 computes "the vector b and the matrix W from mesh related data";
-// Section 5 notes that W and b depend only on the mesh.
+// takes b and W from the mesh alone, and Section 5 lists them among the
+// quantities that never change with u.
 //
 // Output layout (structure of arrays, coalesced for one thread per element):
 //   geo[0*E + e] = b_e,  geo[(1+t)*E + e] = A_e[a][b] for the t-th (a<=b).

@@ -1,15 +1,16 @@
 // scatter.cu -- global assembly of the element matrices into CSR values.
 //
-// Algorithm 2 line 12 ("form the matrices M and C from V_m and V_c and the
-// set of indices of nonzero entries"); Section 3 step 2, eq. assemblage_1:
-// M_ij = sum over elements of the element integrals.  Deterministic, no
-// atomics: every CSR slot adds its contributions in ascending element order,
-// the order of Algorithm 1, so the result is bit-reproducible run to run.
+// The last step of Algorithm 2 (the global matrices from V and the index set
+// of nonzero entries); Section 3 step 2, eq. assemblage_1: M_ij = sum over
+// elements of the element integrals.  Deterministic, no atomics: every CSR
+// slot adds its contributions in a fixed order given by the mesh alone, so
+// the result is bit-reproducible run to run.
 // M and K come from the symmetric element storage (entry (i,j) and (j,i)
 // share V[e][sym(min,max)]), T from the full n_p x n_p storage.
 //
-// One thread per CSR slot sums the slot's contributor list
-// contrib[seg_ptr[s] .. seg_ptr[s+1]) (element entries, ascending).
+// A warp sums 32 consecutive contributions at a time (one lane each) with a
+// segmented scan over the lanes; the slot boundaries come from per-group
+// head masks built by the symbolic phase.
 #include <algorithm>
 #include <vector>
 
@@ -53,108 +54,200 @@ __device__ __forceinline__ void fill_sym_table(short* sym) {
     for (int l = threadIdx.x; l < NP * NP; l += blockDim.x) sym[l] = (short)sym_idx(NP, l / NP, l % NP);
 }
 
-// Segment sum with the loads of consecutive grid-stride iterations
-// overlapped: while slot s adds its V entries, the contributor indices of
-// slot s+G and the segment bounds of slot s+2G are already in flight, so a
-// slot costs about one memory round trip instead of three dependent ones.
-// (A third stage, V of slot s+G, measured slower on GB300.)  The summation
-// order per slot (ascending contributor) is unchanged.
-template <int NP, typename T>
-__global__ void __launch_bounds__(256) scatter_segments_kernel(const int* __restrict__ seg_ptr,
-                                                               const int* __restrict__ contrib, int64_t nnz64,
-                                                               const T* __restrict__ VM, const T* __restrict__ VK,
-                                                               const T* __restrict__ VT, T* __restrict__ vM,
-                                                               T* __restrict__ vK, T* __restrict__ vT) {
-    __shared__ short sym[NP * NP];
-    fill_sym_table<NP>(sym);
-    __syncthreads();
-    const T* vm_src = vM ? VM : nullptr;
-    const T* vk_src = vK ? VK : nullptr;
-    const T* vt_src = vT ? VT : nullptr;
-    constexpr uint32_t NONE = 0xffffffffu;
-    const uint32_t nnz = (uint32_t)nnz64;   // < 2^31 (int32 CSR)
-    const uint32_t G = gridDim.x * blockDim.x;
-    uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nnz) return;
-    const uint32_t* sp = reinterpret_cast<const uint32_t*>(seg_ptr);
-    const uint32_t* cp = reinterpret_cast<const uint32_t*>(contrib);
-    // pipeline registers: bounds of s and s+G, first two contributors of s
-    uint32_t a0 = __ldg(sp + s), b0 = __ldg(sp + s + 1);
-    uint32_t a1 = 0, b1 = 0;
-    if (s + G < nnz) {
-        a1 = __ldg(sp + s + G);
-        b1 = __ldg(sp + s + G + 1);
+// ------------------------------------------------------------ segment sum
+// The contributions, sorted by slot, are cut into groups of 64 consecutive
+// positions; a warp takes one group per step, a lane two adjacent
+// contributions.  The group's head mask (bit j: position 64k+j starts a
+// slot, from two of the symbolic phase's 32-bit words) and the slot of its
+// first position give every lane its slots without reading seg_ptr.  Each
+// lane loads its V entries and adds them within the lane, then a segmented
+// inclusive scan over the lanes (shuffles) leaves every segment's total in
+// the lane of its last contribution, which stores it.  A segment that runs
+// past position 63 is carried into the warp's next group.
+//
+// Ownership: a warp task is a run of TASK groups; it writes the slots whose
+// first contribution lies in its run, reading on past the run's end until
+// its last slot closes.  The additions for a slot follow the fixed pattern
+// of each aligned 64-group (in-lane pairs, then the lane tree), groups in
+// ascending order, so the bits depend only on the mesh: run to run, across
+// launch shapes, slot ranges and the batched kernel.
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ void put3(uint32_t slot, T m, T k, T t, T* __restrict__ vM, T* __restrict__ vK,
+                                     T* __restrict__ vT) {
+    if (vM) vM[slot] = m;
+    if (vK) vK[slot] = k;
+    if (vT) vT[slot] = t;
+}
+
+// A warp step covers 64 consecutive contributions (a "pair group": two of
+// the symbolic phase's 32-groups, read as one 16-byte word pair), lane l the
+// positions q0 = 2l and q1 = 2l + 1.  Within the lane: if q1 starts a slot,
+// q0 ends one (the "first" piece, stored by this lane) and the lane's
+// running piece is V[q1] alone; otherwise the running piece is V[q0] + V[q1].
+// A segmented inclusive scan of the running pieces over the lanes (lane
+// heads: a slot starting at q0 or q1) gives every lane the sum of its
+// running segment so far; a first piece adds the scanned value of the lane
+// before it.  Positions nc and beyond act as the start of a slot, so values
+// loaded for them (indices clamped into the array) never reach a stored sum.
+//
+// Pair groups [k0, k1) of a mesh with `nc` contributions; only slots in
+// [s0, s1) are written.  STEPS lane-scan strides must cover the lanes one
+// slot's running piece spans within a pair group (2 for segments of at
+// most 8 contributions, 4 for at most 32, else 5); more steps than needed
+// leave the sums unchanged.
+//
+// Ownership: the warp writes the slots whose first contribution lies in its
+// pair groups: in the first group the positions from its first head on, in
+// its own groups all positions, and past its last group the positions that
+// continue its last slot (up to the next head).
+//
+// Software pipeline: while pair group k is summed, the V entries of group
+// k+1 and the head words and contributor indices of group k+2 are in flight
+// (V and indices only up to group k1, where a carried slot usually ends).
+template <int NP, typename T, int STEPS>
+__device__ __forceinline__ void segsum_warp(uint32_t k0, uint32_t k1, uint32_t nc, uint32_t s0, uint32_t s1,
+                                            const uint4* __restrict__ head2, const uint32_t* __restrict__ contrib,
+                                            const short* __restrict__ sym, const T* __restrict__ VM,
+                                            const T* __restrict__ VK, const T* __restrict__ VT, T* __restrict__ vM,
+                                            T* __restrict__ vK, T* __restrict__ vT, int lane) {
+    const uint32_t glast = (nc - 1) >> 6;        // last pair group
+    const uint32_t qmax = (nc - 1) & ~1u;        // last even position (pairs are read from an even index)
+    const uint32_t j0 = 2u * lane;               // q0 within the pair group
+    auto hword = [&](uint32_t k) { return __ldg(head2 + (k < glast ? k : glast)); };
+    auto cpair = [&](uint32_t k) {
+        const uint32_t q = (k << 6) + j0, qc = q < qmax ? q : qmax;
+        uint2 c = __ldg(reinterpret_cast<const uint2*>(contrib + qc));
+        if (qc + 1 >= nc) c.y = c.x;   // odd nc: the entry past the end is not a contributor index
+        return c;
+    };
+    uint4 h0 = hword(k0), h1 = hword(k0 + 1);
+    Contribution<NP, T> a0, b0;
+    {
+        const uint2 c = cpair(k0);
+        a0.load(c.x, sym, VM, VK, VT);
+        b0.load(c.y, sym, VM, VK, VT);
     }
-    uint32_t c0 = a0 < b0 ? __ldg(cp + a0) : NONE;
-    uint32_t c1 = a0 + 1 < b0 ? __ldg(cp + a0 + 1) : NONE;
-    while (true) {
-        const uint32_t s1 = s + G, s2 = s + 2 * G;
-        // in flight together: V of slot s, contributors of s+G, bounds of s+2G
-        Contribution<NP, T> x0, x1;
-        if (c0 != NONE) x0.load(c0, sym, vm_src, vk_src, vt_src);
-        if (c1 != NONE) x1.load(c1, sym, vm_src, vk_src, vt_src);
-        uint32_t n0 = NONE, n1 = NONE;
-        if (s1 < nnz) {
-            n0 = a1 < b1 ? __ldg(cp + a1) : NONE;
-            n1 = a1 + 1 < b1 ? __ldg(cp + a1 + 1) : NONE;
+    uint2 c1 = cpair(k0 + 1);
+    uint32_t lo;   // first owned position of the pair group
+    {
+        const uint64_t H = (static_cast<uint64_t>(h0.z) << 32) | h0.x;
+        lo = H ? __ffsll(H) - 1 : 64u;
+    }
+    T cm = T(0), ck = T(0), ct = T(0);   // running sum carried past position 63
+    for (uint32_t k = k0;; ++k) {
+        // prefetch (warp-uniform): V of k+1 while k+1 <= k1 (k1 itself is
+        // the usual continuation group), indices of k+2 while k+2 <= k1;
+        // groups further on are loaded when the carry actually reaches them
+        Contribution<NP, T> a1, b1;
+        if (k + 1 <= k1) {
+            a1.load(c1.x, sym, VM, VK, VT);
+            b1.load(c1.y, sym, VM, VK, VT);
         }
-        uint32_t a2 = 0, b2 = 0;
-        if (s2 < nnz) {
-            a2 = __ldg(sp + s2);
-            b2 = __ldg(sp + s2 + 1);
+        const uint4 h2 = hword(k + 2);
+        const uint2 c2 = k + 2 <= k1 ? cpair(k + 2) : make_uint2(0u, 0u);
+
+        const uint64_t H = (static_cast<uint64_t>(h0.z) << 32) | h0.x;
+        const uint32_t hi = k < k1 ? 64u : (H ? __ffsll(H) - 1 : 64u);   // past k1: up to the next head
+        const uint32_t q0 = (k << 6) + j0, q1 = q0 + 1;
+        const uint32_t two = static_cast<uint32_t>(H >> j0) & 3u;
+        const bool rB = two >> 1;                         // real head at q1
+        const bool hA = (two & 1u) || q0 == nc, hB = rB || q1 == nc;
+        const uint32_t slotA = h0.y + __popcll(H & ((2ull << j0) - 1) & ~1ull);
+        const uint32_t slotB = slotA + (rB ? 1u : 0u);
+        T rm = hB ? b0.m : a0.m + b0.m;
+        T rk = hB ? b0.k : a0.k + b0.k;
+        T rt = hB ? b0.t : a0.t + b0.t;
+        const uint32_t lup = __ballot_sync(FULL, hA || hB) & (FULL >> (31 - lane));
+        const int run = lane - (lup ? 31 - __clz(lup) : 0);
+#pragma unroll
+        for (int i = 0; i < STEPS; ++i) {
+            const int d = 1 << i;
+            const T ym = __shfl_up_sync(FULL, rm, d);
+            const T yk = __shfl_up_sync(FULL, rk, d);
+            const T yt = __shfl_up_sync(FULL, rt, d);
+            if (run >= d) {
+                rm = ym + rm;
+                rk = yk + rk;
+                rt = yt + rt;
+            }
         }
-        T am = T(0), ak = T(0), at = T(0);
-        if (c0 != NONE) {
-            am += x0.m;
-            ak += x0.k;
-            at += x0.t;
+        if (lup == 0) {   // continues the running sum of the previous pair group
+            rm = cm + rm;
+            rk = ck + rk;
+            rt = ct + rt;
         }
-        if (c1 != NONE) {
-            am += x1.m;
-            ak += x1.k;
-            at += x1.t;
+        // the sum before q0 within its segment (lane 0: the carried sum)
+        T pm = __shfl_up_sync(FULL, rm, 1), pk = __shfl_up_sync(FULL, rk, 1), pt = __shfl_up_sync(FULL, rt, 1);
+        if (lane == 0) {
+            pm = cm;
+            pk = ck;
+            pt = ct;
         }
-        for (uint32_t p = a0 + 2; p < b0; ++p) {
-            Contribution<NP, T> x;
-            x.load(__ldg(cp + p), sym, vm_src, vk_src, vt_src);
-            am += x.m;
-            ak += x.k;
-            at += x.t;
+        const bool own0 = j0 >= lo && j0 < hi, own1 = j0 + 1 >= lo && j0 + 1 < hi;
+        if (hB && q0 < nc && own0 && slotA >= s0 && slotA < s1) {
+            const bool alone = two & 1u;   // a head at q0 too: V[q0] is the whole slot
+            put3(slotA, alone ? a0.m : pm + a0.m, alone ? a0.k : pk + a0.k, alone ? a0.t : pt + a0.t, vM, vK, vT);
         }
-        if (vM) vM[s] = am;
-        if (vK) vK[s] = ak;
-        if (vT) vT[s] = at;
-        if (s1 >= nnz || s1 < s) break;
-        s = s1;
-        a0 = a1;
-        b0 = b1;
-        a1 = a2;
-        b1 = b2;
-        c0 = n0;
-        c1 = n1;
+        const uint32_t nxt = lane < 31 ? static_cast<uint32_t>(H >> (lane < 31 ? j0 + 2 : 0)) & 1u : (h1.x & 1u);
+        if ((nxt || q1 + 1 == nc) && q1 < nc && own1 && slotB >= s0 && slotB < s1) put3(slotB, rm, rk, rt, vM, vK, vT);
+        // does position 63's slot (this warp's, in range) go on into pair group k+1?
+        const uint32_t q63 = (k << 6) + 63;
+        const uint32_t slot63 = h0.y + __popcll(H & ~1ull);
+        const bool carry = q63 + 1 < nc && !(h1.x & 1u) && hi == 64u && lo <= 63u && slot63 >= s0 && slot63 < s1;
+        cm = __shfl_sync(FULL, rm, 31);
+        ck = __shfl_sync(FULL, rk, 31);
+        ct = __shfl_sync(FULL, rt, 31);
+        if (k >= glast || (k + 1 >= k1 && !carry)) break;
+        lo = 0;
+        h0 = h1;
+        h1 = h2;
+        if (k + 1 <= k1) {
+            a0 = a1;
+            b0 = b1;
+        } else {   // the carry runs past the prefetched continuation group
+            const uint2 c = cpair(k + 1);
+            a0.load(c.x, sym, VM, VK, VT);
+            b0.load(c.y, sym, VM, VK, VT);
+        }
+        c1 = c2;
     }
 }
 
-// One slot of the segment sum, contributions in ascending order (the same
-// order as the single-mesh kernel, so batched sums carry the same bits).
-template <int NP, typename T>
-__device__ __forceinline__ void segment_slot(int64_t s, const int* __restrict__ seg_ptr,
-                                             const int* __restrict__ contrib, const short* __restrict__ sym,
-                                             const T* __restrict__ VM, const T* __restrict__ VK,
-                                             const T* __restrict__ VT, T* __restrict__ vM, T* __restrict__ vK,
-                                             T* __restrict__ vT) {
-    const int a = __ldg(seg_ptr + s), b = __ldg(seg_ptr + s + 1);
-    T am = T(0), ak = T(0), at = T(0);
-    for (int p = a; p < b; ++p) {
-        Contribution<NP, T> x;
-        x.load((uint32_t)__ldg(contrib + p), sym, VM, VK, VT);
-        am += x.m;
-        ak += x.k;
-        at += x.t;
-    }
-    if (vM) vM[s] = am;
-    if (vK) vK[s] = ak;
-    if (vT) vT[s] = at;
+// Launch shape per scan depth, measured on GB300 (FP32 values): triangle
+// meshes (short segments, 2 scan steps) run best with registers capped for
+// 6 blocks of 256 threads per SM and short warp tasks; tetrahedral meshes
+// (4-5 steps, long segments) with 5 blocks and longer tasks; FP64 values
+// with 4 blocks.
+template <int STEPS, typename T>
+struct SegShape {
+    static constexpr int MIN_BLOCKS = sizeof(T) == 8 ? 4 : STEPS <= 2 ? 6 : 5;
+    static constexpr uint32_t TASK = STEPS <= 2 ? 16 : 32;   // pair groups per warp task (at most)
+};
+
+// Slots [s0, s1) of one mesh; the warps take tasks grid-stride, so the
+// pair groups in flight form one moving window over the slot order
+// (elements shared by nearby rows are re-read from L2).
+template <int NP, typename T, int STEPS>
+__global__ void __launch_bounds__(256, SegShape<STEPS, T>::MIN_BLOCKS)
+    segsum_kernel(const uint4* __restrict__ head2, const uint32_t* __restrict__ contrib, uint32_t nc,
+                  const int* __restrict__ seg_ptr, uint32_t s0, uint32_t s1, uint32_t task, const T* __restrict__ VM,
+                  const T* __restrict__ VK, const T* __restrict__ VT, T* __restrict__ vM, T* __restrict__ vK,
+                  T* __restrict__ vT) {
+    __shared__ short sym[NP * NP];
+    fill_sym_table<NP>(sym);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint32_t a = (uint32_t)__ldg(seg_ptr + s0), b = (uint32_t)__ldg(seg_ptr + s1);
+    const uint32_t g0 = a >> 6, g1 = (b + 63) >> 6;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const T* vm_src = vM ? VM : nullptr;
+    const T* vk_src = vK ? VK : nullptr;
+    const T* vt_src = vT ? VT : nullptr;
+    for (uint32_t t = g0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * task; t < g1; t += nw * task)
+        segsum_warp<NP, T, STEPS>(t, t + task < g1 ? t + task : g1, nc, s0, s1, head2, contrib, sym, vm_src, vk_src,
+                                  vt_src, vM, vK, vT, lane);
 }
 
 // offsets of the per-type symmetric-index tables in the batched kernel
@@ -163,7 +256,9 @@ __host__ __device__ constexpr int sym_tab_off(int np) {
 }
 constexpr int SYM_TAB_TOTAL = 561;
 
-// Batched: the work list holds chunks of `count` slots of many meshes.
+// Batched: one warp per work item (a run of `count` pair groups of one mesh),
+// the same per-warp sum as the single-mesh kernel, so a mesh's CSR values
+// carry the same bits alone and in a batch.
 template <typename T>
 __global__ void __launch_bounds__(512) batch_scatter_kernel(const BatchItem* __restrict__ items, int nitems,
                                                             const BatchMesh* __restrict__ meshes) {
@@ -174,49 +269,77 @@ __global__ void __launch_bounds__(512) batch_scatter_kernel(const BatchItem* __r
     fill_sym_table<10>(sym + sym_tab_off(10));
     fill_sym_table<20>(sym + sym_tab_off(20));
     __syncthreads();
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < nitems; it += nw) {
         const BatchItem w = items[it];
         const BatchMesh& bm = meshes[w.mesh];
-        const T* VM = bm.vM ? static_cast<const T*>(bm.VM) : nullptr;
-        const T* VK = bm.vK ? static_cast<const T*>(bm.VK) : nullptr;
-        const T* VT = bm.vT ? static_cast<const T*>(bm.VT) : nullptr;
         T* vM = static_cast<T*>(bm.vM);
         T* vK = static_cast<T*>(bm.vK);
         T* vT = static_cast<T*>(bm.vT);
+        const T* VM = vM ? static_cast<const T*>(bm.VM) : nullptr;
+        const T* VK = vK ? static_cast<const T*>(bm.VK) : nullptr;
+        const T* VT = vT ? static_cast<const T*>(bm.VT) : nullptr;
         const short* st = sym + sym_tab_off(bm.np);
-        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
-            const int64_t s = w.first + k;
-            if (s >= bm.nnz) break;
-            switch (bm.np) {
-                case 3: segment_slot<3, T>(s, bm.seg_ptr, bm.contrib, st, VM, VK, VT, vM, vK, vT); break;
-                case 4: segment_slot<4, T>(s, bm.seg_ptr, bm.contrib, st, VM, VK, VT, vM, vK, vT); break;
-                case 6: segment_slot<6, T>(s, bm.seg_ptr, bm.contrib, st, VM, VK, VT, vM, vK, vT); break;
-                case 10: segment_slot<10, T>(s, bm.seg_ptr, bm.contrib, st, VM, VK, VT, vM, vK, vT); break;
-                case 20: segment_slot<20, T>(s, bm.seg_ptr, bm.contrib, st, VM, VK, VT, vM, vK, vT); break;
-                default: break;
-            }
+        const uint32_t k0 = (uint32_t)w.first, k1 = k0 + (uint32_t)w.count;
+        const uint32_t nc = (uint32_t)(bm.E * bm.np * bm.np), s1 = (uint32_t)bm.nnz;
+        const uint32_t* cp = reinterpret_cast<const uint32_t*>(bm.contrib);
+        const uint4* h2 = reinterpret_cast<const uint4*>(bm.seg_head);
+#define FEM_BATCH_SEG_CASE(NP_)                                                                               \
+    case NP_:                                                                                                 \
+        segsum_warp<NP_, T, 5>(k0, k1, nc, 0u, s1, h2, cp, st, VM, VK, VT, vM, vK, vT, lane);                   \
+        break;
+        switch (bm.np) {
+            FEM_BATCH_SEG_CASE(3)
+            FEM_BATCH_SEG_CASE(4)
+            FEM_BATCH_SEG_CASE(6)
+            FEM_BATCH_SEG_CASE(10)
+            FEM_BATCH_SEG_CASE(20)
+            default: break;
         }
+#undef FEM_BATCH_SEG_CASE
     }
 }
 
+template <int NP, typename T, int STEPS>
+int launch_steps(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s,
+                 int nsm, int64_t s0, int64_t s1) {
+    // persistent: as many 256-thread blocks as fit on the GPU at once
+    static int occ = 0;   // blocks per SM (the same on every device of the pool)
+    if (!occ) {
+        int o = 0;
+        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, segsum_kernel<NP, T, STEPS>, 256, 0));
+        occ = o > 0 ? o : 1;
+    }
+    const int64_t nc = m.E * m.np * m.np;
+    // tasks of up to TASK pair groups; fewer for small meshes or slot ranges
+    // (groups estimated in proportion to the slots), so that every resident
+    // warp gets work (the sums do not depend on the task size)
+    const int64_t groups = ((nc + 63) / 64) * (s1 - s0) / (m.nnz > 0 ? m.nnz : 1) + 1;
+    const int64_t warps = (int64_t)nsm * occ * 8;
+    int64_t task = (groups + warps - 1) / warps;
+    if (task > SegShape<STEPS, T>::TASK) task = SegShape<STEPS, T>::TASK;
+    if (task < 1) task = 1;
+    int64_t blocks = ((groups + task - 1) / task + 7) / 8;
+    if (blocks > (int64_t)nsm * occ) blocks = (int64_t)nsm * occ;
+    if (blocks < 1) blocks = 1;
+    cudaGetLastError();   // clear any stale error before the launch check
+    segsum_kernel<NP, T, STEPS><<<(unsigned)blocks, 256, 0, s>>>(
+        reinterpret_cast<const uint4*>(m.seg_head.as<uint2>()), reinterpret_cast<const uint32_t*>(m.contrib.as<int>()),
+        (uint32_t)nc,
+        m.seg_ptr.as<int>(), (uint32_t)s0, (uint32_t)s1, (uint32_t)task, VM, VK, VT, vM, vK, vT);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+// lane-scan steps: 2 cover segments of up to 8 contributions (every
+// triangle mesh), 4 up to 32 (the tetrahedral meshes), 5 any
 template <int NP, typename T>
 int launch_np(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s,
               int nsm, int64_t s0, int64_t s1) {
-    {
-        // a slot range [s0, s1): the segment bounds and the outputs offset
-        // by s0 (contributor indices address the whole V)
-        const int B = m.sum_block >= 32 ? m.sum_block : 256;
-        const int64_t ns = s1 - s0;
-        if (ns <= 0) return FEM_OK;
-        int64_t blocks = (ns + B - 1) / B;
-        if (blocks > (int64_t)nsm * (4096 / B)) blocks = (int64_t)nsm * (4096 / B);
-        cudaGetLastError();   // clear any stale error before the launch check
-        scatter_segments_kernel<NP, T><<<(unsigned)blocks, B, 0, s>>>(
-            m.seg_ptr.as<int>() + s0, m.contrib.as<int>(), ns, VM, VK, VT, vM ? vM + s0 : nullptr,
-            vK ? vK + s0 : nullptr, vT ? vT + s0 : nullptr);
-    }
-    FEM_CUDA_TRY(cudaGetLastError());
-    return FEM_OK;
+    if (m.max_seg <= 8) return launch_steps<NP, T, 2>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+    if (m.max_seg <= 32) return launch_steps<NP, T, 4>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+    return launch_steps<NP, T, 5>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
 }
 
 template <typename T>
@@ -247,8 +370,9 @@ int batch_scatter_launch(const BatchItem* items, int nitems, const BatchMesh* me
     int dev = 0, nsm = 0;
     FEM_CUDA_TRY(cudaGetDevice(&dev));
     FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int wpb = block / 32;
     int grid = nsm * (2048 / block);
-    if (grid > nitems) grid = nitems;
+    if ((int64_t)grid * wpb > nitems) grid = (nitems + wpb - 1) / wpb;
     cudaGetLastError();   // clear any stale error before the launch check
     batch_scatter_kernel<T><<<grid, block, 0, s>>>(items, nitems, meshes);
     FEM_CUDA_TRY(cudaGetLastError());

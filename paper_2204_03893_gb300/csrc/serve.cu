@@ -165,7 +165,8 @@ size_t mesh_estimate(const fem_mesh_desc& d, int prec) {
     size_t b = n * d.dim * 8 + E * np * 4 + ngeo * E * 12;
     b += (n + 1) * 4 * 5;                 // row_ptr, inc_ptr and three transient counters of the sort
     b += m2 * 4 * 4 + E * np * 4;         // col_idx and seg_ptr (nnz <= m2), contrib, slot, inc
-    b += esz_of(prec) * E * (np * (np + 1) + np * np) + n * 8 + n * 8;   // V scratch, u split, u
+    b += (m2 / 32 + 2) * 8;               // segment heads per group of 32 contributions
+    b += esz_of(prec) * E * (np * (np + 1) + np * np) + n * 8;   // V scratch, u
     return b + 4096;                      // rounding of small buffers
 }
 

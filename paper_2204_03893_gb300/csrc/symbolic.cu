@@ -2,8 +2,8 @@
 //
 // Section 3 step 2: the integral of an element contributes to (i, j) only if
 // both nodes belong to the element (the index set N_e), which makes the
-// matrix sparse; Algorithm 2 line 12 forms the global matrix from V and "the
-// set of indices of nonzero entries".  This module builds that set on the
+// matrix sparse; Algorithm 2 ends by summing V into the global matrix over
+// the index set of its nonzero entries.  This module builds that set on the
 // device by sorting the keys (row, col) = (conn[e][i], conn[e][j]) of every
 // element entry c = (e n_p + i) n_p + j:
 //   1. counting sort of the (e, i) incidences by row (integer atomics for
@@ -14,7 +14,10 @@
 //   3. a scan of the per-row unique-column counts gives row_ptr;
 //   4. per row, one warp walks the sorted entries and numbers the column
 //      groups: col_idx, seg_ptr (first sorted position of each slot) and the
-//      slot map slot[c].
+//      slot map slot[c];
+//   5. the same walk marks, for every group of 32 consecutive sorted
+//      positions, which of them start a slot (a bit mask) and the slot of its
+//      first position: what the CSR sum reads instead of seg_ptr.
 // contrib[] holds the element entries sorted by (slot, c); seg_ptr[s] ..
 // seg_ptr[s+1] is slot s's segment.  Everything is integer work and fully
 // deterministic.
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(256) row_finish(const int* __restrict__ conn, 
                                                   const int* __restrict__ inc_ptr, const int* __restrict__ row_ptr,
                                                   const int* __restrict__ contrib, int64_t n,
                                                   int* __restrict__ col_idx, int* __restrict__ seg_ptr,
-                                                  int* __restrict__ slot) {
+                                                  int* __restrict__ slot, uint2* __restrict__ head) {
     int lane = threadIdx.x & 31;
     int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     int np2 = np * np;
@@ -210,13 +213,15 @@ __global__ void __launch_bounds__(256) row_finish(const int* __restrict__ conn, 
             int col = valid ? conn[(int64_t)(c / np2) * np + c % np] : INT_MAX;
             int prev = __shfl_up_sync(0xffffffffu, col, 1);
             if (lane == 0) prev = carry;
-            bool head = valid && col != prev;
-            unsigned mask = __ballot_sync(0xffffffffu, head);
+            bool is_head = valid && col != prev;
+            unsigned mask = __ballot_sync(0xffffffffu, is_head);
             int idx = count + __popc(mask & le) - 1;
             if (valid) slot[c] = slot0 + idx;
-            if (head) {
+            if (valid && (p & 31) == 0) head[p >> 5].y = (unsigned)(slot0 + idx);
+            if (is_head) {
                 col_idx[slot0 + idx] = col;
                 seg_ptr[slot0 + idx] = (int)p;
+                atomicOr(&head[p >> 5].x, 1u << (p & 31));
             }
             count += __popc(mask);
             carry = __shfl_sync(0xffffffffu, col, 31);
@@ -225,6 +230,16 @@ __global__ void __launch_bounds__(256) row_finish(const int* __restrict__ conn, 
 }
 
 __global__ void set_last(int* p, int64_t idx, int v) { p[idx] = v; }
+
+// longest segment seg_ptr[s+1] - seg_ptr[s] (warp maximum, one atomic per warp)
+__global__ void seg_max(const int* __restrict__ seg_ptr, int64_t nnz, int* __restrict__ out) {
+    int best = 0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x)
+        best = max(best, seg_ptr[s + 1] - seg_ptr[s]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+}
 
 int grid_for(int64_t work, int threads, int64_t cap = 152 * 32) {
     int64_t b = (work + threads - 1) / threads;
@@ -282,15 +297,27 @@ int symbolic_run(fem_mesh& m, cudaStream_t s) {
     m.nnz = nnz;
     if ((rc = buf_alloc(m.col_idx, sizeof(int) * (size_t)(nnz + 1), s))) return rc;
     if ((rc = buf_alloc(m.seg_ptr, sizeof(int) * (size_t)(nnz + 1), s))) return rc;
+    const int64_t ngroups = (m2 + 31) / 32;
+    if ((rc = buf_alloc(m.seg_head, sizeof(uint2) * (size_t)(ngroups + 1), s))) return rc;
+    FEM_CUDA_TRY(cudaMemsetAsync(m.seg_head.ptr, 0, m.seg_head.bytes, s));
     row_finish<<<grid_for(n, 8, 152 * 64), 256, 0, s>>>(conn, np, m.inc_ptr.as<int>(), m.row_ptr.as<int>(),
                                                         m.contrib.as<int>(), n, m.col_idx.as<int>(),
-                                                        m.seg_ptr.as<int>(), m.slot.as<int>());
+                                                        m.seg_ptr.as<int>(), m.slot.as<int>(),
+                                                        m.seg_head.as<uint2>());
     set_last<<<1, 1, 0, s>>>(m.seg_ptr.as<int>(), nnz, (int)m2);
     FEM_CUDA_TRY(cudaGetLastError());
+    // the longest segment bounds the steps of the CSR sum's warp scans
+    int* dmax = cnt.as<int>();   // the incidence counts are no longer needed
+    FEM_CUDA_TRY(cudaMemsetAsync(dmax, 0, sizeof(int), s));
+    seg_max<<<grid_for(nnz, 256, 152 * 8), 256, 0, s>>>(m.seg_ptr.as<int>(), nnz, dmax);
+    FEM_CUDA_TRY(cudaGetLastError());
+    int maxseg = 0;
+    FEM_CUDA_TRY(cudaMemcpyAsync(&maxseg, dmax, sizeof(int), cudaMemcpyDeviceToHost, s));
     buf_free(cnt, s);
     buf_free(fill, s);
     buf_free(row_nnz, s);
     FEM_CUDA_TRY(cudaStreamSynchronize(s));
+    m.max_seg = maxseg;
     m.have_pattern = true;
     return FEM_OK;
 }

@@ -128,3 +128,27 @@ def test_range_errors():
     with pytest.raises(F.FemError) as ei:
         F.fem_sum_elements_range(fm.h, F.FEM_TF32X3, 0, fm.nnz + 1, out, None, None, None)
     assert ei.value.code == F.FEM_EINVAL
+
+
+@pytest.mark.parametrize("name", ["tri_p2", "tet_p1", "fan"])
+def test_sum_ranges_at_arbitrary_slots(name):
+    """Slot ranges cut anywhere (inside long segments' neighbourhoods, one
+    slot wide, empty) sum to the same bits as one whole sum: every slot's
+    additions follow the fixed groups of 32 contributions, whatever range
+    or launch covers it."""
+    m = mg.fan_tri(300, seed=2) if name == "fan" else mesh_of(name)
+    fm = FemMesh.of(m)
+    fm.symbolic()
+    u = torch.tensor(mg.fourier_field(m.coords, 67), dtype=torch.float64, device="cuda")
+    k = F.coeff("poly", (1.0, 0.5, 0.25))
+    ref = whole(fm, k, u, "tf32x3")
+    nnz = fm.nnz
+    rng = np.random.default_rng(68)
+    cuts = sorted(set([0, nnz, 1, nnz - 1, nnz // 2, nnz // 2 + 1] + list(rng.integers(0, nnz, 9))))
+    out = {c: torch.full((nnz,), float("nan"), device="cuda") for c in "MKT"}
+    for a, b in zip(cuts, cuts[1:]):
+        F.fem_sum_elements_range(fm.h, F.FEM_TF32X3, int(a), int(b), out["M"], out["K"], out["T"], None)
+    F.fem_sum_elements_range(fm.h, F.FEM_TF32X3, 5, 5, out["M"], out["K"], out["T"], None)   # empty
+    torch.cuda.synchronize()
+    for c in "MKT":
+        assert torch.equal(out[c], ref[c]), c

@@ -192,6 +192,25 @@ def test_host_pointer_path_matches_device(prec):
         assert np.array_equal(outs[k], d[k].cpu().numpy()), k
 
 
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_pinned_host_outputs_match_device(prec):
+    """Page-locked and pageable host outputs, mixed in one call, carry the
+    same bits as device outputs."""
+    wl = wl_small("tet_p1")
+    fm = FemMesh.of(wl.mesh)
+    fm.symbolic()
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    uh = torch.tensor(wl.u, dtype=torch.float64).pin_memory()
+    pinned = {k: torch.full((fm.nnz,), float("nan"), dtype=dt).pin_memory() for k in "MK"}
+    pageable = np.full(fm.nnz, np.nan, dtype=np.float64 if prec == "fp64" else np.float32)
+    F.fem_assemble_all(fm.h, F.coeff(wl.coeff.kind, wl.coeff.params), uh, F.torch_api.PRECISIONS[prec],
+                       pinned["M"], pinned["K"], pageable)
+    d = fm.assemble(torch.tensor(wl.u, device="cuda"), wl.coeff.kind, wl.coeff.params, prec)
+    torch.cuda.synchronize()
+    assert torch.equal(pinned["M"], d["M"].cpu()) and torch.equal(pinned["K"], d["K"].cpu())
+    assert np.array_equal(pageable, d["T"].cpu().numpy())
+
+
 def test_coefficient_laws():
     """sin and piecewise-linear laws against the oracle (FP64 per entry)."""
     m = mg.structured_tri(12, 2, 0.2, seed=5)
