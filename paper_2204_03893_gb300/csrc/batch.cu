@@ -224,7 +224,7 @@ int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts,
     for (int i = 0; i < n; ++i) {
         fem_mesh* m = meshes[i];
         const size_t nsym = (size_t)m->np * (m->np + 1) / 2, nt = (size_t)m->np * m->np;
-        if ((rc = buf_alloc(m->VM, esz * (size_t)m->E * nsym, s)) || (rc = buf_alloc(m->VK, esz * (size_t)m->E * nsym, s)) ||
+        if ((rc = buf_alloc(m->VMK, 2 * esz * (size_t)m->E * nsym, s)) ||
             (rc = buf_alloc(m->VT, esz * (size_t)m->E * nt, s))) {
             fem_batch_destroy(b);
             return rc;
@@ -241,8 +241,8 @@ int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts,
         h.np = m->np;
         h.type = m->type;
         h.mass = m->m;
-        h.VM = m->VM.ptr;
-        h.VK = m->VK.ptr;
+        h.VM = m->VMK.ptr;
+        h.VK = static_cast<unsigned char*>(m->VMK.ptr) + esz;   // K: the odd positions
         h.VT = m->VT.ptr;
         h.seg_ptr = m->seg_ptr.as<int>();
         h.contrib = m->contrib.as<int>();
@@ -319,13 +319,13 @@ int fem_batch_launch(fem_batch* b, const fem_coeff* k, const double* const* d_u,
         fem_mesh* m = b->meshes[i];
         const size_t nsym = (size_t)m->np * (m->np + 1) / 2, nt = (size_t)m->np * m->np;
         int rc0;
-        if ((rc0 = buf_alloc(m->VM, esz * (size_t)m->E * nsym, s)) || (rc0 = buf_alloc(m->VK, esz * (size_t)m->E * nsym, s)) ||
+        if ((rc0 = buf_alloc(m->VMK, 2 * esz * (size_t)m->E * nsym, s)) ||
             (rc0 = buf_alloc(m->VT, esz * (size_t)m->E * nt, s)))
             return rc0;
         m->v_prec = -1;
         BatchMesh h = b->host[i];
-        h.VM = m->VM.ptr;
-        h.VK = m->VK.ptr;
+        h.VM = m->VMK.ptr;
+        h.VK = static_cast<unsigned char*>(m->VMK.ptr) + esz;   // K: the odd positions
         h.VT = m->VT.ptr;
         h.vM = d_vM ? d_vM[i] : nullptr;
         h.vK = d_vK ? d_vK[i] : nullptr;

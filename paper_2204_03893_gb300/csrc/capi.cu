@@ -146,13 +146,10 @@ int form_t(fem_mesh* m, const fem_coeff* k, const double* ud, int prec, int mask
     const int nsym = m->np * (m->np + 1) / 2, nt = m->np * m->np;
     int rc;
     T *VM = nullptr, *VK = nullptr, *VT = nullptr;
-    if (mask & 1) {
-        if ((rc = buf_alloc(m->VM, sizeof(T) * (size_t)E * nsym, s))) return rc;
-        VM = m->VM.as<T>();
-    }
-    if (mask & 2) {
-        if ((rc = buf_alloc(m->VK, sizeof(T) * (size_t)E * nsym, s))) return rc;
-        VK = m->VK.as<T>();
+    if (mask & 3) {   // M and K share one interleaved array: M at even, K at odd positions
+        if ((rc = buf_alloc(m->VMK, 2 * sizeof(T) * (size_t)E * nsym, s))) return rc;
+        if (mask & 1) VM = m->VMK.as<T>();
+        if (mask & 2) VK = m->VMK.as<T>() + 1;
     }
     if (mask & 4) {
         if ((rc = buf_alloc(m->VT, sizeof(T) * (size_t)E * nt, s))) return rc;
@@ -175,8 +172,8 @@ int form_t(fem_mesh* m, const fem_coeff* k, const double* ud, int prec, int mask
 // Global assembly (the last step of Algorithm 2) of the formed V into CSR values.
 template <typename T>
 int sum_t(fem_mesh* m, T* vM, T* vK, T* vT, cudaStream_t s, int64_t s0 = 0, int64_t s1 = -1) {
-    const T* VM = vM ? m->VM.as<T>() : nullptr;
-    const T* VK = vK ? m->VK.as<T>() : nullptr;
+    const T* VM = vM ? m->VMK.as<T>() : nullptr;
+    const T* VK = vK ? m->VMK.as<T>() + 1 : nullptr;
     const T* VT = vT ? m->VT.as<T>() : nullptr;
     if constexpr (sizeof(T) == 8) return scatter_fp64(*m, VM, VK, VT, vM, vK, vT, s, s0, s1);
     else return scatter_fp32(*m, VM, VK, VT, vM, vK, vT, s, s0, s1);
@@ -283,7 +280,7 @@ CoeffDev coeff_to_device(const fem_coeff* k) { return to_dev(k); }
 
 size_t fem_mesh::device_bytes() const {
     const fem::DevBuf* bufs[] = {&coords, &conn, &geo64, &geo32, &row_ptr, &col_idx, &seg_ptr, &contrib, &slot,
-                                 &seg_head, &inc_ptr, &inc, &VM, &VK, &VT, &u_stage, &out_stage};
+                                 &seg_head, &inc_ptr, &inc, &VMK, &VT, &u_stage, &out_stage};
     size_t t = 0;
     for (auto* b : bufs) t += b->bytes;
     return t;
@@ -376,7 +373,7 @@ int fem_mesh_destroy(fem_mesh* m) {
     if (!m) return FEM_OK;
     cudaDeviceSynchronize();
     fem::DevBuf* bufs[] = {&m->coords, &m->conn, &m->geo64, &m->geo32, &m->row_ptr, &m->col_idx, &m->seg_ptr,
-                           &m->contrib, &m->slot, &m->seg_head, &m->inc_ptr, &m->inc, &m->VM, &m->VK, &m->VT, &m->u_stage,
+                           &m->contrib, &m->slot, &m->seg_head, &m->inc_ptr, &m->inc, &m->VMK, &m->VT, &m->u_stage,
                            &m->out_stage};
     for (auto* b : bufs) buf_free(*b, nullptr);
     cudaDeviceSynchronize();

@@ -127,9 +127,10 @@ __device__ __forceinline__ void simt_element(int64_t e, const int* __restrict__ 
             X[KM + KK + q * D + a] = ld * s;
         }
     }
-    // --- V = X Q, chunks of CH outputs
+    // --- V = X Q, chunks of CH outputs; entry n of the element at
+    // V[(e N + n) CS] (CS = 2: M and K interleaved, K at VK = VM + 1)
     constexpr int CH = 8;
-    auto product = [&](const T* Xs, int K, const T* Qm, int N, T* V) {
+    auto product = [&](const T* Xs, int K, const T* Qm, int N, T* V, int CS) {
 #pragma unroll 1
         for (int n0 = 0; n0 < N; n0 += CH) {
             T acc[CH];
@@ -145,12 +146,12 @@ __device__ __forceinline__ void simt_element(int64_t e, const int* __restrict__ 
             }
 #pragma unroll
             for (int c = 0; c < CH; ++c)
-                if (n0 + c < N) V[e * N + n0 + c] = acc[c];
+                if (n0 + c < N) V[(e * N + n0 + c) * CS] = acc[c];
         }
     };
-    if (VM) product(X, KM, Q + QM_O, ETy::NSYM, VM);
-    if (VK) product(X + KM, KK, Q + QK_O, ETy::NSYM, VK);
-    if (VT) product(X + KM + KK, KT, Q + QT_O, ETy::NT, VT);
+    if (VM) product(X, KM, Q + QM_O, ETy::NSYM, VM, 2);
+    if (VK) product(X + KM, KK, Q + QK_O, ETy::NSYM, VK, 2);
+    if (VT) product(X + KM + KK, KT, Q + QT_O, ETy::NT, VT, 1);
 }
 
 template <typename ETy, typename T>
@@ -228,7 +229,7 @@ int launch_simt(const fem_mesh& m, const CoeffDev& k, const double* u, const T* 
     if (grid < 1) return FEM_OK;
     cudaGetLastError();   // clear any stale error before the launch check
     kern<<<(unsigned)grid, BT, smem, s>>>(m.conn.as<int>() + e0 * ETy::NP, geo + e0, E, m.E, u, k, (T)m.m,
-                                          VM ? VM + e0 * ETy::NSYM : nullptr, VK ? VK + e0 * ETy::NSYM : nullptr,
+                                          VM ? VM + 2 * e0 * ETy::NSYM : nullptr, VK ? VK + 2 * e0 * ETy::NSYM : nullptr,
                                           VT ? VT + e0 * ETy::NT : nullptr);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;

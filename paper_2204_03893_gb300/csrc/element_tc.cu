@@ -166,17 +166,36 @@ __device__ __forceinline__ void issue_tile(uint32_t tmem, uint32_t sXu, uint32_t
                              tc::idesc_tf32(L::NTp));
 }
 
+// The warp's block `blk` (32 rows of NF floats, the image of V rows
+// row0..row0+31) -> V: lane 0 hands the whole block to one bulk copy
+// (cp.async.bulk shared -> global; the block and V + row0 NF are 16-byte
+// aligned since row0 is a multiple of 32).  The caller waits for the bulk
+// reads before it reuses the block.  A partial last block (rows past E) is
+// copied by the warp with plain stores.
+template <int NF>
+__device__ __forceinline__ void block_out(const float* blk, float* __restrict__ V, int64_t row0, int64_t E,
+                                          int lane) {
+    static_assert((32 * NF * 4) % 16 == 0, "bulk block size");
+    if (E - row0 >= 32) {
+        tc::fence_proxy_async_smem();   // this thread's row -> visible to the copy engine
+        __syncwarp();
+        if (lane == 0) tc::bulk_s2g(V + row0 * NF, tc::smem_u32(blk), 32u * NF * 4u);
+    } else {
+        __syncwarp();
+        const int rows = E - row0 < 32 ? (int)(E - row0) : 32;
+        const int nf = rows * NF, nv = nf >> 2;
+        float* g = V + row0 * NF;   // 16-byte aligned (row0 is a multiple of 32)
+        for (int i = lane; i < nv; i += 32) reinterpret_cast<float4*>(g)[i] = reinterpret_cast<const float4*>(blk)[i];
+        for (int i = (nv << 2) + lane; i < nf; i += 32) g[i] = blk[i];
+        __syncwarp();
+    }
+}
+
 // TMEM (this warp's 32 lanes = 32 consecutive elements, columns col..col+N)
-// -> V with the copy engine: every thread writes its row into the warp's
-// block `blk` (32 N floats, the image of V rows row0..row0+31), and lane 0
-// hands the whole block to one bulk copy (cp.async.bulk shared -> global;
-// the block and V + row0 N are 16-byte aligned since row0 is a multiple of
-// 32).  The caller waits for the bulk reads before it reuses the block.  A
-// partial last block (rows past E) is copied by the warp with plain stores.
+// -> V: every thread writes its row into the warp's block, then block_out.
 template <int N>
 __device__ __forceinline__ void epilogue_bulk(uint32_t tmem, int col, float* blk, float* __restrict__ V, int64_t row0,
                                               int64_t E, int warp, int lane) {
-    static_assert((32 * N * 4) % 16 == 0, "bulk block size");
     if (row0 >= E) return;   // warp-uniform
 #pragma unroll 1
     for (int c0 = 0; c0 < N; c0 += 32) {
@@ -196,38 +215,62 @@ __device__ __forceinline__ void epilogue_bulk(uint32_t tmem, int col, float* blk
                 if (c0 + j < N) dst[j] = __uint_as_float(r[j]);
         }
     }
-    if (E - row0 >= 32) {
-        tc::fence_proxy_async_smem();   // this thread's row -> visible to the copy engine
-        __syncwarp();
-        if (lane == 0) tc::bulk_s2g(V + row0 * N, tc::smem_u32(blk), 32u * N * 4u);
-    } else {
-        __syncwarp();
-        const int rows = E - row0 < 32 ? (int)(E - row0) : 32;
-        const int nf = rows * N, nv = nf >> 2;
-        float* g = V + row0 * N;   // 16-byte aligned (row0 is a multiple of 32)
-        for (int i = lane; i < nv; i += 32) reinterpret_cast<float4*>(g)[i] = reinterpret_cast<const float4*>(blk)[i];
-        for (int i = (nv << 2) + lane; i < nf; i += 32) g[i] = blk[i];
-        __syncwarp();
-    }
+    block_out<N>(blk, V, row0, E, lane);
 }
 
-// The epilogue of one tile (M, K, T as requested) through the X region of
-// shared memory (`stage`, free once the MMAs are complete).  Where the three
-// matrices' blocks fit side by side, all copies are in flight at once;
-// otherwise the warp's one block is reused and each copy's reads are waited
-// for first.  Returns with every bulk read of this warp complete, so the
+// M and K (TMEM columns colM.., colK.., NS symmetric entries each) -> the
+// interleaved V_MK rows (entry s of an element at 2s for M, 2s + 1 for K):
+// each thread stores (M_s, K_s) pairs into its row of the warp's block (an
+// unrequested matrix's half is written as 0), then block_out.  The 8-byte
+// stores of a half-warp hit distinct bank pairs (row stride 2 NS floats,
+// NS odd) or at worst two.
+template <int NS>
+__device__ __forceinline__ void epilogue_mk_bulk(uint32_t tmem, int colM, int colK, float* blk,
+                                                 float* __restrict__ VMK, bool doM, bool doK, int64_t row0, int64_t E,
+                                                 int warp, int lane) {
+    if (row0 >= E) return;   // warp-uniform
+    // columns per TMEM load: the narrowest shape that covers a small NS
+    constexpr int W = NS <= 8 ? 8 : NS <= 16 ? 16 : 32;
+    const uint32_t lanes = static_cast<uint32_t>(warp * 32) << 16;
+#pragma unroll 1
+    for (int c0 = 0; c0 < NS; c0 += W) {
+        uint32_t rm[W], rk[W];
+        if (doM) {
+            tc::tmem_ld<W>(tmem + lanes + colM + c0, rm);
+        } else {
+#pragma unroll
+            for (int j = 0; j < W; ++j) rm[j] = 0u;
+        }
+        if (doK) {
+            tc::tmem_ld<W>(tmem + lanes + colK + c0, rk);
+        } else {
+#pragma unroll
+            for (int j = 0; j < W; ++j) rk[j] = 0u;
+        }
+        float* dst = blk + lane * 2 * NS + 2 * c0;
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+            if (c0 + j < NS)
+                *reinterpret_cast<float2*>(dst + 2 * j) = make_float2(__uint_as_float(rm[j]), __uint_as_float(rk[j]));
+    }
+    block_out<2 * NS>(blk, VMK, row0, E, lane);
+}
+
+// The epilogue of one tile (M and K interleaved, T, as requested) through
+// the X region of shared memory (`stage`, free once the MMAs are complete).
+// Where both blocks fit side by side, both copies are in flight at once;
+// otherwise the warp's one block is reused and the first copy's reads are
+// waited for.  Returns with every bulk read of this warp complete, so the
 // caller may overwrite the region after a block barrier.
 template <typename ETy, int XEND>
 __device__ __forceinline__ void epilogue_tile(uint32_t tmem, int colM, int colK, int colT, float* stage,
-                                              float* __restrict__ VM, float* __restrict__ VK, float* __restrict__ VT,
-                                              bool doM, bool doK, bool doT, int64_t row0, int64_t E, int warp,
-                                              int lane) {
-    constexpr int NSYM = ETy::NSYM, NT = ETy::NT;
-    constexpr bool DISJOINT = TILE * (2 * NSYM + NT) * 4 <= XEND;
-    static_assert(TILE * NT * 4 <= XEND, "epilogue blocks do not fit the X region");
-    float* bM = DISJOINT ? stage + warp * 32 * NSYM : stage + warp * 32 * NT;
-    float* bK = DISJOINT ? stage + TILE * NSYM + warp * 32 * NSYM : bM;
-    float* bT = DISJOINT ? stage + 2 * TILE * NSYM + warp * 32 * NT : bM;
+                                              float* __restrict__ VMK, float* __restrict__ VT, bool doM, bool doK,
+                                              bool doT, int64_t row0, int64_t E, int warp, int lane) {
+    constexpr int NMK = 2 * ETy::NSYM, NT = ETy::NT, NMAX = NMK > NT ? NMK : NT;
+    constexpr bool DISJOINT = TILE * (NMK + NT) * 4 <= XEND;
+    static_assert(TILE * NMAX * 4 <= XEND, "epilogue blocks do not fit the X region");
+    float* bMK = DISJOINT ? stage + warp * 32 * NMK : stage + warp * 32 * NMAX;
+    float* bT = DISJOINT ? stage + TILE * NMK + warp * 32 * NT : bMK;
     auto drain = [&]() {
         if (lane == 0) {
             tc::bulk_commit();
@@ -235,10 +278,8 @@ __device__ __forceinline__ void epilogue_tile(uint32_t tmem, int colM, int colK,
         }
         __syncwarp();
     };
-    if (doM) epilogue_bulk<NSYM>(tmem, colM, bM, VM, row0, E, warp, lane);
-    if (!DISJOINT && doM) drain();
-    if (doK) epilogue_bulk<NSYM>(tmem, colK, bK, VK, row0, E, warp, lane);
-    if (!DISJOINT && doK) drain();
+    if (doM || doK) epilogue_mk_bulk<ETy::NSYM>(tmem, colM, colK, bMK, VMK, doM, doK, row0, E, warp, lane);
+    if (!DISJOINT && (doM || doK)) drain();
     if (doT) epilogue_bulk<NT>(tmem, colT, bT, VT, row0, E, warp, lane);
     drain();
 }
@@ -247,7 +288,9 @@ __device__ __forceinline__ void epilogue_tile(uint32_t tmem, int colM, int colK,
 // 32 x 33 staging tile per warp (stage + warp 32 x 33 floats): each store
 // instruction writes one row.  Used where the whole-block staging of
 // `epilogue` would not fit (the chunked product's 400-column T).
-template <int N, int LD = N>
+// Column c of a row lands at V[row LD + c_off + c CS] (CS = 2: one half of
+// the interleaved M/K storage).
+template <int N, int LD = N, int CS = 1>
 __device__ __forceinline__ void epilogue_staged(uint32_t tmem, int col, float* stage_base, float* __restrict__ V,
                                                 int64_t row0, int64_t E, int warp, int lane, int c_off = 0) {
     float* stage = stage_base + warp * 32 * 33;
@@ -262,7 +305,7 @@ __device__ __forceinline__ void epilogue_staged(uint32_t tmem, int col, float* s
         for (int rr = 0; rr < 32; ++rr) {
             int64_t er = row0 + rr;
             int c = c0 + lane;
-            if (er < E && c < N) V[er * LD + c_off + c] = stage[rr * 33 + lane];
+            if (er < E && c < N) V[er * LD + c_off + c * CS] = stage[rr * 33 + lane];
         }
         __syncwarp();
     }
@@ -365,6 +408,7 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
     const uint32_t sQu = tc::smem_u32(sQ), sXu = tc::smem_u32(sX);
     const bool doM = VM != nullptr, doK = VK != nullptr, doT = VT != nullptr;
     const bool need_u = doK | doT;
+    float* VMK = doM ? VM : doK ? VK - 1 : nullptr;   // interleaved M/K storage (K at odd positions)
     float* stage = reinterpret_cast<float*>(sX);   // epilogue blocks (the X tile is consumed by then)
     uint32_t phase = 0;
     bool timed_out = false;
@@ -433,7 +477,7 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
         }
         tc::fence_after_sync();
         const int64_t row0 = tile * TILE + warp * 32;
-        epilogue_tile<ETy, L::XEND>(tmem, L::COLM, L::COLK, L::COLT, stage, VM, VK, VT, doM, doK, doT, row0, E, warp,
+        epilogue_tile<ETy, L::XEND>(tmem, L::COLM, L::COLK, L::COLT, stage, VMK, VT, doM, doK, doT, row0, E, warp,
                                     lane);
         tc::fence_before_sync();
         __syncthreads();
@@ -499,8 +543,7 @@ __device__ __forceinline__ bool batch_tc_tile(const BatchMesh& bm, int64_t first
     float* stage = reinterpret_cast<float*>(sX);
     const int64_t row0 = first + warp * 32;
     epilogue_tile<ETy, L::XEND>(tmem, L::COLM, L::COLK, L::COLT, stage, static_cast<float*>(bm.VM),
-                                static_cast<float*>(bm.VK), static_cast<float*>(bm.VT), doM, doK, doT, row0, E, warp,
-                                lane);
+                                static_cast<float*>(bm.VT), doM, doK, doT, row0, E, warp, lane);
     tc::fence_before_sync();
     __syncthreads();
     return true;
@@ -715,6 +758,7 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
     constexpr int NP = ETy::NP, NS = ETy::NS;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool doM = VM != nullptr, doK = VK != nullptr, doT = VT != nullptr;
+    float* VMK = doM ? VM : doK ? VK - 1 : nullptr;   // interleaved M/K storage (K at odd positions)
     const bool need_u = doK | doT;
     const int64_t e = first + tid;
     // element data for the whole tile: u differences (hi/lo split, as in
@@ -812,8 +856,8 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
         // drain the pass's accumulator once its last chunk is in (the stage
         // area aliases the X chunk, which the completed MMAs no longer read)
         if (active && L::last_of_pass(s)) {
-            if (kd == 0) epilogue_staged<ETy::NSYM>(tmem, 0, stage, VM, row0, E, warp, lane);
-            else if (kd == 1) epilogue_staged<ETy::NSYM>(tmem, 0, stage, VK, row0, E, warp, lane);
+            if (kd == 0) epilogue_staged<ETy::NSYM, 2 * ETy::NSYM, 2>(tmem, 0, stage, VMK, row0, E, warp, lane, 0);
+            else if (kd == 1) epilogue_staged<ETy::NSYM, 2 * ETy::NSYM, 2>(tmem, 0, stage, VMK, row0, E, warp, lane, 1);
             else if (kd == 2) epilogue_staged<L::NTa, ETy::NT>(tmem, 0, stage, VT, row0, E, warp, lane, 0);
             else epilogue_staged<ETy::NT - L::NTa, ETy::NT>(tmem, 0, stage, VT, row0, E, warp, lane, L::NTa);
             tc::fence_before_sync();
@@ -1071,8 +1115,8 @@ int launch_tc_chunked(const fem_mesh& m, const CoeffDev& k, const double* u, flo
     trace_launch("element_tc_chunked_kernel", grid, TILE, sh.smem, sh.occ);
     cudaGetLastError();   // clear any stale error before the launch check
     kern<<<(unsigned)grid, TILE, sh.smem, s>>>(m.conn.as<int>() + e0 * ETy::NP, m.geo32.as<float>() + e0, E, m.E, u, k,
-                                               (float)m.m, VM ? VM + e0 * ETy::NSYM : nullptr,
-                                               VK ? VK + e0 * ETy::NSYM : nullptr, VT ? VT + e0 * ETy::NT : nullptr,
+                                               (float)m.m, VM ? VM + 2 * e0 * ETy::NSYM : nullptr,
+                                               VK ? VK + 2 * e0 * ETy::NSYM : nullptr, VT ? VT + e0 * ETy::NT : nullptr,
                                                static_cast<const unsigned char*>(sh.img), sh.err);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
@@ -1144,8 +1188,8 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, 
         trace_launch("element_tc_kernel", grid, TILE, sh.smem, sh.occ);
         cudaGetLastError();   // clear any stale error before the launch check
         kern<<<(unsigned)grid, TILE, sh.smem, s>>>(m.conn.as<int>() + e0 * ETy::NP, m.geo32.as<float>() + e0, E, m.E, u,
-                                                   k, (float)m.m, VM ? VM + e0 * ETy::NSYM : nullptr,
-                                                   VK ? VK + e0 * ETy::NSYM : nullptr,
+                                                   k, (float)m.m, VM ? VM + 2 * e0 * ETy::NSYM : nullptr,
+                                                   VK ? VK + 2 * e0 * ETy::NSYM : nullptr,
                                                    VT ? VT + e0 * ETy::NT : nullptr, static_cast<const float*>(sh.img),
                                                    sh.err);
         FEM_CUDA_TRY(cudaGetLastError());

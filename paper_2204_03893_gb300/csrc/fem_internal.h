@@ -67,7 +67,9 @@ struct fem_mesh {
     bool have_plan = false;
     std::vector<int64_t> plan_e, plan_s;
     // numeric scratch: element matrices V (per matrix) in the precision of the last call
-    fem::DevBuf VM, VK, VT;
+    // M and K interleaved (element e, symmetric entry s: M at 2(e n_sym + s),
+    // K at 2(e n_sym + s) + 1), T row-major n_p x n_p per element
+    fem::DevBuf VMK, VT;
     int v_prec = -1, v_mask = 0;        // what VM/VK/VT currently hold
     // staging for host-pointer arguments
     fem::DevBuf u_stage, out_stage;
@@ -120,7 +122,8 @@ struct BatchMesh {
     const double* u;                     // FP64 nodal values
     CoeffDev k;
     double mass;
-    void* VM; void* VK; void* VT;        // element-matrix scratch (FP32 or FP64)
+    void* VM; void* VK; void* VT;        // element-matrix scratch (FP32 or FP64): VM = the interleaved
+                                         // M/K base, VK = VM + one value, VT
     const int* seg_ptr;
     const int* contrib;
     const uint2* seg_head;               // per group of 32 contributions (see fem_mesh)

@@ -63,11 +63,11 @@ extern "C" int fem_assemble_all_noalloc(fem_mesh* m, const fem_coeff* k, const d
         if (!d_u) return fail(FEM_EINVAL, "u is NULL");
     }
     const size_t nsym = (size_t)m->np * (m->np + 1) / 2, nt = (size_t)m->np * m->np;
-    const size_t bM = d_vM ? sizeof(double) * (size_t)m->E * nsym : 0;
-    const size_t bK = d_vK ? sizeof(double) * (size_t)m->E * nsym : 0;
+    // M and K interleaved in one array (K at the odd positions), then T
+    const size_t bMK = (d_vM || d_vK) ? 2 * sizeof(double) * (size_t)m->E * nsym : 0;
     const size_t bT = d_vT ? sizeof(double) * (size_t)m->E * nt : 0;
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t need = up(bM) + up(bK) + up(bT);
+    const size_t need = up(bMK) + up(bT);
     if (need > (size_t)FEM_NOALLOC_SCRATCH_BYTES)
         return fail(FEM_EINVAL, "mesh too large for fem_assemble_all_noalloc: needs " + std::to_string(need) +
                                     " bytes of scratch, the fixed array holds " +
@@ -78,8 +78,8 @@ extern "C" int fem_assemble_all_noalloc(fem_mesh* m, const fem_coeff* k, const d
     int rc = noalloc_setup(dev, &base);
     if (rc) return rc;
     double* VM = d_vM ? reinterpret_cast<double*>(base) : nullptr;
-    double* VK = d_vK ? reinterpret_cast<double*>(base + up(bM)) : nullptr;
-    double* VT = d_vT ? reinterpret_cast<double*>(base + up(bM) + up(bK)) : nullptr;
+    double* VK = d_vK ? reinterpret_cast<double*>(base) + 1 : nullptr;
+    double* VT = d_vT ? reinterpret_cast<double*>(base + up(bMK)) : nullptr;
     const CoeffDev kd = coeff_to_device(k);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if ((rc = element_simt_fp64(*m, kd, d_u, VM, VK, VT, s))) return rc;

@@ -6,7 +6,8 @@
 // slot adds its contributions in a fixed order given by the mesh alone, so
 // the result is bit-reproducible run to run.
 // M and K come from the symmetric element storage (entry (i,j) and (j,i)
-// share V[e][sym(min,max)]), T from the full n_p x n_p storage.
+// share V[e][sym(min,max)]; M and K interleaved), T from the full n_p x n_p
+// storage.
 //
 // A warp sums 32 consecutive contributions at a time (one lane each) with a
 // segmented scan over the lanes; the slot boundaries come from per-group
@@ -25,9 +26,17 @@ __host__ __device__ constexpr int sym_idx(int np, int i, int j) {
 }
 
 // V entries of one element entry c = (e n_p + i) n_p + j: T from the full
-// storage (its index is c itself), M and K from the symmetric storage at
-// e n_p(n_p+1)/2 + sym[i n_p + j], with the local symmetric index from a
-// small shared-memory table.
+// storage (its index is c itself), M and K from the interleaved symmetric
+// storage (M at 2 off, K at 2 off + 1, off = e n_p(n_p+1)/2 + sym[i n_p +
+// j]), with the local symmetric index from a small shared-memory table.
+// VK is VM + 1 when both are requested: one 8- or 16-byte load reads both.
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> { using type = float2; };
+template <>
+struct Pair<double> { using type = double2; };
+
 template <int NP, typename T>
 struct Contribution {
     T m, k, t;
@@ -40,8 +49,14 @@ struct Contribution {
         if (VM || VK) {
             const uint32_t e = c / NT;
             const uint32_t off = e * NSYM + (uint32_t)sym[c - e * NT];
-            m = VM ? __ldg(VM + off) : T(0);
-            k = VK ? __ldg(VK + off) : T(0);
+            if (VM && VK) {
+                const typename Pair<T>::type mk = __ldg(reinterpret_cast<const typename Pair<T>::type*>(VM) + off);
+                m = mk.x;
+                k = mk.y;
+            } else {
+                m = VM ? __ldg(VM + 2 * off) : T(0);
+                k = VK ? __ldg(VK + 2 * off) : T(0);
+            }
         } else {
             m = k = T(0);
         }
