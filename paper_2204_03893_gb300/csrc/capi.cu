@@ -263,10 +263,30 @@ int assemble_t(fem_mesh* m, const fem_coeff* k, const void* u, int prec, void* v
     // -- measured slower on GB300: the sum is bound by its gather latency,
     // not by where V lives, and every extra launch adds a tail.)
     if ((rc = form_t<T>(m, k, ud, prec, mask, s))) return rc;
-    if ((rc = sum_t<T>(m, outd[0], outd[1], outd[2], s))) return rc;
-    for (int i = 0; i < 3; ++i)
-        if (out_staged[i])
-            FEM_CUDA_TRY(cudaMemcpyAsync(outs[i], outd[i], sizeof(T) * (size_t)nnz, cudaMemcpyDeviceToHost, s));
+    if (!nstaged) {
+        if ((rc = sum_t<T>(m, outd[0], outd[1], outd[2], s))) return rc;
+    } else {
+        // staged outputs: sum in NR slot ranges and copy each range to the
+        // host on a second stream as soon as it is summed, so the copies
+        // (bound by the CPU-GPU link) overlap the rest of the sum.  A slot's
+        // value does not depend on the range that covers it.
+        constexpr int NR = 4;
+        if (!m->copy_stream) {
+            FEM_CUDA_TRY(cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking));
+            for (auto& ev : m->copy_ev) FEM_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        }
+        for (int r = 0; r < NR; ++r) {
+            const int64_t a = nnz * r / NR, b = nnz * (r + 1) / NR;
+            if ((rc = sum_t<T>(m, outd[0], outd[1], outd[2], s, a, b))) return rc;
+            FEM_CUDA_TRY(cudaEventRecord(m->copy_ev[r], s));
+            FEM_CUDA_TRY(cudaStreamWaitEvent(m->copy_stream, m->copy_ev[r], 0));
+            for (int i = 0; i < 3; ++i)
+                if (out_staged[i] && b > a)
+                    FEM_CUDA_TRY(cudaMemcpyAsync(static_cast<T*>(outs[i]) + a, outd[i] + a, sizeof(T) * (size_t)(b - a),
+                                                 cudaMemcpyDeviceToHost, m->copy_stream));
+        }
+        FEM_CUDA_TRY(cudaStreamSynchronize(m->copy_stream));
+    }
     if (host_io) FEM_CUDA_TRY(cudaStreamSynchronize(s));
     return FEM_OK;
 }
@@ -376,6 +396,11 @@ int fem_mesh_destroy(fem_mesh* m) {
                            &m->contrib, &m->slot, &m->seg_head, &m->inc_ptr, &m->inc, &m->VMK, &m->VT, &m->u_stage,
                            &m->out_stage};
     for (auto* b : bufs) buf_free(*b, nullptr);
+    if (m->copy_stream) {
+        for (auto ev : m->copy_ev)
+            if (ev) cudaEventDestroy(ev);
+        cudaStreamDestroy(m->copy_stream);
+    }
     cudaDeviceSynchronize();
     delete m;
     return FEM_OK;

@@ -288,9 +288,12 @@ __device__ __forceinline__ void epilogue_tile(uint32_t tmem, int colM, int colK,
 // 32 x 33 staging tile per warp (stage + warp 32 x 33 floats): each store
 // instruction writes one row.  Used where the whole-block staging of
 // `epilogue` would not fit (the chunked product's 400-column T).
-// Column c of a row lands at V[row LD + c_off + c CS] (CS = 2: one half of
-// the interleaved M/K storage).
-template <int N, int LD = N, int CS = 1>
+// Column c of a row lands at V[row LD + c_off + c CS].  The interleaved
+// M/K storage (CS = 2) is written in two passes: M first as full (M, 0)
+// pairs (PAIR: 8-byte stores, whole sectors, so L2 holds them without
+// fetching the sectors from DRAM), then K into the odd positions of the
+// same, still cached, sectors.
+template <int N, int LD = N, int CS = 1, bool PAIR = false>
 __device__ __forceinline__ void epilogue_staged(uint32_t tmem, int col, float* stage_base, float* __restrict__ V,
                                                 int64_t row0, int64_t E, int warp, int lane, int c_off = 0) {
     float* stage = stage_base + warp * 32 * 33;
@@ -305,7 +308,12 @@ __device__ __forceinline__ void epilogue_staged(uint32_t tmem, int col, float* s
         for (int rr = 0; rr < 32; ++rr) {
             int64_t er = row0 + rr;
             int c = c0 + lane;
-            if (er < E && c < N) V[er * LD + c_off + c * CS] = stage[rr * 33 + lane];
+            if (er < E && c < N) {
+                if constexpr (PAIR)
+                    *reinterpret_cast<float2*>(V + er * LD + c * 2) = make_float2(stage[rr * 33 + lane], 0.f);
+                else
+                    V[er * LD + c_off + c * CS] = stage[rr * 33 + lane];
+            }
         }
         __syncwarp();
     }
@@ -856,7 +864,7 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
         // drain the pass's accumulator once its last chunk is in (the stage
         // area aliases the X chunk, which the completed MMAs no longer read)
         if (active && L::last_of_pass(s)) {
-            if (kd == 0) epilogue_staged<ETy::NSYM, 2 * ETy::NSYM, 2>(tmem, 0, stage, VMK, row0, E, warp, lane, 0);
+            if (kd == 0) epilogue_staged<ETy::NSYM, 2 * ETy::NSYM, 2, true>(tmem, 0, stage, VMK, row0, E, warp, lane);
             else if (kd == 1) epilogue_staged<ETy::NSYM, 2 * ETy::NSYM, 2>(tmem, 0, stage, VMK, row0, E, warp, lane, 1);
             else if (kd == 2) epilogue_staged<L::NTa, ETy::NT>(tmem, 0, stage, VT, row0, E, warp, lane, 0);
             else epilogue_staged<ETy::NT - L::NTa, ETy::NT>(tmem, 0, stage, VT, row0, E, warp, lane, L::NTa);

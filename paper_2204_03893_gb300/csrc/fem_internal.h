@@ -71,8 +71,12 @@ struct fem_mesh {
     // K at 2(e n_sym + s) + 1), T row-major n_p x n_p per element
     fem::DevBuf VMK, VT;
     int v_prec = -1, v_mask = 0;        // what VM/VK/VT currently hold
-    // staging for host-pointer arguments
+    // staging for host-pointer arguments; the copy stream and events that
+    // move staged CSR values to the host range by range while later ranges
+    // are still being summed (created on first use)
     fem::DevBuf u_stage, out_stage;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_ev[4] = {};
     size_t device_bytes() const;
 };
 
