@@ -114,6 +114,30 @@ __device__ __forceinline__ void store_row(unsigned char* hi, unsigned char* lo, 
     }
 }
 
+// columns [c0, c0 + NC) of one X row of Kp columns (c0 and NC multiples of 4)
+template <int Kp, int NC>
+__device__ __forceinline__ void store_row_part(unsigned char* hi, unsigned char* lo, const float (&x)[NC], int r,
+                                               int c0) {
+    static_assert(NC % 4 == 0 && Kp % 4 == 0, "column groups of 4");
+    constexpr uint32_t sbo = (Kp / 4) * 128;
+    unsigned char* ph = hi + (r >> 3) * sbo + (r & 7) * 16 + (c0 >> 2) * 128;
+    unsigned char* pl = lo + (r >> 3) * sbo + (r & 7) * 16 + (c0 >> 2) * 128;
+#pragma unroll
+    for (int c = 0; c < NC / 4; ++c) {
+        float4 h, l;
+        h.x = tc::tf32_rna(x[4 * c + 0]);
+        h.y = tc::tf32_rna(x[4 * c + 1]);
+        h.z = tc::tf32_rna(x[4 * c + 2]);
+        h.w = tc::tf32_rna(x[4 * c + 3]);
+        l.x = tc::tf32_rna(x[4 * c + 0] - h.x);
+        l.y = tc::tf32_rna(x[4 * c + 1] - h.y);
+        l.z = tc::tf32_rna(x[4 * c + 2] - h.z);
+        l.w = tc::tf32_rna(x[4 * c + 3] - h.w);
+        *reinterpret_cast<float4*>(ph + c * 128) = h;
+        *reinterpret_cast<float4*>(pl + c * 128) = l;
+    }
+}
+
 // D[dcol..] (+)= sum over K steps of (Xhi Qhi + Xhi Qlo + Xlo Qhi); with
 // `acc` the first product also accumulates onto what D holds
 template <int Kp>
@@ -751,7 +775,13 @@ __device__ __forceinline__ void form_chunk_t(int q0, const float (&du)[ETy::NP],
     }
 }
 
-// One 128-element tile of the chunked product (all 128 threads; uniform
+// Threads of a chunked-product CTA: two per element row.  Thread tid works
+// on row tid mod 128 and forms half of each chunk's quadrature points
+// (half tid / 128), so the serial formation of a chunk is split in two;
+// warps 0-3 (the TMEM lane owners of the 128 rows) drain the accumulators.
+constexpr int CT = 2 * TILE;
+
+// One 128-element tile of the chunked product (all CT threads; uniform
 // control).  Returns false if a bounded wait gave up; *pend_q / *pend_mma
 // then tell which barrier still has an operation in flight.
 template <typename ETy>
@@ -765,10 +795,11 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
     using L = ChL<ETy>;
     constexpr int NP = ETy::NP, NS = ETy::NS;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = tid & (TILE - 1), half = tid / TILE;   // element row, half of each chunk
     const bool doM = VM != nullptr, doK = VK != nullptr, doT = VT != nullptr;
     float* VMK = doM ? VM : doK ? VK - 1 : nullptr;   // interleaved M/K storage (K at odd positions)
     const bool need_u = doK | doT;
-    const int64_t e = first + tid;
+    const int64_t e = first + r;
     // element data for the whole tile: u differences (hi/lo split, as in
     // form_x) and the geometry
     float du[NP], A[NS];
@@ -811,18 +842,23 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
                 }
             }
             pend_q = true;
+            // this thread's half of the chunk: quadrature points
+            // c QC + half QC/2 .., i.e. columns half Kc/2 .. of the X chunk
             if (kd == 0) {
-                float x[L::KcM];
-                form_chunk_m<ETy, L::QCM>(c * L::QCM, b, mass, x);
-                store_row<L::KcM>(sX, sX + TILE * L::KcM * 4, x, tid);
+                constexpr int QH = L::QCM / 2, KH = L::KcM / 2;
+                float x[KH];
+                form_chunk_m<ETy, QH>(c * L::QCM + half * QH, b, mass, x);
+                store_row_part<L::KcM, KH>(sX, sX + TILE * L::KcM * 4, x, r, half * KH);
             } else if (kd == 1) {
-                float x[L::KcK];
-                form_chunk_k<ETy, L::QCK>(c * L::QCK, du, u0, b, A, k, x);
-                store_row<L::KcK>(sX, sX + TILE * L::KcK * 4, x, tid);
+                constexpr int QH = L::QCK / 2, KH = L::KcK / 2;
+                float x[KH];
+                form_chunk_k<ETy, QH>(c * L::QCK + half * QH, du, u0, b, A, k, x);
+                store_row_part<L::KcK, KH>(sX, sX + TILE * L::KcK * 4, x, r, half * KH);
             } else {   // both halves of T use the same X columns
-                float x[L::KcT];
-                form_chunk_t<ETy, L::QCT>(c * L::QCT, du, u0, b, A, k, x);
-                store_row<L::KcT>(sX, sX + TILE * L::KcT * 4, x, tid);
+                constexpr int QH = L::QCT / 2, KH = L::KcT / 2;
+                float x[KH];
+                form_chunk_t<ETy, QH>(c * L::QCT + half * QH, du, u0, b, A, k, x);
+                store_row_part<L::KcT, KH>(sX, sX + TILE * L::KcT * 4, x, r, half * KH);
             }
             tc::fence_proxy_async_smem();
             uint32_t okq = 1;
@@ -864,10 +900,16 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
         // drain the pass's accumulator once its last chunk is in (the stage
         // area aliases the X chunk, which the completed MMAs no longer read)
         if (active && L::last_of_pass(s)) {
-            if (kd == 0) epilogue_staged<ETy::NSYM, 2 * ETy::NSYM, 2, true>(tmem, 0, stage, VMK, row0, E, warp, lane);
-            else if (kd == 1) epilogue_staged<ETy::NSYM, 2 * ETy::NSYM, 2>(tmem, 0, stage, VMK, row0, E, warp, lane, 1);
-            else if (kd == 2) epilogue_staged<L::NTa, ETy::NT>(tmem, 0, stage, VT, row0, E, warp, lane, 0);
-            else epilogue_staged<ETy::NT - L::NTa, ETy::NT>(tmem, 0, stage, VT, row0, E, warp, lane, L::NTa);
+            if (warp < TILE / 32) {   // the warps that own the TMEM lanes of the tile's rows
+                if (kd == 0)
+                    epilogue_staged<ETy::NSYM, 2 * ETy::NSYM, 2, true>(tmem, 0, stage, VMK, row0, E, warp, lane);
+                else if (kd == 1)
+                    epilogue_staged<ETy::NSYM, 2 * ETy::NSYM, 2>(tmem, 0, stage, VMK, row0, E, warp, lane, 1);
+                else if (kd == 2)
+                    epilogue_staged<L::NTa, ETy::NT>(tmem, 0, stage, VT, row0, E, warp, lane, 0);
+                else
+                    epilogue_staged<ETy::NT - L::NTa, ETy::NT>(tmem, 0, stage, VT, row0, E, warp, lane, L::NTa);
+            }
             tc::fence_before_sync();
             __syncthreads();
         }
@@ -876,7 +918,7 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
 }
 
 template <typename ETy>
-__global__ void __launch_bounds__(TILE, 2) element_tc_chunked_kernel(
+__global__ void __launch_bounds__(CT, 2) element_tc_chunked_kernel(
     const int* __restrict__ conn, const float* __restrict__ geo, int64_t E, int64_t gs, const double* __restrict__ u,
     CoeffDev k, float mass, float* __restrict__ VM, float* __restrict__ VK, float* __restrict__ VT,
     const unsigned char* __restrict__ img, int* __restrict__ err) {
@@ -919,7 +961,7 @@ __global__ void __launch_bounds__(TILE, 2) element_tc_chunked_kernel(
 // Batched chunked product: a persistent walk over the 128-element tiles of
 // every P3-tetrahedron mesh of a batch (the same tile code as the
 // single-mesh kernel, so the bits are the same).
-__global__ void __launch_bounds__(TILE, 2) batch_tc_chunked_kernel(const BatchItem* __restrict__ items, int nitems,
+__global__ void __launch_bounds__(CT, 2) batch_tc_chunked_kernel(const BatchItem* __restrict__ items, int nitems,
                                                                    const BatchMesh* __restrict__ meshes,
                                                                    const unsigned char* __restrict__ img,
                                                                    int* __restrict__ err) {
@@ -1107,9 +1149,9 @@ int launch_tc_chunked(const fem_mesh& m, const CoeffDev& k, const double* u, flo
         FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, o.smem));
         FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                           (int)cudaSharedmemCarveoutMaxShared));
-        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, o.smem));
+        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, CT, o.smem));
         if (occ > cmax) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
-        o.occ = std::max(1, std::min(cmax, ctas_per_sm(fa, TILE, o.smem, dev)));
+        o.occ = std::max(1, std::min(cmax, ctas_per_sm(fa, CT, o.smem, dev)));
         void* img = nullptr;
         FEM_CUDA_TRY(cudaGetSymbolAddress(&img, g_tcbig));
         o.img = img;
@@ -1120,9 +1162,9 @@ int launch_tc_chunked(const fem_mesh& m, const CoeffDev& k, const double* u, flo
     const int64_t ntiles = (E + TILE - 1) / TILE;
     int64_t grid = (int64_t)sh.nsm * sh.occ;
     if (grid > ntiles) grid = ntiles;
-    trace_launch("element_tc_chunked_kernel", grid, TILE, sh.smem, sh.occ);
+    trace_launch("element_tc_chunked_kernel", grid, CT, sh.smem, sh.occ);
     cudaGetLastError();   // clear any stale error before the launch check
-    kern<<<(unsigned)grid, TILE, sh.smem, s>>>(m.conn.as<int>() + e0 * ETy::NP, m.geo32.as<float>() + e0, E, m.E, u, k,
+    kern<<<(unsigned)grid, CT, sh.smem, s>>>(m.conn.as<int>() + e0 * ETy::NP, m.geo32.as<float>() + e0, E, m.E, u, k,
                                                (float)m.m, VM ? VM + 2 * e0 * ETy::NSYM : nullptr,
                                                VK ? VK + 2 * e0 * ETy::NSYM : nullptr, VT ? VT + e0 * ETy::NT : nullptr,
                                                static_cast<const unsigned char*>(sh.img), sh.err);
@@ -1342,17 +1384,17 @@ int batch_tc_chunked_launch(const BatchItem* items, int nitems, const BatchMesh*
     FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
-    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, CT, smem));
     if (occ > cmax) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
-    const int per = std::max(1, std::min(cmax, ctas_per_sm(fa, TILE, smem, dev)));
+    const int per = std::max(1, std::min(cmax, ctas_per_sm(fa, CT, smem, dev)));
     const int grid = nitems < nsm * per ? nitems : nsm * per;
     unsigned char* img = nullptr;
     int* err = nullptr;
     FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&img, g_tcbig));
     FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&err, g_tc_err));
-    trace_launch("batch_tc_chunked_kernel", grid, TILE, smem, per);
+    trace_launch("batch_tc_chunked_kernel", grid, CT, smem, per);
     cudaGetLastError();   // clear any stale error before the launch check
-    kern<<<grid, TILE, smem, s>>>(items, nitems, meshes, img, err);
+    kern<<<grid, CT, smem, s>>>(items, nitems, meshes, img, err);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
