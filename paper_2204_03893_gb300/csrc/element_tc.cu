@@ -75,6 +75,19 @@ struct TcL {
     static constexpr int XEND = 2 * TILE * KTOTp * 4;
     static constexpr uint32_t SBO_X = (KTOTp / 4) * 128;
     static constexpr int SMEM = QEND + XEND;
+    // threads per element row in the single-mesh kernel, measured on GB300:
+    // two (each forming half of the quadrature points) pay off for the
+    // elements with many quadrature points (P3 triangles, P2 tetrahedra:
+    // 0.76 vs 0.88 ms on tet_p2_64); P1/P2 triangles and P1 tetrahedra run
+    // faster with one thread per row and 4 CTAs per SM (0.27 vs 0.29 ms on
+    // tri_p2_1024, 0.73 vs 1.10 ms on tet_p1_128)
+    static constexpr int TPR = ETy::NQ >= 11 ? 2 : 1;
+    // CTAs per SM the tile fits (shared memory, TMEM; at most 3), the
+    // register budget of __launch_bounds__ with two threads per row
+    static constexpr int MINB_SMEM = (228 * 1024) / (SMEM + 1024), MINB_TMEM = 512 / ALLOC;
+    static constexpr int MINB2 = MINB_SMEM < 1 ? 1 : MINB_SMEM < MINB_TMEM ? (MINB_SMEM < 3 ? MINB_SMEM : 3)
+                                                                        : (MINB_TMEM < 3 ? MINB_TMEM : 3);
+    static constexpr int MINB = TPR == 2 ? MINB2 : 1;
     // epilogue reads whole 32-column chunks: they must stay inside the allocation
     static constexpr bool FITS = NMp <= 256 && NTp <= 256 && ALLOC <= 512 && SMEM <= SMEM_MAX &&
                                  XEND >= 4 * 32 * ETy::NT * 4 && QEND <= IMG_SLOT_FLOATS * 4 &&
@@ -217,25 +230,26 @@ __device__ __forceinline__ void block_out(const float* blk, float* __restrict__ 
 
 // TMEM (this warp's 32 lanes = 32 consecutive elements, columns col..col+N)
 // -> V: every thread writes its row into the warp's block, then block_out.
-template <int N>
+template <int N, int W = 32>
 __device__ __forceinline__ void epilogue_bulk(uint32_t tmem, int col, float* blk, float* __restrict__ V, int64_t row0,
                                               int64_t E, int warp, int lane) {
     if (row0 >= E) return;   // warp-uniform
+    // W: columns per TMEM load (16 where registers are scarce)
 #pragma unroll 1
-    for (int c0 = 0; c0 < N; c0 += 32) {
-        uint32_t r[32];
-        tc::tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + col + c0, r);
+    for (int c0 = 0; c0 < N; c0 += W) {
+        uint32_t r[W];
+        tc::tmem_ld<W>(tmem + (static_cast<uint32_t>(warp * 32) << 16) + col + c0, r);
         float* dst = blk + lane * N + c0;
         if constexpr (N % 4 == 0) {
 #pragma unroll
-            for (int j = 0; j < 32; j += 4)
+            for (int j = 0; j < W; j += 4)
                 if (c0 + j < N)
                     *reinterpret_cast<float4*>(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
                                                                       __uint_as_float(r[j + 2]),
                                                                       __uint_as_float(r[j + 3]));
         } else {
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
+            for (int j = 0; j < W; ++j)
                 if (c0 + j < N) dst[j] = __uint_as_float(r[j]);
         }
     }
@@ -248,13 +262,13 @@ __device__ __forceinline__ void epilogue_bulk(uint32_t tmem, int col, float* blk
 // unrequested matrix's half is written as 0), then block_out.  The 8-byte
 // stores of a half-warp hit distinct bank pairs (row stride 2 NS floats,
 // NS odd) or at worst two.
-template <int NS>
+template <int NS, int WMAX = 32>
 __device__ __forceinline__ void epilogue_mk_bulk(uint32_t tmem, int colM, int colK, float* blk,
                                                  float* __restrict__ VMK, bool doM, bool doK, int64_t row0, int64_t E,
                                                  int warp, int lane) {
     if (row0 >= E) return;   // warp-uniform
     // columns per TMEM load: the narrowest shape that covers a small NS
-    constexpr int W = NS <= 8 ? 8 : NS <= 16 ? 16 : 32;
+    constexpr int W = NS <= 8 ? 8 : NS <= 16 || WMAX == 16 ? 16 : 32;
     const uint32_t lanes = static_cast<uint32_t>(warp * 32) << 16;
 #pragma unroll 1
     for (int c0 = 0; c0 < NS; c0 += W) {
@@ -286,7 +300,7 @@ __device__ __forceinline__ void epilogue_mk_bulk(uint32_t tmem, int colM, int co
 // otherwise the warp's one block is reused and the first copy's reads are
 // waited for.  Returns with every bulk read of this warp complete, so the
 // caller may overwrite the region after a block barrier.
-template <typename ETy, int XEND>
+template <typename ETy, int XEND, int W = 32>
 __device__ __forceinline__ void epilogue_tile(uint32_t tmem, int colM, int colK, int colT, float* stage,
                                               float* __restrict__ VMK, float* __restrict__ VT, bool doM, bool doK,
                                               bool doT, int64_t row0, int64_t E, int warp, int lane) {
@@ -302,9 +316,9 @@ __device__ __forceinline__ void epilogue_tile(uint32_t tmem, int colM, int colK,
         }
         __syncwarp();
     };
-    if (doM || doK) epilogue_mk_bulk<ETy::NSYM>(tmem, colM, colK, bMK, VMK, doM, doK, row0, E, warp, lane);
+    if (doM || doK) epilogue_mk_bulk<ETy::NSYM, W>(tmem, colM, colK, bMK, VMK, doM, doK, row0, E, warp, lane);
     if (!DISJOINT && (doM || doK)) drain();
-    if (doT) epilogue_bulk<NT>(tmem, colT, bT, VT, row0, E, warp, lane);
+    if (doT) epilogue_bulk<NT, W>(tmem, colT, bT, VT, row0, E, warp, lane);
     drain();
 }
 
@@ -403,8 +417,82 @@ __device__ __forceinline__ void form_x(const float2 (&pu)[ETy::NP], const float 
     }
 }
 
+// One half of an element's X row (Section 4 as in form_x), written straight
+// into the K-major TF32 hi/lo operand: the columns of quadrature points
+// [QLO, QHI) of every matrix, H = 0 for the first ceil(NQ/2) points, H = 1
+// for the rest (which also zeroes the padding columns).  `valid` false (a
+// row past E) writes zeros.  Scalar stores: a half's columns do not form
+// whole 4-column groups.
+template <typename ETy, int KTOTp, int H>
+__device__ __forceinline__ void form_x_half(const float2 (&pu)[ETy::NP], const float (&pgeo)[1 + ETy::NS],
+                                            bool valid, bool need_u, const CoeffDev& k, float mass,
+                                            unsigned char* xh, unsigned char* xl, int r) {
+    constexpr int OFF_K = ETy::KM, OFF_T = ETy::KM + ETy::KK, KTOT = OFF_T + ETy::KT;
+    constexpr int D = ETy::D, NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS;
+    constexpr int QLO = H == 0 ? 0 : (NQ + 1) / 2, QHI = H == 0 ? (NQ + 1) / 2 : NQ;
+    constexpr int TO = type_tab_off(ETy::TYPE);
+    constexpr int PHI = TO, GR = TO + NQ * NP, WQ = TO + NQ * NP * (1 + D);
+    constexpr uint32_t sbo = (KTOTp / 4) * 128;
+    const uint32_t rowoff = (r >> 3) * sbo + (r & 7) * 16;
+    auto put = [&](int c, float v) {
+        const uint32_t o = rowoff + (c >> 2) * 128 + (c & 3) * 4;
+        const float h = tc::tf32_rna(v);
+        *reinterpret_cast<float*>(xh + o) = h;
+        *reinterpret_cast<float*>(xl + o) = tc::tf32_rna(v - h);
+    };
+    float du[NP];
+    float u0 = 0.f;
+    if (valid && need_u) {
+        u0 = pu[0].x + pu[0].y;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) du[i] = (pu[i].x - pu[0].x) + (pu[i].y - pu[0].y);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) du[i] = 0.f;
+    }
+    const float b = valid ? pgeo[0] : 0.f;
+    float A[NS];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) A[t] = valid ? pgeo[1 + t] : 0.f;
+#pragma unroll
+    for (int q = QLO; q < QHI; ++q) {
+        float uq = 0.f, g[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) g[a] = 0.f;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            uq = fmaf(c_tcref[PHI + q * NP + i], du[i], uq);
+#pragma unroll
+            for (int a = 0; a < D; ++a) g[a] = fmaf(c_tcref[GR + (q * NP + i) * D + a], du[i], g[a]);
+        }
+        uq += u0;
+        float dk;
+        const float kq = k_eval<float>(k, uq, dk);
+        const float lam = c_tcref[WQ + q] * b;   // 0 for an invalid row, so every column is 0
+        put(q, mass * lam);
+        const float lk = lam * kq;
+#pragma unroll
+        for (int t = 0; t < NS; ++t) put(OFF_K + q * NS + t, lk * A[t]);
+        const float ld = lam * dk;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            float sacc = 0.f;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const int lo = a < c ? a : c, hi = a < c ? c : a;
+                sacc = fmaf(A[lo * D - (lo * (lo - 1)) / 2 + (hi - lo)], g[c], sacc);
+            }
+            put(OFF_T + q * D + a, ld * sacc);
+        }
+    }
+    if constexpr (H == 1) {
+#pragma unroll
+        for (int c = KTOT; c < KTOTp; ++c) put(c, 0.f);
+    }
+}
+
 template <typename ETy>
-__global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict__ conn, const float* __restrict__ geo,
+__global__ void __launch_bounds__(TcL<ETy>::TPR * TILE, TcL<ETy>::MINB) element_tc_kernel(const int* __restrict__ conn, const float* __restrict__ geo,
                                                           int64_t E, int64_t gs, const double* __restrict__ u, CoeffDev k,
                                                           float mass, float* __restrict__ VM, float* __restrict__ VK,
                                                           float* __restrict__ VT, const float* __restrict__ img,
@@ -415,14 +503,19 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
 
+    // TPR threads per element row.  With two: warps 0-3 form the first half
+    // of each row's quadrature points and drain TMEM (they own its lanes),
+    // warps 4-7 form the second half.
+    constexpr int NTHR = L::TPR * TILE;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = tid & (TILE - 1), half = tid / TILE;
     unsigned char* sQ = smem;
     unsigned char* sX = smem + L::QEND;
 
     {   // resident Q image
         const int4* src = reinterpret_cast<const int4*>(img);
         int4* dst = reinterpret_cast<int4*>(sQ);
-        for (int i = tid; i < L::QEND / 16; i += TILE) dst[i] = src[i];
+        for (int i = tid; i < L::QEND / 16; i += NTHR) dst[i] = src[i];
     }
     const uint32_t mb = tc::smem_u32(&mbar);
     if (tid == 0) {
@@ -454,7 +547,7 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
     float pgeo[1 + NS];
     bool pvalid = false;
     auto fetch_meta = [&](int64_t t) {
-        const int64_t e = t * TILE + tid;
+        const int64_t e = t * TILE + r;
         pvalid = e < E;
         if (pvalid) {
             const int* ce = conn + e * NP;
@@ -476,19 +569,28 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
     }
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         // the whole packed row is written (unrequested parts too: every
-        // matrix's slices overlap its neighbours' columns)
-        float x[L::KTOTp];
-#pragma unroll
-        for (int i = 0; i < L::KTOTp; ++i) x[i] = 0.f;
-        if (pvalid) {
+        // matrix's slices overlap its neighbours' columns); with two threads
+        // per row, half by each (warp-uniform branch)
+        const int64_t next = tile + gridDim.x;
+        {
             float2 su[NP];
 #pragma unroll
-            for (int i = 0; i < NP; ++i) su[i] = need_u ? split_f64(pu[i]) : make_float2(0.f, 0.f);
-            form_x<ETy, L::KTOTp>(su, pgeo, need_u, k, mass, x);
+            for (int i = 0; i < NP; ++i) su[i] = pvalid && need_u ? split_f64(pu[i]) : make_float2(0.f, 0.f);
+            if constexpr (L::TPR == 1) {
+                float x[L::KTOTp];
+#pragma unroll
+                for (int i = 0; i < L::KTOTp; ++i) x[i] = 0.f;
+                if (pvalid) form_x<ETy, L::KTOTp>(su, pgeo, need_u, k, mass, x);
+                if (next < ntiles) fetch_meta(next);
+                store_row<L::KTOTp>(sX + L::XH, sX + L::XL, x, r);
+            } else {
+                if (half == 0)
+                    form_x_half<ETy, L::KTOTp, 0>(su, pgeo, pvalid, need_u, k, mass, sX + L::XH, sX + L::XL, r);
+                else
+                    form_x_half<ETy, L::KTOTp, 1>(su, pgeo, pvalid, need_u, k, mass, sX + L::XH, sX + L::XL, r);
+                if (next < ntiles) fetch_meta(next);
+            }
         }
-        const int64_t next = tile + gridDim.x;
-        if (next < ntiles) fetch_meta(next);
-        store_row<L::KTOTp>(sX + L::XH, sX + L::XL, x, tid);
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         __syncthreads();
@@ -508,9 +610,12 @@ __global__ void __launch_bounds__(TILE) element_tc_kernel(const int* __restrict_
             break;
         }
         tc::fence_after_sync();
-        const int64_t row0 = tile * TILE + warp * 32;
-        epilogue_tile<ETy, L::XEND>(tmem, L::COLM, L::COLK, L::COLT, stage, VMK, VT, doM, doK, doT, row0, E, warp,
-                                    lane);
+        if (half == 0) {
+            const int64_t row0 = tile * TILE + warp * 32;
+            // narrower TMEM loads where two threads per row leave fewer registers
+            epilogue_tile<ETy, L::XEND, L::TPR == 2 ? 16 : 32>(tmem, L::COLM, L::COLK, L::COLT, stage, VMK, VT, doM,
+                                                               doK, doT, row0, E, warp, lane);
+        }
         tc::fence_before_sync();
         __syncthreads();
     }
@@ -535,19 +640,22 @@ __device__ __forceinline__ bool batch_tc_tile(const BatchMesh& bm, int64_t first
     using L = TcL<ETy>;
     constexpr int NP = ETy::NP, NS = ETy::NS;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = tid & (TILE - 1), half = tid / TILE;   // two threads per element row, as in element_tc_kernel
     unsigned char* sX = smem + L::QEND;
     const uint32_t sQu = tc::smem_u32(smem), sXu = tc::smem_u32(sX);
     const bool doM = bm.vM != nullptr, doK = bm.vK != nullptr, doT = bm.vT != nullptr;
     if (!(doM | doK | doT)) return true;   // mesh skipped in this launch (uniform over the CTA)
     const bool need_u = doK | doT;
     const int64_t E = bm.E;
-    float x[L::KTOTp];
+    const int64_t e = first + r;
+    const bool valid = e < E;
+    float2 pu[NP];
+    float pgeo[1 + NS];
 #pragma unroll
-    for (int i = 0; i < L::KTOTp; ++i) x[i] = 0.f;
-    const int64_t e = first + tid;
-    if (e < E) {
-        float2 pu[NP];
-        float pgeo[1 + NS];
+    for (int i = 0; i < NP; ++i) pu[i] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t <= NS; ++t) pgeo[t] = 0.f;
+    if (valid) {
         const int* ce = bm.conn + e * NP;
         if (need_u) {
 #pragma unroll
@@ -555,9 +663,11 @@ __device__ __forceinline__ bool batch_tc_tile(const BatchMesh& bm, int64_t first
         }
 #pragma unroll
         for (int t = 0; t <= NS; ++t) pgeo[t] = __ldg(bm.geo32 + t * E + e);
-        form_x<ETy, L::KTOTp>(pu, pgeo, need_u, bm.k, (float)bm.mass, x);
     }
-    store_row<L::KTOTp>(sX + L::XH, sX + L::XL, x, tid);
+    if (half == 0)
+        form_x_half<ETy, L::KTOTp, 0>(pu, pgeo, valid, need_u, bm.k, (float)bm.mass, sX + L::XH, sX + L::XL, r);
+    else
+        form_x_half<ETy, L::KTOTp, 1>(pu, pgeo, valid, need_u, bm.k, (float)bm.mass, sX + L::XH, sX + L::XL, r);
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -573,9 +683,11 @@ __device__ __forceinline__ bool batch_tc_tile(const BatchMesh& bm, int64_t first
     tc::fence_after_sync();
     // the epilogue stages through the X region (the MMAs are complete)
     float* stage = reinterpret_cast<float*>(sX);
-    const int64_t row0 = first + warp * 32;
-    epilogue_tile<ETy, L::XEND>(tmem, L::COLM, L::COLK, L::COLT, stage, static_cast<float*>(bm.VM),
-                                static_cast<float*>(bm.VT), doM, doK, doT, row0, E, warp, lane);
+    if (half == 0) {
+        const int64_t row0 = first + warp * 32;
+        epilogue_tile<ETy, L::XEND, 16>(tmem, L::COLM, L::COLK, L::COLT, stage, static_cast<float*>(bm.VM),
+                                        static_cast<float*>(bm.VT), doM, doK, doT, row0, E, warp, lane);
+    }
     tc::fence_before_sync();
     __syncthreads();
     return true;
@@ -586,10 +698,10 @@ __host__ __device__ constexpr int tc_qend(int t) {
          : t == 3 ? TcL<ET<3, 1>>::QEND : t == 4 ? TcL<ET<3, 2>>::QEND : 0;
 }
 
-// Persistent batched kernel: one 128-thread CTA per SM walks the work list
+// Persistent batched kernel: 256-thread CTAs (two threads per row) walk the work list
 // (tiles of all meshes, grouped by element type) and reloads the resident Q
 // image whenever the type changes.
-__global__ void __launch_bounds__(TILE) batch_tc_kernel(const BatchItem* __restrict__ items, int nitems,
+__global__ void __launch_bounds__(2 * TILE, 1) batch_tc_kernel(const BatchItem* __restrict__ items, int nitems,
                                                         const BatchMesh* __restrict__ meshes,
                                                         const float* __restrict__ img_all, uint32_t talloc,
                                                         int* __restrict__ err) {
@@ -619,7 +731,7 @@ __global__ void __launch_bounds__(TILE) batch_tc_kernel(const BatchItem* __restr
             const int4* src = reinterpret_cast<const int4*>(img_all + (size_t)w.type * IMG_SLOT_FLOATS);
             int4* dst = reinterpret_cast<int4*>(smem);
             const int n16 = tc_qend(w.type) / 16;
-            for (int i = tid; i < n16; i += TILE) dst[i] = src[i];
+            for (int i = tid; i < n16; i += 2 * TILE) dst[i] = src[i];
             __syncthreads();
             cur = w.type;
         }
@@ -1206,7 +1318,7 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, 
             // MMA and epilogue phases on one SM
             FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                               (int)cudaSharedmemCarveoutMaxShared));
-            FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+            FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, L::TPR * TILE, smem));
             const int occ_max = 512 / ALLOC0;   // co-resident CTAs must fit their TMEM columns
             if (occ > occ_max) {
                 // ask for enough shared memory that at most occ_max CTAs fit on an SM
@@ -1215,7 +1327,7 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, 
                 smem = per_sm / (occ_max + 1) + 1;
                 if (smem > dyn_max) smem = dyn_max;
                 FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-                FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+                FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, L::TPR * TILE, smem));
                 if (occ > occ_max) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
             }
             if (occ < 1) return fail(FEM_ECUDA, "tensor-core kernel does not fit on an SM");
@@ -1223,7 +1335,7 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, 
             // preference; the register / shared-memory budget (bounded by
             // TMEM) decides, and a persistent grid larger than what is
             // co-resident stays correct
-            o.occ = std::max(occ, std::min(occ_max, ctas_per_sm(fa, TILE, smem, dev)));
+            o.occ = std::max(occ, std::min(occ_max, ctas_per_sm(fa, L::TPR * TILE, smem, dev)));
             o.smem = smem;
             void* img = nullptr;
             FEM_CUDA_TRY(cudaGetSymbolAddress(&img, g_tcimg));
@@ -1235,9 +1347,9 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, 
         const int64_t ntiles = (E + TILE - 1) / TILE;
         int64_t grid = (int64_t)sh.nsm * sh.occ;
         if (grid > ntiles) grid = ntiles;
-        trace_launch("element_tc_kernel", grid, TILE, sh.smem, sh.occ);
+        trace_launch("element_tc_kernel", grid, L::TPR * TILE, sh.smem, sh.occ);
         cudaGetLastError();   // clear any stale error before the launch check
-        kern<<<(unsigned)grid, TILE, sh.smem, s>>>(m.conn.as<int>() + e0 * ETy::NP, m.geo32.as<float>() + e0, E, m.E, u,
+        kern<<<(unsigned)grid, L::TPR * TILE, sh.smem, s>>>(m.conn.as<int>() + e0 * ETy::NP, m.geo32.as<float>() + e0, E, m.E, u,
                                                    k, (float)m.m, VM ? VM + 2 * e0 * ETy::NSYM : nullptr,
                                                    VK ? VK + 2 * e0 * ETy::NSYM : nullptr,
                                                    VT ? VT + e0 * ETy::NT : nullptr, static_cast<const float*>(sh.img),
@@ -1338,7 +1450,7 @@ int batch_tc_launch(const BatchItem* items, int nitems, const BatchMesh* meshes,
     FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
-    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 2 * TILE, smem));
     if (occ < 1) return fail(FEM_ECUDA, "batched tensor-core kernel does not fit on an SM");
     // co-resident CTAs must fit their TMEM columns: ask for enough shared
     // memory that at most 512 / talloc CTAs fit on an SM
@@ -1348,19 +1460,19 @@ int batch_tc_launch(const BatchItem* items, int nitems, const BatchMesh* meshes,
         FEM_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
         smem = std::min(per_sm / (occ_max + 1) + 1, optin - (int)fa.sharedSizeBytes);
         FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 2 * TILE, smem));
         if (occ > occ_max) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
     }
-    occ = std::max(occ, std::min(occ_max, ctas_per_sm(fa, TILE, smem, dev)));
+    occ = std::max(occ, std::min(occ_max, ctas_per_sm(fa, 2 * TILE, smem, dev)));
     grid *= occ;
     float* img = nullptr;
     int* err = nullptr;
     FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&img, g_tcimg));
     FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&err, g_tc_err));
     if (grid > nitems) grid = nitems;
-    trace_launch("batch_tc_kernel", grid, TILE, smem, occ);
+    trace_launch("batch_tc_kernel", grid, 2 * TILE, smem, occ);
     cudaGetLastError();   // clear any stale error before the launch check
-    kern<<<grid, TILE, smem, s>>>(items, nitems, meshes, img, (uint32_t)talloc, err);
+    kern<<<grid, 2 * TILE, smem, s>>>(items, nitems, meshes, img, (uint32_t)talloc, err);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
