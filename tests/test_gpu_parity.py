@@ -325,6 +325,41 @@ def test_errors_and_edge_cases():
     empty.assemble(torch.zeros(m.n_nodes, device="cuda", dtype=torch.float64), "poly", (1.0,), "fp64")
 
 
+def _single_simplex(d, p, n_elems):
+    """n_elems copies of one skewed simplex sharing no nodes (one element:
+    n_p^2 contributions, fewer than one 64-contribution group for P1/P2; an
+    odd count for P1 triangles)."""
+    K = mg.local_nodes(d, p).astype(np.float64) / p          # barycentric
+    verts = np.array([[0.1, 0.2], [1.3, 0.1], [0.4, 0.9]]) if d == 2 else \
+        np.array([[0.1, 0.2, 0.0], [1.2, 0.1, 0.3], [0.3, 1.1, 0.2], [0.2, 0.4, 1.3]])
+    one = K @ verts                                           # (n_p, d)
+    n_p = one.shape[0]
+    coords = np.concatenate([one + 2.0 * e for e in range(n_elems)])
+    conn = np.arange(n_elems * n_p, dtype=np.int32).reshape(n_elems, n_p)
+    return mg.Mesh(d=d, p=p, coords=coords, conn=conn, name=f"single_{d}{p}")
+
+
+@pytest.mark.parametrize("d,p,n", [(2, 1, 1), (2, 1, 3), (2, 2, 1), (2, 3, 1), (3, 1, 1), (3, 2, 2), (3, 3, 1)])
+def test_tiny_meshes(d, p, n):
+    """Meshes far below one tile and one contribution group, in every
+    precision, against the oracle."""
+    m = _single_simplex(d, p, n)
+    u = mg.uniform_field(m.n_nodes, 11 + d * 3 + p)
+    c = mg.Coeff("poly", (1.0, 0.5, 0.25, 0.0, 0.0))
+    r = orc.Oracle.of(m).assemble(u, c)
+    fm = FemMesh.of(m)
+    for prec in ("fp64", "tf32x3", "fp32"):
+        g = fm.assemble(torch.tensor(u, device="cuda"), c.kind, c.params, prec)
+        torch.cuda.synchronize()
+        for k in ("M", "K", "T"):
+            gk = g[k].double().cpu().numpy()
+            if prec == "fp64":
+                assert (np.abs(gk - r[k]) <= FP64_TOL * r["abs" + k] + 1e-300).all(), (prec, k)
+            else:
+                assert frob(gk, r[k]) <= (TF32_TOL if prec == "tf32x3" else FP32_TOL), (prec, k, frob(gk, r[k]))
+    F.fem_device_status()
+
+
 def test_sliver_elements_use_fp64_geometry():
     m = mg.sliver_tri(16, 0.05, seed=3)
     fm = FemMesh.of(m)
