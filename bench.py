@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "fp32", "fp64"])
+    ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "fp32", "fp64", "bf16x3", "bf16x6"])
     ap.add_argument("--scale", type=int, default=None, help="override grid size N (not a bench line)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["tri_p1_64", "tri_p2_1024", "tet_p1_128", "tet_p2_64", "tet_p3_32"],
@@ -221,6 +221,13 @@ def _pct(xs, q):
         return None
     i = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
     return xs[i]
+
+
+PRODUCT_DESC = {
+    "tf32x3": "tcgen05 kind::tf32 x3 (Xhi Qhi + Xhi Qlo + Xlo Qhi), FP32 accumulate in TMEM",
+    "bf16x3": "tcgen05 kind::f16 BF16 x3 (x0 q0 + x0 q1 + x1 q0), FP32 accumulate in TMEM",
+    "bf16x6": "tcgen05 kind::f16 BF16 x6 (part products of total order < 3), FP32 accumulate in TMEM",
+}
 
 
 def _per_mesh_prec(F, mesh):
@@ -599,10 +606,12 @@ def run_ours(args, rank, world, local_rank):
     # 4-byte index and V entries; the CSR values written
     bytes_sum = (E * n_p * n_p + 31) // 32 * 8 + E * n_p * n_p * 4 + E * (2 * nsym + nt) * esz + 3 * nnz * esz
     mf, ms = statistics.mean(form_ms), statistics.mean(sum_ms)
+    on_tc = args.prec in ("tf32x3", "bf16x3", "bf16x6")
+    form_kernel = ("element_bf_kernel" if args.prec.startswith("bf16") else
+                   "element_tc_chunked_kernel" if (wl.mesh.d, wl.mesh.p) == (3, 3) else
+                   "element_tc_kernel") if on_tc else "element_simt_kernel"
     kernels = {
-        "element_form": {"kernel": ("element_tc_chunked_kernel" if (wl.mesh.d, wl.mesh.p) == (3, 3) else
-                                    "element_tc_kernel") if args.prec == "tf32x3" else "element_simt_kernel",
-                         "src": "element_tc.cu" if args.prec == "tf32x3" else "element_simt.cu",
+        "element_form": {"kernel": form_kernel, "src": "element_tc.cu" if on_tc else "element_simt.cu",
                          "ms": mf, "bytes": bytes_form},
         "csr_sum": {"kernel": "segsum_kernel", "src": "scatter.cu", "ms": ms, "bytes": bytes_sum},
     }
@@ -638,8 +647,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32" if args.prec != "fp64" else "f64", "data": "synthetic",
         "config": {"workload": args.workload if args.scale is None else f"{args.workload}@N={args.scale}",
                    "desc": WORKLOAD_DESC if args.workload == WORKLOAD else wl.name, "precision": args.prec,
-                   "element_product": "tcgen05 kind::tf32 x3 (Xhi Qhi + Xhi Qlo + Xlo Qhi), FP32 accumulate in TMEM"
-                   if args.prec == "tf32x3" else args.prec,
+                   "element_product": PRODUCT_DESC.get(args.prec, args.prec),
                    "elements": E, "nnz": nnz, "l2": "inputs larger than L2 (per-step traffic > 2 GB; no explicit flush)",
                    "parallelism": f"{world} independent meshes, one per GPU" if world > 1 else "single GPU"},
         "roofline": roofline, "phases": phases,

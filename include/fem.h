@@ -59,7 +59,13 @@ enum {
     FEM_TF32X3 = 1, /* FP32 coefficients; V = X Q on tcgen05 tensor cores as three TF32
                        products (Xhi Qhi + Xhi Qlo + Xlo Qhi), FP32 accumulate in TMEM;
                        FP32 CSR sums */
-    FEM_FP32 = 2    /* FP32 everywhere on the SIMT pipes (no tensor cores); reference point */
+    FEM_FP32 = 2,   /* FP32 everywhere on the SIMT pipes (no tensor cores); reference point */
+    FEM_BF16X3 = 3, /* as FEM_TF32X3 with X and Q split into two BF16 parts and three
+                       kind::f16 products (x0 q0 + x0 q1 + x1 q0): ~16 significant bits */
+    FEM_BF16X6 = 4  /* three BF16 parts and the six products of total part order < 3
+                       (x0 q0 + x0 q1 + x1 q0 + x0 q2 + x1 q1 + x2 q0): ~24 bits.  The BF16
+                       modes run the single-mesh tile kernel; P3 tetrahedra (whose tile does
+                       not fit) and batches return FEM_EINVAL */
 };
 
 /* -------------------------------------------------------- memory locations */

@@ -22,13 +22,14 @@ __all__ = [
     "fem_serve_create", "fem_serve_submit", "fem_serve_poll", "fem_serve_release", "fem_serve_evict",
     "fem_serve_stats", "fem_serve_destroy", "FEM_REQ_ASSEMBLE", "FEM_REQ_REASSEMBLE", "fem_form_elements", "fem_sum_elements", "fem_chunk_plan", "fem_form_elements_range",
     "fem_sum_elements_range", "coeff", "FEM_MAT_M", "FEM_MAT_K", "FEM_MAT_T", "FEM_OK", "FEM_EINVAL", "FEM_ENOMEM", "FEM_EDEGENERATE", "FEM_ECUDA",
-    "FEM_EBUSY", "FEM_EAGAIN", "FEM_ETIMEOUT", "FEM_ESTATE", "FEM_FP64", "FEM_TF32X3", "FEM_FP32",
+    "FEM_EBUSY", "FEM_EAGAIN", "FEM_ETIMEOUT", "FEM_ESTATE", "FEM_FP64", "FEM_TF32X3", "FEM_FP32", "FEM_BF16X3",
+    "FEM_BF16X6",
     "FEM_MEM_HOST", "FEM_MEM_DEVICE", "FEM_K_POLY", "FEM_K_SIN", "FEM_K_PWLIN",
 ]
 
 FEM_OK, FEM_EINVAL, FEM_ENOMEM, FEM_EDEGENERATE, FEM_ECUDA = 0, -1, -2, -3, -4
 FEM_EBUSY, FEM_EAGAIN, FEM_ETIMEOUT, FEM_ESTATE = -5, -6, -7, -8
-FEM_FP64, FEM_TF32X3, FEM_FP32 = 0, 1, 2
+FEM_FP64, FEM_TF32X3, FEM_FP32, FEM_BF16X3, FEM_BF16X6 = 0, 1, 2, 3, 4
 FEM_MEM_HOST, FEM_MEM_DEVICE = 0, 1
 FEM_K_POLY, FEM_K_SIN, FEM_K_PWLIN = 0, 1, 2
 FEM_MAT_M, FEM_MAT_K, FEM_MAT_T = 1, 2, 4

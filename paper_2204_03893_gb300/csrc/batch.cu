@@ -201,7 +201,8 @@ int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts,
     if (!meshes || n <= 0 || !out) return fail(FEM_EINVAL, "need at least one mesh");
     *out = nullptr;
     const int prec = opts ? opts->prec : FEM_TF32X3;
-    if (prec != FEM_FP64 && prec != FEM_TF32X3 && prec != FEM_FP32) return fail(FEM_EINVAL, "unknown precision");
+    if (prec != FEM_FP64 && prec != FEM_TF32X3 && prec != FEM_FP32)
+        return fail(FEM_EINVAL, "batched reassembly runs FEM_TF32X3, FEM_FP32 or FEM_FP64");
     for (int i = 0; i < n; ++i) {
         if (!meshes[i]) return fail(FEM_EINVAL, "NULL mesh in batch");
         if (!meshes[i]->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run on every mesh");

@@ -88,6 +88,7 @@ int tc_error_flag(int clear);
 namespace {
 
 int type_of(int d, int p) { return (d - 2) * 3 + (p - 1); }
+bool valid_prec(int prec) { return prec >= FEM_FP64 && prec <= FEM_BF16X6; }
 int nlocal(int d, int p) { return d == 2 ? (p + 1) * (p + 2) / 2 : (p + 1) * (p + 2) * (p + 3) / 6; }
 
 bool is_device_ptr(const void* p) {
@@ -160,8 +161,10 @@ int form_t(fem_mesh* m, const fem_coeff* k, const double* ud, int prec, int mask
         rc = element_simt_fp64(*m, kd, ud, VM, VK, VT, s, e0, e1);
     } else {
         const double* us = (mask & 6) ? ud : nullptr;
-        rc = prec == FEM_TF32X3 ? element_tc_tf32x3(*m, kd, us, VM, VK, VT, s, e0, e1)
-                                : element_simt_fp32(*m, kd, us, VM, VK, VT, s, e0, e1);
+        rc = prec == FEM_TF32X3   ? element_tc_tf32x3(*m, kd, us, VM, VK, VT, s, e0, e1)
+             : prec == FEM_BF16X3 ? element_tc_bf16(*m, kd, us, VM, VK, VT, 2, s, e0, e1)
+             : prec == FEM_BF16X6 ? element_tc_bf16(*m, kd, us, VM, VK, VT, 3, s, e0, e1)
+                                  : element_simt_fp32(*m, kd, us, VM, VK, VT, s, e0, e1);
     }
     if (rc) return rc;
     m->v_prec = prec;
@@ -460,7 +463,7 @@ int fem_assemble_all(fem_mesh* m, const fem_coeff* k, const void* u, int prec, v
                      void* stream) {
     if (!m) return fail(FEM_EINVAL, "NULL mesh");
     if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
-    if (prec != FEM_FP64 && prec != FEM_TF32X3 && prec != FEM_FP32) return fail(FEM_EINVAL, "unknown precision");
+    if (!valid_prec(prec)) return fail(FEM_EINVAL, "unknown precision");
     if (!vM && !vK && !vT) return FEM_OK;
     if ((vK || vT)) {
         int rc = check_coeff(k);
@@ -473,7 +476,7 @@ int fem_assemble_all(fem_mesh* m, const fem_coeff* k, const void* u, int prec, v
 
 int fem_form_elements(fem_mesh* m, const fem_coeff* k, const void* d_u, int prec, int which, void* stream) {
     if (!m) return fail(FEM_EINVAL, "NULL mesh");
-    if (prec != FEM_FP64 && prec != FEM_TF32X3 && prec != FEM_FP32) return fail(FEM_EINVAL, "unknown precision");
+    if (!valid_prec(prec)) return fail(FEM_EINVAL, "unknown precision");
     if (which <= 0 || which > 7) return fail(FEM_EINVAL, "which must be a nonzero mask of FEM_MAT_M|K|T");
     if (which & 6) {
         int rc = check_coeff(k);
@@ -502,7 +505,7 @@ int fem_chunk_plan(fem_mesh* m, int prec, size_t target_bytes, int max_chunks, i
                    int64_t* s_bounds, void* stream) {
     if (!m || !n_chunks || !e_bounds || !s_bounds) return fail(FEM_EINVAL, "NULL argument");
     if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
-    if (prec != FEM_FP64 && prec != FEM_TF32X3 && prec != FEM_FP32) return fail(FEM_EINVAL, "unknown precision");
+    if (!valid_prec(prec)) return fail(FEM_EINVAL, "unknown precision");
     if (max_chunks < 1) return fail(FEM_EINVAL, "max_chunks must be >= 1");
     std::vector<int64_t> eb, sb;
     int rc = plan_chunks(m, prec, target_bytes ? target_bytes : CHUNK_TARGET_BYTES, max_chunks,
@@ -519,7 +522,7 @@ int fem_chunk_plan(fem_mesh* m, int prec, size_t target_bytes, int max_chunks, i
 int fem_form_elements_range(fem_mesh* m, const fem_coeff* k, const void* d_u, int prec, int which, int64_t e_begin,
                             int64_t e_end, void* stream) {
     if (!m) return fail(FEM_EINVAL, "NULL mesh");
-    if (prec != FEM_FP64 && prec != FEM_TF32X3 && prec != FEM_FP32) return fail(FEM_EINVAL, "unknown precision");
+    if (!valid_prec(prec)) return fail(FEM_EINVAL, "unknown precision");
     if (which <= 0 || which > 7) return fail(FEM_EINVAL, "which must be a nonzero mask of FEM_MAT_M|K|T");
     if (e_begin < 0 || e_begin > e_end || e_end > m->E || (e_begin % 128 != 0 && e_begin != e_end))
         return fail(FEM_EINVAL, "element range must satisfy 0 <= begin <= end <= n_elems, begin % 128 == 0");

@@ -24,6 +24,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "fem_internal.h"
 #include "refelem.h"
 #include "tc_ptx.cuh"
@@ -1120,6 +1122,224 @@ __global__ void __launch_bounds__(CT, 2) batch_tc_chunked_kernel(const BatchItem
     if (warp == 0) tc::tmem_dealloc(tmem, L::ALLOC);
 }
 
+// ------------------------------------------------------ BF16 x3 / x6 tiles
+// The split-precision product in BF16 (Section 4's V = X Q, as the TF32 tile
+// above): X and Q are split into NPART BF16 parts (x = x0 + x1 (+ x2), each
+// part the round-to-nearest BF16 of what the earlier parts leave), and
+// kind::f16 MMAs accumulate the products of total part order below NPART in
+// FP32 in TMEM: NPART = 2 (BF16x3) x0 q0 + x0 q1 + x1 q0, NPART = 3
+// (BF16x6) adds x0 q2 + x1 q1 + x2 q0.  Same packed operand [X_M | X_K |
+// X_T] in K steps of 16 (one MMA), same TMEM columns and epilogue; the core
+// matrices hold 8 BF16 per 16-byte row, the byte geometry of the TF32 tile.
+constexpr int BF_IMG_SLOT = 72 * 1024;   // bytes of Q parts per element type and scheme
+
+template <typename ETy, int NPART>
+struct TbL {
+    static constexpr int KM = ETy::KM, KK = ETy::KK, KT = ETy::KT;
+    static constexpr int KTOT = KM + KK + KT, KTOTp = ru(KTOT, 16);
+    static constexpr int OFF_M = 0, OFF_K = KM, OFF_T = KM + KK;
+    static constexpr int SM0 = 0, NSM = ru(KM, 16) / 16;
+    static constexpr int SK0 = KM / 16, NSK = ru(KM + KK, 16) / 16 - KM / 16;
+    static constexpr int ST0 = (KM + KK) / 16, NST = KTOTp / 16 - (KM + KK) / 16;
+    static constexpr int NMp = ru(ETy::NSYM, 16), NTp = ru(ETy::NT, 16);
+    static constexpr int COLM = 0, COLK = NMp, COLT = 2 * NMp, COLS = 2 * NMp + NTp;
+    static constexpr int ALLOC = pow2_at_least(COLS);
+    // Q parts: per matrix NPART images of N x (slices x 16) BF16, K-major
+    static constexpr int QM_B = NMp * NSM * 32, QK_B = NMp * NSK * 32, QT_B = NTp * NST * 32;
+    static constexpr int QM0 = 0, QK0 = NPART * QM_B, QT0 = QK0 + NPART * QK_B, QEND = QT0 + NPART * QT_B;
+    static constexpr int XPART = TILE * KTOTp * 2;   // one BF16 part of the X tile
+    static constexpr int XEND = NPART * XPART;
+    static constexpr int NMK = 2 * ETy::NSYM, NMAXE = NMK > ETy::NT ? NMK : ETy::NT;
+    static constexpr int XREG = XEND > TILE * NMAXE * 4 ? XEND : TILE * NMAXE * 4;   // X tile, then epilogue blocks
+    static constexpr uint32_t SBO_X = (KTOTp / 8) * 128;
+    static constexpr int SMEM = QEND + XREG;
+    static constexpr bool FITS = NMp <= 256 && NTp <= 256 && ALLOC <= 512 && SMEM <= SMEM_MAX &&
+                                 QEND <= BF_IMG_SLOT && COLM + ru(ETy::NSYM, 32) <= ALLOC &&
+                                 COLK + ru(ETy::NSYM, 32) <= ALLOC && COLT + ru(ETy::NT, 32) <= ALLOC;
+};
+
+__device__ __align__(128) unsigned char g_tbimg[2 * 6 * BF_IMG_SLOT];
+
+// one thread's X row (Kp values) as NPART BF16 parts, 8 values per 16-byte store
+template <int Kp, int NPART>
+__device__ __forceinline__ void store_row_bf(unsigned char* x0, const float (&x)[Kp], int r) {
+    constexpr uint32_t sbo = (Kp / 8) * 128, part = TILE * Kp * 2;
+    unsigned char* base = x0 + (r >> 3) * sbo + (r & 7) * 16;
+#pragma unroll
+    for (int c = 0; c < Kp / 8; ++c) {
+        uint32_t w[NPART][4];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            uint32_t pk[NPART];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float rem = x[8 * c + j + h];
+#pragma unroll
+                for (int q = 0; q < NPART; ++q) {
+                    const __nv_bfloat16 b = __float2bfloat16_rn(rem);
+                    rem = rem - __bfloat162float(b);
+                    const uint32_t bits = __bfloat16_as_ushort(b);
+                    pk[q] = h == 0 ? bits : (pk[q] | (bits << 16));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NPART; ++q) w[q][j / 2] = pk[q];
+        }
+#pragma unroll
+        for (int q = 0; q < NPART; ++q)
+            *reinterpret_cast<uint4*>(base + q * part + c * 128) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+    }
+}
+
+// One matrix: D (+)= sum over its `ns` K slices of the products of the
+// parts of total order below NPART (X slices s0.., Q slices 0..).
+template <int NS_, int NPART>
+__device__ __forceinline__ void issue_bf_matrix(uint32_t tmem_d, uint32_t x0, uint32_t xpart, uint32_t sbo_x, int s0,
+                                                uint32_t q0, uint32_t qpart, uint32_t idesc) {
+    constexpr uint32_t sbo_q = NS_ * 256;
+#pragma unroll
+    for (int ks = 0; ks < NS_; ++ks) {
+        const uint32_t xo = (uint32_t)(s0 + ks) * 256, qo = (uint32_t)ks * 256;
+#pragma unroll
+        for (int i = 0; i < NPART; ++i)
+#pragma unroll
+            for (int j = 0; i + j < NPART; ++j) {
+                const uint64_t a = tc::smem_desc(x0 + i * xpart + xo, 128, sbo_x);
+                const uint64_t b = tc::smem_desc(q0 + j * qpart + qo, 128, sbo_q);
+                tc::mma_bf16(tmem_d, a, b, idesc, (ks > 0 || i > 0 || j > 0) ? 1u : 0u);
+            }
+    }
+}
+
+template <typename L, int NPART>
+__device__ __forceinline__ void issue_tile_bf(uint32_t tmem, uint32_t sXu, uint32_t sQu, bool doM, bool doK,
+                                              bool doT) {
+    if (doM)
+        issue_bf_matrix<L::NSM, NPART>(tmem + L::COLM, sXu, L::XPART, L::SBO_X, L::SM0, sQu + L::QM0, L::QM_B,
+                                       tc::idesc_bf16(L::NMp));
+    if (doK)
+        issue_bf_matrix<L::NSK, NPART>(tmem + L::COLK, sXu, L::XPART, L::SBO_X, L::SK0, sQu + L::QK0, L::QK_B,
+                                       tc::idesc_bf16(L::NMp));
+    if (doT)
+        issue_bf_matrix<L::NST, NPART>(tmem + L::COLT, sXu, L::XPART, L::SBO_X, L::ST0, sQu + L::QT0, L::QT_B,
+                                       tc::idesc_bf16(L::NTp));
+}
+
+// The BF16 tile kernel: the structure of element_tc_kernel with one thread
+// per element row (persistent CTAs, resident Q parts, next-tile prefetch,
+// one waiting thread, bulk-copy epilogue).
+template <typename ETy, int NPART>
+__global__ void __launch_bounds__(TILE) element_bf_kernel(const int* __restrict__ conn, const float* __restrict__ geo,
+                                                          int64_t E, int64_t gs, const double* __restrict__ u,
+                                                          CoeffDev k, float mass, float* __restrict__ VM,
+                                                          float* __restrict__ VK, float* __restrict__ VT,
+                                                          const unsigned char* __restrict__ img,
+                                                          int* __restrict__ err) {
+    using L = TbL<ETy, NPART>;
+    constexpr int NP = ETy::NP, NS = ETy::NS;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* sQ = smem;
+    unsigned char* sX = smem + L::QEND;
+    {   // resident Q parts
+        const int4* src = reinterpret_cast<const int4*>(img);
+        int4* dst = reinterpret_cast<int4*>(sQ);
+        for (int i = tid; i < L::QEND / 16; i += TILE) dst[i] = src[i];
+    }
+    const uint32_t mb = tc::smem_u32(&mbar);
+    if (tid == 0) {
+        tc::mbar_init(mb, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(&tmem_slot), L::ALLOC);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t sQu = tc::smem_u32(sQ), sXu = tc::smem_u32(sX);
+    const bool doM = VM != nullptr, doK = VK != nullptr, doT = VT != nullptr;
+    const bool need_u = doK | doT;
+    float* VMK = doM ? VM : doK ? VK - 1 : nullptr;   // interleaved M/K storage (K at odd positions)
+    float* stage = reinterpret_cast<float*>(sX);      // epilogue blocks (the X tile is consumed by then)
+    uint32_t phase = 0;
+    bool timed_out = false;
+    const int64_t ntiles = (E + TILE - 1) / TILE;
+    int pidx[NP];
+    double pu[NP];
+    float pgeo[1 + NS];
+    bool pvalid = false;
+    auto fetch_meta = [&](int64_t t) {
+        const int64_t e = t * TILE + tid;
+        pvalid = e < E;
+        if (pvalid) {
+            const int* ce = conn + e * NP;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) pidx[i] = need_u ? __ldg(ce + i) : 0;
+#pragma unroll
+            for (int t2 = 0; t2 <= NS; ++t2) pgeo[t2] = __ldg(geo + t2 * gs + e);
+        }
+    };
+    auto fetch_u = [&]() {
+        if (pvalid && need_u) {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) pu[i] = __ldg(u + pidx[i]);
+        }
+    };
+    if ((int64_t)blockIdx.x < ntiles) {
+        fetch_meta(blockIdx.x);
+        fetch_u();
+    }
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        float x[L::KTOTp];
+#pragma unroll
+        for (int i = 0; i < L::KTOTp; ++i) x[i] = 0.f;
+        if (pvalid) {
+            float2 su[NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) su[i] = need_u ? split_f64(pu[i]) : make_float2(0.f, 0.f);
+            form_x<ETy, L::KTOTp>(su, pgeo, need_u, k, mass, x);
+        }
+        const int64_t next = tile + gridDim.x;
+        if (next < ntiles) fetch_meta(next);
+        store_row_bf<L::KTOTp, NPART>(sX, x, tid);
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            issue_tile_bf<L, NPART>(tmem, sXu, sQu, doM, doK, doT);
+            tc::mma_commit(mb);
+        }
+        if (next < ntiles) fetch_u();
+        uint32_t ok = 1;
+        if (tid == 0) ok = tc::mbar_wait_bounded(mb, phase, WAIT_LIMIT);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        tc::fence_after_sync();
+        const int64_t row0 = tile * TILE + warp * 32;
+        epilogue_tile<ETy, L::XREG>(tmem, L::COLM, L::COLK, L::COLT, stage, VMK, VT, doM, doK, doT, row0, E, warp,
+                                    lane);
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (timed_out) {
+        if (tid == 0) atomicExch(err, 1);
+        tc::mbar_wait_bounded(mb, phase ^ 1u, WAIT_LIMIT);
+    }
+    if ((tid & 31) == 0) tc::bulk_wait_all();   // V copies of this warp are complete
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, L::ALLOC);
+}
+
 // host-side TF32 rounding, nearest with ties away from zero (matches cvt.rna)
 float tf32_rna_host(float x) {
     uint32_t b;
@@ -1171,6 +1391,65 @@ void build_image(std::vector<float>& all, const RefElem& R) {
         put_operand(img, L::QTh, L::QTl, PT.data(), L::NST * 8, ETy::NT, L::NST * 8);
     }
     std::copy(img.begin(), img.end(), all.begin() + (size_t)ETy::TYPE * IMG_SLOT_FLOATS);
+}
+
+// host-side BF16 rounding to nearest even (matches cvt.rn.bf16.f32)
+uint16_t bf16_rn_host(float x) {
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    if ((b & 0x7F800000u) == 0x7F800000u) return static_cast<uint16_t>((b >> 16) | ((b & 0xFFFFu) ? 0x40u : 0u));
+    b += 0x7FFFu + ((b >> 16) & 1u);
+    return static_cast<uint16_t>(b >> 16);
+}
+float bf16_to_float_host(uint16_t h) {
+    const uint32_t b = static_cast<uint32_t>(h) << 16;
+    float f;
+    std::memcpy(&f, &b, 4);
+    return f;
+}
+
+// Q (K x N, FP64, row-major) -> NPART BF16 parts of the B operand (N x Kp,
+// K-major core matrices of 8 rows x 8 values), part q at byte off + q * pstride
+void put_operand_bf(std::vector<unsigned char>& img, int off, int pstride, int npart, const double* Q, int K, int N,
+                    int Kp) {
+    const int sbo = (Kp / 8) * 128;
+    for (int n = 0; n < N; ++n)
+        for (int kk = 0; kk < K; ++kk) {
+            double rem = Q[(size_t)kk * N + n];
+            const int byte = (n >> 3) * sbo + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2;
+            for (int q = 0; q < npart; ++q) {
+                const uint16_t h = bf16_rn_host(static_cast<float>(rem));
+                rem -= static_cast<double>(bf16_to_float_host(h));
+                std::memcpy(&img[(size_t)off + (size_t)q * pstride + byte], &h, 2);
+            }
+        }
+}
+
+template <typename ETy, int NPART>
+void build_image_bf(std::vector<unsigned char>& all, const RefElem& R) {
+    using L = TbL<ETy, NPART>;
+    std::vector<unsigned char> img(BF_IMG_SLOT, 0);
+    if constexpr (L::FITS) {
+        // each matrix's slices: its own Q rows at their packed columns, zero
+        // rows at the neighbours' columns (as in build_image)
+        auto slices = [](const std::vector<double>& Q, int K, int N, int off, int s0, int ns) {
+            std::vector<double> P((size_t)ns * 16 * N, 0.0);
+            for (int kk = 0; kk < ns * 16; ++kk) {
+                const int own = s0 * 16 + kk - off;
+                if (own >= 0 && own < K)
+                    for (int n = 0; n < N; ++n) P[(size_t)kk * N + n] = Q[(size_t)own * N + n];
+            }
+            return P;
+        };
+        const auto PM = slices(R.QM, ETy::KM, ETy::NSYM, L::OFF_M, L::SM0, L::NSM);
+        const auto PK = slices(R.QK, ETy::KK, ETy::NSYM, L::OFF_K, L::SK0, L::NSK);
+        const auto PT = slices(R.QT, ETy::KT, ETy::NT, L::OFF_T, L::ST0, L::NST);
+        put_operand_bf(img, L::QM0, L::QM_B, NPART, PM.data(), L::NSM * 16, ETy::NSYM, L::NSM * 16);
+        put_operand_bf(img, L::QK0, L::QK_B, NPART, PK.data(), L::NSK * 16, ETy::NSYM, L::NSK * 16);
+        put_operand_bf(img, L::QT0, L::QT_B, NPART, PT.data(), L::NST * 16, ETy::NT, L::NST * 16);
+    }
+    const size_t slot = (size_t)(NPART - 2) * 6 + ETy::TYPE;
+    std::copy(img.begin(), img.end(), all.begin() + slot * BF_IMG_SLOT);
 }
 
 // Operand images of the Q chunks of the chunked product, step after step:
@@ -1387,6 +1666,21 @@ int tables_init_tc() {
     FEM_CUDA_TRY(cudaMemcpyToSymbol(c_tcref, ref.data(), sizeof(float) * TAB_TOTAL));
     FEM_CUDA_TRY(cudaMemcpyToSymbol(g_tcimg, img.data(), sizeof(float) * img.size()));
     {
+        std::vector<unsigned char> bimg((size_t)2 * 6 * BF_IMG_SLOT, 0);
+        for (int t = 0; t < 6; ++t) {
+            const RefElem* R = refelem_for_type(t);
+            switch (t) {
+                case 0: build_image_bf<ET<2, 1>, 2>(bimg, *R); build_image_bf<ET<2, 1>, 3>(bimg, *R); break;
+                case 1: build_image_bf<ET<2, 2>, 2>(bimg, *R); build_image_bf<ET<2, 2>, 3>(bimg, *R); break;
+                case 2: build_image_bf<ET<2, 3>, 2>(bimg, *R); build_image_bf<ET<2, 3>, 3>(bimg, *R); break;
+                case 3: build_image_bf<ET<3, 1>, 2>(bimg, *R); build_image_bf<ET<3, 1>, 3>(bimg, *R); break;
+                case 4: build_image_bf<ET<3, 2>, 2>(bimg, *R); build_image_bf<ET<3, 2>, 3>(bimg, *R); break;
+                case 5: build_image_bf<ET<3, 3>, 2>(bimg, *R); build_image_bf<ET<3, 3>, 3>(bimg, *R); break;
+            }
+        }
+        FEM_CUDA_TRY(cudaMemcpyToSymbol(g_tbimg, bimg.data(), bimg.size()));
+    }
+    {
         std::vector<float> big;
         const RefElem* R5 = refelem_for_type(5);
         if (!R5) return fail(FEM_EINVAL, "reference element tables failed");
@@ -1521,6 +1815,93 @@ int tc_error_flag(int clear) {
         cudaMemcpyToSymbol(g_tc_err, &zero, sizeof(int));
     }
     return v;
+}
+
+template <typename ETy, int NPART>
+int launch_bf(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT, cudaStream_t s,
+              int64_t e0, int64_t e1) {
+    using L = TbL<ETy, NPART>;
+    if constexpr (!L::FITS) {
+        return fail(FEM_EINVAL, "FEM_BF16X3 / FEM_BF16X6 are not available for this element type (tile does not fit)");
+    } else {
+        const int64_t E = e1 - e0;
+        if (E <= 0) return FEM_OK;
+        auto kern = element_bf_kernel<ETy, NPART>;
+        static std::atomic<int> have[64];
+        static LaunchShape cache[64];
+        static std::mutex mu;
+        LaunchShape sh;
+        int rc = cached_shape(have, cache, mu, [&](int dev, LaunchShape& o) -> int {
+            int optin = 0, occ = 0;
+            FEM_CUDA_TRY(cudaDeviceGetAttribute(&o.nsm, cudaDevAttrMultiProcessorCount, dev));
+            FEM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            cudaFuncAttributes fa;
+            FEM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+            const int dyn_max = optin - (int)fa.sharedSizeBytes;
+            int smem = L::SMEM;
+            if (smem > dyn_max) return fail(FEM_EINVAL, "BF16 tensor-core tile does not fit in shared memory");
+            FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                              (int)cudaSharedmemCarveoutMaxShared));
+            FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+            const int occ_max = 512 / L::ALLOC;   // co-resident CTAs must fit their TMEM columns
+            if (occ > occ_max) {
+                int per_sm = 0;
+                FEM_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+                smem = per_sm / (occ_max + 1) + 1;
+                if (smem > dyn_max) smem = dyn_max;
+                FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+                if (occ > occ_max) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
+            }
+            if (occ < 1) return fail(FEM_ECUDA, "BF16 tensor-core kernel does not fit on an SM");
+            o.occ = std::max(occ, std::min(occ_max, ctas_per_sm(fa, TILE, smem, dev)));
+            o.smem = smem;
+            void* img = nullptr;
+            FEM_CUDA_TRY(cudaGetSymbolAddress(&img, g_tbimg));
+            o.img = static_cast<const unsigned char*>(img) + ((size_t)(NPART - 2) * 6 + ETy::TYPE) * BF_IMG_SLOT;
+            FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&o.err, g_tc_err));
+            return FEM_OK;
+        }, sh);
+        if (rc) return rc;
+        const int64_t ntiles = (E + TILE - 1) / TILE;
+        int64_t grid = (int64_t)sh.nsm * sh.occ;
+        if (grid > ntiles) grid = ntiles;
+        trace_launch("element_bf_kernel", grid, TILE, sh.smem, sh.occ);
+        cudaGetLastError();   // clear any stale error before the launch check
+        kern<<<(unsigned)grid, TILE, sh.smem, s>>>(m.conn.as<int>() + e0 * ETy::NP, m.geo32.as<float>() + e0, E, m.E, u,
+                                                   k, (float)m.m, VM ? VM + 2 * e0 * ETy::NSYM : nullptr,
+                                                   VK ? VK + 2 * e0 * ETy::NSYM : nullptr,
+                                                   VT ? VT + e0 * ETy::NT : nullptr,
+                                                   static_cast<const unsigned char*>(sh.img), sh.err);
+        FEM_CUDA_TRY(cudaGetLastError());
+        return FEM_OK;
+    }
+}
+
+template <int NPART>
+int dispatch_bf(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
+                cudaStream_t s, int64_t e0, int64_t e1) {
+    switch (m.type) {
+        case 0: return launch_bf<ET<2, 1>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 1: return launch_bf<ET<2, 2>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 2: return launch_bf<ET<2, 3>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 3: return launch_bf<ET<3, 1>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 4: return launch_bf<ET<3, 2>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 5: return launch_bf<ET<3, 3>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
+    }
+    return fail(FEM_EINVAL, "element type");
+}
+
+int element_tc_bf16(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
+                    int nparts, cudaStream_t s, int64_t e0, int64_t e1) {
+    if (e1 < 0) e1 = m.E;
+    if (e0 < 0 || e0 > e1 || e1 > m.E) return fail(FEM_EINVAL, "element range out of bounds");
+    int rc = tables_init_tc();
+    if (rc) return rc;
+    if (nparts == 2) return dispatch_bf<2>(m, k, u, VM, VK, VT, s, e0, e1);
+    if (nparts == 3) return dispatch_bf<3>(m, k, u, VM, VK, VT, s, e0, e1);
+    return fail(FEM_EINVAL, "BF16 split into 2 or 3 parts");
 }
 
 int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,

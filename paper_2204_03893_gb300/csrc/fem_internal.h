@@ -96,6 +96,9 @@ int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const double* u, flo
 // whole-mesh arrays, rows e0.. are written.
 int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
                       cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);
+// The BF16 split-precision product (nparts 2: BF16x3, 3: BF16x6).
+int element_tc_bf16(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
+                    int nparts, cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);
 
 // Segmented reduction of V into CSR values (outputs may be null).
 // s0, s1: slot range [s0, s1) (s1 = -1: to the end); outputs are the

@@ -366,7 +366,7 @@ extern "C" {
 int fem_serve_create(const fem_serve_opts* opts, fem_server** out) {
     if (!opts || !out) return fail(FEM_EINVAL, "NULL argument");
     *out = nullptr;
-    if (opts->prec != FEM_FP64 && opts->prec != FEM_TF32X3 && opts->prec != FEM_FP32)
+    if (opts->prec < FEM_FP64 || opts->prec > FEM_BF16X6)
         return fail(FEM_EINVAL, "unknown precision");
     if (opts->max_inflight < 1 || opts->n_streams < 1 || opts->n_streams > 64 || opts->budget_bytes == 0)
         return fail(FEM_EINVAL, "need max_inflight >= 1, 1 <= n_streams <= 64 and a nonzero budget");

@@ -6,12 +6,12 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (FEM_FP32, FEM_FP64, FEM_MEM_HOST, FEM_REQ_ASSEMBLE, FEM_REQ_REASSEMBLE, FEM_TF32X3, coeff,
+from . import (FEM_BF16X3, FEM_BF16X6, FEM_FP32, FEM_FP64, FEM_MEM_HOST, FEM_REQ_ASSEMBLE, FEM_REQ_REASSEMBLE, FEM_TF32X3, coeff,
                fem_assemble_all, fem_copy_pattern, fem_get_slot_map, fem_mesh_create, fem_mesh_desc,
                fem_mesh_destroy, fem_mesh_get_info, fem_serve_create, fem_serve_destroy, fem_serve_evict,
                fem_serve_opts, fem_serve_poll, fem_serve_release, fem_serve_stats, fem_serve_submit, fem_symbolic)
 
-PRECISIONS = {"fp64": FEM_FP64, "tf32x3": FEM_TF32X3, "fp32": FEM_FP32}
+PRECISIONS = {"fp64": FEM_FP64, "tf32x3": FEM_TF32X3, "fp32": FEM_FP32, "bf16x3": FEM_BF16X3, "bf16x6": FEM_BF16X6}
 
 
 class FemMesh:

@@ -7,6 +7,13 @@ Bars (per matrix M, K(u), T(u)):
     slot (entries that cancel are judged against the size of what cancelled);
   * FEM_TF32X3: relative Frobenius error <= 1e-6 per matrix;
   * FEM_FP32 (SIMT reference point): relative Frobenius error <= 1e-5;
+  * FEM_BF16X6: relative Frobenius error <= 1e-6 (three BF16 parts carry
+    the 24 bits of an FP32 value; the dropped products are of order 2^-24);
+  * FEM_BF16X3: relative Frobenius error <= 2e-4: two parts leave each
+    operand within 2^-16 of its value and drop x1 q1, so a product term is
+    within about 3 * 2^-16 = 4.6e-5 of |x||q|, and the sums over the
+    quadrature points (signed terms in K and T) lose up to a small factor
+    more relative to the entry;
   * every precision: bitwise identical results run to run.
 Sizes span several 128-element tiles with a ragged last tile.
 """
@@ -25,11 +32,14 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_2204_03893_gb300 as F  # noqa: E402
-from paper_2204_03893_gb300.torch_api import FemMesh  # noqa: E402
+from paper_2204_03893_gb300.torch_api import PRECISIONS, FemMesh  # noqa: E402
 
 FP64_TOL = 1e-12
 TF32_TOL = 1e-6
 FP32_TOL = 1e-5
+BF16X6_TOL = 1e-6
+BF16X3_TOL = 2e-4
+BF_TOL = {"bf16x3": BF16X3_TOL, "bf16x6": BF16X6_TOL}
 
 
 def wl_small(name):
@@ -148,7 +158,53 @@ def test_fp32_simt_parity_frobenius(name):
         assert frob(g[k], o[k]) <= FP32_TOL, (k, frob(g[k], o[k]))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("name", ["tri_p1", "tri_p2", "tet_p1", "tet_p2", "tri_p3"])
+def test_bf16_split_parity_frobenius(prec, name):
+    """The BF16 split products (kind::f16 tensor-core MMAs) against the
+    oracle; tet_p3 has no BF16 tile (test_bf16_unavailable_cases)."""
+    wl = wl_small(name)
+    _, o = oracle_result(name, wl)
+    fm = FemMesh.of(wl.mesh)
+    g = gpu_assemble(fm, wl, prec)
+    F.fem_device_status()
+    for k in ("M", "K", "T"):
+        assert frob(g[k], o[k]) <= BF_TOL[prec], (k, frob(g[k], o[k]))
+
+
+def test_bf16x6_closer_than_bf16x3():
+    """The third part must bring the error down to the FP32 floor of the
+    formation (X in FP32, FP32 accumulation), well below BF16X3's: a slip in
+    the x2 / q2 operands would leave BF16X6 at or above BF16X3's level."""
+    wl = wl_small("tet_p2")
+    _, o = oracle_result("tet_p2", wl)
+    fm = FemMesh.of(wl.mesh)
+    g3 = gpu_assemble(fm, wl, "bf16x3")
+    g6 = gpu_assemble(fm, wl, "bf16x6")
+    errs = {k: (frob(g3[k], o[k]), frob(g6[k], o[k])) for k in ("M", "K", "T")}
+    for k, (e3, e6) in errs.items():
+        assert e6 * 4 < e3 and e6 <= BF16X6_TOL, errs
+
+
+def test_bf16_unavailable_cases():
+    """P3 tetrahedra (their BF16 tile exceeds shared memory) and batches
+    refuse the BF16 modes with FEM_EINVAL and leave the device usable."""
+    wl = wl_small("tet_p3")
+    fm = FemMesh.of(wl.mesh)
+    u = torch.tensor(wl.u, dtype=torch.float64, device="cuda")
+    for prec in ("bf16x3", "bf16x6"):
+        with pytest.raises(F.FemError) as ei:
+            fm.assemble(u, wl.coeff.kind, wl.coeff.params, prec)
+        assert ei.value.code == F.FEM_EINVAL
+        with pytest.raises(F.FemError) as ei:
+            F.fem_batch_create([fm.h], F.fem_batch_opts(PRECISIONS[prec], 0, 1, 0))
+        assert ei.value.code == F.FEM_EINVAL
+    fm.assemble(u, wl.coeff.kind, wl.coeff.params, "tf32x3")
+    torch.cuda.synchronize()
+    F.fem_device_status()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "fp32", "bf16x3", "bf16x6"])
 def test_run_to_run_bitwise(prec):
     wl = wl_small("tri_p2")
     fm = FemMesh.of(wl.mesh)
@@ -348,7 +404,9 @@ def test_tiny_meshes(d, p, n):
     c = mg.Coeff("poly", (1.0, 0.5, 0.25, 0.0, 0.0))
     r = orc.Oracle.of(m).assemble(u, c)
     fm = FemMesh.of(m)
-    for prec in ("fp64", "tf32x3", "fp32"):
+    precs = ("fp64", "tf32x3", "fp32") + (("bf16x3", "bf16x6") if (d, p) != (3, 3) else ())
+    tol = {"tf32x3": TF32_TOL, "fp32": FP32_TOL, **BF_TOL}
+    for prec in precs:
         g = fm.assemble(torch.tensor(u, device="cuda"), c.kind, c.params, prec)
         torch.cuda.synchronize()
         for k in ("M", "K", "T"):
@@ -356,7 +414,7 @@ def test_tiny_meshes(d, p, n):
             if prec == "fp64":
                 assert (np.abs(gk - r[k]) <= FP64_TOL * r["abs" + k] + 1e-300).all(), (prec, k)
             else:
-                assert frob(gk, r[k]) <= (TF32_TOL if prec == "tf32x3" else FP32_TOL), (prec, k, frob(gk, r[k]))
+                assert frob(gk, r[k]) <= tol[prec], (prec, k, frob(gk, r[k]))
     F.fem_device_status()
 
 
