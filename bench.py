@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-modes", action="store_true",
+                    help="skip the per-precision step times and errors on the bench workload")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-mesh batched measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream measurement")
     ap.add_argument("--serve-requests", type=int, default=20000)
@@ -221,6 +223,50 @@ def _pct(xs, q):
         return None
     i = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
     return xs[i]
+
+
+def measure_modes(F, torch, fm, k, us, u64, o64, stream, E, steps=30, warmup=3):
+    """Every single-mesh precision on the bench workload: the form + sum step
+    timed with CUDA events on its stream (fresh u each step, as the headline),
+    and the relative Frobenius error of M, K(u), T(u) against the FEM_FP64
+    reassembly o64 of u64 (itself within 1e-12 * absum of the oracle)."""
+    sh = stream.cuda_stream
+    which = F.FEM_MAT_M | F.FEM_MAT_K | F.FEM_MAT_T
+    res = {}
+    for name in ("tf32x3", "bf16x3", "bf16x6", "fp32"):
+        p = PRECISIONS[name]
+        out = {c: torch.empty_like(o64["M"], dtype=torch.float32) for c in "MKT"}
+
+        def step(u):
+            F.fem_form_elements(fm.h, k, u, p, which, sh)
+            F.fem_sum_elements(fm.h, p, out["M"], out["K"], out["T"], sh)
+
+        try:
+            for i in range(warmup):
+                step(us[i % len(us)])
+        except F.FemError as ex:
+            res[name] = {"unavailable": str(ex)}
+            continue
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        torch.cuda.synchronize()
+        for i in range(steps):
+            ev[i][0].record(stream)
+            F.fem_form_elements(fm.h, k, us[i % len(us)], p, which, sh)
+            ev[i][1].record(stream)
+            F.fem_sum_elements(fm.h, p, out["M"], out["K"], out["T"], sh)
+            ev[i][2].record(stream)
+        torch.cuda.synchronize()
+        form = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+        summ = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+        step(u64)
+        torch.cuda.synchronize()
+        err = {c: float(torch.linalg.vector_norm(out[c].double() - o64[c]) / torch.linalg.vector_norm(o64[c]))
+               for c in "MKT"}
+        res[name] = {"ms_per_step": form + summ, "value": E / ((form + summ) / 1e3), "unit": "elements/s",
+                     "element_form_ms": form, "csr_sum_ms": summ, "rel_frobenius_vs_fp64": err,
+                     "product": PRODUCT_DESC.get(name, "FP32 SIMT (no tensor cores)")}
+        del out
+    return res
 
 
 PRODUCT_DESC = {
@@ -551,6 +597,7 @@ def run_ours(args, rank, world, local_rank):
 
         # FP64 plain path on the same workload (one-matrix-at-a-time reference point)
         fp64 = None
+        modes = None
         if not args.no_fp64 and args.prec != "fp64":
             u64 = torch.tensor(wl.u, dtype=torch.float64, device="cuda")
             o64 = {kk: torch.empty(nnz, dtype=torch.float64, device="cuda") for kk in "MKT"}
@@ -571,6 +618,8 @@ def run_ours(args, rank, world, local_rank):
             ms64 = a.elapsed_time(b) / n64
             fp64 = {"value": E / (ms64 / 1e3), "unit": "elements/s", "ms_per_step": ms64,
                     "mode": "FEM_FP64 SIMT, one matrix per call (3 calls, 6 launches)"}
+            if not args.no_modes:
+                modes = measure_modes(F, torch, fm, k, us, u64, o64, stream, E)
             del o64
 
         # end to end through the C ABI with pinned host buffers
@@ -652,7 +701,7 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"{world} independent meshes, one per GPU" if world > 1 else "single GPU"},
         "roofline": roofline, "phases": phases,
         "setup_once_per_mesh_ms": {"mesh_create_geometry": 1e3 * t_mesh, "symbolic_pattern": 1e3 * t_sym},
-        "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64, "clocks": clk.summary(),
+        "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64, "modes": modes, "clocks": clk.summary(),
         "gpu_launches": args.steps * 2,
         "batched": batched, "serve": served, "configs": configs,
     }
