@@ -230,6 +230,7 @@ def measure_modes(F, torch, fm, k, us, u64, o64, stream, E, steps=30, warmup=3):
     timed with CUDA events on its stream (fresh u each step, as the headline),
     and the relative Frobenius error of M, K(u), T(u) against the FEM_FP64
     reassembly o64 of u64 (itself within 1e-12 * absum of the oracle)."""
+    from paper_2204_03893_gb300.torch_api import PRECISIONS
     sh = stream.cuda_stream
     which = F.FEM_MAT_M | F.FEM_MAT_K | F.FEM_MAT_T
     res = {}
