@@ -230,15 +230,16 @@ __device__ __forceinline__ void segsum_warp(uint32_t k0, uint32_t k1, uint32_t n
     }
 }
 
-// Launch shape per scan depth, measured on GB300 (FP32 values): triangle
-// meshes (short segments, 2 scan steps) run best with registers capped for
-// 6 blocks of 256 threads per SM and short warp tasks; tetrahedral meshes
-// (4-5 steps, long segments) with 5 blocks and longer tasks; FP64 values
-// with 4 blocks.
+// Launch shape, measured on GB300: FP32 values run best with registers
+// capped for 5 blocks of 256 threads per SM (tri_p2_1024: 0.390 ms vs 0.434
+// with 6 blocks and 0.398 with 4; the tetrahedral meshes lose 5-20% with 4
+// or 6), FP64 values with 4; warp tasks of 32 pair groups (tri_p2_1024:
+// 0.382 ms vs 0.389 with 16 and 0.412 with 8; the tetrahedral meshes are
+// flat from 32 to 48).
 template <int STEPS, typename T>
 struct SegShape {
-    static constexpr int MIN_BLOCKS = sizeof(T) == 8 ? 4 : STEPS <= 2 ? 6 : 5;
-    static constexpr uint32_t TASK = STEPS <= 2 ? 16 : 32;   // pair groups per warp task (at most)
+    static constexpr int MIN_BLOCKS = sizeof(T) == 8 ? 4 : 5;
+    static constexpr uint32_t TASK = 32;   // pair groups per warp task (at most)
 };
 
 // Slots [s0, s1) of one mesh; the warps take tasks grid-stride, so the
