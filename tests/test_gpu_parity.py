@@ -495,3 +495,49 @@ def test_full_size_tri_p2_1024_sampled(prec):
     for k in ("M", "K", "T"):
         err = np.abs(g[k][slots] - s[k])
         assert (err <= tol * s["abs" + k] + 1e-300).all(), (k, (err / s["abs" + k]).max())
+
+
+_TET_FULL = {"tet_p1_128": (128, lambda N: 15 * N**3 + 21 * N**2 + 9 * N + 1),
+             "tet_p2_64": (64, lambda N: 230 * N**3 + 138 * N**2 + 24 * N + 1)}
+
+
+@pytest.mark.parametrize("name,prec", [("tet_p1_128", "tf32x3"), ("tet_p2_64", "tf32x3"), ("tet_p2_64", "fp64")])
+def test_full_size_tetrahedra_sweep_sampled(name, prec):
+    """12 582 912 P1 / 1 572 864 P2 tetrahedra in the benchmark's launch
+    configuration, reassembled with fresh fields on one symbolic pattern
+    (Newton-style sweep): nnz by its closed form, sampled rows' patterns
+    from the element definition, the last reassembly's sampled entries
+    against the oracle computed one by one, and the first field reassembled
+    again at the end equal bit for bit to its first reassembly."""
+    wl = mg.workload(name)
+    N, nnz_of = _TET_FULL[name]
+    fm = FemMesh.of(wl.mesh)
+    fm.symbolic()
+    assert fm.nnz == nnz_of(N)
+    rp, ci = (t.cpu().numpy() for t in fm.pattern())
+    conn = wl.mesh.conn
+    rng = np.random.default_rng(321)
+    flat = conn.ravel()
+    perm = np.argsort(flat, kind="stable")
+    order = perm // conn.shape[1]                                  # elements, grouped by node
+    starts = np.searchsorted(flat[perm], np.arange(wl.mesh.n_nodes + 1))
+    for r in rng.choice(wl.mesh.n_nodes, 10, replace=False):
+        els = order[starts[r]:starts[r + 1]]
+        assert np.array_equal(ci[rp[r]:rp[r + 1]], np.unique(conn[els]))
+    fields = [mg.fourier_field(wl.mesh.coords, 3 + s) for s in range(3)]
+    first = None
+    for f in fields:
+        g = gpu_assemble(fm, mg.Workload(wl.name, wl.mesh, f, wl.coeff), prec)
+        if first is None:
+            first = g
+    again = gpu_assemble(fm, mg.Workload(wl.name, wl.mesh, fields[0], wl.coeff), prec)
+    F.fem_device_status()
+    for k in ("M", "K", "T"):
+        assert np.array_equal(again[k], first[k]), k
+    slots = rng.choice(fm.nnz, 2000, replace=False)
+    row_of = np.searchsorted(rp, slots, side="right") - 1
+    s = orc.Oracle.of(wl.mesh).entries(row_of, ci[slots], fields[-1], wl.coeff)
+    tol = FP64_TOL if prec == "fp64" else 2e-6
+    for k in ("M", "K", "T"):
+        err = np.abs(g[k][slots] - s[k])
+        assert (err <= tol * s["abs" + k] + 1e-300).all(), (k, (err / s["abs" + k]).max())
