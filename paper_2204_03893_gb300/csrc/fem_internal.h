@@ -137,8 +137,8 @@ struct BatchMesh {
     int max_seg, pad2;
     void* vM; void* vK; void* vT;        // CSR outputs, NULL = skip
 };
-// One unit of work: `count` consecutive elements (or nodes, or groups of 32
-// contributions) of one mesh.
+// One unit of work: `count` consecutive elements (or nodes, or pair groups of
+// 64 contributions) of one mesh.
 struct BatchItem {
     int mesh;
     int type;

@@ -9,9 +9,9 @@
 // share V[e][sym(min,max)]; M and K interleaved), T from the full n_p x n_p
 // storage.
 //
-// A warp sums 32 consecutive contributions at a time (one lane each) with a
-// segmented scan over the lanes; the slot boundaries come from per-group
-// head masks built by the symbolic phase.
+// A warp sums 64 consecutive contributions at a time (two per lane) with a
+// segmented scan over the lanes; the slot boundaries come from the head
+// masks of the groups of 32 contributions built by the symbolic phase.
 #include <algorithm>
 #include <vector>
 
