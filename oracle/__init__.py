@@ -7,7 +7,8 @@ never imports, links or runs it; the two share no code.
 The arithmetic lives in ``fem_oracle.c`` (plain C, FP64): Algorithm 1 of the
 paper (element loop, quadrature loop, dense local matrices, scatter-add), the
 tangent as the Section 5.2 conductivity tensor multiplied by u in its second
-mode, and its own quadrature tables, Lagrange basis and CSR construction.
+mode, the u-dependent mass with the Section 5.1 mass tensor multiplied by
+u - u^s in its second mode, and its own quadrature tables, Lagrange basis and CSR construction.
 This module compiles it with gcc and wraps it with ctypes.
 """
 from __future__ import annotations
@@ -68,6 +69,8 @@ def lib():
             L.oracle_entries.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, dp, C.c_int, dp,
                                          C.c_longlong, ip, ip] + [dp] * 6
             L.oracle_entries.restype = C.c_int
+            L.oracle_assemble_mass_u.argtypes = [C.c_void_p, C.c_int, C.c_int, dp, C.c_int, dp, dp] + [dp] * 4
+            L.oracle_assemble_mass_u.restype = C.c_int
             _lib = L
     return _lib
 
@@ -162,6 +165,25 @@ class Oracle:
                                    _dp(out.get("absM")), _dp(out.get("absK")), _dp(out.get("absT")))
         if rc != 0:
             raise RuntimeError(f"oracle_assemble failed ({rc})")
+        return out
+
+    def assemble_mass_u(self, u, us, mcoeff, deg: int = 0):
+        """M(u) (mass with the coefficient law m(u)) and the mass tensor of
+        Section 5.1 multiplied by z = u - us in its second mode, as CSR
+        values: dict with 'Mu', 'Mt', 'absMu', 'absMt' (us may be None:
+        'Mt' then is not computed)."""
+        nz = self.nnz()
+        out = {k: np.zeros(nz) for k in ("Mu", "absMu")}
+        if us is not None:
+            out.update({k: np.zeros(nz) for k in ("Mt", "absMt")})
+        cp = mcoeff.numpy()
+        uu = np.ascontiguousarray(u, dtype=np.float64)
+        ss = None if us is None else np.ascontiguousarray(us, dtype=np.float64)
+        rc = lib().oracle_assemble_mass_u(self._h, self._deg(deg, self.p), KIND[mcoeff.kind], _dp(cp), len(cp),
+                                          _dp(uu), _dp(ss), _dp(out["Mu"]), _dp(out.get("Mt")),
+                                          _dp(out["absMu"]), _dp(out.get("absMt")))
+        if rc != 0:
+            raise RuntimeError(f"oracle_assemble_mass_u failed ({rc})")
         return out
 
     def entries(self, rows, cols, u, coeff, m: float = 1.0, deg: int = 0):

@@ -26,6 +26,8 @@
  *                   = sum_q w_q k'_q |det B_e| (S_q u_e)[i] phi_q[k],
  *     with S_q = J_q A_e J_q^T; row i is the test function, column k the
  *     trial direction.
+ *   - The u-dependent mass M(u) (m = m(u_h)) and the Section 5.1 mass
+ *     tensor multiplied by u - u^s in its second mode (oracle_assemble_mass_u).
  *   - B_e = [x_1 - x_0, ..., x_d - x_0] (Section 3 step 3, affine map).
  *   - Global assembly: every (row, col) pair of nodes that share an element
  *     is a structural nonzero (Section 3 step 2); contributions are added in
@@ -610,6 +612,85 @@ int oracle_entries(void* h, int deg, double m, int kkind, const double* kp, int 
         if (absM) absM[k] = s[3];
         if (absK) absK[k] = s[4];
         if (absT) absT[k] = s[5];
+    }
+    return 0;
+}
+
+/* u-dependent mass and the mass tensor (Section 2 with m = m(u_h); Section 5,
+ * the Jacobian term  (mass tensor) o_2 (u - u^s) + M(u); Section 5.1, the
+ * local mass tensor):
+ *     Mu_e        = sum_q w_q m(u_q)  phi_q phi_q^T               |det B_e|
+ *     Mc_e[i][j][k] = sum_q w_q m'(u_q) phi_q[i] phi_q[j] phi_q[k] |det B_e|
+ *     Mt_e[i][k]  = sum_j Mc_e[i][j][k] z_e[j],   z = u - us,
+ * the tensor formed in full and then multiplied by z in its second mode,
+ * assembled over ascending elements into the CSR pattern.  m is a
+ * coefficient law as k (kind, parameters).  absMu/absMt receive the sums of
+ * the magnitudes of the expanded terms.  Any output may be NULL; us may be
+ * NULL when Mt and absMt are. */
+int oracle_assemble_mass_u(void* h, int deg, int mkind, const double* mp, int nmp, const double* u,
+                           const double* us, double* Mu, double* Mt, double* absMu, double* absMt) {
+    octx* c = (octx*)h;
+    if (build_pattern(c)) return -1;
+    otab t;
+    if (make_tab(c->d, c->p, deg, &t)) return -1;
+    if ((Mt || absMt) && !us) return -3;
+    int np = c->np;
+    size_t nz = (size_t)c->nnz;
+    double* out[4] = {Mu, Mt, absMu, absMt};
+    for (int k = 0; k < 4; ++k) if (out[k]) memset(out[k], 0, sizeof(double) * nz);
+    static double Mc[OR_MAXNP * OR_MAXNP * OR_MAXNP], aMc[OR_MAXNP * OR_MAXNP * OR_MAXNP];
+    double Me[OR_MAXNP * OR_MAXNP], aMe[OR_MAXNP * OR_MAXNP], Te[OR_MAXNP * OR_MAXNP], aTe[OR_MAXNP * OR_MAXNP];
+    for (int e = 0; e < c->E; ++e) {
+        double A[3][3];
+        double b = fabs(geometry(c, e, A));
+        const int* v = c->conn + (long long)e * np;
+        double ue[OR_MAXNP], ze[OR_MAXNP];
+        for (int i = 0; i < np; ++i) {
+            ue[i] = u[v[i]];
+            ze[i] = us ? u[v[i]] - us[v[i]] : 0.0;
+        }
+        memset(Me, 0, sizeof(Me));
+        memset(aMe, 0, sizeof(aMe));
+        memset(Mc, 0, sizeof(double) * np * np * np);
+        memset(aMc, 0, sizeof(double) * np * np * np);
+        for (int q = 0; q < t.nq; ++q) {
+            const double* phi = t.phi[q];
+            double uq = 0.0;
+            for (int i = 0; i < np; ++i) uq += phi[i] * ue[i];
+            double dm;
+            double mq = oracle_k(mkind, mp, nmp, uq, &dm);
+            double wb = t.w[q] * b;
+            for (int i = 0; i < np; ++i)
+                for (int j = 0; j < np; ++j) {
+                    Me[i * np + j] += wb * mq * phi[i] * phi[j];
+                    aMe[i * np + j] += fabs(wb * mq * phi[i] * phi[j]);
+                    for (int k = 0; k < np; ++k) {
+                        Mc[(i * np + j) * np + k] += wb * dm * phi[i] * phi[j] * phi[k];
+                        aMc[(i * np + j) * np + k] += fabs(wb * dm * phi[i] * phi[j] * phi[k]);
+                    }
+                }
+        }
+        /* second-mode product with z_e */
+        for (int i = 0; i < np; ++i)
+            for (int k = 0; k < np; ++k) {
+                double s = 0.0, a = 0.0;
+                for (int j = 0; j < np; ++j) {
+                    s += Mc[(i * np + j) * np + k] * ze[j];
+                    a += aMc[(i * np + j) * np + k] * fabs(ze[j]);
+                }
+                Te[i * np + k] = s;
+                aTe[i * np + k] = a;
+            }
+        for (int i = 0; i < np; ++i)
+            for (int j = 0; j < np; ++j) {
+                long long s = find_slot(c, v[i], v[j]);
+                if (s < 0) return -2;
+                int l = i * np + j;
+                if (Mu) Mu[s] += Me[l];
+                if (Mt) Mt[s] += Te[l];
+                if (absMu) absMu[s] += aMe[l];
+                if (absMt) absMt[s] += aTe[l];
+            }
     }
     return 0;
 }
