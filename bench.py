@@ -291,6 +291,41 @@ def gemm_flops_per_element(d, p):
     return 2 * (n_q * nsym + n_q * ns * nsym + n_q * d * n_p * n_p)
 
 
+def measure_mass_u(F, torch, fm, wl, us, stream, fp64_peak, steps=20, warmup=3):
+    """The u-dependent mass and its Newton term (fem_assemble_mass_u: M(u)
+    with m(u) = 1 + u/2 + u^2/4 and the mass tensor times (u - u^s)) on the
+    bench workload, FEM_FP64 and FEM_FP32, timed with CUDA events; each
+    call forms the two Q_M products and sums both into CSR."""
+    sh = stream.cuda_stream
+    mk = F.coeff("poly", (1.0, 0.5, 0.25))
+    E = wl.mesh.n_elems
+    n_p = wl.mesh.conn.shape[1]
+    nsym = n_p * (n_p + 1) // 2
+    n_q = {(2, 1): 3, (2, 2): 6, (2, 3): 12, (3, 1): 4, (3, 2): 11, (3, 3): 24}[(wl.mesh.d, wl.mesh.p)]
+    res = {"law": "poly (1.0, 0.5, 0.25)", "elements": E}
+    for name, prec, dt in (("fp64", F.FEM_FP64, torch.float64), ("fp32", F.FEM_FP32, torch.float32)):
+        out = [torch.empty(fm.nnz, dtype=dt, device="cuda") for _ in range(2)]
+        for i in range(warmup):
+            F.fem_assemble_mass_u(fm.h, mk, us[i % len(us)], us[(i + 1) % len(us)], prec, out[0], out[1], sh)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(steps):
+            F.fem_assemble_mass_u(fm.h, mk, us[i % len(us)], us[(i + 1) % len(us)], prec, out[0], out[1], sh)
+        b.record(stream)
+        torch.cuda.synchronize()
+        F.fem_device_status(sh)
+        ms = a.elapsed_time(b) / steps
+        r = {"ms_per_call": ms, "value": E / (ms / 1e3), "unit": "elements/s"}
+        if name == "fp64" and fp64_peak:
+            tf = 4.0 * n_q * nsym * E / (ms / 1e3) / 1e12   # two products of K = n_q, N = n_sym
+            r["gemm_rate"] = {"achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": tf / fp64_peak,
+                              "note": "whole call (products and CSR sum) timed"}
+        res[name] = r
+        del out
+    return res
+
+
 def measure_fp64_peak(torch, stream, n=4096, reps=5):
     """Measured FP64 peak: a cuBLAS DGEMM of n^3 (torch.mm on FP64 tensors),
     timed with CUDA events on the stream after one warm-up."""
@@ -643,6 +678,7 @@ def run_ours(args, rank, world, local_rank):
         # FP64 plain path on the same workload (one-matrix-at-a-time reference point)
         fp64 = None
         modes = None
+        mass_u = None
         if not args.no_fp64 and args.prec != "fp64":
             u64 = torch.tensor(wl.u, dtype=torch.float64, device="cuda")
             o64 = {kk: torch.empty(nnz, dtype=torch.float64, device="cuda") for kk in "MKT"}
@@ -665,6 +701,7 @@ def run_ours(args, rank, world, local_rank):
                     "mode": "FEM_FP64 SIMT, one matrix per call (3 calls, 6 launches)"}
             if not args.no_modes:
                 modes = measure_modes(F, torch, fm, k, us, u64, o64, stream, E)
+                mass_u = measure_mass_u(F, torch, fm, wl, us, stream, measure_fp64_peak(torch, stream))
             del o64
 
         # end to end through the C ABI with pinned host buffers
@@ -748,7 +785,7 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"{world} independent meshes, one per GPU" if world > 1 else "single GPU"},
         "roofline": roofline, "phases": phases,
         "setup_once_per_mesh_ms": {"mesh_create_geometry": 1e3 * t_mesh, "symbolic_pattern": 1e3 * t_sym},
-        "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64, "modes": modes, "clocks": clk.summary(),
+        "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64, "modes": modes, "mass_u": mass_u, "clocks": clk.summary(),
         "gpu_launches": args.steps * 2,
         "batched": batched, "serve": served, "configs": configs,
     }

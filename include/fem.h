@@ -192,6 +192,27 @@ int fem_assemble_tangent(fem_mesh* mesh, const fem_coeff* k, const void* u, int 
 int fem_assemble_all(fem_mesh* mesh, const fem_coeff* k, const void* u, int prec,
                      void* vM, void* vK, void* vT, void* stream);
 
+/* u-dependent mass and its Newton term (Section 2 with a coefficient
+ * m = m(u_h) in the mass; Section 5, where the Jacobian of the implicit
+ * Euler residual holds  M(u) + (mass tensor) o_2 (u - u^s);  Section 5.1,
+ * the mass tensor  M_ijk = int m'(u_h) phi_i phi_j phi_k):
+ *   d_vMu <- M(u)_ij = int m(u_h) phi_j phi_i,
+ *   d_vMt <- sum_j M_ijk (u - u^s)_j = int m'(u_h) (u - u^s)_h phi_k phi_i,
+ * both symmetric, on the mesh's CSR pattern, each the product of the mass
+ * basis matrix Q_M with new X (w_q |det B_e| m(u_q), resp.
+ * w_q |det B_e| m'(u_q) (u - u^s)_q), then the deterministic CSR sum.
+ * m: a coefficient law as k (FEM_COEFF_*; m' from the same law); the mesh's
+ * constant mass coefficient is not used.  prec: FEM_FP64 or FEM_FP32 (SIMT
+ * element products; other precisions: FEM_EINVAL).  d_u, d_us: FP64 nodal
+ * values; d_us may be NULL when d_vMt is.  All four pointers are device
+ * pointers (FEM_EINVAL otherwise); outputs FP64 for FEM_FP64 and FP32
+ * otherwise, nnz each, either may be NULL to skip it.  The call reuses the
+ * mesh's element-matrix scratch: matrices formed earlier by
+ * fem_form_elements must be formed again before fem_sum_elements
+ * (FEM_ESTATE otherwise).  Requires fem_symbolic. */
+int fem_assemble_mass_u(fem_mesh* mesh, const fem_coeff* m, const void* d_u, const void* d_us, int prec,
+                        void* d_vMu, void* d_vMt, void* stream);
+
 /* The two phases of fem_assemble_all, which the paper times separately
  * (Section 4.2: formation of the element matrices versus assemblage of the
  * global matrices, the two parts of Algorithm 2).

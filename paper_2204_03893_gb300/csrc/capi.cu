@@ -474,6 +474,34 @@ int fem_assemble_all(fem_mesh* m, const fem_coeff* k, const void* u, int prec, v
     return assemble_t<float>(m, k, u, prec, vM, vK, vT, s);
 }
 
+int fem_assemble_mass_u(fem_mesh* m, const fem_coeff* mk, const void* d_u, const void* d_us, int prec, void* d_vMu,
+                        void* d_vMt, void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    if (prec != FEM_FP64 && prec != FEM_FP32)
+        return fail(FEM_EINVAL, "the u-dependent mass runs FEM_FP64 or FEM_FP32");
+    if (!d_vMu && !d_vMt) return FEM_OK;
+    int rc = check_coeff(mk);
+    if (rc) return rc;
+    if (!d_u) return fail(FEM_EINVAL, "u is NULL");
+    if (d_vMt && !d_us) return fail(FEM_EINVAL, "u^s is NULL");
+    const void* ptrs[4] = {d_u, d_vMt ? d_us : nullptr, d_vMu, d_vMt};
+    for (const void* p : ptrs)
+        if (p && !is_device_ptr(p)) return fail(FEM_EINVAL, "fem_assemble_mass_u takes device pointers only");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t esz = prec == FEM_FP64 ? 8 : 4, nsym = (size_t)m->np * (m->np + 1) / 2;
+    if ((rc = buf_alloc(m->VMK, 2 * esz * (size_t)m->E * nsym, s))) return rc;
+    m->v_prec = -1;   // the scratch no longer holds matrices of fem_form_elements
+    m->v_mask = 0;
+    rc = element_mass_u(*m, to_dev(mk), static_cast<const double*>(d_u), static_cast<const double*>(d_us),
+                        prec == FEM_FP64, m->VMK.ptr, d_vMu != nullptr, d_vMt != nullptr, s);
+    if (rc) return rc;
+    // M(u) from the even, the tensor term from the odd positions
+    if (prec == FEM_FP64)
+        return sum_t<double>(m, static_cast<double*>(d_vMu), static_cast<double*>(d_vMt), nullptr, s);
+    return sum_t<float>(m, static_cast<float*>(d_vMu), static_cast<float*>(d_vMt), nullptr, s);
+}
+
 int fem_form_elements(fem_mesh* m, const fem_coeff* k, const void* d_u, int prec, int which, void* stream) {
     if (!m) return fail(FEM_EINVAL, "NULL mesh");
     if (!valid_prec(prec)) return fail(FEM_EINVAL, "unknown precision");

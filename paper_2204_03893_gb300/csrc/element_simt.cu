@@ -251,6 +251,104 @@ int dispatch(const fem_mesh& m, const CoeffDev& k, const double* u, const T* geo
     return fail(FEM_EINVAL, "element type");
 }
 
+// The u-dependent mass (Section 2 with m = m(u_h)) and the Section 5.1 mass
+// tensor multiplied by z = u - u^s in its second mode, both as products with
+// the mass basis matrix Q_M (Section 4.1; the tensor's Q = Phi (.) Phi (.) Phi
+// contracted with z_e over one factor leaves Q_M with z_q = phi_q . z_e in X):
+//     X_u[q] = w_q b_e m(u_q),   X_t[q] = w_q b_e m'(u_q) z_q,   V = X Q_M,
+// the n_sym distinct entries of each symmetric local matrix, M(u) at the even
+// and the tensor term at the odd positions of the interleaved M/K storage.
+// FP32 values take u through the (hi, lo) split as the other kernels, and z
+// is formed in FP64 before it is rounded.
+template <typename ETy, typename T>
+__global__ void __launch_bounds__(BT) mass_u_kernel(const int* __restrict__ conn, const T* __restrict__ geo,
+                                                    int64_t E, const double* __restrict__ u,
+                                                    const double* __restrict__ us, CoeffDev mk,
+                                                    T* __restrict__ VMK, bool doMu, bool doMt) {
+    constexpr int NP = ETy::NP, NQ = ETy::NQ, NSYM = ETy::NSYM, D = ETy::D;
+    constexpr int TO = type_tab_off(ETy::TYPE);
+    constexpr int PHI = TO, WQ = TO + NQ * NP * (1 + D);
+    const T* Q = Tabs<T>::Q() + q_off(ETy::TYPE);   // Q_M, NQ x NSYM row-major
+    for (int64_t e = (int64_t)blockIdx.x * BT + threadIdx.x; e < E; e += (int64_t)gridDim.x * BT) {
+        const int* ce = conn + e * NP;
+        T du[NP], dz[NP];
+        T u0;
+        if constexpr (sizeof(T) == 8) {
+            u0 = u[ce[0]];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) du[i] = u[ce[i]] - u0;
+        } else {
+            const float2 a = split_f64(u[ce[0]]);
+            u0 = a.x + a.y;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const float2 c = split_f64(u[ce[i]]);
+                du[i] = (c.x - a.x) + (c.y - a.y);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) dz[i] = doMt ? (T)(u[ce[i]] - us[ce[i]]) : T(0);
+        const T b = geo[e];
+        T Xu[NQ], Xt[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            T uq = T(0), zq = T(0);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                uq += Tabs<T>::ref(PHI + q * NP + i) * du[i];
+                zq += Tabs<T>::ref(PHI + q * NP + i) * dz[i];
+            }
+            uq += u0;
+            T dm;
+            const T mq = k_eval<T>(mk, uq, dm);
+            const T lam = Tabs<T>::ref(WQ + q) * b;
+            Xu[q] = lam * mq;
+            Xt[q] = lam * dm * zq;
+        }
+#pragma unroll 1
+        for (int n = 0; n < NSYM; ++n) {
+            T au = T(0), at = T(0);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const T qv = Q[q * NSYM + n];
+                au += Xu[q] * qv;
+                at += Xt[q] * qv;
+            }
+            if (doMu) VMK[2 * (e * NSYM + n)] = au;
+            if (doMt) VMK[2 * (e * NSYM + n) + 1] = at;
+        }
+    }
+}
+
+template <typename T>
+int launch_mass_u(const fem_mesh& m, const CoeffDev& mk, const double* u, const double* us, const T* geo, T* VMK,
+                  bool doMu, bool doMt, cudaStream_t s) {
+    if (m.E <= 0) return FEM_OK;
+    int dev = 0, nsm = 0;
+    FEM_CUDA_TRY(cudaGetDevice(&dev));
+    FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int64_t grid = (m.E + BT - 1) / BT;
+    if (grid > (int64_t)nsm * 16) grid = (int64_t)nsm * 16;
+    cudaGetLastError();   // clear any stale error before the launch check
+    switch (m.type) {
+#define FEM_MASS_U_CASE(TY, DD, PP)                                                                          \
+    case TY:                                                                                             \
+        mass_u_kernel<ET<DD, PP>, T><<<(unsigned)grid, BT, 0, s>>>(m.conn.as<int>(), geo, m.E, u, us, mk, VMK, \
+                                                                    doMu, doMt);                            \
+        break;
+        FEM_MASS_U_CASE(0, 2, 1)
+        FEM_MASS_U_CASE(1, 2, 2)
+        FEM_MASS_U_CASE(2, 2, 3)
+        FEM_MASS_U_CASE(3, 3, 1)
+        FEM_MASS_U_CASE(4, 3, 2)
+        FEM_MASS_U_CASE(5, 3, 3)
+#undef FEM_MASS_U_CASE
+        default: return fail(FEM_EINVAL, "element type");
+    }
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
 std::mutex g_init_mu;
 bool g_init_done[64] = {};
 
@@ -320,6 +418,14 @@ int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const double* u, flo
     int rc = tables_init_simt();
     if (rc) return rc;
     return dispatch<float>(m, k, u, m.geo32.as<float>(), VM, VK, VT, s, e0, e1);
+}
+
+int element_mass_u(const fem_mesh& m, const CoeffDev& mk, const double* u, const double* us, int fp64, void* VMK,
+                   bool doMu, bool doMt, cudaStream_t s) {
+    int rc = tables_init_simt();
+    if (rc) return rc;
+    if (fp64) return launch_mass_u<double>(m, mk, u, us, m.geo64.as<double>(), static_cast<double*>(VMK), doMu, doMt, s);
+    return launch_mass_u<float>(m, mk, u, us, m.geo32.as<float>(), static_cast<float*>(VMK), doMu, doMt, s);
 }
 
 }  // namespace fem

@@ -97,6 +97,10 @@ int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const double* u, flo
 int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
                       cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);
 // The BF16 split-precision product (nparts 2: BF16x3, 3: BF16x6).
+// u-dependent mass and mass-tensor term into the interleaved M/K storage
+// (M(u) at even, the tensor term at odd positions); SIMT, FP64 or FP32.
+int element_mass_u(const fem_mesh& m, const CoeffDev& mk, const double* u, const double* us, int fp64, void* VMK,
+                   bool doMu, bool doMt, cudaStream_t s);
 int element_tc_bf16(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
                     int nparts, cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);
 

@@ -7,7 +7,7 @@ import numpy as np
 import torch
 
 from . import (FEM_BF16X3, FEM_BF16X6, FEM_FP32, FEM_FP64, FEM_MEM_HOST, FEM_REQ_ASSEMBLE, FEM_REQ_REASSEMBLE, FEM_TF32X3, coeff,
-               fem_assemble_all, fem_copy_pattern, fem_get_slot_map, fem_mesh_create, fem_mesh_desc,
+               fem_assemble_all, fem_assemble_mass_u, fem_copy_pattern, fem_get_slot_map, fem_mesh_create, fem_mesh_desc,
                fem_mesh_destroy, fem_mesh_get_info, fem_serve_create, fem_serve_destroy, fem_serve_evict,
                fem_serve_opts, fem_serve_poll, fem_serve_release, fem_serve_stats, fem_serve_submit, fem_symbolic)
 
@@ -70,6 +70,17 @@ class FemMesh:
                 outs[w] = out[w] if out is not None else torch.empty(max(self.nnz, 1), dtype=dt, device="cuda")
         fem_assemble_all(self.h, coeff(kind, params), u, PRECISIONS[prec], outs.get("M"), outs.get("K"),
                          outs.get("T"), self.stream)
+        return {k: v[: self.nnz] for k, v in outs.items()}
+
+    def assemble_mass_u(self, u, us, kind: str, params, prec: str = "fp64", which=("Mu", "Mt")):
+        """M(u) with the mass law (kind, params) and the mass tensor times
+        (u - us), as CUDA tensors {'Mu', 'Mt'} (FP64 or FP32)."""
+        if self.nnz < 0:
+            self.symbolic()
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        outs = {w: torch.empty(max(self.nnz, 1), dtype=dt, device="cuda") for w in ("Mu", "Mt") if w in which}
+        fem_assemble_mass_u(self.h, coeff(kind, params), u, us, PRECISIONS[prec], outs.get("Mu"), outs.get("Mt"),
+                            self.stream)
         return {k: v[: self.nnz] for k, v in outs.items()}
 
     def close(self):
