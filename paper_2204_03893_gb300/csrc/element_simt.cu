@@ -259,7 +259,16 @@ int dispatch(const fem_mesh& m, const CoeffDev& k, const double* u, const T* geo
 // the n_sym distinct entries of each symmetric local matrix, M(u) at the even
 // and the tensor term at the odd positions of the interleaved M/K storage.
 // FP32 values take u through the (hi, lo) split as the other kernels, and z
-// is formed in FP64 before it is rounded.
+// is formed in FP64 before it is rounded.  Where a block's rows fit
+// (BT x (2 n_sym + 1) values, the odd row stride keeps the per-thread rows
+// free of bank conflicts), each thread stores its element's row in shared
+// memory and the block copies its BT consecutive rows out with coalesced
+// stores; otherwise every thread stores its row directly.
+template <typename ETy, typename T>
+__host__ __device__ constexpr bool mass_u_staged() {
+    return BT * (2 * ETy::NSYM + 1) * sizeof(T) <= 48 * 1024;
+}
+
 template <typename ETy, typename T>
 __global__ void __launch_bounds__(BT) mass_u_kernel(const int* __restrict__ conn, const T* __restrict__ geo,
                                                     int64_t E, const double* __restrict__ u,
@@ -268,54 +277,74 @@ __global__ void __launch_bounds__(BT) mass_u_kernel(const int* __restrict__ conn
     constexpr int NP = ETy::NP, NQ = ETy::NQ, NSYM = ETy::NSYM, D = ETy::D;
     constexpr int TO = type_tab_off(ETy::TYPE);
     constexpr int PHI = TO, WQ = TO + NQ * NP * (1 + D);
+    constexpr bool STAGED = mass_u_staged<ETy, T>();
+    constexpr int LDS = 2 * NSYM + 1;
+    extern __shared__ __align__(16) unsigned char mu_smem[];
+    T* stage = reinterpret_cast<T*>(mu_smem);
     const T* Q = Tabs<T>::Q() + q_off(ETy::TYPE);   // Q_M, NQ x NSYM row-major
-    for (int64_t e = (int64_t)blockIdx.x * BT + threadIdx.x; e < E; e += (int64_t)gridDim.x * BT) {
-        const int* ce = conn + e * NP;
-        T du[NP], dz[NP];
-        T u0;
-        if constexpr (sizeof(T) == 8) {
-            u0 = u[ce[0]];
+    for (int64_t e0 = (int64_t)blockIdx.x * BT; e0 < E; e0 += (int64_t)gridDim.x * BT) {   // block-uniform
+        const int64_t e = e0 + threadIdx.x;
+        if (e < E) {
+            const int* ce = conn + e * NP;
+            T du[NP], dz[NP];
+            T u0;
+            if constexpr (sizeof(T) == 8) {
+                u0 = u[ce[0]];
 #pragma unroll
-            for (int i = 0; i < NP; ++i) du[i] = u[ce[i]] - u0;
-        } else {
-            const float2 a = split_f64(u[ce[0]]);
-            u0 = a.x + a.y;
+                for (int i = 0; i < NP; ++i) du[i] = u[ce[i]] - u0;
+            } else {
+                const float2 a = split_f64(u[ce[0]]);
+                u0 = a.x + a.y;
 #pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                const float2 c = split_f64(u[ce[i]]);
-                du[i] = (c.x - a.x) + (c.y - a.y);
+                for (int i = 0; i < NP; ++i) {
+                    const float2 c = split_f64(u[ce[i]]);
+                    du[i] = (c.x - a.x) + (c.y - a.y);
+                }
             }
-        }
 #pragma unroll
-        for (int i = 0; i < NP; ++i) dz[i] = doMt ? (T)(u[ce[i]] - us[ce[i]]) : T(0);
-        const T b = geo[e];
-        T Xu[NQ], Xt[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            T uq = T(0), zq = T(0);
-#pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                uq += Tabs<T>::ref(PHI + q * NP + i) * du[i];
-                zq += Tabs<T>::ref(PHI + q * NP + i) * dz[i];
-            }
-            uq += u0;
-            T dm;
-            const T mq = k_eval<T>(mk, uq, dm);
-            const T lam = Tabs<T>::ref(WQ + q) * b;
-            Xu[q] = lam * mq;
-            Xt[q] = lam * dm * zq;
-        }
-#pragma unroll 1
-        for (int n = 0; n < NSYM; ++n) {
-            T au = T(0), at = T(0);
+            for (int i = 0; i < NP; ++i) dz[i] = doMt ? (T)(u[ce[i]] - us[ce[i]]) : T(0);
+            const T b = geo[e];
+            T Xu[NQ], Xt[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                const T qv = Q[q * NSYM + n];
-                au += Xu[q] * qv;
-                at += Xt[q] * qv;
+                T uq = T(0), zq = T(0);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    uq += Tabs<T>::ref(PHI + q * NP + i) * du[i];
+                    zq += Tabs<T>::ref(PHI + q * NP + i) * dz[i];
+                }
+                uq += u0;
+                T dm;
+                const T mq = k_eval<T>(mk, uq, dm);
+                const T lam = Tabs<T>::ref(WQ + q) * b;
+                Xu[q] = lam * mq;
+                Xt[q] = lam * dm * zq;
             }
-            if (doMu) VMK[2 * (e * NSYM + n)] = au;
-            if (doMt) VMK[2 * (e * NSYM + n) + 1] = at;
+#pragma unroll 1
+            for (int n = 0; n < NSYM; ++n) {
+                T au = T(0), at = T(0);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const T qv = Q[q * NSYM + n];
+                    au += Xu[q] * qv;
+                    at += Xt[q] * qv;
+                }
+                if constexpr (STAGED) {
+                    stage[threadIdx.x * LDS + 2 * n] = au;
+                    stage[threadIdx.x * LDS + 2 * n + 1] = at;
+                } else {
+                    if (doMu) VMK[2 * (e * NSYM + n)] = au;
+                    if (doMt) VMK[2 * (e * NSYM + n) + 1] = at;
+                }
+            }
+        }
+        if constexpr (STAGED) {
+            __syncthreads();
+            const int rows = E - e0 < BT ? (int)(E - e0) : BT;
+            T* g = VMK + 2 * e0 * NSYM;   // the block's rows are consecutive in V
+            for (int i = threadIdx.x; i < rows * 2 * NSYM; i += BT)
+                g[i] = stage[(i / (2 * NSYM)) * LDS + i % (2 * NSYM)];
+            __syncthreads();
         }
     }
 }
@@ -333,8 +362,9 @@ int launch_mass_u(const fem_mesh& m, const CoeffDev& mk, const double* u, const 
     switch (m.type) {
 #define FEM_MASS_U_CASE(TY, DD, PP)                                                                          \
     case TY:                                                                                             \
-        mass_u_kernel<ET<DD, PP>, T><<<(unsigned)grid, BT, 0, s>>>(m.conn.as<int>(), geo, m.E, u, us, mk, VMK, \
-                                                                    doMu, doMt);                            \
+        mass_u_kernel<ET<DD, PP>, T>                                                                     \
+            <<<(unsigned)grid, BT, mass_u_staged<ET<DD, PP>, T>() ? BT * (2 * ET<DD, PP>::NSYM + 1) * sizeof(T) : 0, \
+               s>>>(m.conn.as<int>(), geo, m.E, u, us, mk, VMK, doMu, doMt);                             \
         break;
         FEM_MASS_U_CASE(0, 2, 1)
         FEM_MASS_U_CASE(1, 2, 2)
