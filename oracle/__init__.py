@@ -71,6 +71,8 @@ def lib():
             L.oracle_entries.restype = C.c_int
             L.oracle_assemble_mass_u.argtypes = [C.c_void_p, C.c_int, C.c_int, dp, C.c_int, dp, dp] + [dp] * 4
             L.oracle_assemble_mass_u.restype = C.c_int
+            L.oracle_set_conductivity.argtypes = [C.c_void_p, dp]
+            L.oracle_set_conductivity.restype = None
             _lib = L
     return _lib
 
@@ -137,6 +139,13 @@ class Oracle:
         if h:
             lib().oracle_destroy(h)
             self._h = None
+
+    def set_conductivity(self, c=None):
+        """Constant conductivity tensor c (d x d, SPD): the conductivity
+        becomes k(u) c and A_e = B_e^-1 c B_e^-T (None: identity)."""
+        cc = None if c is None else np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(self.d, self.d))
+        lib().oracle_set_conductivity(self._h, _dp(cc))
+        return self
 
     def nnz(self) -> int:
         return int(lib().oracle_nnz(self._h))

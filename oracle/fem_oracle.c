@@ -290,6 +290,9 @@ typedef struct {
     /* node -> element incidence, ascending element */
     int* inc_ptr;
     int* inc_el;
+    /* constant conductivity tensor c (d x d, SPD; identity unless set):
+     * the conductivity is k(u) c (Section 8, anisotropic conductivity) */
+    double cond[3][3];
 } octx;
 
 void* oracle_create(int d, int p, int n_nodes, int n_elems, const double* coords, const int* conn) {
@@ -301,6 +304,7 @@ void* oracle_create(int d, int p, int n_nodes, int n_elems, const double* coords
     c->d = d; c->p = p; c->np = np; c->n = n_nodes; c->E = n_elems;
     c->X = coords; c->conn = conn;
     c->nnz = -1;
+    for (int a = 0; a < 3; ++a) c->cond[a][a] = 1.0;
     c->inc_ptr = (int*)calloc((size_t)n_nodes + 1, sizeof(int));
     for (long long k = 0; k < (long long)n_elems * np; ++k) c->inc_ptr[conn[k] + 1]++;
     for (int r = 0; r < n_nodes; ++r) c->inc_ptr[r + 1] += c->inc_ptr[r];
@@ -393,7 +397,19 @@ static int make_tab(int d, int p, int deg, otab* t) {
     return 0;
 }
 
-/* det, |det| and A = (B^T B)^-1 = B^-1 B^-T of element e */
+/* Exported: set the constant conductivity tensor (d x d row-major; NULL:
+ * identity). */
+void oracle_set_conductivity(void* h, const double* cd) {
+    octx* c = (octx*)h;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) c->cond[a][b] = (a == b) ? 1.0 : 0.0;
+    if (cd)
+        for (int a = 0; a < c->d; ++a)
+            for (int b = 0; b < c->d; ++b) c->cond[a][b] = cd[a * c->d + b];
+}
+
+/* det, |det| and A = B^-1 c B^-T of element e (c the conductivity tensor;
+ * the identity gives (B^T B)^-1) */
 static double geometry(const octx* c, int e, double A[3][3]) {
     int d = c->d;
     const int* v = c->conn + (long long)e * c->np;
@@ -425,7 +441,8 @@ static double geometry(const octx* c, int e, double A[3][3]) {
     for (int a = 0; a < d; ++a)
         for (int b = 0; b < d; ++b) {
             double s = 0.0;
-            for (int k = 0; k < d; ++k) s += Bi[a][k] * Bi[b][k];
+            for (int k = 0; k < d; ++k)
+                for (int l = 0; l < d; ++l) s += Bi[a][k] * c->cond[k][l] * Bi[b][l];
             A[a][b] = s;
         }
     return det;
