@@ -192,6 +192,18 @@ int fem_assemble_tangent(fem_mesh* mesh, const fem_coeff* k, const void* u, int 
 int fem_assemble_all(fem_mesh* mesh, const fem_coeff* k, const void* u, int prec,
                      void* vM, void* vK, void* vT, void* stream);
 
+/* Anisotropic conductivity (Section 8: with a d x d conductivity c the
+ * element conductivity matrix takes A_e = B_e^-1 c B_e^-T in place of
+ * B_e^-1 B_e^-T).  Sets a constant tensor c for the mesh: the conductivity
+ * becomes k(u) c, in K(u) and in the tangent T(u) (whose entries become
+ * int k'(u_h) phi_j (c grad u_h) . grad phi_i), on every path (single mesh,
+ * ranges, batches, served requests).  c: d x d row-major, symmetric and
+ * positive definite (FEM_EINVAL otherwise; checked on the host), or NULL
+ * for the identity (the isotropic default).  Recomputes the mesh's geometry
+ * cache on `stream` and waits for it; the pattern is kept; element matrices
+ * formed earlier must be formed again before fem_sum_elements. */
+int fem_mesh_set_conductivity(fem_mesh* mesh, const double* c, void* stream);
+
 /* u-dependent mass and its Newton term (Section 2 with a coefficient
  * m = m(u_h) in the mass; Section 5, where the Jacobian of the implicit
  * Euler residual holds  M(u) + (mass tensor) o_2 (u - u^s);  Section 5.1,

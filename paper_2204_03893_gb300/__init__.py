@@ -16,7 +16,7 @@ __all__ = [
     "FemError", "lib", "library_path", "fem_mesh_desc", "fem_coeff", "fem_mesh_info", "fem_csr_pattern",
     "fem_allocator", "fem_mesh_create", "fem_mesh_destroy", "fem_mesh_get_info", "fem_symbolic",
     "fem_get_slot_map", "fem_copy_pattern", "fem_assemble_mass", "fem_assemble_stiffness", "fem_assemble_tangent",
-    "fem_assemble_all", "fem_assemble_mass_u", "fem_reference_tables", "fem_set_allocator", "fem_last_error", "fem_version",
+    "fem_assemble_all", "fem_assemble_mass_u", "fem_mesh_set_conductivity", "fem_reference_tables", "fem_set_allocator", "fem_last_error", "fem_version",
     "fem_device_status", "fem_batch_create", "fem_batch_launch", "fem_batch_get_info", "fem_batch_destroy",
     "fem_batch_opts", "fem_batch_info", "fem_serve_opts", "fem_request", "fem_result", "fem_serve_counters",
     "fem_serve_create", "fem_serve_submit", "fem_serve_poll", "fem_serve_release", "fem_serve_evict",
@@ -123,6 +123,7 @@ _SIGS = {
                                C.c_int),
     "fem_assemble_tangent": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
                              C.c_int),
+    "fem_mesh_set_conductivity": ([C.c_void_p, C.POINTER(C.c_double), C.c_void_p], C.c_int),
     "fem_assemble_mass_u": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                              C.c_void_p, C.c_void_p], C.c_int),
     "fem_assemble_all": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
@@ -270,6 +271,17 @@ def fem_assemble_tangent(mesh: int, k: fem_coeff, u, prec: int, values, stream=N
 def fem_assemble_all(mesh: int, k, u, prec: int, vM, vK, vT, stream=None) -> None:
     _check(lib().fem_assemble_all(mesh, C.byref(k) if k is not None else None, _vp(u), prec, _vp(vM), _vp(vK),
                                   _vp(vT), _stream(stream)))
+
+
+def fem_mesh_set_conductivity(mesh: int, c=None, stream=None) -> None:
+    """Constant anisotropic conductivity tensor c (d x d, symmetric positive
+    definite; None: the identity); recomputes the geometry cache."""
+    if c is None:
+        _check(lib().fem_mesh_set_conductivity(mesh, None, _stream(stream)))
+        return
+    flat = [float(x) for row in c for x in (row if hasattr(row, "__len__") else [row])]
+    arr = (C.c_double * len(flat))(*flat)
+    _check(lib().fem_mesh_set_conductivity(mesh, arr, _stream(stream)))
 
 
 def fem_assemble_mass_u(mesh: int, m, d_u, d_us, prec: int, d_vMu, d_vMt, stream=None) -> None:

@@ -474,6 +474,42 @@ int fem_assemble_all(fem_mesh* m, const fem_coeff* k, const void* u, int prec, v
     return assemble_t<float>(m, k, u, prec, vM, vK, vT, s);
 }
 
+int fem_mesh_set_conductivity(fem_mesh* m, const double* c, void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    const int d = m->d;
+    double cn[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (c) {
+        double amax = 0.0;
+        for (int i = 0; i < d * d; ++i) {
+            if (!std::isfinite(c[i])) return fail(FEM_EINVAL, "non-finite conductivity tensor");
+            amax = std::max(amax, std::fabs(c[i]));
+        }
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) {
+                if (std::fabs(c[a * d + b] - c[b * d + a]) > 1e-12 * amax)
+                    return fail(FEM_EINVAL, "conductivity tensor is not symmetric");
+                cn[a * 3 + b] = c[a * d + b];
+            }
+        // positive definite: a Cholesky factorisation exists
+        double L[3][3] = {};
+        for (int j = 0; j < d; ++j) {
+            double s = cn[j * 3 + j];
+            for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+            if (!(s > 1e-14 * amax)) return fail(FEM_EINVAL, "conductivity tensor is not positive definite");
+            L[j][j] = std::sqrt(s);
+            for (int i = j + 1; i < d; ++i) {
+                double t = cn[i * 3 + j];
+                for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+                L[i][j] = t / L[j][j];
+            }
+        }
+    }
+    for (int i = 0; i < 9; ++i) m->cond[i] = cn[i];
+    m->v_prec = -1;   // formed element matrices used the previous tensor
+    m->v_mask = 0;
+    return geometry_run(*m, static_cast<cudaStream_t>(stream));
+}
+
 int fem_assemble_mass_u(fem_mesh* m, const fem_coeff* mk, const void* d_u, const void* d_us, int prec, void* d_vMu,
                         void* d_vMt, void* stream) {
     if (!m) return fail(FEM_EINVAL, "NULL mesh");

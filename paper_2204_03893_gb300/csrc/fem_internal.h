@@ -54,6 +54,9 @@ struct fem_mesh {
     fem::DevBuf coords, conn;           // FP64 n x d, int32 E x np
     fem::DevBuf geo64, geo32;           // SoA [NGEO][E]: b_e, A_e upper triangle
     int64_t n_flagged = 0;
+    // constant conductivity tensor c (SPD; identity by default), stored
+    // 3 x 3 row-major whatever d (entry (a, b) at 3a + b): A_e = B_e^-1 c B_e^-T
+    double cond[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     // symbolic
     bool have_pattern = false;
     int64_t nnz = -1;

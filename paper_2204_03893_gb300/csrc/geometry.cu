@@ -49,9 +49,26 @@ __device__ __forceinline__ T det_inv(const T B[D][D], T Bi[D][D]) {
     return det;
 }
 
-// A = Bi Bi^T, upper triangle in (a<=b) order
+// the constant conductivity tensor c (3 x 3 row-major, entry (a, b) at
+// 3a + b, whatever d; the identity for an isotropic conductivity)
+struct Cond {
+    double c[9];
+};
+
+// A = Bi c Bi^T (Section 8, anisotropic conductivity: A_e = B_e^-1 c B_e^-T;
+// c = I gives Bi Bi^T), upper triangle in (a<=b) order
 template <int D, typename T>
-__device__ __forceinline__ void make_A(const T Bi[D][D], T* A) {
+__device__ __forceinline__ void make_A(const T Bi[D][D], const Cond& cd, T* A) {
+    T cb[D][D];   // c Bi^T
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            T s = T(0);
+#pragma unroll
+            for (int l = 0; l < D; ++l) s += (T)cd.c[k * 3 + l] * Bi[b][l];
+            cb[k][b] = s;
+        }
     int t = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -59,14 +76,14 @@ __device__ __forceinline__ void make_A(const T Bi[D][D], T* A) {
         for (int b = a; b < D; ++b) {
             T s = T(0);
 #pragma unroll
-            for (int k = 0; k < D; ++k) s += Bi[a][k] * Bi[b][k];
+            for (int k = 0; k < D; ++k) s += Bi[a][k] * cb[k][b];
             A[t++] = s;
         }
 }
 
 template <int D>
 __global__ void geometry_kernel(const double* __restrict__ X, const int* __restrict__ conn, int64_t E, int np,
-                                int64_t n, double* __restrict__ geo64, float* __restrict__ geo32,
+                                int64_t n, double* __restrict__ geo64, float* __restrict__ geo32, Cond cd,
                                 unsigned long long* __restrict__ counters /* [0] bad index, [1] degenerate, [2] flagged */) {
     constexpr int NS = D * (D + 1) / 2;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
@@ -103,7 +120,7 @@ __global__ void geometry_kernel(const double* __restrict__ X, const int* __restr
             continue;
         }
         double A[NS];
-        make_A<D, double>(Bi, A);
+        make_A<D, double>(Bi, cd, A);
         geo64[e] = fabs(det);
 #pragma unroll
         for (int t = 0; t < NS; ++t) geo64[(1 + t) * E + e] = A[t];
@@ -128,7 +145,7 @@ __global__ void geometry_kernel(const double* __restrict__ X, const int* __restr
             for (int t = 0; t < NS; ++t) geo32[(1 + t) * E + e] = (float)A[t];
         } else {
             float Af[NS];
-            make_A<D, float>(Bif, Af);
+            make_A<D, float>(Bif, cd, Af);
             geo32[e] = fabsf(detf);
 #pragma unroll
             for (int t = 0; t < NS; ++t) geo32[(1 + t) * E + e] = Af[t];
@@ -148,6 +165,8 @@ int geometry_run(fem_mesh& m, cudaStream_t s) {
     rc = buf_alloc(cnt, 4 * sizeof(unsigned long long), s);
     if (rc) return rc;
     FEM_CUDA_TRY(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
+    Cond cd;
+    for (int i = 0; i < 9; ++i) cd.c[i] = m.cond[i];
     if (m.E > 0) {
         cudaGetLastError();   // clear any stale error before the launch check
         int threads = 256;
@@ -156,11 +175,11 @@ int geometry_run(fem_mesh& m, cudaStream_t s) {
         if (m.d == 2)
             geometry_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(m.coords.as<double>(), m.conn.as<int>(), m.E, m.np,
                                                                     m.n, m.geo64.as<double>(), m.geo32.as<float>(),
-                                                                    cnt.as<unsigned long long>());
+                                                                    cd, cnt.as<unsigned long long>());
         else
             geometry_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(m.coords.as<double>(), m.conn.as<int>(), m.E, m.np,
                                                                     m.n, m.geo64.as<double>(), m.geo32.as<float>(),
-                                                                    cnt.as<unsigned long long>());
+                                                                    cd, cnt.as<unsigned long long>());
         FEM_CUDA_TRY(cudaGetLastError());
     }
     unsigned long long h[4] = {0, 0, 0, 0};

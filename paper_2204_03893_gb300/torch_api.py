@@ -7,7 +7,7 @@ import numpy as np
 import torch
 
 from . import (FEM_BF16X3, FEM_BF16X6, FEM_FP32, FEM_FP64, FEM_MEM_HOST, FEM_REQ_ASSEMBLE, FEM_REQ_REASSEMBLE, FEM_TF32X3, coeff,
-               fem_assemble_all, fem_assemble_mass_u, fem_copy_pattern, fem_get_slot_map, fem_mesh_create, fem_mesh_desc,
+               fem_assemble_all, fem_assemble_mass_u, fem_copy_pattern, fem_mesh_set_conductivity, fem_get_slot_map, fem_mesh_create, fem_mesh_desc,
                fem_mesh_destroy, fem_mesh_get_info, fem_serve_create, fem_serve_destroy, fem_serve_evict,
                fem_serve_opts, fem_serve_poll, fem_serve_release, fem_serve_stats, fem_serve_submit, fem_symbolic)
 
@@ -71,6 +71,11 @@ class FemMesh:
         fem_assemble_all(self.h, coeff(kind, params), u, PRECISIONS[prec], outs.get("M"), outs.get("K"),
                          outs.get("T"), self.stream)
         return {k: v[: self.nnz] for k, v in outs.items()}
+
+    def set_conductivity(self, c=None):
+        """Constant anisotropic conductivity tensor (d x d SPD; None: identity)."""
+        fem_mesh_set_conductivity(self.h, c, self.stream)
+        return self
 
     def assemble_mass_u(self, u, us, kind: str, params, prec: str = "fp64", which=("Mu", "Mt")):
         """M(u) with the mass law (kind, params) and the mass tensor times
