@@ -266,7 +266,7 @@ int dispatch(const fem_mesh& m, const CoeffDev& k, const double* u, const T* geo
 // stores; otherwise every thread stores its row directly.
 template <typename ETy, typename T>
 __host__ __device__ constexpr bool mass_u_staged() {
-    return BT * (2 * ETy::NSYM + 1) * sizeof(T) <= 48 * 1024;
+    return (BT * (2 * ETy::NSYM + 1) + ETy::NQ * ETy::NSYM) * sizeof(T) <= 48 * 1024;
 }
 
 template <typename ETy, typename T>
@@ -282,6 +282,12 @@ __global__ void __launch_bounds__(BT) mass_u_kernel(const int* __restrict__ conn
     extern __shared__ __align__(16) unsigned char mu_smem[];
     T* stage = reinterpret_cast<T*>(mu_smem);
     const T* Q = Tabs<T>::Q() + q_off(ETy::TYPE);   // Q_M, NQ x NSYM row-major
+    if constexpr (STAGED) {   // Q_M to shared memory, after the staging rows
+        T* sQ = stage + BT * LDS;
+        for (int i = threadIdx.x; i < NQ * NSYM; i += BT) sQ[i] = Q[i];
+        __syncthreads();
+        Q = sQ;
+    }
     for (int64_t e0 = (int64_t)blockIdx.x * BT; e0 < E; e0 += (int64_t)gridDim.x * BT) {   // block-uniform
         const int64_t e = e0 + threadIdx.x;
         if (e < E) {
@@ -363,7 +369,10 @@ int launch_mass_u(const fem_mesh& m, const CoeffDev& mk, const double* u, const 
 #define FEM_MASS_U_CASE(TY, DD, PP)                                                                          \
     case TY:                                                                                             \
         mass_u_kernel<ET<DD, PP>, T>                                                                     \
-            <<<(unsigned)grid, BT, mass_u_staged<ET<DD, PP>, T>() ? BT * (2 * ET<DD, PP>::NSYM + 1) * sizeof(T) : 0, \
+            <<<(unsigned)grid, BT,                                                                         \
+               mass_u_staged<ET<DD, PP>, T>()                                                               \
+                   ? (BT * (2 * ET<DD, PP>::NSYM + 1) + ET<DD, PP>::NQ * ET<DD, PP>::NSYM) * sizeof(T)      \
+                   : 0,                                                                                     \
                s>>>(m.conn.as<int>(), geo, m.E, u, us, mk, VMK, doMu, doMt);                             \
         break;
         FEM_MASS_U_CASE(0, 2, 1)
