@@ -294,8 +294,9 @@ def gemm_flops_per_element(d, p):
 def measure_mass_u(F, torch, fm, wl, us, stream, fp64_peak, steps=20, warmup=3):
     """The u-dependent mass and its Newton term (fem_assemble_mass_u: M(u)
     with m(u) = 1 + u/2 + u^2/4 and the mass tensor times (u - u^s)) on the
-    bench workload, FEM_FP64 and FEM_FP32, timed with CUDA events; each
-    call forms the two Q_M products and sums both into CSR."""
+    bench workload, FEM_FP64, FEM_FP32 (SIMT) and FEM_TF32X3 (tcgen05 tile),
+    timed with CUDA events; each call forms the two Q_M products and sums
+    both into CSR."""
     sh = stream.cuda_stream
     mk = F.coeff("poly", (1.0, 0.5, 0.25))
     E = wl.mesh.n_elems
@@ -303,7 +304,8 @@ def measure_mass_u(F, torch, fm, wl, us, stream, fp64_peak, steps=20, warmup=3):
     nsym = n_p * (n_p + 1) // 2
     n_q = {(2, 1): 3, (2, 2): 6, (2, 3): 12, (3, 1): 4, (3, 2): 11, (3, 3): 24}[(wl.mesh.d, wl.mesh.p)]
     res = {"law": "poly (1.0, 0.5, 0.25)", "elements": E}
-    for name, prec, dt in (("fp64", F.FEM_FP64, torch.float64), ("fp32", F.FEM_FP32, torch.float32)):
+    for name, prec, dt in (("fp64", F.FEM_FP64, torch.float64), ("fp32", F.FEM_FP32, torch.float32),
+                           ("tf32x3", F.FEM_TF32X3, torch.float32)):
         out = [torch.empty(fm.nnz, dtype=dt, device="cuda") for _ in range(2)]
         for i in range(warmup):
             F.fem_assemble_mass_u(fm.h, mk, us[i % len(us)], us[(i + 1) % len(us)], prec, out[0], out[1], sh)

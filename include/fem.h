@@ -215,7 +215,8 @@ int fem_mesh_set_conductivity(fem_mesh* mesh, const double* c, void* stream);
  * w_q |det B_e| m'(u_q) (u - u^s)_q), then the deterministic CSR sum.
  * m: a coefficient law as k (FEM_COEFF_*; m' from the same law); the mesh's
  * constant mass coefficient is not used.  prec: FEM_FP64 or FEM_FP32 (SIMT
- * element products; other precisions: FEM_EINVAL).  d_u, d_us: FP64 nodal
+ * element products) or FEM_TF32X3 (tcgen05 tile; P3 tetrahedra: FEM_EINVAL);
+ * other precisions: FEM_EINVAL.  d_u, d_us: FP64 nodal
  * values; d_us may be NULL when d_vMt is.  All four pointers are device
  * pointers (FEM_EINVAL otherwise); outputs FP64 for FEM_FP64 and FP32
  * otherwise, nnz each, either may be NULL to skip it.  The call reuses the

@@ -514,8 +514,8 @@ int fem_assemble_mass_u(fem_mesh* m, const fem_coeff* mk, const void* d_u, const
                         void* d_vMt, void* stream) {
     if (!m) return fail(FEM_EINVAL, "NULL mesh");
     if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
-    if (prec != FEM_FP64 && prec != FEM_FP32)
-        return fail(FEM_EINVAL, "the u-dependent mass runs FEM_FP64 or FEM_FP32");
+    if (prec != FEM_FP64 && prec != FEM_FP32 && prec != FEM_TF32X3)
+        return fail(FEM_EINVAL, "the u-dependent mass runs FEM_FP64, FEM_FP32 or FEM_TF32X3");
     if (!d_vMu && !d_vMt) return FEM_OK;
     int rc = check_coeff(mk);
     if (rc) return rc;
@@ -529,8 +529,11 @@ int fem_assemble_mass_u(fem_mesh* m, const fem_coeff* mk, const void* d_u, const
     if ((rc = buf_alloc(m->VMK, 2 * esz * (size_t)m->E * nsym, s))) return rc;
     m->v_prec = -1;   // the scratch no longer holds matrices of fem_form_elements
     m->v_mask = 0;
-    rc = element_mass_u(*m, to_dev(mk), static_cast<const double*>(d_u), static_cast<const double*>(d_us),
-                        prec == FEM_FP64, m->VMK.ptr, d_vMu != nullptr, d_vMt != nullptr, s);
+    rc = prec == FEM_TF32X3
+             ? element_mass_u_tc(*m, to_dev(mk), static_cast<const double*>(d_u), static_cast<const double*>(d_us),
+                                 m->VMK.as<float>(), d_vMu != nullptr, d_vMt != nullptr, s)
+             : element_mass_u(*m, to_dev(mk), static_cast<const double*>(d_u), static_cast<const double*>(d_us),
+                              prec == FEM_FP64, m->VMK.ptr, d_vMu != nullptr, d_vMt != nullptr, s);
     if (rc) return rc;
     // M(u) from the even, the tensor term from the odd positions
     if (prec == FEM_FP64)

@@ -1122,6 +1122,146 @@ __global__ void __launch_bounds__(CT, 2) batch_tc_chunked_kernel(const BatchItem
     if (warp == 0) tc::tmem_dealloc(tmem, L::ALLOC);
 }
 
+// ------------------------------------------------ u-dependent mass, TF32x3
+// M(u) and the mass tensor times z = u - u^s (Sections 2, 5, 5.1) as two
+// products with Q_M: the packed row [X_u | X_t] with X_u[q] = w_q b_e m(u_q)
+// and X_t[q] = w_q b_e m'(u_q) z_q feeds the tile layout with the K product
+// replaced by the second Q_M product and no T, so the MMA issue and the
+// interleaved M/K epilogue of the tile kernel serve unchanged.
+template <typename ETy>
+struct MUET {
+    static constexpr int D = ETy::D, P = ETy::P, NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS, NSYM = ETy::NSYM;
+    static constexpr int NT = 0, KM = NQ, KK = NQ, KT = 0, TYPE = ETy::TYPE, NGEO = ETy::NGEO;
+};
+
+// its fit: the interleaved epilogue reads W columns per step (8, 16 or 32,
+// as epilogue_mk_bulk chooses them), which must stay inside each product's
+// columns and the allocation; both products' X columns are covered by their
+// slices; X tile, then the epilogue blocks, in the X region
+template <typename ETy>
+struct MuL {
+    using L = TcL<MUET<ETy>>;
+    static constexpr int NQ = ETy::NQ, NSYM = ETy::NSYM;
+    static constexpr int W = NSYM <= 8 ? 8 : NSYM <= 16 ? 16 : 32;
+    static constexpr int XREG = L::XEND > TILE * 2 * NSYM * 4 ? L::XEND : TILE * 2 * NSYM * 4;
+    static constexpr int SMEM = L::QEND + XREG;
+    static constexpr bool FITS = L::NMp <= 256 && L::ALLOC <= 512 && SMEM <= SMEM_MAX &&
+                                 L::QEND <= IMG_SLOT_FLOATS * 4 && L::COLM + ru(NSYM, W) <= L::COLK &&
+                                 L::COLK + ru(NSYM, W) <= L::ALLOC && L::OFF_M == 0 && L::SM0 == 0 &&
+                                 L::NSM * 8 >= NQ && L::OFF_K == NQ && L::SK0 * 8 <= NQ &&
+                                 (L::SK0 + L::NSK) * 8 >= 2 * NQ && L::XEND == 2 * TILE * L::KTOTp * 4;
+};
+
+__device__ float g_tcimg_mu[6 * IMG_SLOT_FLOATS];
+
+template <typename ETy>
+__global__ void __launch_bounds__(TILE) mass_u_tc_kernel(const int* __restrict__ conn, const float* __restrict__ geo,
+                                                         int64_t E, const double* __restrict__ u,
+                                                         const double* __restrict__ us, CoeffDev mk,
+                                                         float* __restrict__ VMK, bool doMu, bool doMt,
+                                                         const float* __restrict__ img, int* __restrict__ err) {
+    using L = TcL<MUET<ETy>>;
+    constexpr int NP = ETy::NP, NQ = ETy::NQ, D = ETy::D;
+    constexpr int TO = type_tab_off(ETy::TYPE);
+    constexpr int PHI = TO, WQ = TO + NQ * NP * (1 + D);
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* sQ = smem;
+    unsigned char* sX = smem + L::QEND;
+    {   // resident Q_M images
+        const int4* src = reinterpret_cast<const int4*>(img);
+        int4* dst = reinterpret_cast<int4*>(sQ);
+        for (int i = tid; i < L::QEND / 16; i += TILE) dst[i] = src[i];
+    }
+    const uint32_t mb = tc::smem_u32(&mbar);
+    if (tid == 0) {
+        tc::mbar_init(mb, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(&tmem_slot), L::ALLOC);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t sQu = tc::smem_u32(sQ), sXu = tc::smem_u32(sX);
+    float* stage = reinterpret_cast<float*>(sX);   // epilogue blocks (the X tile is consumed by then)
+    uint32_t phase = 0;
+    bool timed_out = false;
+    const int64_t ntiles = (E + TILE - 1) / TILE;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t e = tile * TILE + tid;
+        float x[L::KTOTp];
+#pragma unroll
+        for (int i = 0; i < L::KTOTp; ++i) x[i] = 0.f;
+        if (e < E) {
+            const int* ce = conn + e * NP;
+            double uv[NP];
+            float du[NP], dz[NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) uv[i] = __ldg(u + __ldg(ce + i));
+            const float2 a = split_f64(uv[0]);
+            const float u0 = a.x + a.y;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const float2 c = split_f64(uv[i]);
+                du[i] = (c.x - a.x) + (c.y - a.y);
+                dz[i] = doMt ? (float)(uv[i] - __ldg(us + __ldg(ce + i))) : 0.f;
+            }
+            const float b = __ldg(geo + e);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                float uq = 0.f, zq = 0.f;
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    uq = fmaf(c_tcref[PHI + q * NP + i], du[i], uq);
+                    zq = fmaf(c_tcref[PHI + q * NP + i], dz[i], zq);
+                }
+                uq += u0;
+                float dm;
+                const float mq = k_eval<float>(mk, uq, dm);
+                const float lam = c_tcref[WQ + q] * b;
+                x[q] = lam * mq;
+                x[NQ + q] = lam * dm * zq;
+            }
+        }
+        store_row<L::KTOTp>(sX + L::XH, sX + L::XL, x, tid);
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            issue_tile<L>(tmem, sXu, sQu, true, true, false);
+            tc::mma_commit(mb);
+        }
+        uint32_t ok = 1;
+        if (tid == 0) ok = tc::mbar_wait_bounded(mb, phase, WAIT_LIMIT);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        tc::fence_after_sync();
+        const int64_t row0 = tile * TILE + warp * 32;
+        epilogue_tile<MUET<ETy>, MuL<ETy>::XREG, 32>(tmem, L::COLM, L::COLK, L::COLT, stage, VMK, nullptr, doMu, doMt,
+                                                     false, row0, E, warp, lane);
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (timed_out) {
+        if (tid == 0) atomicExch(err, 1);
+        tc::mbar_wait_bounded(mb, phase ^ 1u, WAIT_LIMIT);
+    }
+    if ((tid & 31) == 0) tc::bulk_wait_all();   // V copies of this warp are complete
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, L::ALLOC);
+}
+
 // ------------------------------------------------------ BF16 x3 / x6 tiles
 // The split-precision product in BF16 (Section 4's V = X Q, as the TF32 tile
 // above): X and Q are split into NPART BF16 parts (x = x0 + x1 (+ x2), each
@@ -1389,6 +1529,31 @@ void build_image(std::vector<float>& all, const RefElem& R) {
         put_operand(img, L::QMh, L::QMl, PM.data(), L::NSM * 8, ETy::NSYM, L::NSM * 8);
         put_operand(img, L::QKh, L::QKl, PK.data(), L::NSK * 8, ETy::NSYM, L::NSK * 8);
         put_operand(img, L::QTh, L::QTl, PT.data(), L::NST * 8, ETy::NT, L::NST * 8);
+    }
+    std::copy(img.begin(), img.end(), all.begin() + (size_t)ETy::TYPE * IMG_SLOT_FLOATS);
+}
+
+// Q_M images of the u-dependent mass tile: the M product over the X_u
+// columns, the second product over the X_t columns (both Q_M; zero rows
+// at the neighbours' columns, as in build_image)
+template <typename ETy>
+void build_image_mu(std::vector<float>& all, const RefElem& R) {
+    using L = TcL<MUET<ETy>>;
+    std::vector<float> img(IMG_SLOT_FLOATS, 0.f);
+    if constexpr (MuL<ETy>::FITS) {
+        auto slices = [](const std::vector<double>& Q, int K, int N, int off, int s0, int ns) {
+            std::vector<double> P((size_t)ns * 8 * N, 0.0);
+            for (int kk = 0; kk < ns * 8; ++kk) {
+                const int own = s0 * 8 + kk - off;
+                if (own >= 0 && own < K)
+                    for (int n = 0; n < N; ++n) P[(size_t)kk * N + n] = Q[(size_t)own * N + n];
+            }
+            return P;
+        };
+        const auto PU = slices(R.QM, ETy::NQ, ETy::NSYM, L::OFF_M, L::SM0, L::NSM);
+        const auto PT = slices(R.QM, ETy::NQ, ETy::NSYM, L::OFF_K, L::SK0, L::NSK);
+        put_operand(img, L::QMh, L::QMl, PU.data(), L::NSM * 8, ETy::NSYM, L::NSM * 8);
+        put_operand(img, L::QKh, L::QKl, PT.data(), L::NSK * 8, ETy::NSYM, L::NSK * 8);
     }
     std::copy(img.begin(), img.end(), all.begin() + (size_t)ETy::TYPE * IMG_SLOT_FLOATS);
 }
@@ -1666,6 +1831,20 @@ int tables_init_tc() {
     FEM_CUDA_TRY(cudaMemcpyToSymbol(c_tcref, ref.data(), sizeof(float) * TAB_TOTAL));
     FEM_CUDA_TRY(cudaMemcpyToSymbol(g_tcimg, img.data(), sizeof(float) * img.size()));
     {
+        std::vector<float> mimg((size_t)6 * IMG_SLOT_FLOATS, 0.f);
+        for (int t = 0; t < 5; ++t) {
+            const RefElem* R = refelem_for_type(t);
+            switch (t) {
+                case 0: build_image_mu<ET<2, 1>>(mimg, *R); break;
+                case 1: build_image_mu<ET<2, 2>>(mimg, *R); break;
+                case 2: build_image_mu<ET<2, 3>>(mimg, *R); break;
+                case 3: build_image_mu<ET<3, 1>>(mimg, *R); break;
+                case 4: build_image_mu<ET<3, 2>>(mimg, *R); break;
+            }
+        }
+        FEM_CUDA_TRY(cudaMemcpyToSymbol(g_tcimg_mu, mimg.data(), sizeof(float) * mimg.size()));
+    }
+    {
         std::vector<unsigned char> bimg((size_t)2 * 6 * BF_IMG_SLOT, 0);
         for (int t = 0; t < 6; ++t) {
             const RefElem* R = refelem_for_type(t);
@@ -1891,6 +2070,79 @@ int dispatch_bf(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM
         case 5: return launch_bf<ET<3, 3>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
     }
     return fail(FEM_EINVAL, "element type");
+}
+
+template <typename ETy>
+int launch_mu(const fem_mesh& m, const CoeffDev& mk, const double* u, const double* us, float* VMK, bool doMu,
+              bool doMt, cudaStream_t s) {
+    using L = TcL<MUET<ETy>>;
+    if constexpr (!MuL<ETy>::FITS) {
+        return fail(FEM_EINVAL, "the TF32x3 u-dependent mass is not available for this element type");
+    } else {
+        const int64_t E = m.E;
+        if (E <= 0) return FEM_OK;
+        auto kern = mass_u_tc_kernel<ETy>;
+        static std::atomic<int> have[64];
+        static LaunchShape cache[64];
+        static std::mutex mu;
+        LaunchShape sh;
+        int rc = cached_shape(have, cache, mu, [&](int dev, LaunchShape& o) -> int {
+            int optin = 0, occ = 0;
+            FEM_CUDA_TRY(cudaDeviceGetAttribute(&o.nsm, cudaDevAttrMultiProcessorCount, dev));
+            FEM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            cudaFuncAttributes fa;
+            FEM_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+            const int dyn_max = optin - (int)fa.sharedSizeBytes;
+            int smem = MuL<ETy>::SMEM;
+            if (smem > dyn_max) return fail(FEM_EINVAL, "u-dependent mass tile does not fit in shared memory");
+            FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                              (int)cudaSharedmemCarveoutMaxShared));
+            FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+            const int occ_max = 512 / L::ALLOC;   // co-resident CTAs must fit their TMEM columns
+            if (occ > occ_max) {
+                int per_sm = 0;
+                FEM_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+                smem = per_sm / (occ_max + 1) + 1;
+                if (smem > dyn_max) smem = dyn_max;
+                FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TILE, smem));
+                if (occ > occ_max) return fail(FEM_ECUDA, "cannot bound CTAs per SM for tensor memory");
+            }
+            if (occ < 1) return fail(FEM_ECUDA, "u-dependent mass tile does not fit on an SM");
+            o.occ = std::max(occ, std::min(occ_max, ctas_per_sm(fa, TILE, smem, dev)));
+            o.smem = smem;
+            void* img = nullptr;
+            FEM_CUDA_TRY(cudaGetSymbolAddress(&img, g_tcimg_mu));
+            o.img = static_cast<const float*>(img) + (size_t)ETy::TYPE * IMG_SLOT_FLOATS;
+            FEM_CUDA_TRY(cudaGetSymbolAddress((void**)&o.err, g_tc_err));
+            return FEM_OK;
+        }, sh);
+        if (rc) return rc;
+        const int64_t ntiles = (E + TILE - 1) / TILE;
+        int64_t grid = (int64_t)sh.nsm * sh.occ;
+        if (grid > ntiles) grid = ntiles;
+        trace_launch("mass_u_tc_kernel", grid, TILE, sh.smem, sh.occ);
+        cudaGetLastError();   // clear any stale error before the launch check
+        kern<<<(unsigned)grid, TILE, sh.smem, s>>>(m.conn.as<int>(), m.geo32.as<float>(), E, u, us, mk, VMK, doMu,
+                                                    doMt, static_cast<const float*>(sh.img), sh.err);
+        FEM_CUDA_TRY(cudaGetLastError());
+        return FEM_OK;
+    }
+}
+
+int element_mass_u_tc(const fem_mesh& m, const CoeffDev& mk, const double* u, const double* us, float* VMK, bool doMu,
+                      bool doMt, cudaStream_t s) {
+    int rc = tables_init_tc();
+    if (rc) return rc;
+    switch (m.type) {
+        case 0: return launch_mu<ET<2, 1>>(m, mk, u, us, VMK, doMu, doMt, s);
+        case 1: return launch_mu<ET<2, 2>>(m, mk, u, us, VMK, doMu, doMt, s);
+        case 2: return launch_mu<ET<2, 3>>(m, mk, u, us, VMK, doMu, doMt, s);
+        case 3: return launch_mu<ET<3, 1>>(m, mk, u, us, VMK, doMu, doMt, s);
+        case 4: return launch_mu<ET<3, 2>>(m, mk, u, us, VMK, doMu, doMt, s);
+    }
+    return fail(FEM_EINVAL, "the TF32x3 u-dependent mass is not available for P3 tetrahedra");
 }
 
 int element_tc_bf16(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,

@@ -104,6 +104,10 @@ int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const double* u, flo
 // (M(u) at even, the tensor term at odd positions); SIMT, FP64 or FP32.
 int element_mass_u(const fem_mesh& m, const CoeffDev& mk, const double* u, const double* us, int fp64, void* VMK,
                    bool doMu, bool doMt, cudaStream_t s);
+// the same products as element_mass_u on tcgen05 (TF32x3), P1-P3
+// triangles and P1-P2 tetrahedra
+int element_mass_u_tc(const fem_mesh& m, const CoeffDev& mk, const double* u, const double* us, float* VMK, bool doMu,
+                      bool doMt, cudaStream_t s);
 int element_tc_bf16(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
                     int nparts, cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);
 

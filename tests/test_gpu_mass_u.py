@@ -2,7 +2,8 @@
 Mt = (mass tensor) o_2 (u - us) (fem_assemble_mass_u) against the oracle,
 through the C ABI.  Bars: FEM_FP64 |gpu - oracle| <= 1e-12 * absum per
 entry (absum: the oracle's sum of the magnitudes of the expanded terms);
-FEM_FP32 relative Frobenius error <= 1e-5 per matrix; repeatable bits."""
+FEM_FP32 relative Frobenius error <= 1e-5 and FEM_TF32X3 (tcgen05 tile,
+P1-P3 triangles, P1-P2 tetrahedra) <= 1e-6 per matrix; repeatable bits."""
 import numpy as np
 import pytest
 
@@ -50,27 +51,38 @@ def test_mass_u_parity(name, law):
     du, dus = (torch.tensor(x, dtype=torch.float64, device="cuda") for x in (u, us))
     g64 = {k: v.cpu().numpy() for k, v in fm.assemble_mass_u(du, dus, kind, params, "fp64").items()}
     g32 = {k: v.double().cpu().numpy() for k, v in fm.assemble_mass_u(du, dus, kind, params, "fp32").items()}
+    if name == "tet_p3":
+        with pytest.raises(F.FemError) as ei:                   # no tensor-core tile for P3 tetrahedra
+            fm.assemble_mass_u(du, dus, kind, params, "tf32x3")
+        assert ei.value.code == F.FEM_EINVAL
+        gtc = None
+    else:
+        gtc = {k: v.double().cpu().numpy() for k, v in fm.assemble_mass_u(du, dus, kind, params, "tf32x3").items()}
     torch.cuda.synchronize()
     F.fem_device_status()
     for k in ("Mu", "Mt"):
         err = np.abs(g64[k] - o[k])
         assert (err <= 1e-12 * o["abs" + k] + 1e-300).all(), (k, (err / (o["abs" + k] + 1e-300)).max())
         assert frob(g32[k], o[k]) <= 1e-5, (k, frob(g32[k], o[k]))
+        if gtc is not None:
+            assert frob(gtc[k], o[k]) <= 1e-6, ("tf32x3", k, frob(gtc[k], o[k]))
 
 
-def test_mass_u_single_output_and_repeatable():
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_mass_u_single_output_and_repeatable(prec):
     m = MESHES["tri_p2"]()
     u, us = fields(m, 70)
     fm = FemMesh.of(m)
     du, dus = (torch.tensor(x, dtype=torch.float64, device="cuda") for x in (u, us))
-    both = {k: v.clone() for k, v in fm.assemble_mass_u(du, dus, "poly", (1.0, 0.5), "fp32").items()}
-    only = fm.assemble_mass_u(du, None, "poly", (1.0, 0.5), "fp32", which=("Mu",))
+    both = {k: v.clone() for k, v in fm.assemble_mass_u(du, dus, "poly", (1.0, 0.5), prec).items()}
+    only = fm.assemble_mass_u(du, None, "poly", (1.0, 0.5), prec, which=("Mu",))
     assert torch.equal(only["Mu"], both["Mu"])
     for _ in range(3):
-        again = fm.assemble_mass_u(du, dus, "poly", (1.0, 0.5), "fp32")
+        again = fm.assemble_mass_u(du, dus, "poly", (1.0, 0.5), prec)
         for k in both:
             assert torch.equal(again[k], both[k]), k
     torch.cuda.synchronize()
+    F.fem_device_status()
 
 
 def test_mass_u_errors_and_scratch_state():
@@ -81,8 +93,8 @@ def test_mass_u_errors_and_scratch_state():
     du, dus = (torch.tensor(x, dtype=torch.float64, device="cuda") for x in (u, us))
     out = torch.empty(fm.nnz, dtype=torch.float64, device="cuda")
     k = F.coeff("poly", (1.0, 0.5))
-    with pytest.raises(F.FemError) as ei:                                   # tensor-core precisions
-        F.fem_assemble_mass_u(fm.h, k, du, dus, F.FEM_TF32X3, out, None, None)
+    with pytest.raises(F.FemError) as ei:                                   # BF16 splits
+        F.fem_assemble_mass_u(fm.h, k, du, dus, F.FEM_BF16X3, out, None, None)
     assert ei.value.code == F.FEM_EINVAL
     with pytest.raises(F.FemError) as ei:                                   # Mt without u^s
         F.fem_assemble_mass_u(fm.h, k, du, None, F.FEM_FP64, None, out, None)
