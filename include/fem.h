@@ -192,7 +192,7 @@ int fem_assemble_tangent(fem_mesh* mesh, const fem_coeff* k, const void* u, int 
 int fem_assemble_all(fem_mesh* mesh, const fem_coeff* k, const void* u, int prec,
                      void* vM, void* vK, void* vT, void* stream);
 
-/* Anisotropic conductivity (Section 8: with a d x d conductivity c the
+/* Anisotropic conductivity (Section 7: with a d x d conductivity c the
  * element conductivity matrix takes A_e = B_e^-1 c B_e^-T in place of
  * B_e^-1 B_e^-T).  Sets a constant tensor c for the mesh: the conductivity
  * becomes k(u) c, in K(u) and in the tangent T(u) (whose entries become
@@ -450,8 +450,16 @@ const char* fem_version(void);
  *    part rounded up to 256 bytes) <= FEM_NOALLOC_SCRATCH_BYTES; larger meshes
  *    get FEM_EINVAL with the sizes in the message.
  *  - Set-up: the first call on a device looks up the array's device address
- *    and uploads the reference tables; make that first call before any
- *    stream capture.
+ *    and uploads the reference tables.  With CUDA's default lazy module
+ *    loading, that look-up is when the driver loads the array into the
+ *    device's memory: the first call on each device therefore makes that one
+ *    driver allocation and may synchronise the device.  Make the first call
+ *    before any stream capture and outside latency-critical loops (a warm-up
+ *    call); later calls allocate nothing.
+ *  - Pointers: d_u (when K or T is requested) and every non-NULL output must
+ *    be device (or managed) memory of the current device, and the mesh must
+ *    have been created on the current device; FEM_EINVAL otherwise, before
+ *    any work is enqueued.
  *  - Sharing: all calls use the same array and it keeps the last call's
  *    contents (every entry is rewritten before it is read, nothing needs
  *    clearing); calls whose GPU work overlaps race on it.

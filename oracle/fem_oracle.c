@@ -291,7 +291,7 @@ typedef struct {
     int* inc_ptr;
     int* inc_el;
     /* constant conductivity tensor c (d x d, SPD; identity unless set):
-     * the conductivity is k(u) c (Section 8, anisotropic conductivity) */
+     * the conductivity is k(u) c (Section 7, anisotropic conductivity) */
     double cond[3][3];
 } octx;
 

@@ -55,7 +55,7 @@ struct Cond {
     double c[9];
 };
 
-// A = Bi c Bi^T (Section 8, anisotropic conductivity: A_e = B_e^-1 c B_e^-T;
+// A = Bi c Bi^T (Section 7, anisotropic conductivity: A_e = B_e^-1 c B_e^-T;
 // c = I gives Bi Bi^T), upper triangle in (a<=b) order
 template <int D, typename T>
 __device__ __forceinline__ void make_A(const T Bi[D][D], const Cond& cd, T* A) {

@@ -10,8 +10,13 @@
 // acceptable.  They still pass their own inputs and outputs; the mesh handle,
 // its geometry and its pattern were created earlier by the ordinary calls.
 //
-// The array is part of the library's module: every GPU that loads the
-// library holds it until the process exits.  All calls share it and it keeps
+// The array is part of the library: every GPU that loads the library holds
+// it until the process exits.  The driver loads the array's module into a
+// device's memory when the first call on that device looks up its address
+// (with CUDA's default lazy module loading); that first call therefore makes
+// one driver allocation, which may synchronise the device, and should come
+// before any stream capture and outside latency-critical loops.  Later calls
+// on the device allocate nothing.  All calls share it and it keeps
 // the last call's contents; every entry of V is overwritten before it is
 // read, so nothing has to start at zero.  Calls whose GPU work overlaps (on
 // different streams, or from different threads) race on the array.
@@ -28,6 +33,20 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[FEM_NOALLOC_SCR
 
 std::mutex g_na_mu;
 void* g_na_ptr[64] = {};   // device address of the array, per device (set up once)
+
+// A pointer the caller passes must be device memory of the current device
+// (or managed memory): a host pointer handed to the kernels would fault.
+// cudaPointerGetAttributes only reads the driver's records; it allocates
+// nothing.
+bool on_device(const void* p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
 
 // Host code cannot use the array's name as a device address; fetch the real
 // address once per device, with that device current.
@@ -74,6 +93,13 @@ extern "C" int fem_assemble_all_noalloc(fem_mesh* m, const fem_coeff* k, const d
                                     std::to_string((size_t)FEM_NOALLOC_SCRATCH_BYTES));
     int dev = 0;
     FEM_CUDA_TRY(cudaGetDevice(&dev));
+    if (m->device != dev)
+        return fail(FEM_EINVAL, "fem_assemble_all_noalloc: the mesh lives on device " + std::to_string(m->device) +
+                                    ", the current device is " + std::to_string(dev));
+    const void* ptrs[4] = {(d_vK || d_vT) ? d_u : nullptr, d_vM, d_vK, d_vT};
+    for (const void* p : ptrs)
+        if (p && !on_device(p, dev))
+            return fail(FEM_EINVAL, "fem_assemble_all_noalloc takes device pointers of the current device only");
     unsigned char* base = nullptr;
     int rc = noalloc_setup(dev, &base);
     if (rc) return rc;

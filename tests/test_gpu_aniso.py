@@ -1,5 +1,5 @@
 """GPU parity with an anisotropic conductivity tensor (fem_mesh_set_conductivity,
-Section 8: A_e = B_e^-1 c B_e^-T, conductivity k(u) c) against the oracle
+Section 7: A_e = B_e^-1 c B_e^-T, conductivity k(u) c) against the oracle
 with the same tensor, through the C ABI: FEM_FP64 within 1e-12 * absum per
 entry, FEM_TF32X3 / FEM_BF16X6 within 1e-6 relative Frobenius; resetting
 to the identity restores the isotropic bits; batches read the same cache."""

@@ -1,4 +1,4 @@
-"""Pins of the oracle's anisotropic conductivity (Section 8: a d x d
+"""Pins of the oracle's anisotropic conductivity (Section 7: a d x d
 conductivity c gives A_e = B_e^-1 c B_e^-T; here the conductivity is
 k(u) c with c constant and SPD), against the mathematics: c = I is the
 isotropic oracle, c = a I scales K and T by a, a rotation of the mesh with

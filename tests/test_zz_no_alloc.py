@@ -1,13 +1,16 @@
 """The FP64 reassembly entry point that allocates no device memory.
 
-Callers that must not allocate device memory while they run (a framework
-that owns the whole device pool, a latency-critical loop in which a driver
-allocation would stall) use fem_assemble_all_noalloc: its scratch lives in a
-fixed array inside the library.  This test checks, through the C ABI, that
+Some callers cannot allocate device memory while they run: a framework that
+owns the whole device pool and hands out fixed budgets, or a latency-critical
+solver loop in which a driver allocation (which can synchronise the device)
+would stall.  fem_assemble_all_noalloc serves them: its scratch lives in a
+fixed array inside the library.  These tests check, through the C ABI, that
 two calls in a row give the same CSR values as the ordinary entry point
-fem_assemble_all, within the FP64 tolerance the parity tests use, and that a
-mesh too large for the fixed array is refused.  The file name makes pytest
-collect it last.
+fem_assemble_all bit for bit (both run the same FP64 element kernel and the
+same fixed-order CSR sum, so any difference is a layout mistake), for all
+three matrices and for each one alone; that no device memory is taken by the
+calls after the first; that host pointers and a mesh too large for the array
+are refused.  The file name makes pytest collect it last.
 """
 import numpy as np
 import pytest
@@ -23,34 +26,63 @@ if not torch.cuda.is_available():
 import paper_2204_03893_gb300 as F  # noqa: E402
 from paper_2204_03893_gb300.torch_api import FemMesh  # noqa: E402
 
-FP64_TOL = 1e-12
-
 
 def _values(fm, which):
     return {k: torch.empty(fm.nnz, dtype=torch.float64, device="cuda") for k in which}
 
 
-@pytest.mark.parametrize("case", ["tri_p2", "tet_p2"])
-def test_noalloc_matches_assemble_all_twice(case):
+def _setup(case):
     wl = mg.workload("tri_p2_1024", scale=41) if case == "tri_p2" else mg.workload("tet_p2_64", scale=5)
     fm = FemMesh.of(wl.mesh)
     fm.symbolic()
     u = torch.tensor(wl.u, dtype=torch.float64, device="cuda")
     k = F.coeff(wl.coeff.kind, wl.coeff.params)
-    ref = _values(fm, "MKT")
-    F.fem_assemble_all(fm.h, k, u, F.FEM_FP64, ref["M"], ref["K"], ref["T"])
+    return fm, u, k
+
+
+@pytest.mark.parametrize("which", ["MKT", "M", "K", "T"])
+@pytest.mark.parametrize("case", ["tri_p2", "tet_p2"])
+def test_noalloc_matches_assemble_all_twice(case, which):
+    fm, u, k = _setup(case)
+    ref = _values(fm, which)
+    F.fem_assemble_all(fm.h, k, u, F.FEM_FP64, ref.get("M"), ref.get("K"), ref.get("T"))
     torch.cuda.synchronize()
-    for _ in range(2):
-        out = _values(fm, "MKT")
-        for v in out.values():
+    u_arg = None if which == "M" else u     # M alone needs no nodal values
+    # the first call on the device loads the library's fixed array (a one-time
+    # driver allocation); the calls after it must take no device memory at all
+    warm = _values(fm, which)
+    F.fem_assemble_all_noalloc(fm.h, k, u_arg, warm.get("M"), warm.get("K"), warm.get("T"))
+    torch.cuda.synchronize()
+    outs = [_values(fm, which) for _ in range(2)]
+    for o in outs:
+        for v in o.values():
             v.fill_(np.nan)
-        F.fem_assemble_all_noalloc(fm.h, k, u, out["M"], out["K"], out["T"])
-        torch.cuda.synchronize()
-        for name in "MKT":
-            scale = ref[name].abs().max().item()
-            err = (out[name] - ref[name]).abs().max().item()
-            assert err <= FP64_TOL * scale, (name, err, scale)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    mesh_bytes0 = F.fem_mesh_get_info(fm.h).device_bytes
+    for o in outs:
+        F.fem_assemble_all_noalloc(fm.h, k, u_arg, o.get("M"), o.get("K"), o.get("T"))
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert F.fem_mesh_get_info(fm.h).device_bytes == mesh_bytes0
+    for o in outs:
+        for name in which:
+            assert torch.equal(o[name], ref[name]), name
     F.fem_device_status()
+
+
+def test_noalloc_refuses_host_pointers():
+    fm, u, k = _setup("tri_p2")
+    out = _values(fm, "MKT")
+    host = np.zeros(fm.nnz, dtype=np.float64)
+    with pytest.raises(F.FemError) as ei:
+        F.fem_assemble_all_noalloc(fm.h, k, u, host, out["K"], out["T"])
+    assert ei.value.code == F.FEM_EINVAL
+    u_host = u.cpu().numpy()
+    with pytest.raises(F.FemError) as ei:
+        F.fem_assemble_all_noalloc(fm.h, k, u_host, out["M"], out["K"], out["T"])
+    assert ei.value.code == F.FEM_EINVAL
+    assert not np.any(host)
 
 
 def test_noalloc_refuses_mesh_beyond_limit():
