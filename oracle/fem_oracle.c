@@ -524,7 +524,7 @@ static void element(const octx* c, const otab* t, int e, double m, int kkind, co
             double awb = fabs(wb);
             for (int i = 0; i < np; ++i)
                 for (int j = 0; j < np; ++j) {
-                    if (aM) aM[i * np + j] += awb * fabs(m * phi[i] * phi[j]);
+                    if (aM) aM[i * np + j] += fabs(wb * m * phi[i] * phi[j]);   /* |term| of Me, same rounding */
                     if (aK) aK[i * np + j] += awb * fabs(kq) * aS[i][j];
                     if (aT) aT[i * np + j] += awb * fabs(dk) * aSu[i] * fabs(phi[j]);
                 }

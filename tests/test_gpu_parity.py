@@ -4,7 +4,9 @@ Bars (per matrix M, K(u), T(u)):
   * pattern (row_ptr, col_idx) and slot map: bit-exact;
   * FEM_FP64: |gpu - oracle| <= 1e-12 * absum per entry, absum = the
     oracle's sum of the magnitudes of the expanded quadrature terms of the
-    slot (entries that cancel are judged against the size of what cancelled);
+    slot (entries that cancel are judged against the size of what cancelled),
+    and |gpu - oracle| <= 1e-12 |oracle| on the entries with
+    |oracle| >= 1e-3 * absum (plain relative error where nothing cancels);
   * FEM_TF32X3: relative Frobenius error <= 1e-6 per matrix;
   * FEM_FP32 (SIMT reference point): relative Frobenius error <= 1e-5;
   * FEM_BF16X6: relative Frobenius error <= 1e-6 (three BF16 parts carry
@@ -24,6 +26,7 @@ import pytest
 
 import meshgen as mg
 import oracle as orc
+from fp64bar import check_fp64
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -34,7 +37,6 @@ if not torch.cuda.is_available():
 import paper_2204_03893_gb300 as F  # noqa: E402
 from paper_2204_03893_gb300.torch_api import PRECISIONS, FemMesh  # noqa: E402
 
-FP64_TOL = 1e-12
 TF32_TOL = 1e-6
 FP32_TOL = 1e-5
 BF16X6_TOL = 1e-6
@@ -108,10 +110,7 @@ def test_fp64_parity_per_entry(name):
     fm = FemMesh.of(wl.mesh)
     g = gpu_assemble(fm, wl, "fp64")
     for k in ("M", "K", "T"):
-        err = np.abs(g[k] - o[k])
-        bound = FP64_TOL * o["abs" + k] + 1e-300
-        worst = (err / bound).max()
-        assert worst <= 1.0, (k, worst)
+        check_fp64(g[k], o[k], o["abs" + k], k)
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -280,7 +279,7 @@ def test_coefficient_laws():
         g = fm.assemble(torch.tensor(uu, device="cuda"), c.kind, c.params, "fp64")
         for k in ("K", "T"):
             gk = g[k].cpu().numpy()
-            assert (np.abs(gk - r[k]) <= FP64_TOL * r["abs" + k] + 1e-300).all(), (c.kind, k)
+            check_fp64(gk, r[k], r["abs" + k], (c.kind, k))
 
 
 @pytest.mark.parametrize("law", [("sin", (2.0, 1.0, 3.0), 1.0, 0.0),
@@ -336,7 +335,7 @@ def test_long_rows_fallback_paths(prec):
     for k in ("M", "K", "T"):
         gk = g[k].double().cpu().numpy()
         if prec == "fp64":
-            assert (np.abs(gk - r[k]) <= FP64_TOL * r["abs" + k] + 1e-300).all(), k
+            check_fp64(gk, r[k], r["abs" + k], k)
         else:
             assert frob(gk, r[k]) <= TF32_TOL, k
 
@@ -412,7 +411,7 @@ def test_tiny_meshes(d, p, n):
         for k in ("M", "K", "T"):
             gk = g[k].double().cpu().numpy()
             if prec == "fp64":
-                assert (np.abs(gk - r[k]) <= FP64_TOL * r["abs" + k] + 1e-300).all(), (prec, k)
+                check_fp64(gk, r[k], r["abs" + k], (prec, k))
             else:
                 assert frob(gk, r[k]) <= tol[prec], (prec, k, frob(gk, r[k]))
     F.fem_device_status()
@@ -491,17 +490,20 @@ def test_full_size_tri_p2_1024_sampled(prec):
     slots = rng.choice(fm.nnz, 3000, replace=False)
     row_of = np.searchsorted(rp, slots, side="right") - 1
     s = orc.Oracle.of(wl.mesh).entries(row_of, ci[slots], wl.u, wl.coeff)
-    tol = FP64_TOL if prec == "fp64" else 2e-6
     for k in ("M", "K", "T"):
-        err = np.abs(g[k][slots] - s[k])
-        assert (err <= tol * s["abs" + k] + 1e-300).all(), (k, (err / s["abs" + k]).max())
+        if prec == "fp64":
+            check_fp64(g[k][slots], s[k], s["abs" + k], k)
+        else:
+            err = np.abs(g[k][slots] - s[k])
+            assert (err <= 2e-6 * s["abs" + k] + 1e-300).all(), (k, (err / s["abs" + k]).max())
 
 
 _TET_FULL = {"tet_p1_128": (128, lambda N: 15 * N**3 + 21 * N**2 + 9 * N + 1),
              "tet_p2_64": (64, lambda N: 230 * N**3 + 138 * N**2 + 24 * N + 1)}
 
 
-@pytest.mark.parametrize("name,prec", [("tet_p1_128", "tf32x3"), ("tet_p2_64", "tf32x3"), ("tet_p2_64", "fp64")])
+@pytest.mark.parametrize("name,prec", [("tet_p1_128", "tf32x3"), ("tet_p1_128", "fp64"), ("tet_p2_64", "tf32x3"),
+                                       ("tet_p2_64", "fp64")])
 def test_full_size_tetrahedra_sweep_sampled(name, prec):
     """12 582 912 P1 / 1 572 864 P2 tetrahedra in the benchmark's launch
     configuration, reassembled with fresh fields on one symbolic pattern
@@ -537,7 +539,9 @@ def test_full_size_tetrahedra_sweep_sampled(name, prec):
     slots = rng.choice(fm.nnz, 2000, replace=False)
     row_of = np.searchsorted(rp, slots, side="right") - 1
     s = orc.Oracle.of(wl.mesh).entries(row_of, ci[slots], fields[-1], wl.coeff)
-    tol = FP64_TOL if prec == "fp64" else 2e-6
     for k in ("M", "K", "T"):
-        err = np.abs(g[k][slots] - s[k])
-        assert (err <= tol * s["abs" + k] + 1e-300).all(), (k, (err / s["abs" + k]).max())
+        if prec == "fp64":
+            check_fp64(g[k][slots], s[k], s["abs" + k], k)
+        else:
+            err = np.abs(g[k][slots] - s[k])
+            assert (err <= 2e-6 * s["abs" + k] + 1e-300).all(), (k, (err / s["abs" + k]).max())
