@@ -408,6 +408,15 @@ int fem_serve_stats(fem_server* s, fem_serve_counters* out);
  * work in flight and frees everything the server holds. */
 int fem_serve_destroy(fem_server* s);
 
+/* The conductivity law alone, in FP64 on the GPU: d_k[i] = k(u_i) and
+ * d_dk[i] = k'(u_i) for i < n, with the very device code the FP64 element
+ * kernels evaluate at the quadrature points (the S of Algorithm 2, whose
+ * entries are k(u_h) at the nodes x_q, Section 4.2; k' enters the tangent,
+ * Section 5.2).  The sine law uses a table-driven sin/cos accurate to about
+ * one unit in the last place.  All pointers are device pointers (FEM_EINVAL
+ * otherwise); d_k or d_dk may be NULL to skip it.  Enqueued on `stream`. */
+int fem_law_eval(const fem_coeff* k, const double* d_u, int64_t n, double* d_k, double* d_dk, void* stream);
+
 /* ------------------------------------------------------ reference element */
 /* The library's reference tables for (dim, order, qdeg): quadrature points
  * xq (nq x dim) and weights wq (nq, summing to 1/dim!), basis values phi

@@ -145,6 +145,7 @@ _SIGS = {
     "fem_assemble_all_noalloc": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p], C.c_int),
     "fem_form_elements": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_int, C.c_void_p], C.c_int),
+    "fem_law_eval": ([C.POINTER(fem_coeff), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fem_chunk_plan": ([C.c_void_p, C.c_int, C.c_size_t, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64),
                         C.POINTER(C.c_int64), C.c_void_p], C.c_int),
     "fem_form_elements_range": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_int, C.c_int64,
@@ -308,6 +309,11 @@ def fem_assemble_all_noalloc(mesh: int, k, d_u, d_vM, d_vK, d_vT, stream=None) -
     library array of FEM_NOALLOC_SCRATCH_BYTES); device pointers only."""
     _check(lib().fem_assemble_all_noalloc(mesh, C.byref(k) if k is not None else None, _vp(d_u), _vp(d_vM),
                                           _vp(d_vK), _vp(d_vT), _stream(stream)))
+
+
+def fem_law_eval(k, d_u, n: int, d_k, d_dk, stream=None) -> None:
+    """k(u) and k'(u) of a law at n device values, in FP64 on the GPU."""
+    _check(lib().fem_law_eval(C.byref(k), _vp(d_u), int(n), _vp(d_k), _vp(d_dk), _stream(stream)))
 
 
 def _ptr_array(seq):

@@ -108,13 +108,16 @@ int enqueue(fem_batch* b, cudaStream_t s) {
     return batch_scatter_launch<float>(b->d_scatter.as<BatchItem>(), b->n_scatter, tab, b->scatter_block, s);
 }
 
-// One item per run of block/32 pair groups of 64 contributions (a warp's task).
+// One item per run of block/32 groups of contributions (a warp's task):
+// pair groups of 64 for FP32 values, steps of 256 for FP64 (the FP64 sum adds
+// eight contributions per lane).
 int build_scatter_items(fem_batch* b, int block, cudaStream_t s) {
     std::vector<BatchItem> items;
     const int run = std::max(1, block / 32);
+    const int64_t unit = b->prec == FEM_FP64 ? 256 : 64;
     for (int i = 0; i < b->n; ++i) {
         const fem_mesh* m = b->meshes[i];
-        const int64_t ng = (m->E * m->np * m->np + 63) / 64;
+        const int64_t ng = (m->E * m->np * m->np + unit - 1) / unit;
         for (int64_t f = 0; f < ng; f += run)
             items.push_back(BatchItem{i, m->type, f, (int)std::min<int64_t>(run, ng - f), 0});
     }

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "fem_internal.h"
+#include "law64.cuh"
 #include "refelem.h"
 
 namespace fem {
@@ -45,6 +46,11 @@ struct Tabs<float> {
 };
 
 constexpr int BT = 64;   // elements (threads) per block
+
+// FP64 P1 tables: the mass factor sum_q w_q phi_q[i] phi_q[j] (n_sym values,
+// triangles then tetrahedra) and the sine table of law64.cuh
+__constant__ double c_p1m[6 + 10];
+__device__ double2 g_sincos_tab[SC_TAB];
 
 // nodal values: FP64 as given; the FP32 path splits each gathered value
 // as hi + lo (split_f64) so that the differences u_i - u_0 that carry the
@@ -171,6 +177,255 @@ __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict_
     }
 }
 
+// ------------------------------------------------------- P1 simplices in FP64
+// For P1 the reference basis is the barycentric one, phi_0 = 1 - sum_a xhat_a
+// and phi_a = xhat_a, whose gradients are constant: G = [-1 ... -1; I].  The
+// rows of Q_K and Q_T then no longer depend on the quadrature point, so the
+// products of Algorithm 2 can be summed over q first (Section 4.2 with X
+// contracted over q before the product):
+//     K_e = b_e (sum_q w_q k(u_q)) G A_e G^T,
+//     T_e[i][j] = b_e (G A_e ghat)_i (sum_q w_q k'(u_q) phi_q[j]),
+//     M_e = m b_e sum_q w_q phi_q phi_q^T,
+// with ghat = G^T u_e = (u_1 - u_0, ..., u_d - u_0).  G A G^T needs no
+// multiplications: its (i, j) entry for i, j >= 1 is A[i-1][j-1], its (0, j)
+// entry minus the (j-1)-th column sum of A, its (0, 0) entry the sum of all
+// of A.  This is the same quadrature sum as the general path, regrouped:
+// tetrahedra need ~110 FP64 operations per element (polynomial law) instead
+// of ~780 for the general product, which matters because the FP64 pipe, not
+// HBM, bounds the FP64 path on this part.
+//
+// The element's rows are written through `mk` (2 n_sym values: M at even, K
+// at odd positions) and `tr` (n_p^2 values), which point into shared memory
+// in the single-mesh kernel and into V in the batched one.
+template <int D, int LAW>
+__device__ __forceinline__ void p1_element_fp64(int64_t e, const int* __restrict__ conn, const double* __restrict__ geo,
+                                                int64_t gs, const double* __restrict__ u, const CoeffDev& k,
+                                                double mass, const double2* tab, bool doM, bool doK, bool doT,
+                                                double* mk, double* tr) {
+    constexpr int NP = D + 1, NQ = D == 2 ? 3 : 4, NS = D * (D + 1) / 2;
+    constexpr int TYPE = D == 2 ? 0 : 3;
+    constexpr int PHI = type_tab_off(TYPE), WQ = PHI + NQ * NP * (1 + D);
+    constexpr int M0 = D == 2 ? 0 : 6;   // offset in c_p1m
+    const double b = geo[e];
+    if (doM) {
+        const double mb = mass * b;
+#pragma unroll
+        for (int t = 0; t < NP * (NP + 1) / 2; ++t) mk[2 * t] = mb * c_p1m[M0 + t];
+    }
+    if (!doK && !doT) return;
+    double A[NS];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) A[t] = geo[(1 + t) * gs + e];
+    const int* ce = conn + e * NP;
+    const double u0 = u[ce[0]];
+    double du[NP];
+    du[0] = 0.0;
+#pragma unroll
+    for (int i = 1; i < NP; ++i) du[i] = u[ce[i]] - u0;
+    // sums over the quadrature points: s0 = sum w k(u_q), s1[j] = sum w k'(u_q) phi_q[j]
+    double s0 = 0.0, s1[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) s1[j] = 0.0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double uq = u0;
+#pragma unroll
+        for (int i = 1; i < NP; ++i) uq = fma(c_ref64[PHI + q * NP + i], du[i], uq);
+        double dk;
+        const double kq = law64<LAW>(k, uq, dk, tab);
+        const double w = c_ref64[WQ + q];
+        s0 = fma(w, kq, s0);
+        const double wd = w * dk;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) s1[j] = fma(wd, c_ref64[PHI + q * NP + j], s1[j]);
+    }
+    auto At = [&](int a, int c) {   // A[a][c] from the upper triangle
+        const int lo = a < c ? a : c, hi = a < c ? c : a;
+        return A[lo * D - (lo * (lo - 1)) / 2 + (hi - lo)];
+    };
+    if (doK) {
+        const double bs = b * s0;
+        double cs[D];   // column sums of A
+        double tot = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            double v = At(0, c);
+#pragma unroll
+            for (int a = 1; a < D; ++a) v += At(a, c);
+            cs[c] = v;
+            tot = c == 0 ? v : tot + v;
+        }
+        mk[1] = bs * tot;   // sym(0, 0) = 0
+#pragma unroll
+        for (int j = 1; j < NP; ++j) mk[2 * j + 1] = -(bs * cs[j - 1]);   // sym(0, j) = j
+#pragma unroll
+        for (int i = 1; i < NP; ++i)
+#pragma unroll
+            for (int j = i; j < NP; ++j) mk[2 * sym_index(NP, i, j) + 1] = bs * At(i - 1, j - 1);
+    }
+    if (doT) {
+        double r[D];   // A ghat
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            double v = At(a, 0) * du[1];
+#pragma unroll
+            for (int c = 1; c < D; ++c) v = fma(At(a, c), du[c + 1], v);
+            r[a] = v;
+        }
+        double bt[NP];   // b (G A ghat)
+        double r0 = r[0];
+#pragma unroll
+        for (int a = 1; a < D; ++a) r0 += r[a];
+        bt[0] = -(b * r0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) bt[a + 1] = b * r[a];
+#pragma unroll
+        for (int i = 0; i < NP; ++i)
+#pragma unroll
+            for (int j = 0; j < NP; ++j) tr[i * NP + j] = bt[i] * s1[j];
+    }
+}
+
+constexpr int P1_BT = 128;   // elements (threads) per block of the FP64 P1 kernel
+
+template <int D>
+__host__ __device__ constexpr int p1_ldmk() { return (D + 1) * (D + 2) | 1; }   // 2 n_sym, odd
+template <int D>
+__host__ __device__ constexpr int p1_ldt() { return (D + 1) * (D + 1) | 1; }
+
+template <int D, int LAW>
+__host__ __device__ constexpr size_t p1_smem() {
+    return (LAW == LAW_SIN ? SC_TAB * sizeof(double2) : 0) + sizeof(double) * P1_BT * (p1_ldmk<D>() + p1_ldt<D>());
+}
+
+// One element per thread; each thread builds its element's rows in shared
+// memory (odd row strides: no bank conflicts), then the block copies its
+// P1_BT consecutive rows out with coalesced stores (the rows of consecutive
+// elements are contiguous in V).
+template <int D, int LAW>
+__global__ void __launch_bounds__(P1_BT) element_p1_fp64_kernel(const int* __restrict__ conn,
+                                                                const double* __restrict__ geo, int64_t E, int64_t gs,
+                                                                const double* __restrict__ u, CoeffDev k, double mass,
+                                                                double* __restrict__ VMK, bool doM, bool doK,
+                                                                double* __restrict__ VT) {
+    constexpr int NP = D + 1, NSYM = NP * (NP + 1) / 2, NT = NP * NP;
+    constexpr int LDMK = p1_ldmk<D>(), LDT = p1_ldt<D>();
+    extern __shared__ __align__(16) unsigned char p1_smem_raw[];
+    const double2* tab = reinterpret_cast<const double2*>(p1_smem_raw);
+    double* sMK = reinterpret_cast<double*>(p1_smem_raw + (LAW == LAW_SIN ? SC_TAB * sizeof(double2) : 0));
+    double* sT = sMK + P1_BT * LDMK;
+    if constexpr (LAW == LAW_SIN) {
+        double2* t = reinterpret_cast<double2*>(p1_smem_raw);
+        for (int i = threadIdx.x; i < SC_TAB; i += P1_BT) t[i] = g_sincos_tab[i];
+        __syncthreads();
+    }
+    const bool doT = VT != nullptr;
+    for (int64_t e0 = (int64_t)blockIdx.x * P1_BT; e0 < E; e0 += (int64_t)gridDim.x * P1_BT) {   // block-uniform
+        const int64_t e = e0 + threadIdx.x;
+        if (e < E)
+            p1_element_fp64<D, LAW>(e, conn, geo, gs, u, k, mass, tab, doM, doK, doT, sMK + threadIdx.x * LDMK,
+                                    sT + threadIdx.x * LDT);
+        __syncthreads();
+        const int rows = E - e0 < P1_BT ? (int)(E - e0) : P1_BT;
+        if (doM || doK) {
+            double* g = VMK + 2 * e0 * NSYM;   // the block's rows, contiguous
+            if (doM && doK) {
+                double2* g2 = reinterpret_cast<double2*>(g);
+                for (int i = threadIdx.x; i < rows * NSYM; i += P1_BT) {
+                    const double* r = sMK + (i / NSYM) * LDMK + 2 * (i % NSYM);
+                    g2[i] = make_double2(r[0], r[1]);
+                }
+            } else {
+                const int o = doM ? 0 : 1;
+                for (int i = threadIdx.x; i < rows * NSYM; i += P1_BT)
+                    g[2 * i + o] = sMK[(i / NSYM) * LDMK + 2 * (i % NSYM) + o];
+            }
+        }
+        if (doT) {
+            double* g = VT + e0 * NT;
+            for (int i = threadIdx.x; i < rows * NT; i += P1_BT) g[i] = sT[(i / NT) * LDT + i % NT];
+        }
+        __syncthreads();
+    }
+}
+
+template <int D, int LAW>
+int launch_p1_law(const fem_mesh& m, const CoeffDev& k, const double* u, const double* geo, double* VMK, bool doM,
+                  bool doK, double* VT, cudaStream_t s, int64_t e0, int64_t E) {
+    constexpr size_t smem = p1_smem<D, LAW>();
+    auto kern = element_p1_fp64_kernel<D, LAW>;
+    FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, nsm = 0, per_sm = 0;
+    FEM_CUDA_TRY(cudaGetDevice(&dev));
+    FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P1_BT, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t tiles = (E + P1_BT - 1) / P1_BT;
+    int64_t grid = (int64_t)nsm * per_sm;
+    if (grid > tiles) grid = tiles;
+    constexpr int NP = D + 1;
+    cudaGetLastError();   // clear any stale error before the launch check
+    kern<<<(unsigned)grid, P1_BT, smem, s>>>(m.conn.as<int>() + e0 * NP, geo + e0, E, m.E, u, k, m.m,
+                                              VMK ? VMK + 2 * e0 * (NP * (NP + 1) / 2) : nullptr, doM, doK,
+                                              VT ? VT + e0 * NP * NP : nullptr);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+template <int D>
+int launch_p1_fp64(const fem_mesh& m, const CoeffDev& k, const double* u, double* VM, double* VK, double* VT,
+                   cudaStream_t s, int64_t e0, int64_t e1) {
+    const int64_t E = e1 - e0;
+    if (E <= 0) return FEM_OK;
+    double* VMK = VM ? VM : VK ? VK - 1 : nullptr;
+    const bool doM = VM != nullptr, doK = VK != nullptr;
+    const double* geo = m.geo64.as<double>();
+    const int law = (doK || VT) ? law_code(k) : 0;
+    switch (law) {
+#define FEM_P1_LAW(L) \
+    case L: return launch_p1_law<D, L>(m, k, u, geo, VMK, doM, doK, VT, s, e0, E);
+        FEM_P1_LAW(0) FEM_P1_LAW(1) FEM_P1_LAW(2) FEM_P1_LAW(3) FEM_P1_LAW(4)
+        FEM_P1_LAW(5) FEM_P1_LAW(6) FEM_P1_LAW(7) FEM_P1_LAW(8) FEM_P1_LAW(9)
+#undef FEM_P1_LAW
+    }
+    return fail(FEM_EINVAL, "conductivity law");
+}
+
+// The FP64 law on its own (fem_law_eval): k(u) and k'(u) at n values.
+template <int LAW>
+__global__ void __launch_bounds__(256) law_eval_kernel(CoeffDev k, const double* __restrict__ u, int64_t n,
+                                                       double* __restrict__ kv, double* __restrict__ dkv) {
+    __shared__ double2 tab[SC_TAB];
+    if constexpr (LAW == LAW_SIN) {
+        for (int i = threadIdx.x; i < SC_TAB; i += blockDim.x) tab[i] = g_sincos_tab[i];
+        __syncthreads();
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double dk;
+        const double v = law64<LAW>(k, u[i], dk, tab);
+        if (kv) kv[i] = v;
+        if (dkv) dkv[i] = dk;
+    }
+}
+
+// FP64 P1 element with the law chosen at run time (batched kernel; the sine
+// table is read from global memory there, the values are the same)
+template <int D>
+__device__ __forceinline__ void p1_element_fp64_any(const CoeffDev& k, int64_t e, const int* __restrict__ conn,
+                                                    const double* __restrict__ geo, int64_t gs,
+                                                    const double* __restrict__ u, double mass, bool doM, bool doK,
+                                                    double* mk, double* tr) {
+    const bool doT = tr != nullptr;
+    switch (law_code(k)) {
+#define FEM_P1_ANY(L) \
+    case L: p1_element_fp64<D, L>(e, conn, geo, gs, u, k, mass, g_sincos_tab, doM, doK, doT, mk, tr); break;
+        FEM_P1_ANY(0) FEM_P1_ANY(1) FEM_P1_ANY(2) FEM_P1_ANY(3) FEM_P1_ANY(4)
+        FEM_P1_ANY(5) FEM_P1_ANY(6) FEM_P1_ANY(7) FEM_P1_ANY(8) FEM_P1_ANY(9)
+#undef FEM_P1_ANY
+        default: break;
+    }
+}
+
 // Batched: the work list holds blocks of BT elements of many meshes.
 template <typename T>
 __global__ void __launch_bounds__(BT) batch_simt_kernel(const BatchItem* __restrict__ items, int nitems,
@@ -187,6 +442,20 @@ __global__ void __launch_bounds__(BT) batch_simt_kernel(const BatchItem* __restr
         T* VK = bm.vK ? static_cast<T*>(bm.VK) : nullptr;
         T* VT = bm.vT ? static_cast<T*>(bm.VT) : nullptr;
         const T mass = (T)bm.mass;
+        if constexpr (sizeof(T) == 8) {
+            // FP64 P1: the same regrouped product as the single-mesh kernel
+            // (same bits), rows written straight into V
+            if (w.type == 0 || w.type == 3) {
+                const int nsym = w.type == 0 ? 6 : 10, nt = w.type == 0 ? 9 : 16;
+                double* mk = (VM || VK) ? static_cast<double*>(bm.VM) + 2 * e * nsym : nullptr;
+                double* tr = VT ? VT + e * nt : nullptr;
+                if (w.type == 0)
+                    p1_element_fp64_any<2>(bm.k, e, bm.conn, geo, bm.E, u, mass, VM != nullptr, VK != nullptr, mk, tr);
+                else
+                    p1_element_fp64_any<3>(bm.k, e, bm.conn, geo, bm.E, u, mass, VM != nullptr, VK != nullptr, mk, tr);
+                continue;
+            }
+        }
         switch (w.type) {
 #define FEM_BATCH_SIMT_CASE(TY, DD, PP)                                                                     \
     case TY: {                                                                                          \
@@ -240,6 +509,10 @@ int dispatch(const fem_mesh& m, const CoeffDev& k, const double* u, const T* geo
              T* VT, cudaStream_t s, int64_t e0, int64_t e1) {
     if (e1 < 0) e1 = m.E;
     if (e0 < 0 || e0 > e1 || e1 > m.E) return fail(FEM_EINVAL, "element range out of bounds");
+    if constexpr (sizeof(T) == 8) {
+        if (m.type == 0) return launch_p1_fp64<2>(m, k, u, VM, VK, VT, s, e0, e1);
+        if (m.type == 3) return launch_p1_fp64<3>(m, k, u, VM, VK, VT, s, e0, e1);
+    }
     switch (m.type) {
         case 0: return launch_simt<ET<2, 1>, T>(m, k, u, geo, VM, VK, VT, s, e0, e1);
         case 1: return launch_simt<ET<2, 2>, T>(m, k, u, geo, VM, VK, VT, s, e0, e1);
@@ -414,12 +687,62 @@ int tables_init_simt() {
         std::copy(R->QK.begin(), R->QK.end(), q64.begin() + qo + a);
         std::copy(R->QT.begin(), R->QT.end(), q64.begin() + qo + a + b);
     }
+    // FP64 P1 mass factors sum_q w_q phi_q[i] phi_q[j], i <= j (triangles, then tetrahedra)
+    double p1m[16] = {};
+    for (int t : {0, 3}) {
+        const RefElem* R = refelem_for_type(t);
+        const int np = R->np, o = t == 0 ? 0 : 6;
+        for (int i = 0; i < np; ++i)
+            for (int j = i; j < np; ++j) {
+                double v = 0.0;
+                for (int q = 0; q < R->nq; ++q) v += R->wq[q] * R->phi[q * np + i] * R->phi[q * np + j];
+                p1m[o + sym_index(np, i, j)] = v;
+            }
+    }
+    // sine table of the FP64 laws: (sin, cos)(k pi/128), k = 0..255, from
+    // the first quadrant by symmetry, so that the zeros and ones are exact:
+    // s_j = sin(j pi/128), c_j = sin((64 - j) pi/128) for j < 64 from the
+    // host's long double sine (arguments in [0, pi/2], rounded once), then
+    // quadrant q = k / 64 maps (s_j, c_j) to (c_j, -s_j), (-s_j, -c_j), (-c_j, s_j)
+    std::vector<double2> sct(SC_TAB);
+    const long double pi_l = 3.14159265358979323846264338327950288L;
+    for (int k = 0; k < SC_TAB; ++k) {
+        const int q = k / 64, j = k % 64;
+        const double sj = (double)sinl((long double)j * pi_l / 128.0L);
+        const double cj = (double)sinl((long double)(64 - j) * pi_l / 128.0L);
+        sct[k] = q == 0 ? make_double2(sj, cj) : q == 1 ? make_double2(cj, -sj)
+               : q == 2 ? make_double2(-sj, -cj) : make_double2(-cj, sj);
+    }
+    FEM_CUDA_TRY(cudaMemcpyToSymbol(c_p1m, p1m, sizeof(p1m)));
+    FEM_CUDA_TRY(cudaMemcpyToSymbol(g_sincos_tab, sct.data(), sizeof(double2) * SC_TAB));
     std::vector<float> ref32(ref64.begin(), ref64.end()), q32(q64.begin(), q64.end());
     FEM_CUDA_TRY(cudaMemcpyToSymbol(c_ref64, ref64.data(), sizeof(double) * TAB_TOTAL));
     FEM_CUDA_TRY(cudaMemcpyToSymbol(c_ref32, ref32.data(), sizeof(float) * TAB_TOTAL));
     FEM_CUDA_TRY(cudaMemcpyToSymbol(g_Q64, q64.data(), sizeof(double) * Q_TOTAL));
     FEM_CUDA_TRY(cudaMemcpyToSymbol(g_Q32, q32.data(), sizeof(float) * Q_TOTAL));
     if (dev < 64) g_init_done[dev] = true;
+    return FEM_OK;
+}
+
+int law_eval_fp64(const CoeffDev& k, const double* u, int64_t n, double* kv, double* dkv, cudaStream_t s) {
+    if (n <= 0) return FEM_OK;
+    int rc = tables_init_simt();
+    if (rc) return rc;
+    int dev = 0, nsm = 0;
+    FEM_CUDA_TRY(cudaGetDevice(&dev));
+    FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int64_t grid = (n + 255) / 256;
+    if (grid > (int64_t)nsm * 8) grid = (int64_t)nsm * 8;
+    cudaGetLastError();   // clear any stale error before the launch check
+    switch (law_code(k)) {
+#define FEM_LAW_EVAL(L) \
+    case L: law_eval_kernel<L><<<(unsigned)grid, 256, 0, s>>>(k, u, n, kv, dkv); break;
+        FEM_LAW_EVAL(0) FEM_LAW_EVAL(1) FEM_LAW_EVAL(2) FEM_LAW_EVAL(3) FEM_LAW_EVAL(4)
+        FEM_LAW_EVAL(5) FEM_LAW_EVAL(6) FEM_LAW_EVAL(7) FEM_LAW_EVAL(8) FEM_LAW_EVAL(9)
+#undef FEM_LAW_EVAL
+        default: return fail(FEM_EINVAL, "conductivity law");
+    }
+    FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
 

@@ -230,6 +230,150 @@ __device__ __forceinline__ void segsum_warp(uint32_t k0, uint32_t k1, uint32_t n
     }
 }
 
+// ------------------------------------------------------- FP64 octet sum
+// FP64 values take a different grouping, because FP64 additions, not memory,
+// bound the pair-group sum in FP64 on this part (about 2 FP64 operations per
+// clock and SM: the pair-group scan spends ~10.5 additions per contribution,
+// most of them on scan steps whose result is discarded).  Here a warp step
+// covers 256 consecutive contributions, lane l the eight positions
+// 256k + 8l .. 256k + 8l + 7, added in order inside the lane (a segment that
+// starts and ends inside the lane is complete there); only the piece open at
+// the lane's end takes part in a segmented inclusive scan over the lanes
+// (STEPS strides cover a segment of up to 8 (2^STEPS - 1) + 1 contributions
+// within one step: 1 step for 9, 2 for 25, 3 for 57, 5 for any), and the
+// piece before the lane's first head adds the scanned value of the lane
+// before it.  About 4 additions per contribution (7 in-lane and ~6 scan and
+// carry additions per matrix and 256 contributions, for 2 scan steps).
+//
+// Stores: a slot's total is stored by the lane holding its last
+// contribution: inside the loop when the lane meets the next head, after the
+// scan when the lane's first head closes a slot begun in earlier lanes, or
+// when the position after the lane is a head (or the end).  Positions nc and
+// beyond act as heads; lanes wholly past nc store nothing.
+//
+// Ownership: a warp task covers steps [k0, k1) and writes the slots whose
+// first contribution lies in [256 k0, 256 k1) (and in [s0, s1)), going on
+// past k1 while its last slot is open.  The order of additions for a slot
+// depends only on the positions (eight per lane, the fixed scan tree, steps
+// in ascending order), so the bits are the same for every task shape, slot
+// range and the batched kernel.
+template <int NP, int STEPS>
+__device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t nc, uint32_t s0, uint32_t s1,
+                                             const uint2* __restrict__ head, const uint32_t* __restrict__ contrib,
+                                             const short* __restrict__ sym, const double* __restrict__ VM,
+                                             const double* __restrict__ VK, const double* __restrict__ VT,
+                                             double* __restrict__ vM, double* __restrict__ vK,
+                                             double* __restrict__ vT, int lane) {
+    const uint32_t nwords = (nc + 31) >> 5;
+    auto word = [&](uint32_t w) { return __ldg(head + (w < nwords ? w : nwords - 1)); };
+    // first slot whose first contribution is at or after position p (p a multiple of 256)
+    auto first_slot_from = [&](uint32_t p) -> uint32_t {
+        if (p >= nc) return 0xffffffffu;
+        const uint2 h = word(p >> 5);
+        return h.y + ((h.x & 1u) ? 0u : 1u);
+    };
+    const uint32_t slo = max(first_slot_from(k0 << 8), s0);
+    const uint32_t shi = min(first_slot_from(k1 << 8), s1);
+    double cm = 0.0, ck = 0.0, ct = 0.0;   // running sum carried into the step
+    const int sh = (lane & 3) * 8;
+    // the lane's eight contributor indices of a step (positions past nc: 0)
+    auto indices = [&](uint32_t k, uint32_t* c) {
+        const uint32_t p0 = (k << 8) + 8u * lane;
+        if (p0 + 8 <= nc) {
+            const uint4 a = __ldg(reinterpret_cast<const uint4*>(contrib + p0));
+            const uint4 b = __ldg(reinterpret_cast<const uint4*>(contrib + p0 + 4));
+            c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+            c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) c[i] = p0 + i < nc ? __ldg(contrib + p0 + i) : 0u;
+        }
+    };
+    for (uint32_t k = k0;; ++k) {
+        const uint32_t p0 = (k << 8) + 8u * lane;
+        const bool live = p0 < nc;
+        const uint2 hw = word((k << 3) + (lane >> 2));
+        uint32_t bits = (hw.x >> sh) & 0xffu;
+        if (p0 + 8 > nc) bits |= nc > p0 ? (0xffu << (nc - p0)) & 0xffu : 0xffu;   // positions >= nc: heads
+        // slot of position p0 (the word's slot plus the heads after its first position)
+        const uint32_t slot0 = hw.y + __popc(hw.x & ((2u << sh) - 1u) & ~1u);
+        // the lane's eight contributors and their V entries
+        uint32_t c[8];
+        indices(k, c);
+        Contribution<NP, double> v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (p0 + i < nc) v[i].load(c[i], sym, VM, VK, VT);
+            else v[i].m = v[i].k = v[i].t = 0.0;
+        }
+        auto own = [&](uint32_t sl) { return live && sl >= slo && sl < shi; };
+        // in-lane pass: am = the open piece, pm = the piece before the first head
+        const bool h0 = bits & 1u;
+        double am = v[0].m, ak = v[0].k, at = v[0].t;
+        double pm = 0.0, pk = 0.0, pt = 0.0;
+        bool seen = h0;
+        uint32_t cur = slot0;   // slot of the open piece once a head was seen
+#pragma unroll
+        for (int i = 1; i < 8; ++i) {
+            const bool h = (bits >> i) & 1u;
+            if (h && seen && own(cur)) put3(cur, am, ak, at, vM, vK, vT);   // a slot complete in the lane
+            if (h && !seen) {
+                pm = am;
+                pk = ak;
+                pt = at;
+            }
+            cur += h ? 1u : 0u;   // the first head opens slot0 + 1, each later one the next slot
+            seen = seen || h;
+            am = h ? v[i].m : am + v[i].m;
+            ak = h ? v[i].k : ak + v[i].k;
+            at = h ? v[i].t : at + v[i].t;
+        }
+        // segmented inclusive scan of the open pieces over the lanes
+        const uint32_t lup = __ballot_sync(FULL, seen) & (FULL >> (31 - lane));
+        const int run = lane - (lup ? 31 - __clz(lup) : 0);
+#pragma unroll
+        for (int i = 0; i < STEPS; ++i) {
+            const int d = 1 << i;
+            const double ym = __shfl_up_sync(FULL, am, d);
+            const double yk = __shfl_up_sync(FULL, ak, d);
+            const double yt = __shfl_up_sync(FULL, at, d);
+            if (run >= d) {
+                am = ym + am;
+                ak = yk + ak;
+                at = yt + at;
+            }
+        }
+        if (lup == 0) {   // continues the piece carried from the previous step
+            am = cm + am;
+            ak = ck + ak;
+            at = ct + at;
+        }
+        // the lane's first head closes the slot begun before the lane
+        double qm = __shfl_up_sync(FULL, am, 1), qk = __shfl_up_sync(FULL, ak, 1), qt = __shfl_up_sync(FULL, at, 1);
+        if (lane == 0) {
+            qm = cm;
+            qk = ck;
+            qt = ct;
+        }
+        if (seen && !h0 && own(slot0)) put3(slot0, qm + pm, qk + pk, qt + pt, vM, vK, vT);
+        // the position after the lane starts a slot (or is the end): the open piece is complete
+        const uint32_t nb = __shfl_down_sync(FULL, bits, 1);
+        const bool next_head = lane < 31 ? (nb & 1u) != 0u
+                                         : ((k + 1) << 8) >= nc || (word((k + 1) << 3).x & 1u) != 0u;
+        if (next_head && own(cur)) put3(cur, am, ak, at, vM, vK, vT);
+        cm = __shfl_sync(FULL, am, 31);
+        ck = __shfl_sync(FULL, ak, 31);
+        ct = __shfl_sync(FULL, at, 31);
+        // go on past k1 only while the slot open at the step's end is this warp's
+        if (k + 1 >= k1) {
+            const uint32_t pn = (k + 1) << 8;
+            if (pn >= nc) break;
+            const uint2 hn = word(pn >> 5);
+            if ((hn.x & 1u) || hn.y >= shi || hn.y < slo) break;
+        }
+    }
+}
+
 // Launch shape, measured on GB300: FP32 values run best with registers
 // capped for 5 blocks of 256 threads per SM (tri_p2_1024: 0.390 ms vs 0.434
 // with 6 blocks and 0.398 with 4; the tetrahedral meshes lose 5-20% with 4
@@ -264,6 +408,68 @@ __global__ void __launch_bounds__(256, SegShape<STEPS, T>::MIN_BLOCKS)
     for (uint32_t t = g0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * task; t < g1; t += nw * task)
         segsum_warp<NP, T, STEPS>(t, t + task < g1 ? t + task : g1, nc, s0, s1, head2, contrib, sym, vm_src, vk_src,
                                   vt_src, vM, vK, vT, lane);
+}
+
+// FP64: steps of 256 contributions (eight per lane), warps take tasks of up
+// to TASK8 steps grid-stride
+constexpr uint32_t TASK8 = 8;
+
+template <int NP, int STEPS, int MINB>
+__global__ void __launch_bounds__(256, MINB) segsum8_kernel(const uint2* __restrict__ head,
+                                                      const uint32_t* __restrict__ contrib, uint32_t nc,
+                                                      const int* __restrict__ seg_ptr, uint32_t s0, uint32_t s1,
+                                                      uint32_t task, const double* __restrict__ VM,
+                                                      const double* __restrict__ VK, const double* __restrict__ VT,
+                                                      double* __restrict__ vM, double* __restrict__ vK,
+                                                      double* __restrict__ vT) {
+    __shared__ short sym[NP * NP];
+    fill_sym_table<NP>(sym);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint32_t a = (uint32_t)__ldg(seg_ptr + s0), b = (uint32_t)__ldg(seg_ptr + s1);
+    const uint32_t g0 = a >> 8, g1 = (b + 255) >> 8;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const double* vm_src = vM ? VM : nullptr;
+    const double* vk_src = vK ? VK : nullptr;
+    const double* vt_src = vT ? VT : nullptr;
+    for (uint32_t t = g0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * task; t < g1; t += nw * task)
+        segsum8_warp<NP, STEPS>(t, t + task < g1 ? t + task : g1, nc, s0, s1, head, contrib, sym, vm_src, vk_src,
+                                vt_src, vM, vK, vT, lane);
+}
+
+template <int NP, int STEPS, int MINB>
+int launch_steps8_b(const fem_mesh& m, const double* VM, const double* VK, const double* VT, double* vM, double* vK,
+                    double* vT, cudaStream_t s, int nsm, int64_t s0, int64_t s1) {
+    static int occ = 0;   // blocks per SM (the same on every device of the pool)
+    if (!occ) {
+        int o = 0;
+        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, segsum8_kernel<NP, STEPS, MINB>, 256, 0));
+        occ = o > 0 ? o : 1;
+    }
+    const int64_t nc = m.E * m.np * m.np;
+    const int64_t steps = ((nc + 255) / 256) * (s1 - s0) / (m.nnz > 0 ? m.nnz : 1) + 1;
+    const int64_t warps = (int64_t)nsm * occ * 8;
+    int64_t task = (steps + warps - 1) / warps;
+    if (task > TASK8) task = TASK8;
+    if (task < 1) task = 1;
+    int64_t blocks = ((steps + task - 1) / task + 7) / 8;
+    if (blocks > (int64_t)nsm * occ) blocks = (int64_t)nsm * occ;
+    if (blocks < 1) blocks = 1;
+    cudaGetLastError();   // clear any stale error before the launch check
+    segsum8_kernel<NP, STEPS, MINB><<<(unsigned)blocks, 256, 0, s>>>(
+        m.seg_head.as<uint2>(), reinterpret_cast<const uint32_t*>(m.contrib.as<int>()), (uint32_t)nc,
+        m.seg_ptr.as<int>(), (uint32_t)s0, (uint32_t)s1, (uint32_t)task, VM, VK, VT, vM, vK, vT);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+// Two blocks of 256 per SM (the kernel's ~104 registers); capping registers
+// for three spilled and was no faster (tet_p1_128: 3.08 vs 3.01 ms), nor was
+// prefetching the next step's V lines into L2 (3.47 ms).
+template <int NP, int STEPS>
+int launch_steps8(const fem_mesh& m, const double* VM, const double* VK, const double* VT, double* vM, double* vK,
+                  double* vT, cudaStream_t s, int nsm, int64_t s0, int64_t s1) {
+    return launch_steps8_b<NP, STEPS, 2>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
 }
 
 // offsets of the per-type symmetric-index tables in the batched kernel
@@ -303,7 +509,10 @@ __global__ void __launch_bounds__(512) batch_scatter_kernel(const BatchItem* __r
         const uint4* h2 = reinterpret_cast<const uint4*>(bm.seg_head);
 #define FEM_BATCH_SEG_CASE(NP_)                                                                               \
     case NP_:                                                                                                 \
-        segsum_warp<NP_, T, 5>(k0, k1, nc, 0u, s1, h2, cp, st, VM, VK, VT, vM, vK, vT, lane);                   \
+        if constexpr (sizeof(T) == 8)                                                                         \
+            segsum8_warp<NP_, 5>(k0, k1, nc, 0u, s1, bm.seg_head, cp, st, VM, VK, VT, vM, vK, vT, lane);       \
+        else                                                                                                  \
+            segsum_warp<NP_, T, 5>(k0, k1, nc, 0u, s1, h2, cp, st, VM, VK, VT, vM, vK, vT, lane);               \
         break;
         switch (bm.np) {
             FEM_BATCH_SEG_CASE(3)
@@ -353,6 +562,13 @@ int launch_steps(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM
 template <int NP, typename T>
 int launch_np(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s,
               int nsm, int64_t s0, int64_t s1) {
+    if constexpr (sizeof(T) == 8) {
+        // eight contributions per lane: scan strides for the longest segment
+        if (m.max_seg <= 9) return launch_steps8<NP, 1>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+        if (m.max_seg <= 25) return launch_steps8<NP, 2>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+        if (m.max_seg <= 57) return launch_steps8<NP, 3>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+        return launch_steps8<NP, 5>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+    }
     if (m.max_seg <= 8) return launch_steps<NP, T, 2>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
     if (m.max_seg <= 32) return launch_steps<NP, T, 4>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
     return launch_steps<NP, T, 5>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);

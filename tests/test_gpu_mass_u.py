@@ -62,7 +62,7 @@ def test_mass_u_parity(name, law):
     torch.cuda.synchronize()
     F.fem_device_status()
     for k in ("Mu", "Mt"):
-        check_fp64(g64[k], o[k], o["abs" + k], k)
+        check_fp64(g64[k], o[k], o["abs" + k], k, rel_factor=10.0)
         assert frob(g32[k], o[k]) <= 1e-5, (k, frob(g32[k], o[k]))
         if gtc is not None:
             assert frob(gtc[k], o[k]) <= 1e-6, ("tf32x3", k, frob(gtc[k], o[k]))

@@ -5,8 +5,8 @@ Bars (per matrix M, K(u), T(u)):
   * FEM_FP64: |gpu - oracle| <= 1e-12 * absum per entry, absum = the
     oracle's sum of the magnitudes of the expanded quadrature terms of the
     slot (entries that cancel are judged against the size of what cancelled),
-    and |gpu - oracle| <= 1e-12 |oracle| on the entries with
-    |oracle| >= 1e-3 * absum (plain relative error where nothing cancels);
+    and the plain relative error |gpu - oracle| / |oracle| <= 1e-12 where
+    |oracle| >= 0.1 absum, <= 1e-10 where |oracle| >= 1e-3 absum;
   * FEM_TF32X3: relative Frobenius error <= 1e-6 per matrix;
   * FEM_FP32 (SIMT reference point): relative Frobenius error <= 1e-5;
   * FEM_BF16X6: relative Frobenius error <= 1e-6 (three BF16 parts carry
