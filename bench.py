@@ -1,12 +1,15 @@
 """Benchmark: reassembly of M, K(u) and the Newton tangent T(u) into CSR on
-GB300, elements per second.
+GB300, elements per second, in FP64 (the paper's arithmetic).
 
-One step = one reassembly of all three matrices (element formation V = X Q
-on the tensor cores + the deterministic segmented CSR sum) for a fresh
-nodal field u, with the mesh geometry and the CSR pattern cached (they are
-computed once per mesh and reported separately).  Workload: the unit square
-1024 x 1024 grid of 2 097 152 jittered P2 triangles, 6-point degree-4 rule,
-k(u) = 1 + u^2, u a smooth 8-mode random Fourier field; synthetic, seeded.
+One step = one reassembly of all three matrices through the public call
+fem_assemble_all (element formation V = X Q + the deterministic segmented
+CSR sum) for a fresh nodal field u, with the mesh geometry and the CSR
+pattern cached (computed once per mesh and reported separately).  Workload:
+the unit cube 128^3 grid, each cube split into 6 jittered P1 tetrahedra
+(12 582 912 elements, the largest single-GPU configuration), 4-point
+degree-2 rule, k(u) = 2 + sin(3u), u a smooth 8-mode random Fourier field;
+synthetic, seeded.  The mixed-precision modes (TF32x3, BF16x3, BF16x6, FP32)
+and the other configurations are reported beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N>1) every rank reassembles its own mesh (independent
@@ -32,10 +35,10 @@ sys.path.insert(0, ROOT)
 import meshgen as mg  # noqa: E402
 
 METRIC = "K(u)+M reassembly elements/s, % HBM/TC roofline; served p50/p99 latency"
-WORKLOAD = "tri_p2_1024"
-WORKLOAD_DESC = ("unit square 1024x1024 grid, 2,097,152 P2 triangles (6 dofs/elem, 4,198,401 dofs), "
-                 "jitter 0.2h, 6-point degree-4 rule, u = 8-mode Fourier field, k(u) = 1 + u^2; "
-                 "M, K(u) and tangent T(u) reassembled into CSR (nnz 48,250,881) per step")
+WORKLOAD = "tet_p1_128"
+WORKLOAD_DESC = ("unit cube 128^3 grid, 6 Kuhn tetrahedra per cube: 12,582,912 P1 tetrahedra (2,146,689 dofs), "
+                 "jitter 0.15h, 4-point degree-2 rule, u = 8-mode Fourier field, k(u) = 2 + sin(3u); "
+                 "M, K(u) and tangent T(u) reassembled into CSR (nnz 31,802,497) per step, FP64")
 
 
 def parse():
@@ -44,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="tf32x3", choices=["tf32x3", "fp32", "fp64", "bf16x3", "bf16x6"])
+    ap.add_argument("--prec", default="fp64", choices=["tf32x3", "fp32", "fp64", "bf16x3", "bf16x6"])
     ap.add_argument("--scale", type=int, default=None, help="override grid size N (not a bench line)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["tri_p1_64", "tri_p2_1024", "tet_p1_128", "tet_p2_64", "tet_p3_32"],
@@ -58,7 +61,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream measurement")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--no-configs", action="store_true",
-                    help="skip the sweeps on the other configurations (tri_p1_64, tet_p1_128, tet_p2_64)")
+                    help="skip the sweeps on the other configurations (tri_p1_64, tri_p2_1024, tet_p2_64, tet_p3_32)")
     return ap.parse_args()
 
 
@@ -141,41 +144,73 @@ def kernel_traffic(kernel: str, src: str):
     return d.get("bytes_per_launch")
 
 
-def cpu_baseline_oracle(budget_s: float = 12.0):
-    """The oracle (single-threaded C, Algorithm 1) reassembling M, K, T on a
-    bounded sample of the same recipe: a 256x256-cell P2 triangle mesh."""
-    import oracle as orc
-    wl = mg.workload(WORKLOAD, scale=256)
-    o = orc.Oracle.of(wl.mesh)
-    o.nnz()   # pattern once (not timed: cached like the GPU pattern)
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_rate(o, wl, budget_s, threads=None):
+    """Reassemblies of M, K, T by the oracle for about budget_s seconds
+    (pattern cached, as the GPU pattern is): (elements/s, runs, seconds,
+    threads used)."""
     t0 = time.perf_counter()
-    n = 0
+    n, used = 0, 1
     while True:
-        o.assemble(wl.u, wl.coeff, want_abs=False)
+        if threads is None:
+            o.assemble(wl.u, wl.coeff, want_abs=False)
+        else:
+            _, used = o.assemble_mt(wl.u, wl.coeff, threads=threads)
         n += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": n * wl.mesh.n_elems / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} reassemblies of M,K,T on tri_p2 N=256 ({wl.mesh.n_elems} elements), "
-                      f"pattern cached, {dt:.1f} s single-threaded"}
+    return n * wl.mesh.n_elems / dt, n, dt, used
+
+
+def cpu_baseline_oracle(name: str = WORKLOAD, N: int = 32, budget_s: float = 10.0):
+    """The oracle on a bounded sample of the bench workload's recipe (the
+    same element type, rule, law and field recipe on an N^3 grid): the
+    single-threaded oracle (Algorithm 1, the parity reference) and its
+    multi-core variant (element loop on all host cores, the same ordered CSR
+    sum, the same bits)."""
+    import oracle as orc
+    wl = mg.workload(name, scale=N)
+    o = orc.Oracle.of(wl.mesh)
+    o.nnz()   # pattern once (not timed: cached like the GPU pattern)
+    v1, n1, dt1, _ = _oracle_rate(o, wl, budget_s)
+    vm, nm, dtm, used = _oracle_rate(o, wl, budget_s / 2, threads=0)
+    sample = f"{name} recipe at N={N} ({wl.mesh.n_elems} elements), M+K+T per reassembly, pattern cached"
+    return {"value": v1, "unit": "elements/s", "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": f"{n1} reassemblies of the {sample}, {dt1:.1f} s single-threaded",
+            "multicore": {"value": vm, "unit": "elements/s", "cores": used,
+                          "kind": "oracle element loop on all host cores (OpenMP), same ordered CSR sum, same bits",
+                          "sample": f"{nm} reassemblies of the {sample}, {dtm:.1f} s"}}
 
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
+    """The oracle (the reference for this method, single-threaded C) timed on
+    the host cores for the bench's metric, on a bounded sample of the bench's
+    workload sized so that warmup + steps take about a minute."""
     if rank != 0:
         return 0
     import oracle as orc
-    # size each step so that warmup + steps take about a minute
-    probe = mg.workload(WORKLOAD, scale=16)
+    probe = mg.workload(args.workload, scale=8)
     po = orc.Oracle.of(probe.mesh)
     po.nnz()
     t0 = time.perf_counter()
     po.assemble(probe.u, probe.coeff, want_abs=False)
     rate = probe.mesh.n_elems / max(time.perf_counter() - t0, 1e-6)
     per_step = 60.0 / max(args.steps + args.warmup, 1)
-    N = int(max(4, min(256, (per_step * rate / 2.0) ** 0.5)))
-    wl = mg.workload(WORKLOAD, scale=N)
+    elems_per_cell = probe.mesh.n_elems / 8 ** probe.mesh.d
+    N = int(max(4, min(64, (per_step * rate / elems_per_cell) ** (1.0 / probe.mesh.d))))
+    wl = mg.workload(args.workload, scale=N)
     o = orc.Oracle.of(wl.mesh)
     o.nnz()
     for _ in range(args.warmup):
@@ -188,10 +223,11 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": val, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "sample_N": N,
-                       "sample_elements": wl.mesh.n_elems},
-            "cpu_baseline": {"value": val, "unit": "elements/s", "cores": 1, "kind": "oracle",
-                             "sample": f"tri_p2 N={N} ({wl.mesh.n_elems} elements) per step, pattern cached"},
+            "config": {"workload": args.workload, "desc": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload,
+                       "sample_N": N, "sample_elements": wl.mesh.n_elems},
+            "cpu_baseline": {"value": val, "unit": "elements/s", "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+                             "sample": f"{args.workload} recipe at N={N} ({wl.mesh.n_elems} elements) per step, "
+                                       f"pattern cached"},
             "e2e": {"value": val, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -289,6 +325,85 @@ def gemm_flops_per_element(d, p):
     n_q = {(2, 1): 3, (2, 2): 6, (2, 3): 12, (3, 1): 4, (3, 2): 11, (3, 3): 24}[(d, p)]
     nsym, ns = n_p * (n_p + 1) // 2, d * (d + 1) // 2
     return 2 * (n_q * nsym + n_q * ns * nsym + n_q * d * n_p * n_p)
+
+
+def law_ops(kind: str, n: int):
+    """(FP64 operations, of which fused multiply-adds) of one evaluation of
+    k(u) and k'(u) in the FP64 kernels: Horner of the actual degree for a
+    polynomial with n coefficients; for the sine law the table-driven sin/cos
+    (argument 1, reduction 4, h^2 1, sin h 4, cos h - 1 3, combination 6) and
+    k, k' (3); the piecewise-linear law about 4."""
+    if kind == "poly":
+        return (0, 0) if n <= 1 else (2 * n - 3, 2 * n - 3)
+    if kind == "sin":
+        return 22, 10
+    return 4, 1
+
+
+def fp64_element_ops(d: int, p: int, kind: str, n: int):
+    """(FP64 operations, flops with a fused multiply-add counted as 2) per
+    element of the FP64 element product, counted from the kernel's algorithm.
+    P1 (element_p1_fp64_kernel): M m b_e Qbar (1 + n_sym), du (d), per
+    quadrature point u_q (d FMA), the law, s0 (1 FMA), w k' (1), s1 (n_p
+    FMA); K: b s0 (1), column sums of A (d(d-1) + d-1 adds), n_sym products;
+    T: A ghat (d + d(d-1) FMA), its sum (d-1), b (G A ghat) (n_p), n_p^2
+    products.  P2/P3 (element_simt_kernel): the product V = X Q
+    (gemm_flops_per_element) plus, per point, u_q and ghat (n_p (1+d) FMA),
+    A ghat (d^2 FMA) and the law."""
+    lo, lf = law_ops(kind, n)
+    n_p = (p + 1) * (p + 2) // 2 if d == 2 else (p + 1) * (p + 2) * (p + 3) // 6
+    n_q = {(2, 1): 3, (2, 2): 6, (2, 3): 12, (3, 1): 4, (3, 2): 11, (3, 3): 24}[(d, p)]
+    nsym = n_p * (n_p + 1) // 2
+    if p == 1:
+        ops = (1 + nsym) + d + n_q * (d + lo + 2 + n_p) + (1 + d * (d - 1) + (d - 1) + nsym) \
+            + (d + d * (d - 1) + (d - 1) + n_p + n_p * n_p)
+        fma = n_q * (d + lf + 1 + n_p) + d * (d - 1)
+        return ops, ops + fma
+    gemm = gemm_flops_per_element(d, p)
+    fma = n_q * (n_p * (1 + d) + d * d + lf)
+    ops = gemm // 2 + fma + n_q * lo
+    return ops, gemm + 2 * fma + n_q * (lo - lf)
+
+
+def measure_setup_kernels(F, torch, wl, stream, peak_gbs):
+    """The once-per-mesh phases timed on the device (CUDA events on the
+    stream): the geometry cache (recomputed by fem_mesh_set_conductivity,
+    which runs the geometry kernel alone) and the symbolic phase (all its
+    kernels on a fresh mesh handle; the span includes the host's read-back
+    of nnz in the middle), each with its compulsory bytes."""
+    from paper_2204_03893_gb300.torch_api import FemMesh
+    sh = stream.cuda_stream
+    m = wl.mesh
+    E, n_p, d = m.n_elems, m.conn.shape[1], m.d
+    ns = d * (d + 1) // 2
+    out = {}
+    with torch.cuda.stream(stream):
+        fm = FemMesh.of(m, stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        F.fem_mesh_set_conductivity(fm.h, None, sh)     # warm
+        torch.cuda.synchronize()
+        a.record(stream)
+        F.fem_mesh_set_conductivity(fm.h, None, sh)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        # vertex rows of conn, the vertices' coordinates, both caches written
+        gb = E * (4 * (d + 1) + 8 * d * (d + 1) + 8 * (1 + ns) + 4 * (1 + ns))
+        out["geometry"] = {"ms": ms, "bytes": gb, "GB/s": gb / (ms / 1e3) / 1e9, "frac_hbm": gb / (ms / 1e3) / 1e9 / peak_gbs,
+                           "bytes_per_element": gb / E}
+        a.record(stream)
+        fm.symbolic()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        nc, nnz, n = E * n_p * n_p, fm.nnz, m.n_nodes
+        # conn read; contrib, slot (4 B per element entry), seg_head (8 B per 32),
+        # seg_ptr and col_idx (4 B per slot), row_ptr written once
+        sb = 4 * E * n_p + 8 * nc + nc // 4 + 8 * nnz + 4 * (n + 1)
+        out["symbolic"] = {"ms": ms, "bytes": sb, "GB/s": sb / (ms / 1e3) / 1e9, "frac_hbm": sb / (ms / 1e3) / 1e9 / peak_gbs,
+                           "note": "compulsory bytes (inputs read once, outputs written once); the sort passes move more"}
+        fm.close()
+    return out
 
 
 def measure_mass_u(F, torch, fm, wl, us, stream, fp64_peak, steps=20, warmup=3):
@@ -620,6 +735,7 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
+    peak, peak_kind = measured_peaks()
 
     wl = mg.workload(args.workload, scale=args.scale)
     E = wl.mesh.n_elems
@@ -642,15 +758,8 @@ def run_ours(args, rank, world, local_rank):
         k = F.coeff(wl.coeff.kind, wl.coeff.params)
         which = F.FEM_MAT_M | F.FEM_MAT_K | F.FEM_MAT_T
 
-        def step(i, ev=None):
-            if ev is not None:
-                ev[0].record(stream)
-            F.fem_form_elements(fm.h, k, us[i % len(us)], prec, which, sh)
-            if ev is not None:
-                ev[1].record(stream)
-            F.fem_sum_elements(fm.h, prec, out["M"], out["K"], out["T"], sh)
-            if ev is not None:
-                ev[2].record(stream)
+        def step(i):   # the public call; with device pointers it enqueues the formation and the CSR sum
+            F.fem_assemble_all(fm.h, k, us[i % len(us)], prec, out["M"], out["K"], out["T"], sh)
 
         for i in range(args.warmup):
             step(i)
@@ -665,11 +774,20 @@ def run_ours(args, rank, world, local_rank):
             t_end = torch.cuda.Event(enable_timing=True)
             t_start.record(stream)
             for i in range(args.steps):
-                step(i, evs[i])
+                step(i)
             t_end.record(stream)
             torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
+            if dist:
+                dist.barrier()
+            # the same steps again as their two launches with events between
+            # them: each kernel's duration on its launch stream
+            for i in range(args.steps):
+                evs[i][0].record(stream)
+                F.fem_form_elements(fm.h, k, us[i % len(us)], prec, which, sh)
+                evs[i][1].record(stream)
+                F.fem_sum_elements(fm.h, prec, out["M"], out["K"], out["T"], sh)
+                evs[i][2].record(stream)
+            torch.cuda.synchronize()
         F.fem_device_status(sh)
         total_ms = t_start.elapsed_time(t_end)
         form_ms = [e[0].elapsed_time(e[1]) for e in evs]
@@ -677,13 +795,14 @@ def run_ours(args, rank, world, local_rank):
         total_ms, value = whole_job_rate(total_ms, E, args.steps, dist, "cuda")
         ms_per_step = total_ms / args.steps
 
-        # FP64 plain path on the same workload (one-matrix-at-a-time reference point)
-        fp64 = None
-        modes = None
-        mass_u = None
-        if not args.no_fp64 and args.prec != "fp64":
-            u64 = torch.tensor(wl.u, dtype=torch.float64, device="cuda")
-            o64 = {kk: torch.empty(nnz, dtype=torch.float64, device="cuda") for kk in "MKT"}
+        # the FP64 result of the workload's own field: reference for the modes' errors
+        u64 = torch.tensor(wl.u, dtype=torch.float64, device="cuda")
+        o64 = {kk: torch.empty(nnz, dtype=torch.float64, device="cuda") for kk in "MKT"}
+        F.fem_assemble_all(fm.h, k, u64, F.FEM_FP64, o64["M"], o64["K"], o64["T"], sh)
+        torch.cuda.synchronize()
+        fp64_plain = modes = mass_u = None
+        if not args.no_fp64:
+            # plain FP64, one matrix per call (3 calls, 6 launches) on the same workload
             for _ in range(2):
                 F.fem_assemble_mass(fm.h, F.FEM_FP64, o64["M"], sh)
                 F.fem_assemble_stiffness(fm.h, k, u64, F.FEM_FP64, o64["K"], sh)
@@ -699,12 +818,13 @@ def run_ours(args, rank, world, local_rank):
             b.record(stream)
             torch.cuda.synchronize()
             ms64 = a.elapsed_time(b) / n64
-            fp64 = {"value": E / (ms64 / 1e3), "unit": "elements/s", "ms_per_step": ms64,
-                    "mode": "FEM_FP64 SIMT, one matrix per call (3 calls, 6 launches)"}
-            if not args.no_modes:
-                modes = measure_modes(F, torch, fm, k, us, u64, o64, stream, E)
-                mass_u = measure_mass_u(F, torch, fm, wl, us, stream, measure_fp64_peak(torch, stream))
-            del o64
+            fp64_plain = {"value": E / (ms64 / 1e3), "unit": "elements/s", "ms_per_step": ms64,
+                          "mode": "FEM_FP64, one matrix per call (3 calls, 6 launches)"}
+        fp64_peak = measure_fp64_peak(torch, stream)
+        if not args.no_modes:
+            modes = measure_modes(F, torch, fm, k, us, u64, o64, stream, E)
+            mass_u = measure_mass_u(F, torch, fm, wl, us, stream, fp64_peak)
+        del o64
 
         # end to end through the C ABI with pinned host buffers
         e2e = None
@@ -729,66 +849,94 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return 0
 
-    # roofline of the dominant kernel (algorithmic bytes per launch / mean launch time)
+    # roofline of the dominant kernel: algorithmic bytes (and FP64 flops) per
+    # launch / mean launch time
+    d, p = wl.mesh.d, wl.mesh.p
     n_p = wl.mesh.conn.shape[1]
-    nsym, nt, ngeo = n_p * (n_p + 1) // 2, n_p * n_p, 1 + wl.mesh.d * (wl.mesh.d + 1) // 2
+    nsym, nt, ngeo = n_p * (n_p + 1) // 2, n_p * n_p, 1 + d * (d + 1) // 2
     esz = 8 if args.prec == "fp64" else 4
     n = wl.mesh.n_nodes
+    nc = E * n_p * n_p
     bytes_form = E * (n_p * 4 + ngeo * esz + (2 * nsym + nt) * esz) + n * 8
     # per group of 32 contributions an 8-byte head word; every contribution's
     # 4-byte index and V entries; the CSR values written
-    bytes_sum = (E * n_p * n_p + 31) // 32 * 8 + E * n_p * n_p * 4 + E * (2 * nsym + nt) * esz + 3 * nnz * esz
-    mf, ms = statistics.mean(form_ms), statistics.mean(sum_ms)
+    bytes_sum = (nc + 31) // 32 * 8 + nc * 4 + E * (2 * nsym + nt) * esz + 3 * nnz * esz
+    mf, msum = statistics.mean(form_ms), statistics.mean(sum_ms)
     on_tc = args.prec in ("tf32x3", "bf16x3", "bf16x6")
+    fp64 = args.prec == "fp64"
     form_kernel = ("element_bf_kernel" if args.prec.startswith("bf16") else
-                   "element_tc_chunked_kernel" if (wl.mesh.d, wl.mesh.p) == (3, 3) else
-                   "element_tc_kernel") if on_tc else "element_simt_kernel"
+                   "element_tc_chunked_kernel" if (d, p) == (3, 3) else "element_tc_kernel") if on_tc else \
+        ("element_p1_fp64_kernel" if fp64 and p == 1 else "element_simt_kernel")
+    ops, flops = fp64_element_ops(d, p, wl.coeff.kind, len(wl.coeff.params)) if fp64 else (0, 0)
     kernels = {
         "element_form": {"kernel": form_kernel, "src": "element_tc.cu" if on_tc else "element_simt.cu",
-                         "ms": mf, "bytes": bytes_form},
-        "csr_sum": {"kernel": "segsum_kernel", "src": "scatter.cu", "ms": ms, "bytes": bytes_sum},
+                         "ms": mf, "bytes": bytes_form, "flops": flops * E, "fp64_ops": ops * E},
+        "csr_sum": {"kernel": "segsum8_kernel" if fp64 else "segsum_kernel", "src": "scatter.cu", "ms": msum,
+                    "bytes": bytes_sum, "flops": 3 * (nc - nnz) if fp64 else 0, "fp64_ops": 3 * (nc - nnz) if fp64 else 0},
     }
-    dom = max(kernels.values(), key=lambda d: d["ms"])
-    peak, peak_kind = measured_peaks()
-    achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
+    phases = {}
+    for name, kd in kernels.items():
+        sec = kd["ms"] / 1e3
+        ph = {"kernel": kd["kernel"], "ms": kd["ms"], "GB/s": kd["bytes"] / sec / 1e9,
+              "frac_hbm": kd["bytes"] / sec / 1e9 / peak, "bytes_per_launch": kd["bytes"]}
+        if fp64:
+            ph.update({"TFLOP/s": kd["flops"] / sec / 1e12, "frac_fp64": kd["flops"] / sec / 1e12 / fp64_peak,
+                       "fp64_ops_frac": 2 * kd["fp64_ops"] / sec / 1e12 / fp64_peak})
+        phases[name] = ph
+    dom_name = max(kernels, key=lambda nm: kernels[nm]["ms"])
+    dom, dph = kernels[dom_name], phases[dom_name]
     traffic = None if args.scale is not None else kernel_traffic(f"{dom['kernel']}:{args.prec}:{args.workload}",
                                                                   dom["src"])
-    roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": achieved, "peak": peak,
-                "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs copy)" if peak_kind == "measured" else peak_kind,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "algorithmic_bytes_per_launch": dom["bytes"]}
-    phases = {name: {"ms": d["ms"], "GB/s": d["bytes"] / (d["ms"] / 1e3) / 1e9,
-                     "frac_hbm": d["bytes"] / (d["ms"] / 1e3) / 1e9 / peak} for name, d in kernels.items()}
+    hbm_part = {"achieved": dph["GB/s"], "peak": peak, "unit": "GB/s", "frac": dph["frac_hbm"],
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs copy)" if peak_kind == "measured" else peak_kind}
+    if fp64 and dph["frac_fp64"] > dph["frac_hbm"]:
+        roofline = {"bound": "alu", "kernel": dom["kernel"], "achieved": dph["TFLOP/s"], "peak": fp64_peak,
+                    "unit": "TFLOP/s", "frac": dph["frac_fp64"],
+                    "peak_kind": "measured in this run: cuBLAS DGEMM 4096^3 (torch.mm), FP64 pipe; nominal 1.25",
+                    "fp64_ops_frac": dph["fp64_ops_frac"],
+                    "flops_per_element": flops, "fp64_ops_per_element": ops,
+                    "traffic": traffic, "algorithmic_bytes_per_launch": dom["bytes"], "hbm": hbm_part}
+    else:
+        roofline = {"bound": "hbm", "kernel": dom["kernel"], "traffic": traffic,
+                    "algorithmic_bytes_per_launch": dom["bytes"], **hbm_part}
+        if fp64:
+            roofline["fp64"] = {"achieved": dph["TFLOP/s"], "peak": fp64_peak, "frac": dph["frac_fp64"]}
 
-    # batched and served configurations (rank 0, after the timed region)
+    # once-per-mesh phases timed on the device, then the batched and served
+    # configurations and the other workloads (rank 0, after the timed region)
     del fm, us, out
     torch.cuda.empty_cache()
+    setup = {"host_wall_ms": {"mesh_create_geometry": 1e3 * t_mesh, "symbolic_pattern": 1e3 * t_sym,
+                              "note": "host clock, including the upload of coords and conn"}}
+    if args.scale is None and not args.no_configs:
+        setup["kernels"] = measure_setup_kernels(F, torch, wl, stream, peak)
     bwls = None if (args.no_batched and args.no_serve) else mg.batched_meshes(64, seed=4)
     batched = None if args.no_batched else measure_batched(F, torch, stream, bwls)
     served = None if args.no_serve else measure_serve(F, torch, bwls, n_requests=args.serve_requests)
     del bwls
     configs = None
     if not args.no_configs:
-        p64 = measure_fp64_peak(torch, stream)
-        configs = {"tri_p1_64": measure_sweep(F, torch, stream, "tri_p1_64", precs=("fp64", "tf32x3"), fp64_peak=p64),
-                   "tet_p1_128": measure_sweep(F, torch, stream, "tet_p1_128", fp64_peak=p64),
-                   "tet_p2_64": measure_sweep(F, torch, stream, "tet_p2_64", fp64_peak=p64),
-                   "fp64_peak_tflops": p64}
+        configs = {name: measure_sweep(F, torch, stream, name, precs=precs, fp64_peak=fp64_peak)
+                   for name, precs in (("tri_p1_64", ("fp64", "tf32x3")), ("tri_p2_1024", ("tf32x3", "fp64")),
+                                       ("tet_p2_64", ("fp64", "tf32x3")), ("tet_p3_32", ("fp64", "tf32x3")))}
 
-    cpu = None if args.no_cpu_baseline else cpu_baseline_oracle()
+    cpu = None if args.no_cpu_baseline else cpu_baseline_oracle(args.workload if args.scale is None else WORKLOAD)
     line = {
         "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.prec != "fp64" else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
         "config": {"workload": args.workload if args.scale is None else f"{args.workload}@N={args.scale}",
                    "desc": WORKLOAD_DESC if args.workload == WORKLOAD else wl.name, "precision": args.prec,
-                   "element_product": PRODUCT_DESC.get(args.prec, args.prec),
-                   "elements": E, "nnz": nnz, "l2": "inputs larger than L2 (per-step traffic > 2 GB; no explicit flush)",
+                   "element_product": PRODUCT_DESC.get(args.prec, "FP64 SIMT" if fp64 else args.prec),
+                   "api": "fem_assemble_all, device-resident u and CSR values",
+                   "elements": E, "nnz": nnz,
+                   "l2": "inputs larger than L2 (V alone is 3.6 GB per step in FP64; no explicit flush)",
                    "parallelism": f"{world} independent meshes, one per GPU" if world > 1 else "single GPU"},
-        "roofline": roofline, "phases": phases,
-        "setup_once_per_mesh_ms": {"mesh_create_geometry": 1e3 * t_mesh, "symbolic_pattern": 1e3 * t_sym},
-        "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64, "modes": modes, "mass_u": mass_u, "clocks": clk.summary(),
-        "gpu_launches": args.steps * 2,
+        "roofline": roofline, "phases": phases, "fp64_peak_tflops": fp64_peak,
+        "setup_once_per_mesh": setup,
+        "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64_plain, "modes": modes, "mass_u": mass_u,
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps * 4,
         "batched": batched, "serve": served, "configs": configs,
     }
     print(json.dumps(line), flush=True)

@@ -30,10 +30,15 @@ KIND = {"poly": 0, "sin": 1, "pwlin": 2}
 
 
 def build(force: bool = False) -> str:
-    """Compile fem_oracle.c into liboracle.so (plain gcc, -O2, no -ffast-math)."""
+    """Compile fem_oracle.c into liboracle.so (plain gcc, -O2, no -ffast-math;
+    -fopenmp for the multi-core timing variant)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        try:   # OpenMP for the multi-core timing variant; without it that variant runs on one thread
+            subprocess.check_call(base[:4] + ["-fopenmp"] + base[4:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -66,6 +71,9 @@ def lib():
             L.oracle_geometry.restype = C.c_double
             L.oracle_assemble.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, dp, C.c_int, dp] + [dp] * 6
             L.oracle_assemble.restype = C.c_int
+            L.oracle_assemble_mt.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, dp, C.c_int, dp] + [dp] * 3 \
+                + [C.c_int]
+            L.oracle_assemble_mt.restype = C.c_int
             L.oracle_entries.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, dp, C.c_int, dp,
                                          C.c_longlong, ip, ip] + [dp] * 6
             L.oracle_entries.restype = C.c_int
@@ -175,6 +183,20 @@ class Oracle:
         if rc != 0:
             raise RuntimeError(f"oracle_assemble failed ({rc})")
         return out
+
+    def assemble_mt(self, u, coeff, m: float = 1.0, deg: int = 0, threads: int = 0):
+        """The multi-core timing variant: the same M, K, T (same bits) with
+        the element loop on `threads` host threads (0 = all cores).  Returns
+        (dict, threads used)."""
+        nz = self.nnz()
+        out = {k: np.zeros(nz) for k in ("M", "K", "T")}
+        cp = coeff.numpy()
+        uu = np.ascontiguousarray(u, dtype=np.float64)
+        used = lib().oracle_assemble_mt(self._h, self._deg(deg, self.p), float(m), KIND[coeff.kind], _dp(cp),
+                                        len(cp), _dp(uu), _dp(out["M"]), _dp(out["K"]), _dp(out["T"]), int(threads))
+        if used < 0:
+            raise RuntimeError(f"oracle_assemble_mt failed ({used})")
+        return out, used
 
     def assemble_mass_u(self, u, us, mcoeff, deg: int = 0):
         """M(u) (mass with the coefficient law m(u)) and the mass tensor of

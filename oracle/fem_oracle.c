@@ -56,6 +56,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_MAXNP 20
 #define OR_MAXQ 24
@@ -595,6 +598,63 @@ int oracle_assemble(void* h, int deg, double m, int kkind, const double* kp, int
             }
     }
     return 0;
+}
+
+/* The same assembly with the element loop spread over `nthreads` host
+ * threads (OpenMP; 0 = all the host's cores): every element's local
+ * matrices are formed in parallel into a buffer by the same element()
+ * routine, then added into the CSR values by one thread in ascending element
+ * order, exactly as oracle_assemble adds them, so the results are the same
+ * bits.  This is the multi-core CPU baseline (a timing reference); the
+ * parity reference is oracle_assemble.  No error scales.  Returns the number
+ * of threads used (negative on failure). */
+int oracle_assemble_mt(void* h, int deg, double m, int kkind, const double* kp, int nkp, const double* u,
+                       double* M, double* K, double* T, int nthreads) {
+    octx* c = (octx*)h;
+    if (build_pattern(c)) return -1;
+    otab t;
+    if (make_tab(c->d, c->p, deg, &t)) return -1;
+    const int np = c->np;
+    const size_t ne = (size_t)np * np;
+    const size_t nz = (size_t)c->nnz;
+    double* out[3] = {M, K, T};
+    for (int k = 0; k < 3; ++k) if (out[k]) memset(out[k], 0, sizeof(double) * nz);
+    double* buf = (double*)malloc(sizeof(double) * 3 * ne * (size_t)c->E);
+    if (!buf && c->E > 0) return -3;
+    int used = 1;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_num_procs();
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int e = 0; e < c->E; ++e) {
+        if (e == 0) used = omp_get_num_threads();
+        double* b = buf + 3 * ne * (size_t)e;
+        element(c, &t, e, m, kkind, kp, nkp, u, b, b + ne, b + 2 * ne, NULL, NULL, NULL);
+    }
+#else
+    (void)nthreads;
+    for (int e = 0; e < c->E; ++e) {
+        double* b = buf + 3 * ne * (size_t)e;
+        element(c, &t, e, m, kkind, kp, nkp, u, b, b + ne, b + 2 * ne, NULL, NULL, NULL);
+    }
+#endif
+    for (int e = 0; e < c->E; ++e) {
+        const int* v = c->conn + (long long)e * np;
+        const double* b = buf + 3 * ne * (size_t)e;
+        for (int i = 0; i < np; ++i)
+            for (int j = 0; j < np; ++j) {
+                long long s = find_slot(c, v[i], v[j]);
+                if (s < 0) {
+                    free(buf);
+                    return -2;
+                }
+                int l = i * np + j;
+                if (M) M[s] += b[l];
+                if (K) K[s] += b[ne + l];
+                if (T) T[s] += b[2 * ne + l];
+            }
+    }
+    free(buf);
+    return used;
 }
 
 /* Selected entries (rows[k], cols[k]) computed one by one: the sum over the

@@ -396,3 +396,18 @@ def test_entries_match_full_assembly():
     s = o.entries(rows[sel], ci[sel], u, coeff)
     for k in ("M", "K", "T", "absK"):
         assert np.array_equal(s[k], r[k][sel])     # same order of summation: bit-identical
+
+
+@pytest.mark.parametrize("name", ["tri_p2", "tet_p1"])
+def test_multicore_oracle_same_bits(name):
+    """The multi-core timing variant forms the element matrices in parallel
+    and adds them in the same element order: identical bits."""
+    mesh = mg.structured_tri(7, 2, 0.2, seed=21) if name == "tri_p2" else mg.structured_tet(4, 1, 0.15, seed=22)
+    o = orc.Oracle.of(mesh)
+    u = mg.fourier_field(mesh.coords, 23)
+    law = mg.Coeff("sin", (2.0, 1.0, 3.0))
+    ref = o.assemble(u, law, want_abs=False)
+    got, used = o.assemble_mt(u, law, threads=3)
+    assert used >= 1
+    for k in ("M", "K", "T"):
+        assert np.array_equal(got[k], ref[k]), k
