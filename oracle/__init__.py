@@ -74,6 +74,16 @@ def lib():
             L.oracle_assemble_mt.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, dp, C.c_int, dp] + [dp] * 3 \
                 + [C.c_int]
             L.oracle_assemble_mt.restype = C.c_int
+            L.oracle_boundary_facets.argtypes = [C.c_void_p, ip, ip]
+            L.oracle_boundary_facets.restype = C.c_int
+            L.oracle_boundary.argtypes = [C.c_void_p, C.c_int, dp, C.c_int, dp, dp, dp, dp, dp]
+            L.oracle_boundary.restype = C.c_int
+            L.oracle_residual.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, C.c_double, dp, dp]
+            L.oracle_residual.restype = C.c_int
+            L.oracle_jacobian.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, C.c_double, dp]
+            L.oracle_jacobian.restype = C.c_int
+            L.oracle_facet_rule.argtypes = [C.c_int, C.c_int, dp, dp]
+            L.oracle_facet_rule.restype = C.c_int
             L.oracle_entries.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, dp, C.c_int, dp,
                                          C.c_longlong, ip, ip] + [dp] * 6
             L.oracle_entries.restype = C.c_int
@@ -231,6 +241,47 @@ class Oracle:
             raise RuntimeError("oracle_entries failed")
         return out
 
+    def boundary_facets(self):
+        """Boundary facets (faces of exactly one element) as arrays (element,
+        local face = the local vertex it is opposite to), ascending."""
+        nb = lib().oracle_boundary_facets(self._h, None, None)
+        fe = np.zeros(max(nb, 1), dtype=np.int32)
+        ff = np.zeros(max(nb, 1), dtype=np.int32)
+        lib().oracle_boundary_facets(self._h, _ip(fe), _ip(ff))
+        return fe[:nb], ff[:nb]
+
+    def boundary(self, u, gcoeff):
+        """Boundary matrix B_ik = int g'(u_h) phi_i phi_k dS (CSR values) and
+        boundary load b_i = int g(u_h) phi_i dS over the whole boundary:
+        dict with 'B', 'b', 'absB', 'absb'."""
+        nz = self.nnz()
+        out = {"B": np.zeros(nz), "absB": np.zeros(nz), "b": np.zeros(self.n), "absb": np.zeros(self.n)}
+        cp = gcoeff.numpy()
+        uu = np.ascontiguousarray(u, dtype=np.float64)
+        rc = lib().oracle_boundary(self._h, KIND[gcoeff.kind], _dp(cp), len(cp), _dp(uu), _dp(out["B"]),
+                                   _dp(out["b"]), _dp(out["absB"]), _dp(out["absb"]))
+        if rc != 0:
+            raise RuntimeError(f"oracle_boundary failed ({rc})")
+        return out
+
+    def residual(self, M, K, b, u, us, dt):
+        """F = M (u - us) + dt K u - dt b and its error scale: (F, absF)."""
+        F = np.zeros(self.n)
+        aF = np.zeros(self.n)
+        arr = [np.ascontiguousarray(x, dtype=np.float64) if x is not None else None for x in (M, K, b, u, us)]
+        rc = lib().oracle_residual(self._h, *[_dp(x) for x in arr], float(dt), _dp(F), _dp(aF))
+        if rc != 0:
+            raise RuntimeError("oracle_residual failed")
+        return F, aF
+
+    def jacobian(self, M, Mt, K, T, B, dt):
+        """J = Mt + M + dt (K + T) - dt B on the pattern (Mt, T, B may be None)."""
+        J = np.zeros(self.nnz())
+        arr = [np.ascontiguousarray(x, dtype=np.float64) if x is not None else None for x in (M, Mt, K, T, B)]
+        if lib().oracle_jacobian(self._h, *[_dp(x) for x in arr], float(dt), _dp(J)) != 0:
+            raise RuntimeError("oracle_jacobian failed")
+        return J
+
     def element(self, e: int, u, coeff, m: float = 1.0, deg: int = 0):
         """Dense local matrices (Me, Ke, Te) of element e, row = test index."""
         np_ = self.conn.shape[1]
@@ -247,6 +298,15 @@ class Oracle:
         A = np.zeros((self.d, self.d))
         det = lib().oracle_geometry(self._h, int(e), _dp(A))
         return det, A
+
+
+def facet_rule(d: int, p: int):
+    """The oracle's facet quadrature: (points (n x (d-1)), weights)."""
+    L = lib()
+    xi = np.zeros(64)
+    w = np.zeros(32)
+    n = L.oracle_facet_rule(d, p, _dp(xi), _dp(w))
+    return xi[: n * (d - 1)].reshape(n, d - 1), w[:n]
 
 
 def csr_to_dense(rp, ci, vals, n):

@@ -771,3 +771,229 @@ int oracle_assemble_mass_u(void* h, int deg, int mkind, const double* mp, int nm
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Boundary terms, residual and Jacobian (Section 5; Section 6, Exp. 2) */
+/* ------------------------------------------------------------------ */
+/* The load vector holds f_i = int_Omega f phi_i + int_{dOmega_N} g_N(u_h)
+ * phi_i dS (Section 2) and its derivative B_ik = int_{dOmega_N}
+ * g_N'(u_h) phi_i phi_k dS (Section 5).  Here dOmega_N is the whole boundary
+ * (Experiment 2: convection and radiation on every side), f = 0, and g_N is
+ * a law of u (for Experiment 2 the polynomial h_c (T_a - u) + h_r (T_a^4 -
+ * u^4)).  The boundary facets are the element faces that belong to one
+ * element only; face f of an element is the face opposite its local vertex
+ * f.  They are listed in ascending (element, face) order, the order in
+ * which their contributions are added. */
+
+typedef struct { int e, f; int key[3]; } oface;
+
+static int cmp_face(const void* a, const void* b) {
+    const oface* x = (const oface*)a; const oface* y = (const oface*)b;
+    for (int t = 0; t < 3; ++t) if (x->key[t] != y->key[t]) return x->key[t] < y->key[t] ? -1 : 1;
+    if (x->e != y->e) return x->e < y->e ? -1 : 1;
+    return x->f - y->f;
+}
+static int cmp_ef(const void* a, const void* b) {
+    const int* x = (const int*)a; const int* y = (const int*)b;
+    if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;
+    return x[1] - y[1];
+}
+
+/* Boundary facets as (element, face) pairs in ascending order; returns the
+ * count (out may be NULL: count only), -1 on allocation failure. */
+int oracle_boundary_facets(void* h, int* fe, int* ff) {
+    octx* c = (octx*)h;
+    int d = c->d, nv = d + 1;
+    long long nf = (long long)c->E * nv;
+    oface* F = (oface*)malloc(sizeof(oface) * (size_t)(nf > 0 ? nf : 1));
+    if (!F) return -1;
+    for (int e = 0; e < c->E; ++e)
+        for (int f = 0; f < nv; ++f) {
+            oface* o = &F[(long long)e * nv + f];
+            o->e = e; o->f = f;
+            int k = 0;
+            for (int a = 0; a < nv; ++a) if (a != f) o->key[k++] = c->conn[(long long)e * c->np + a];
+            for (; k < 3; ++k) o->key[k] = -1;
+            /* sort the face's vertex ids (at most 3) */
+            for (int i = 0; i < 3; ++i) for (int j = i + 1; j < 3; ++j)
+                if (o->key[j] < o->key[i]) { int t = o->key[i]; o->key[i] = o->key[j]; o->key[j] = t; }
+        }
+    qsort(F, (size_t)nf, sizeof(oface), cmp_face);
+    int* pairs = (int*)malloc(sizeof(int) * 2 * (size_t)(nf > 0 ? nf : 1));
+    int nb = 0;
+    for (long long i = 0; i < nf;) {
+        long long j = i + 1;
+        while (j < nf && F[j].key[0] == F[i].key[0] && F[j].key[1] == F[i].key[1] && F[j].key[2] == F[i].key[2]) ++j;
+        if (j - i == 1) { pairs[2 * nb] = F[i].e; pairs[2 * nb + 1] = F[i].f; ++nb; }
+        i = j;
+    }
+    qsort(pairs, (size_t)nb, 2 * sizeof(int), cmp_ef);
+    if (fe && ff) for (int i = 0; i < nb; ++i) { fe[i] = pairs[2 * i]; ff[i] = pairs[2 * i + 1]; }
+    free(F); free(pairs);
+    return nb;
+}
+
+/* The local nodes of face f: the nodes whose associated vertices (one for a
+ * vertex node, the two ends of its edge, the three corners of its face, in
+ * the local order of oracle_basis) do not include vertex f. */
+static int face_nodes(int d, int p, int f, int* out) {
+    int nv = d + 1, k = 0, n = 0;
+    for (int a = 0; a < nv; ++a, ++k) if (a != f) out[n++] = k;
+    if (p >= 2)
+        for (int a = 0; a < nv; ++a) for (int b = a + 1; b < nv; ++b)
+            for (int t = 0; t < p - 1; ++t, ++k) if (a != f && b != f) out[n++] = k;
+    if (p == 3)
+        for (int a = 0; a < nv; ++a) for (int b = a + 1; b < nv; ++b) for (int e = b + 1; e < nv; ++e, ++k)
+            if (a != f && b != f && e != f) out[n++] = k;
+    return n;
+}
+
+/* Quadrature on the reference facet: Gauss-Legendre with p+1 points on
+ * [0, 1] (weights summing to 1) for the edges of triangles; for the
+ * triangular faces of tetrahedra the triangle rule of degree 2p (weights
+ * summing to 1/2).  xi: n x (d-1).  Returns n. */
+static int facet_rule(int d, int p, double* xi, double* w) {
+    if (d == 3) return oracle_rule(2, 2 * p, xi, w);
+    static const double t2[] = {-0.57735026918962576451, 0.57735026918962576451};
+    static const double w2[] = {1.0, 1.0};
+    static const double t3[] = {-0.77459666924148337704, 0.0, 0.77459666924148337704};
+    static const double w3[] = {0.55555555555555555556, 0.88888888888888888889, 0.55555555555555555556};
+    static const double t4[] = {-0.86113631159405257522, -0.33998104358485626480, 0.33998104358485626480,
+                                0.86113631159405257522};
+    static const double w4[] = {0.34785484513745385737, 0.65214515486254614263, 0.65214515486254614263,
+                                0.34785484513745385737};
+    const double* t = p == 1 ? t2 : p == 2 ? t3 : t4;
+    const double* ww = p == 1 ? w2 : p == 2 ? w3 : w4;
+    int n = p + 1;
+    for (int q = 0; q < n; ++q) { xi[q] = 0.5 * (1.0 + t[q]); w[q] = 0.5 * ww[q]; }
+    return n;
+}
+
+/* B (CSR values of the mesh pattern) and b (n values); absB, absb receive the
+ * sums of the magnitudes of the terms (the error scale).  Any output may be
+ * NULL.  Returns 0, or negative on failure. */
+int oracle_boundary(void* h, int gkind, const double* gp, int ngp, const double* u, double* B, double* b,
+                    double* absB, double* absb) {
+    octx* c = (octx*)h;
+    if (build_pattern(c)) return -1;
+    int d = c->d, p = c->p, np = c->np, nv = d + 1;
+    int nb = oracle_boundary_facets(h, NULL, NULL);
+    if (nb < 0) return -1;
+    int* fe = (int*)malloc(sizeof(int) * (size_t)(nb + 1));
+    int* ff = (int*)malloc(sizeof(int) * (size_t)(nb + 1));
+    oracle_boundary_facets(h, fe, ff);
+    if (B) memset(B, 0, sizeof(double) * (size_t)c->nnz);
+    if (absB) memset(absB, 0, sizeof(double) * (size_t)c->nnz);
+    if (b) memset(b, 0, sizeof(double) * (size_t)c->n);
+    if (absb) memset(absb, 0, sizeof(double) * (size_t)c->n);
+    double xi[OR_MAXQ * 2], w[OR_MAXQ];
+    int nq = facet_rule(d, p, xi, w);
+    for (int k = 0; k < nb; ++k) {
+        int e = fe[k], f = ff[k];
+        const int* v = c->conn + (long long)e * np;
+        int fn[OR_MAXNP];
+        int nf = face_nodes(d, p, f, fn);
+        int wv[3], m = 0;
+        for (int a = 0; a < nv; ++a) if (a != f) wv[m++] = a;
+        /* facet measure: edge length (2D), twice the triangle's area (3D) */
+        double E1[3], E2[3], J;
+        for (int a = 0; a < d; ++a) E1[a] = c->X[(long long)v[wv[1]] * d + a] - c->X[(long long)v[wv[0]] * d + a];
+        if (d == 2) {
+            J = sqrt(E1[0] * E1[0] + E1[1] * E1[1]);
+        } else {
+            for (int a = 0; a < 3; ++a) E2[a] = c->X[(long long)v[wv[2]] * 3 + a] - c->X[(long long)v[wv[0]] * 3 + a];
+            double cx = E1[1] * E2[2] - E1[2] * E2[1], cy = E1[2] * E2[0] - E1[0] * E2[2],
+                   cz = E1[0] * E2[1] - E1[1] * E2[0];
+            J = sqrt(cx * cx + cy * cy + cz * cz);
+        }
+        double Be[OR_MAXNP][OR_MAXNP], aBe[OR_MAXNP][OR_MAXNP], be[OR_MAXNP], abe[OR_MAXNP];
+        memset(Be, 0, sizeof(Be)); memset(aBe, 0, sizeof(aBe)); memset(be, 0, sizeof(be)); memset(abe, 0, sizeof(abe));
+        for (int q = 0; q < nq; ++q) {
+            /* the facet point in reference coordinates of the element: the
+             * barycentric combination of the face's reference vertices
+             * (reference vertex 0 at the origin, vertex a at e_a) */
+            double mu[3], xh[3] = {0.0, 0.0, 0.0};
+            if (d == 2) { mu[0] = 1.0 - xi[q]; mu[1] = xi[q]; }
+            else { mu[0] = 1.0 - xi[2 * q] - xi[2 * q + 1]; mu[1] = xi[2 * q]; mu[2] = xi[2 * q + 1]; }
+            for (int t = 0; t < d; ++t) if (wv[t] > 0) xh[wv[t] - 1] += mu[t];
+            double phi[OR_MAXNP], grad[OR_MAXNP * 3];
+            oracle_basis(d, p, xh, phi, grad);
+            double uq = 0.0;   /* the trace of u_h: face nodes only */
+            for (int i = 0; i < nf; ++i) uq += phi[fn[i]] * (u ? u[v[fn[i]]] : 0.0);
+            double dg;
+            double gq = oracle_k(gkind, gp, ngp, uq, &dg);
+            double wj = w[q] * J;
+            for (int i = 0; i < nf; ++i) {
+                double ti = wj * gq * phi[fn[i]];
+                be[i] += ti;
+                abe[i] += fabs(ti);
+                for (int kk = 0; kk < nf; ++kk) {
+                    double t = wj * dg * phi[fn[i]] * phi[fn[kk]];
+                    Be[i][kk] += t;
+                    aBe[i][kk] += fabs(t);
+                }
+            }
+        }
+        for (int i = 0; i < nf; ++i) {
+            int r = v[fn[i]];
+            if (b) b[r] += be[i];
+            if (absb) absb[r] += abe[i];
+            for (int kk = 0; kk < nf; ++kk) {
+                long long s = find_slot(c, r, v[fn[kk]]);
+                if (s < 0) { free(fe); free(ff); return -2; }
+                if (B) B[s] += Be[i][kk];
+                if (absB) absB[s] += aBe[i][kk];
+            }
+        }
+    }
+    free(fe); free(ff);
+    return 0;
+}
+
+/* Residual of one implicit Euler step (Section 5):
+ *   F_i = sum_j M_ij (u_j - us_j) + dt sum_j K_ij u_j - dt b_i,
+ * with M, K CSR values of the mesh pattern (M may be M(u)) and b the
+ * boundary load (f = 0).  absF receives the sum of the magnitudes of the
+ * terms.  Columns in ascending order. */
+int oracle_residual(void* h, const double* M, const double* K, const double* b, const double* u, const double* us,
+                    double dt, double* F, double* absF) {
+    octx* c = (octx*)h;
+    if (build_pattern(c)) return -1;
+    for (int r = 0; r < c->n; ++r) {
+        double s = 0.0, a = 0.0;
+        for (int k = c->row_ptr[r]; k < c->row_ptr[r + 1]; ++k) {
+            int j = c->col_idx[k];
+            double t1 = M[k] * (u[j] - us[j]), t2 = dt * K[k] * u[j];
+            s += t1 + t2;
+            a += fabs(t1) + fabs(t2);
+        }
+        double t3 = b ? dt * b[r] : 0.0;
+        F[r] = s - t3;
+        if (absF) absF[r] = a + fabs(t3);
+    }
+    return 0;
+}
+
+/* Jacobian of the residual (Section 5):
+ *   J = Mt + M + dt (K + T) - dt B
+ * entry by entry on the mesh pattern (Mt: the mass tensor times u - u^s, T:
+ * the conductivity tensor times u; any of Mt, T, B may be NULL for zero). */
+int oracle_jacobian(void* h, const double* M, const double* Mt, const double* K, const double* T, const double* B,
+                    double dt, double* J) {
+    octx* c = (octx*)h;
+    if (build_pattern(c)) return -1;
+    for (long long s = 0; s < c->nnz; ++s) {
+        double kt = K[s] + (T ? T[s] : 0.0);
+        J[s] = (Mt ? Mt[s] : 0.0) + M[s] + dt * kt - (B ? dt * B[s] : 0.0);
+    }
+    return 0;
+}
+
+/* Exported: the facet quadrature rule (for tests). */
+int oracle_facet_rule(int d, int p, double* xi, double* w) {
+    double x[OR_MAXQ * 2], ww[OR_MAXQ];
+    int n = facet_rule(d, p, x, ww);
+    if (xi) memcpy(xi, x, sizeof(double) * (size_t)n * (d - 1));
+    if (w) memcpy(w, ww, sizeof(double) * (size_t)n);
+    return n;
+}
