@@ -408,6 +408,60 @@ int fem_serve_stats(fem_server* s, fem_serve_counters* out);
  * work in flight and frees everything the server holds. */
 int fem_serve_destroy(fem_server* s);
 
+/* ------------------------------------------- boundary terms and Newton step */
+/* The Newton quantities of one implicit Euler step (Section 5):
+ *   F(u) = M (u - u^s) + dt K(u) u - dt f(u),
+ *   dF/du = Mt + M + dt (K + T) - dt B,
+ * where f holds the boundary load b_i = int_{dOmega_N} g_N(u_h) phi_i dS
+ * (Section 2; no volume source) and B_ik = int_{dOmega_N} g_N'(u_h) phi_i
+ * phi_k dS is its derivative (Section 5).  Experiment 2 (Section 6) uses
+ * convection plus radiation on the whole boundary, g_N = h_c (T_a - u) +
+ * h_r (T_a^4 - u^4): pass it as a FEM_K_POLY law (coefficients h_c T_a +
+ * h_r T_a^4, -h_c, 0, 0, -h_r); g_N' comes from the same law.  All in FP64.
+ *
+ * Boundary facets are the element faces that belong to no other element;
+ * face f of an element is the face opposite its local vertex f, and its
+ * nodes are the element's local nodes off that vertex.  fem_boundary_facets
+ * finds them once per mesh on the device (requires fem_symbolic;
+ * synchronises `stream`) and lists them in ascending (element, face) order;
+ * *n_facets receives their number.  Idempotent. */
+int fem_boundary_facets(fem_mesh* mesh, void* stream, int64_t* n_facets);
+/* Copies the facet list: d_elem[f], d_face[f] (device, caller-owned, either
+ * may be NULL).  Requires fem_boundary_facets. */
+int fem_get_boundary_facets(fem_mesh* mesh, int32_t* d_elem, int32_t* d_face, void* stream);
+/* B(u) into d_vB (nnz FP64 CSR values on the mesh pattern: the boundary
+ * pattern is part of the volume pattern) and the boundary load into d_b (n
+ * FP64 values; 0 off the boundary); either may be NULL.  Each facet's
+ * matrices are one product V = X Q on the facet (X[q] = w_q |J_f| g'(u_q),
+ * the paper's mass-type product, Section 4.1), then each boundary row adds
+ * its facets in ascending order (deterministic).  Quadrature on a facet:
+ * Gauss-Legendre with p+1 points on edges, the degree-2p triangle rule on
+ * faces.  d_mask: one byte per facet, nonzero where the facet belongs to
+ * dOmega_N (NULL: the whole boundary).  d_u: FP64 nodal values.  Device
+ * pointers only (FEM_EINVAL otherwise).  Requires fem_symbolic (the facets
+ * are found on the first call, which synchronises `stream`). */
+int fem_assemble_boundary(fem_mesh* mesh, const fem_coeff* g, const double* d_u, const uint8_t* d_mask,
+                          double* d_vB, double* d_b, void* stream);
+/* d_y = alpha A d_x + beta d_y with A the FP64 CSR values d_vals on the mesh
+ * pattern (a row's terms added by ascending column).  Device pointers. */
+int fem_csr_spmv(fem_mesh* mesh, const double* d_vals, double alpha, const double* d_x, double beta, double* d_y,
+                 void* stream);
+/* d_F = M (u - u^s) + dt K u - dt b (FP64, n values; d_b may be NULL for
+ * b = 0; M may be M(u) from fem_assemble_mass_u) and, if d_norms is not
+ * NULL, d_norms[0] = ||F||_2 and d_norms[1] = ||F||_inf computed on the
+ * device in one fixed order (rows by ascending column; chunks of 256 rows,
+ * then the chunks in ascending order), so the norms are reproducible bit for
+ * bit.  Device pointers only. */
+int fem_residual(fem_mesh* mesh, const double* d_vM, const double* d_vK, const double* d_b, const double* d_u,
+                 const double* d_us, double dt, double* d_F, double* d_norms, void* stream);
+/* d_vJ = Mt + M + dt (K + T) - dt B entry by entry on the mesh pattern (the
+ * Jacobian of the implicit Euler residual, Section 5); d_vMt (the mass
+ * tensor times u - u^s, from fem_assemble_mass_u), d_vT (the tangent) and
+ * d_vB may be NULL for zero.  FP64 device pointers.  d_vJ may alias one of
+ * the inputs. */
+int fem_jacobian(fem_mesh* mesh, double dt, const double* d_vM, const double* d_vMt, const double* d_vK,
+                 const double* d_vT, const double* d_vB, double* d_vJ, void* stream);
+
 /* The conductivity law alone, in FP64 on the GPU: d_k[i] = k(u_i) and
  * d_dk[i] = k'(u_i) for i < n, with the very device code the FP64 element
  * kernels evaluate at the quadrature points (the S of Algorithm 2, whose

@@ -146,6 +146,15 @@ _SIGS = {
                                   C.c_void_p], C.c_int),
     "fem_form_elements": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_int, C.c_void_p], C.c_int),
     "fem_law_eval": ([C.POINTER(fem_coeff), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "fem_boundary_facets": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
+    "fem_get_boundary_facets": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "fem_assemble_boundary": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.c_void_p], C.c_int),
+    "fem_csr_spmv": ([C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p], C.c_int),
+    "fem_residual": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                      C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "fem_jacobian": ([C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                      C.c_void_p, C.c_void_p], C.c_int),
     "fem_chunk_plan": ([C.c_void_p, C.c_int, C.c_size_t, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64),
                         C.POINTER(C.c_int64), C.c_void_p], C.c_int),
     "fem_form_elements_range": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_int, C.c_int64,
@@ -314,6 +323,37 @@ def fem_assemble_all_noalloc(mesh: int, k, d_u, d_vM, d_vK, d_vT, stream=None) -
 def fem_law_eval(k, d_u, n: int, d_k, d_dk, stream=None) -> None:
     """k(u) and k'(u) of a law at n device values, in FP64 on the GPU."""
     _check(lib().fem_law_eval(C.byref(k), _vp(d_u), int(n), _vp(d_k), _vp(d_dk), _stream(stream)))
+
+
+def fem_boundary_facets(mesh: int, stream=None) -> int:
+    """Finds the boundary facets once per mesh; returns their number."""
+    n = C.c_int64()
+    _check(lib().fem_boundary_facets(mesh, _stream(stream), C.byref(n)))
+    return n.value
+
+
+def fem_get_boundary_facets(mesh: int, d_elem, d_face, stream=None) -> None:
+    _check(lib().fem_get_boundary_facets(mesh, _vp(d_elem), _vp(d_face), _stream(stream)))
+
+
+def fem_assemble_boundary(mesh: int, g, d_u, d_mask, d_vB, d_b, stream=None) -> None:
+    """B(u) (CSR values) and the boundary load b(u), FP64."""
+    _check(lib().fem_assemble_boundary(mesh, C.byref(g), _vp(d_u), _vp(d_mask), _vp(d_vB), _vp(d_b),
+                                       _stream(stream)))
+
+
+def fem_csr_spmv(mesh: int, d_vals, alpha: float, d_x, beta: float, d_y, stream=None) -> None:
+    _check(lib().fem_csr_spmv(mesh, _vp(d_vals), float(alpha), _vp(d_x), float(beta), _vp(d_y), _stream(stream)))
+
+
+def fem_residual(mesh: int, d_vM, d_vK, d_b, d_u, d_us, dt: float, d_F, d_norms, stream=None) -> None:
+    _check(lib().fem_residual(mesh, _vp(d_vM), _vp(d_vK), _vp(d_b), _vp(d_u), _vp(d_us), float(dt), _vp(d_F),
+                              _vp(d_norms), _stream(stream)))
+
+
+def fem_jacobian(mesh: int, dt: float, d_vM, d_vMt, d_vK, d_vT, d_vB, d_vJ, stream=None) -> None:
+    _check(lib().fem_jacobian(mesh, float(dt), _vp(d_vM), _vp(d_vMt), _vp(d_vK), _vp(d_vT), _vp(d_vB), _vp(d_vJ),
+                              _stream(stream)))
 
 
 def _ptr_array(seq):

@@ -303,7 +303,8 @@ CoeffDev coeff_to_device(const fem_coeff* k) { return to_dev(k); }
 
 size_t fem_mesh::device_bytes() const {
     const fem::DevBuf* bufs[] = {&coords, &conn, &geo64, &geo32, &row_ptr, &col_idx, &seg_ptr, &contrib, &slot,
-                                 &seg_head, &inc_ptr, &inc, &VMK, &VT, &u_stage, &out_stage};
+                                 &seg_head, &inc_ptr, &inc, &VMK, &VT, &u_stage, &out_stage, &bfacet, &bnode_ptr,
+                                 &bnode_inc, &bscratch, &npart};
     size_t t = 0;
     for (auto* b : bufs) t += b->bytes;
     return t;
@@ -397,7 +398,7 @@ int fem_mesh_destroy(fem_mesh* m) {
     cudaDeviceSynchronize();
     fem::DevBuf* bufs[] = {&m->coords, &m->conn, &m->geo64, &m->geo32, &m->row_ptr, &m->col_idx, &m->seg_ptr,
                            &m->contrib, &m->slot, &m->seg_head, &m->inc_ptr, &m->inc, &m->VMK, &m->VT, &m->u_stage,
-                           &m->out_stage};
+                           &m->out_stage, &m->bfacet, &m->bnode_ptr, &m->bnode_inc, &m->bscratch, &m->npart};
     for (auto* b : bufs) buf_free(*b, nullptr);
     if (m->copy_stream) {
         for (auto ev : m->copy_ev)
@@ -539,6 +540,84 @@ int fem_assemble_mass_u(fem_mesh* m, const fem_coeff* mk, const void* d_u, const
     if (prec == FEM_FP64)
         return sum_t<double>(m, static_cast<double*>(d_vMu), static_cast<double*>(d_vMt), nullptr, s);
     return sum_t<float>(m, static_cast<float*>(d_vMu), static_cast<float*>(d_vMt), nullptr, s);
+}
+
+int fem_boundary_facets(fem_mesh* m, void* stream, int64_t* n_facets) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    int rc = boundary_setup(*m, static_cast<cudaStream_t>(stream));
+    if (rc) return rc;
+    if (n_facets) *n_facets = m->n_bfacets;
+    return FEM_OK;
+}
+
+int fem_get_boundary_facets(fem_mesh* m, int32_t* d_elem, int32_t* d_face, void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (!m->have_boundary) return fail(FEM_ESTATE, "fem_boundary_facets has not run");
+    if (m->n_bfacets == 0) return FEM_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int32_t* dst[2] = {d_elem, d_face};
+    for (int i = 0; i < 2; ++i) {
+        if (!dst[i]) continue;
+        if (!is_device_ptr(dst[i])) return fail(FEM_EINVAL, "fem_get_boundary_facets takes device pointers");
+        FEM_CUDA_TRY(cudaMemcpy2DAsync(const_cast<int32_t*>(dst[i]), sizeof(int32_t), m->bfacet.as<int>() + i,
+                                       2 * sizeof(int32_t), sizeof(int32_t), (size_t)m->n_bfacets,
+                                       cudaMemcpyDeviceToDevice, s));
+    }
+    return FEM_OK;
+}
+
+int fem_assemble_boundary(fem_mesh* m, const fem_coeff* g, const double* d_u, const uint8_t* d_mask, double* d_vB,
+                          double* d_b, void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    int rc = check_coeff(g);
+    if (rc) return rc;
+    if (!d_vB && !d_b) return FEM_OK;
+    const void* ptrs[4] = {d_u, d_mask, d_vB, d_b};
+    for (const void* p : ptrs)
+        if (p && !is_device_ptr(p)) return fail(FEM_EINVAL, "fem_assemble_boundary takes device pointers only");
+    if (!d_u) return fail(FEM_EINVAL, "u is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((rc = boundary_setup(*m, s))) return rc;
+    return boundary_assemble(*m, to_dev(g), d_u, d_mask, d_vB, d_b, s);
+}
+
+int fem_csr_spmv(fem_mesh* m, const double* d_vals, double alpha, const double* d_x, double beta, double* d_y,
+                 void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    const void* ptrs[3] = {d_vals, d_x, d_y};
+    for (const void* p : ptrs)
+        if (!p || !is_device_ptr(p)) return fail(FEM_EINVAL, "fem_csr_spmv takes non-NULL device pointers");
+    return csr_spmv(*m, d_vals, alpha, d_x, beta, d_y, static_cast<cudaStream_t>(stream));
+}
+
+int fem_residual(fem_mesh* m, const double* d_vM, const double* d_vK, const double* d_b, const double* d_u,
+                 const double* d_us, double dt, double* d_F, double* d_norms, void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    const void* need[5] = {d_vM, d_vK, d_u, d_us, d_F};
+    for (const void* p : need)
+        if (!p || !is_device_ptr(p)) return fail(FEM_EINVAL, "fem_residual: M, K, u, u^s and F are device pointers");
+    if ((d_b && !is_device_ptr(d_b)) || (d_norms && !is_device_ptr(d_norms)))
+        return fail(FEM_EINVAL, "fem_residual takes device pointers only");
+    if (!std::isfinite(dt)) return fail(FEM_EINVAL, "dt is not finite");
+    return csr_residual(*m, d_vM, d_vK, d_b, d_u, d_us, dt, d_F, d_norms, static_cast<cudaStream_t>(stream));
+}
+
+int fem_jacobian(fem_mesh* m, double dt, const double* d_vM, const double* d_vMt, const double* d_vK,
+                 const double* d_vT, const double* d_vB, double* d_vJ, void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    const void* need[3] = {d_vM, d_vK, d_vJ};
+    for (const void* p : need)
+        if (!p || !is_device_ptr(p)) return fail(FEM_EINVAL, "fem_jacobian: M, K and J are device pointers");
+    const void* opt[3] = {d_vMt, d_vT, d_vB};
+    for (const void* p : opt)
+        if (p && !is_device_ptr(p)) return fail(FEM_EINVAL, "fem_jacobian takes device pointers only");
+    if (!std::isfinite(dt)) return fail(FEM_EINVAL, "dt is not finite");
+    return csr_jacobian(*m, dt, d_vM, d_vMt, d_vK, d_vT, d_vB, d_vJ, static_cast<cudaStream_t>(stream));
 }
 
 int fem_law_eval(const fem_coeff* k, const double* d_u, int64_t n, double* d_k, double* d_dk, void* stream) {

@@ -78,6 +78,12 @@ struct fem_mesh {
     // move staged CSR values to the host range by range while later ranges
     // are still being summed (created on first use)
     fem::DevBuf u_stage, out_stage;
+    // boundary facets (once per mesh): (element, face opposite local vertex)
+    // pairs ascending, node -> facet incidences, facet products scratch;
+    // partial sums of the residual norms
+    bool have_boundary = false;
+    int64_t n_bfacets = 0;
+    fem::DevBuf bfacet, bnode_ptr, bnode_inc, bscratch, npart;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_ev[4] = {};
     size_t device_bytes() const;
@@ -88,6 +94,20 @@ namespace fem {
 // ---------------------------------------------------------- kernel launches
 int geometry_run(fem_mesh& m, cudaStream_t s);           // fills geo64, geo32, n_flagged
 int symbolic_run(fem_mesh& m, cudaStream_t s);           // fills pattern and segments
+int scan_exclusive(const int* in, int64_t n, int* out, cudaStream_t s);   // n ints -> n+1 prefix sums
+// boundary facets, node -> facet incidences (once; needs the pattern)
+int boundary_setup(fem_mesh& m, cudaStream_t s);
+// B (CSR values, zeroed first) and the boundary load b (n values), FP64;
+// mask: one byte per facet (NULL: all facets)
+int boundary_assemble(fem_mesh& m, const CoeffDev& g, const double* u, const unsigned char* mask, double* vB,
+                      double* b, cudaStream_t s);
+// CSR-level Newton quantities on the mesh pattern, FP64 (csr_ops.cu)
+int csr_spmv(const fem_mesh& m, const double* vals, double alpha, const double* x, double beta, double* y,
+             cudaStream_t s);
+int csr_residual(fem_mesh& m, const double* vM, const double* vK, const double* b, const double* u, const double* us,
+                 double dt, double* F, double* norms, cudaStream_t s);
+int csr_jacobian(const fem_mesh& m, double dt, const double* vM, const double* vMt, const double* vK,
+                 const double* vT, const double* vB, double* vJ, cudaStream_t s);
 
 // Element products V = X Q.  Any of VM, VK, VT may be null (matrix skipped).
 int element_simt_fp64(const fem_mesh& m, const CoeffDev& k, const double* u, double* VM, double* VK, double* VT,

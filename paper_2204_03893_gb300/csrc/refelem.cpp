@@ -267,7 +267,126 @@ std::vector<std::vector<int>> local_nodes(int d, int p) {
     return out;
 }
 
+
+// Coefficients of the Lagrange basis in the monomials of degree <= p:
+// Cm[m * np + i] = coefficient of monomial m in basis function i (the
+// inverse of the Vandermonde matrix of the monomials at the local nodes).
+bool basis_coefficients(int d, int p, std::vector<std::vector<int>>& mons, std::vector<double>& Cm, int& np) {
+    auto nodes = local_nodes(d, p);
+    np = (int)nodes.size();
+    mons = monomials(d, p);
+    const int nm = (int)mons.size();
+    if (nm != np) return false;
+    std::vector<double> V((size_t)np * nm);
+    for (int i = 0; i < np; ++i)
+        for (int m = 0; m < nm; ++m) {
+            double v = 1.0;
+            for (int a = 0; a < d; ++a) v *= std::pow((double)nodes[i][a + 1] / p, mons[m][a]);
+            V[(size_t)i * nm + m] = v;
+        }
+    Cm.assign((size_t)nm * np, 0.0);
+    for (int col = 0; col < np; ++col) {
+        std::vector<double> A = V, b(np, 0.0);
+        b[col] = 1.0;
+        if (!solve_small(A, b, np)) return false;
+        for (int m = 0; m < nm; ++m) Cm[(size_t)m * np + col] = b[m];
+    }
+    return true;
+}
+
+// Gauss-Legendre points and weights on [0, 1]: the roots of the Legendre
+// polynomial P_n by Newton's method from the Chebyshev-like guesses
+// cos(pi (i + 3/4) / (n + 1/2)), with P_n and P_n' from the three-term
+// recurrence; weights 2 / ((1 - t^2) P_n'(t)^2), halved for [0, 1].
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+    const double pi = 3.14159265358979323846;
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double t = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double pn = n == 0 ? 1.0 : p1, pm = n == 0 ? 0.0 : p0;
+            dp = n * (t * pn - pm) / (t * t - 1.0);
+            const double dt = pn / dp;
+            t -= dt;
+            if (std::fabs(dt) < 1e-17) break;
+        }
+        double p0 = 1.0, p1 = t;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (t * p1 - p0) / (t * t - 1.0);
+        x[n - 1 - i] = 0.5 * (1.0 + t);
+        w[n - 1 - i] = 1.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
 }  // namespace
+
+bool build_facets(int d, int p, FacetTab& F) {
+    if ((d != 2 && d != 3) || p < 1 || p > 3) return false;
+    std::vector<std::vector<int>> mons;
+    std::vector<double> Cm;
+    int np = 0;
+    if (!basis_coefficients(d, p, mons, Cm, np)) return false;
+    auto nodes = local_nodes(d, p);
+    F.d = d;
+    F.p = p;
+    F.nfaces = d + 1;
+    // reference facet rule: points xi (nq x (d-1)), weights
+    std::vector<double> xi, w;
+    if (d == 2) {
+        gauss_legendre01(p + 1, xi, w);
+    } else if (!solve_rule(2, 2 * p, xi, w)) {
+        return false;
+    }
+    F.nq = (int)w.size();
+    F.w = w;
+    F.nf = 0;
+    for (int f = 0; f <= d; ++f) {
+        std::vector<int> fn;
+        for (int i = 0; i < np; ++i)
+            if (nodes[i][f] == 0) fn.push_back(i);
+        if (f == 0) F.nf = (int)fn.size();
+        if ((int)fn.size() != F.nf) return false;
+        F.fnode.insert(F.fnode.end(), fn.begin(), fn.end());
+        std::vector<int> wv;   // the face's vertices, ascending
+        for (int a = 0; a <= d; ++a)
+            if (a != f) wv.push_back(a);
+        for (int q = 0; q < F.nq; ++q) {
+            double mu[3];
+            if (d == 2) {
+                mu[0] = 1.0 - xi[q];
+                mu[1] = xi[q];
+            } else {
+                mu[0] = 1.0 - xi[2 * q] - xi[2 * q + 1];
+                mu[1] = xi[2 * q];
+                mu[2] = xi[2 * q + 1];
+            }
+            double x[3] = {0.0, 0.0, 0.0};   // reference vertex 0 at the origin, vertex a at e_a
+            for (int t = 0; t < d; ++t)
+                if (wv[t] > 0) x[wv[t] - 1] += mu[t];
+            for (int a = 0; a < F.nf; ++a) {
+                double v = 0.0;
+                for (size_t m = 0; m < mons.size(); ++m) {
+                    double mv = 1.0;
+                    for (int c = 0; c < d; ++c) mv *= std::pow(x[c], mons[m][c]);
+                    v += Cm[m * np + fn[a]] * mv;
+                }
+                F.phi.push_back(v);
+            }
+        }
+    }
+    return true;
+}
 
 bool build_refelem(int d, int p, int qdeg, RefElem& R) {
     if ((d != 2 && d != 3) || p < 1 || p > 3) return false;
@@ -355,6 +474,15 @@ bool build_refelem(int d, int p, int qdeg, RefElem& R) {
 #include <mutex>
 
 namespace fem {
+
+const FacetTab* facets_for_type(int t) {
+    static std::once_flag flags[6];
+    static FacetTab F[6];
+    static bool ok[6] = {false, false, false, false, false, false};
+    if (t < 0 || t > 5) return nullptr;
+    std::call_once(flags[t], [t] { ok[t] = build_facets(t < 3 ? 2 : 3, t % 3 + 1, F[t]); });
+    return ok[t] ? &F[t] : nullptr;
+}
 
 const RefElem* refelem_for_type(int t) {
     static std::once_flag flags[6];
