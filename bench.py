@@ -443,6 +443,63 @@ def measure_mass_u(F, torch, fm, wl, us, stream, fp64_peak, steps=20, warmup=3):
     return res
 
 
+def measure_newton(F, torch, fm, wl, us, k, stream, peak_gbs, steps=10):
+    """One Newton step's assembly on the bench workload (Section 5; the
+    boundary law of Section 6, Experiment 2: convection + radiation on the
+    whole boundary): M, K(u), T(u) (fem_assemble_all), B(u) and the boundary
+    load (fem_assemble_boundary), F(u) with ||F||_2, ||F||_inf
+    (fem_residual) and the Jacobian (fem_jacobian), all FP64, each timed with
+    CUDA events on its stream."""
+    sh = stream.cuda_stream
+    E, n, nnz = wl.mesh.n_elems, wl.mesh.n_nodes, fm.nnz
+    g = F.coeff("poly", (10.0 * 1000.0 + 0.8 * 5.670373e-8 * 1000.0 ** 4, -10.0, 0.0, 0.0, -0.8 * 5.670373e-8))
+    dt = 10.0
+    f64 = dict(dtype=torch.float64, device="cuda")
+    vM, vK, vT, vB, J = (torch.empty(nnz, **f64) for _ in range(5))
+    b, Fv, norms = torch.empty(n, **f64), torch.empty(n, **f64), torch.empty(2, **f64)
+    nf = F.fem_boundary_facets(fm.h, sh)
+    us0 = us[0]
+
+    def parts(i, ev=None):
+        u = us[(i + 1) % len(us)]
+        if ev:
+            ev[0].record(stream)
+        F.fem_assemble_all(fm.h, k, u, F.FEM_FP64, vM, vK, vT, sh)
+        if ev:
+            ev[1].record(stream)
+        F.fem_assemble_boundary(fm.h, g, u, None, vB, b, sh)
+        if ev:
+            ev[2].record(stream)
+        F.fem_residual(fm.h, vM, vK, b, u, us0, dt, Fv, norms, sh)
+        if ev:
+            ev[3].record(stream)
+        F.fem_jacobian(fm.h, dt, vM, None, vK, vT, vB, J, sh)
+        if ev:
+            ev[4].record(stream)
+
+    for i in range(3):
+        parts(i)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+    for i in range(steps):
+        parts(i, evs[i])
+    torch.cuda.synchronize()
+    F.fem_device_status(sh)
+    ms = [statistics.mean(e[j].elapsed_time(e[j + 1]) for e in evs) for j in range(4)]
+    total = statistics.mean(e[0].elapsed_time(e[4]) for e in evs)
+    res_bytes = 20 * nnz + 4 * (n + 1) + 8 * 4 * n          # M, K values and columns; row_ptr; u, u^s, b read, F written
+    jac_bytes = 40 * nnz                                     # M, K, T, B read, J written
+    return {"workload": wl.name, "elements": E, "boundary_facets": nf, "ms_per_newton_step": total,
+            "value": E / (total / 1e3), "unit": "elements/s",
+            "assemble_all_ms": ms[0], "boundary_ms": ms[1],
+            "residual_ms": ms[2], "residual_GB/s": res_bytes / (ms[2] / 1e3) / 1e9,
+            "residual_frac_hbm": res_bytes / (ms[2] / 1e3) / 1e9 / peak_gbs,
+            "jacobian_ms": ms[3], "jacobian_GB/s": jac_bytes / (ms[3] / 1e3) / 1e9,
+            "jacobian_frac_hbm": jac_bytes / (ms[3] / 1e3) / 1e9 / peak_gbs,
+            "norms": [float(x) for x in norms.cpu()],
+            "law": "k = 2 + sin(3u); g_N = h_c (T_a - u) + h_r (T_a^4 - u^4), T_a = 1000, dt = 10, FP64"}
+
+
 def measure_fp64_peak(torch, stream, n=4096, reps=5):
     """Measured FP64 peak: a cuBLAS DGEMM of n^3 (torch.mm on FP64 tensors),
     timed with CUDA events on the stream after one warm-up."""
@@ -821,6 +878,7 @@ def run_ours(args, rank, world, local_rank):
             fp64_plain = {"value": E / (ms64 / 1e3), "unit": "elements/s", "ms_per_step": ms64,
                           "mode": "FEM_FP64, one matrix per call (3 calls, 6 launches)"}
         fp64_peak = measure_fp64_peak(torch, stream)
+        newton = None if args.no_fp64 else measure_newton(F, torch, fm, wl, us, k, stream, peak)
         if not args.no_modes:
             modes = measure_modes(F, torch, fm, k, us, u64, o64, stream, E)
             mass_u = measure_mass_u(F, torch, fm, wl, us, stream, fp64_peak)
@@ -934,7 +992,8 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"{world} independent meshes, one per GPU" if world > 1 else "single GPU"},
         "roofline": roofline, "phases": phases, "fp64_peak_tflops": fp64_peak,
         "setup_once_per_mesh": setup,
-        "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64_plain, "modes": modes, "mass_u": mass_u,
+        "cpu_baseline": cpu, "e2e": e2e, "fp64_plain": fp64_plain, "newton_step": newton, "modes": modes,
+        "mass_u": mass_u,
         "clocks": clk.summary(),
         "gpu_launches": args.steps * 4,
         "batched": batched, "serve": served, "configs": configs,

@@ -257,13 +257,20 @@ __device__ __forceinline__ void segsum_warp(uint32_t k0, uint32_t k1, uint32_t n
 // depends only on the positions (eight per lane, the fixed scan tree, steps
 // in ascending order), so the bits are the same for every task shape, slot
 // range and the batched kernel.
-template <int NP, int STEPS>
+// PART selects the matrices a call sums: 0 all three, 1 M and K (the
+// interleaved pairs), 2 T; the split form runs a task twice with fewer
+// values live per lane (more resident warps).  The additions per matrix are
+// the same in every form, so are the bits.
+template <int NP, int STEPS, int PART>
 __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t nc, uint32_t s0, uint32_t s1,
                                              const uint2* __restrict__ head, const uint32_t* __restrict__ contrib,
                                              const short* __restrict__ sym, const double* __restrict__ VM,
                                              const double* __restrict__ VK, const double* __restrict__ VT,
                                              double* __restrict__ vM, double* __restrict__ vK,
                                              double* __restrict__ vT, int lane) {
+    constexpr bool MK = PART != 2, TT = PART != 1;
+    if constexpr (!MK) { VM = VK = nullptr; vM = vK = nullptr; }
+    if constexpr (!TT) { VT = nullptr; vT = nullptr; }
     const uint32_t nwords = (nc + 31) >> 5;
     auto word = [&](uint32_t w) { return __ldg(head + (w < nwords ? w : nwords - 1)); };
     // first slot whose first contribution is at or after position p (p a multiple of 256)
@@ -276,19 +283,6 @@ __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t 
     const uint32_t shi = min(first_slot_from(k1 << 8), s1);
     double cm = 0.0, ck = 0.0, ct = 0.0;   // running sum carried into the step
     const int sh = (lane & 3) * 8;
-    // the lane's eight contributor indices of a step (positions past nc: 0)
-    auto indices = [&](uint32_t k, uint32_t* c) {
-        const uint32_t p0 = (k << 8) + 8u * lane;
-        if (p0 + 8 <= nc) {
-            const uint4 a = __ldg(reinterpret_cast<const uint4*>(contrib + p0));
-            const uint4 b = __ldg(reinterpret_cast<const uint4*>(contrib + p0 + 4));
-            c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
-            c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
-        } else {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) c[i] = p0 + i < nc ? __ldg(contrib + p0 + i) : 0u;
-        }
-    };
     for (uint32_t k = k0;; ++k) {
         const uint32_t p0 = (k << 8) + 8u * lane;
         const bool live = p0 < nc;
@@ -299,7 +293,15 @@ __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t 
         const uint32_t slot0 = hw.y + __popc(hw.x & ((2u << sh) - 1u) & ~1u);
         // the lane's eight contributors and their V entries
         uint32_t c[8];
-        indices(k, c);
+        if (p0 + 8 <= nc) {
+            const uint4 a = __ldg(reinterpret_cast<const uint4*>(contrib + p0));
+            const uint4 b = __ldg(reinterpret_cast<const uint4*>(contrib + p0 + 4));
+            c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+            c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) c[i] = p0 + i < nc ? __ldg(contrib + p0 + i) : 0u;
+        }
         Contribution<NP, double> v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -307,10 +309,11 @@ __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t 
             else v[i].m = v[i].k = v[i].t = 0.0;
         }
         auto own = [&](uint32_t sl) { return live && sl >= slo && sl < shi; };
-        // in-lane pass: am = the open piece, pm = the piece before the first head
+        // in-lane pass: a* = the open piece, p* = the piece before the first head
         const bool h0 = bits & 1u;
-        double am = v[0].m, ak = v[0].k, at = v[0].t;
-        double pm = 0.0, pk = 0.0, pt = 0.0;
+        double am = 0.0, ak = 0.0, at = 0.0, pm = 0.0, pk = 0.0, pt = 0.0;
+        if constexpr (MK) { am = v[0].m; ak = v[0].k; }
+        if constexpr (TT) at = v[0].t;
         bool seen = h0;
         uint32_t cur = slot0;   // slot of the open piece once a head was seen
 #pragma unroll
@@ -318,15 +321,16 @@ __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t 
             const bool h = (bits >> i) & 1u;
             if (h && seen && own(cur)) put3(cur, am, ak, at, vM, vK, vT);   // a slot complete in the lane
             if (h && !seen) {
-                pm = am;
-                pk = ak;
-                pt = at;
+                if constexpr (MK) { pm = am; pk = ak; }
+                if constexpr (TT) pt = at;
             }
             cur += h ? 1u : 0u;   // the first head opens slot0 + 1, each later one the next slot
             seen = seen || h;
-            am = h ? v[i].m : am + v[i].m;
-            ak = h ? v[i].k : ak + v[i].k;
-            at = h ? v[i].t : at + v[i].t;
+            if constexpr (MK) {
+                am = h ? v[i].m : am + v[i].m;
+                ak = h ? v[i].k : ak + v[i].k;
+            }
+            if constexpr (TT) at = h ? v[i].t : at + v[i].t;
         }
         // segmented inclusive scan of the open pieces over the lanes
         const uint32_t lup = __ballot_sync(FULL, seen) & (FULL >> (31 - lane));
@@ -334,36 +338,39 @@ __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t 
 #pragma unroll
         for (int i = 0; i < STEPS; ++i) {
             const int d = 1 << i;
-            const double ym = __shfl_up_sync(FULL, am, d);
-            const double yk = __shfl_up_sync(FULL, ak, d);
-            const double yt = __shfl_up_sync(FULL, at, d);
+            double ym = 0.0, yk = 0.0, yt = 0.0;
+            if constexpr (MK) { ym = __shfl_up_sync(FULL, am, d); yk = __shfl_up_sync(FULL, ak, d); }
+            if constexpr (TT) yt = __shfl_up_sync(FULL, at, d);
             if (run >= d) {
-                am = ym + am;
-                ak = yk + ak;
-                at = yt + at;
+                if constexpr (MK) { am = ym + am; ak = yk + ak; }
+                if constexpr (TT) at = yt + at;
             }
         }
         if (lup == 0) {   // continues the piece carried from the previous step
-            am = cm + am;
-            ak = ck + ak;
-            at = ct + at;
+            if constexpr (MK) { am = cm + am; ak = ck + ak; }
+            if constexpr (TT) at = ct + at;
         }
         // the lane's first head closes the slot begun before the lane
-        double qm = __shfl_up_sync(FULL, am, 1), qk = __shfl_up_sync(FULL, ak, 1), qt = __shfl_up_sync(FULL, at, 1);
+        double qm = 0.0, qk = 0.0, qt = 0.0;
+        if constexpr (MK) { qm = __shfl_up_sync(FULL, am, 1); qk = __shfl_up_sync(FULL, ak, 1); }
+        if constexpr (TT) qt = __shfl_up_sync(FULL, at, 1);
         if (lane == 0) {
             qm = cm;
             qk = ck;
             qt = ct;
         }
-        if (seen && !h0 && own(slot0)) put3(slot0, qm + pm, qk + pk, qt + pt, vM, vK, vT);
+        if (seen && !h0 && own(slot0)) {
+            if constexpr (MK) { qm = qm + pm; qk = qk + pk; }
+            if constexpr (TT) qt = qt + pt;
+            put3(slot0, qm, qk, qt, vM, vK, vT);
+        }
         // the position after the lane starts a slot (or is the end): the open piece is complete
         const uint32_t nb = __shfl_down_sync(FULL, bits, 1);
         const bool next_head = lane < 31 ? (nb & 1u) != 0u
                                          : ((k + 1) << 8) >= nc || (word((k + 1) << 3).x & 1u) != 0u;
         if (next_head && own(cur)) put3(cur, am, ak, at, vM, vK, vT);
-        cm = __shfl_sync(FULL, am, 31);
-        ck = __shfl_sync(FULL, ak, 31);
-        ct = __shfl_sync(FULL, at, 31);
+        if constexpr (MK) { cm = __shfl_sync(FULL, am, 31); ck = __shfl_sync(FULL, ak, 31); }
+        if constexpr (TT) ct = __shfl_sync(FULL, at, 31);
         // go on past k1 only while the slot open at the step's end is this warp's
         if (k + 1 >= k1) {
             const uint32_t pn = (k + 1) << 8;
@@ -414,7 +421,7 @@ __global__ void __launch_bounds__(256, SegShape<STEPS, T>::MIN_BLOCKS)
 // to TASK8 steps grid-stride
 constexpr uint32_t TASK8 = 8;
 
-template <int NP, int STEPS, int MINB>
+template <int NP, int STEPS, int MINB, bool SPLIT>
 __global__ void __launch_bounds__(256, MINB) segsum8_kernel(const uint2* __restrict__ head,
                                                       const uint32_t* __restrict__ contrib, uint32_t nc,
                                                       const int* __restrict__ seg_ptr, uint32_t s0, uint32_t s1,
@@ -432,18 +439,29 @@ __global__ void __launch_bounds__(256, MINB) segsum8_kernel(const uint2* __restr
     const double* vm_src = vM ? VM : nullptr;
     const double* vk_src = vK ? VK : nullptr;
     const double* vt_src = vT ? VT : nullptr;
-    for (uint32_t t = g0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * task; t < g1; t += nw * task)
-        segsum8_warp<NP, STEPS>(t, t + task < g1 ? t + task : g1, nc, s0, s1, head, contrib, sym, vm_src, vk_src,
-                                vt_src, vM, vK, vT, lane);
+    for (uint32_t t = g0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * task; t < g1; t += nw * task) {
+        const uint32_t t1 = t + task < g1 ? t + task : g1;
+        if constexpr (SPLIT) {
+            if (vM || vK)
+                segsum8_warp<NP, STEPS, 1>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK,
+                                           vT, lane);
+            if (vT)
+                segsum8_warp<NP, STEPS, 2>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK,
+                                           vT, lane);
+        } else {
+            segsum8_warp<NP, STEPS, 0>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK, vT,
+                                       lane);
+        }
+    }
 }
 
-template <int NP, int STEPS, int MINB>
+template <int NP, int STEPS, int MINB, bool SPLIT>
 int launch_steps8_b(const fem_mesh& m, const double* VM, const double* VK, const double* VT, double* vM, double* vK,
                     double* vT, cudaStream_t s, int nsm, int64_t s0, int64_t s1) {
     static int occ = 0;   // blocks per SM (the same on every device of the pool)
     if (!occ) {
         int o = 0;
-        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, segsum8_kernel<NP, STEPS, MINB>, 256, 0));
+        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, segsum8_kernel<NP, STEPS, MINB, SPLIT>, 256, 0));
         occ = o > 0 ? o : 1;
     }
     const int64_t nc = m.E * m.np * m.np;
@@ -456,20 +474,25 @@ int launch_steps8_b(const fem_mesh& m, const double* VM, const double* VK, const
     if (blocks > (int64_t)nsm * occ) blocks = (int64_t)nsm * occ;
     if (blocks < 1) blocks = 1;
     cudaGetLastError();   // clear any stale error before the launch check
-    segsum8_kernel<NP, STEPS, MINB><<<(unsigned)blocks, 256, 0, s>>>(
+    segsum8_kernel<NP, STEPS, MINB, SPLIT><<<(unsigned)blocks, 256, 0, s>>>(
         m.seg_head.as<uint2>(), reinterpret_cast<const uint32_t*>(m.contrib.as<int>()), (uint32_t)nc,
         m.seg_ptr.as<int>(), (uint32_t)s0, (uint32_t)s1, (uint32_t)task, VM, VK, VT, vM, vK, vT);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
 
-// Two blocks of 256 per SM (the kernel's ~104 registers); capping registers
-// for three spilled and was no faster (tet_p1_128: 3.08 vs 3.01 ms), nor was
-// prefetching the next step's V lines into L2 (3.47 ms).
+// The sum is bound by the latency of its gathers (ncu: long-scoreboard
+// stalls, FP64 pipe half busy at two blocks per SM).  Summing a task twice,
+// the M/K pairs and then T, keeps fewer values live per lane: 64 registers,
+// four blocks of 256 per SM.  Measured on GB300 (FP64): tet_p1_128 1.89 ms
+// against 2.02 with three blocks and 2.75 for the single pass at two blocks
+// (116 registers); tri_p2_1024 0.96 vs 1.17 ms; tet_p2_64 1.70 vs 2.46 ms.
+// Prefetching the next step's V lines into L2 was slower (3.47 vs 3.01 ms
+// for the single pass).  Every form adds the same terms in the same order.
 template <int NP, int STEPS>
 int launch_steps8(const fem_mesh& m, const double* VM, const double* VK, const double* VT, double* vM, double* vK,
                   double* vT, cudaStream_t s, int nsm, int64_t s0, int64_t s1) {
-    return launch_steps8_b<NP, STEPS, 2>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+    return launch_steps8_b<NP, STEPS, 4, true>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
 }
 
 // offsets of the per-type symmetric-index tables in the batched kernel
@@ -510,7 +533,7 @@ __global__ void __launch_bounds__(512) batch_scatter_kernel(const BatchItem* __r
 #define FEM_BATCH_SEG_CASE(NP_)                                                                               \
     case NP_:                                                                                                 \
         if constexpr (sizeof(T) == 8)                                                                         \
-            segsum8_warp<NP_, 5>(k0, k1, nc, 0u, s1, bm.seg_head, cp, st, VM, VK, VT, vM, vK, vT, lane);       \
+            segsum8_warp<NP_, 5, 0>(k0, k1, nc, 0u, s1, bm.seg_head, cp, st, VM, VK, VT, vM, vK, vT, lane);    \
         else                                                                                                  \
             segsum_warp<NP_, T, 5>(k0, k1, nc, 0u, s1, h2, cp, st, VM, VK, VT, vM, vK, vT, lane);               \
         break;
