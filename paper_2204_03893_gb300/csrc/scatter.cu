@@ -261,13 +261,12 @@ __device__ __forceinline__ void segsum_warp(uint32_t k0, uint32_t k1, uint32_t n
 // interleaved pairs), 2 T; the split form runs a task twice with fewer
 // values live per lane (more resident warps).  The additions per matrix are
 // the same in every form, so are the bits.
-template <int NP, int STEPS, int PART>
+template <int NP, int STEPS, int PART, typename T>
 __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t nc, uint32_t s0, uint32_t s1,
                                              const uint2* __restrict__ head, const uint32_t* __restrict__ contrib,
-                                             const short* __restrict__ sym, const double* __restrict__ VM,
-                                             const double* __restrict__ VK, const double* __restrict__ VT,
-                                             double* __restrict__ vM, double* __restrict__ vK,
-                                             double* __restrict__ vT, int lane) {
+                                             const short* __restrict__ sym, const T* __restrict__ VM,
+                                             const T* __restrict__ VK, const T* __restrict__ VT,
+                                             T* __restrict__ vM, T* __restrict__ vK, T* __restrict__ vT, int lane) {
     constexpr bool MK = PART != 2, TT = PART != 1;
     if constexpr (!MK) { VM = VK = nullptr; vM = vK = nullptr; }
     if constexpr (!TT) { VT = nullptr; vT = nullptr; }
@@ -281,7 +280,7 @@ __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t 
     };
     const uint32_t slo = max(first_slot_from(k0 << 8), s0);
     const uint32_t shi = min(first_slot_from(k1 << 8), s1);
-    double cm = 0.0, ck = 0.0, ct = 0.0;   // running sum carried into the step
+    T cm = T(0), ck = T(0), ct = T(0);   // running sum carried into the step
     const int sh = (lane & 3) * 8;
     for (uint32_t k = k0;; ++k) {
         const uint32_t p0 = (k << 8) + 8u * lane;
@@ -302,16 +301,16 @@ __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t 
 #pragma unroll
             for (int i = 0; i < 8; ++i) c[i] = p0 + i < nc ? __ldg(contrib + p0 + i) : 0u;
         }
-        Contribution<NP, double> v[8];
+        Contribution<NP, T> v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             if (p0 + i < nc) v[i].load(c[i], sym, VM, VK, VT);
-            else v[i].m = v[i].k = v[i].t = 0.0;
+            else v[i].m = v[i].k = v[i].t = T(0);
         }
         auto own = [&](uint32_t sl) { return live && sl >= slo && sl < shi; };
         // in-lane pass: a* = the open piece, p* = the piece before the first head
         const bool h0 = bits & 1u;
-        double am = 0.0, ak = 0.0, at = 0.0, pm = 0.0, pk = 0.0, pt = 0.0;
+        T am = T(0), ak = T(0), at = T(0), pm = T(0), pk = T(0), pt = T(0);
         if constexpr (MK) { am = v[0].m; ak = v[0].k; }
         if constexpr (TT) at = v[0].t;
         bool seen = h0;
@@ -338,7 +337,7 @@ __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t 
 #pragma unroll
         for (int i = 0; i < STEPS; ++i) {
             const int d = 1 << i;
-            double ym = 0.0, yk = 0.0, yt = 0.0;
+            T ym = T(0), yk = T(0), yt = T(0);
             if constexpr (MK) { ym = __shfl_up_sync(FULL, am, d); yk = __shfl_up_sync(FULL, ak, d); }
             if constexpr (TT) yt = __shfl_up_sync(FULL, at, d);
             if (run >= d) {
@@ -351,7 +350,7 @@ __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t 
             if constexpr (TT) at = ct + at;
         }
         // the lane's first head closes the slot begun before the lane
-        double qm = 0.0, qk = 0.0, qt = 0.0;
+        T qm = T(0), qk = T(0), qt = T(0);
         if constexpr (MK) { qm = __shfl_up_sync(FULL, am, 1); qk = __shfl_up_sync(FULL, ak, 1); }
         if constexpr (TT) qt = __shfl_up_sync(FULL, at, 1);
         if (lane == 0) {
@@ -421,14 +420,13 @@ __global__ void __launch_bounds__(256, SegShape<STEPS, T>::MIN_BLOCKS)
 // to TASK8 steps grid-stride
 constexpr uint32_t TASK8 = 8;
 
-template <int NP, int STEPS, int MINB, bool SPLIT>
+template <int NP, int STEPS, int MINB, bool SPLIT, typename T>
 __global__ void __launch_bounds__(256, MINB) segsum8_kernel(const uint2* __restrict__ head,
                                                       const uint32_t* __restrict__ contrib, uint32_t nc,
                                                       const int* __restrict__ seg_ptr, uint32_t s0, uint32_t s1,
-                                                      uint32_t task, const double* __restrict__ VM,
-                                                      const double* __restrict__ VK, const double* __restrict__ VT,
-                                                      double* __restrict__ vM, double* __restrict__ vK,
-                                                      double* __restrict__ vT) {
+                                                      uint32_t task, const T* __restrict__ VM,
+                                                      const T* __restrict__ VK, const T* __restrict__ VT,
+                                                      T* __restrict__ vM, T* __restrict__ vK, T* __restrict__ vT) {
     __shared__ short sym[NP * NP];
     fill_sym_table<NP>(sym);
     __syncthreads();
@@ -436,32 +434,32 @@ __global__ void __launch_bounds__(256, MINB) segsum8_kernel(const uint2* __restr
     const uint32_t a = (uint32_t)__ldg(seg_ptr + s0), b = (uint32_t)__ldg(seg_ptr + s1);
     const uint32_t g0 = a >> 8, g1 = (b + 255) >> 8;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    const double* vm_src = vM ? VM : nullptr;
-    const double* vk_src = vK ? VK : nullptr;
-    const double* vt_src = vT ? VT : nullptr;
+    const T* vm_src = vM ? VM : nullptr;
+    const T* vk_src = vK ? VK : nullptr;
+    const T* vt_src = vT ? VT : nullptr;
     for (uint32_t t = g0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * task; t < g1; t += nw * task) {
         const uint32_t t1 = t + task < g1 ? t + task : g1;
         if constexpr (SPLIT) {
             if (vM || vK)
-                segsum8_warp<NP, STEPS, 1>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK,
+                segsum8_warp<NP, STEPS, 1, T>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK,
                                            vT, lane);
             if (vT)
-                segsum8_warp<NP, STEPS, 2>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK,
+                segsum8_warp<NP, STEPS, 2, T>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK,
                                            vT, lane);
         } else {
-            segsum8_warp<NP, STEPS, 0>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK, vT,
+            segsum8_warp<NP, STEPS, 0, T>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK, vT,
                                        lane);
         }
     }
 }
 
-template <int NP, int STEPS, int MINB, bool SPLIT>
-int launch_steps8_b(const fem_mesh& m, const double* VM, const double* VK, const double* VT, double* vM, double* vK,
-                    double* vT, cudaStream_t s, int nsm, int64_t s0, int64_t s1) {
+template <int NP, int STEPS, int MINB, bool SPLIT, typename T>
+int launch_steps8_b(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s,
+                    int nsm, int64_t s0, int64_t s1) {
     static int occ = 0;   // blocks per SM (the same on every device of the pool)
     if (!occ) {
         int o = 0;
-        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, segsum8_kernel<NP, STEPS, MINB, SPLIT>, 256, 0));
+        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, segsum8_kernel<NP, STEPS, MINB, SPLIT, T>, 256, 0));
         occ = o > 0 ? o : 1;
     }
     const int64_t nc = m.E * m.np * m.np;
@@ -474,7 +472,7 @@ int launch_steps8_b(const fem_mesh& m, const double* VM, const double* VK, const
     if (blocks > (int64_t)nsm * occ) blocks = (int64_t)nsm * occ;
     if (blocks < 1) blocks = 1;
     cudaGetLastError();   // clear any stale error before the launch check
-    segsum8_kernel<NP, STEPS, MINB, SPLIT><<<(unsigned)blocks, 256, 0, s>>>(
+    segsum8_kernel<NP, STEPS, MINB, SPLIT, T><<<(unsigned)blocks, 256, 0, s>>>(
         m.seg_head.as<uint2>(), reinterpret_cast<const uint32_t*>(m.contrib.as<int>()), (uint32_t)nc,
         m.seg_ptr.as<int>(), (uint32_t)s0, (uint32_t)s1, (uint32_t)task, VM, VK, VT, vM, vK, vT);
     FEM_CUDA_TRY(cudaGetLastError());
@@ -489,10 +487,10 @@ int launch_steps8_b(const fem_mesh& m, const double* VM, const double* VK, const
 // (116 registers); tri_p2_1024 0.96 vs 1.17 ms; tet_p2_64 1.70 vs 2.46 ms.
 // Prefetching the next step's V lines into L2 was slower (3.47 vs 3.01 ms
 // for the single pass).  Every form adds the same terms in the same order.
-template <int NP, int STEPS>
-int launch_steps8(const fem_mesh& m, const double* VM, const double* VK, const double* VT, double* vM, double* vK,
-                  double* vT, cudaStream_t s, int nsm, int64_t s0, int64_t s1) {
-    return launch_steps8_b<NP, STEPS, 4, true>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+template <int NP, int STEPS, typename T>
+int launch_steps8(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s,
+                  int nsm, int64_t s0, int64_t s1) {
+    return launch_steps8_b<NP, STEPS, 4, true, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
 }
 
 // offsets of the per-type symmetric-index tables in the batched kernel
@@ -533,7 +531,7 @@ __global__ void __launch_bounds__(512) batch_scatter_kernel(const BatchItem* __r
 #define FEM_BATCH_SEG_CASE(NP_)                                                                               \
     case NP_:                                                                                                 \
         if constexpr (sizeof(T) == 8)                                                                         \
-            segsum8_warp<NP_, 5, 0>(k0, k1, nc, 0u, s1, bm.seg_head, cp, st, VM, VK, VT, vM, vK, vT, lane);    \
+            segsum8_warp<NP_, 5, 0, double>(k0, k1, nc, 0u, s1, bm.seg_head, cp, st, VM, VK, VT, vM, vK, vT, lane);    \
         else                                                                                                  \
             segsum_warp<NP_, T, 5>(k0, k1, nc, 0u, s1, h2, cp, st, VM, VK, VT, vM, vK, vT, lane);               \
         break;
