@@ -361,3 +361,27 @@ def batched_meshes(count: int = 64, seed: int = 4, e_min: float = 1e3, e_max: fl
         a, b = rng.uniform(0.0, 1.0, 2)
         out.append(Workload(f"batch{idx}_{mesh.name}", mesh, u, Coeff("poly", (1.0, float(a), float(b), 0.0, 0.0))))
     return out
+
+
+def curved(mesh: Mesh, amp: float = 0.1, seed: int = 0) -> Mesh:
+    """A copy with curved elements for isoparametric mappings: every
+    higher-order node (edge, face, interior) off the domain's boundary is
+    moved by a smooth random field of size amp * h / p (h the mean edge
+    length of the first element); vertices and nodes on the boundary stay, so
+    neighbouring elements still share their curved sides and the elements
+    still tile the unit square / cube."""
+    d = mesh.d
+    X = mesh.coords.copy()
+    verts = np.unique(mesh.conn[:, : d + 1])
+    ho = np.ones(mesh.n_nodes, dtype=bool)
+    ho[verts] = False
+    inner = np.all((X > 1e-12) & (X < 1 - 1e-12), axis=1)
+    move = ho & inner
+    v0 = mesh.coords[mesh.conn[0, : d + 1]]
+    h = float(np.mean([np.linalg.norm(v0[a] - v0[b]) for a in range(d + 1) for b in range(a + 1, d + 1)]))
+    rng = np.random.default_rng(seed)
+    k = rng.integers(1, 3, size=(d, d))
+    ph = rng.uniform(0, 2 * np.pi, size=d)
+    disp = np.stack([np.sin(2 * np.pi * (X @ k[a]) + ph[a]) for a in range(d)], axis=1)
+    X[move] += amp * h / mesh.p * disp[move]
+    return Mesh(d=d, p=mesh.p, coords=X, conn=mesh.conn.copy(), name=mesh.name + "_curved")

@@ -89,6 +89,10 @@ def lib():
             L.oracle_entries.restype = C.c_int
             L.oracle_assemble_mass_u.argtypes = [C.c_void_p, C.c_int, C.c_int, dp, C.c_int, dp, dp] + [dp] * 4
             L.oracle_assemble_mass_u.restype = C.c_int
+            L.oracle_set_isoparametric.argtypes = [C.c_void_p, C.c_int]
+            L.oracle_set_isoparametric.restype = None
+            L.oracle_set_conductivity_field.argtypes = [C.c_void_p, dp]
+            L.oracle_set_conductivity_field.restype = C.c_int
             L.oracle_set_conductivity.argtypes = [C.c_void_p, dp]
             L.oracle_set_conductivity.restype = None
             _lib = L
@@ -163,6 +167,23 @@ class Oracle:
         becomes k(u) c and A_e = B_e^-1 c B_e^-T (None: identity)."""
         cc = None if c is None else np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(self.d, self.d))
         lib().oracle_set_conductivity(self._h, _dp(cc))
+        return self
+
+    def set_isoparametric(self, on: bool = True):
+        """Map every element through all its nodes (curved elements): the
+        Jacobian, its determinant and A depend on the quadrature point."""
+        lib().oracle_set_isoparametric(self._h, 1 if on else 0)
+        return self
+
+    def set_conductivity_field(self, cf=None):
+        """Conductivity tensors per quadrature point of the degree-2p rule,
+        shape (E, n_q, d, d) (None: clear)."""
+        if cf is None:
+            lib().oracle_set_conductivity_field(self._h, None)
+            return self
+        self._cf = np.ascontiguousarray(cf, dtype=np.float64)
+        if lib().oracle_set_conductivity_field(self._h, _dp(self._cf)) != 0:
+            raise RuntimeError("oracle_set_conductivity_field failed")
         return self
 
     def nnz(self) -> int:

@@ -296,6 +296,12 @@ typedef struct {
     /* constant conductivity tensor c (d x d, SPD; identity unless set):
      * the conductivity is k(u) c (Section 7, anisotropic conductivity) */
     double cond[3][3];
+    /* per-quadrature-point geometry (Section 7): iso = 1 maps each element
+     * through all its nodes, x(xhat) = sum_i x_i phi_i(xhat), so B depends
+     * on the point; cfield (E x n_q x d x d, row-major per point, owned) a
+     * conductivity tensor per quadrature point of the degree-2p rule */
+    int iso;
+    double* cfield;
 } octx;
 
 void* oracle_create(int d, int p, int n_nodes, int n_elems, const double* coords, const int* conn) {
@@ -325,7 +331,7 @@ void* oracle_create(int d, int p, int n_nodes, int n_elems, const double* coords
 void oracle_destroy(void* h) {
     octx* c = (octx*)h;
     if (!c) return;
-    free(c->row_ptr); free(c->col_idx); free(c->inc_ptr); free(c->inc_el);
+    free(c->row_ptr); free(c->col_idx); free(c->inc_ptr); free(c->inc_el); free(c->cfield);
     free(c);
 }
 
@@ -413,6 +419,8 @@ void oracle_set_conductivity(void* h, const double* cd) {
 
 /* det, |det| and A = B^-1 c B^-T of element e (c the conductivity tensor;
  * the identity gives (B^T B)^-1) */
+static double invert_a(int d, double B[3][3], double cond[3][3], double A[3][3]);
+
 static double geometry(const octx* c, int e, double A[3][3]) {
     int d = c->d;
     const int* v = c->conn + (long long)e * c->np;
@@ -420,6 +428,13 @@ static double geometry(const octx* c, int e, double A[3][3]) {
     for (int col = 0; col < d; ++col)
         for (int row = 0; row < d; ++row)
             B[row][col] = c->X[(long long)v[col + 1] * d + row] - c->X[(long long)v[0] * d + row];
+    double cond[3][3];
+    memcpy(cond, c->cond, sizeof(cond));
+    return invert_a(d, B, cond, A);
+}
+
+/* det B and A = B^-1 cond B^-T (cofactor inverse) */
+static double invert_a(int d, double B[3][3], double cond[3][3], double A[3][3]) {
     double det, Bi[3][3];
     if (d == 2) {
         det = B[0][0] * B[1][1] - B[0][1] * B[1][0];
@@ -445,10 +460,60 @@ static double geometry(const octx* c, int e, double A[3][3]) {
         for (int b = 0; b < d; ++b) {
             double s = 0.0;
             for (int k = 0; k < d; ++k)
-                for (int l = 0; l < d; ++l) s += Bi[a][k] * c->cond[k][l] * Bi[b][l];
+                for (int l = 0; l < d; ++l) s += Bi[a][k] * cond[k][l] * Bi[b][l];
             A[a][b] = s;
         }
     return det;
+}
+
+/* The geometry at quadrature point q of element e (Section 7): B_q =
+ * sum_i x_i (J_q)_i^T through all the element's nodes for an isoparametric
+ * mesh (the vertices' edge vectors otherwise), and the point's conductivity
+ * tensor when a field is set (the mesh's constant tensor otherwise):
+ * A_q = B_q^-1 c_q B_q^-T.  Returns det B_q. */
+static double geometry_q(const octx* c, const otab* t, int e, int q, double A[3][3]) {
+    int d = c->d, np = c->np;
+    const int* v = c->conn + (long long)e * np;
+    double B[3][3];
+    if (c->iso) {
+        for (int row = 0; row < d; ++row)
+            for (int col = 0; col < d; ++col) {
+                double s = 0.0;
+                for (int i = 0; i < np; ++i) s += c->X[(long long)v[i] * d + row] * t->J[q][i][col];
+                B[row][col] = s;
+            }
+    } else {
+        for (int col = 0; col < d; ++col)
+            for (int row = 0; row < d; ++row)
+                B[row][col] = c->X[(long long)v[col + 1] * d + row] - c->X[(long long)v[0] * d + row];
+    }
+    double cond[3][3];
+    if (c->cfield) {
+        const double* cf = c->cfield + ((long long)e * t->nq + q) * d * d;
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) cond[a][b] = cf[a * d + b];
+    } else {
+        memcpy(cond, c->cond, sizeof(cond));
+    }
+    return invert_a(d, B, cond, A);
+}
+
+/* Exported: isoparametric mapping on (1) or off (0). */
+void oracle_set_isoparametric(void* h, int on) { ((octx*)h)->iso = on ? 1 : 0; }
+
+/* Exported: conductivity tensors per quadrature point of the degree-2p rule
+ * (E x n_q x d x d, copied), or NULL to clear. */
+int oracle_set_conductivity_field(void* h, const double* cf) {
+    octx* c = (octx*)h;
+    free(c->cfield);
+    c->cfield = NULL;
+    if (!cf) return 0;
+    int nq = oracle_rule(c->d, 2 * c->p, NULL, NULL);
+    size_t n = (size_t)c->E * nq * c->d * c->d;
+    c->cfield = (double*)malloc(sizeof(double) * (n ? n : 1));
+    if (!c->cfield) return -1;
+    memcpy(c->cfield, cf, sizeof(double) * n);
+    return 0;
 }
 
 /* Local matrices of element e (dense n_p x n_p, row = test index).  If
@@ -475,6 +540,11 @@ static void element(const octx* c, const otab* t, int e, double m, int kkind, co
     for (int a = 0; a < d; ++a)
         for (int bb = 0; bb < d; ++bb) Ab[a][bb] = sqrt(fabs(A[a][a] * A[bb][bb]));
     for (int q = 0; q < t->nq; ++q) {
+        if (c->iso || c->cfield) {   /* per-point geometry (Section 7) */
+            b = fabs(geometry_q(c, t, e, q, A));
+            for (int a = 0; a < d; ++a)
+                for (int bb = 0; bb < d; ++bb) Ab[a][bb] = sqrt(fabs(A[a][a] * A[bb][bb]));
+        }
         const double* phi = t->phi[q];
         double uq = 0.0;
         for (int i = 0; i < np; ++i) uq += phi[i] * ue[i];
@@ -731,6 +801,7 @@ int oracle_assemble_mass_u(void* h, int deg, int mkind, const double* mp, int nm
         memset(Mc, 0, sizeof(double) * np * np * np);
         memset(aMc, 0, sizeof(double) * np * np * np);
         for (int q = 0; q < t.nq; ++q) {
+            if (c->iso || c->cfield) b = fabs(geometry_q(c, &t, e, q, A));   /* per-point geometry (Section 7) */
             const double* phi = t.phi[q];
             double uq = 0.0;
             for (int i = 0; i < np; ++i) uq += phi[i] * ue[i];
@@ -876,6 +947,7 @@ int oracle_boundary(void* h, int gkind, const double* gp, int ngp, const double*
                     double* absB, double* absb) {
     octx* c = (octx*)h;
     if (build_pattern(c)) return -1;
+    if (c->iso) return -3;   /* straight facets only */
     int d = c->d, p = c->p, np = c->np, nv = d + 1;
     int nb = oracle_boundary_facets(h, NULL, NULL);
     if (nb < 0) return -1;
