@@ -204,6 +204,27 @@ int fem_assemble_all(fem_mesh* mesh, const fem_coeff* k, const void* u, int prec
  * formed earlier must be formed again before fem_sum_elements. */
 int fem_mesh_set_conductivity(fem_mesh* mesh, const double* c, void* stream);
 
+/* Per-quadrature-point geometry (Section 7: with isoparametric mappings the
+ * Jacobian depends on the quadrature point, so each element carries n_q
+ * determinants and d^2 n_q Jacobian entries; an anisotropic conductivity
+ * may vary over the points, A_qe = B^-1 c_q B^-T; only X changes).
+ * fem_mesh_set_isoparametric(on = 1) maps every element through all its
+ * nodes, x(xhat) = sum_i x_i phi_i(xhat): the higher-order nodes may sit off
+ * their affine positions (curved elements).  on = 0 restores the affine
+ * map.  fem_mesh_set_conductivity_field sets a d x d conductivity tensor
+ * per quadrature point of the mesh's rule (n_elems x n_q x d x d,
+ * row-major per point, host or device, copied; symmetric positive definite,
+ * not checked on the device), overriding the constant tensor; NULL clears
+ * it.  Either call recomputes a per-point geometry cache (|det B_q| and A_q
+ * per element and point) on `stream` and waits for it (FEM_EDEGENERATE if
+ * some det B_q vanishes); the pattern is kept; element matrices formed
+ * earlier must be formed again.  While a mesh is in per-point mode its
+ * products run on the SIMT pipes: FEM_FP64 and FEM_FP32 (the tensor-core
+ * precisions, batches and, for isoparametric meshes, the boundary terms
+ * return FEM_EINVAL). */
+int fem_mesh_set_isoparametric(fem_mesh* mesh, int on, void* stream);
+int fem_mesh_set_conductivity_field(fem_mesh* mesh, const double* c_field, void* stream);
+
 /* u-dependent mass and its Newton term (Section 2 with a coefficient
  * m = m(u_h) in the mass; Section 5, where the Jacobian of the implicit
  * Euler residual holds  M(u) + (mass tensor) o_2 (u - u^s);  Section 5.1,

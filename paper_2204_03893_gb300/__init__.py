@@ -146,6 +146,8 @@ _SIGS = {
                                   C.c_void_p], C.c_int),
     "fem_form_elements": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_int, C.c_void_p], C.c_int),
     "fem_law_eval": ([C.POINTER(fem_coeff), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "fem_mesh_set_isoparametric": ([C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "fem_mesh_set_conductivity_field": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fem_boundary_facets": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
     "fem_get_boundary_facets": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fem_assemble_boundary": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -323,6 +325,18 @@ def fem_assemble_all_noalloc(mesh: int, k, d_u, d_vM, d_vK, d_vT, stream=None) -
 def fem_law_eval(k, d_u, n: int, d_k, d_dk, stream=None) -> None:
     """k(u) and k'(u) of a law at n device values, in FP64 on the GPU."""
     _check(lib().fem_law_eval(C.byref(k), _vp(d_u), int(n), _vp(d_k), _vp(d_dk), _stream(stream)))
+
+
+def fem_mesh_set_isoparametric(mesh: int, on: bool = True, stream=None) -> None:
+    _check(lib().fem_mesh_set_isoparametric(mesh, 1 if on else 0, _stream(stream)))
+
+
+def fem_mesh_set_conductivity_field(mesh: int, c_field=None, stream=None) -> None:
+    """c_field: (n_elems, n_q, d, d) float64 (numpy or a device tensor), or None."""
+    if c_field is not None and not hasattr(c_field, "data_ptr"):
+        import numpy as _np
+        c_field = _np.ascontiguousarray(c_field, dtype=_np.float64)
+    _check(lib().fem_mesh_set_conductivity_field(mesh, _vp(c_field), _stream(stream)))
 
 
 def fem_boundary_facets(mesh: int, stream=None) -> int:

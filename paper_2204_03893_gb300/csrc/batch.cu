@@ -209,6 +209,9 @@ int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts,
     for (int i = 0; i < n; ++i) {
         if (!meshes[i]) return fail(FEM_EINVAL, "NULL mesh in batch");
         if (!meshes[i]->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run on every mesh");
+        if (meshes[i]->perq)
+            return fail(FEM_EINVAL, "batches take meshes with per-element geometry (no isoparametric mapping or "
+                                    "conductivity field)");
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int rc;

@@ -161,6 +161,9 @@ int form_t(fem_mesh* m, const fem_coeff* k, const double* ud, int prec, int mask
         rc = element_simt_fp64(*m, kd, ud, VM, VK, VT, s, e0, e1);
     } else {
         const double* us = (mask & 6) ? ud : nullptr;
+        if (m->perq && prec != FEM_FP32)
+            return fail(FEM_EINVAL, "per-point geometry (isoparametric or a conductivity field) runs FEM_FP64 and "
+                                    "FEM_FP32 only");
         rc = prec == FEM_TF32X3   ? element_tc_tf32x3(*m, kd, us, VM, VK, VT, s, e0, e1)
              : prec == FEM_BF16X3 ? element_tc_bf16(*m, kd, us, VM, VK, VT, 2, s, e0, e1)
              : prec == FEM_BF16X6 ? element_tc_bf16(*m, kd, us, VM, VK, VT, 3, s, e0, e1)
@@ -304,7 +307,7 @@ CoeffDev coeff_to_device(const fem_coeff* k) { return to_dev(k); }
 size_t fem_mesh::device_bytes() const {
     const fem::DevBuf* bufs[] = {&coords, &conn, &geo64, &geo32, &row_ptr, &col_idx, &seg_ptr, &contrib, &slot,
                                  &seg_head, &inc_ptr, &inc, &VMK, &VT, &u_stage, &out_stage, &bfacet, &bnode_ptr,
-                                 &bnode_inc, &bscratch, &npart};
+                                 &bnode_inc, &bscratch, &npart, &cfield, &geoq64, &geoq32};
     size_t t = 0;
     for (auto* b : bufs) t += b->bytes;
     return t;
@@ -398,7 +401,7 @@ int fem_mesh_destroy(fem_mesh* m) {
     cudaDeviceSynchronize();
     fem::DevBuf* bufs[] = {&m->coords, &m->conn, &m->geo64, &m->geo32, &m->row_ptr, &m->col_idx, &m->seg_ptr,
                            &m->contrib, &m->slot, &m->seg_head, &m->inc_ptr, &m->inc, &m->VMK, &m->VT, &m->u_stage,
-                           &m->out_stage, &m->bfacet, &m->bnode_ptr, &m->bnode_inc, &m->bscratch, &m->npart};
+                           &m->out_stage, &m->bfacet, &m->bnode_ptr, &m->bnode_inc, &m->bscratch, &m->npart, &m->cfield, &m->geoq64, &m->geoq32};
     for (auto* b : bufs) buf_free(*b, nullptr);
     if (m->copy_stream) {
         for (auto ev : m->copy_ev)
@@ -508,7 +511,48 @@ int fem_mesh_set_conductivity(fem_mesh* m, const double* c, void* stream) {
     for (int i = 0; i < 9; ++i) m->cond[i] = cn[i];
     m->v_prec = -1;   // formed element matrices used the previous tensor
     m->v_mask = 0;
-    return geometry_run(*m, static_cast<cudaStream_t>(stream));
+    int rc = geometry_run(*m, static_cast<cudaStream_t>(stream));
+    if (rc || !m->perq) return rc;
+    return geometry_q_run(*m, static_cast<cudaStream_t>(stream));
+}
+
+int fem_mesh_set_isoparametric(fem_mesh* m, int on, void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    m->iso = on != 0;
+    m->perq = m->iso || m->cfield.ptr != nullptr;
+    m->v_prec = -1;
+    m->v_mask = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!m->perq) {
+        buf_free(m->geoq64, s);
+        buf_free(m->geoq32, s);
+        return FEM_OK;
+    }
+    return geometry_q_run(*m, s);
+}
+
+int fem_mesh_set_conductivity_field(fem_mesh* m, const double* c_field, void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    m->v_prec = -1;
+    m->v_mask = 0;
+    if (!c_field) {
+        buf_free(m->cfield, s);
+        m->perq = m->iso;
+        if (!m->perq) {
+            buf_free(m->geoq64, s);
+            buf_free(m->geoq32, s);
+            return FEM_OK;
+        }
+        return geometry_q_run(*m, s);
+    }
+    const size_t n = (size_t)m->E * m->nq * m->d * m->d;
+    int rc = buf_alloc(m->cfield, sizeof(double) * n + 8, s);
+    if (rc) return rc;
+    FEM_CUDA_TRY(cudaMemcpyAsync(m->cfield.ptr, c_field, sizeof(double) * n,
+                                 is_device_ptr(c_field) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    m->perq = true;
+    return geometry_q_run(*m, s);
 }
 
 int fem_assemble_mass_u(fem_mesh* m, const fem_coeff* mk, const void* d_u, const void* d_us, int prec, void* d_vMu,
@@ -517,6 +561,8 @@ int fem_assemble_mass_u(fem_mesh* m, const fem_coeff* mk, const void* d_u, const
     if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
     if (prec != FEM_FP64 && prec != FEM_FP32 && prec != FEM_TF32X3)
         return fail(FEM_EINVAL, "the u-dependent mass runs FEM_FP64, FEM_FP32 or FEM_TF32X3");
+    if (m->perq && prec == FEM_TF32X3)
+        return fail(FEM_EINVAL, "per-point geometry runs the SIMT products (FEM_FP64, FEM_FP32) only");
     if (!d_vMu && !d_vMt) return FEM_OK;
     int rc = check_coeff(mk);
     if (rc) return rc;
@@ -571,6 +617,7 @@ int fem_assemble_boundary(fem_mesh* m, const fem_coeff* g, const double* d_u, co
                           double* d_b, void* stream) {
     if (!m) return fail(FEM_EINVAL, "NULL mesh");
     if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    if (m->iso) return fail(FEM_EINVAL, "boundary terms are formed on straight facets: not on isoparametric meshes");
     int rc = check_coeff(g);
     if (rc) return rc;
     if (!d_vB && !d_b) return FEM_OK;

@@ -57,7 +57,7 @@ __device__ double2 g_sincos_tab[SC_TAB];
 // gradient keep FP32 relative accuracy.
 
 // X row and V = X Q of element e (thread-private X row in shared memory).
-template <typename ETy, typename T>
+template <typename ETy, typename T, bool PQ = false>
 __device__ __forceinline__ void simt_element(int64_t e, const int* __restrict__ conn, const T* __restrict__ geo,
                                              int64_t gs, const double* __restrict__ u,
                                              const CoeffDev& k, T mass, T* __restrict__ VM, T* __restrict__ VK,
@@ -92,13 +92,25 @@ __device__ __forceinline__ void simt_element(int64_t e, const int* __restrict__ 
 #pragma unroll
         for (int i = 0; i < NP; ++i) du[i] = T(0);
     }
-    T b = geo[e];
+    // geometry: per element, or per quadrature point (PQ: the cache entry of
+    // point q of element e at e n_q + q, Section 7 isoparametric mappings
+    // and point-wise conductivity tensors)
+    T b = T(0);
     T A[NS];
+    if constexpr (!PQ) {
+        b = geo[e];
 #pragma unroll
-    for (int t = 0; t < NS; ++t) A[t] = geo[(1 + t) * gs + e];
+        for (int t = 0; t < NS; ++t) A[t] = geo[(1 + t) * gs + e];
+    }
     // --- X = Lambda, Lambda (.) W, tangent factors
 #pragma unroll 1
     for (int q = 0; q < NQ; ++q) {
+        if constexpr (PQ) {
+            const int64_t gi = e * NQ + q;
+            b = geo[gi];
+#pragma unroll
+            for (int t = 0; t < NS; ++t) A[t] = geo[(1 + t) * gs + gi];
+        }
         // u_q = u_0 + sum_i phi_i (u_i - u_0) (the basis sums to one); the
         // reference gradient uses the differences only (its rows sum to zero)
         T uq = T(0);
@@ -160,7 +172,7 @@ __device__ __forceinline__ void simt_element(int64_t e, const int* __restrict__ 
     if (VT) product(X + KM + KK, KT, Q + QT_O, ETy::NT, VT, 1);
 }
 
-template <typename ETy, typename T>
+template <typename ETy, typename T, bool PQ>
 __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict__ conn, const T* __restrict__ geo,
                                                           int64_t E, int64_t gs,
                                                           const double* __restrict__ u,
@@ -173,7 +185,7 @@ __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict_
     for (int64_t e0 = (int64_t)blockIdx.x * BT; e0 < E; e0 += (int64_t)gridDim.x * BT) {
         int64_t e = e0 + threadIdx.x;
         if (e >= E) continue;
-        simt_element<ETy, T>(e, conn, geo, gs, u, k, mass, VM, VK, VT, X);
+        simt_element<ETy, T, PQ>(e, conn, geo, gs, u, k, mass, VM, VK, VT, X);
     }
 }
 
@@ -475,7 +487,7 @@ __global__ void __launch_bounds__(BT) batch_simt_kernel(const BatchItem* __restr
     }
 }
 
-template <typename ETy, typename T>
+template <typename ETy, typename T, bool PQ>
 int launch_simt(const fem_mesh& m, const CoeffDev& k, const double* u, const T* geo, T* VM, T* VK,
                 T* VT, cudaStream_t s, int64_t e0, int64_t e1) {
     const int64_t E = e1 - e0;
@@ -483,7 +495,7 @@ int launch_simt(const fem_mesh& m, const CoeffDev& k, const double* u, const T* 
     constexpr int KTOT = ETy::KM + ETy::KK + ETy::KT;
     constexpr int LD = KTOT | 1;
     size_t smem = sizeof(T) * (size_t)LD * BT;
-    auto kern = element_simt_kernel<ETy, T>;
+    auto kern = element_simt_kernel<ETy, T, PQ>;
     FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
@@ -497,7 +509,10 @@ int launch_simt(const fem_mesh& m, const CoeffDev& k, const double* u, const T* 
     if (grid > tiles) grid = tiles;
     if (grid < 1) return FEM_OK;
     cudaGetLastError();   // clear any stale error before the launch check
-    kern<<<(unsigned)grid, BT, smem, s>>>(m.conn.as<int>() + e0 * ETy::NP, geo + e0, E, m.E, u, k, (T)m.m,
+    // per-point geometry: entries (e, q) at e n_q + q, SoA stride E n_q
+    const T* g = PQ ? geo + e0 * ETy::NQ : geo + e0;
+    const int64_t gs = PQ ? m.E * ETy::NQ : m.E;
+    kern<<<(unsigned)grid, BT, smem, s>>>(m.conn.as<int>() + e0 * ETy::NP, g, E, gs, u, k, (T)m.m,
                                           VM ? VM + 2 * e0 * ETy::NSYM : nullptr, VK ? VK + 2 * e0 * ETy::NSYM : nullptr,
                                           VT ? VT + e0 * ETy::NT : nullptr);
     FEM_CUDA_TRY(cudaGetLastError());
@@ -509,17 +524,29 @@ int dispatch(const fem_mesh& m, const CoeffDev& k, const double* u, const T* geo
              T* VT, cudaStream_t s, int64_t e0, int64_t e1) {
     if (e1 < 0) e1 = m.E;
     if (e0 < 0 || e0 > e1 || e1 > m.E) return fail(FEM_EINVAL, "element range out of bounds");
+    if (m.perq) {   // per-point geometry: the general product, b and A read per point
+        const T* gq = sizeof(T) == 8 ? reinterpret_cast<const T*>(m.geoq64.ptr) : reinterpret_cast<const T*>(m.geoq32.ptr);
+        switch (m.type) {
+            case 0: return launch_simt<ET<2, 1>, T, true>(m, k, u, gq, VM, VK, VT, s, e0, e1);
+            case 1: return launch_simt<ET<2, 2>, T, true>(m, k, u, gq, VM, VK, VT, s, e0, e1);
+            case 2: return launch_simt<ET<2, 3>, T, true>(m, k, u, gq, VM, VK, VT, s, e0, e1);
+            case 3: return launch_simt<ET<3, 1>, T, true>(m, k, u, gq, VM, VK, VT, s, e0, e1);
+            case 4: return launch_simt<ET<3, 2>, T, true>(m, k, u, gq, VM, VK, VT, s, e0, e1);
+            case 5: return launch_simt<ET<3, 3>, T, true>(m, k, u, gq, VM, VK, VT, s, e0, e1);
+        }
+        return fail(FEM_EINVAL, "element type");
+    }
     if constexpr (sizeof(T) == 8) {
         if (m.type == 0) return launch_p1_fp64<2>(m, k, u, VM, VK, VT, s, e0, e1);
         if (m.type == 3) return launch_p1_fp64<3>(m, k, u, VM, VK, VT, s, e0, e1);
     }
     switch (m.type) {
-        case 0: return launch_simt<ET<2, 1>, T>(m, k, u, geo, VM, VK, VT, s, e0, e1);
-        case 1: return launch_simt<ET<2, 2>, T>(m, k, u, geo, VM, VK, VT, s, e0, e1);
-        case 2: return launch_simt<ET<2, 3>, T>(m, k, u, geo, VM, VK, VT, s, e0, e1);
-        case 3: return launch_simt<ET<3, 1>, T>(m, k, u, geo, VM, VK, VT, s, e0, e1);
-        case 4: return launch_simt<ET<3, 2>, T>(m, k, u, geo, VM, VK, VT, s, e0, e1);
-        case 5: return launch_simt<ET<3, 3>, T>(m, k, u, geo, VM, VK, VT, s, e0, e1);
+        case 0: return launch_simt<ET<2, 1>, T, false>(m, k, u, geo, VM, VK, VT, s, e0, e1);
+        case 1: return launch_simt<ET<2, 2>, T, false>(m, k, u, geo, VM, VK, VT, s, e0, e1);
+        case 2: return launch_simt<ET<2, 3>, T, false>(m, k, u, geo, VM, VK, VT, s, e0, e1);
+        case 3: return launch_simt<ET<3, 1>, T, false>(m, k, u, geo, VM, VK, VT, s, e0, e1);
+        case 4: return launch_simt<ET<3, 2>, T, false>(m, k, u, geo, VM, VK, VT, s, e0, e1);
+        case 5: return launch_simt<ET<3, 3>, T, false>(m, k, u, geo, VM, VK, VT, s, e0, e1);
     }
     return fail(FEM_EINVAL, "element type");
 }
@@ -542,7 +569,7 @@ __host__ __device__ constexpr bool mass_u_staged() {
     return (BT * (2 * ETy::NSYM + 1) + ETy::NQ * ETy::NSYM) * sizeof(T) <= 48 * 1024;
 }
 
-template <typename ETy, typename T>
+template <typename ETy, typename T, bool PQ>
 __global__ void __launch_bounds__(BT) mass_u_kernel(const int* __restrict__ conn, const T* __restrict__ geo,
                                                     int64_t E, const double* __restrict__ u,
                                                     const double* __restrict__ us, CoeffDev mk,
@@ -582,10 +609,11 @@ __global__ void __launch_bounds__(BT) mass_u_kernel(const int* __restrict__ conn
             }
 #pragma unroll
             for (int i = 0; i < NP; ++i) dz[i] = doMt ? (T)(u[ce[i]] - us[ce[i]]) : T(0);
-            const T b = geo[e];
+            const T b0 = PQ ? T(0) : geo[e];
             T Xu[NQ], Xt[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
+                const T b = PQ ? geo[e * NQ + q] : b0;   // |det B| per point (Section 7) or per element
                 T uq = T(0), zq = T(0);
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
@@ -628,7 +656,7 @@ __global__ void __launch_bounds__(BT) mass_u_kernel(const int* __restrict__ conn
     }
 }
 
-template <typename T>
+template <typename T, bool PQ>
 int launch_mass_u(const fem_mesh& m, const CoeffDev& mk, const double* u, const double* us, const T* geo, T* VMK,
                   bool doMu, bool doMt, cudaStream_t s) {
     if (m.E <= 0) return FEM_OK;
@@ -641,7 +669,7 @@ int launch_mass_u(const fem_mesh& m, const CoeffDev& mk, const double* u, const 
     switch (m.type) {
 #define FEM_MASS_U_CASE(TY, DD, PP)                                                                          \
     case TY:                                                                                             \
-        mass_u_kernel<ET<DD, PP>, T>                                                                     \
+        mass_u_kernel<ET<DD, PP>, T, PQ>                                                                 \
             <<<(unsigned)grid, BT,                                                                         \
                mass_u_staged<ET<DD, PP>, T>()                                                               \
                    ? (BT * (2 * ET<DD, PP>::NSYM + 1) + ET<DD, PP>::NQ * ET<DD, PP>::NSYM) * sizeof(T)      \
@@ -786,8 +814,16 @@ int element_mass_u(const fem_mesh& m, const CoeffDev& mk, const double* u, const
                    bool doMu, bool doMt, cudaStream_t s) {
     int rc = tables_init_simt();
     if (rc) return rc;
-    if (fp64) return launch_mass_u<double>(m, mk, u, us, m.geo64.as<double>(), static_cast<double*>(VMK), doMu, doMt, s);
-    return launch_mass_u<float>(m, mk, u, us, m.geo32.as<float>(), static_cast<float*>(VMK), doMu, doMt, s);
+    if (m.perq) {
+        if (fp64)
+            return launch_mass_u<double, true>(m, mk, u, us, m.geoq64.as<double>(), static_cast<double*>(VMK), doMu,
+                                               doMt, s);
+        return launch_mass_u<float, true>(m, mk, u, us, m.geoq32.as<float>(), static_cast<float*>(VMK), doMu, doMt, s);
+    }
+    if (fp64)
+        return launch_mass_u<double, false>(m, mk, u, us, m.geo64.as<double>(), static_cast<double*>(VMK), doMu, doMt,
+                                            s);
+    return launch_mass_u<float, false>(m, mk, u, us, m.geo32.as<float>(), static_cast<float*>(VMK), doMu, doMt, s);
 }
 
 }  // namespace fem

@@ -57,6 +57,12 @@ struct fem_mesh {
     // constant conductivity tensor c (SPD; identity by default), stored
     // 3 x 3 row-major whatever d (entry (a, b) at 3a + b): A_e = B_e^-1 c B_e^-T
     double cond[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    // per-quadrature-point geometry (Section 7): iso = map through all the
+    // element's nodes; cfield = E x n_q x d x d conductivity tensors (FP64);
+    // perq = either is set, the element kernels then read geoq64/geoq32
+    // (SoA [1 + d(d+1)/2][E n_q], point (e, q) at e n_q + q)
+    bool iso = false, perq = false;
+    fem::DevBuf cfield, geoq64, geoq32;
     // symbolic
     bool have_pattern = false;
     int64_t nnz = -1;
@@ -93,6 +99,7 @@ namespace fem {
 
 // ---------------------------------------------------------- kernel launches
 int geometry_run(fem_mesh& m, cudaStream_t s);           // fills geo64, geo32, n_flagged
+int geometry_q_run(fem_mesh& m, cudaStream_t s);         // fills geoq64, geoq32 (per-point mode)
 int symbolic_run(fem_mesh& m, cudaStream_t s);           // fills pattern and segments
 int scan_exclusive(const int* in, int64_t n, int* out, cudaStream_t s);   // n ints -> n+1 prefix sums
 // boundary facets, node -> facet incidences (once; needs the pattern)

@@ -13,6 +13,7 @@
 // whose condition estimate kappa = ||B||_F^d / |det B| exceeds 1e3 are
 // recomputed in FP64 and rounded.
 #include "fem_internal.h"
+#include "refelem.h"
 
 namespace fem {
 
@@ -153,7 +154,155 @@ __global__ void geometry_kernel(const double* __restrict__ X, const int* __restr
     }
 }
 
+// ---------------------------------------------------- per-point geometry
+// Section 7: with an isoparametric mapping x(xhat) = sum_i x_i phi_i(xhat)
+// the Jacobian B_q = sum_i x_i (grad phi_i(xhat_q))^T depends on the
+// quadrature point (n_q determinants and d^2 n_q Jacobian entries per
+// element), and a conductivity tensor may vary over the points:
+// A_q = B_q^-1 c_q B_q^-T.  One thread per (element, point); the cache is
+// geoq[comp * E n_q + e n_q + q], comp 0 = |det B_q|, 1.. = A_q (upper
+// triangle).  The FP32 cache holds the FP64 values rounded.
+__constant__ double c_gq[2200];   // reference gradients at the points, per element type
+struct GqType {
+    int off[6];
+};
+
+template <int D>
+__global__ void geometry_q_kernel(const double* __restrict__ X, const int* __restrict__ conn, int64_t E, int np,
+                                  int nq, int goff, int iso, const double* __restrict__ cfield, Cond cd,
+                                  double* __restrict__ g64, float* __restrict__ g32,
+                                  unsigned long long* __restrict__ counters) {
+    constexpr int NS = D * (D + 1) / 2;
+    const int64_t m = E * nq;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = k / nq;
+        const int q = (int)(k - e * nq);
+        const int* ce = conn + e * np;
+        double B[D][D];
+        if (iso) {
+            const double* G = c_gq + goff + q * np * D;
+#pragma unroll
+            for (int r = 0; r < D; ++r)
+#pragma unroll
+                for (int c = 0; c < D; ++c) B[r][c] = 0.0;
+            for (int i = 0; i < np; ++i) {
+                const int vi = ce[i];
+#pragma unroll
+                for (int r = 0; r < D; ++r) {
+                    const double x = X[(int64_t)vi * D + r];
+#pragma unroll
+                    for (int c = 0; c < D; ++c) B[r][c] = fma(x, G[i * D + c], B[r][c]);
+                }
+            }
+        } else {
+            const int v0 = ce[0];
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const int vc = ce[c + 1];
+#pragma unroll
+                for (int r = 0; r < D; ++r) B[r][c] = X[(int64_t)vc * D + r] - X[(int64_t)v0 * D + r];
+            }
+        }
+        double Bi[D][D];
+        const double det = det_inv<D, double>(B, Bi);
+        double nf = 0.0;
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int c = 0; c < D; ++c) nf += B[r][c] * B[r][c];
+        const double nfd = (D == 2) ? nf : nf * sqrt(nf);
+        if (!(fabs(det) > 1e-14 * nfd)) {
+            atomicAdd(&counters[1], 1ull);
+            for (int t = 0; t <= NS; ++t) {
+                g64[t * m + k] = 0.0;
+                g32[t * m + k] = 0.0f;
+            }
+            continue;
+        }
+        Cond cq = cd;
+        if (cfield) {
+            const double* cf = cfield + k * D * D;
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = 0; b < D; ++b) cq.c[a * 3 + b] = cf[a * D + b];
+        }
+        double A[NS];
+        make_A<D, double>(Bi, cq, A);
+        g64[k] = fabs(det);
+        g32[k] = (float)fabs(det);
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+            g64[(1 + t) * m + k] = A[t];
+            g32[(1 + t) * m + k] = (float)A[t];
+        }
+    }
+}
+
+int gq_tables_init(GqType& out) {
+    static bool done[64] = {};
+    static GqType offs;
+    int dev = 0;
+    FEM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 64 && done[dev]) {
+        out = offs;
+        return FEM_OK;
+    }
+    std::vector<double> g;
+    for (int t = 0; t < 6; ++t) {
+        const RefElem* R = refelem_for_type(t);
+        if (!R) return fail(FEM_EINVAL, "reference element tables failed");
+        offs.off[t] = (int)g.size();
+        g.insert(g.end(), R->grad.begin(), R->grad.end());
+    }
+    if (g.size() > sizeof(c_gq) / sizeof(double)) return fail(FEM_EINVAL, "gradient tables too large");
+    FEM_CUDA_TRY(cudaMemcpyToSymbol(c_gq, g.data(), sizeof(double) * g.size()));
+    if (dev < 64) done[dev] = true;
+    out = offs;
+    return FEM_OK;
+}
+
 }  // namespace
+
+// The per-point cache of a mesh in per-point mode (isoparametric and/or a
+// conductivity field); FEM_EDEGENERATE if some det B_q vanishes.
+int geometry_q_run(fem_mesh& m, cudaStream_t s) {
+    GqType offs;
+    int rc = gq_tables_init(offs);
+    if (rc) return rc;
+    const int ngeo = 1 + m.d * (m.d + 1) / 2;
+    const size_t pts = (size_t)m.E * m.nq;
+    if ((rc = buf_alloc(m.geoq64, sizeof(double) * ngeo * pts + 8, s))) return rc;
+    if ((rc = buf_alloc(m.geoq32, sizeof(float) * ngeo * pts + 8, s))) return rc;
+    DevBuf cnt;
+    if ((rc = buf_alloc(cnt, 4 * sizeof(unsigned long long), s))) return rc;
+    FEM_CUDA_TRY(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
+    Cond cd;
+    for (int i = 0; i < 9; ++i) cd.c[i] = m.cond[i];
+    if (pts > 0) {
+        cudaGetLastError();   // clear any stale error before the launch check
+        int64_t blocks = ((int64_t)pts + 255) / 256;
+        if (blocks > 152 * 64) blocks = 152 * 64;
+        const double* cf = m.cfield.ptr ? m.cfield.as<double>() : nullptr;
+        if (m.d == 2)
+            geometry_q_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(m.coords.as<double>(), m.conn.as<int>(), m.E, m.np,
+                                                                  m.nq, offs.off[m.type], m.iso ? 1 : 0, cf, cd,
+                                                                  m.geoq64.as<double>(), m.geoq32.as<float>(),
+                                                                  cnt.as<unsigned long long>());
+        else
+            geometry_q_kernel<3><<<(unsigned)blocks, 256, 0, s>>>(m.coords.as<double>(), m.conn.as<int>(), m.E, m.np,
+                                                                  m.nq, offs.off[m.type], m.iso ? 1 : 0, cf, cd,
+                                                                  m.geoq64.as<double>(), m.geoq32.as<float>(),
+                                                                  cnt.as<unsigned long long>());
+        FEM_CUDA_TRY(cudaGetLastError());
+    }
+    unsigned long long h[4] = {0, 0, 0, 0};
+    FEM_CUDA_TRY(cudaMemcpyAsync(h, cnt.ptr, sizeof(h), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA_TRY(cudaStreamSynchronize(s));
+    buf_free(cnt, s);
+    if (h[1]) return fail(FEM_EDEGENERATE, std::to_string(h[1]) + " quadrature point(s) with a degenerate Jacobian");
+    return FEM_OK;
+}
 
 int geometry_run(fem_mesh& m, cudaStream_t s) {
     int ngeo = 1 + m.d * (m.d + 1) / 2;
