@@ -9,8 +9,10 @@
 //   1. counting sort of the (e, i) incidences by row (integer atomics for
 //      the counts, then each row's list sorted ascending so that the order
 //      does not depend on atomic timing);
-//   2. per row, a stable rank sort of its n_p * |incidences| entries by
-//      column (ties keep ascending c), one warp per row;
+//   2. per row, a stable counting sort of its n_p * |incidences| entries by
+//      column (ties keep ascending c), one warp per row: the row's distinct
+//      columns by repeated warp minima, a count per column, then the entries
+//      placed in order (very long rows fall back to a rank sort);
 //   3. a scan of the per-row unique-column counts gives row_ptr;
 //   4. per row, one warp walks the sorted entries and numbers the column
 //      groups: col_idx, seg_ptr (first sorted position of each slot) and the
@@ -142,44 +144,155 @@ __global__ void inc_sort(const int* __restrict__ inc_ptr, int64_t n, int* __rest
 
 // ---------------------------------------------------------------- row sort
 constexpr int RS_WARPS = 8;
-constexpr int RS_CAP = 768;   // staged columns per warp
 
-__global__ void __launch_bounds__(RS_WARPS * 32) row_sort(const int* __restrict__ conn, int np,
-                                                          const int* __restrict__ inc_ptr, const int* __restrict__ inc,
-                                                          int64_t n, int* __restrict__ contrib,
-                                                          int* __restrict__ row_nnz) {
-    __shared__ int sc_all[RS_WARPS][RS_CAP];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// Row sort by counting: entries ordered by column, ties by ascending element
+// entry (a stable sort by column).  One warp per row; the row's
+// columns are staged in shared memory, then
+//   1. its distinct columns U, ascending, by repeated warp minima (each pass
+//      takes the smallest column above the last one found);
+//   2. per entry the index of its column in U (binary search) and a count
+//      per column (shared-memory atomics on integers: order-free);
+//   3. exclusive offsets of the columns, then the entries placed in
+//      ascending order, 32 at a time: lanes holding the same column rank
+//      among themselves with __match_any_sync, after the entries of earlier
+//      chunks (stable).
+// Rows with more than RC_CAP entries or RC_UCAP distinct columns are left to
+// a rank sort (row_sort_rest, the same order).
+constexpr int RC_WARPS = 4;
+constexpr int RC_CAP = 768;    // staged entries per warp
+constexpr int RC_UCAP = 384;   // distinct columns per warp
+
+__global__ void __launch_bounds__(RC_WARPS * 32) row_sort_count(const int* __restrict__ conn, int np,
+                                                                const int* __restrict__ inc_ptr,
+                                                                const int* __restrict__ inc, int64_t n,
+                                                                int* __restrict__ contrib, int* __restrict__ row_nnz,
+                                                                int* __restrict__ overflow) {
+    __shared__ int sc_all[RC_WARPS][RC_CAP];
+    __shared__ short sb_all[RC_WARPS][RC_CAP];
+    __shared__ int su_all[RC_WARPS][RC_UCAP];
+    __shared__ int so_all[RC_WARPS][RC_UCAP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int* sc = sc_all[w];
-    int64_t nwarps = (int64_t)gridDim.x * RS_WARPS;
-    for (int64_t r = blockIdx.x * (int64_t)RS_WARPS + w; r < n; r += nwarps) {
-        int start = inc_ptr[r];
-        int len = inc_ptr[r + 1] - start;
-        int L = np * len;
-        int64_t base = (int64_t)np * start;
-        bool staged = L <= RS_CAP;
-        if (staged) {
+    short* sb = sb_all[w];
+    int* U = su_all[w];
+    int* off = so_all[w];
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t nwarps = (int64_t)gridDim.x * RC_WARPS;
+    for (int64_t r = blockIdx.x * (int64_t)RC_WARPS + w; r < n; r += nwarps) {
+        const int start = inc_ptr[r];
+        const int L = np * (inc_ptr[r + 1] - start);
+        if (L > RC_CAP) {   // left to the rank sort
+            if (lane == 0) atomicAdd(overflow, 1);
+            continue;
+        }
+        for (int k = lane; k < L; k += 32) {
+            const int ei = inc[start + k / np];
+            sc[k] = conn[(int64_t)(ei / np) * np + k % np];
+        }
+        __syncwarp();
+        // 1. distinct columns, ascending
+        int u = 0, last = INT_MIN;
+        bool too_many = false;
+        for (;;) {
+            int m = INT_MAX;
             for (int k = lane; k < L; k += 32) {
-                int ei = inc[start + k / np];
-                sc[k] = conn[(int64_t)(ei / np) * np + k % np];
+                const int c = sc[k];
+                if (c > last && c < m) m = c;
+            }
+            m = __reduce_min_sync(0xffffffffu, m);
+            if (m == INT_MAX) break;
+            if (u == RC_UCAP) {
+                too_many = true;
+                break;
+            }
+            if (lane == 0) U[u] = m;
+            ++u;
+            last = m;
+        }
+        if (too_many) {
+            if (lane == 0) atomicAdd(overflow, 1);
+            __syncwarp();
+            continue;
+        }
+        for (int b = lane; b < u; b += 32) off[b] = 0;
+        __syncwarp();
+        // 2. bucket of every entry and the count per bucket
+        for (int k = lane; k < L; k += 32) {
+            const int c = sc[k];
+            int lo = 0, hi = u - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (U[mid] < c) lo = mid + 1;
+                else hi = mid;
+            }
+            sb[k] = (short)lo;
+            atomicAdd(&off[lo], 1);
+        }
+        __syncwarp();
+        // 3. exclusive offsets (lane l scans buckets l*chunk .. ), then stable placement
+        {
+            const int chunk = (u + 31) / 32;
+            const int b0 = lane * chunk, b1 = min(b0 + chunk, u);
+            int sum = 0;
+            for (int b = b0; b < b1; ++b) sum += off[b];
+            int incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            int run = incl - sum;
+            __syncwarp();
+            for (int b = b0; b < b1; ++b) {
+                const int c = off[b];
+                off[b] = run;
+                run += c;
             }
         }
         __syncwarp();
+        const int64_t base = (int64_t)np * start;
+        for (int k0 = 0; k0 < L; k0 += 32) {
+            const int k = k0 + lane;
+            const bool valid = k < L;
+            const unsigned act = __ballot_sync(0xffffffffu, valid);
+            if (valid) {
+                const int b = sb[k];
+                const unsigned peers = __match_any_sync(act, b);
+                const int pos = off[b] + __popc(peers & lt);
+                const int ei = inc[start + k / np];
+                contrib[base + pos] = ei * np + (k % np);
+                __syncwarp(act);
+                if ((peers & lt) == 0) off[b] += __popc(peers);   // the lowest lane of the group
+            }
+            __syncwarp();
+        }
+        if (lane == 0) row_nnz[r] = u;
+        __syncwarp();
+    }
+}
+
+// The rank sort for the rows the counting sort left (row_nnz < 0 marks
+// them): same result, O(L^2) per row.
+__global__ void __launch_bounds__(RS_WARPS * 32) row_sort_rest(const int* __restrict__ conn, int np,
+                                                               const int* __restrict__ inc_ptr,
+                                                               const int* __restrict__ inc, int64_t n,
+                                                               int* __restrict__ contrib, int* __restrict__ row_nnz) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * RS_WARPS;
+    for (int64_t r = blockIdx.x * (int64_t)RS_WARPS + w; r < n; r += nwarps) {
+        if (row_nnz[r] >= 0) continue;
+        const int start = inc_ptr[r];
+        const int L = np * (inc_ptr[r + 1] - start);
+        const int64_t base = (int64_t)np * start;
         int heads = 0;
         for (int k = lane; k < L; k += 32) {
-            int ei = inc[start + k / np];
-            int ck = staged ? sc[k] : conn[(int64_t)(ei / np) * np + k % np];
-            int rank = 0;
-            int head = 1;
+            const int ei = inc[start + k / np];
+            const int ck = conn[(int64_t)(ei / np) * np + k % np];
+            int rank = 0, head = 1;
             for (int k2 = 0; k2 < L; ++k2) {
-                int c2;
-                if (staged) c2 = sc[k2];
-                else {
-                    int e2 = inc[start + k2 / np];
-                    c2 = conn[(int64_t)(e2 / np) * np + k2 % np];
-                }
-                bool before = (c2 < ck) | ((c2 == ck) & (k2 < k));
-                rank += before;
+                const int e2 = inc[start + k2 / np];
+                const int c2 = conn[(int64_t)(e2 / np) * np + k2 % np];
+                rank += (c2 < ck) | ((c2 == ck) & (k2 < k));
                 head &= !((c2 == ck) & (k2 < k));
             }
             contrib[base + rank] = ei * np + (k % np);
@@ -188,7 +301,6 @@ __global__ void __launch_bounds__(RS_WARPS * 32) row_sort(const int* __restrict_
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) heads += __shfl_xor_sync(0xffffffffu, heads, o);
         if (lane == 0) row_nnz[r] = heads;
-        __syncwarp();
     }
 }
 
@@ -287,9 +399,20 @@ int symbolic_run(fem_mesh& m, cudaStream_t s) {
     if ((rc = scan_exclusive(cnt.as<int>(), n, m.inc_ptr.as<int>(), s))) return rc;
     inc_fill<<<grid_for(m1, 256), 256, 0, s>>>(conn, m1, m.inc_ptr.as<int>(), fill.as<int>(), m.inc.as<int>());
     inc_sort<<<grid_for(n, 128), 128, 0, s>>>(m.inc_ptr.as<int>(), n, m.inc.as<int>());
-    row_sort<<<grid_for(n, RS_WARPS, 152 * 64), RS_WARPS * 32, 0, s>>>(conn, np, m.inc_ptr.as<int>(), m.inc.as<int>(), n,
-                                                                      m.contrib.as<int>(), row_nnz.as<int>());
+    // rows by counting sort; the few rows it leaves (marked -1) by rank sort
+    FEM_CUDA_TRY(cudaMemsetAsync(row_nnz.ptr, 0xff, row_nnz.bytes, s));
+    FEM_CUDA_TRY(cudaMemsetAsync(cnt.ptr, 0, sizeof(int), s));   // overflow count (the incidence counts are scanned)
+    row_sort_count<<<grid_for(n, RC_WARPS, 152 * 64), RC_WARPS * 32, 0, s>>>(
+        conn, np, m.inc_ptr.as<int>(), m.inc.as<int>(), n, m.contrib.as<int>(), row_nnz.as<int>(), cnt.as<int>());
     FEM_CUDA_TRY(cudaGetLastError());
+    int left = 0;
+    FEM_CUDA_TRY(cudaMemcpyAsync(&left, cnt.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (left > 0) {
+        row_sort_rest<<<grid_for(n, RS_WARPS, 152 * 64), RS_WARPS * 32, 0, s>>>(
+            conn, np, m.inc_ptr.as<int>(), m.inc.as<int>(), n, m.contrib.as<int>(), row_nnz.as<int>());
+        FEM_CUDA_TRY(cudaGetLastError());
+    }
     if ((rc = scan_exclusive(row_nnz.as<int>(), n, m.row_ptr.as<int>(), s))) return rc;
     int nnz = 0;
     FEM_CUDA_TRY(cudaMemcpyAsync(&nnz, m.row_ptr.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, s));
