@@ -483,6 +483,40 @@ int fem_residual(fem_mesh* mesh, const double* d_vM, const double* d_vK, const d
 int fem_jacobian(fem_mesh* mesh, double dt, const double* d_vM, const double* d_vMt, const double* d_vK,
                  const double* d_vT, const double* d_vB, double* d_vJ, void* stream);
 
+/* ----------------------------------------------------- solving the heat problem */
+/* The paper solves the Newton systems of Section 5 with MATLAB's backslash
+ * or with GMRES (Section 6, Experiment 2); the linear solver is not part of
+ * its method.  These calls close the loop on the GPU in FP64.
+ *
+ * fem_bicgstab: A x = b for FP64 CSR values d_vA on the mesh pattern,
+ * Jacobi-preconditioned BiCGStab starting from the given d_x, until
+ * ||b - A x||_2 <= rtol ||b||_2 or maxit iterations; *iters and *relres
+ * (may be NULL) receive the iterations and the final relative residual.
+ * Every reduction runs in a fixed order, so a solve is bitwise repeatable.
+ * Scratch (8 vectors of n) is owned by the mesh.  Synchronises `stream`
+ * once per iteration (the convergence test reads one number). */
+int fem_bicgstab(fem_mesh* mesh, const double* d_vA, const double* d_b, double* d_x, double rtol, int maxit,
+                 int* iters, double* relres, void* stream);
+
+/* One implicit Euler step of m du/dt - div(k(u) grad u) = 0 with the
+ * boundary flux g(u) (the load of fem_assemble_boundary; Experiment 2:
+ * convection + radiation), the mesh's constant mass coefficient m, and
+ * time step dt: Newton's method on F(u) = M (u - u^s) + dt K(u) u - dt b(u)
+ * with the Jacobian M + dt (K + T) - dt B, each linear system solved by
+ * fem_bicgstab (relative tolerance krylov_rtol, at most max_krylov
+ * iterations).  d_us: the previous state; d_u: the initial guess on entry,
+ * the new state on return.  Stops when ||F||_2 <= newton_rtol ||F(u_0)||_2
+ * or after max_newton Newton updates.  *rep (may be NULL) receives the
+ * counts and residuals.  Matrices and vectors of the step are owned by the
+ * mesh.  Synchronises `stream`. */
+typedef struct {
+    int newton_iters, krylov_iters, converged, pad;
+    double residual0, residual, max_krylov_relres;
+} fem_heat_report;
+int fem_heat_step(fem_mesh* mesh, const fem_coeff* k, const fem_coeff* g, const uint8_t* d_mask, double dt,
+                  const double* d_us, double* d_u, double newton_rtol, int max_newton, double krylov_rtol,
+                  int max_krylov, fem_heat_report* rep, void* stream);
+
 /* The conductivity law alone, in FP64 on the GPU: d_k[i] = k(u_i) and
  * d_dk[i] = k'(u_i) for i < n, with the very device code the FP64 element
  * kernels evaluate at the quadrature points (the S of Algorithm 2, whose

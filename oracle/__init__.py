@@ -303,6 +303,30 @@ class Oracle:
             raise RuntimeError("oracle_jacobian failed")
         return J
 
+    def heat_step(self, k, g, us, dt, m, u0=None, rtol=1e-12, maxit=30):
+        """One implicit Euler step (Section 5): Newton's method on
+        F(u) = M (u - us) + dt K(u) u - dt b(u) with the Jacobian
+        M + dt (K + T) - dt B (constant mass m), each linear system solved by
+        a sparse direct solve (scipy.sparse.linalg.spsolve, a library step).
+        Returns (u, {'newton': updates, 'residuals': [||F||_2 per iterate]})."""
+        import scipy.sparse as sp
+        import scipy.sparse.linalg as spl
+        rp, ci = self.pattern()
+        us = np.ascontiguousarray(us, dtype=np.float64)
+        u = us.copy() if u0 is None else np.ascontiguousarray(u0, dtype=np.float64).copy()
+        res = []
+        for it in range(maxit + 1):
+            r = self.assemble(u, k, m=m, want_abs=False)
+            bd = self.boundary(u, g)
+            F, _ = self.residual(r["M"], r["K"], bd["b"], u, us, dt)
+            res.append(float(np.linalg.norm(F)))
+            if res[-1] <= rtol * res[0] or it == maxit:
+                break
+            J = self.jacobian(r["M"], None, r["K"], r["T"], bd["B"], dt)
+            A = sp.csr_matrix((J, ci, rp), shape=(self.n, self.n))
+            u = u - spl.spsolve(A.tocsc(), F)
+        return u, {"newton": len(res) - 1, "residuals": res}
+
     def element(self, e: int, u, coeff, m: float = 1.0, deg: int = 0):
         """Dense local matrices (Me, Ke, Te) of element e, row = test index."""
         np_ = self.conn.shape[1]

@@ -76,6 +76,11 @@ class fem_allocator(C.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
 
 
+class fem_heat_report(C.Structure):
+    _fields_ = [("newton_iters", C.c_int), ("krylov_iters", C.c_int), ("converged", C.c_int), ("pad", C.c_int),
+                ("residual0", C.c_double), ("residual", C.c_double), ("max_krylov_relres", C.c_double)]
+
+
 class fem_batch_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("tune", C.c_int), ("use_graph", C.c_int), ("reserved", C.c_int)]
 
@@ -146,6 +151,11 @@ _SIGS = {
                                   C.c_void_p], C.c_int),
     "fem_form_elements": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_int, C.c_void_p], C.c_int),
     "fem_law_eval": ([C.POINTER(fem_coeff), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "fem_bicgstab": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int),
+                      C.POINTER(C.c_double), C.c_void_p], C.c_int),
+    "fem_heat_step": ([C.c_void_p, C.POINTER(fem_coeff), C.POINTER(fem_coeff), C.c_void_p, C.c_double, C.c_void_p,
+                       C.c_void_p, C.c_double, C.c_int, C.c_double, C.c_int, C.POINTER(fem_heat_report), C.c_void_p],
+                      C.c_int),
     "fem_mesh_set_isoparametric": ([C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "fem_mesh_set_conductivity_field": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fem_boundary_facets": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
@@ -325,6 +335,25 @@ def fem_assemble_all_noalloc(mesh: int, k, d_u, d_vM, d_vK, d_vT, stream=None) -
 def fem_law_eval(k, d_u, n: int, d_k, d_dk, stream=None) -> None:
     """k(u) and k'(u) of a law at n device values, in FP64 on the GPU."""
     _check(lib().fem_law_eval(C.byref(k), _vp(d_u), int(n), _vp(d_k), _vp(d_dk), _stream(stream)))
+
+
+def fem_bicgstab(mesh: int, d_vA, d_b, d_x, rtol: float, maxit: int, stream=None):
+    """Solves A x = b in place (Jacobi-preconditioned BiCGStab); returns
+    (iterations, relative residual)."""
+    it, rr = C.c_int(), C.c_double()
+    _check(lib().fem_bicgstab(mesh, _vp(d_vA), _vp(d_b), _vp(d_x), float(rtol), int(maxit), C.byref(it), C.byref(rr),
+                              _stream(stream)))
+    return it.value, rr.value
+
+
+def fem_heat_step(mesh: int, k, g, d_mask, dt: float, d_us, d_u, newton_rtol: float = 1e-10, max_newton: int = 20,
+                  krylov_rtol: float = 1e-12, max_krylov: int = 1000, stream=None) -> fem_heat_report:
+    """One implicit Euler step (d_u: initial guess in, new state out)."""
+    rep = fem_heat_report()
+    _check(lib().fem_heat_step(mesh, C.byref(k), C.byref(g), _vp(d_mask), float(dt), _vp(d_us), _vp(d_u),
+                               float(newton_rtol), int(max_newton), float(krylov_rtol), int(max_krylov), C.byref(rep),
+                               _stream(stream)))
+    return rep
 
 
 def fem_mesh_set_isoparametric(mesh: int, on: bool = True, stream=None) -> None:

@@ -307,7 +307,7 @@ CoeffDev coeff_to_device(const fem_coeff* k) { return to_dev(k); }
 size_t fem_mesh::device_bytes() const {
     const fem::DevBuf* bufs[] = {&coords, &conn, &geo64, &geo32, &row_ptr, &col_idx, &seg_ptr, &contrib, &slot,
                                  &seg_head, &inc_ptr, &inc, &VMK, &VT, &u_stage, &out_stage, &bfacet, &bnode_ptr,
-                                 &bnode_inc, &bscratch, &npart, &cfield, &geoq64, &geoq32};
+                                 &bnode_inc, &bscratch, &npart, &cfield, &geoq64, &geoq32, &solve, &newton};
     size_t t = 0;
     for (auto* b : bufs) t += b->bytes;
     return t;
@@ -401,7 +401,8 @@ int fem_mesh_destroy(fem_mesh* m) {
     cudaDeviceSynchronize();
     fem::DevBuf* bufs[] = {&m->coords, &m->conn, &m->geo64, &m->geo32, &m->row_ptr, &m->col_idx, &m->seg_ptr,
                            &m->contrib, &m->slot, &m->seg_head, &m->inc_ptr, &m->inc, &m->VMK, &m->VT, &m->u_stage,
-                           &m->out_stage, &m->bfacet, &m->bnode_ptr, &m->bnode_inc, &m->bscratch, &m->npart, &m->cfield, &m->geoq64, &m->geoq32};
+                           &m->out_stage, &m->bfacet, &m->bnode_ptr, &m->bnode_inc, &m->bscratch, &m->npart, &m->cfield, &m->geoq64, &m->geoq32, &m->solve,
+                           &m->newton};
     for (auto* b : bufs) buf_free(*b, nullptr);
     if (m->copy_stream) {
         for (auto ev : m->copy_ev)
@@ -665,6 +666,39 @@ int fem_jacobian(fem_mesh* m, double dt, const double* d_vM, const double* d_vMt
         if (p && !is_device_ptr(p)) return fail(FEM_EINVAL, "fem_jacobian takes device pointers only");
     if (!std::isfinite(dt)) return fail(FEM_EINVAL, "dt is not finite");
     return csr_jacobian(*m, dt, d_vM, d_vMt, d_vK, d_vT, d_vB, d_vJ, static_cast<cudaStream_t>(stream));
+}
+
+int fem_bicgstab(fem_mesh* m, const double* d_vA, const double* d_b, double* d_x, double rtol, int maxit, int* iters,
+                 double* relres, void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    const void* need[3] = {d_vA, d_b, d_x};
+    for (const void* p : need)
+        if (!p || !is_device_ptr(p)) return fail(FEM_EINVAL, "fem_bicgstab takes non-NULL device pointers");
+    if (!(rtol > 0) || maxit < 0) return fail(FEM_EINVAL, "rtol must be positive and maxit non-negative");
+    return bicgstab(*m, d_vA, d_b, d_x, rtol, maxit, iters, relres, static_cast<cudaStream_t>(stream));
+}
+
+int fem_heat_step(fem_mesh* m, const fem_coeff* k, const fem_coeff* g, const uint8_t* d_mask, double dt,
+                  const double* d_us, double* d_u, double newton_rtol, int max_newton, double krylov_rtol,
+                  int max_krylov, fem_heat_report* rep, void* stream) {
+    if (!m) return fail(FEM_EINVAL, "NULL mesh");
+    if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    if (m->iso) return fail(FEM_EINVAL, "boundary terms are formed on straight facets: not on isoparametric meshes");
+    int rc = check_coeff(k);
+    if (rc) return rc;
+    if ((rc = check_coeff(g))) return rc;
+    const void* need[2] = {d_us, d_u};
+    for (const void* p : need)
+        if (!p || !is_device_ptr(p)) return fail(FEM_EINVAL, "fem_heat_step: u^s and u are device pointers");
+    if (d_mask && !is_device_ptr(d_mask)) return fail(FEM_EINVAL, "fem_heat_step takes device pointers only");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(FEM_EINVAL, "dt must be positive");
+    if (!(newton_rtol > 0) || !(krylov_rtol > 0) || max_newton < 0 || max_krylov < 0)
+        return fail(FEM_EINVAL, "tolerances must be positive and iteration limits non-negative");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((rc = boundary_setup(*m, s))) return rc;
+    return heat_step(*m, k, to_dev(g), d_mask, dt, d_us, d_u, newton_rtol, max_newton, krylov_rtol, max_krylov, rep,
+                     s);
 }
 
 int fem_law_eval(const fem_coeff* k, const double* d_u, int64_t n, double* d_k, double* d_dk, void* stream) {

@@ -90,6 +90,9 @@ struct fem_mesh {
     bool have_boundary = false;
     int64_t n_bfacets = 0;
     fem::DevBuf bfacet, bnode_ptr, bnode_inc, bscratch, npart;
+    // solver scratch: Krylov vectors and reduction partials; the Newton
+    // step's matrices and vectors
+    fem::DevBuf solve, newton;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_ev[4] = {};
     size_t device_bytes() const;
@@ -115,6 +118,13 @@ int csr_residual(fem_mesh& m, const double* vM, const double* vK, const double* 
                  double dt, double* F, double* norms, cudaStream_t s);
 int csr_jacobian(const fem_mesh& m, double dt, const double* vM, const double* vMt, const double* vK,
                  const double* vT, const double* vB, double* vJ, cudaStream_t s);
+// Jacobi-preconditioned BiCGStab for A x = b on the mesh pattern (solve.cu)
+int bicgstab(fem_mesh& m, const double* A, const double* b, double* x, double rtol, int maxit, int* iters,
+             double* relres, cudaStream_t s);
+// one implicit Euler step by Newton's method (solve.cu)
+int heat_step(fem_mesh& m, const fem_coeff* k, const CoeffDev& g, const unsigned char* mask, double dt,
+              const double* us, double* u, double newton_rtol, int max_newton, double krylov_rtol, int max_krylov,
+              fem_heat_report* rep, cudaStream_t s);
 
 // Element products V = X Q.  Any of VM, VK, VT may be null (matrix skipped).
 int element_simt_fp64(const fem_mesh& m, const CoeffDev& k, const double* u, double* VM, double* VK, double* VT,
