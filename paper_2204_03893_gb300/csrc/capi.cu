@@ -135,6 +135,12 @@ CoeffDev to_dev(const fem_coeff* k) {
     } else {
         for (int i = 0; i < k->n; ++i) c.p[i] = k->p[i];   // unused parameters stay zero
     }
+    if (k->kind == FEM_K_POLY) {
+        // Zero leading coefficients are dropped: the device Horner of the
+        // remaining degree gives the same bits (the dropped steps only carry
+        // exact zeros) and is specialised for short polynomials.
+        while (c.n > 1 && c.p[c.n - 1] == 0.0) --c.n;
+    }
     return c;
 }
 

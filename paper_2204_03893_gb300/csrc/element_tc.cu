@@ -107,6 +107,35 @@ __device__ int g_tc_err;
 
 constexpr long long WAIT_LIMIT = 2000000000LL;   // SM clocks (~1 s)
 
+// Per-phase SM clock counters, compiled in only with -DFEM_PHASE_TIMERS (the
+// default build has none): thread 0 of each CTA adds the clocks spent since
+// its previous mark to a slot of g_phase (summed over CTAs), so a phase's
+// share of a tile is read from thread 0's timeline.  Slots 0-4: tile kernel
+// (formation incl. the barrier, MMA issue, MMA wait, epilogue, tiles);
+// 8-14: chunked kernel (tile gathers, formation, copy wait, MMA issue, MMA
+// wait, epilogue, tiles).
+struct PhaseTimer {
+#ifdef FEM_PHASE_TIMERS
+    long long last = 0;
+    __device__ __forceinline__ void start() {
+        if (threadIdx.x == 0) last = clock64();
+    }
+    __device__ __forceinline__ void mark(int slot, long long add = -1);
+#else
+    __device__ __forceinline__ void start() {}
+    __device__ __forceinline__ void mark(int, long long = -1) {}
+#endif
+};
+#ifdef FEM_PHASE_TIMERS
+__device__ unsigned long long g_phase[16];
+__device__ __forceinline__ void PhaseTimer::mark(int slot, long long add) {
+    if (threadIdx.x != 0) return;
+    const long long t = clock64();
+    atomicAdd(&g_phase[slot], (unsigned long long)(add >= 0 ? add : t - last));
+    last = t;
+}
+#endif
+
 // store one thread's X row (Kp values) as TF32 hi / lo parts
 template <int Kp>
 __device__ __forceinline__ void store_row(unsigned char* hi, unsigned char* lo, const float (&x)[Kp], int r) {
@@ -569,6 +598,8 @@ __global__ void __launch_bounds__(TcL<ETy>::TPR * TILE, TcL<ETy>::MINB) element_
         fetch_meta(blockIdx.x);
         fetch_u();
     }
+    PhaseTimer pt;
+    pt.start();
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         // the whole packed row is written (unrequested parts too: every
         // matrix's slices overlap its neighbours' columns); with two threads
@@ -596,11 +627,13 @@ __global__ void __launch_bounds__(TcL<ETy>::TPR * TILE, TcL<ETy>::MINB) element_
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         __syncthreads();
+        pt.mark(0);
         if (tid == 0) {
             tc::fence_after_sync();
             issue_tile<L>(tmem, sXu, sQu, doM, doK, doT);
             tc::mma_commit(mb);
         }
+        pt.mark(1);
         if (next < ntiles) fetch_u();
         // one thread waits (the other warps sleep at the barrier instead of
         // spinning on the mbarrier and taking issue slots from other CTAs)
@@ -611,6 +644,7 @@ __global__ void __launch_bounds__(TcL<ETy>::TPR * TILE, TcL<ETy>::MINB) element_
             timed_out = true;
             break;
         }
+        pt.mark(2);
         tc::fence_after_sync();
         if (half == 0) {
             const int64_t row0 = tile * TILE + warp * 32;
@@ -620,6 +654,8 @@ __global__ void __launch_bounds__(TcL<ETy>::TPR * TILE, TcL<ETy>::MINB) element_
         }
         tc::fence_before_sync();
         __syncthreads();
+        pt.mark(3);
+        pt.mark(4, 1);
     }
     if (timed_out) {
         if (tid == 0) atomicExch(err, 1);
@@ -914,6 +950,8 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
     float* VMK = doM ? VM : doK ? VK - 1 : nullptr;   // interleaved M/K storage (K at odd positions)
     const bool need_u = doK | doT;
     const int64_t e = first + r;
+    PhaseTimer pt;
+    pt.start();
     // element data for the whole tile: u differences (hi/lo split, as in
     // form_x) and the geometry
     float du[NP], A[NS];
@@ -942,6 +980,7 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
     const uint32_t sXu = tc::smem_u32(sX), sQu = tc::smem_u32(sQ);
     const int64_t row0 = first + warp * 32;
     float* stage = reinterpret_cast<float*>(smem);
+    pt.mark(8);
 #pragma unroll 1
     for (int s = 0; s < L::NSTEP; ++s) {
         const int kd = L::kind(s), c = L::chunk(s);
@@ -975,10 +1014,12 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
                 store_row_part<L::KcT, KH>(sX, sX + TILE * L::KcT * 4, x, r, half * KH);
             }
             tc::fence_proxy_async_smem();
+            pt.mark(9);
             uint32_t okq = 1;
             if (tid == 0) okq = tc::mbar_wait_bounded(mb_q, ph_q, WAIT_LIMIT);
             tc::fence_before_sync();
             if (__syncthreads_or(!okq)) return false;
+            pt.mark(10);
             ph_q ^= 1u;
             pend_q = false;
             if (tid == 0) {
@@ -1003,10 +1044,12 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
                 }
                 tc::mma_commit(mb_mma);
             }
+            pt.mark(11);
             pend_mma = true;
             uint32_t okm = 1;
             if (tid == 0) okm = tc::mbar_wait_bounded(mb_mma, ph_mma, WAIT_LIMIT);
             if (__syncthreads_or(!okm)) return false;
+            pt.mark(12);
             ph_mma ^= 1u;
             pend_mma = false;
             tc::fence_after_sync();
@@ -1026,8 +1069,10 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
             }
             tc::fence_before_sync();
             __syncthreads();
+            pt.mark(13);
         }
     }
+    pt.mark(14, 1);
     return true;
 }
 
@@ -1985,6 +2030,18 @@ int batch_tc_chunked_launch(const BatchItem* items, int nitems, const BatchMesh*
 }
 
 int tc_chunked_supported(int type) { return type == 5 && ChL<ET<3, 3>>::OK; }
+
+#ifdef FEM_PHASE_TIMERS
+// Reads (and optionally clears) the 16 phase counters of a timer build.
+extern "C" int fem_debug_phase_cycles(unsigned long long* out, int clear) {
+    if (cudaMemcpyFromSymbol(out, g_phase, sizeof(unsigned long long) * 16) != cudaSuccess) return FEM_ECUDA;
+    if (clear) {
+        unsigned long long z[16] = {};
+        if (cudaMemcpyToSymbol(g_phase, z, sizeof z) != cudaSuccess) return FEM_ECUDA;
+    }
+    return FEM_OK;
+}
+#endif
 
 int tc_error_flag(int clear) {
     int v = 0;

@@ -108,13 +108,46 @@ __device__ __forceinline__ float2 split_f64(double v) {
     return split_f64_edge(v);
 }
 
-// k(u) and k'(u).  Loops run over the fixed maxima (8 polynomial
-// coefficients, 8 knots) with predicates so that the parameters stay in the
-// kernel-parameter space instead of being copied to local memory; unused
-// parameters are zero.
+// Horner for a polynomial with N coefficients and its derivative at once.
+// It performs the same operations as the 8-coefficient loop below does on a
+// polynomial whose leading 8 - N coefficients are zero (those steps only
+// carry exact zeros), so both give the same bits for finite u.
+template <typename T, int N>
+__device__ __forceinline__ T horner_n(const CoeffDev& c, T u, T& dk) {
+    if constexpr (N == 1) {
+        dk = T(0);
+        return T(c.p[0]);
+    } else {
+        T v = T(c.p[N - 1]);
+        T dv = v;
+        v = v * u + T(c.p[N - 2]);
+#pragma unroll
+        for (int i = N - 3; i >= 0; --i) {
+            dv = dv * u + v;
+            v = v * u + T(c.p[i]);
+        }
+        dk = dv;
+        return v;
+    }
+}
+
+// k(u) and k'(u).  Polynomials of up to 5 coefficients take a Horner of
+// their own degree (the branch is uniform: the law is a kernel parameter, and
+// the host drops zero leading coefficients); longer ones, and the knot loop, run over
+// the fixed maxima (8 coefficients, 8 knots) with predicates so that the
+// parameters stay in the kernel-parameter space instead of being copied to
+// local memory; unused parameters are zero.
 template <typename T>
 __device__ __forceinline__ T k_eval(const CoeffDev& c, T u, T& dk) {
     if (c.kind == 0) {
+        switch (c.n) {
+            case 1: return horner_n<T, 1>(c, u, dk);
+            case 2: return horner_n<T, 2>(c, u, dk);
+            case 3: return horner_n<T, 3>(c, u, dk);
+            case 4: return horner_n<T, 4>(c, u, dk);
+            case 5: return horner_n<T, 5>(c, u, dk);
+            default: break;
+        }
         T v = T(0), dv = T(0);
 #pragma unroll
         for (int i = 7; i >= 0; --i) {
