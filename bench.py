@@ -624,6 +624,22 @@ def measure_sweep(F, torch, stream, name, precs=("tf32x3", "fp64"), nsweep=10, w
     return out
 
 
+def phase_bytes(mesh, nnz: int, esz: int):
+    """Algorithmic bytes of one reassembly of M, K, T: (element phase, CSR sum).
+    Element phase: connectivity (4 B per node of an element), the geometry
+    cache (b and the d(d+1)/2 entries of A), V written (2 n_sym + n_p^2
+    values), u read once.  CSR sum: an 8-byte head word per group of 32
+    contributions, every contribution's 4-byte index and V entries, the CSR
+    values written."""
+    d, E, n = mesh.d, mesh.n_elems, mesh.n_nodes
+    n_p = mesh.conn.shape[1]
+    nsym, nt, ngeo = n_p * (n_p + 1) // 2, n_p * n_p, 1 + d * (d + 1) // 2
+    nc = E * n_p * n_p
+    form = E * (n_p * 4 + ngeo * esz + (2 * nsym + nt) * esz) + n * 8
+    summ = (nc + 31) // 32 * 8 + nc * 4 + E * (2 * nsym + nt) * esz + 3 * nnz * esz
+    return form, summ
+
+
 def measure_batched(F, torch, stream, wls, steps=50, warmup=5):
     """64 meshes of uneven size and type (2D/3D, P1-P3, 1e3-2e5 elements,
     log-uniform) reassembled (M, K, T) per launch: one CUDA graph of
@@ -658,6 +674,7 @@ def measure_batched(F, torch, stream, wls, steps=50, warmup=5):
             F.fem_device_status(sh)
             ms = a.elapsed_time(z) / steps
             info = F.fem_batch_get_info(b)
+            nbytes = sum(sum(phase_bytes(w.mesh, fm.nnz, 4)) for w, fm in zip(wls, fms))
             # bit-identity with single-mesh calls on three meshes
             same = True
             for i in (0, len(wls) // 2, len(wls) - 1):
@@ -713,6 +730,10 @@ def measure_batched(F, torch, stream, wls, steps=50, warmup=5):
             "unit": "elements/s", "ms_per_launch": ms, "steps": steps,
             "per_mesh_launches": {"value": E_tot / (ms_pm / 1e3), "ms": ms_pm, "launches": 2 * len(wls),
                                   "by_type": by_type},
+            "roofline": {"bound": "hbm", "algorithmic_bytes_per_launch": nbytes,
+                         "achieved": nbytes / (ms / 1e3) / 1e9, "peak": measured_peaks()[0], "unit": "GB/s",
+                         "frac": nbytes / (ms / 1e3) / 1e9 / measured_peaks()[0],
+                         "note": "element phases and CSR sums of all meshes (bench.py phase_bytes) / launch time"},
             "kernels_per_launch": info.kernels_per_launch, "graph": bool(info.graph),
             "tuned": {"sum_block": info.sum_block, "simt_grid": info.simt_grid, "ms": info.tuned_ms},
             "tc_tiles": info.tc_tiles, "simt_blocks": info.simt_blocks,
@@ -734,10 +755,10 @@ def measure_serve(F, torch, wls, n_requests=20000, rates=(1000.0, 3000.0, 10000.
     rng = np.random.default_rng(seed)
     fields = [[mg.fourier_field(m.coords, 5000 + 3 * j + t) for t in range(2)] for j, m in enumerate(meshes)]
     laws = [(w.coeff.kind, w.coeff.params) for w in wls] + [("sin", (2.0, 1.0, 3.0))] * len(large)
-    S = FemServer("tf32x3", budget_bytes=120 * 10**9, max_inflight=16, n_streams=8, max_queue=1 << 20)
+    S = FemServer("tf32x3", budget_bytes=120 * 10**9, max_inflight=64, n_streams=8, max_queue=1 << 20, fuse_min=2)
     out = {"workload": "REASSEMBLE of M, K, T over 66 resident meshes (64 batched + 2 tet P2 of 998,250 elements "
-                       "taking 5% of requests); Poisson arrivals", "budget_bytes": 120 * 10**9, "max_inflight": 16,
-           "n_streams": 8, "precision": "tf32x3"}
+                       "taking 5% of requests); Poisson arrivals", "budget_bytes": 120 * 10**9, "max_inflight": 64,
+           "n_streams": 8, "fuse_min": 2, "precision": "tf32x3"}
     try:
         t0 = time.perf_counter()
         tick = [S.assemble(m, laws[j][0], laws[j][1], fields[j][0]) for j, m in enumerate(meshes)]
@@ -773,27 +794,59 @@ def measure_serve(F, torch, wls, n_requests=20000, rates=(1000.0, 3000.0, 10000.
                 tq.put(None)
 
             th = threading.Thread(target=submitter)
+            st0 = S.stats()
             w0 = time.perf_counter()
             th.start()
             lat, first, last, elems = [], None, None, 0
-            while True:
-                item = tq.get()
-                if item is None:
-                    break
-                j, t = item
-                r = F.fem_serve_poll(S.h, t, 120_000_000)
+            wait_ms, run_ms = [], []
+            # results are taken in completion order (fem_serve_next_done) and
+            # released at once, as a client would
+            mesh_of = {}
+            got = 0
+            while got < n:
+                while True:
+                    try:
+                        item = tq.get_nowait()
+                    except queue.Empty:
+                        break
+                    if item is not None:
+                        mesh_of[item[1]] = item[0]
+                t = F.fem_serve_next_done(S.h, 120_000_000)
+                while t not in mesh_of:
+                    item = tq.get()
+                    if item is not None:
+                        mesh_of[item[1]] = item[0]
+                j = mesh_of.pop(t)
+                got += 1
+                r = F.fem_serve_poll(S.h, t, 0)
                 if r.status != 0:
                     raise RuntimeError(f"REASSEMBLE failed with status {r.status}")
                 lat.append((r.t_done_us - r.t_submit_us) / 1e3)
+                wait_ms.append((r.t_start_us - r.t_submit_us) / 1e3)
+                run_ms.append((r.t_done_us - r.t_start_us) / 1e3)
                 first = r.t_submit_us if first is None else min(first, r.t_submit_us)
                 last = r.t_done_us if last is None else max(last, r.t_done_us)
                 elems += E_of[j]
                 F.fem_serve_release(S.h, t)
             th.join()
             span = (last - first) / 1e6
+            st1 = S.stats()
+            fl = st1.fused_launches - st0.fused_launches
+            fr = st1.fused_requests - st0.fused_requests
+            sl = st1.single_launches - st0.single_launches
             sweeps.append({"offered_req_per_s": rate if rate is not None else "all at once",
                            "requests": n, "req_per_s": n / span, "elements_per_s": elems / span,
-                           "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "wall_s": time.perf_counter() - w0})
+                           "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "wall_s": time.perf_counter() - w0,
+                           # where a request's time goes: waiting for admission (queue, busy mesh,
+                           # in-flight limit) and from start to completion seen by the scheduler
+                           # (device work, incl. waiting behind other launches); the scheduler's own
+                           # time enqueueing launches per request
+                           "split": {"wait_p50_ms": _pct(wait_ms, 50), "run_p50_ms": _pct(run_ms, 50),
+                                     "scheduler_enqueue_us_per_request":
+                                         (st1.host_start_us - st0.host_start_us) / max(n, 1),
+                                     "fused_launches": int(fl), "requests_per_fused_launch": fr / fl if fl else 0.0,
+                                     "single_launches": int(sl),
+                                     "batch_builds": int(st1.batch_builds - st0.batch_builds)}})
         out["sweeps"] = sweeps
         out["peak_bytes"] = int(S.stats().peak_bytes)
         # accuracy of served results: bitwise against single-mesh calls, and
@@ -959,10 +1012,7 @@ def run_ours(args, rank, world, local_rank):
     esz = 8 if args.prec == "fp64" else 4
     n = wl.mesh.n_nodes
     nc = E * n_p * n_p
-    bytes_form = E * (n_p * 4 + ngeo * esz + (2 * nsym + nt) * esz) + n * 8
-    # per group of 32 contributions an 8-byte head word; every contribution's
-    # 4-byte index and V entries; the CSR values written
-    bytes_sum = (nc + 31) // 32 * 8 + nc * 4 + E * (2 * nsym + nt) * esz + 3 * nnz * esz
+    bytes_form, bytes_sum = phase_bytes(wl.mesh, nnz, esz)
     mf, msum = statistics.mean(form_ms), statistics.mean(sum_ms)
     on_tc = args.prec in ("tf32x3", "bf16x3", "bf16x6")
     fp64 = args.prec == "fp64"

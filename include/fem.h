@@ -338,7 +338,10 @@ typedef struct fem_batch fem_batch;
 /* Every mesh must have run fem_symbolic.  Allocates the meshes' element
  * scratch for the batch precision, builds the work lists and (unless tuning
  * is requested) captures the graph.  Synchronises `stream`.  While a batch
- * launch is in flight, its meshes must not be used by other calls. */
+ * launch is in flight, its meshes must not be used by other calls.  While
+ * the graph is captured (here, or after tuning in the first launch), no
+ * other thread may synchronise the whole device: CUDA refuses that during a
+ * stream capture. */
 int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts, void* stream, fem_batch** out);
 /* One reassembly of every mesh i: k[i] (law), d_u[i] (FP64 device nodal
  * values, may be NULL if mesh i needs M only), outputs d_vM[i], d_vK[i],
@@ -373,7 +376,16 @@ int fem_batch_destroy(fem_batch* b);
  * queue full, is refused at submit with FEM_EBUSY.  An ASSEMBLE request builds
  * the mesh and its pattern on the scheduler thread (it synchronises its
  * stream there), then reassembles it.  Results are the same values as
- * fem_assemble_all with the same precision. */
+ * fem_assemble_all with the same precision.
+ *
+ * Fused launches (fuse_min > 0; FEM_FP64, FEM_TF32X3 and FEM_FP32 servers):
+ * when at least fuse_min REASSEMBLE requests of idle meshes are startable,
+ * they start together as one launch of a batch (fem_batch_*) over all
+ * resident meshes, the meshes without a request in it skipped, on a stream
+ * of its own.  The batch is rebuilt (the scheduler waits for the device
+ * then) when the set of resident meshes has changed since it was built.
+ * Batched results carry the same bits as single-mesh calls, so fusing
+ * changes no value.  Fewer startable requests start one by one as above. */
 enum { FEM_REQ_ASSEMBLE = 1, FEM_REQ_REASSEMBLE = 2 };
 typedef struct {
     int prec;             /* FEM_FP64, FEM_TF32X3 or FEM_FP32 for every request */
@@ -381,6 +393,8 @@ typedef struct {
     int n_streams;        /* CUDA streams the requests are spread over, 1..64 */
     int max_queue;        /* pending requests before submit refuses (FEM_EBUSY) */
     size_t budget_bytes;  /* device bytes for resident meshes + unreleased outputs */
+    int fuse_min;         /* fuse this many startable REASSEMBLE requests or more; 0: never */
+    int reserved;
 } fem_serve_opts;
 typedef struct {
     int kind;                    /* FEM_REQ_ASSEMBLE or FEM_REQ_REASSEMBLE */
@@ -406,10 +420,19 @@ typedef struct {
 typedef struct {
     int pending, inflight, resident_meshes;
     size_t bytes_in_use, peak_bytes;
+    int64_t single_launches;    /* requests started one by one */
+    int64_t fused_launches;     /* fused launches, and the requests they carried */
+    int64_t fused_requests;
+    int64_t batch_builds;       /* builds of the fused launches' batch */
+    double host_start_us;       /* scheduler time spent enqueueing device work (incl. batch builds) */
 } fem_serve_counters;
 typedef struct fem_server fem_server;
 
-/* Creates a server on the current device (starts its scheduler thread). */
+/* Creates a server on the current device (starts its scheduler thread).
+ * Raises the release threshold of the device's default memory pool (the
+ * source of request outputs) to budget_bytes if it is lower, so that freed
+ * outputs stay mapped for later requests; the setting belongs to this
+ * process's context and ends with it. */
 int fem_serve_create(const fem_serve_opts* opts, fem_server** out);
 /* Copies the request's inputs and queues it; *ticket identifies it. */
 int fem_serve_submit(fem_server* s, const fem_request* req, uint64_t* ticket);
@@ -417,6 +440,13 @@ int fem_serve_submit(fem_server* s, const fem_request* req, uint64_t* ticket);
  * finished (out->status is the request's own status), FEM_EAGAIN if
  * timeout_us <= 0 and it has not, FEM_ETIMEOUT if the wait ran out. */
 int fem_serve_poll(fem_server* s, uint64_t ticket, int timeout_us, fem_result* out);
+/* Completion order: waits up to timeout_us for a finished request that no
+ * earlier call returned and that is not released, and stores its ticket
+ * (then fem_serve_poll gives its result at once).  FEM_EAGAIN if
+ * timeout_us <= 0 and none is ready, FEM_ETIMEOUT if the wait ran out.
+ * Lets a client release results as they finish instead of in submission
+ * order, where one slow mesh would hold every later result's memory. */
+int fem_serve_next_done(fem_server* s, int timeout_us, uint64_t* ticket);
 /* Frees a finished request's outputs (the caller's reads of them must have
  * completed) and forgets the ticket. */
 int fem_serve_release(fem_server* s, uint64_t ticket);

@@ -19,7 +19,8 @@ __all__ = [
     "fem_assemble_all", "fem_assemble_mass_u", "fem_mesh_set_conductivity", "fem_reference_tables", "fem_set_allocator", "fem_last_error", "fem_version",
     "fem_device_status", "fem_batch_create", "fem_batch_launch", "fem_batch_get_info", "fem_batch_destroy",
     "fem_batch_opts", "fem_batch_info", "fem_serve_opts", "fem_request", "fem_result", "fem_serve_counters",
-    "fem_serve_create", "fem_serve_submit", "fem_serve_poll", "fem_serve_release", "fem_serve_evict",
+    "fem_serve_create", "fem_serve_submit", "fem_serve_poll", "fem_serve_next_done", "fem_serve_release",
+    "fem_serve_evict",
     "fem_serve_stats", "fem_serve_destroy", "FEM_REQ_ASSEMBLE", "FEM_REQ_REASSEMBLE", "fem_form_elements", "fem_sum_elements", "fem_chunk_plan", "fem_form_elements_range",
     "fem_sum_elements_range", "coeff", "FEM_MAT_M", "FEM_MAT_K", "FEM_MAT_T", "FEM_OK", "FEM_EINVAL", "FEM_ENOMEM", "FEM_EDEGENERATE", "FEM_ECUDA",
     "FEM_EBUSY", "FEM_EAGAIN", "FEM_ETIMEOUT", "FEM_ESTATE", "FEM_FP64", "FEM_TF32X3", "FEM_FP32", "FEM_BF16X3",
@@ -93,7 +94,7 @@ class fem_batch_info(C.Structure):
 
 class fem_serve_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("max_inflight", C.c_int), ("n_streams", C.c_int), ("max_queue", C.c_int),
-                ("budget_bytes", C.c_size_t)]
+                ("budget_bytes", C.c_size_t), ("fuse_min", C.c_int), ("reserved", C.c_int)]
 
 
 class fem_request(C.Structure):
@@ -110,7 +111,9 @@ class fem_result(C.Structure):
 
 class fem_serve_counters(C.Structure):
     _fields_ = [("pending", C.c_int), ("inflight", C.c_int), ("resident_meshes", C.c_int),
-                ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t)]
+                ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t), ("single_launches", C.c_int64),
+                ("fused_launches", C.c_int64), ("fused_requests", C.c_int64), ("batch_builds", C.c_int64),
+                ("host_start_us", C.c_double)]
 
 
 _lock = threading.Lock()
@@ -144,6 +147,7 @@ _SIGS = {
     "fem_serve_submit": ([C.c_void_p, C.POINTER(fem_request), C.POINTER(C.c_uint64)], C.c_int),
     "fem_serve_poll": ([C.c_void_p, C.c_uint64, C.c_int, C.POINTER(fem_result)], C.c_int),
     "fem_serve_release": ([C.c_void_p, C.c_uint64], C.c_int),
+    "fem_serve_next_done": ([C.c_void_p, C.c_int, C.POINTER(C.c_uint64)], C.c_int),
     "fem_serve_evict": ([C.c_void_p, C.c_uint64], C.c_int),
     "fem_serve_stats": ([C.c_void_p, C.POINTER(fem_serve_counters)], C.c_int),
     "fem_serve_destroy": ([C.c_void_p], C.c_int),
@@ -462,6 +466,18 @@ def fem_serve_poll(server: int, ticket: int, timeout_us: int = 0) -> fem_result 
         return None
     _check(rc)
     return out
+
+
+def fem_serve_next_done(server: int, timeout_us: int = 0) -> int | None:
+    """Ticket of a finished request not returned before, in completion order;
+    None if none is ready and timeout_us <= 0.  Raises FemError(FEM_ETIMEOUT)
+    if a wait ran out."""
+    t = C.c_uint64(0)
+    rc = lib().fem_serve_next_done(server, timeout_us, C.byref(t))
+    if rc == FEM_EAGAIN:
+        return None
+    _check(rc)
+    return int(t.value)
 
 
 def fem_serve_release(server: int, ticket: int) -> None:

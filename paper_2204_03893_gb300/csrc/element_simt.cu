@@ -447,6 +447,7 @@ __global__ void __launch_bounds__(BT) batch_simt_kernel(const BatchItem* __restr
         const BatchItem w = items[it];
         const BatchMesh& bm = meshes[w.mesh];
         const int64_t e = w.first + threadIdx.x;
+        if (!(bm.vM || bm.vK || bm.vT)) continue;   // mesh skipped in this launch
         if (threadIdx.x >= w.count || e >= bm.E) continue;
         const T* geo = static_cast<const T*>(sizeof(T) == 8 ? (const void*)bm.geo64 : (const void*)bm.geo32);
         const double* u = bm.u;

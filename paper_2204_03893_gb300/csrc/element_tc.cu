@@ -362,14 +362,18 @@ __device__ __forceinline__ void epilogue_tile(uint32_t tmem, int colM, int colK,
 // pairs (PAIR: 8-byte stores, whole sectors, so L2 holds them without
 // fetching the sectors from DRAM), then K into the odd positions of the
 // same, still cached, sectors.
+// The warp reads TMEM lane quadrant `quad` (its own: warp mod 4), stages
+// through tile `slot`, and drains the 32-column chunks part, part + parts, ...
+// (so two warps of one quadrant can split a block).
 template <int N, int LD = N, int CS = 1, bool PAIR = false>
 __device__ __forceinline__ void epilogue_staged(uint32_t tmem, int col, float* stage_base, float* __restrict__ V,
-                                                int64_t row0, int64_t E, int warp, int lane, int c_off = 0) {
-    float* stage = stage_base + warp * 32 * 33;
+                                                int64_t row0, int64_t E, int quad, int lane, int c_off, int slot,
+                                                int part, int parts) {
+    float* stage = stage_base + slot * 32 * 33;
 #pragma unroll 1
-    for (int c0 = 0; c0 < N; c0 += 32) {
+    for (int c0 = 32 * part; c0 < N; c0 += 32 * parts) {
         uint32_t r[32];
-        tc::tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + col + c0, r);
+        tc::tmem_ld32(tmem + (static_cast<uint32_t>(quad * 32) << 16) + col + c0, r);
 #pragma unroll
         for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
         __syncwarp();
@@ -827,8 +831,16 @@ struct ChL {
     static constexpr int QB_M = NMp * KcM * 8, QB_K = NMp * KcK * 8, QB_Ta = NTa * KcT * 8, QB_Tb = NTb * KcT * 8;
     static constexpr int QBMAX = QB_K > QB_M ? (QB_K > QB_Ta ? QB_K : QB_Ta) : (QB_M > QB_Ta ? QB_M : QB_Ta);
     static constexpr int IMG_BYTES = NCM * QB_M + NCK * QB_K + NCT * (QB_Ta + QB_Tb);
-    static constexpr int SMEM = XBYTES + QBMAX;                          // X chunk + Q chunk
+    // reference tables in shared memory, read with 16-byte broadcast loads:
+    // {phi_i, d phi_i / d xhat_0..2} at (q, i), then phi rows (NP floats per
+    // point), then the weights
+    static constexpr int NP = ETy::NP;
+    static constexpr int TAB_PG = XBYTES + QBMAX, TAB_P = TAB_PG + NQ * NP * 16, TAB_W = TAB_P + NQ * NP * 4;
+    static constexpr int SMEM = TAB_W + ru(NQ * 4, 16);                  // X chunk + Q chunk + tables
+    // the epilogue of all eight warps stages through the X and Q chunks
+    static constexpr int STAGE8_BYTES = 8 * 32 * 33 * 4;
     static constexpr bool OK = NQ % QCM == 0 && NQ % QCK == 0 && NQ % QCT == 0 && KcK % 8 == 0 && KcT % 8 == 0 &&
+                               D == 3 && NP % 4 == 0 && STAGE8_BYTES <= TAB_PG &&
                                NMp <= 256 && NTa <= 256 && NTb <= 256 && NTb % 16 == 0 && NTb > 0 &&
                                QB_Tb <= QBMAX && ALLOC <= 256 && ru(ETy::NSYM, 32) <= ALLOC &&
                                ru(NTa, 32) <= ALLOC && ru(NTb, 32) <= ALLOC && XBYTES >= STAGE_FLOATS * 4 &&
@@ -857,45 +869,54 @@ struct ChL {
 constexpr int CHUNK_IMG_BYTES = ChL<ET<3, 3>>::IMG_BYTES;
 __device__ __align__(128) unsigned char g_tcbig[CHUNK_IMG_BYTES];
 
-// X columns of quadrature points q0 .. q0+QC-1 for one matrix (the same
-// quantities as form_x, restricted to a chunk).
+// X columns of quadrature points q0 .. q0+QC-1 for one matrix: the same
+// quantities as form_x, restricted to a chunk, in the same operations and
+// order.  The reference values come from the shared-memory tables
+// (ChL::TAB_*): a chunk's point index is not a compile-time constant, so
+// constant-bank reads would each be a separate load, while a 16-byte shared
+// load brings four values at once.
 template <typename ETy, int QC>
-__device__ __forceinline__ void form_chunk_m(int q0, float b, float mass, float (&x)[QC]) {
-    constexpr int TO = type_tab_off(ETy::TYPE);
-    constexpr int WQ = TO + ETy::NQ * ETy::NP * (1 + ETy::D);
+__device__ __forceinline__ void form_chunk_m_s(int q0, float b, float mass, const float* __restrict__ tw,
+                                               float (&x)[QC]) {
 #pragma unroll
-    for (int j = 0; j < QC; ++j) x[j] = mass * (c_tcref[WQ + q0 + j] * b);
+    for (int j = 0; j < QC; ++j) x[j] = mass * (tw[q0 + j] * b);
 }
 
 template <typename ETy, int QC>
-__device__ __forceinline__ void form_chunk_k(int q0, const float (&du)[ETy::NP], float u0, float b,
-                                             const float (&A)[ETy::NS], const CoeffDev& k,
-                                             float (&x)[QC * ETy::NS]) {
-    constexpr int NP = ETy::NP, NQ = ETy::NQ, NS = ETy::NS, D = ETy::D;
-    constexpr int TO = type_tab_off(ETy::TYPE);
-    constexpr int PHI = TO, WQ = TO + NQ * NP * (1 + D);
+__device__ __forceinline__ void form_chunk_k_s(int q0, const float (&du)[ETy::NP], float u0, float b,
+                                               const float (&A)[ETy::NS], const CoeffDev& k,
+                                               const float* __restrict__ tp, const float* __restrict__ tw,
+                                               float (&x)[QC * ETy::NS]) {
+    constexpr int NP = ETy::NP, NS = ETy::NS;
 #pragma unroll
     for (int j = 0; j < QC; ++j) {
         const int q = q0 + j;
+        const float4* prow = reinterpret_cast<const float4*>(tp + q * NP);
         float uq = 0.f;
 #pragma unroll
-        for (int i = 0; i < NP; ++i) uq = fmaf(c_tcref[PHI + q * NP + i], du[i], uq);
+        for (int i4 = 0; i4 < NP / 4; ++i4) {
+            const float4 p = prow[i4];
+            uq = fmaf(p.x, du[4 * i4 + 0], uq);
+            uq = fmaf(p.y, du[4 * i4 + 1], uq);
+            uq = fmaf(p.z, du[4 * i4 + 2], uq);
+            uq = fmaf(p.w, du[4 * i4 + 3], uq);
+        }
         uq += u0;
         float dk;
         const float kq = k_eval<float>(k, uq, dk);
-        const float lk = (c_tcref[WQ + q] * b) * kq;
+        const float lk = (tw[q] * b) * kq;
 #pragma unroll
         for (int t = 0; t < NS; ++t) x[j * NS + t] = lk * A[t];
     }
 }
 
 template <typename ETy, int QC>
-__device__ __forceinline__ void form_chunk_t(int q0, const float (&du)[ETy::NP], float u0, float b,
-                                             const float (&A)[ETy::NS], const CoeffDev& k,
-                                             float (&x)[QC * ETy::D]) {
-    constexpr int NP = ETy::NP, NQ = ETy::NQ, D = ETy::D;
-    constexpr int TO = type_tab_off(ETy::TYPE);
-    constexpr int PHI = TO, GR = TO + NQ * NP, WQ = TO + NQ * NP * (1 + D);
+__device__ __forceinline__ void form_chunk_t_s(int q0, const float (&du)[ETy::NP], float u0, float b,
+                                               const float (&A)[ETy::NS], const CoeffDev& k,
+                                               const float4* __restrict__ tpg, const float* __restrict__ tw,
+                                               float (&x)[QC * ETy::D]) {
+    constexpr int NP = ETy::NP, D = ETy::D;
+    static_assert(D == 3, "one 16-byte entry holds phi and a 3-component gradient");
 #pragma unroll
     for (int j = 0; j < QC; ++j) {
         const int q = q0 + j;
@@ -904,14 +925,16 @@ __device__ __forceinline__ void form_chunk_t(int q0, const float (&du)[ETy::NP],
         for (int a = 0; a < D; ++a) g[a] = 0.f;
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-            uq = fmaf(c_tcref[PHI + q * NP + i], du[i], uq);
-#pragma unroll
-            for (int a = 0; a < D; ++a) g[a] = fmaf(c_tcref[GR + (q * NP + i) * D + a], du[i], g[a]);
+            const float4 t = tpg[q * NP + i];
+            uq = fmaf(t.x, du[i], uq);
+            g[0] = fmaf(t.y, du[i], g[0]);
+            g[1] = fmaf(t.z, du[i], g[1]);
+            g[2] = fmaf(t.w, du[i], g[2]);
         }
         uq += u0;
         float dk;
         k_eval<float>(k, uq, dk);
-        const float ld = (c_tcref[WQ + q] * b) * dk;
+        const float ld = (tw[q] * b) * dk;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             float sacc = 0.f;
@@ -923,6 +946,24 @@ __device__ __forceinline__ void form_chunk_t(int q0, const float (&du)[ETy::NP],
             x[j * D + a] = ld * sacc;
         }
     }
+}
+
+// Fills the chunked kernel's shared-memory tables from the constant bank
+// (all threads; once per CTA, before the CTA's first barrier).
+template <typename ETy>
+__device__ __forceinline__ void chunk_tables_fill(unsigned char* smem) {
+    using L = ChL<ETy>;
+    constexpr int NP = ETy::NP, NQ = ETy::NQ, D = ETy::D;
+    constexpr int TO = type_tab_off(ETy::TYPE);
+    constexpr int PHI = TO, GR = TO + NQ * NP, WQ = TO + NQ * NP * (1 + D);
+    float4* pg = reinterpret_cast<float4*>(smem + L::TAB_PG);
+    float* p = reinterpret_cast<float*>(smem + L::TAB_P);
+    float* w = reinterpret_cast<float*>(smem + L::TAB_W);
+    for (int i = threadIdx.x; i < NQ * NP; i += blockDim.x) {
+        pg[i] = make_float4(c_tcref[PHI + i], c_tcref[GR + i * D + 0], c_tcref[GR + i * D + 1], c_tcref[GR + i * D + 2]);
+        p[i] = c_tcref[PHI + i];
+    }
+    for (int q = threadIdx.x; q < NQ; q += blockDim.x) w[q] = c_tcref[WQ + q];
 }
 
 // Threads of a chunked-product CTA: two per element row.  Thread tid works
@@ -978,7 +1019,12 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
     unsigned char* sX = smem;
     unsigned char* sQ = smem + L::XBYTES;
     const uint32_t sXu = tc::smem_u32(sX), sQu = tc::smem_u32(sQ);
-    const int64_t row0 = first + warp * 32;
+    const float4* tpg = reinterpret_cast<const float4*>(smem + L::TAB_PG);
+    const float* tp = reinterpret_cast<const float*>(smem + L::TAB_P);
+    const float* tw = reinterpret_cast<const float*>(smem + L::TAB_W);
+    // epilogue: warp w drains lane quadrant w mod 4, every other 32-column chunk
+    const int quad = warp & 3, part = warp >> 2;
+    const int64_t row0 = first + quad * 32;
     float* stage = reinterpret_cast<float*>(smem);
     pt.mark(8);
 #pragma unroll 1
@@ -1000,17 +1046,17 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
             if (kd == 0) {
                 constexpr int QH = L::QCM / 2, KH = L::KcM / 2;
                 float x[KH];
-                form_chunk_m<ETy, QH>(c * L::QCM + half * QH, b, mass, x);
+                form_chunk_m_s<ETy, QH>(c * L::QCM + half * QH, b, mass, tw, x);
                 store_row_part<L::KcM, KH>(sX, sX + TILE * L::KcM * 4, x, r, half * KH);
             } else if (kd == 1) {
                 constexpr int QH = L::QCK / 2, KH = L::KcK / 2;
                 float x[KH];
-                form_chunk_k<ETy, QH>(c * L::QCK + half * QH, du, u0, b, A, k, x);
+                form_chunk_k_s<ETy, QH>(c * L::QCK + half * QH, du, u0, b, A, k, tp, tw, x);
                 store_row_part<L::KcK, KH>(sX, sX + TILE * L::KcK * 4, x, r, half * KH);
             } else {   // both halves of T use the same X columns
                 constexpr int QH = L::QCT / 2, KH = L::KcT / 2;
                 float x[KH];
-                form_chunk_t<ETy, QH>(c * L::QCT + half * QH, du, u0, b, A, k, x);
+                form_chunk_t_s<ETy, QH>(c * L::QCT + half * QH, du, u0, b, A, k, tpg, tw, x);
                 store_row_part<L::KcT, KH>(sX, sX + TILE * L::KcT * 4, x, r, half * KH);
             }
             tc::fence_proxy_async_smem();
@@ -1055,18 +1101,22 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
             tc::fence_after_sync();
         }
         // drain the pass's accumulator once its last chunk is in (the stage
-        // area aliases the X chunk, which the completed MMAs no longer read)
+        // tiles alias the X and Q chunks, which the completed MMAs no longer
+        // read and the next step's copy only overwrites after the barrier
+        // below); all eight warps, two per TMEM lane quadrant
         if (active && L::last_of_pass(s)) {
-            if (warp < TILE / 32) {   // the warps that own the TMEM lanes of the tile's rows
-                if (kd == 0)
-                    epilogue_staged<ETy::NSYM, 2 * ETy::NSYM, 2, true>(tmem, 0, stage, VMK, row0, E, warp, lane);
-                else if (kd == 1)
-                    epilogue_staged<ETy::NSYM, 2 * ETy::NSYM, 2>(tmem, 0, stage, VMK, row0, E, warp, lane, 1);
-                else if (kd == 2)
-                    epilogue_staged<L::NTa, ETy::NT>(tmem, 0, stage, VT, row0, E, warp, lane, 0);
-                else
-                    epilogue_staged<ETy::NT - L::NTa, ETy::NT>(tmem, 0, stage, VT, row0, E, warp, lane, L::NTa);
-            }
+            if (kd == 0)
+                epilogue_staged<ETy::NSYM, 2 * ETy::NSYM, 2, true>(tmem, 0, stage, VMK, row0, E, quad, lane, 0, warp,
+                                                                   part, 2);
+            else if (kd == 1)
+                epilogue_staged<ETy::NSYM, 2 * ETy::NSYM, 2>(tmem, 0, stage, VMK, row0, E, quad, lane, 1, warp, part,
+                                                             2);
+            else if (kd == 2)
+                epilogue_staged<L::NTa, ETy::NT>(tmem, 0, stage, VT, row0, E, quad, lane, 0, warp, part, 2);
+            else
+                epilogue_staged<ETy::NT - L::NTa, ETy::NT>(tmem, 0, stage, VT, row0, E, quad, lane, L::NTa, warp, part,
+                                                           2);
+            tc::fence_proxy_async_smem();   // stage writes before the next bulk copy into the Q chunk
             tc::fence_before_sync();
             __syncthreads();
             pt.mark(13);
@@ -1092,6 +1142,7 @@ __global__ void __launch_bounds__(CT, 2) element_tc_chunked_kernel(
         tc::mbar_init(mb_q, 1);
         tc::fence_mbar_init();
     }
+    chunk_tables_fill<ETy>(smem);
     if (warp == 0) {
         tc::tmem_alloc(tc::smem_u32(&tmem_slot), L::ALLOC);
         tc::tmem_relinquish();
@@ -1136,6 +1187,7 @@ __global__ void __launch_bounds__(CT, 2) batch_tc_chunked_kernel(const BatchItem
         tc::mbar_init(mb_q, 1);
         tc::fence_mbar_init();
     }
+    chunk_tables_fill<ETy>(smem);
     if (warp == 0) {
         tc::tmem_alloc(tc::smem_u32(&tmem_slot), L::ALLOC);
         tc::tmem_relinquish();

@@ -520,6 +520,7 @@ __global__ void __launch_bounds__(512) batch_scatter_kernel(const BatchItem* __r
         T* vM = static_cast<T*>(bm.vM);
         T* vK = static_cast<T*>(bm.vK);
         T* vT = static_cast<T*>(bm.vT);
+        if (!(vM || vK || vT)) continue;   // mesh skipped in this launch (warp-uniform)
         const T* VM = vM ? static_cast<const T*>(bm.VM) : nullptr;
         const T* VK = vK ? static_cast<const T*>(bm.VK) : nullptr;
         const T* VT = vT ? static_cast<const T*>(bm.VT) : nullptr;

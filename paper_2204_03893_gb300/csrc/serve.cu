@@ -18,6 +18,14 @@
 // streams, so work of different meshes overlaps on the device; completion is
 // detected with CUDA events.  A request that can never fit the budget is
 // refused at submit (FEM_EBUSY).
+//
+// Fused launches: when at least fuse_min REASSEMBLE requests of idle meshes
+// are startable, they start together as one launch of a batch over all
+// resident meshes (the meshes without a request skipped), on a stream of
+// their own, instead of one element launch and one CSR-sum launch each.  The
+// batch is rebuilt when the set of resident meshes has changed; a mesh the
+// batch still references is destroyed only after the batch is (the
+// scheduler then waits for the device).
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -81,6 +89,7 @@ struct Request {
     State state = PENDING;
     std::string msg;                       // error message of a failed request
     double t_submit = 0, t_start = 0, t_done = 0;
+    int64_t group = 0;                     // fused launch the request started in (0: alone)
 };
 
 // Pinned host blocks for the nodal values of queued requests, so that the
@@ -145,9 +154,30 @@ struct fem_server {
     size_t in_use = 0;                                           // accounted device bytes
     size_t peak = 0;
     PinnedPool pinned;
+    // fused launches: a batch over the resident meshes (mesh id -> index)
+    fem_batch* batch = nullptr;
+    bool batch_stale = true, building = false, fuse_off = false;
+    bool hold = false;   // a batch build waits for the device to drain: start nothing new
+    // fused launches in flight (at most FUSED_MAX: the batch stages its
+    // per-launch tables in two pinned buffers, and a third launch would make
+    // the scheduler wait for the first)
+    std::set<int64_t> groups;
+    int64_t next_group = 1;
+    std::deque<uint64_t> done_order;   // finished tickets not yet returned by fem_serve_next_done
+    std::map<uint64_t, int> batch_index;
+    int batch_n = 0;
+    cudaStream_t bstream = nullptr;
+    // evicted meshes the batch may still reference, destroyed with it
+    std::vector<std::pair<fem_mesh*, fem::DevBuf>> graveyard;
+    int64_t n_single = 0, n_fused = 0, n_fused_req = 0, n_builds = 0;
+    double host_start_us = 0;
 };
 
 namespace {
+
+constexpr int FUSED_MAX = 2;
+
+bool fusing(const fem_server* S);
 
 double now_us(const fem_server* s) {
     return std::chrono::duration<double, std::micro>(Clock::now() - s->t0).count();
@@ -221,6 +251,7 @@ void finish(fem_server* S, Request& r, int status, const std::string& msg) {
     r.msg = msg;
     r.state = DONE;
     r.t_done = now_us(S);
+    S->done_order.push_back(r.ticket);
 }
 
 // Puts a request of an idle mesh (or an ASSEMBLE) into the ready set, or
@@ -263,6 +294,7 @@ bool reap(fem_server* S) {
         }
         if (q == cudaSuccess) finish(S, r, FEM_OK, "");
         else finish(S, r, FEM_ECUDA, std::string("request failed on the device: ") + cudaGetErrorString(q));
+        if (r.group) S->groups.erase(r.group);   // the group's events complete together
         --S->inflight;
         Resident& res = S->meshes[r.mesh_id];
         mesh_idle(S, res);
@@ -284,9 +316,12 @@ bool reap(fem_server* S) {
 // not fit the budget, nothing behind it is admitted).  Starts it with the lock
 // released.  Returns false if nothing could be admitted.
 bool admit_one(fem_server* S, std::unique_lock<std::mutex>& lk) {
-    if (S->inflight >= S->opts.max_inflight || S->ready.empty()) return false;
+    if (S->hold || S->inflight >= S->opts.max_inflight || S->ready.empty()) return false;
     const uint64_t ticket = *S->ready.begin();
     Request& r = *S->reqs[ticket];
+    // while fused launches fill their slots, reassembly requests wait for the
+    // next one instead of starting alone beside them
+    if (r.kind == FEM_REQ_REASSEMBLE && fusing(S) && (int)S->groups.size() >= FUSED_MAX) return false;
     Resident* res = nullptr;
     if (r.kind == FEM_REQ_REASSEMBLE) {
         auto m = S->meshes.find(r.mesh_id);
@@ -319,7 +354,9 @@ bool admit_one(fem_server* S, std::unique_lock<std::mutex>& lk) {
     cudaStream_t st = S->streams[r.stream];
     fem_mesh* created = nullptr;
     lk.unlock();
+    const double t0 = now_us(S);
     int rc = start_request(S, r, res, &created, st);
+    const double t1 = now_us(S);
     std::string msg;
     if (rc) {
         char buf[512];
@@ -332,7 +369,12 @@ bool admit_one(fem_server* S, std::unique_lock<std::mutex>& lk) {
         }
     }
     lk.lock();
-    if (created) res->mesh = created;
+    S->host_start_us += t1 - t0;
+    ++S->n_single;
+    if (created) {
+        res->mesh = created;
+        S->batch_stale = true;   // the resident set changed
+    }
     if (rc) {
         finish(S, r, rc, msg);
         --S->inflight;
@@ -346,12 +388,210 @@ bool admit_one(fem_server* S, std::unique_lock<std::mutex>& lk) {
     return true;
 }
 
+bool fusable_prec(int prec) { return prec == FEM_FP64 || prec == FEM_TF32X3 || prec == FEM_FP32; }
+
+bool fusing(const fem_server* S) { return S->opts.fuse_min > 0 && !S->fuse_off && fusable_prec(S->opts.prec); }
+
+// Enqueues one fused launch for the requests `rs` of the meshes `res` (lock
+// released): outputs and u uploads on the batch stream, the batch launch with
+// the other meshes skipped, then each request's completion event.
+int start_fused(fem_server* S, fem_batch* b, int n, const std::map<uint64_t, int>& index,
+                const std::vector<Request*>& rs, const std::vector<Resident*>& res) {
+    cudaStream_t st = S->bstream;
+    const size_t esz = esz_of(S->opts.prec);
+    std::vector<fem_coeff> k((size_t)n);
+    std::memset(k.data(), 0, sizeof(fem_coeff) * k.size());
+    std::vector<const double*> du((size_t)n, nullptr);
+    std::vector<void*> vM((size_t)n, nullptr), vK((size_t)n, nullptr), vT((size_t)n, nullptr);
+    int rc;
+    for (size_t j = 0; j < rs.size(); ++j) {
+        Request& r = *rs[j];
+        Resident& re = *res[j];
+        fem_mesh* m = re.mesh;
+        auto it = index.find(r.mesh_id);
+        if (it == index.end()) return fail(FEM_ESTATE, "mesh is not in the fused batch");
+        const int i = it->second;
+        for (int c = 0; c < 3; ++c)
+            if (r.which & (1 << c))
+                if ((rc = buf_alloc(r.out[c], esz * (size_t)(m->nnz > 0 ? m->nnz : 1), st))) return rc;
+        if (r.which & 6) {
+            if (r.u_n != (size_t)m->n) return fail(FEM_EINVAL, "u has the wrong length for this mesh");
+            if ((rc = buf_alloc(re.u, sizeof(double) * (size_t)m->n, st))) return rc;
+            cudaError_t e = cudaMemcpyAsync(re.u.ptr, r.u_data(), sizeof(double) * r.u_n, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "upload u");
+            du[i] = re.u.as<double>();
+            k[i] = r.k;
+        }
+        vM[i] = r.out[0].ptr;
+        vK[i] = r.out[1].ptr;
+        vT[i] = r.out[2].ptr;
+    }
+    if ((rc = fem_batch_launch(b, k.data(), du.data(), vM.data(), vK.data(), vT.data(), st))) return rc;
+    for (Request* r : rs) {
+        cudaError_t e = cudaEventRecord(r->done, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    }
+    return FEM_OK;
+}
+
+// Destroys the batch and the evicted meshes it may reference (waits for the
+// device).  Lock held on entry and exit, released meanwhile.
+void bury(fem_server* S, std::unique_lock<std::mutex>& lk) {
+    fem_batch* old = S->batch;
+    S->batch = nullptr;
+    S->batch_index.clear();
+    S->batch_n = 0;
+    S->batch_stale = true;
+    std::vector<std::pair<fem_mesh*, fem::DevBuf>> dead;
+    dead.swap(S->graveyard);
+    S->building = true;
+    lk.unlock();
+    const double t0 = now_us(S);
+    if (old) fem_batch_destroy(old);
+    for (auto& d : dead) {
+        buf_free(d.second, nullptr);
+        fem_mesh_destroy(d.first);
+    }
+    const double t1 = now_us(S);
+    lk.lock();
+    S->building = false;
+    S->host_start_us += t1 - t0;
+}
+
+// Starts the startable REASSEMBLE requests (oldest first, within the
+// in-flight and budget limits) as one fused launch if there are at least
+// fuse_min of them, (re)building the batch first if the resident set
+// changed.  Returns false if nothing was done.  Lock held on entry and exit.
+bool admit_fused(fem_server* S, std::unique_lock<std::mutex>& lk) {
+    if (!fusing(S) || (int)S->groups.size() >= FUSED_MAX) return false;
+    std::vector<uint64_t> cand;
+    size_t bytes = 0;
+    for (uint64_t t : S->ready) {
+        if (S->inflight + (int)cand.size() >= S->opts.max_inflight) break;
+        Request& r = *S->reqs[t];
+        if (r.kind != FEM_REQ_REASSEMBLE) continue;
+        auto m = S->meshes.find(r.mesh_id);
+        if (m == S->meshes.end() || m->second.evicted || !m->second.mesh) continue;
+        if (S->in_use + bytes + r.est_bytes > S->opts.budget_bytes) break;
+        bytes += r.est_bytes;
+        cand.push_back(t);
+    }
+    if ((int)cand.size() < S->opts.fuse_min) {
+        S->hold = false;
+        return false;
+    }
+    if (S->batch_stale || !S->batch) {
+        // building allocates the meshes' element scratch where it is missing,
+        // which must not happen under a kernel of another stream: let the
+        // device drain first (nothing new starts meanwhile)
+        if (S->inflight > 0) {
+            S->hold = true;
+            return false;
+        }
+        S->hold = false;
+        bury(S, lk);
+        std::vector<uint64_t> ids;
+        std::vector<fem_mesh*> ms;
+        for (auto& kv : S->meshes)
+            if (kv.second.mesh && !kv.second.evicted) {
+                ids.push_back(kv.first);
+                ms.push_back(kv.second.mesh);
+            }
+        S->building = true;   // eviction now leaves these meshes to the scheduler
+        lk.unlock();
+        const double t0 = now_us(S);
+        fem_batch_opts bo;
+        std::memset(&bo, 0, sizeof bo);
+        bo.prec = S->opts.prec;
+        // no graph: capturing one would make device-wide synchronisation by
+        // the caller's threads fail meanwhile; a fused launch enqueues its few
+        // kernels directly
+        bo.use_graph = 0;
+        fem_batch* nb = nullptr;
+        const int rc = fem_batch_create(ms.data(), (int)ms.size(), &bo, S->bstream, &nb);
+        const double t1 = now_us(S);
+        lk.lock();
+        S->building = false;
+        S->host_start_us += t1 - t0;
+        ++S->n_builds;
+        if (rc) {
+            S->fuse_off = true;   // requests start one by one from now on
+            return true;
+        }
+        S->batch = nb;
+        S->batch_n = (int)ids.size();
+        for (size_t i = 0; i < ids.size(); ++i) S->batch_index[ids[i]] = (int)i;
+        S->batch_stale = false;
+        return true;   // the ready set may have changed meanwhile: collect again
+    }
+    std::vector<Request*> rs;
+    std::vector<Resident*> res;
+    const double now = now_us(S);
+    const int64_t group = S->next_group++;
+    S->groups.insert(group);
+    for (uint64_t t : cand) {
+        Request& r = *S->reqs[t];
+        Resident& re = S->meshes[r.mesh_id];
+        S->ready.erase(t);
+        --S->pending;
+        re.in_ready = false;
+        re.busy = 1;
+        S->in_use += r.est_bytes;
+        r.state = RUNNING;
+        r.t_start = now;
+        r.stream = -1;
+        r.group = group;
+        ++S->inflight;
+        rs.push_back(&r);
+        res.push_back(&re);
+    }
+    S->peak = std::max(S->peak, S->in_use);
+    fem_batch* b = S->batch;
+    const int n = S->batch_n;
+    const std::map<uint64_t, int> index = S->batch_index;
+    lk.unlock();
+    const double t0 = now_us(S);
+    int rc = start_fused(S, b, n, index, rs, res);
+    std::string msg;
+    if (rc) {
+        char buf[512];
+        fem_last_error(buf, sizeof buf);
+        msg = buf;
+        cudaStreamSynchronize(S->bstream);   // nothing of the failed launch stays in flight
+    }
+    const double t1 = now_us(S);
+    lk.lock();
+    S->host_start_us += t1 - t0;
+    ++S->n_fused;
+    S->n_fused_req += (int64_t)rs.size();
+    if (rc) S->groups.erase(group);
+    for (size_t j = 0; j < rs.size(); ++j) {
+        if (rc) {
+            finish(S, *rs[j], rc, msg);
+            --S->inflight;
+            mesh_idle(S, *res[j]);
+        } else {
+            S->running.push_back(rs[j]->ticket);
+        }
+    }
+    return true;
+}
+
 void scheduler(fem_server* S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     while (!S->stop) {
         bool progress = reap(S);
-        while (!S->stop && admit_one(S, lk)) progress = true;
+        if (!S->graveyard.empty()) {
+            bury(S, lk);
+            progress = true;
+        }
+        // a fused launch is tried before every single start, so that requests
+        // that queued up while the scheduler was busy start together
+        while (!S->stop) {
+            if (admit_fused(S, lk) || admit_one(S, lk)) progress = true;
+            else break;
+        }
         if (progress) S->cv_done.notify_all();
         else S->cv_work.wait_for(lk, std::chrono::microseconds(S->inflight ? 10 : 1000));
     }
@@ -386,6 +626,25 @@ int fem_serve_create(const fem_serve_opts* opts, fem_server** out) {
             return cuda_fail(e, "cudaStreamCreate");
         }
         S->streams.push_back(st);
+    }
+    e = cudaStreamCreateWithFlags(&S->bstream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        for (auto x : S->streams) cudaStreamDestroy(x);
+        delete S;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    {
+        // request outputs and uploads come from the device's default memory
+        // pool; keep up to the budget mapped in it, so that the memory of
+        // released requests serves the next ones instead of being returned
+        // to the driver at every synchronisation and mapped again
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = 0, want = (uint64_t)opts->budget_bytes;
+            if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess && keep < want)
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &want);
+        }
+        cudaGetLastError();
     }
     S->th = std::thread(scheduler, S);
     *out = S;
@@ -520,6 +779,26 @@ int fem_serve_poll(fem_server* S, uint64_t ticket, int timeout_us, fem_result* o
     return FEM_OK;
 }
 
+int fem_serve_next_done(fem_server* S, int timeout_us, uint64_t* ticket) {
+    if (!S || !ticket) return fail(FEM_EINVAL, "NULL argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    const auto deadline = Clock::now() + std::chrono::microseconds(timeout_us > 0 ? timeout_us : 0);
+    for (;;) {
+        // skip tickets released meanwhile
+        while (!S->done_order.empty() && !S->reqs.count(S->done_order.front())) S->done_order.pop_front();
+        if (!S->done_order.empty()) {
+            *ticket = S->done_order.front();
+            S->done_order.pop_front();
+            return FEM_OK;
+        }
+        if (timeout_us <= 0) return FEM_EAGAIN;
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+            while (!S->done_order.empty() && !S->reqs.count(S->done_order.front())) S->done_order.pop_front();
+            if (S->done_order.empty()) return fail(FEM_ETIMEOUT, "no request finished within the timeout");
+        }
+    }
+}
+
 int fem_serve_release(fem_server* S, uint64_t ticket) {
     if (!S) return fail(FEM_EINVAL, "NULL server");
     std::unique_ptr<Request> r;
@@ -531,6 +810,13 @@ int fem_serve_release(fem_server* S, uint64_t ticket) {
         r = std::move(it->second);
         S->reqs.erase(it);
         S->in_use -= std::min(S->in_use, r->out_bytes);
+        if (S->done_order.size() > 2 * S->reqs.size() + 4096) {
+            // drop released tickets (clients that poll by ticket never drain it)
+            std::deque<uint64_t> keep;
+            for (uint64_t t : S->done_order)
+                if (S->reqs.count(t)) keep.push_back(t);
+            S->done_order.swap(keep);
+        }
     }
     for (auto& b : r->out) buf_free(b, nullptr);
     if (r->done) cudaEventDestroy(r->done);
@@ -562,9 +848,19 @@ int fem_serve_evict(fem_server* S, uint64_t mesh_id) {
         res = it->second;
         S->in_use -= std::min(S->in_use, res.bytes);
         S->meshes.erase(it);
+        S->batch_stale = true;
+        if (S->building || S->batch_index.count(mesh_id)) {
+            // the fused batch may reference the mesh: the scheduler destroys
+            // it together with the batch
+            S->graveyard.emplace_back(res.mesh, res.u);
+            res.u = fem::DevBuf();
+            res.mesh = nullptr;
+        }
     }
-    buf_free(res.u, nullptr);
-    fem_mesh_destroy(res.mesh);
+    if (res.mesh) {
+        buf_free(res.u, nullptr);
+        fem_mesh_destroy(res.mesh);
+    }
     S->cv_work.notify_one();
     return FEM_OK;
 }
@@ -577,6 +873,11 @@ int fem_serve_stats(fem_server* S, fem_serve_counters* out) {
     out->resident_meshes = (int)S->meshes.size();
     out->bytes_in_use = S->in_use;
     out->peak_bytes = S->peak;
+    out->single_launches = S->n_single;
+    out->fused_launches = S->n_fused;
+    out->fused_requests = S->n_fused_req;
+    out->batch_builds = S->n_builds;
+    out->host_start_us = S->host_start_us;
     return FEM_OK;
 }
 
@@ -589,6 +890,14 @@ int fem_serve_destroy(fem_server* S) {
     S->cv_work.notify_all();
     if (S->th.joinable()) S->th.join();
     for (auto st : S->streams) cudaStreamSynchronize(st);
+    if (S->bstream) cudaStreamSynchronize(S->bstream);
+    if (S->batch) fem_batch_destroy(S->batch);
+    S->batch = nullptr;
+    for (auto& d : S->graveyard) {
+        buf_free(d.second, nullptr);
+        fem_mesh_destroy(d.first);
+    }
+    S->graveyard.clear();
     for (auto& kv : S->reqs) {
         for (auto& b : kv.second->out) buf_free(b, nullptr);
         if (kv.second->done) cudaEventDestroy(kv.second->done);
@@ -600,6 +909,7 @@ int fem_serve_destroy(fem_server* S) {
         if (kv.second.mesh) fem_mesh_destroy(kv.second.mesh);
     }
     for (auto st : S->streams) cudaStreamDestroy(st);
+    if (S->bstream) cudaStreamDestroy(S->bstream);
     delete S;
     return FEM_OK;
 }

@@ -135,9 +135,10 @@ class FemServer:
     """The request server of libfem (fem_serve_*) with torch-tensor results."""
 
     def __init__(self, prec: str = "tf32x3", budget_bytes: int = 8 << 30, max_inflight: int = 8, n_streams: int = 4,
-                 max_queue: int = 1 << 20):
+                 max_queue: int = 1 << 20, fuse_min: int = 2):
         self.prec = prec
-        self.h = fem_serve_create(fem_serve_opts(PRECISIONS[prec], max_inflight, n_streams, max_queue, budget_bytes))
+        self.h = fem_serve_create(fem_serve_opts(PRECISIONS[prec], max_inflight, n_streams, max_queue, budget_bytes,
+                                                 fuse_min, 0))
 
     def assemble(self, mesh, kind: str = "poly", params=(1.0,), u=None, which="MKT", mass: float = 1.0) -> int:
         desc, keep = mesh_desc(mesh, mass)

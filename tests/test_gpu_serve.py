@@ -37,10 +37,11 @@ def single(m, u, kind, params, prec):
     return out
 
 
+@pytest.mark.parametrize("fuse_min", [0, 2])
 @pytest.mark.parametrize("prec", ["tf32x3", "fp64"])
-def test_serve_matches_single_calls(prec):
+def test_serve_matches_single_calls(prec, fuse_min):
     ms = meshes()
-    S = FemServer(prec, budget_bytes=2 << 30, max_inflight=4, n_streams=3)
+    S = FemServer(prec, budget_bytes=2 << 30, max_inflight=4, n_streams=3, fuse_min=fuse_min)
     try:
         # ASSEMBLE every mesh, then interleave 3 REASSEMBLE rounds with new u over all meshes
         tick = [S.assemble(m, "poly", (1.0, 0.3, 0.2), mg.fourier_field(m.coords, 1 + i)) for i, m in enumerate(ms)]
@@ -69,6 +70,71 @@ def test_serve_matches_single_calls(prec):
         st = S.stats()
         assert st.pending == 0 and st.inflight == 0 and st.resident_meshes == len(ms)
         assert st.peak_bytes <= 2 << 30
+        assert st.single_launches + st.fused_requests == len(ms) * 4
+        if fuse_min == 0:
+            assert st.fused_launches == 0
+    finally:
+        S.close()
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "fp64", "fp32"])
+def test_serve_fused_launches(prec):
+    """Requests of many meshes queued at once start as fused batch launches
+    (fewer launches than requests, several requests per launch); partial
+    matrix subsets and meshes skipped in a launch; results equal single-mesh
+    calls bit for bit; a mesh assembled later joins the batch (rebuilt), an
+    evicted one leaves it."""
+    ms = meshes()
+    S = FemServer(prec, budget_bytes=4 << 30, max_inflight=64, n_streams=2, fuse_min=2)
+    try:
+        ids = []
+        for i, m in enumerate(ms[:5]):
+            r, _ = S.result(S.assemble(m, "poly", (1.0,), mg.fourier_field(m.coords, 300 + i), which="M"))
+            assert r.status == 0
+            ids.append(r.mesh_id)
+        subsets = ["MKT", "M", "KT", "T", "MK"]
+        todo = []
+        for rnd in range(3):
+            for i in range(5):
+                if rnd == 1 and i == 2:
+                    continue           # mesh 2 skipped in this round's launches
+                u = mg.fourier_field(ms[i].coords, 400 + 10 * rnd + i)
+                law = ("sin", (2.0, 1.0, 3.0)) if (i + rnd) % 2 else ("poly", (1.0, 0.3, 0.2))
+                todo.append((i, u, law, subsets[(i + rnd) % len(subsets)]))
+        # a larger ASSEMBLE first keeps the scheduler busy (it builds the
+        # pattern synchronously) while the requests queue up behind it
+        tb = S.assemble(mg.structured_tri(200, 2, 0.2, seed=9), which="M")
+        pend = [(i, u, law, which, S.reassemble(ids[i], law[0], law[1], u, which=which))
+                for i, u, law, which in todo]
+        assert S.result(tb)[0].status == 0
+        for i, u, law, which, t in pend:
+            r, vals = S.result(t)
+            assert r.status == 0, F._err()
+            assert set(vals) == set(which)
+            ref = single(ms[i], u, law[0], law[1], prec)
+            for k in which:
+                assert torch.equal(vals[k], ref[k]), (i, which, k)
+        st = S.stats()
+        assert st.fused_launches >= 1 and st.fused_requests >= 2 * st.fused_launches
+        assert st.fused_launches < st.fused_requests
+        builds = st.batch_builds
+        # the resident set changes: one mesh more, one fewer
+        r, _ = S.result(S.assemble(ms[5], "poly", (1.0,), mg.fourier_field(ms[5].coords, 305), which="M"))
+        ids.append(r.mesh_id)
+        S.evict(ids[0])
+        us = {i: mg.fourier_field(ms[i].coords, 500 + i) for i in range(1, 6)}
+        tb = S.assemble(mg.structured_tri(200, 2, 0.2, seed=10), which="M")
+        pend = [(i, us[i], S.reassemble(ids[i], "poly", (1.0, 0.0, 1.0), us[i])) for i in range(1, 6)]
+        assert S.result(tb)[0].status == 0
+        for i, u, t in pend:
+            r, vals = S.result(t)
+            assert r.status == 0, F._err()
+            ref = single(ms[i], u, "poly", (1.0, 0.0, 1.0), prec)
+            for k in "MKT":
+                assert torch.equal(vals[k], ref[k]), (i, k)
+        st = S.stats()
+        assert st.batch_builds > builds and st.resident_meshes == 7
+        assert st.pending == 0 and st.inflight == 0
     finally:
         S.close()
 
@@ -171,5 +237,49 @@ def test_serve_errors():
             F.fem_serve_evict(S.h, 424242)
         assert ei.value.code == F.FEM_EINVAL
         F.fem_serve_release(S.h, t)
+    finally:
+        S.close()
+
+
+def test_serve_next_done_completion_order():
+    """fem_serve_next_done hands out every finished, unreleased request once,
+    in completion order; a released request is never handed out."""
+    ms = meshes()[:4]
+    S = FemServer("fp32", max_inflight=8, n_streams=2)
+    try:
+        ids = []
+        for m in ms:
+            r, _ = S.result(S.assemble(m, which="M"))
+            ids.append(r.mesh_id)
+        # the ASSEMBLE results were taken by ticket and released: none is pending here
+        assert F.fem_serve_next_done(S.h, 0) is None
+        want = {}
+        for s in range(3):
+            for i, m in enumerate(ms):
+                u = mg.fourier_field(m.coords, 600 + 10 * s + i)
+                want[S.reassemble(ids[i], "poly", (1.0, 0.5), u, which="KT")] = (i, u)
+        got = []
+        while len(got) < len(want):
+            t = F.fem_serve_next_done(S.h, 10_000_000)
+            assert t in want and t not in got
+            got.append(t)
+            r = F.fem_serve_poll(S.h, t, 0)
+            assert r is not None and r.status == 0
+        assert F.fem_serve_next_done(S.h, 0) is None
+        # requests of one mesh finish in submission order
+        for i in range(len(ms)):
+            mine = [t for t in got if want[t][0] == i]
+            assert mine == sorted(mine)
+        for t in got[:3]:
+            i, u = want[t]
+            r, vals = S.result(t)
+            ref = single(ms[i], u, "poly", (1.0, 0.5), "fp32")
+            for k in "KT":
+                assert torch.equal(vals[k], ref[k])
+        for t in got[3:]:
+            F.fem_serve_release(S.h, t)
+        with pytest.raises(F.FemError) as ei:
+            F.fem_serve_next_done(S.h, 1000)
+        assert ei.value.code == F.FEM_ETIMEOUT
     finally:
         S.close()
