@@ -22,6 +22,7 @@
 #include <atomic>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -89,7 +90,10 @@ struct TcL {
     static constexpr int MINB_SMEM = (228 * 1024) / (SMEM + 1024), MINB_TMEM = 512 / ALLOC;
     static constexpr int MINB2 = MINB_SMEM < 1 ? 1 : MINB_SMEM < MINB_TMEM ? (MINB_SMEM < 3 ? MINB_SMEM : 3)
                                                                         : (MINB_TMEM < 3 ? MINB_TMEM : 3);
-    static constexpr int MINB = TPR == 2 ? MINB2 : 1;
+    // one thread per row: ask for the 4 CTAs per SM the tile fits, so that
+    // the formation code specialised per law class stays within 128 registers
+    static constexpr int MINB1 = MINB_SMEM < 4 || MINB_TMEM < 4 ? 1 : 4;
+    static constexpr int MINB = TPR == 2 ? MINB2 : MINB1;
     // epilogue reads whole 32-column chunks: they must stay inside the allocation
     static constexpr bool FITS = NMp <= 256 && NTp <= 256 && ALLOC <= 512 && SMEM <= SMEM_MAX &&
                                  XEND >= 4 * 32 * ETy::NT * 4 && QEND <= IMG_SLOT_FLOATS * 4 &&
@@ -106,6 +110,17 @@ __device__ float g_tcimg[6 * IMG_SLOT_FLOATS];
 __device__ int g_tc_err;
 
 constexpr long long WAIT_LIMIT = 2000000000LL;   // SM clocks (~1 s)
+
+// Calls f(std::integral_constant<int, LC>) for the law class of k: the
+// formation code is compiled once per class and the branch is taken once per
+// tile, outside the quadrature loops.  SIN = false leaves the sine law to the
+// generic code (one copy fewer where registers are tight).
+template <bool SIN = true, typename F>
+__device__ __forceinline__ void with_law(int lc, F&& f) {
+    if (lc == LC_POLY3) f(std::integral_constant<int, LC_POLY3>{});
+    else if (SIN && lc == LC_SIN) f(std::integral_constant<int, LC_SIN>{});
+    else f(std::integral_constant<int, LC_ANY>{});
+}
 
 // Per-phase SM clock counters, compiled in only with -DFEM_PHASE_TIMERS (the
 // default build has none): thread 0 of each CTA adds the clocks spent since
@@ -396,7 +411,7 @@ __device__ __forceinline__ void epilogue_staged(uint32_t tmem, int col, float* s
 // Lambda (.) W; the tangent factors), from its gathered nodal values (split
 // as hi + lo) and its geometry (b_e, A_e upper triangle), packed as
 // [X_M | X_K | X_T]; the padding columns stay as the caller set them (zero).
-template <typename ETy, int KTOTp>
+template <typename ETy, int KTOTp, int LC = LC_ANY>
 __device__ __forceinline__ void form_x(const float2 (&pu)[ETy::NP], const float (&pgeo)[1 + ETy::NS], bool need_u,
                                        const CoeffDev& k, float mass, float (&x)[KTOTp]) {
     constexpr int OFF_K = ETy::KM, OFF_T = ETy::KM + ETy::KK;
@@ -432,7 +447,7 @@ __device__ __forceinline__ void form_x(const float2 (&pu)[ETy::NP], const float 
         }
         uq += u0;
         float dk;
-        const float kq = k_eval<float>(k, uq, dk);
+        const float kq = k_eval<float, LC>(k, uq, dk);
         const float lam = c_tcref[WQ + q] * b;
         x[q] = mass * lam;
         const float lk = lam * kq;
@@ -458,7 +473,7 @@ __device__ __forceinline__ void form_x(const float2 (&pu)[ETy::NP], const float 
 // for the rest (which also zeroes the padding columns).  `valid` false (a
 // row past E) writes zeros.  Scalar stores: a half's columns do not form
 // whole 4-column groups.
-template <typename ETy, int KTOTp, int H>
+template <typename ETy, int KTOTp, int H, int LC = LC_ANY>
 __device__ __forceinline__ void form_x_half(const float2 (&pu)[ETy::NP], const float (&pgeo)[1 + ETy::NS],
                                             bool valid, bool need_u, const CoeffDev& k, float mass,
                                             unsigned char* xh, unsigned char* xl, int r) {
@@ -502,7 +517,7 @@ __device__ __forceinline__ void form_x_half(const float2 (&pu)[ETy::NP], const f
         }
         uq += u0;
         float dk;
-        const float kq = k_eval<float>(k, uq, dk);
+        const float kq = k_eval<float, LC>(k, uq, dk);
         const float lam = c_tcref[WQ + q] * b;   // 0 for an invalid row, so every column is 0
         put(q, mass * lam);
         const float lk = lam * kq;
@@ -526,7 +541,9 @@ __device__ __forceinline__ void form_x_half(const float2 (&pu)[ETy::NP], const f
     }
 }
 
-template <typename ETy>
+// LC: the law class the formation is compiled for (the launch picks it from
+// k; LC_ANY evaluates every law).
+template <typename ETy, int LC>
 __global__ void __launch_bounds__(TcL<ETy>::TPR * TILE, TcL<ETy>::MINB) element_tc_kernel(const int* __restrict__ conn, const float* __restrict__ geo,
                                                           int64_t E, int64_t gs, const double* __restrict__ u, CoeffDev k,
                                                           float mass, float* __restrict__ VM, float* __restrict__ VK,
@@ -617,14 +634,14 @@ __global__ void __launch_bounds__(TcL<ETy>::TPR * TILE, TcL<ETy>::MINB) element_
                 float x[L::KTOTp];
 #pragma unroll
                 for (int i = 0; i < L::KTOTp; ++i) x[i] = 0.f;
-                if (pvalid) form_x<ETy, L::KTOTp>(su, pgeo, need_u, k, mass, x);
+                if (pvalid) form_x<ETy, L::KTOTp, LC>(su, pgeo, need_u, k, mass, x);
                 if (next < ntiles) fetch_meta(next);
                 store_row<L::KTOTp>(sX + L::XH, sX + L::XL, x, r);
             } else {
                 if (half == 0)
-                    form_x_half<ETy, L::KTOTp, 0>(su, pgeo, pvalid, need_u, k, mass, sX + L::XH, sX + L::XL, r);
+                    form_x_half<ETy, L::KTOTp, 0, LC>(su, pgeo, pvalid, need_u, k, mass, sX + L::XH, sX + L::XL, r);
                 else
-                    form_x_half<ETy, L::KTOTp, 1>(su, pgeo, pvalid, need_u, k, mass, sX + L::XH, sX + L::XL, r);
+                    form_x_half<ETy, L::KTOTp, 1, LC>(su, pgeo, pvalid, need_u, k, mass, sX + L::XH, sX + L::XL, r);
                 if (next < ntiles) fetch_meta(next);
             }
         }
@@ -706,10 +723,13 @@ __device__ __forceinline__ bool batch_tc_tile(const BatchMesh& bm, int64_t first
 #pragma unroll
         for (int t = 0; t <= NS; ++t) pgeo[t] = __ldg(bm.geo32 + t * E + e);
     }
-    if (half == 0)
-        form_x_half<ETy, L::KTOTp, 0>(pu, pgeo, valid, need_u, bm.k, (float)bm.mass, sX + L::XH, sX + L::XL, r);
-    else
-        form_x_half<ETy, L::KTOTp, 1>(pu, pgeo, valid, need_u, bm.k, (float)bm.mass, sX + L::XH, sX + L::XL, r);
+    with_law(law_class(bm.k), [&](auto lcv) {
+        constexpr int LC = decltype(lcv)::value;
+        if (half == 0)
+            form_x_half<ETy, L::KTOTp, 0, LC>(pu, pgeo, valid, need_u, bm.k, (float)bm.mass, sX + L::XH, sX + L::XL, r);
+        else
+            form_x_half<ETy, L::KTOTp, 1, LC>(pu, pgeo, valid, need_u, bm.k, (float)bm.mass, sX + L::XH, sX + L::XL, r);
+    });
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -882,7 +902,7 @@ __device__ __forceinline__ void form_chunk_m_s(int q0, float b, float mass, cons
     for (int j = 0; j < QC; ++j) x[j] = mass * (tw[q0 + j] * b);
 }
 
-template <typename ETy, int QC>
+template <typename ETy, int QC, int LC = LC_ANY>
 __device__ __forceinline__ void form_chunk_k_s(int q0, const float (&du)[ETy::NP], float u0, float b,
                                                const float (&A)[ETy::NS], const CoeffDev& k,
                                                const float* __restrict__ tp, const float* __restrict__ tw,
@@ -903,14 +923,14 @@ __device__ __forceinline__ void form_chunk_k_s(int q0, const float (&du)[ETy::NP
         }
         uq += u0;
         float dk;
-        const float kq = k_eval<float>(k, uq, dk);
+        const float kq = k_eval<float, LC>(k, uq, dk);
         const float lk = (tw[q] * b) * kq;
 #pragma unroll
         for (int t = 0; t < NS; ++t) x[j * NS + t] = lk * A[t];
     }
 }
 
-template <typename ETy, int QC>
+template <typename ETy, int QC, int LC = LC_ANY>
 __device__ __forceinline__ void form_chunk_t_s(int q0, const float (&du)[ETy::NP], float u0, float b,
                                                const float (&A)[ETy::NS], const CoeffDev& k,
                                                const float4* __restrict__ tpg, const float* __restrict__ tw,
@@ -933,7 +953,7 @@ __device__ __forceinline__ void form_chunk_t_s(int q0, const float (&du)[ETy::NP
         }
         uq += u0;
         float dk;
-        k_eval<float>(k, uq, dk);
+        k_eval<float, LC>(k, uq, dk);
         const float ld = (tw[q] * b) * dk;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
@@ -1051,6 +1071,8 @@ __device__ __forceinline__ bool chunked_tile(const int* __restrict__ conn, const
             } else if (kd == 1) {
                 constexpr int QH = L::QCK / 2, KH = L::KcK / 2;
                 float x[KH];
+                // generic law code: the chunk loop is not unrolled, and three
+                // specialised copies cost the kernel registers (it runs at 128)
                 form_chunk_k_s<ETy, QH>(c * L::QCK + half * QH, du, u0, b, A, k, tp, tw, x);
                 store_row_part<L::KcK, KH>(sX, sX + TILE * L::KcK * 4, x, r, half * KH);
             } else {   // both halves of T use the same X columns
@@ -1465,7 +1487,7 @@ __device__ __forceinline__ void issue_tile_bf(uint32_t tmem, uint32_t sXu, uint3
 // The BF16 tile kernel: the structure of element_tc_kernel with one thread
 // per element row (persistent CTAs, resident Q parts, next-tile prefetch,
 // one waiting thread, bulk-copy epilogue).
-template <typename ETy, int NPART>
+template <typename ETy, int NPART, int LC>
 __global__ void __launch_bounds__(TILE) element_bf_kernel(const int* __restrict__ conn, const float* __restrict__ geo,
                                                           int64_t E, int64_t gs, const double* __restrict__ u,
                                                           CoeffDev k, float mass, float* __restrict__ VM,
@@ -1539,7 +1561,7 @@ __global__ void __launch_bounds__(TILE) element_bf_kernel(const int* __restrict_
             float2 su[NP];
 #pragma unroll
             for (int i = 0; i < NP; ++i) su[i] = need_u ? split_f64(pu[i]) : make_float2(0.f, 0.f);
-            form_x<ETy, L::KTOTp>(su, pgeo, need_u, k, mass, x);
+            form_x<ETy, L::KTOTp, LC>(su, pgeo, need_u, k, mass, x);
         }
         const int64_t next = tile + gridDim.x;
         if (next < ntiles) fetch_meta(next);
@@ -1825,7 +1847,7 @@ int launch_tc_chunked(const fem_mesh& m, const CoeffDev& k, const double* u, flo
     return FEM_OK;
 }
 
-template <typename ETy>
+template <typename ETy, int LC>
 int launch_tc(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
               cudaStream_t s, int64_t e0, int64_t e1) {
     using L = TcL<ETy>;
@@ -1837,7 +1859,7 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, 
     } else {
         const int64_t E = e1 - e0;
         if (E <= 0) return FEM_OK;
-        auto kern = element_tc_kernel<ETy>;
+        auto kern = element_tc_kernel<ETy, LC>;
         constexpr int SMEM0 = L::SMEM;
         constexpr int ALLOC0 = L::ALLOC;
         static std::atomic<int> have[64];
@@ -1897,6 +1919,22 @@ int launch_tc(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, 
                                                    sh.err);
         FEM_CUDA_TRY(cudaGetLastError());
         return FEM_OK;
+    }
+}
+
+// The tile kernel compiled for k's law class (one formation copy per kernel;
+// every class gives the same bits).
+template <typename ETy>
+int launch_tc_law(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
+                  cudaStream_t s, int64_t e0, int64_t e1) {
+    if constexpr (!TcL<ETy>::FITS) {
+        return launch_tc<ETy, LC_ANY>(m, k, u, VM, VK, VT, s, e0, e1);
+    } else {
+        switch (law_class(k)) {
+            case LC_POLY3: return launch_tc<ETy, LC_POLY3>(m, k, u, VM, VK, VT, s, e0, e1);
+            case LC_SIN: return launch_tc<ETy, LC_SIN>(m, k, u, VM, VK, VT, s, e0, e1);
+            default: return launch_tc<ETy, LC_ANY>(m, k, u, VM, VK, VT, s, e0, e1);
+        }
     }
 }
 
@@ -2105,7 +2143,7 @@ int tc_error_flag(int clear) {
     return v;
 }
 
-template <typename ETy, int NPART>
+template <typename ETy, int NPART, int LC>
 int launch_bf(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT, cudaStream_t s,
               int64_t e0, int64_t e1) {
     using L = TbL<ETy, NPART>;
@@ -2114,7 +2152,7 @@ int launch_bf(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, 
     } else {
         const int64_t E = e1 - e0;
         if (E <= 0) return FEM_OK;
-        auto kern = element_bf_kernel<ETy, NPART>;
+        auto kern = element_bf_kernel<ETy, NPART, LC>;
         static std::atomic<int> have[64];
         static LaunchShape cache[64];
         static std::mutex mu;
@@ -2167,16 +2205,30 @@ int launch_bf(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, 
     }
 }
 
+template <typename ETy, int NPART>
+int launch_bf_law(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
+                  cudaStream_t s, int64_t e0, int64_t e1) {
+    if constexpr (!TbL<ETy, NPART>::FITS) {
+        return launch_bf<ETy, NPART, LC_ANY>(m, k, u, VM, VK, VT, s, e0, e1);
+    } else {
+        switch (law_class(k)) {
+            case LC_POLY3: return launch_bf<ETy, NPART, LC_POLY3>(m, k, u, VM, VK, VT, s, e0, e1);
+            case LC_SIN: return launch_bf<ETy, NPART, LC_SIN>(m, k, u, VM, VK, VT, s, e0, e1);
+            default: return launch_bf<ETy, NPART, LC_ANY>(m, k, u, VM, VK, VT, s, e0, e1);
+        }
+    }
+}
+
 template <int NPART>
 int dispatch_bf(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
                 cudaStream_t s, int64_t e0, int64_t e1) {
     switch (m.type) {
-        case 0: return launch_bf<ET<2, 1>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
-        case 1: return launch_bf<ET<2, 2>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
-        case 2: return launch_bf<ET<2, 3>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
-        case 3: return launch_bf<ET<3, 1>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
-        case 4: return launch_bf<ET<3, 2>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
-        case 5: return launch_bf<ET<3, 3>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 0: return launch_bf_law<ET<2, 1>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 1: return launch_bf_law<ET<2, 2>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 2: return launch_bf_law<ET<2, 3>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 3: return launch_bf_law<ET<3, 1>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 4: return launch_bf_law<ET<3, 2>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 5: return launch_bf_law<ET<3, 3>, NPART>(m, k, u, VM, VK, VT, s, e0, e1);
     }
     return fail(FEM_EINVAL, "element type");
 }
@@ -2272,12 +2324,12 @@ int element_tc_tf32x3(const fem_mesh& m, const CoeffDev& k, const double* u, flo
     int rc = tables_init_tc();
     if (rc) return rc;
     switch (m.type) {
-        case 0: return launch_tc<ET<2, 1>>(m, k, u, VM, VK, VT, s, e0, e1);
-        case 1: return launch_tc<ET<2, 2>>(m, k, u, VM, VK, VT, s, e0, e1);
-        case 2: return launch_tc<ET<2, 3>>(m, k, u, VM, VK, VT, s, e0, e1);
-        case 3: return launch_tc<ET<3, 1>>(m, k, u, VM, VK, VT, s, e0, e1);
-        case 4: return launch_tc<ET<3, 2>>(m, k, u, VM, VK, VT, s, e0, e1);
-        case 5: return launch_tc<ET<3, 3>>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 0: return launch_tc_law<ET<2, 1>>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 1: return launch_tc_law<ET<2, 2>>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 2: return launch_tc_law<ET<2, 3>>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 3: return launch_tc_law<ET<3, 1>>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 4: return launch_tc_law<ET<3, 2>>(m, k, u, VM, VK, VT, s, e0, e1);
+        case 5: return launch_tc_law<ET<3, 3>>(m, k, u, VM, VK, VT, s, e0, e1);
     }
     return fail(FEM_EINVAL, "element type");
 }

@@ -131,23 +131,38 @@ __device__ __forceinline__ T horner_n(const CoeffDev& c, T u, T& dk) {
     }
 }
 
-// k(u) and k'(u).  Polynomials of up to 5 coefficients take a Horner of
-// their own degree (the branch is uniform: the law is a kernel parameter, and
-// the host drops zero leading coefficients); longer ones, and the knot loop, run over
-// the fixed maxima (8 coefficients, 8 knots) with predicates so that the
-// parameters stay in the kernel-parameter space instead of being copied to
-// local memory; unused parameters are zero.
+// Law classes that formation code can be specialised for (the class is
+// uniform over a launch, or over a batch work item, so the dispatch costs one
+// branch outside the quadrature loops): polynomials with at most three
+// coefficients, the sine law, and everything else.
+enum : int { LC_ANY = 0, LC_POLY3 = 1, LC_SIN = 2 };
+__host__ __device__ inline int law_class(const CoeffDev& c) {
+    return c.kind == 0 && c.n <= 3 ? LC_POLY3 : c.kind == 1 ? LC_SIN : LC_ANY;
+}
+
+// k(u) and k'(u).  LC_POLY3 takes a 3-term Horner (unused coefficients are
+// zero, so it gives the bits of the general loop below); LC_SIN the sine law
+// alone; LC_ANY every law, with loops over the fixed maxima (8 polynomial
+// coefficients, 8 knots) and predicates so that the parameters stay in the
+// kernel-parameter space instead of being copied to local memory; unused
+// parameters are zero.
 template <typename T>
+__device__ __forceinline__ T k_sin(const CoeffDev& c, T u, T& dk) {
+    T g = T(c.p[2]);
+    T s, co;
+    if constexpr (sizeof(T) == 8) { sincos(g * u, &s, &co); }
+    else { sincosf(g * u, &s, &co); }
+    dk = T(c.p[1]) * g * co;
+    return T(c.p[0]) + T(c.p[1]) * s;
+}
+
+template <typename T, int LC = LC_ANY>
 __device__ __forceinline__ T k_eval(const CoeffDev& c, T u, T& dk) {
-    if (c.kind == 0) {
-        switch (c.n) {
-            case 1: return horner_n<T, 1>(c, u, dk);
-            case 2: return horner_n<T, 2>(c, u, dk);
-            case 3: return horner_n<T, 3>(c, u, dk);
-            case 4: return horner_n<T, 4>(c, u, dk);
-            case 5: return horner_n<T, 5>(c, u, dk);
-            default: break;
-        }
+    if constexpr (LC == LC_POLY3) {
+        return horner_n<T, 3>(c, u, dk);
+    } else if constexpr (LC == LC_SIN) {
+        return k_sin<T>(c, u, dk);
+    } else if (c.kind == 0) {
         T v = T(0), dv = T(0);
 #pragma unroll
         for (int i = 7; i >= 0; --i) {
@@ -157,12 +172,7 @@ __device__ __forceinline__ T k_eval(const CoeffDev& c, T u, T& dk) {
         dk = dv;
         return v;
     } else if (c.kind == 1) {
-        T g = T(c.p[2]);
-        T s, co;
-        if constexpr (sizeof(T) == 8) { sincos(g * u, &s, &co); }
-        else { sincosf(g * u, &s, &co); }
-        dk = T(c.p[1]) * g * co;
-        return T(c.p[0]) + T(c.p[1]) * s;
+        return k_sin<T>(c, u, dk);
     } else {
         // device layout (set by the host): knots in p[0..7], values in p[8..15], m = n/2 knots
         const int m = c.n / 2;
