@@ -270,10 +270,47 @@ int assemble_t(fem_mesh* m, const fem_coeff* k, const void* u, int prec, void* v
             if (out_staged[i]) outd[i] = m->out_stage.as<T>() + (size_t)i * nnz;
     }
     int mask = (vM ? 1 : 0) | (vK ? 2 : 0) | (vT ? 4 : 0);
+    if (nstaged) {
+        // staged outputs: the element ranges of a chunk plan are formed and
+        // their completed slots summed in turn, and each chunk's values are
+        // copied to the host on a second stream while the next chunk is
+        // formed, so the copies (bound by the CPU-GPU link) overlap both
+        // phases.  A slot's value does not depend on the plan.
+        const size_t nsym = (size_t)m->np * (m->np + 1) / 2, nt = (size_t)m->np * m->np;
+        const size_t vbytes = sizeof(T) * (size_t)m->E * (2 * nsym + nt);
+        std::vector<int64_t> eb, sb;
+        constexpr int NCH = 8;
+        if ((rc = plan_chunks(m, prec, std::max(vbytes / NCH, CHUNK_TARGET_BYTES), NCH, s, eb, sb))) return rc;
+        if (eb.size() > 2) {
+            if (!m->copy_stream) {
+                FEM_CUDA_TRY(cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking));
+                for (auto& ev : m->copy_ev) FEM_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            }
+            const int n = (int)eb.size() - 1;
+            for (int c = 0; c < n; ++c) {
+                if ((rc = form_t<T>(m, k, ud, prec, mask, s, eb[c], eb[c + 1]))) return rc;
+                const int64_t a = sb[c], b = sb[c + 1];
+                if (b <= a) continue;
+                if ((rc = sum_t<T>(m, outd[0], outd[1], outd[2], s, a, b))) return rc;
+                // the copy stream waits for this chunk's sums (an event may be
+                // recorded again once a wait on it has been enqueued)
+                FEM_CUDA_TRY(cudaEventRecord(m->copy_ev[0], s));
+                FEM_CUDA_TRY(cudaStreamWaitEvent(m->copy_stream, m->copy_ev[0], 0));
+                for (int i = 0; i < 3; ++i)
+                    if (out_staged[i])
+                        FEM_CUDA_TRY(cudaMemcpyAsync(static_cast<T*>(outs[i]) + a, outd[i] + a, sizeof(T) * (size_t)(b - a),
+                                                     cudaMemcpyDeviceToHost, m->copy_stream));
+            }
+            FEM_CUDA_TRY(cudaStreamSynchronize(m->copy_stream));
+            FEM_CUDA_TRY(cudaStreamSynchronize(s));
+            return FEM_OK;
+        }
+    }
     // One formation, then one sum.  (Chunking the two phases so that each
     // range's V is summed while in L2 -- fem_chunk_plan and the range calls
-    // -- measured slower on GB300: the sum is bound by its gather latency,
-    // not by where V lives, and every extra launch adds a tail.)
+    // -- measured slower on GB300 for device outputs: the sum is bound by its
+    // gather latency, not by where V lives, and every extra launch adds a
+    // tail.)
     if ((rc = form_t<T>(m, k, ud, prec, mask, s))) return rc;
     if (!nstaged) {
         if ((rc = sum_t<T>(m, outd[0], outd[1], outd[2], s))) return rc;
