@@ -43,6 +43,11 @@ struct fem_batch {
     cudaEvent_t fork = nullptr, join[NBRANCH] = {};
     int simt_smem = 0, simt_grid = 0;
     int scatter_block = 256;
+    // CSR-sum items grouped by n_p: one launch per group
+    struct SumRange {
+        int np, begin, count, max_seg;
+    };
+    std::vector<SumRange> sum_ranges;
     double tuned_ms = 0.0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -71,10 +76,19 @@ int upload_items(DevBuf& buf, const std::vector<BatchItem>& items, cudaStream_t 
 int enqueue(fem_batch* b, cudaStream_t s) {
     int rc;
     const BatchMesh* tab = b->d_meshes.as<BatchMesh>();
+    auto sums = [&](auto zero) -> int {
+        using T = decltype(zero);
+        for (const auto& g : b->sum_ranges) {
+            const int r = batch_scatter_launch<T>(b->d_scatter.as<BatchItem>() + g.begin, g.count, tab, g.np,
+                                                  g.max_seg, s);
+            if (r) return r;
+        }
+        return FEM_OK;
+    };
     if (b->prec == FEM_FP64) {
         if ((rc = batch_simt_launch<double>(b->d_simt.as<BatchItem>(), b->n_simt, tab, b->simt_smem, b->simt_grid, s)))
             return rc;
-        return batch_scatter_launch<double>(b->d_scatter.as<BatchItem>(), b->n_scatter, tab, b->scatter_block, s);
+        return sums(0.0);
     }
     int nb = 0;
     FEM_CUDA_TRY(cudaEventRecord(b->fork, s));
@@ -105,7 +119,7 @@ int enqueue(fem_batch* b, cudaStream_t s) {
         FEM_CUDA_TRY(cudaStreamWaitEvent(s, b->join[k], 0));
     }
     if (b->n_tc5 && (rc = batch_tc_chunked_launch(b->d_tc5.as<BatchItem>(), b->n_tc5, tab, s))) return rc;
-    return batch_scatter_launch<float>(b->d_scatter.as<BatchItem>(), b->n_scatter, tab, b->scatter_block, s);
+    return sums(0.0f);
 }
 
 // One item per run of block/32 groups of contributions (a warp's task):
@@ -115,11 +129,19 @@ int build_scatter_items(fem_batch* b, int block, cudaStream_t s) {
     std::vector<BatchItem> items;
     const int run = std::max(1, block / 32);
     const int64_t unit = b->prec == FEM_FP64 ? 256 : 64;
-    for (int i = 0; i < b->n; ++i) {
-        const fem_mesh* m = b->meshes[i];
-        const int64_t ng = (m->E * m->np * m->np + unit - 1) / unit;
-        for (int64_t f = 0; f < ng; f += run)
-            items.push_back(BatchItem{i, m->type, f, (int)std::min<int64_t>(run, ng - f), 0});
+    b->sum_ranges.clear();
+    for (int np : {3, 4, 6, 10, 20}) {   // grouped by n_p, meshes in batch order within a group
+        fem_batch::SumRange g{np, (int)items.size(), 0, 0};
+        for (int i = 0; i < b->n; ++i) {
+            const fem_mesh* m = b->meshes[i];
+            if (m->np != np) continue;
+            g.max_seg = std::max(g.max_seg, m->max_seg);
+            const int64_t ng = (m->E * m->np * m->np + unit - 1) / unit;
+            for (int64_t f = 0; f < ng; f += run)
+                items.push_back(BatchItem{i, m->type, f, (int)std::min<int64_t>(run, ng - f), 0});
+        }
+        g.count = (int)items.size() - g.begin;
+        if (g.count > 0) b->sum_ranges.push_back(g);
     }
     b->n_scatter = (int)items.size();
     return upload_items(b->d_scatter, items, s);
@@ -369,7 +391,8 @@ int fem_batch_get_info(const fem_batch* b, fem_batch_info* out) {
     if (!b || !out) return fail(FEM_EINVAL, "NULL argument");
     std::memset(out, 0, sizeof(*out));
     out->n_meshes = b->n;
-    out->kernels_per_launch = (int)b->tc_ranges.size() + (b->n_tc5 ? 1 : 0) + (b->n_simt ? 1 : 0) + 1;
+    out->kernels_per_launch =
+        (int)b->tc_ranges.size() + (b->n_tc5 ? 1 : 0) + (b->n_simt ? 1 : 0) + (int)b->sum_ranges.size();
     out->tc_tiles = b->n_tc + b->n_tc5;
     out->simt_blocks = b->n_simt;
     out->sum_chunks = b->n_scatter;

@@ -208,8 +208,11 @@ template <typename T>
 int batch_simt_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int max_type_smem, int grid,
                       cudaStream_t s);
 int batch_simt_smem(int type, int fp64);
+// the CSR sums of the items of meshes with n_p nodes per element (max_seg:
+// the longest slot of those meshes)
 template <typename T>
-int batch_scatter_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int block, cudaStream_t s);
+int batch_scatter_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int np, int max_seg,
+                         cudaStream_t s);
 
 // One-time per-device upload of the reference tables of each kernel module.
 int tables_init_simt();

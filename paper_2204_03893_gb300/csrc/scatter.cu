@@ -493,24 +493,24 @@ int launch_steps8(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* v
     return launch_steps8_b<NP, STEPS, 4, true, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
 }
 
-// offsets of the per-type symmetric-index tables in the batched kernel
-__host__ __device__ constexpr int sym_tab_off(int np) {
-    return np == 3 ? 0 : np == 4 ? 9 : np == 6 ? 25 : np == 10 ? 61 : 161;
-}
-constexpr int SYM_TAB_TOTAL = 561;
 
-// Batched: one warp per work item (a run of `count` pair groups of one mesh),
-// the same per-warp sum as the single-mesh kernel, so a mesh's CSR values
-// carry the same bits alone and in a batch.
+// Batched: one warp per work item (a run of `count` groups of one mesh),
+// the same per-warp sum as the single-mesh kernels, so a mesh's CSR values
+// carry the same bits alone and in a batch.  The items are grouped by n_p
+// and each group has its own launch, compiled for its n_p and scan depth
+// (the deepest any of its meshes needs; deeper scans leave the sums
+// unchanged), with its registers capped so that 3 (FP64) or 4 (FP32) blocks
+// of 256 threads share an SM.
+// One block per SM fewer than the single-mesh sums: the per-item mesh
+// parameters take registers, and at the single-mesh cap the loop spills.
 template <typename T>
-__global__ void __launch_bounds__(512) batch_scatter_kernel(const BatchItem* __restrict__ items, int nitems,
-                                                            const BatchMesh* __restrict__ meshes) {
-    __shared__ short sym[SYM_TAB_TOTAL];
-    fill_sym_table<3>(sym + sym_tab_off(3));
-    fill_sym_table<4>(sym + sym_tab_off(4));
-    fill_sym_table<6>(sym + sym_tab_off(6));
-    fill_sym_table<10>(sym + sym_tab_off(10));
-    fill_sym_table<20>(sym + sym_tab_off(20));
+constexpr int batch_sum_blocks() { return SegShape<1, T>::MIN_BLOCKS - 1; }
+
+template <int NP, typename T, int STEPS>
+__global__ void __launch_bounds__(256, batch_sum_blocks<T>())
+    batch_segsum_kernel(const BatchItem* __restrict__ items, int nitems, const BatchMesh* __restrict__ meshes) {
+    __shared__ short sym[NP * NP];
+    fill_sym_table<NP>(sym);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -524,27 +524,46 @@ __global__ void __launch_bounds__(512) batch_scatter_kernel(const BatchItem* __r
         const T* VM = vM ? static_cast<const T*>(bm.VM) : nullptr;
         const T* VK = vK ? static_cast<const T*>(bm.VK) : nullptr;
         const T* VT = vT ? static_cast<const T*>(bm.VT) : nullptr;
-        const short* st = sym + sym_tab_off(bm.np);
         const uint32_t k0 = (uint32_t)w.first, k1 = k0 + (uint32_t)w.count;
         const uint32_t nc = (uint32_t)(bm.E * bm.np * bm.np), s1 = (uint32_t)bm.nnz;
         const uint32_t* cp = reinterpret_cast<const uint32_t*>(bm.contrib);
-        const uint4* h2 = reinterpret_cast<const uint4*>(bm.seg_head);
-#define FEM_BATCH_SEG_CASE(NP_)                                                                               \
-    case NP_:                                                                                                 \
-        if constexpr (sizeof(T) == 8)                                                                         \
-            segsum8_warp<NP_, 5, 0, double>(k0, k1, nc, 0u, s1, bm.seg_head, cp, st, VM, VK, VT, vM, vK, vT, lane);    \
-        else                                                                                                  \
-            segsum_warp<NP_, T, 5>(k0, k1, nc, 0u, s1, h2, cp, st, VM, VK, VT, vM, vK, vT, lane);               \
-        break;
-        switch (bm.np) {
-            FEM_BATCH_SEG_CASE(3)
-            FEM_BATCH_SEG_CASE(4)
-            FEM_BATCH_SEG_CASE(6)
-            FEM_BATCH_SEG_CASE(10)
-            FEM_BATCH_SEG_CASE(20)
-            default: break;
+        if constexpr (sizeof(T) == 8) {   // the single-mesh FP64 form: M/K pairs, then T
+            if (vM || vK)
+                segsum8_warp<NP, STEPS, 1, double>(k0, k1, nc, 0u, s1, bm.seg_head, cp, sym, VM, VK, VT, vM, vK, vT,
+                                                   lane);
+            if (vT)
+                segsum8_warp<NP, STEPS, 2, double>(k0, k1, nc, 0u, s1, bm.seg_head, cp, sym, VM, VK, VT, vM, vK, vT,
+                                                   lane);
+        } else {
+            segsum_warp<NP, T, STEPS>(k0, k1, nc, 0u, s1, reinterpret_cast<const uint4*>(bm.seg_head), cp, sym, VM,
+                                      VK, VT, vM, vK, vT, lane);
         }
-#undef FEM_BATCH_SEG_CASE
+    }
+}
+
+template <int NP, typename T, int STEPS>
+int batch_segsum_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int nsm, cudaStream_t s) {
+    const int wpb = 8;
+    int grid = nsm * batch_sum_blocks<T>();
+    if ((int64_t)grid * wpb > nitems) grid = (nitems + wpb - 1) / wpb;
+    cudaGetLastError();   // clear any stale error before the launch check
+    batch_segsum_kernel<NP, T, STEPS><<<grid, 256, 0, s>>>(items, nitems, meshes);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+template <int NP, typename T>
+int batch_segsum_np(const BatchItem* items, int nitems, const BatchMesh* meshes, int max_seg, int nsm,
+                    cudaStream_t s) {
+    if constexpr (sizeof(T) == 8) {
+        if (max_seg <= 9) return batch_segsum_launch<NP, T, 1>(items, nitems, meshes, nsm, s);
+        if (max_seg <= 25) return batch_segsum_launch<NP, T, 2>(items, nitems, meshes, nsm, s);
+        if (max_seg <= 57) return batch_segsum_launch<NP, T, 3>(items, nitems, meshes, nsm, s);
+        return batch_segsum_launch<NP, T, 5>(items, nitems, meshes, nsm, s);
+    } else {
+        if (max_seg <= 8) return batch_segsum_launch<NP, T, 2>(items, nitems, meshes, nsm, s);
+        if (max_seg <= 32) return batch_segsum_launch<NP, T, 4>(items, nitems, meshes, nsm, s);
+        return batch_segsum_launch<NP, T, 5>(items, nitems, meshes, nsm, s);
     }
 }
 
@@ -618,22 +637,23 @@ int run(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, 
 }  // namespace
 
 template <typename T>
-int batch_scatter_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int block, cudaStream_t s) {
+int batch_scatter_launch(const BatchItem* items, int nitems, const BatchMesh* meshes, int np, int max_seg,
+                         cudaStream_t s) {
     if (nitems <= 0) return FEM_OK;
-    if (block < 32 || block > 512) block = 256;
     int dev = 0, nsm = 0;
     FEM_CUDA_TRY(cudaGetDevice(&dev));
     FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int wpb = block / 32;
-    int grid = nsm * (2048 / block);
-    if ((int64_t)grid * wpb > nitems) grid = (nitems + wpb - 1) / wpb;
-    cudaGetLastError();   // clear any stale error before the launch check
-    batch_scatter_kernel<T><<<grid, block, 0, s>>>(items, nitems, meshes);
-    FEM_CUDA_TRY(cudaGetLastError());
-    return FEM_OK;
+    switch (np) {
+        case 3: return batch_segsum_np<3, T>(items, nitems, meshes, max_seg, nsm, s);
+        case 4: return batch_segsum_np<4, T>(items, nitems, meshes, max_seg, nsm, s);
+        case 6: return batch_segsum_np<6, T>(items, nitems, meshes, max_seg, nsm, s);
+        case 10: return batch_segsum_np<10, T>(items, nitems, meshes, max_seg, nsm, s);
+        case 20: return batch_segsum_np<20, T>(items, nitems, meshes, max_seg, nsm, s);
+        default: return fail(FEM_EINVAL, "element type");
+    }
 }
-template int batch_scatter_launch<float>(const BatchItem*, int, const BatchMesh*, int, cudaStream_t);
-template int batch_scatter_launch<double>(const BatchItem*, int, const BatchMesh*, int, cudaStream_t);
+template int batch_scatter_launch<float>(const BatchItem*, int, const BatchMesh*, int, int, cudaStream_t);
+template int batch_scatter_launch<double>(const BatchItem*, int, const BatchMesh*, int, int, cudaStream_t);
 
 int scatter_fp64(const fem_mesh& m, const double* VM, const double* VK, const double* VT, double* vM, double* vK,
                  double* vT, cudaStream_t s, int64_t s0, int64_t s1) {
