@@ -555,6 +555,11 @@ int fem_heat_step(fem_mesh* mesh, const fem_coeff* k, const fem_coeff* g, const 
  * one unit in the last place.  All pointers are device pointers (FEM_EINVAL
  * otherwise); d_k or d_dk may be NULL to skip it.  Enqueued on `stream`. */
 int fem_law_eval(const fem_coeff* k, const double* d_u, int64_t n, double* d_k, double* d_dk, void* stream);
+/* The same in FP32, with the device code of the FP32 and tensor-core
+ * element kernels, at u_i rounded to FP32: polynomials by Horner, the sine
+ * law by CUDA's sincosf, the piecewise-linear law as in FP64.  Same pointer
+ * rules and errors as fem_law_eval. */
+int fem_law_eval_fp32(const fem_coeff* k, const double* d_u, int64_t n, float* d_k, float* d_dk, void* stream);
 
 /* ------------------------------------------------------ reference element */
 /* The library's reference tables for (dim, order, qdeg): quadrature points

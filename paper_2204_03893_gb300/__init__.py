@@ -155,6 +155,7 @@ _SIGS = {
                                   C.c_void_p], C.c_int),
     "fem_form_elements": ([C.c_void_p, C.POINTER(fem_coeff), C.c_void_p, C.c_int, C.c_int, C.c_void_p], C.c_int),
     "fem_law_eval": ([C.POINTER(fem_coeff), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "fem_law_eval_fp32": ([C.POINTER(fem_coeff), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fem_bicgstab": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int),
                       C.POINTER(C.c_double), C.c_void_p], C.c_int),
     "fem_heat_step": ([C.c_void_p, C.POINTER(fem_coeff), C.POINTER(fem_coeff), C.c_void_p, C.c_double, C.c_void_p,
@@ -339,6 +340,10 @@ def fem_assemble_all_noalloc(mesh: int, k, d_u, d_vM, d_vK, d_vT, stream=None) -
 def fem_law_eval(k, d_u, n: int, d_k, d_dk, stream=None) -> None:
     """k(u) and k'(u) of a law at n device values, in FP64 on the GPU."""
     _check(lib().fem_law_eval(C.byref(k), _vp(d_u), int(n), _vp(d_k), _vp(d_dk), _stream(stream)))
+
+def fem_law_eval_fp32(k, d_u, n: int, d_k, d_dk, stream=None) -> None:
+    """k(u) and k'(u) in FP32 with the FP32 element kernels' device code."""
+    _check(lib().fem_law_eval_fp32(C.byref(k), _vp(d_u), int(n), _vp(d_k), _vp(d_dk), _stream(stream)))
 
 
 def fem_bicgstab(mesh: int, d_vA, d_b, d_x, rtol: float, maxit: int, stream=None):

@@ -756,6 +756,18 @@ int fem_law_eval(const fem_coeff* k, const double* d_u, int64_t n, double* d_k, 
     return law_eval_fp64(to_dev(k), d_u, n, d_k, d_dk, static_cast<cudaStream_t>(stream));
 }
 
+int fem_law_eval_fp32(const fem_coeff* k, const double* d_u, int64_t n, float* d_k, float* d_dk, void* stream) {
+    int rc = check_coeff(k);
+    if (rc) return rc;
+    if (n < 0) return fail(FEM_EINVAL, "negative count");
+    if (n == 0 || (!d_k && !d_dk)) return FEM_OK;
+    const void* ptrs[3] = {d_u, d_k, d_dk};
+    for (const void* p : ptrs)
+        if (p && !is_device_ptr(p)) return fail(FEM_EINVAL, "fem_law_eval_fp32 takes device pointers only");
+    if (!d_u) return fail(FEM_EINVAL, "u is NULL");
+    return law_eval_fp32(to_dev(k), d_u, n, d_k, d_dk, static_cast<cudaStream_t>(stream));
+}
+
 int fem_form_elements(fem_mesh* m, const fem_coeff* k, const void* d_u, int prec, int which, void* stream) {
     if (!m) return fail(FEM_EINVAL, "NULL mesh");
     if (!valid_prec(prec)) return fail(FEM_EINVAL, "unknown precision");

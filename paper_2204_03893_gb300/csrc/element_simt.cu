@@ -9,6 +9,7 @@
 // Section 5.2 conductivity tensor with u in its second mode.  Only the
 // n_p(n_p+1)/2 distinct entries of the symmetric M and K are formed
 // (Section 7).  V is written element-major: V[e][n].
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -750,6 +751,38 @@ int tables_init_simt() {
     FEM_CUDA_TRY(cudaMemcpyToSymbol(g_Q64, q64.data(), sizeof(double) * Q_TOTAL));
     FEM_CUDA_TRY(cudaMemcpyToSymbol(g_Q32, q32.data(), sizeof(float) * Q_TOTAL));
     if (dev < 64) g_init_done[dev] = true;
+    return FEM_OK;
+}
+
+// The FP32 law code of the FP32 and tensor-core element kernels (class LC),
+// at u rounded to FP32.
+template <int LC>
+__global__ void __launch_bounds__(256) law_eval32_kernel(CoeffDev k, const double* __restrict__ u, int64_t n,
+                                                         float* __restrict__ kv, float* __restrict__ dkv) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float dk;
+        const float v = k_eval<float, LC>(k, (float)u[i], dk);
+        if (kv) kv[i] = v;
+        if (dkv) dkv[i] = dk;
+    }
+}
+
+int law_eval_fp32(const CoeffDev& k, const double* u, int64_t n, float* kv, float* dkv, cudaStream_t s) {
+    if (n <= 0) return FEM_OK;
+    int rc = tables_init_simt();
+    if (rc) return rc;
+    int dev = 0, nsm = 0;
+    FEM_CUDA_TRY(cudaGetDevice(&dev));
+    FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int64_t grid = (n + 255) / 256;
+    if (grid > (int64_t)nsm * 8) grid = (int64_t)nsm * 8;
+    cudaGetLastError();   // clear any stale error before the launch check
+    switch (law_class(k)) {
+        case LC_POLY3: law_eval32_kernel<LC_POLY3><<<(unsigned)grid, 256, 0, s>>>(k, u, n, kv, dkv); break;
+        case LC_SIN: law_eval32_kernel<LC_SIN><<<(unsigned)grid, 256, 0, s>>>(k, u, n, kv, dkv); break;
+        default: law_eval32_kernel<LC_ANY><<<(unsigned)grid, 256, 0, s>>>(k, u, n, kv, dkv); break;
+    }
+    FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
 

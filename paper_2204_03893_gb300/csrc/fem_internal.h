@@ -131,6 +131,7 @@ int element_simt_fp64(const fem_mesh& m, const CoeffDev& k, const double* u, dou
                       cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);
 // The FP64 conductivity law alone: k(u_i), k'(u_i) for i < n (either output may be null).
 int law_eval_fp64(const CoeffDev& k, const double* u, int64_t n, double* kv, double* dkv, cudaStream_t s);
+int law_eval_fp32(const CoeffDev& k, const double* u, int64_t n, float* kv, float* dkv, cudaStream_t s);
 // FP32 paths split each gathered FP64 nodal value as hi + lo (split_f64).
 int element_simt_fp32(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
                       cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);

@@ -94,3 +94,41 @@ def test_law_eval_refuses_host_pointers():
     with pytest.raises(F.FemError) as ei:
         F.fem_law_eval(F.coeff("poly", (1.0,)), u, 10, u, u)
     assert ei.value.code == F.FEM_EINVAL
+
+
+def test_fp32_law_code():
+    """fem_law_eval_fp32: the FP32 law code of the FP32 and tensor-core
+    element kernels.  Its sin/cos (CUDA's sincosf) against the sine and
+    cosine of the same FP32 argument in FP64 (numpy): at most 3 FP32 units in
+    the last place over |x| < 100 (multiples of pi/128 and of pi, tiny and
+    spread arguments), 8 beyond; a polynomial law against its Horner form in
+    FP32."""
+    rng = np.random.default_rng(11)
+    x = np.concatenate([rng.uniform(-99.0, 99.0, 200000), rng.uniform(0.0, 3.0, 50000),
+                        np.arange(-4000, 4000) * (np.pi / 128), np.arange(-30, 31) * np.pi,
+                        np.arange(-30, 30) * np.pi + np.pi / 2, rng.uniform(-1e-6, 1e-6, 1000),
+                        rng.uniform(100.0, 2e4, 2000) * rng.choice([-1, 1], 2000)]).astype(np.float32)
+    du = torch.tensor(x.astype(np.float64), device="cuda")
+    k = torch.empty(x.size, dtype=torch.float32, device="cuda")
+    dk = torch.empty_like(k)
+    F.fem_law_eval_fp32(F.coeff("sin", (0.0, 1.0, 1.0)), du, x.size, k, dk)
+    torch.cuda.synchronize()
+    xs = x.astype(np.float64)
+    for got, ref in ((k.cpu().numpy(), np.sin(xs)), (dk.cpu().numpy(), np.cos(xs))):
+        ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+        err = np.abs(got.astype(np.float64) - ref) / ulp
+        inner = np.abs(xs) < 100.0
+        assert err[inner].max() <= 3.0, err[inner].max()
+        assert err[~inner].max() <= 8.0, err[~inner].max()
+    # a quadratic law: the 3-term Horner of the FP32 kernels
+    u = rng.uniform(-2.0, 2.0, 10000)
+    du = torch.tensor(u, device="cuda")
+    k = torch.empty(u.size, dtype=torch.float32, device="cuda")
+    dk = torch.empty_like(k)
+    F.fem_law_eval_fp32(F.coeff("poly", (1.0, 0.5, 0.25)), du, u.size, k, dk)
+    torch.cuda.synchronize()
+    uf = u.astype(np.float32).astype(np.float64)
+    assert np.abs(k.cpu().numpy() - (1.0 + 0.5 * uf + 0.25 * uf ** 2)).max() <= 4e-7 * 3
+    assert np.abs(dk.cpu().numpy() - (0.5 + 0.5 * uf)).max() <= 4e-7 * 3
+    with pytest.raises(F.FemError):
+        F.fem_law_eval_fp32(F.coeff("sin", (0.0, 1.0, 1.0)), np.zeros(4), 4, k, dk)
