@@ -331,12 +331,12 @@ def law_ops(kind: str, n: int):
     """(FP64 operations, of which fused multiply-adds) of one evaluation of
     k(u) and k'(u) in the FP64 kernels: Horner of the actual degree for a
     polynomial with n coefficients; for the sine law the table-driven sin/cos
-    (argument 1, reduction 4, h^2 1, sin h 4, cos h - 1 3, combination 6) and
+    (argument 1, reduction 4, h^2 1, sin h 3, cos h - 1 2, combination 6) and
     k, k' (3); the piecewise-linear law about 4."""
     if kind == "poly":
         return (0, 0) if n <= 1 else (2 * n - 3, 2 * n - 3)
     if kind == "sin":
-        return 22, 10
+        return 20, 9
     return 4, 1
 
 

@@ -729,17 +729,17 @@ int tables_init_simt() {
                 p1m[o + sym_index(np, i, j)] = v;
             }
     }
-    // sine table of the FP64 laws: (sin, cos)(k pi/128), k = 0..255, from
+    // sine table of the FP64 laws: (sin, cos)(k pi/512), k = 0..1023, from
     // the first quadrant by symmetry, so that the zeros and ones are exact:
-    // s_j = sin(j pi/128), c_j = sin((64 - j) pi/128) for j < 64 from the
+    // s_j = sin(j pi/512), c_j = sin((256 - j) pi/512) for j < 256 from the
     // host's long double sine (arguments in [0, pi/2], rounded once), then
-    // quadrant q = k / 64 maps (s_j, c_j) to (c_j, -s_j), (-s_j, -c_j), (-c_j, s_j)
+    // quadrant q = k / 256 maps (s_j, c_j) to (c_j, -s_j), (-s_j, -c_j), (-c_j, s_j)
     std::vector<double2> sct(SC_TAB);
     const long double pi_l = 3.14159265358979323846264338327950288L;
     for (int k = 0; k < SC_TAB; ++k) {
-        const int q = k / 64, j = k % 64;
-        const double sj = (double)sinl((long double)j * pi_l / 128.0L);
-        const double cj = (double)sinl((long double)(64 - j) * pi_l / 128.0L);
+        const int q = k / 256, j = k % 256;
+        const double sj = (double)sinl((long double)j * pi_l / 512.0L);
+        const double cj = (double)sinl((long double)(256 - j) * pi_l / 512.0L);
         sct[k] = q == 0 ? make_double2(sj, cj) : q == 1 ? make_double2(cj, -sj)
                : q == 2 ? make_double2(-sj, -cj) : make_double2(-cj, sj);
     }

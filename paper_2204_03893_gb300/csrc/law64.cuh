@@ -25,35 +25,38 @@ __host__ __device__ inline int law_code(const CoeffDev& k) {
 // ------------------------------------------------------------------ sine law
 // sin x and cos x by table lookup and short Taylor polynomials (the
 // table-driven method of Tang, and of Gal and Bachelis' accurate tables).
-// x is split as k (pi/128) + h with k = rint(x 128/pi) and |h| <= pi/256 (a
-// little more after rounding), the subtraction done in two pieces (Cody and
-// Waite): pi/128 = SC_HI + SC_LO with SC_HI holding 33 significant bits, so
-// k SC_HI is exact and x - k SC_HI is exact (Sterbenz) for |k| < 2^20.  Then
-//     sin h = h - h^3/3! + h^5/5! - h^7/7!           (next term < 2e-21 |h|)
-//     cos h - 1 = -h^2/2! + h^4/4! - h^6/6!          (next term < 2e-20)
+// x is split as k (pi/512) + h with k = rint(x 512/pi) and |h| <= pi/1024 (a
+// little more after rounding).  k comes from one fused multiply-add with
+// 1.5 2^52, which leaves rint(x 512/pi) in the low bits of the sum (read
+// with an integer move; one subtraction gives it as a double), and the
+// range test is an integer test of x's exponent, so the reduction takes 4
+// FP64 operations.  The subtraction is done in two pieces (Cody and Waite):
+// pi/512 = SC_HI + SC_LO with SC_HI holding 33 significant bits, so k SC_HI
+// is exact and x - k SC_HI is exact (Sterbenz) for |k| < 2^20.  Then
+//     sin h = h - h^3/3! + h^5/5!                    (next term < 2e-19 |h|)
+//     cos h - 1 = -h^2/2! + h^4/4!                   (next term < 2e-18)
 //     sin x = S_k + (C_k sin h + S_k (cos h - 1)),
 //     cos x = C_k + (C_k (cos h - 1) - S_k sin h),
-// with S_k, C_k = sin, cos (k pi/128) correctly rounded in a 256-entry table
-// (one period).  The corrections are small against S_k, C_k, so the result is
-// within about one unit in the last place.  |x| >= 2^20 pi/128 (about 25736)
-// and non-finite x fall back to CUDA's sincos.  18 FP64 operations.
-constexpr double SC_INV = 0x1.45f306dc9c883p+5;   // 128/pi
-constexpr double SC_HI = 0x1.921fb544p-6;         // pi/128 to 33 bits
-constexpr double SC_LO = 0x1.0b4611a626331p-40;   // pi/128 - SC_HI
-constexpr int SC_TAB = 256;
+// with S_k, C_k = sin, cos (k pi/512) correctly rounded in a 1024-entry
+// table (one period).  The corrections are small against S_k, C_k, so the
+// result is within about one unit in the last place.  |x| >= 4096 and
+// non-finite x fall back to CUDA's sincos.  16 FP64 operations.
+constexpr double SC_INV = 0x1.45f306dc9c883p+7;   // 512/pi
+constexpr double SC_HI = 0x1.921fb544p-8;         // pi/512 to 33 bits
+constexpr double SC_LO = 0x1.0b4611a626331p-42;   // pi/512 - SC_HI
+constexpr double SC_RND = 0x1.8p+52;              // adding it rounds to an integer, kept in the low bits
+constexpr int SC_TAB = 1024;
 
 __device__ __forceinline__ void sincos_tab(double x, const double2* __restrict__ tab, double& s, double& c) {
-    const double kf = rint(x * SC_INV);
-    if (fabs(kf) < 1048576.0) {
+    if ((__double2hiint(x) & 0x7fffffff) < 0x40b00000) {   // |x| < 4096 (so |k| < 2^20), finite
+        const double kr = fma(x, SC_INV, SC_RND);
+        const int k = __double2loint(kr);
+        const double kf = kr - SC_RND;
         const double h = fma(-kf, SC_LO, fma(-kf, SC_HI, x));
         const double h2 = h * h;
-        double ps = fma(h2, -1.0 / 5040.0, 1.0 / 120.0);
-        ps = fma(h2, ps, -1.0 / 6.0);
-        const double sh = fma(h * h2, ps, h);
-        double pc = fma(h2, -1.0 / 720.0, 1.0 / 24.0);
-        pc = fma(h2, pc, -0.5);
-        const double ch = h2 * pc;
-        const double2 t = tab[static_cast<int>(kf) & (SC_TAB - 1)];
+        const double sh = fma(h * h2, fma(h2, 1.0 / 120.0, -1.0 / 6.0), h);
+        const double ch = h2 * fma(h2, 1.0 / 24.0, -0.5);
+        const double2 t = tab[k & (SC_TAB - 1)];
         s = t.x + fma(t.x, ch, t.y * sh);
         c = t.y + fma(t.y, ch, -(t.x * sh));
     } else {
