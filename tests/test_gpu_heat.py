@@ -39,10 +39,12 @@ def _dev(x):
     return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
 
-def test_bicgstab_against_direct_solve():
+@pytest.mark.parametrize("N", [8, 100])
+def test_bicgstab_against_direct_solve(N):
+    """A small (n = 289) and a larger (n = 40 401) Experiment-2 system."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as spl
-    m = _mesh()
+    m = _mesh(N)
     o = orc.Oracle.of(m)
     u = 300.0 * mg.fourier_field(m.coords / 0.2, 92)
     r = o.assemble(u, mg.Coeff(*KLAW), m=RHOC, want_abs=False)
