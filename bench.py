@@ -343,11 +343,11 @@ def law_ops(kind: str, n: int):
 def fp64_element_ops(d: int, p: int, kind: str, n: int):
     """(FP64 operations, flops with a fused multiply-add counted as 2) per
     element of the FP64 element product, counted from the kernel's algorithm.
-    P1 (element_p1_fp64_kernel): M m b_e Qbar (1 + n_sym), du (d), per
-    quadrature point u_q (d FMA), the law, s0 (1 FMA), w k' (1), s1 (n_p
-    FMA); K: b s0 (1), column sums of A (d(d-1) + d-1 adds), n_sym products;
-    T: A ghat (d + d(d-1) FMA), its sum (d-1), b (G A ghat) (n_p), n_p^2
-    products.  P2/P3 (element_simt_kernel): the product V = X Q
+    P1 (element_p1_fp64_kernel): M m b_e and its diagonal and off-diagonal
+    factors (3), du (d), per quadrature point u_q (d FMA), the law, s0 (1
+    FMA), w k' (1), s1 (n_p FMA); K: b s0 (1), column sums of A (d(d-1) + d-1
+    adds), n_sym products; T: A ghat (d + d(d-1) FMA), its sum (d-1),
+    b (G A ghat) (n_p); T_e's outer product is left to the CSR sum.  P2/P3 (element_simt_kernel): the product V = X Q
     (gemm_flops_per_element) plus, per point, u_q and ghat (n_p (1+d) FMA),
     A ghat (d^2 FMA) and the law."""
     lo, lf = law_ops(kind, n)
@@ -355,8 +355,8 @@ def fp64_element_ops(d: int, p: int, kind: str, n: int):
     n_q = {(2, 1): 3, (2, 2): 6, (2, 3): 12, (3, 1): 4, (3, 2): 11, (3, 3): 24}[(d, p)]
     nsym = n_p * (n_p + 1) // 2
     if p == 1:
-        ops = (1 + nsym) + d + n_q * (d + lo + 2 + n_p) + (1 + d * (d - 1) + (d - 1) + nsym) \
-            + (d + d * (d - 1) + (d - 1) + n_p + n_p * n_p)
+        ops = 3 + d + n_q * (d + lo + 2 + n_p) + (1 + d * (d - 1) + (d - 1) + nsym) \
+            + (d + d * (d - 1) + (d - 1) + n_p)
         fma = n_q * (d + lf + 1 + n_p) + d * (d - 1)
         return ops, ops + fma
     gemm = gemm_flops_per_element(d, p)
@@ -624,16 +624,19 @@ def measure_sweep(F, torch, stream, name, precs=("tf32x3", "fp64"), nsweep=10, w
     return out
 
 
-def phase_bytes(mesh, nnz: int, esz: int):
+def phase_bytes(mesh, nnz: int, esz: int, t_factored: bool = False):
     """Algorithmic bytes of one reassembly of M, K, T: (element phase, CSR sum).
     Element phase: connectivity (4 B per node of an element), the geometry
     cache (b and the d(d+1)/2 entries of A), V written (2 n_sym + n_p^2
-    values), u read once.  CSR sum: an 8-byte head word per group of 32
+    values, or 2 n_sym + 2 n_p where T_e is stored as its two factors: P1 in
+    FP64), u read once.  CSR sum: an 8-byte head word per group of 32
     contributions, every contribution's 4-byte index and V entries, the CSR
     values written."""
     d, E, n = mesh.d, mesh.n_elems, mesh.n_nodes
     n_p = mesh.conn.shape[1]
     nsym, nt, ngeo = n_p * (n_p + 1) // 2, n_p * n_p, 1 + d * (d + 1) // 2
+    if t_factored:
+        nt = 2 * n_p
     nc = E * n_p * n_p
     form = E * (n_p * 4 + ngeo * esz + (2 * nsym + nt) * esz) + n * 8
     summ = (nc + 31) // 32 * 8 + nc * 4 + E * (2 * nsym + nt) * esz + 3 * nnz * esz
@@ -1057,7 +1060,8 @@ def run_ours(args, rank, world, local_rank):
     esz = 8 if args.prec == "fp64" else 4
     n = wl.mesh.n_nodes
     nc = E * n_p * n_p
-    bytes_form, bytes_sum = phase_bytes(wl.mesh, nnz, esz)
+    t_fac = args.prec == "fp64" and p == 1   # P1 in FP64: T_e stored as its two factors
+    bytes_form, bytes_sum = phase_bytes(wl.mesh, nnz, esz, t_fac)
     mf, msum = statistics.mean(form_ms), statistics.mean(sum_ms)
     on_tc = args.prec in ("tf32x3", "bf16x3", "bf16x6")
     fp64 = args.prec == "fp64"
@@ -1068,8 +1072,13 @@ def run_ours(args, rank, world, local_rank):
     kernels = {
         "element_form": {"kernel": form_kernel, "src": "element_tc.cu" if on_tc else "element_simt.cu",
                          "ms": mf, "bytes": bytes_form, "flops": flops * E, "fp64_ops": ops * E},
+        # FP64 sum: the additions of M and K (nc - nnz each) and of T, whose
+        # contributions are products of T_e's factors where those are stored
+        # (nc multiplications fused with nc - nnz additions)
         "csr_sum": {"kernel": "segsum8_kernel" if fp64 else "segsum_kernel", "src": "scatter.cu", "ms": msum,
-                    "bytes": bytes_sum, "flops": 3 * (nc - nnz) if fp64 else 0, "fp64_ops": 3 * (nc - nnz) if fp64 else 0},
+                    "bytes": bytes_sum,
+                    "flops": (2 * (nc - nnz) + (2 * nc - nnz if t_fac else nc - nnz)) if fp64 else 0,
+                    "fp64_ops": (2 * (nc - nnz) + (nc if t_fac else nc - nnz)) if fp64 else 0},
     }
     phases = {}
     for name, kd in kernels.items():

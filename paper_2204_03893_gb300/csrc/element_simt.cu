@@ -10,6 +10,7 @@
 // n_p(n_p+1)/2 distinct entries of the symmetric M and K are formed
 // (Section 7).  V is written element-major: V[e][n].
 #include <atomic>
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -49,8 +50,13 @@ struct Tabs<float> {
 constexpr int BT = 64;   // elements (threads) per block
 
 // FP64 P1 tables: the mass factor sum_q w_q phi_q[i] phi_q[j] (n_sym values,
-// triangles then tetrahedra) and the sine table of law64.cuh
+// triangles then tetrahedra) and the sine table of law64.cuh.  With a rule
+// that treats the vertices alike the factor takes one value on the diagonal
+// and one off it: c_p1m2 = (diagonal, off-diagonal) for triangles, then
+// tetrahedra, used where c_p1m2_on is set.
 __constant__ double c_p1m[6 + 10];
+__constant__ double c_p1m2[4];
+__constant__ int c_p1m2_on[2];
 __device__ double2 g_sincos_tab[SC_TAB];
 
 // nodal values: FP64 as given; the FP32 path splits each gathered value
@@ -199,6 +205,12 @@ __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict_
 //     K_e = b_e (sum_q w_q k(u_q)) G A_e G^T,
 //     T_e[i][j] = b_e (G A_e ghat)_i (sum_q w_q k'(u_q) phi_q[j]),
 //     M_e = m b_e sum_q w_q phi_q phi_q^T,
+// T_e is the outer product of two vectors of n_p values, and is stored as
+// those two factors (t_e = b_e G A_e ghat, then s_e with s_e[j] = sum_q w_q
+// k'(u_q) phi_q[j]): the CSR sum multiplies them as it adds (one fused
+// multiply-add per contribution, where the outer product would cost the
+// element n_p^2 multiplications).  M_e takes two multiplications when the
+// rule treats the vertices alike (one value on the diagonal, one off it).
 // with ghat = G^T u_e = (u_1 - u_0, ..., u_d - u_0).  G A G^T needs no
 // multiplications: its (i, j) entry for i, j >= 1 is A[i-1][j-1], its (0, j)
 // entry minus the (j-1)-th column sum of A, its (0, 0) entry the sum of all
@@ -208,8 +220,8 @@ __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict_
 // HBM, bounds the FP64 path on this part.
 //
 // The element's rows are written through `mk` (2 n_sym values: M at even, K
-// at odd positions) and `tr` (n_p^2 values), which point into shared memory
-// in the single-mesh kernel and into V in the batched one.
+// at odd positions) and `tr` (2 n_p values: the factors of T_e), which point
+// into shared memory in the single-mesh kernel and into V in the batched one.
 template <int D, int LAW>
 __device__ __forceinline__ void p1_element_fp64(int64_t e, const int* __restrict__ conn, const double* __restrict__ geo,
                                                 int64_t gs, const double* __restrict__ u, const CoeffDev& k,
@@ -222,8 +234,16 @@ __device__ __forceinline__ void p1_element_fp64(int64_t e, const int* __restrict
     const double b = geo[e];
     if (doM) {
         const double mb = mass * b;
+        if (c_p1m2_on[D - 2]) {
+            const double md = mb * c_p1m2[2 * (D - 2)], mo = mb * c_p1m2[2 * (D - 2) + 1];
 #pragma unroll
-        for (int t = 0; t < NP * (NP + 1) / 2; ++t) mk[2 * t] = mb * c_p1m[M0 + t];
+            for (int i = 0; i < NP; ++i)
+#pragma unroll
+                for (int j = i; j < NP; ++j) mk[2 * sym_index(NP, i, j)] = i == j ? md : mo;
+        } else {
+#pragma unroll
+            for (int t = 0; t < NP * (NP + 1) / 2; ++t) mk[2 * t] = mb * c_p1m[M0 + t];
+        }
     }
     if (!doK && !doT) return;
     double A[NS];
@@ -293,9 +313,9 @@ __device__ __forceinline__ void p1_element_fp64(int64_t e, const int* __restrict
 #pragma unroll
         for (int a = 0; a < D; ++a) bt[a + 1] = b * r[a];
 #pragma unroll
-        for (int i = 0; i < NP; ++i)
+        for (int i = 0; i < NP; ++i) tr[i] = bt[i];
 #pragma unroll
-            for (int j = 0; j < NP; ++j) tr[i * NP + j] = bt[i] * s1[j];
+        for (int j = 0; j < NP; ++j) tr[NP + j] = s1[j];
     }
 }
 
@@ -304,7 +324,7 @@ constexpr int P1_BT = 128;   // elements (threads) per block of the FP64 P1 kern
 template <int D>
 __host__ __device__ constexpr int p1_ldmk() { return (D + 1) * (D + 2) | 1; }   // 2 n_sym, odd
 template <int D>
-__host__ __device__ constexpr int p1_ldt() { return (D + 1) * (D + 1) | 1; }
+__host__ __device__ constexpr int p1_ldt() { return 2 * (D + 1) | 1; }   // the two factors of T_e, odd
 
 template <int D, int LAW>
 __host__ __device__ constexpr size_t p1_smem() {
@@ -321,7 +341,7 @@ __global__ void __launch_bounds__(P1_BT) element_p1_fp64_kernel(const int* __res
                                                                 const double* __restrict__ u, CoeffDev k, double mass,
                                                                 double* __restrict__ VMK, bool doM, bool doK,
                                                                 double* __restrict__ VT) {
-    constexpr int NP = D + 1, NSYM = NP * (NP + 1) / 2, NT = NP * NP;
+    constexpr int NP = D + 1, NSYM = NP * (NP + 1) / 2, NT = 2 * NP;   // NT: T_e's factors
     constexpr int LDMK = p1_ldmk<D>(), LDT = p1_ldt<D>();
     extern __shared__ __align__(16) unsigned char p1_smem_raw[];
     const double2* tab = reinterpret_cast<const double2*>(p1_smem_raw);
@@ -380,7 +400,7 @@ int launch_p1_law(const fem_mesh& m, const CoeffDev& k, const double* u, const d
     cudaGetLastError();   // clear any stale error before the launch check
     kern<<<(unsigned)grid, P1_BT, smem, s>>>(m.conn.as<int>() + e0 * NP, geo + e0, E, m.E, u, k, m.m,
                                               VMK ? VMK + 2 * e0 * (NP * (NP + 1) / 2) : nullptr, doM, doK,
-                                              VT ? VT + e0 * NP * NP : nullptr);
+                                              VT ? VT + e0 * 2 * NP : nullptr);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
@@ -460,9 +480,9 @@ __global__ void __launch_bounds__(BT) batch_simt_kernel(const BatchItem* __restr
             // FP64 P1: the same regrouped product as the single-mesh kernel
             // (same bits), rows written straight into V
             if (w.type == 0 || w.type == 3) {
-                const int nsym = w.type == 0 ? 6 : 10, nt = w.type == 0 ? 9 : 16;
+                const int nsym = w.type == 0 ? 6 : 10, ntf = w.type == 0 ? 6 : 8;   // ntf: T_e's factors
                 double* mk = (VM || VK) ? static_cast<double*>(bm.VM) + 2 * e * nsym : nullptr;
-                double* tr = VT ? VT + e * nt : nullptr;
+                double* tr = VT ? VT + e * ntf : nullptr;
                 if (w.type == 0)
                     p1_element_fp64_any<2>(bm.k, e, bm.conn, geo, bm.E, u, mass, VM != nullptr, VK != nullptr, mk, tr);
                 else
@@ -744,6 +764,25 @@ int tables_init_simt() {
                : q == 2 ? make_double2(-sj, -cj) : make_double2(-cj, sj);
     }
     FEM_CUDA_TRY(cudaMemcpyToSymbol(c_p1m, p1m, sizeof(p1m)));
+    // one diagonal and one off-diagonal value where every entry of each kind
+    // agrees to within rounding (a rule symmetric in the vertices)
+    double p1m2[4] = {};
+    int p1m2_on[2] = {0, 0};
+    for (int t : {0, 3}) {
+        const int np = t == 0 ? 3 : 4, o = t == 0 ? 0 : 6, c = t == 0 ? 0 : 1;
+        const double dg = p1m[o + sym_index(np, 0, 0)], od = p1m[o + sym_index(np, 0, 1)];
+        bool same = dg > 0.0 && od > 0.0;
+        for (int i = 0; i < np; ++i)
+            for (int j = i; j < np; ++j) {
+                const double v = p1m[o + sym_index(np, i, j)], ref = i == j ? dg : od;
+                same = same && std::fabs(v - ref) <= 4e-16 * ref;
+            }
+        p1m2[2 * c] = dg;
+        p1m2[2 * c + 1] = od;
+        p1m2_on[c] = same ? 1 : 0;
+    }
+    FEM_CUDA_TRY(cudaMemcpyToSymbol(c_p1m2, p1m2, sizeof(p1m2)));
+    FEM_CUDA_TRY(cudaMemcpyToSymbol(c_p1m2_on, p1m2_on, sizeof(p1m2_on)));
     FEM_CUDA_TRY(cudaMemcpyToSymbol(g_sincos_tab, sct.data(), sizeof(double2) * SC_TAB));
     std::vector<float> ref32(ref64.begin(), ref64.end()), q32(q64.begin(), q64.end());
     FEM_CUDA_TRY(cudaMemcpyToSymbol(c_ref64, ref64.data(), sizeof(double) * TAB_TOTAL));

@@ -151,6 +151,11 @@ int element_mass_u_tc(const fem_mesh& m, const CoeffDev& mk, const double* u, co
 int element_tc_bf16(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
                     int nparts, cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);
 
+// FP64 element matrices of P1 simplices (per-element geometry) hold T_e as
+// its two factors, 2 n_p values per element (element_simt.cu); the FP64 CSR
+// sums read them so.
+inline bool p1_t_factored(const fem_mesh& m) { return (m.type == 0 || m.type == 3) && !m.perq; }
+
 // Segmented reduction of V into CSR values (outputs may be null).
 // s0, s1: slot range [s0, s1) (s1 = -1: to the end); outputs are the
 // whole CSR arrays.

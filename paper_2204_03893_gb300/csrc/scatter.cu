@@ -37,15 +37,29 @@ struct Pair<float> { using type = float2; };
 template <>
 struct Pair<double> { using type = double2; };
 
-template <int NP, typename T>
+// TF: T is stored as the two factors of each element's outer product
+// (P1 simplices in FP64: t_e then s_e, 2 n_p values per element), and a
+// contribution carries the pair (t_e[i], s_e[j]) whose product it adds.
+template <int NP, typename T, bool TF = false>
 struct Contribution {
-    T m, k, t;
+    T m, k, t, s;   // s: the second factor (TF only)
     // 32-bit unsigned index arithmetic (element entries, slots and V
     // offsets of a mesh are below 2^31)
     __device__ __forceinline__ void load(uint32_t c, const short* __restrict__ sym, const T* __restrict__ VM,
                                          const T* __restrict__ VK, const T* __restrict__ VT) {
         constexpr uint32_t NT = NP * NP, NSYM = NP * (NP + 1) / 2;
-        t = VT ? __ldg(VT + c) : T(0);
+        if constexpr (TF) {
+            if (VT) {
+                const uint32_t e = c / NT, l = c - e * NT;
+                const T* f = VT + e * (2 * NP);
+                t = __ldg(f + l / NP);
+                s = __ldg(f + NP + l % NP);
+            } else {
+                t = s = T(0);
+            }
+        } else {
+            t = VT ? __ldg(VT + c) : T(0);
+        }
         if (VM || VK) {
             const uint32_t e = c / NT;
             const uint32_t off = e * NSYM + (uint32_t)sym[c - e * NT];
@@ -261,7 +275,9 @@ __device__ __forceinline__ void segsum_warp(uint32_t k0, uint32_t k1, uint32_t n
 // interleaved pairs), 2 T; the split form runs a task twice with fewer
 // values live per lane (more resident warps).  The additions per matrix are
 // the same in every form, so are the bits.
-template <int NP, int STEPS, int PART, typename T>
+// TF: T held as per-element factors (see Contribution); each T
+// contribution is added as a fused multiply-add of its two factors.
+template <int NP, int STEPS, int PART, typename T, bool TF = false>
 __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t nc, uint32_t s0, uint32_t s1,
                                              const uint2* __restrict__ head, const uint32_t* __restrict__ contrib,
                                              const short* __restrict__ sym, const T* __restrict__ VM,
@@ -301,18 +317,18 @@ __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t 
 #pragma unroll
             for (int i = 0; i < 8; ++i) c[i] = p0 + i < nc ? __ldg(contrib + p0 + i) : 0u;
         }
-        Contribution<NP, T> v[8];
+        Contribution<NP, T, TF> v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             if (p0 + i < nc) v[i].load(c[i], sym, VM, VK, VT);
-            else v[i].m = v[i].k = v[i].t = T(0);
+            else v[i].m = v[i].k = v[i].t = v[i].s = T(0);
         }
         auto own = [&](uint32_t sl) { return live && sl >= slo && sl < shi; };
         // in-lane pass: a* = the open piece, p* = the piece before the first head
         const bool h0 = bits & 1u;
         T am = T(0), ak = T(0), at = T(0), pm = T(0), pk = T(0), pt = T(0);
         if constexpr (MK) { am = v[0].m; ak = v[0].k; }
-        if constexpr (TT) at = v[0].t;
+        if constexpr (TT) at = TF ? v[0].t * v[0].s : v[0].t;
         bool seen = h0;
         uint32_t cur = slot0;   // slot of the open piece once a head was seen
 #pragma unroll
@@ -329,7 +345,10 @@ __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t 
                 am = h ? v[i].m : am + v[i].m;
                 ak = h ? v[i].k : ak + v[i].k;
             }
-            if constexpr (TT) at = h ? v[i].t : at + v[i].t;
+            if constexpr (TT) {
+                if constexpr (TF) at = fma(v[i].t, v[i].s, h ? T(0) : at);
+                else at = h ? v[i].t : at + v[i].t;
+            }
         }
         // segmented inclusive scan of the open pieces over the lanes
         const uint32_t lup = __ballot_sync(FULL, seen) & (FULL >> (31 - lane));
@@ -420,7 +439,7 @@ __global__ void __launch_bounds__(256, SegShape<STEPS, T>::MIN_BLOCKS)
 // to TASK8 steps grid-stride
 constexpr uint32_t TASK8 = 8;
 
-template <int NP, int STEPS, int MINB, bool SPLIT, typename T>
+template <int NP, int STEPS, int MINB, bool SPLIT, typename T, bool TF>
 __global__ void __launch_bounds__(256, MINB) segsum8_kernel(const uint2* __restrict__ head,
                                                       const uint32_t* __restrict__ contrib, uint32_t nc,
                                                       const int* __restrict__ seg_ptr, uint32_t s0, uint32_t s1,
@@ -444,22 +463,23 @@ __global__ void __launch_bounds__(256, MINB) segsum8_kernel(const uint2* __restr
                 segsum8_warp<NP, STEPS, 1, T>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK,
                                            vT, lane);
             if (vT)
-                segsum8_warp<NP, STEPS, 2, T>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK,
-                                           vT, lane);
+                segsum8_warp<NP, STEPS, 2, T, TF>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM,
+                                                  vK, vT, lane);
         } else {
-            segsum8_warp<NP, STEPS, 0, T>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK, vT,
-                                       lane);
+            segsum8_warp<NP, STEPS, 0, T, TF>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK,
+                                              vT, lane);
         }
     }
 }
 
-template <int NP, int STEPS, int MINB, bool SPLIT, typename T>
+template <int NP, int STEPS, int MINB, bool SPLIT, typename T, bool TF>
 int launch_steps8_b(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s,
                     int nsm, int64_t s0, int64_t s1) {
     static int occ = 0;   // blocks per SM (the same on every device of the pool)
     if (!occ) {
         int o = 0;
-        FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, segsum8_kernel<NP, STEPS, MINB, SPLIT, T>, 256, 0));
+        FEM_CUDA_TRY(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, segsum8_kernel<NP, STEPS, MINB, SPLIT, T, TF>, 256, 0));
         occ = o > 0 ? o : 1;
     }
     const int64_t nc = m.E * m.np * m.np;
@@ -472,7 +492,7 @@ int launch_steps8_b(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T*
     if (blocks > (int64_t)nsm * occ) blocks = (int64_t)nsm * occ;
     if (blocks < 1) blocks = 1;
     cudaGetLastError();   // clear any stale error before the launch check
-    segsum8_kernel<NP, STEPS, MINB, SPLIT, T><<<(unsigned)blocks, 256, 0, s>>>(
+    segsum8_kernel<NP, STEPS, MINB, SPLIT, T, TF><<<(unsigned)blocks, 256, 0, s>>>(
         m.seg_head.as<uint2>(), reinterpret_cast<const uint32_t*>(m.contrib.as<int>()), (uint32_t)nc,
         m.seg_ptr.as<int>(), (uint32_t)s0, (uint32_t)s1, (uint32_t)task, VM, VK, VT, vM, vK, vT);
     FEM_CUDA_TRY(cudaGetLastError());
@@ -490,7 +510,10 @@ int launch_steps8_b(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T*
 template <int NP, int STEPS, typename T>
 int launch_steps8(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s,
                   int nsm, int64_t s0, int64_t s1) {
-    return launch_steps8_b<NP, STEPS, 4, true, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+    if constexpr (NP == 3 || NP == 4) {
+        if (p1_t_factored(m)) return launch_steps8_b<NP, STEPS, 4, true, T, true>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+    }
+    return launch_steps8_b<NP, STEPS, 4, true, T, false>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
 }
 
 
@@ -531,9 +554,16 @@ __global__ void __launch_bounds__(256, batch_sum_blocks<T>())
             if (vM || vK)
                 segsum8_warp<NP, STEPS, 1, double>(k0, k1, nc, 0u, s1, bm.seg_head, cp, sym, VM, VK, VT, vM, vK, vT,
                                                    lane);
-            if (vT)
-                segsum8_warp<NP, STEPS, 2, double>(k0, k1, nc, 0u, s1, bm.seg_head, cp, sym, VM, VK, VT, vM, vK, vT,
-                                                   lane);
+            if (vT) {
+                bool tf = false;
+                if constexpr (NP == 3 || NP == 4) tf = bm.type == 0 || bm.type == 3;   // P1: T as factors
+                if (tf)
+                    segsum8_warp<NP, STEPS, 2, double, true>(k0, k1, nc, 0u, s1, bm.seg_head, cp, sym, VM, VK, VT, vM,
+                                                             vK, vT, lane);
+                else
+                    segsum8_warp<NP, STEPS, 2, double, false>(k0, k1, nc, 0u, s1, bm.seg_head, cp, sym, VM, VK, VT,
+                                                              vM, vK, vT, lane);
+            }
         } else {
             segsum_warp<NP, T, STEPS>(k0, k1, nc, 0u, s1, reinterpret_cast<const uint4*>(bm.seg_head), cp, sym, VM,
                                       VK, VT, vM, vK, vT, lane);
