@@ -343,11 +343,13 @@ def law_ops(kind: str, n: int):
 def fp64_element_ops(d: int, p: int, kind: str, n: int):
     """(FP64 operations, flops with a fused multiply-add counted as 2) per
     element of the FP64 element product, counted from the kernel's algorithm.
-    P1 (element_p1_fp64_kernel): M m b_e and its diagonal and off-diagonal
-    factors (3), du (d), per quadrature point u_q (d FMA), the law, s0 (1
-    FMA), w k' (1), s1 (n_p FMA); K: b s0 (1), column sums of A (d(d-1) + d-1
-    adds), n_sym products; T: A ghat (d + d(d-1) FMA), its sum (d-1),
-    b (G A ghat) (n_p); T_e's outer product is left to the CSR sum.  P2/P3 (element_simt_kernel): the product V = X Q
+    P1 (element_p1_fp64_kernel, whose degree-2 rules have one point per
+    vertex with equal weights): M m b_e and its diagonal and off-diagonal
+    factors (3), du (d), beta sum u (n_p), per point u_q (1 FMA) and the law,
+    s0 = w sum k (n_p), s1 = beta w sum k' + gamma w k'_j (2 n_p); K: b s0
+    (1), column sums of A (d(d-1) + d-1 adds), n_sym products; T: A ghat (d +
+    d(d-1) FMA), its sum (d-1), b (G A ghat) (n_p); T_e's outer product is
+    left to the CSR sum.  P2/P3 (element_simt_kernel): the product V = X Q
     (gemm_flops_per_element) plus, per point, u_q and ghat (n_p (1+d) FMA),
     A ghat (d^2 FMA) and the law."""
     lo, lf = law_ops(kind, n)
@@ -355,9 +357,9 @@ def fp64_element_ops(d: int, p: int, kind: str, n: int):
     n_q = {(2, 1): 3, (2, 2): 6, (2, 3): 12, (3, 1): 4, (3, 2): 11, (3, 3): 24}[(d, p)]
     nsym = n_p * (n_p + 1) // 2
     if p == 1:
-        ops = 3 + d + n_q * (d + lo + 2 + n_p) + (1 + d * (d - 1) + (d - 1) + nsym) \
+        ops = 3 + d + n_p + n_p * (1 + lo) + n_p + 2 * n_p + (1 + d * (d - 1) + (d - 1) + nsym) \
             + (d + d * (d - 1) + (d - 1) + n_p)
-        fma = n_q * (d + lf + 1 + n_p) + d * (d - 1)
+        fma = n_p * (1 + lf) + n_p + d * (d - 1)
         return ops, ops + fma
     gemm = gemm_flops_per_element(d, p)
     fma = n_q * (n_p * (1 + d) + d * d + lf)

@@ -9,6 +9,7 @@
 // Section 5.2 conductivity tensor with u in its second mode.  Only the
 // n_p(n_p+1)/2 distinct entries of the symmetric M and K are formed
 // (Section 7).  V is written element-major: V[e][n].
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <mutex>
@@ -57,6 +58,13 @@ constexpr int BT = 64;   // elements (threads) per block
 __constant__ double c_p1m[6 + 10];
 __constant__ double c_p1m2[4];
 __constant__ int c_p1m2_on[2];
+// A rule of n_p points, one per vertex, with equal weights w and basis
+// values phi_q[j] = beta + gamma [j = vertex of q] (the degree-2 rules of
+// both simplices): per simplex (beta, gamma, w, beta w, gamma w), used where
+// c_p1q_on is set.  Then u at the point of vertex j is beta sum_i u_i +
+// gamma u_j, and the sums over the points need no products by the basis.
+__constant__ double c_p1q[10];
+__constant__ int c_p1q_on[2];
 __device__ double2 g_sincos_tab[SC_TAB];
 
 // nodal values: FP64 as given; the FP32 path splits each gathered value
@@ -250,27 +258,54 @@ __device__ __forceinline__ void p1_element_fp64(int64_t e, const int* __restrict
 #pragma unroll
     for (int t = 0; t < NS; ++t) A[t] = geo[(1 + t) * gs + e];
     const int* ce = conn + e * NP;
-    const double u0 = u[ce[0]];
-    double du[NP];
+    double uv[NP], du[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) uv[i] = u[ce[i]];
+    const double u0 = uv[0];
     du[0] = 0.0;
 #pragma unroll
-    for (int i = 1; i < NP; ++i) du[i] = u[ce[i]] - u0;
+    for (int i = 1; i < NP; ++i) du[i] = uv[i] - u0;
     // sums over the quadrature points: s0 = sum w k(u_q), s1[j] = sum w k'(u_q) phi_q[j]
     double s0 = 0.0, s1[NP];
+    if (NQ == NP && c_p1q_on[D - 2]) {
+        // one point per vertex, equal weights (taken per vertex, so the
+        // points' order does not matter): s0 = w sum k, s1[j] = beta w sum k'
+        // + gamma w k'(point of vertex j)
+        const double* cq = c_p1q + 5 * (D - 2);
+        const double be = cq[0], ga = cq[1], w = cq[2], bw = cq[3], gw = cq[4];
+        double su = uv[0];
 #pragma unroll
-    for (int j = 0; j < NP; ++j) s1[j] = 0.0;
+        for (int i = 1; i < NP; ++i) su += uv[i];
+        const double bsu = be * su;
+        double kq[NP], dkq[NP];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        double uq = u0;
+        for (int j = 0; j < NP; ++j) kq[j] = law64<LAW>(k, fma(ga, uv[j], bsu), dkq[j], tab);
+        double sk = kq[0], sd = dkq[0];
 #pragma unroll
-        for (int i = 1; i < NP; ++i) uq = fma(c_ref64[PHI + q * NP + i], du[i], uq);
-        double dk;
-        const double kq = law64<LAW>(k, uq, dk, tab);
-        const double w = c_ref64[WQ + q];
-        s0 = fma(w, kq, s0);
-        const double wd = w * dk;
+        for (int j = 1; j < NP; ++j) {
+            sk += kq[j];
+            sd += dkq[j];
+        }
+        s0 = w * sk;
+        const double bws = bw * sd;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) s1[j] = fma(wd, c_ref64[PHI + q * NP + j], s1[j]);
+        for (int j = 0; j < NP; ++j) s1[j] = fma(gw, dkq[j], bws);
+    } else {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) s1[j] = 0.0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double uq = u0;
+#pragma unroll
+            for (int i = 1; i < NP; ++i) uq = fma(c_ref64[PHI + q * NP + i], du[i], uq);
+            double dk;
+            const double kq = law64<LAW>(k, uq, dk, tab);
+            const double w = c_ref64[WQ + q];
+            s0 = fma(w, kq, s0);
+            const double wd = w * dk;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) s1[j] = fma(wd, c_ref64[PHI + q * NP + j], s1[j]);
+        }
     }
     auto At = [&](int a, int c) {   // A[a][c] from the upper triangle
         const int lo = a < c ? a : c, hi = a < c ? c : a;
@@ -782,6 +817,48 @@ int tables_init_simt() {
         p1m2_on[c] = same ? 1 : 0;
     }
     FEM_CUDA_TRY(cudaMemcpyToSymbol(c_p1m2, p1m2, sizeof(p1m2)));
+    // rules of one point per vertex: every point has the basis value
+    // beta + gamma at one vertex and beta at the others, each vertex has one
+    // point, and all weights are equal
+    double p1q[10] = {};
+    int p1q_on[2] = {0, 0};
+    for (int t : {0, 3}) {
+        const RefElem* R = refelem_for_type(t);
+        const int np = R->np, c = t == 0 ? 0 : 1;
+        if (R->nq != np) continue;
+        const double w = R->wq[0];
+        double al = R->phi[0], be = R->phi[0];
+        for (int j = 1; j < np; ++j) {
+            al = std::max(al, R->phi[j]);
+            be = std::min(be, R->phi[j]);
+        }
+        bool ok = al - be > 1e-3;
+        std::vector<int> hits(np, 0);
+        for (int q = 0; q < np && ok; ++q) {
+            ok = std::fabs(R->wq[q] - w) <= 4e-16 * std::fabs(w);
+            int nal = 0;
+            for (int j = 0; j < np; ++j) {
+                const double v = R->phi[q * np + j];
+                if (std::fabs(v - al) <= 4e-16 * std::fabs(al)) {
+                    ++nal;
+                    ++hits[j];
+                } else {
+                    ok = ok && std::fabs(v - be) <= 4e-16 * std::fabs(be);
+                }
+            }
+            ok = ok && nal == 1;
+        }
+        for (int j = 0; j < np; ++j) ok = ok && hits[j] == 1;
+        if (!ok) continue;
+        p1q[5 * c] = be;
+        p1q[5 * c + 1] = al - be;
+        p1q[5 * c + 2] = w;
+        p1q[5 * c + 3] = be * w;
+        p1q[5 * c + 4] = (al - be) * w;
+        p1q_on[c] = 1;
+    }
+    FEM_CUDA_TRY(cudaMemcpyToSymbol(c_p1q, p1q, sizeof(p1q)));
+    FEM_CUDA_TRY(cudaMemcpyToSymbol(c_p1q_on, p1q_on, sizeof(p1q_on)));
     FEM_CUDA_TRY(cudaMemcpyToSymbol(c_p1m2_on, p1m2_on, sizeof(p1m2_on)));
     FEM_CUDA_TRY(cudaMemcpyToSymbol(g_sincos_tab, sct.data(), sizeof(double2) * SC_TAB));
     std::vector<float> ref32(ref64.begin(), ref64.end()), q32(q64.begin(), q64.end());
