@@ -346,10 +346,10 @@ def fp64_element_ops(d: int, p: int, kind: str, n: int):
     P1 (element_p1_fp64_kernel, whose degree-2 rules have one point per
     vertex with equal weights): M m b_e and its diagonal and off-diagonal
     factors (3), du (d), beta sum u (n_p), per point u_q (1 FMA) and the law,
-    s0 = w sum k (n_p), s1 = beta w sum k' + gamma w k'_j (2 n_p); K: b s0
-    (1), column sums of A (d(d-1) + d-1 adds), n_sym products; T: A ghat (d +
-    d(d-1) FMA), its sum (d-1), b (G A ghat) (n_p); T_e's outer product is
-    left to the CSR sum.  P2/P3 (element_simt_kernel): the product V = X Q
+    s0 = w sum k (n_p), s1 = beta w sum k' + gamma w k'_j (2 n_p); K: its
+    factor b s0 (1; the Gram matrix is cached per mesh); T: A ghat (d +
+    d(d-1) FMA), its sum (d-1), b (G A ghat) (n_p); the products of K's and
+    T's factors are left to the CSR sum.  P2/P3 (element_simt_kernel): the product V = X Q
     (gemm_flops_per_element) plus, per point, u_q and ghat (n_p (1+d) FMA),
     A ghat (d^2 FMA) and the law."""
     lo, lf = law_ops(kind, n)
@@ -357,8 +357,7 @@ def fp64_element_ops(d: int, p: int, kind: str, n: int):
     n_q = {(2, 1): 3, (2, 2): 6, (2, 3): 12, (3, 1): 4, (3, 2): 11, (3, 3): 24}[(d, p)]
     nsym = n_p * (n_p + 1) // 2
     if p == 1:
-        ops = 3 + d + n_p + n_p * (1 + lo) + n_p + 2 * n_p + (1 + d * (d - 1) + (d - 1) + nsym) \
-            + (d + d * (d - 1) + (d - 1) + n_p)
+        ops = 3 + d + n_p + n_p * (1 + lo) + n_p + 2 * n_p + 1 + (d + d * (d - 1) + (d - 1) + n_p)
         fma = n_p * (1 + lf) + n_p + d * (d - 1)
         return ops, ops + fma
     gemm = gemm_flops_per_element(d, p)
@@ -626,22 +625,22 @@ def measure_sweep(F, torch, stream, name, precs=("tf32x3", "fp64"), nsweep=10, w
     return out
 
 
-def phase_bytes(mesh, nnz: int, esz: int, t_factored: bool = False):
+def phase_bytes(mesh, nnz: int, esz: int, p1_factored: bool = False):
     """Algorithmic bytes of one reassembly of M, K, T: (element phase, CSR sum).
     Element phase: connectivity (4 B per node of an element), the geometry
     cache (b and the d(d+1)/2 entries of A), V written (2 n_sym + n_p^2
-    values, or 2 n_sym + 2 n_p where T_e is stored as its two factors: P1 in
-    FP64), u read once.  CSR sum: an 8-byte head word per group of 32
-    contributions, every contribution's 4-byte index and V entries, the CSR
-    values written."""
+    values; for P1 in FP64 the factored form, 4 + 2 n_p values), u read once.
+    CSR sum: an 8-byte head word per group of 32 contributions, every
+    contribution's 4-byte index and V entries (for P1 in FP64 also the n_sym
+    entries of each element's cached Gram matrix), the CSR values written."""
     d, E, n = mesh.d, mesh.n_elems, mesh.n_nodes
     n_p = mesh.conn.shape[1]
-    nsym, nt, ngeo = n_p * (n_p + 1) // 2, n_p * n_p, 1 + d * (d + 1) // 2
-    if t_factored:
-        nt = 2 * n_p
+    nsym, ngeo = n_p * (n_p + 1) // 2, 1 + d * (d + 1) // 2
+    nv = 4 + 2 * n_p if p1_factored else 2 * nsym + n_p * n_p
+    gram = nsym if p1_factored else 0
     nc = E * n_p * n_p
-    form = E * (n_p * 4 + ngeo * esz + (2 * nsym + nt) * esz) + n * 8
-    summ = (nc + 31) // 32 * 8 + nc * 4 + E * (2 * nsym + nt) * esz + 3 * nnz * esz
+    form = E * (n_p * 4 + ngeo * esz + nv * esz) + n * 8
+    summ = (nc + 31) // 32 * 8 + nc * 4 + E * (nv + gram) * esz + 3 * nnz * esz
     return form, summ
 
 
@@ -1062,8 +1061,8 @@ def run_ours(args, rank, world, local_rank):
     esz = 8 if args.prec == "fp64" else 4
     n = wl.mesh.n_nodes
     nc = E * n_p * n_p
-    t_fac = args.prec == "fp64" and p == 1   # P1 in FP64: T_e stored as its two factors
-    bytes_form, bytes_sum = phase_bytes(wl.mesh, nnz, esz, t_fac)
+    p1f = args.prec == "fp64" and p == 1   # P1 in FP64: factored element matrices
+    bytes_form, bytes_sum = phase_bytes(wl.mesh, nnz, esz, p1f)
     mf, msum = statistics.mean(form_ms), statistics.mean(sum_ms)
     on_tc = args.prec in ("tf32x3", "bf16x3", "bf16x6")
     fp64 = args.prec == "fp64"
@@ -1074,13 +1073,13 @@ def run_ours(args, rank, world, local_rank):
     kernels = {
         "element_form": {"kernel": form_kernel, "src": "element_tc.cu" if on_tc else "element_simt.cu",
                          "ms": mf, "bytes": bytes_form, "flops": flops * E, "fp64_ops": ops * E},
-        # FP64 sum: the additions of M and K (nc - nnz each) and of T, whose
-        # contributions are products of T_e's factors where those are stored
-        # (nc multiplications fused with nc - nnz additions)
+        # FP64 sum: the additions of M, K and T (nc - nnz each); where the
+        # element matrices are factored (P1), K's and T's contributions are
+        # products, fused with the additions (nc operations, 2 nc - nnz flops each)
         "csr_sum": {"kernel": "segsum8_kernel" if fp64 else "segsum_kernel", "src": "scatter.cu", "ms": msum,
                     "bytes": bytes_sum,
-                    "flops": (2 * (nc - nnz) + (2 * nc - nnz if t_fac else nc - nnz)) if fp64 else 0,
-                    "fp64_ops": (2 * (nc - nnz) + (nc if t_fac else nc - nnz)) if fp64 else 0},
+                    "flops": ((nc - nnz) + 2 * (2 * nc - nnz) if p1f else 3 * (nc - nnz)) if fp64 else 0,
+                    "fp64_ops": ((nc - nnz) + 2 * nc if p1f else 3 * (nc - nnz)) if fp64 else 0},
     }
     phases = {}
     for name, kd in kernels.items():

@@ -264,6 +264,7 @@ int fem_batch_create(fem_mesh* const* meshes, int n, const fem_batch_opts* opts,
         h.conn = m->conn.as<int>();
         h.geo32 = m->geo32.as<float>();
         h.geo64 = m->geo64.as<double>();
+        h.gram64 = m->gram64.as<double>();
         h.E = m->E;
         h.n = m->n;
         h.nnz = m->nnz;

@@ -182,12 +182,16 @@ int form_t(fem_mesh* m, const fem_coeff* k, const double* ud, int prec, int mask
 }
 
 // Global assembly (the last step of Algorithm 2) of the formed V into CSR values.
+// plain: the M/K scratch holds M/K pairs per symmetric entry whatever the
+// element type (the u-dependent mass); otherwise it holds what the element
+// kernels formed (factored for P1 simplices in FP64).
 template <typename T>
-int sum_t(fem_mesh* m, T* vM, T* vK, T* vT, cudaStream_t s, int64_t s0 = 0, int64_t s1 = -1) {
+int sum_t(fem_mesh* m, T* vM, T* vK, T* vT, cudaStream_t s, int64_t s0 = 0, int64_t s1 = -1, bool plain = false) {
     const T* VM = vM ? m->VMK.as<T>() : nullptr;
     const T* VK = vK ? m->VMK.as<T>() + 1 : nullptr;
     const T* VT = vT ? m->VT.as<T>() : nullptr;
-    if constexpr (sizeof(T) == 8) return scatter_fp64(*m, VM, VK, VT, vM, vK, vT, s, s0, s1);
+    if constexpr (sizeof(T) == 8)
+        return scatter_fp64(*m, VM, VK, VT, vM, vK, vT, !plain && p1_factored(*m), s, s0, s1);
     else return scatter_fp32(*m, VM, VK, VT, vM, vK, vT, s, s0, s1);
 }
 
@@ -348,7 +352,7 @@ CoeffDev coeff_to_device(const fem_coeff* k) { return to_dev(k); }
 }  // namespace fem
 
 size_t fem_mesh::device_bytes() const {
-    const fem::DevBuf* bufs[] = {&coords, &conn, &geo64, &geo32, &row_ptr, &col_idx, &seg_ptr, &contrib, &slot,
+    const fem::DevBuf* bufs[] = {&coords, &conn, &geo64, &geo32, &gram64, &row_ptr, &col_idx, &seg_ptr, &contrib, &slot,
                                  &seg_head, &inc_ptr, &inc, &VMK, &VT, &u_stage, &out_stage, &bfacet, &bnode_ptr,
                                  &bnode_inc, &bscratch, &npart, &cfield, &geoq64, &geoq32, &solve, &newton};
     size_t t = 0;
@@ -442,7 +446,7 @@ int fem_mesh_create(const fem_mesh_desc* desc, void* stream, fem_mesh** out) {
 int fem_mesh_destroy(fem_mesh* m) {
     if (!m) return FEM_OK;
     cudaDeviceSynchronize();
-    fem::DevBuf* bufs[] = {&m->coords, &m->conn, &m->geo64, &m->geo32, &m->row_ptr, &m->col_idx, &m->seg_ptr,
+    fem::DevBuf* bufs[] = {&m->coords, &m->conn, &m->geo64, &m->geo32, &m->gram64, &m->row_ptr, &m->col_idx, &m->seg_ptr,
                            &m->contrib, &m->slot, &m->seg_head, &m->inc_ptr, &m->inc, &m->VMK, &m->VT, &m->u_stage,
                            &m->out_stage, &m->bfacet, &m->bnode_ptr, &m->bnode_inc, &m->bscratch, &m->npart, &m->cfield, &m->geoq64, &m->geoq32, &m->solve,
                            &m->newton};
@@ -628,7 +632,7 @@ int fem_assemble_mass_u(fem_mesh* m, const fem_coeff* mk, const void* d_u, const
     if (rc) return rc;
     // M(u) from the even, the tensor term from the odd positions
     if (prec == FEM_FP64)
-        return sum_t<double>(m, static_cast<double*>(d_vMu), static_cast<double*>(d_vMt), nullptr, s);
+        return sum_t<double>(m, static_cast<double*>(d_vMu), static_cast<double*>(d_vMt), nullptr, s, 0, -1, true);
     return sum_t<float>(m, static_cast<float*>(d_vMu), static_cast<float*>(d_vMt), nullptr, s);
 }
 

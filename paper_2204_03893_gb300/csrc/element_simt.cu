@@ -50,14 +50,11 @@ struct Tabs<float> {
 
 constexpr int BT = 64;   // elements (threads) per block
 
-// FP64 P1 tables: the mass factor sum_q w_q phi_q[i] phi_q[j] (n_sym values,
-// triangles then tetrahedra) and the sine table of law64.cuh.  With a rule
-// that treats the vertices alike the factor takes one value on the diagonal
-// and one off it: c_p1m2 = (diagonal, off-diagonal) for triangles, then
-// tetrahedra, used where c_p1m2_on is set.
-__constant__ double c_p1m[6 + 10];
+// FP64 P1 tables: the mass factor sum_q w_q phi_q[i] phi_q[j], which the
+// rules (all symmetric in the vertices) make one value on the diagonal and
+// one off it: c_p1m2 = (diagonal, off-diagonal) for triangles, then
+// tetrahedra (checked at set-up); and the sine table of law64.cuh.
 __constant__ double c_p1m2[4];
-__constant__ int c_p1m2_on[2];
 // A rule of n_p points, one per vertex, with equal weights w and basis
 // values phi_q[j] = beta + gamma [j = vertex of q] (the degree-2 rules of
 // both simplices): per simplex (beta, gamma, w, beta w, gamma w), used where
@@ -213,23 +210,26 @@ __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict_
 //     K_e = b_e (sum_q w_q k(u_q)) G A_e G^T,
 //     T_e[i][j] = b_e (G A_e ghat)_i (sum_q w_q k'(u_q) phi_q[j]),
 //     M_e = m b_e sum_q w_q phi_q phi_q^T,
-// T_e is the outer product of two vectors of n_p values, and is stored as
-// those two factors (t_e = b_e G A_e ghat, then s_e with s_e[j] = sum_q w_q
-// k'(u_q) phi_q[j]): the CSR sum multiplies them as it adds (one fused
-// multiply-add per contribution, where the outer product would cost the
-// element n_p^2 multiplications).  M_e takes two multiplications when the
-// rule treats the vertices alike (one value on the diagonal, one off it).
-// with ghat = G^T u_e = (u_1 - u_0, ..., u_d - u_0).  G A G^T needs no
-// multiplications: its (i, j) entry for i, j >= 1 is A[i-1][j-1], its (0, j)
-// entry minus the (j-1)-th column sum of A, its (0, 0) entry the sum of all
-// of A.  This is the same quadrature sum as the general path, regrouped:
-// tetrahedra need ~110 FP64 operations per element (polynomial law) instead
-// of ~780 for the general product, which matters because the FP64 pipe, not
-// HBM, bounds the FP64 path on this part.
+// with ghat = G^T u_e = (u_1 - u_0, ..., u_d - u_0).  This is the same
+// quadrature sum as the general path, regrouped, and every matrix is stored
+// factored, for the CSR sum to multiply out as it adds (one fused
+// multiply-add per contribution in place of its addition):
+//   - K_e as its scalar factor b_e sum_q w_q k(u_q): the Gram matrix
+//     G A_e G^T does not change with u and is kept per mesh (geometry.cu);
+//   - T_e, an outer product, as its two factors t_e = b_e G A_e ghat and
+//     s_e with s_e[j] = sum_q w_q k'(u_q) phi_q[j];
+//   - M_e as its diagonal and off-diagonal value (the rules are symmetric in
+//     the vertices, so sum_q w_q phi_q phi_q^T takes only these two).
+// Tetrahedra need 122 FP64 operations per element with the sine law
+// (mostly the law at four points) against ~780 for the general product,
+// which matters because the FP64 pipe, not HBM, bounds the FP64 path on
+// this part.
 //
-// The element's rows are written through `mk` (2 n_sym values: M at even, K
-// at odd positions) and `tr` (2 n_p values: the factors of T_e), which point
-// into shared memory in the single-mesh kernel and into V in the batched one.
+// The element's values are written through `mk` (4 values: M's diagonal
+// value, K's factor, M's off-diagonal value, K's factor again, so that the
+// sum reads the pair it needs with one 16-byte load) and `tr` (2 n_p values:
+// the factors of T_e), which point into shared memory in the single-mesh
+// kernel and into V in the batched one.
 template <int D, int LAW>
 __device__ __forceinline__ void p1_element_fp64(int64_t e, const int* __restrict__ conn, const double* __restrict__ geo,
                                                 int64_t gs, const double* __restrict__ u, const CoeffDev& k,
@@ -238,25 +238,18 @@ __device__ __forceinline__ void p1_element_fp64(int64_t e, const int* __restrict
     constexpr int NP = D + 1, NQ = D == 2 ? 3 : 4, NS = D * (D + 1) / 2;
     constexpr int TYPE = D == 2 ? 0 : 3;
     constexpr int PHI = type_tab_off(TYPE), WQ = PHI + NQ * NP * (1 + D);
-    constexpr int M0 = D == 2 ? 0 : 6;   // offset in c_p1m
     const double b = geo[e];
-    if (doM) {
+    if (doM) {   // M's diagonal and off-diagonal value
         const double mb = mass * b;
-        if (c_p1m2_on[D - 2]) {
-            const double md = mb * c_p1m2[2 * (D - 2)], mo = mb * c_p1m2[2 * (D - 2) + 1];
-#pragma unroll
-            for (int i = 0; i < NP; ++i)
-#pragma unroll
-                for (int j = i; j < NP; ++j) mk[2 * sym_index(NP, i, j)] = i == j ? md : mo;
-        } else {
-#pragma unroll
-            for (int t = 0; t < NP * (NP + 1) / 2; ++t) mk[2 * t] = mb * c_p1m[M0 + t];
-        }
+        mk[0] = mb * c_p1m2[2 * (D - 2)];
+        mk[2] = mb * c_p1m2[2 * (D - 2) + 1];
     }
     if (!doK && !doT) return;
     double A[NS];
+    if (doT) {
 #pragma unroll
-    for (int t = 0; t < NS; ++t) A[t] = geo[(1 + t) * gs + e];
+        for (int t = 0; t < NS; ++t) A[t] = geo[(1 + t) * gs + e];
+    }
     const int* ce = conn + e * NP;
     double uv[NP], du[NP];
 #pragma unroll
@@ -311,25 +304,10 @@ __device__ __forceinline__ void p1_element_fp64(int64_t e, const int* __restrict
         const int lo = a < c ? a : c, hi = a < c ? c : a;
         return A[lo * D - (lo * (lo - 1)) / 2 + (hi - lo)];
     };
-    if (doK) {
+    if (doK) {   // K's factor (its Gram matrix G A_e G^T is cached per mesh)
         const double bs = b * s0;
-        double cs[D];   // column sums of A
-        double tot = 0.0;
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            double v = At(0, c);
-#pragma unroll
-            for (int a = 1; a < D; ++a) v += At(a, c);
-            cs[c] = v;
-            tot = c == 0 ? v : tot + v;
-        }
-        mk[1] = bs * tot;   // sym(0, 0) = 0
-#pragma unroll
-        for (int j = 1; j < NP; ++j) mk[2 * j + 1] = -(bs * cs[j - 1]);   // sym(0, j) = j
-#pragma unroll
-        for (int i = 1; i < NP; ++i)
-#pragma unroll
-            for (int j = i; j < NP; ++j) mk[2 * sym_index(NP, i, j) + 1] = bs * At(i - 1, j - 1);
+        mk[1] = bs;
+        mk[3] = bs;
     }
     if (doT) {
         double r[D];   // A ghat
@@ -357,7 +335,7 @@ __device__ __forceinline__ void p1_element_fp64(int64_t e, const int* __restrict
 constexpr int P1_BT = 128;   // elements (threads) per block of the FP64 P1 kernel
 
 template <int D>
-__host__ __device__ constexpr int p1_ldmk() { return (D + 1) * (D + 2) | 1; }   // 2 n_sym, odd
+__host__ __device__ constexpr int p1_ldmk() { return 5; }   // the 4-value M/K block, odd
 template <int D>
 __host__ __device__ constexpr int p1_ldt() { return 2 * (D + 1) | 1; }   // the two factors of T_e, odd
 
@@ -396,17 +374,17 @@ __global__ void __launch_bounds__(P1_BT) element_p1_fp64_kernel(const int* __res
         __syncthreads();
         const int rows = E - e0 < P1_BT ? (int)(E - e0) : P1_BT;
         if (doM || doK) {
-            double* g = VMK + 2 * e0 * NSYM;   // the block's rows, contiguous
+            double* g = VMK + 4 * e0;   // the block's M/K blocks (two pairs each), contiguous
             if (doM && doK) {
                 double2* g2 = reinterpret_cast<double2*>(g);
-                for (int i = threadIdx.x; i < rows * NSYM; i += P1_BT) {
-                    const double* r = sMK + (i / NSYM) * LDMK + 2 * (i % NSYM);
+                for (int i = threadIdx.x; i < rows * 2; i += P1_BT) {
+                    const double* r = sMK + (i / 2) * LDMK + 2 * (i % 2);
                     g2[i] = make_double2(r[0], r[1]);
                 }
             } else {
                 const int o = doM ? 0 : 1;
-                for (int i = threadIdx.x; i < rows * NSYM; i += P1_BT)
-                    g[2 * i + o] = sMK[(i / NSYM) * LDMK + 2 * (i % NSYM) + o];
+                for (int i = threadIdx.x; i < rows * 2; i += P1_BT)
+                    g[2 * i + o] = sMK[(i / 2) * LDMK + 2 * (i % 2) + o];
             }
         }
         if (doT) {
@@ -434,7 +412,7 @@ int launch_p1_law(const fem_mesh& m, const CoeffDev& k, const double* u, const d
     constexpr int NP = D + 1;
     cudaGetLastError();   // clear any stale error before the launch check
     kern<<<(unsigned)grid, P1_BT, smem, s>>>(m.conn.as<int>() + e0 * NP, geo + e0, E, m.E, u, k, m.m,
-                                              VMK ? VMK + 2 * e0 * (NP * (NP + 1) / 2) : nullptr, doM, doK,
+                                              VMK ? VMK + 4 * e0 : nullptr, doM, doK,
                                               VT ? VT + e0 * 2 * NP : nullptr);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
@@ -515,8 +493,8 @@ __global__ void __launch_bounds__(BT) batch_simt_kernel(const BatchItem* __restr
             // FP64 P1: the same regrouped product as the single-mesh kernel
             // (same bits), rows written straight into V
             if (w.type == 0 || w.type == 3) {
-                const int nsym = w.type == 0 ? 6 : 10, ntf = w.type == 0 ? 6 : 8;   // ntf: T_e's factors
-                double* mk = (VM || VK) ? static_cast<double*>(bm.VM) + 2 * e * nsym : nullptr;
+                const int ntf = w.type == 0 ? 6 : 8;   // T_e's factors
+                double* mk = (VM || VK) ? static_cast<double*>(bm.VM) + 4 * e : nullptr;   // the M/K block
                 double* tr = VT ? VT + e * ntf : nullptr;
                 if (w.type == 0)
                     p1_element_fp64_any<2>(bm.k, e, bm.conn, geo, bm.E, u, mass, VM != nullptr, VK != nullptr, mk, tr);
@@ -798,11 +776,9 @@ int tables_init_simt() {
         sct[k] = q == 0 ? make_double2(sj, cj) : q == 1 ? make_double2(cj, -sj)
                : q == 2 ? make_double2(-sj, -cj) : make_double2(-cj, sj);
     }
-    FEM_CUDA_TRY(cudaMemcpyToSymbol(c_p1m, p1m, sizeof(p1m)));
-    // one diagonal and one off-diagonal value where every entry of each kind
-    // agrees to within rounding (a rule symmetric in the vertices)
+    // one diagonal and one off-diagonal value: every entry of each kind must
+    // agree to within rounding (rules symmetric in the vertices)
     double p1m2[4] = {};
-    int p1m2_on[2] = {0, 0};
     for (int t : {0, 3}) {
         const int np = t == 0 ? 3 : 4, o = t == 0 ? 0 : 6, c = t == 0 ? 0 : 1;
         const double dg = p1m[o + sym_index(np, 0, 0)], od = p1m[o + sym_index(np, 0, 1)];
@@ -810,11 +786,11 @@ int tables_init_simt() {
         for (int i = 0; i < np; ++i)
             for (int j = i; j < np; ++j) {
                 const double v = p1m[o + sym_index(np, i, j)], ref = i == j ? dg : od;
-                same = same && std::fabs(v - ref) <= 4e-16 * ref;
+                same = same && std::fabs(v - ref) <= 1e-14 * ref;
             }
+        if (!same) return fail(FEM_EINVAL, "P1 mass factors of the quadrature rule are not symmetric in the vertices");
         p1m2[2 * c] = dg;
         p1m2[2 * c + 1] = od;
-        p1m2_on[c] = same ? 1 : 0;
     }
     FEM_CUDA_TRY(cudaMemcpyToSymbol(c_p1m2, p1m2, sizeof(p1m2)));
     // rules of one point per vertex: every point has the basis value
@@ -859,7 +835,6 @@ int tables_init_simt() {
     }
     FEM_CUDA_TRY(cudaMemcpyToSymbol(c_p1q, p1q, sizeof(p1q)));
     FEM_CUDA_TRY(cudaMemcpyToSymbol(c_p1q_on, p1q_on, sizeof(p1q_on)));
-    FEM_CUDA_TRY(cudaMemcpyToSymbol(c_p1m2_on, p1m2_on, sizeof(p1m2_on)));
     FEM_CUDA_TRY(cudaMemcpyToSymbol(g_sincos_tab, sct.data(), sizeof(double2) * SC_TAB));
     std::vector<float> ref32(ref64.begin(), ref64.end()), q32(q64.begin(), q64.end());
     FEM_CUDA_TRY(cudaMemcpyToSymbol(c_ref64, ref64.data(), sizeof(double) * TAB_TOTAL));

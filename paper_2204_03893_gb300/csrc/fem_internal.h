@@ -53,6 +53,10 @@ struct fem_mesh {
     double m = 1.0;
     fem::DevBuf coords, conn;           // FP64 n x d, int32 E x np
     fem::DevBuf geo64, geo32;           // SoA [NGEO][E]: b_e, A_e upper triangle
+    // P1 simplices: the Gram matrix G A_e G^T of every element (n_sym FP64
+    // values per element, symmetric storage; G = the constant reference
+    // gradients), the u-independent part of K_e
+    fem::DevBuf gram64;
     int64_t n_flagged = 0;
     // constant conductivity tensor c (SPD; identity by default), stored
     // 3 x 3 row-major whatever d (entry (a, b) at 3a + b): A_e = B_e^-1 c B_e^-T
@@ -151,16 +155,20 @@ int element_mass_u_tc(const fem_mesh& m, const CoeffDev& mk, const double* u, co
 int element_tc_bf16(const fem_mesh& m, const CoeffDev& k, const double* u, float* VM, float* VK, float* VT,
                     int nparts, cudaStream_t s, int64_t e0 = 0, int64_t e1 = -1);
 
-// FP64 element matrices of P1 simplices (per-element geometry) hold T_e as
-// its two factors, 2 n_p values per element (element_simt.cu); the FP64 CSR
-// sums read them so.
-inline bool p1_t_factored(const fem_mesh& m) { return (m.type == 0 || m.type == 3) && !m.perq; }
+// The FP64 element kernel of P1 simplices (per-element geometry) stores
+// factored element matrices (element_simt.cu): per element 4 values (M's
+// diagonal and off-diagonal value, K's factor b s0 twice) at the start of
+// the M/K scratch, K_e = b s0 times the element's Gram matrix in gram64,
+// and T_e as its two factors (2 n_p values).
+inline bool p1_factored(const fem_mesh& m) { return (m.type == 0 || m.type == 3) && !m.perq; }
 
 // Segmented reduction of V into CSR values (outputs may be null).
+// p1f: V holds the factored P1 element matrices (only where p1_factored);
+// otherwise M/K pairs per symmetric entry and T's full entries.
 // s0, s1: slot range [s0, s1) (s1 = -1: to the end); outputs are the
 // whole CSR arrays.
 int scatter_fp64(const fem_mesh& m, const double* VM, const double* VK, const double* VT, double* vM, double* vK,
-                 double* vT, cudaStream_t s, int64_t s0 = 0, int64_t s1 = -1);
+                 double* vT, bool p1f, cudaStream_t s, int64_t s0 = 0, int64_t s1 = -1);
 int scatter_fp32(const fem_mesh& m, const float* VM, const float* VK, const float* VT, float* vM, float* vK,
                  float* vT, cudaStream_t s, int64_t s0 = 0, int64_t s1 = -1);
 
@@ -187,6 +195,7 @@ struct BatchMesh {
     double mass;
     void* VM; void* VK; void* VT;        // element-matrix scratch (FP32 or FP64): VM = the interleaved
                                          // M/K base, VK = VM + one value, VT
+    const double* gram64;                // P1: Gram matrices of the elements (see fem_mesh)
     const int* seg_ptr;
     const int* contrib;
     const uint2* seg_head;               // per group of 32 contributions (see fem_mesh)

@@ -8,6 +8,11 @@
 //
 // Output layout (structure of arrays, coalesced for one thread per element):
 //   geo[0*E + e] = b_e,  geo[(1+t)*E + e] = A_e[a][b] for the t-th (a<=b).
+// P1 simplices also keep the Gram matrix G A_e G^T of every element (G the
+// constant reference gradients [-1 ... -1; I]; element-major, n_sym FP64
+// values in symmetric storage): the part of K_e that does not change with u
+// (K_e = b_e (sum_q w_q k(u_q)) G A_e G^T, Section 4.2 with the point sum
+// taken first), so the FP64 element kernel forms only its scalar factor.
 // geo64: everything in FP64.  geo32: edge vectors in FP64 (the coordinates
 // are FP64 and nearby vertices cancel), det / inverse / A in FP32; elements
 // whose condition estimate kappa = ||B||_F^d / |det B| exceeds 1e3 are
@@ -262,6 +267,42 @@ int gq_tables_init(GqType& out) {
     return FEM_OK;
 }
 
+// G A G^T needs no multiplications: entry (i, j), i, j >= 1, is A[i-1][j-1];
+// entry (0, j) minus the (j-1)-th column sum of A; entry (0, 0) the sum of
+// all of A (the column sums added in order).
+template <int D>
+__global__ void __launch_bounds__(256) p1_gram_kernel(const double* __restrict__ geo, int64_t E,
+                                                      double* __restrict__ gram) {
+    constexpr int NP = D + 1, NSYM = NP * (NP + 1) / 2;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        double A[D * (D + 1) / 2];
+#pragma unroll
+        for (int t = 0; t < D * (D + 1) / 2; ++t) A[t] = geo[(1 + t) * E + e];
+        auto At = [&](int a, int c) {   // A[a][c] from the upper triangle
+            const int lo = a < c ? a : c, hi = a < c ? c : a;
+            return A[lo * D - (lo * (lo - 1)) / 2 + (hi - lo)];
+        };
+        double g[NSYM];
+        double tot = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            double v = At(0, c);
+#pragma unroll
+            for (int a = 1; a < D; ++a) v += At(a, c);
+            g[sym_index(NP, 0, c + 1)] = -v;
+            tot = c == 0 ? v : tot + v;
+        }
+        g[0] = tot;   // sym(0, 0) = 0
+#pragma unroll
+        for (int i = 1; i < NP; ++i)
+#pragma unroll
+            for (int j = i; j < NP; ++j) g[sym_index(NP, i, j)] = At(i - 1, j - 1);
+        double* o = gram + e * NSYM;
+#pragma unroll
+        for (int t = 0; t < NSYM; ++t) o[t] = g[t];
+    }
+}
+
 }  // namespace
 
 // The per-point cache of a mesh in per-point mode (isoparametric and/or a
@@ -330,6 +371,19 @@ int geometry_run(fem_mesh& m, cudaStream_t s) {
                                                                     m.n, m.geo64.as<double>(), m.geo32.as<float>(),
                                                                     cd, cnt.as<unsigned long long>());
         FEM_CUDA_TRY(cudaGetLastError());
+    }
+    if (m.type == 0 || m.type == 3) {   // P1: the elements' Gram matrices
+        const size_t nsym = (size_t)m.np * (m.np + 1) / 2;
+        if ((rc = buf_alloc(m.gram64, sizeof(double) * nsym * (size_t)(m.E > 0 ? m.E : 1), s))) return rc;
+        if (m.E > 0) {
+            int64_t blocks = (m.E + 255) / 256;
+            if (blocks > 152 * 64) blocks = 152 * 64;
+            if (m.d == 2)
+                p1_gram_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(m.geo64.as<double>(), m.E, m.gram64.as<double>());
+            else
+                p1_gram_kernel<3><<<(unsigned)blocks, 256, 0, s>>>(m.geo64.as<double>(), m.E, m.gram64.as<double>());
+            FEM_CUDA_TRY(cudaGetLastError());
+        }
     }
     unsigned long long h[4] = {0, 0, 0, 0};
     FEM_CUDA_TRY(cudaMemcpyAsync(h, cnt.ptr, sizeof(h), cudaMemcpyDeviceToHost, s));

@@ -109,5 +109,5 @@ extern "C" int fem_assemble_all_noalloc(fem_mesh* m, const fem_coeff* k, const d
     const CoeffDev kd = coeff_to_device(k);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if ((rc = element_simt_fp64(*m, kd, d_u, VM, VK, VT, s))) return rc;
-    return scatter_fp64(*m, VM, VK, VT, d_vM, d_vK, d_vT, s);
+    return scatter_fp64(*m, VM, VK, VT, d_vM, d_vK, d_vT, p1_factored(*m), s);
 }

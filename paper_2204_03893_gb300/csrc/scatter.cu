@@ -37,29 +37,45 @@ struct Pair<float> { using type = float2; };
 template <>
 struct Pair<double> { using type = double2; };
 
-// TF: T is stored as the two factors of each element's outer product
-// (P1 simplices in FP64: t_e then s_e, 2 n_p values per element), and a
-// contribution carries the pair (t_e[i], s_e[j]) whose product it adds.
-template <int NP, typename T, bool TF = false>
+// F: the element matrices of a P1 simplex in FP64 as the P1 kernel stores
+// them (element_simt.cu): per element the block (m_d, b s0, m_o, b s0) --
+// M's diagonal and off-diagonal value and K's factor, K_e = b s0 Gram_e
+// with the element's Gram matrix G A_e G^T from the geometry cache -- and
+// T_e as its two factors (t_e then s_e, 2 n_p values).  A contribution
+// then carries m, the pair (k, g) whose product is K's entry and the pair
+// (t, s) whose product is T's.
+template <int NP, typename T, bool F = false>
 struct Contribution {
-    T m, k, t, s;   // s: the second factor (TF only)
+    T m, k, t, s, g;   // s, g: the second factors (F only)
     // 32-bit unsigned index arithmetic (element entries, slots and V
     // offsets of a mesh are below 2^31)
     __device__ __forceinline__ void load(uint32_t c, const short* __restrict__ sym, const T* __restrict__ VM,
-                                         const T* __restrict__ VK, const T* __restrict__ VT) {
+                                         const T* __restrict__ VK, const T* __restrict__ VT,
+                                         const T* __restrict__ gram) {
         constexpr uint32_t NT = NP * NP, NSYM = NP * (NP + 1) / 2;
-        if constexpr (TF) {
+        if constexpr (F) {
+            const uint32_t e = c / NT, l = c - e * NT;
             if (VT) {
-                const uint32_t e = c / NT, l = c - e * NT;
                 const T* f = VT + e * (2 * NP);
                 t = __ldg(f + l / NP);
                 s = __ldg(f + NP + l % NP);
             } else {
                 t = s = T(0);
             }
-        } else {
-            t = VT ? __ldg(VT + c) : T(0);
+            if (VM || VK) {
+                const T* base = VM ? VM : VK - 1;
+                const uint32_t i = l / NP, j = l - i * NP;
+                const typename Pair<T>::type mb =
+                    __ldg(reinterpret_cast<const typename Pair<T>::type*>(base) + 2 * e + (i == j ? 0u : 1u));
+                m = VM ? mb.x : T(0);
+                k = VK ? mb.y : T(0);
+                g = VK ? __ldg(gram + e * NSYM + (uint32_t)sym[l]) : T(0);
+            } else {
+                m = k = g = T(0);
+            }
+            return;
         }
+        t = VT ? __ldg(VT + c) : T(0);
         if (VM || VK) {
             const uint32_t e = c / NT;
             const uint32_t off = e * NSYM + (uint32_t)sym[c - e * NT];
@@ -155,8 +171,8 @@ __device__ __forceinline__ void segsum_warp(uint32_t k0, uint32_t k1, uint32_t n
     Contribution<NP, T> a0, b0;
     {
         const uint2 c = cpair(k0);
-        a0.load(c.x, sym, VM, VK, VT);
-        b0.load(c.y, sym, VM, VK, VT);
+        a0.load(c.x, sym, VM, VK, VT, nullptr);
+        b0.load(c.y, sym, VM, VK, VT, nullptr);
     }
     uint2 c1 = cpair(k0 + 1);
     uint32_t lo;   // first owned position of the pair group
@@ -171,8 +187,8 @@ __device__ __forceinline__ void segsum_warp(uint32_t k0, uint32_t k1, uint32_t n
         // groups further on are loaded when the carry actually reaches them
         Contribution<NP, T> a1, b1;
         if (k + 1 <= k1) {
-            a1.load(c1.x, sym, VM, VK, VT);
-            b1.load(c1.y, sym, VM, VK, VT);
+            a1.load(c1.x, sym, VM, VK, VT, nullptr);
+            b1.load(c1.y, sym, VM, VK, VT, nullptr);
         }
         const uint4 h2 = hword(k + 2);
         const uint2 c2 = k + 2 <= k1 ? cpair(k + 2) : make_uint2(0u, 0u);
@@ -237,8 +253,8 @@ __device__ __forceinline__ void segsum_warp(uint32_t k0, uint32_t k1, uint32_t n
             b0 = b1;
         } else {   // the carry runs past the prefetched continuation group
             const uint2 c = cpair(k + 1);
-            a0.load(c.x, sym, VM, VK, VT);
-            b0.load(c.y, sym, VM, VK, VT);
+            a0.load(c.x, sym, VM, VK, VT, nullptr);
+            b0.load(c.y, sym, VM, VK, VT, nullptr);
         }
         c1 = c2;
     }
@@ -275,14 +291,15 @@ __device__ __forceinline__ void segsum_warp(uint32_t k0, uint32_t k1, uint32_t n
 // interleaved pairs), 2 T; the split form runs a task twice with fewer
 // values live per lane (more resident warps).  The additions per matrix are
 // the same in every form, so are the bits.
-// TF: T held as per-element factors (see Contribution); each T
+// F: the P1 factored element matrices (see Contribution); each K and T
 // contribution is added as a fused multiply-add of its two factors.
-template <int NP, int STEPS, int PART, typename T, bool TF = false>
+template <int NP, int STEPS, int PART, typename T, bool F = false, int LAF = 4>
 __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t nc, uint32_t s0, uint32_t s1,
                                              const uint2* __restrict__ head, const uint32_t* __restrict__ contrib,
                                              const short* __restrict__ sym, const T* __restrict__ VM,
                                              const T* __restrict__ VK, const T* __restrict__ VT,
-                                             T* __restrict__ vM, T* __restrict__ vK, T* __restrict__ vT, int lane) {
+                                             const T* __restrict__ gram, T* __restrict__ vM, T* __restrict__ vK,
+                                             T* __restrict__ vT, int lane) {
     constexpr bool MK = PART != 2, TT = PART != 1;
     if constexpr (!MK) { VM = VK = nullptr; vM = vK = nullptr; }
     if constexpr (!TT) { VT = nullptr; vT = nullptr; }
@@ -317,22 +334,28 @@ __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t 
 #pragma unroll
             for (int i = 0; i < 8; ++i) c[i] = p0 + i < nc ? __ldg(contrib + p0 + i) : 0u;
         }
-        Contribution<NP, T, TF> v[8];
+        // the lane's V entries: all eight in flight at once, or, for the
+        // factored M/K pass (three values per entry), four at a time, each
+        // next one issued as the oldest is added (64 registers either way)
+        constexpr int LA = (F && MK) ? LAF : 8;
+        Contribution<NP, T, F> v[8];
+        auto fetch = [&](int i) {
+            if (p0 + i < nc) v[i].load(c[i], sym, VM, VK, VT, gram);
+            else v[i].m = v[i].k = v[i].t = v[i].s = v[i].g = T(0);
+        };
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (p0 + i < nc) v[i].load(c[i], sym, VM, VK, VT);
-            else v[i].m = v[i].k = v[i].t = v[i].s = T(0);
-        }
+        for (int i = 0; i < LA; ++i) fetch(i);
         auto own = [&](uint32_t sl) { return live && sl >= slo && sl < shi; };
         // in-lane pass: a* = the open piece, p* = the piece before the first head
         const bool h0 = bits & 1u;
         T am = T(0), ak = T(0), at = T(0), pm = T(0), pk = T(0), pt = T(0);
-        if constexpr (MK) { am = v[0].m; ak = v[0].k; }
-        if constexpr (TT) at = TF ? v[0].t * v[0].s : v[0].t;
+        if constexpr (MK) { am = v[0].m; ak = F ? v[0].k * v[0].g : v[0].k; }
+        if constexpr (TT) at = F ? v[0].t * v[0].s : v[0].t;
         bool seen = h0;
         uint32_t cur = slot0;   // slot of the open piece once a head was seen
 #pragma unroll
         for (int i = 1; i < 8; ++i) {
+            if (i + LA - 1 < 8 && i + LA - 1 >= LA) fetch(i + LA - 1);
             const bool h = (bits >> i) & 1u;
             if (h && seen && own(cur)) put3(cur, am, ak, at, vM, vK, vT);   // a slot complete in the lane
             if (h && !seen) {
@@ -343,10 +366,11 @@ __device__ __forceinline__ void segsum8_warp(uint32_t k0, uint32_t k1, uint32_t 
             seen = seen || h;
             if constexpr (MK) {
                 am = h ? v[i].m : am + v[i].m;
-                ak = h ? v[i].k : ak + v[i].k;
+                if constexpr (F) ak = fma(v[i].k, v[i].g, h ? T(0) : ak);
+                else ak = h ? v[i].k : ak + v[i].k;
             }
             if constexpr (TT) {
-                if constexpr (TF) at = fma(v[i].t, v[i].s, h ? T(0) : at);
+                if constexpr (F) at = fma(v[i].t, v[i].s, h ? T(0) : at);
                 else at = h ? v[i].t : at + v[i].t;
             }
         }
@@ -439,13 +463,14 @@ __global__ void __launch_bounds__(256, SegShape<STEPS, T>::MIN_BLOCKS)
 // to TASK8 steps grid-stride
 constexpr uint32_t TASK8 = 8;
 
-template <int NP, int STEPS, int MINB, bool SPLIT, typename T, bool TF>
+template <int NP, int STEPS, int MINB, bool SPLIT, typename T, bool F>
 __global__ void __launch_bounds__(256, MINB) segsum8_kernel(const uint2* __restrict__ head,
                                                       const uint32_t* __restrict__ contrib, uint32_t nc,
                                                       const int* __restrict__ seg_ptr, uint32_t s0, uint32_t s1,
                                                       uint32_t task, const T* __restrict__ VM,
                                                       const T* __restrict__ VK, const T* __restrict__ VT,
-                                                      T* __restrict__ vM, T* __restrict__ vK, T* __restrict__ vT) {
+                                                      const T* __restrict__ gram, T* __restrict__ vM,
+                                                      T* __restrict__ vK, T* __restrict__ vT) {
     __shared__ short sym[NP * NP];
     fill_sym_table<NP>(sym);
     __syncthreads();
@@ -460,26 +485,26 @@ __global__ void __launch_bounds__(256, MINB) segsum8_kernel(const uint2* __restr
         const uint32_t t1 = t + task < g1 ? t + task : g1;
         if constexpr (SPLIT) {
             if (vM || vK)
-                segsum8_warp<NP, STEPS, 1, T>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK,
-                                           vT, lane);
+                segsum8_warp<NP, STEPS, 1, T, F, (MINB >= 4 ? 4 : 8)>(t, t1, nc, s0, s1, head, contrib, sym, vm_src,
+                                                                      vk_src, vt_src, gram, vM, vK, vT, lane);
             if (vT)
-                segsum8_warp<NP, STEPS, 2, T, TF>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM,
-                                                  vK, vT, lane);
+                segsum8_warp<NP, STEPS, 2, T, F>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, gram,
+                                                 vM, vK, vT, lane);
         } else {
-            segsum8_warp<NP, STEPS, 0, T, TF>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, vM, vK,
-                                              vT, lane);
+            segsum8_warp<NP, STEPS, 0, T, F>(t, t1, nc, s0, s1, head, contrib, sym, vm_src, vk_src, vt_src, gram, vM,
+                                             vK, vT, lane);
         }
     }
 }
 
-template <int NP, int STEPS, int MINB, bool SPLIT, typename T, bool TF>
+template <int NP, int STEPS, int MINB, bool SPLIT, typename T, bool F>
 int launch_steps8_b(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s,
                     int nsm, int64_t s0, int64_t s1) {
     static int occ = 0;   // blocks per SM (the same on every device of the pool)
     if (!occ) {
         int o = 0;
         FEM_CUDA_TRY(
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, segsum8_kernel<NP, STEPS, MINB, SPLIT, T, TF>, 256, 0));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, segsum8_kernel<NP, STEPS, MINB, SPLIT, T, F>, 256, 0));
         occ = o > 0 ? o : 1;
     }
     const int64_t nc = m.E * m.np * m.np;
@@ -492,9 +517,10 @@ int launch_steps8_b(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T*
     if (blocks > (int64_t)nsm * occ) blocks = (int64_t)nsm * occ;
     if (blocks < 1) blocks = 1;
     cudaGetLastError();   // clear any stale error before the launch check
-    segsum8_kernel<NP, STEPS, MINB, SPLIT, T, TF><<<(unsigned)blocks, 256, 0, s>>>(
+    segsum8_kernel<NP, STEPS, MINB, SPLIT, T, F><<<(unsigned)blocks, 256, 0, s>>>(
         m.seg_head.as<uint2>(), reinterpret_cast<const uint32_t*>(m.contrib.as<int>()), (uint32_t)nc,
-        m.seg_ptr.as<int>(), (uint32_t)s0, (uint32_t)s1, (uint32_t)task, VM, VK, VT, vM, vK, vT);
+        m.seg_ptr.as<int>(), (uint32_t)s0, (uint32_t)s1, (uint32_t)task, VM, VK, VT,
+        F ? reinterpret_cast<const T*>(m.gram64.ptr) : nullptr, vM, vK, vT);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
@@ -509,9 +535,9 @@ int launch_steps8_b(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T*
 // for the single pass).  Every form adds the same terms in the same order.
 template <int NP, int STEPS, typename T>
 int launch_steps8(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s,
-                  int nsm, int64_t s0, int64_t s1) {
+                  int nsm, int64_t s0, int64_t s1, bool p1f) {
     if constexpr (NP == 3 || NP == 4) {
-        if (p1_t_factored(m)) return launch_steps8_b<NP, STEPS, 4, true, T, true>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+        if (p1f) return launch_steps8_b<NP, STEPS, 4, true, T, true>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
     }
     return launch_steps8_b<NP, STEPS, 4, true, T, false>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
 }
@@ -551,18 +577,23 @@ __global__ void __launch_bounds__(256, batch_sum_blocks<T>())
         const uint32_t nc = (uint32_t)(bm.E * bm.np * bm.np), s1 = (uint32_t)bm.nnz;
         const uint32_t* cp = reinterpret_cast<const uint32_t*>(bm.contrib);
         if constexpr (sizeof(T) == 8) {   // the single-mesh FP64 form: M/K pairs, then T
-            if (vM || vK)
-                segsum8_warp<NP, STEPS, 1, double>(k0, k1, nc, 0u, s1, bm.seg_head, cp, sym, VM, VK, VT, vM, vK, vT,
-                                                   lane);
-            if (vT) {
-                bool tf = false;
-                if constexpr (NP == 3 || NP == 4) tf = bm.type == 0 || bm.type == 3;   // P1: T as factors
-                if (tf)
-                    segsum8_warp<NP, STEPS, 2, double, true>(k0, k1, nc, 0u, s1, bm.seg_head, cp, sym, VM, VK, VT, vM,
-                                                             vK, vT, lane);
-                else
+            bool f = false;   // P1 simplices: the factored element matrices
+            if constexpr (NP == 3 || NP == 4) f = bm.type == 0 || bm.type == 3;
+            const double* gram = bm.gram64;
+            if (f) {
+                if (vM || vK)
+                    segsum8_warp<NP, STEPS, 1, double, true>(k0, k1, nc, 0u, s1, bm.seg_head, cp, sym, VM, VK, VT,
+                                                             gram, vM, vK, vT, lane);
+                if (vT)
+                    segsum8_warp<NP, STEPS, 2, double, true>(k0, k1, nc, 0u, s1, bm.seg_head, cp, sym, VM, VK, VT,
+                                                             gram, vM, vK, vT, lane);
+            } else {
+                if (vM || vK)
+                    segsum8_warp<NP, STEPS, 1, double, false>(k0, k1, nc, 0u, s1, bm.seg_head, cp, sym, VM, VK, VT,
+                                                              nullptr, vM, vK, vT, lane);
+                if (vT)
                     segsum8_warp<NP, STEPS, 2, double, false>(k0, k1, nc, 0u, s1, bm.seg_head, cp, sym, VM, VK, VT,
-                                                              vM, vK, vT, lane);
+                                                              nullptr, vM, vK, vT, lane);
             }
         } else {
             segsum_warp<NP, T, STEPS>(k0, k1, nc, 0u, s1, reinterpret_cast<const uint4*>(bm.seg_head), cp, sym, VM,
@@ -632,13 +663,13 @@ int launch_steps(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM
 // triangle mesh), 4 up to 32 (the tetrahedral meshes), 5 any
 template <int NP, typename T>
 int launch_np(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s,
-              int nsm, int64_t s0, int64_t s1) {
+              int nsm, int64_t s0, int64_t s1, bool p1f) {
     if constexpr (sizeof(T) == 8) {
         // eight contributions per lane: scan strides for the longest segment
-        if (m.max_seg <= 9) return launch_steps8<NP, 1>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
-        if (m.max_seg <= 25) return launch_steps8<NP, 2>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
-        if (m.max_seg <= 57) return launch_steps8<NP, 3>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
-        return launch_steps8<NP, 5>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+        if (m.max_seg <= 9) return launch_steps8<NP, 1>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1, p1f);
+        if (m.max_seg <= 25) return launch_steps8<NP, 2>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1, p1f);
+        if (m.max_seg <= 57) return launch_steps8<NP, 3>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1, p1f);
+        return launch_steps8<NP, 5>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1, p1f);
     }
     if (m.max_seg <= 8) return launch_steps<NP, T, 2>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
     if (m.max_seg <= 32) return launch_steps<NP, T, 4>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
@@ -647,7 +678,7 @@ int launch_np(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T
 
 template <typename T>
 int run(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, T* vT, cudaStream_t s, int64_t s0,
-        int64_t s1) {
+        int64_t s1, bool p1f) {
     if (s1 < 0) s1 = m.nnz;
     if (s0 < 0 || s0 > s1 || s1 > m.nnz) return fail(FEM_EINVAL, "slot range out of bounds");
     if (m.nnz <= 0 || s1 == s0) return FEM_OK;
@@ -655,11 +686,11 @@ int run(const fem_mesh& m, const T* VM, const T* VK, const T* VT, T* vM, T* vK, 
     FEM_CUDA_TRY(cudaGetDevice(&dev));
     FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     switch (m.np) {
-        case 3: return launch_np<3, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
-        case 4: return launch_np<4, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
-        case 6: return launch_np<6, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
-        case 10: return launch_np<10, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
-        case 20: return launch_np<20, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1);
+        case 3: return launch_np<3, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1, p1f);
+        case 4: return launch_np<4, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1, p1f);
+        case 6: return launch_np<6, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1, p1f);
+        case 10: return launch_np<10, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1, p1f);
+        case 20: return launch_np<20, T>(m, VM, VK, VT, vM, vK, vT, s, nsm, s0, s1, p1f);
     }
     return fail(FEM_EINVAL, "unsupported n_p");
 }
@@ -686,13 +717,14 @@ template int batch_scatter_launch<float>(const BatchItem*, int, const BatchMesh*
 template int batch_scatter_launch<double>(const BatchItem*, int, const BatchMesh*, int, int, cudaStream_t);
 
 int scatter_fp64(const fem_mesh& m, const double* VM, const double* VK, const double* VT, double* vM, double* vK,
-                 double* vT, cudaStream_t s, int64_t s0, int64_t s1) {
-    return run<double>(m, VM, VK, VT, vM, vK, vT, s, s0, s1);
+                 double* vT, bool p1f, cudaStream_t s, int64_t s0, int64_t s1) {
+    if (p1f && !p1_factored(m)) return fail(FEM_EINVAL, "factored element matrices of a mesh that has none");
+    return run<double>(m, VM, VK, VT, vM, vK, vT, s, s0, s1, p1f);
 }
 
 int scatter_fp32(const fem_mesh& m, const float* VM, const float* VK, const float* VT, float* vM, float* vK,
                  float* vT, cudaStream_t s, int64_t s0, int64_t s1) {
-    return run<float>(m, VM, VK, VT, vM, vK, vT, s, s0, s1);
+    return run<float>(m, VM, VK, VT, vM, vK, vT, s, s0, s1, false);
 }
 
 

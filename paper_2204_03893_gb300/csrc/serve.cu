@@ -197,6 +197,7 @@ size_t mesh_estimate(const fem_mesh_desc& d, int prec) {
     b += m2 * 4 * 4 + E * np * 4;         // col_idx and seg_ptr (nnz <= m2), contrib, slot, inc
     b += (m2 / 32 + 2) * 8;               // segment heads per group of 32 contributions
     b += esz_of(prec) * E * (np * (np + 1) + np * np) + n * 8;   // V scratch, u
+    if (np == (size_t)d.dim + 1) b += E * np * (np + 1) / 2 * 8;   // P1: the elements' Gram matrices
     return b + 4096;                      // rounding of small buffers
 }
 
