@@ -369,7 +369,7 @@ def fp64_element_ops(d: int, p: int, kind: str, n: int):
 def measure_setup_kernels(F, torch, wl, stream, peak_gbs):
     """The once-per-mesh phases timed on the device (CUDA events on the
     stream): the geometry cache (recomputed by fem_mesh_set_conductivity,
-    which runs the geometry kernel alone) and the symbolic phase (all its
+    which runs the geometry kernel and, for P1, the Gram kernel) and the symbolic phase (all its
     kernels on a fresh mesh handle; the span includes the host's read-back
     of nnz in the middle), each with its compulsory bytes."""
     from paper_2204_03893_gb300.torch_api import FemMesh
@@ -388,8 +388,11 @@ def measure_setup_kernels(F, torch, wl, stream, peak_gbs):
         b.record(stream)
         torch.cuda.synchronize()
         ms = a.elapsed_time(b)
-        # vertex rows of conn, the vertices' coordinates, both caches written
+        # vertex rows of conn, the vertices' coordinates, both caches written;
+        # P1 simplices: A read back and the elements' Gram matrices written
         gb = E * (4 * (d + 1) + 8 * d * (d + 1) + 8 * (1 + ns) + 4 * (1 + ns))
+        if n_p == d + 1:
+            gb += E * 8 * (ns + n_p * (n_p + 1) // 2)
         out["geometry"] = {"ms": ms, "bytes": gb, "GB/s": gb / (ms / 1e3) / 1e9, "frac_hbm": gb / (ms / 1e3) / 1e9 / peak_gbs,
                            "bytes_per_element": gb / E}
         a.record(stream)
