@@ -118,8 +118,10 @@ typedef struct fem_mesh fem_mesh;
  * step 3; Algorithm 2; Section 5: W and b depend only on the mesh):
  * an FP64 cache for FEM_FP64, and an FP32 cache computed in FP32 with an FP64
  * recomputation for elements whose condition estimate ||B||_F^d/|det B|
- * exceeds 1e3.  Returns FEM_EDEGENERATE if an element is degenerate.
- * Synchronises `stream` before returning. */
+ * exceeds 1e3.  P1 meshes also keep each element's Gram matrix G A_e G^T
+ * (G the constant reference gradients; n_sym FP64 values per element), the
+ * part of K_e that does not change with u.  Returns FEM_EDEGENERATE if an
+ * element is degenerate.  Synchronises `stream` before returning. */
 int fem_mesh_create(const fem_mesh_desc* desc, void* stream, fem_mesh** out);
 int fem_mesh_destroy(fem_mesh* mesh);
 
@@ -200,7 +202,8 @@ int fem_assemble_all(fem_mesh* mesh, const fem_coeff* k, const void* u, int prec
  * ranges, batches, served requests).  c: d x d row-major, symmetric and
  * positive definite (FEM_EINVAL otherwise; checked on the host), or NULL
  * for the identity (the isotropic default).  Recomputes the mesh's geometry
- * cache on `stream` and waits for it; the pattern is kept; element matrices
+ * cache (and, for P1, the elements' Gram matrices, which include c) on
+ * `stream` and waits for it; the pattern is kept; element matrices
  * formed earlier must be formed again before fem_sum_elements. */
 int fem_mesh_set_conductivity(fem_mesh* mesh, const double* c, void* stream);
 
