@@ -357,7 +357,15 @@ def fp64_element_ops(d: int, p: int, kind: str, n: int):
     n_q = {(2, 1): 3, (2, 2): 6, (2, 3): 12, (3, 1): 4, (3, 2): 11, (3, 3): 24}[(d, p)]
     nsym = n_p * (n_p + 1) // 2
     if p == 1:
-        ops = 3 + d + n_p + n_p * (1 + lo) + n_p + 2 * n_p + 1 + (d + d * (d - 1) + (d - 1) + n_p)
+        tail = 1 + (d + d * (d - 1) + (d - 1) + n_p)   # K's factor; T's factor t_e
+        if kind == "sin":
+            # sums over sin and cos: the argument (3 + 1 FMA per point), the
+            # table-driven sin/cos (16 per point, 8 of them FMAs), the two
+            # sums (2 (n_p - 1)), s0 (4), s1 (4 + n_p FMAs)
+            ops = 3 + d + (n_p - 1) + 3 + n_p * 17 + 2 * (n_p - 1) + 4 + 4 + n_p + tail
+            fma = n_p * 9 + 1 + n_p + d * (d - 1)
+            return ops, ops + fma
+        ops = 3 + d + n_p + n_p * (1 + lo) + n_p + 2 * n_p + tail
         fma = n_p * (1 + lf) + n_p + d * (d - 1)
         return ops, ops + fma
     gemm = gemm_flops_per_element(d, p)

@@ -269,20 +269,42 @@ __device__ __forceinline__ void p1_element_fp64(int64_t e, const int* __restrict
         double su = uv[0];
 #pragma unroll
         for (int i = 1; i < NP; ++i) su += uv[i];
-        const double bsu = be * su;
-        double kq[NP], dkq[NP];
+        if constexpr (LAW == LAW_SIN) {
+            // k = a + b sin(c u) is affine in sin and k' = b c cos(c u) linear
+            // in cos, so the point sums are taken over sin and cos:
+            // s0 = n_p a w + b w sum sin, s1[j] = b c (beta w sum cos + gamma w cos_j),
+            // with the argument c u = (c beta) sum u + (c gamma) u_j
+            const double ka = k.p[0], kb = k.p[1], kc = k.p[2];
+            const double cga = kc * ga, xb = (kc * be) * su;
+            double sn[NP], co[NP];
 #pragma unroll
-        for (int j = 0; j < NP; ++j) kq[j] = law64<LAW>(k, fma(ga, uv[j], bsu), dkq[j], tab);
-        double sk = kq[0], sd = dkq[0];
+            for (int j = 0; j < NP; ++j) sincos_tab(fma(cga, uv[j], xb), tab, sn[j], co[j]);
+            double ss = sn[0], sc = co[0];
 #pragma unroll
-        for (int j = 1; j < NP; ++j) {
-            sk += kq[j];
-            sd += dkq[j];
+            for (int j = 1; j < NP; ++j) {
+                ss += sn[j];
+                sc += co[j];
+            }
+            s0 = fma(w * kb, ss, (NP * w) * ka);
+            const double bc = kb * kc, g1 = gw * bc, g0 = (bw * bc) * sc;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) s1[j] = fma(g1, co[j], g0);
+        } else {
+            const double bsu = be * su;
+            double kq[NP], dkq[NP];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) kq[j] = law64<LAW>(k, fma(ga, uv[j], bsu), dkq[j], tab);
+            double sk = kq[0], sd = dkq[0];
+#pragma unroll
+            for (int j = 1; j < NP; ++j) {
+                sk += kq[j];
+                sd += dkq[j];
+            }
+            s0 = w * sk;
+            const double bws = bw * sd;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) s1[j] = fma(gw, dkq[j], bws);
         }
-        s0 = w * sk;
-        const double bws = bw * sd;
-#pragma unroll
-        for (int j = 0; j < NP; ++j) s1[j] = fma(gw, dkq[j], bws);
     } else {
 #pragma unroll
         for (int j = 0; j < NP; ++j) s1[j] = 0.0;
