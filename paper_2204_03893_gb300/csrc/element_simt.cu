@@ -220,8 +220,8 @@ __global__ void __launch_bounds__(BT) element_simt_kernel(const int* __restrict_
 //     s_e with s_e[j] = sum_q w_q k'(u_q) phi_q[j];
 //   - M_e as its diagonal and off-diagonal value (the rules are symmetric in
 //     the vertices, so sum_q w_q phi_q phi_q^T takes only these two).
-// Tetrahedra need 122 FP64 operations per element with the sine law
-// (mostly the law at four points) against ~780 for the general product,
+// Tetrahedra need 114 FP64 operations per element with the sine law
+// (mostly sin/cos at four points) against ~780 for the general product,
 // which matters because the FP64 pipe, not HBM, bounds the FP64 path on
 // this part.
 //
