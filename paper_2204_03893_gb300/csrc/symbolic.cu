@@ -7,8 +7,8 @@
 // device by sorting the keys (row, col) = (conn[e][i], conn[e][j]) of every
 // element entry c = (e n_p + i) n_p + j:
 //   1. counting sort of the (e, i) incidences by row (integer atomics for
-//      the counts, then each row's list sorted ascending so that the order
-//      does not depend on atomic timing);
+//      the counts, then each row's list sorted ascending, by ranks, so that
+//      the order does not depend on atomic timing);
 //   2. per row, a stable counting sort of its n_p * |incidences| entries by
 //      column (ties keep ascending c), one warp per row: the row's distinct
 //      columns by repeated warp minima, a count per column, then the entries
@@ -127,17 +127,57 @@ __global__ void inc_fill(const int* __restrict__ conn, int64_t m, const int* __r
     }
 }
 
-__global__ void inc_sort(const int* __restrict__ inc_ptr, int64_t n, int* __restrict__ inc) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        int a = inc_ptr[r], b = inc_ptr[r + 1];
-        for (int i = a + 1; i < b; ++i) {
-            int v = inc[i];
-            int j = i - 1;
-            while (j >= a && inc[j] > v) {
-                inc[j + 1] = inc[j];
-                --j;
+// Each row's incidences ascending, one warp per row: the keys (k = e n_p + i)
+// are distinct, so an entry's position is the number of smaller keys.  The
+// lanes hold up to IS_MAX / 32 keys each in registers, count their ranks
+// against every key by shuffles, then store; longer rows (more than IS_MAX
+// incident elements) fall back to an insertion sort by lane 0.
+constexpr int IS_PER_LANE = 8, IS_MAX = 32 * IS_PER_LANE;
+
+__global__ void __launch_bounds__(256) inc_sort(const int* __restrict__ inc_ptr, int64_t n, int* __restrict__ inc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += nwarps) {
+        const int a = inc_ptr[r], b = inc_ptr[r + 1], L = b - a;
+        if (L <= 1) continue;
+        if (L <= 32) {   // the common case: one key per lane
+            const int v = lane < L ? inc[a + lane] : INT_MAX;
+            int rank = 0;
+            for (int m = 0; m < L; ++m) rank += __shfl_sync(0xffffffffu, v, m) < v ? 1 : 0;
+            __syncwarp();
+            if (lane < L) inc[a + rank] = v;
+        } else if (L <= IS_MAX) {
+            int v[IS_PER_LANE], rank[IS_PER_LANE];
+#pragma unroll
+            for (int t = 0; t < IS_PER_LANE; ++t) {
+                const int i = t * 32 + lane;
+                v[t] = i < L ? inc[a + i] : INT_MAX;
+                rank[t] = 0;
             }
-            inc[j + 1] = v;
+            const int chunks = (L + 31) >> 5;
+#pragma unroll
+            for (int c = 0; c < IS_PER_LANE; ++c) {
+                if (c >= chunks) break;   // warp-uniform
+                for (int m = 0; m < 32; ++m) {
+                    const int o = __shfl_sync(0xffffffffu, v[c], m);
+#pragma unroll
+                    for (int t = 0; t < IS_PER_LANE; ++t) rank[t] += o < v[t] ? 1 : 0;
+                }
+            }
+            __syncwarp();   // every key is in registers before any is stored
+#pragma unroll
+            for (int t = 0; t < IS_PER_LANE; ++t)
+                if (t * 32 + lane < L) inc[a + rank[t]] = v[t];
+        } else if (lane == 0) {
+            for (int i = a + 1; i < b; ++i) {
+                const int v = inc[i];
+                int j = i - 1;
+                while (j >= a && inc[j] > v) {
+                    inc[j + 1] = inc[j];
+                    --j;
+                }
+                inc[j + 1] = v;
+            }
         }
     }
 }
@@ -398,7 +438,7 @@ int symbolic_run(fem_mesh& m, cudaStream_t s) {
     inc_count<<<grid_for(m1, 256), 256, 0, s>>>(conn, m1, cnt.as<int>());
     if ((rc = scan_exclusive(cnt.as<int>(), n, m.inc_ptr.as<int>(), s))) return rc;
     inc_fill<<<grid_for(m1, 256), 256, 0, s>>>(conn, m1, m.inc_ptr.as<int>(), fill.as<int>(), m.inc.as<int>());
-    inc_sort<<<grid_for(n, 128), 128, 0, s>>>(m.inc_ptr.as<int>(), n, m.inc.as<int>());
+    inc_sort<<<grid_for(n * 32, 256, 152 * 64), 256, 0, s>>>(m.inc_ptr.as<int>(), n, m.inc.as<int>());
     // rows by counting sort; the few rows it leaves (marked -1) by rank sort
     FEM_CUDA_TRY(cudaMemsetAsync(row_nnz.ptr, 0xff, row_nnz.bytes, s));
     FEM_CUDA_TRY(cudaMemsetAsync(cnt.ptr, 0, sizeof(int), s));   // overflow count (the incidence counts are scanned)
