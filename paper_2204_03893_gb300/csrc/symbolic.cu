@@ -197,11 +197,12 @@ constexpr int RS_WARPS = 8;
 //      among themselves with __match_any_sync, after the entries of earlier
 //      chunks (stable).
 // Rows with more than RC_CAP entries or RC_UCAP distinct columns are left to
-// a rank sort (row_sort_rest, the same order).
-constexpr int RC_WARPS = 4;
-constexpr int RC_CAP = 768;    // staged entries per warp
-constexpr int RC_UCAP = 384;   // distinct columns per warp
-
+// a rank sort (row_sort_rest, the same order).  The staging takes shared
+// memory per warp, and the sort waits on its gathers of conn: the launch
+// picks the smallest staging that holds the mesh's longest row, so that
+// more warps share an SM (a P1 tetrahedral mesh: rows of at most 4 x 24
+// entries, 8 warps of 128 entries per block instead of 4 of 768).
+template <int RC_WARPS, int RC_CAP, int RC_UCAP>
 __global__ void __launch_bounds__(RC_WARPS * 32) row_sort_count(const int* __restrict__ conn, int np,
                                                                 const int* __restrict__ inc_ptr,
                                                                 const int* __restrict__ inc, int64_t n,
@@ -383,6 +384,15 @@ __global__ void __launch_bounds__(256) row_finish(const int* __restrict__ conn, 
 
 __global__ void set_last(int* p, int64_t idx, int v) { p[idx] = v; }
 
+// the largest incidence count of a row (warp maximum, one atomic per warp)
+__global__ void inc_max(const int* __restrict__ inc_ptr, int64_t n, int* __restrict__ out) {
+    int best = 0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        best = max(best, inc_ptr[r + 1] - inc_ptr[r]);
+    best = __reduce_max_sync(0xffffffffu, best);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+}
+
 // longest segment seg_ptr[s+1] - seg_ptr[s] (warp maximum, one atomic per warp)
 __global__ void seg_max(const int* __restrict__ seg_ptr, int64_t nnz, int* __restrict__ out) {
     int best = 0;
@@ -442,8 +452,24 @@ int symbolic_run(fem_mesh& m, cudaStream_t s) {
     // rows by counting sort; the few rows it leaves (marked -1) by rank sort
     FEM_CUDA_TRY(cudaMemsetAsync(row_nnz.ptr, 0xff, row_nnz.bytes, s));
     FEM_CUDA_TRY(cudaMemsetAsync(cnt.ptr, 0, sizeof(int), s));   // overflow count (the incidence counts are scanned)
-    row_sort_count<<<grid_for(n, RC_WARPS, 152 * 64), RC_WARPS * 32, 0, s>>>(
-        conn, np, m.inc_ptr.as<int>(), m.inc.as<int>(), n, m.contrib.as<int>(), row_nnz.as<int>(), cnt.as<int>());
+    {
+        // the longest row (entries = n_p x incidences) picks the staging
+        FEM_CUDA_TRY(cudaMemsetAsync(fill.ptr, 0, sizeof(int), s));
+        inc_max<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(m.inc_ptr.as<int>(), n, fill.as<int>());
+        FEM_CUDA_TRY(cudaGetLastError());
+        int maxinc = 0;
+        FEM_CUDA_TRY(cudaMemcpyAsync(&maxinc, fill.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA_TRY(cudaStreamSynchronize(s));
+        const int64_t maxL = (int64_t)np * maxinc;
+        auto sort_rows = [&](auto kern, int warps) {
+            kern<<<grid_for(n, warps, 152 * 64), warps * 32, 0, s>>>(conn, np, m.inc_ptr.as<int>(), m.inc.as<int>(), n,
+                                                                    m.contrib.as<int>(), row_nnz.as<int>(),
+                                                                    cnt.as<int>());
+        };
+        if (maxL <= 128) sort_rows(row_sort_count<8, 128, 64>, 8);
+        else if (maxL <= 256) sort_rows(row_sort_count<8, 256, 128>, 8);
+        else sort_rows(row_sort_count<4, 768, 384>, 4);
+    }
     FEM_CUDA_TRY(cudaGetLastError());
     int left = 0;
     FEM_CUDA_TRY(cudaMemcpyAsync(&left, cnt.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
