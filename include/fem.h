@@ -158,7 +158,10 @@ int fem_symbolic(fem_mesh* mesh, void* stream, fem_csr_pattern* out);
 int fem_copy_pattern(fem_mesh* mesh, int32_t* d_row_ptr, int32_t* d_col_idx, void* stream);
 
 /* Copies the element-entry -> slot map (n_elems * n_p^2 int32, entry
- * c = (e n_p + i) n_p + j) to d_slot (device, caller-owned). */
+ * c = (e n_p + i) n_p + j) to d_slot (device, caller-owned).  Reassembly
+ * does not read the map; the mesh builds it on the first call that needs
+ * it (this one or fem_boundary_facets), from the sorted entries, and keeps
+ * it (n_elems * n_p^2 int32 of device memory). */
 int fem_get_slot_map(fem_mesh* mesh, int32_t* d_slot, void* stream);
 
 /* ------------------------------------------------------------- numeric */

@@ -235,6 +235,7 @@ int boundary_setup(fem_mesh& m, cudaStream_t s) {
     if (m.have_boundary) return FEM_OK;
     int rc = facet_tables_init();
     if (rc) return rc;
+    if ((rc = slot_map_build(m, s))) return rc;   // the facet rows are scattered through it
     const int nv = m.d + 1;
     const int64_t mf = m.E * nv;
     DevBuf flag, pos, cnt, fill;

@@ -506,6 +506,8 @@ int fem_copy_pattern(fem_mesh* m, int32_t* d_row_ptr, int32_t* d_col_idx, void* 
 int fem_get_slot_map(fem_mesh* m, int32_t* d_slot, void* stream) {
     if (!m || !d_slot) return fail(FEM_EINVAL, "NULL argument");
     if (!m->have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    int rc = slot_map_build(*m, static_cast<cudaStream_t>(stream));
+    if (rc) return rc;
     FEM_CUDA_TRY(cudaMemcpyAsync(d_slot, m->slot.ptr, sizeof(int32_t) * (size_t)(m->E * m->np * m->np),
                                  cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
     return FEM_OK;

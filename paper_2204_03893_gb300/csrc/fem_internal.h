@@ -71,6 +71,7 @@ struct fem_mesh {
     bool have_pattern = false;
     int64_t nnz = -1;
     fem::DevBuf row_ptr, col_idx, seg_ptr, contrib, slot, inc_ptr, inc;
+    bool have_slot = false;             // slot (element entry -> slot) built (slot_map_build)
     // per group of 32 consecutive contributions k: x = bit l set iff
     // contribution 32k+l is the first of its slot, y = slot of contribution 32k
     fem::DevBuf seg_head;               // uint2 per group
@@ -108,6 +109,7 @@ namespace fem {
 int geometry_run(fem_mesh& m, cudaStream_t s);           // fills geo64, geo32, n_flagged
 int geometry_q_run(fem_mesh& m, cudaStream_t s);         // fills geoq64, geoq32 (per-point mode)
 int symbolic_run(fem_mesh& m, cudaStream_t s);           // fills pattern and segments
+int slot_map_build(fem_mesh& m, cudaStream_t s);         // the element-entry -> slot map (once, on demand)
 int scan_exclusive(const int* in, int64_t n, int* out, cudaStream_t s);   // n ints -> n+1 prefix sums
 // boundary facets, node -> facet incidences (once; needs the pattern)
 int boundary_setup(fem_mesh& m, cudaStream_t s);

@@ -15,8 +15,8 @@
 //      placed in order (very long rows fall back to a rank sort);
 //   3. a scan of the per-row unique-column counts gives row_ptr;
 //   4. per row, one warp walks the sorted entries and numbers the column
-//      groups: col_idx, seg_ptr (first sorted position of each slot) and the
-//      slot map slot[c];
+//      groups: col_idx and seg_ptr (first sorted position of each slot); the
+//      slot map slot[c] is derived from the sorted list when first needed;
 //   5. the same walk marks, for every group of 32 consecutive sorted
 //      positions, which of them start a slot (a bit mask) and the slot of its
 //      first position: what the CSR sum reads instead of seg_ptr.
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(256) row_finish(const int* __restrict__ conn, 
                                                   const int* __restrict__ inc_ptr, const int* __restrict__ row_ptr,
                                                   const int* __restrict__ contrib, int64_t n,
                                                   int* __restrict__ col_idx, int* __restrict__ seg_ptr,
-                                                  int* __restrict__ slot, uint2* __restrict__ head) {
+                                                  uint2* __restrict__ head) {
     int lane = threadIdx.x & 31;
     int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     int np2 = np * np;
@@ -369,7 +369,6 @@ __global__ void __launch_bounds__(256) row_finish(const int* __restrict__ conn, 
             bool is_head = valid && col != prev;
             unsigned mask = __ballot_sync(0xffffffffu, is_head);
             int idx = count + __popc(mask & le) - 1;
-            if (valid) slot[c] = slot0 + idx;
             if (valid && (p & 31) == 0) head[p >> 5].y = (unsigned)(slot0 + idx);
             if (is_head) {
                 col_idx[slot0 + idx] = col;
@@ -383,6 +382,18 @@ __global__ void __launch_bounds__(256) row_finish(const int* __restrict__ conn, 
 }
 
 __global__ void set_last(int* p, int64_t idx, int v) { p[idx] = v; }
+
+// slot[c] for every element entry c: position p of the sorted list holds
+// contrib[p]; its slot is the slot of the first position of its group of 32
+// plus the heads after that position up to p
+__global__ void slot_map_kernel(const int* __restrict__ contrib, const uint2* __restrict__ head, int64_t nc,
+                                int* __restrict__ slot) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nc; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint2 h = head[p >> 5];
+        const unsigned b = (unsigned)(p & 31);
+        slot[contrib[p]] = (int)(h.y + __popc(h.x & ((2u << b) - 1u) & ~1u));
+    }
+}
 
 // the largest incidence count of a row (warp maximum, one atomic per warp)
 __global__ void inc_max(const int* __restrict__ inc_ptr, int64_t n, int* __restrict__ out) {
@@ -427,6 +438,23 @@ int scan_exclusive(const int* in, int64_t n, int* out, cudaStream_t s) {
     return FEM_OK;
 }
 
+// The element-entry -> slot map, built when first needed (the boundary
+// terms and fem_get_slot_map read it; reassembly does not).
+int slot_map_build(fem_mesh& m, cudaStream_t s) {
+    if (m.have_slot) return FEM_OK;
+    if (!m.have_pattern) return fail(FEM_ESTATE, "fem_symbolic has not run");
+    const int64_t nc = m.E * m.np * m.np;
+    int rc = buf_alloc(m.slot, sizeof(int) * (size_t)(nc + 1), s);
+    if (rc) return rc;
+    cudaGetLastError();   // clear any stale error before the launch check
+    if (nc > 0)
+        slot_map_kernel<<<grid_for(nc, 256, 152 * 64), 256, 0, s>>>(m.contrib.as<int>(), m.seg_head.as<uint2>(), nc,
+                                                                    m.slot.as<int>());
+    FEM_CUDA_TRY(cudaGetLastError());
+    m.have_slot = true;
+    return FEM_OK;
+}
+
 int symbolic_run(fem_mesh& m, cudaStream_t s) {
     const int np = m.np;
     const int64_t n = m.n, E = m.E;
@@ -438,7 +466,6 @@ int symbolic_run(fem_mesh& m, cudaStream_t s) {
     if ((rc = buf_alloc(m.inc, sizeof(int) * (size_t)(m1 + 1), s))) return rc;
     if ((rc = buf_alloc(fill, sizeof(int) * (size_t)(n + 1), s))) return rc;
     if ((rc = buf_alloc(m.contrib, sizeof(int) * (size_t)(m2 + 1), s))) return rc;
-    if ((rc = buf_alloc(m.slot, sizeof(int) * (size_t)(m2 + 1), s))) return rc;
     if ((rc = buf_alloc(row_nnz, sizeof(int) * (size_t)(n + 1), s))) return rc;
     if ((rc = buf_alloc(m.row_ptr, sizeof(int) * (size_t)(n + 1), s))) return rc;
     FEM_CUDA_TRY(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
@@ -491,8 +518,7 @@ int symbolic_run(fem_mesh& m, cudaStream_t s) {
     FEM_CUDA_TRY(cudaMemsetAsync(m.seg_head.ptr, 0, m.seg_head.bytes, s));
     row_finish<<<grid_for(n, 8, 152 * 64), 256, 0, s>>>(conn, np, m.inc_ptr.as<int>(), m.row_ptr.as<int>(),
                                                         m.contrib.as<int>(), n, m.col_idx.as<int>(),
-                                                        m.seg_ptr.as<int>(), m.slot.as<int>(),
-                                                        m.seg_head.as<uint2>());
+                                                        m.seg_ptr.as<int>(), m.seg_head.as<uint2>());
     set_last<<<1, 1, 0, s>>>(m.seg_ptr.as<int>(), nnz, (int)m2);
     FEM_CUDA_TRY(cudaGetLastError());
     // the longest segment bounds the steps of the CSR sum's warp scans
