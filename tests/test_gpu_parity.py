@@ -341,11 +341,14 @@ def test_form_and_sum_phases(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
-def test_long_rows_fallback_paths(prec):
-    """A 300-triangle fan: the centre row has 301 entries and its diagonal
-    slot 300 contributors; the symbolic phase sorts the row's 900 keys
-    without staging them in shared memory."""
-    m = mg.fan_tri(300, seed=2)
+@pytest.mark.parametrize("fan", [100, 300])
+def test_long_rows_fallback_paths(prec, fan):
+    """Triangle fans: the centre row has fan + 1 entries and its diagonal
+    slot `fan` contributors.  With 300 triangles the symbolic phase sorts
+    the centre's 300 incidences and the row's 900 keys without staging them
+    in shared memory; with 100 it ranks the incidences over several keys
+    per lane and stages the row's 300 keys."""
+    m = mg.fan_tri(fan, seed=2)
     u = mg.uniform_field(m.n_nodes, 3)
     c = mg.Coeff("poly", (1.0, 0.5, 0.25, 0.0, 0.0))
     o = orc.Oracle.of(m)
