@@ -142,15 +142,16 @@ typedef struct {
     const int32_t* d_col_idx;   /* nnz, device, owned by the mesh */
 } fem_csr_pattern;
 
-/* Builds, once per mesh, the CSR pattern and the map from element entries to
- * CSR slots by a device sort of the keys (conn[e][i], conn[e][j]) (Section 3
+/* Builds, once per mesh, the CSR pattern and the element entries of every
+ * CSR slot by a device sort of the keys (conn[e][i], conn[e][j]) (Section 3
  * step 2; the index set of nonzero entries that Algorithm 2 sums into): a
  * counting sort by row, then a per-row sort by column, stable in the element
  * entry index c = (e n_p + i) n_p + j.  Keeps on the device: row_ptr, col_idx,
- * slot[c] (CSR slot of element entry c), the segmented lists seg_ptr /
- * contrib (contributing c of every slot, ascending) and, per 32 consecutive
- * contributions, a mask of slot starts and the slot of the first (what the
- * CSR sum reads).  Idempotent. */
+ * the segmented lists seg_ptr / contrib (contributing c of every slot,
+ * ascending) and, per 32 consecutive contributions, a mask of slot starts
+ * and the slot of the first (what the CSR sum reads).  The map slot[c] from
+ * element entries to CSR slots is derived from these when first needed
+ * (fem_get_slot_map, fem_boundary_facets).  Idempotent. */
 int fem_symbolic(fem_mesh* mesh, void* stream, fem_csr_pattern* out);
 
 /* Copies the pattern into caller-owned device buffers d_row_ptr (n+1) and
